@@ -1,0 +1,68 @@
+"""Independent numpy restatement of the plane-wave basis and the antisymmetrized
+Minnesota elements for two neutrons (arXiv:1611.06765, Sec. "Single-particle basis for
+infinite matter", Sec. "Two-body interaction", Table tab:minnesotatab).
+
+TEST INFRASTRUCTURE ONLY.  Written separately from ``pnm_oracle.c`` so the two can be
+compared with each other.  Here the spin algebra is done by hand instead of with
+operator matrices: for two neutrons (P_tau = 1) the exchange form
+V = 1/2 (V_R + 1/2(1+P_s) V_T + 1/2(1-P_s) V_S)(1 - P_s) reduces, with P_s^2 = 1, to
+1/2 (V_R + V_S)(1 - P_s); its antisymmetrized momentum-space element is
+<pq|v|rs> = 1/2 [Vt(k_p-k_r) + Vt(k_p-k_s)] (d(s_p,s_r) d(s_q,s_s) - d(s_p,s_s) d(s_q,s_r))
+times momentum conservation, with Vt(q) = sum_{a=R,S} (V_a/L^3)(pi/kappa_a)^{3/2} exp(-q^2/4kappa_a).
+"""
+import math
+
+import numpy as np
+
+
+def basis(n2max):
+    """States (nx, ny, nz, s) in the shell-ordered loop order, s in units of hbar/2."""
+    r = math.isqrt(n2max)
+    out = []
+    for shell in range(n2max + 1):
+        for x in range(-r, r + 1):
+            for y in range(-r, r + 1):
+                for z in range(-r, r + 1):
+                    if x * x + y * y + z * z != shell:
+                        continue
+                    for s in (-1, 1):
+                        out.append((x, y, z, s))
+    return np.array(out, dtype=np.int64)
+
+
+def box_length(N, rho):
+    """L^3 = N / rho."""
+    return (N / rho) ** (1.0 / 3.0)
+
+
+def vtilde(q2, L, params):
+    """Sum of the R and S Gaussians in momentum space (the T term cancels for nn)."""
+    VR, kR, _VT, _kT, VS, kS, _h = params
+    L3 = L ** 3
+    return (VR / L3 * (math.pi / kR) ** 1.5 * np.exp(-q2 / (4 * kR))
+            + VS / L3 * (math.pi / kS) ** 1.5 * np.exp(-q2 / (4 * kS)))
+
+
+def v_dense(states, L, params):
+    """Full antisymmetrized <pq|v|rs> as an (n, n, n, n) array."""
+    n = len(states)
+    k = states[:, :3].astype(float) * (2 * math.pi / L)
+    s = states[:, 3]
+    P = states[:, None, :3] + states[None, :, :3]                       # (p, q)
+    cons = np.all(P[:, :, None, None, :] == P[None, None, :, :, :], axis=-1)
+    dk_pr = k[:, None, :] - k[None, :, :]                              # k_p - k_r
+    q2 = np.sum(dk_pr ** 2, axis=-1)
+    Vt = vtilde(q2, L, params)                                          # (p, r)
+    sp = s[:, None] == s[None, :]                                       # d(s_p, s_r)
+    direct = Vt[:, None, :, None]                                       # Vt(k_p-k_r): (p,_,r,_)
+    exch = Vt[:, None, None, :]                                         # Vt(k_p-k_s): (p,_,_,s)
+    spin = (sp[:, None, :, None] & sp[None, :, None, :]).astype(float) - \
+           (sp[:, None, None, :] & sp[None, :, :, None]).astype(float)
+    v = 0.5 * (direct + exch) * spin * cons
+    assert v.shape == (n, n, n, n)
+    return v
+
+
+def kinetic(states, L, hbar2_2m):
+    n2 = np.sum(states[:, :3] ** 2, axis=1).astype(float)
+    return hbar2_2m * (2 * math.pi / L) ** 2 * n2
