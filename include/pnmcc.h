@@ -1,0 +1,157 @@
+/*
+ * pnmcc.h -- C ABI of the GB300 (sm_103a) coupled-cluster doubles library for pure
+ * neutron matter with the Minnesota interaction.
+ *
+ * Method: Lietz, Novario, Jansen, Hagen, Hjorth-Jensen, "Computational Nuclear Physics
+ * and Post Hartree-Fock Methods" (arXiv:1611.06765).  Each call below names the passage
+ * of that paper which defines what it computes.
+ *
+ * Conventions for every call:
+ *   - Return value: PNM_OK (0) or a negative PNM_E* code.  No C++ exception crosses the
+ *     ABI.  pnm_last_error() returns a thread-local text for the last failure.
+ *   - Host arrays passed in are read only during the call; host output arrays are owned by
+ *     the caller and must hold the stated number of elements.  A NULL output pointer is
+ *     allowed where stated and turns the call into a size query.
+ *   - All device memory is owned by the context: allocated by pnm_create*, released by
+ *     pnm_destroy.  Work runs on the CUDA stream given at creation (NULL = the legacy
+ *     default stream) and every call that returns host data synchronises that stream.
+ *   - Energies are totals in MeV (not per particle).  Momenta are integer lattice vectors
+ *     n (k = 2 pi n / L); spins are in units of hbar/2 (-1 or +1).
+ *   - A context holds one or more independent systems (N, rho, n2max); calls taking
+ *     `sys` address one of them (0 for a single-system context).
+ */
+#ifndef PNMCC_H
+#define PNMCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PNM_OK 0
+#define PNM_EINVAL (-1)     /* bad argument: N not a closed shell, no particle states, ... */
+#define PNM_ENOMEM (-2)     /* device or host allocation failed */
+#define PNM_ECUDA (-3)      /* a CUDA runtime call failed */
+#define PNM_ENOTCONV (-4)   /* iteration cap reached before the energy change met the tolerance */
+#define PNM_EDIVERGED (-5)  /* NaN/Inf energy or residual */
+#define PNM_ETIMEOUT (-6)   /* a device-side wait ran out of its budget */
+
+typedef struct pnm_ctx pnm_ctx;
+
+/* Minnesota interaction (Sec. "Two-body interaction", Table tab:minnesotatab):
+ * V(r) = 1/2 (V_R e^{-kR r^2} + 1/2(1+Ps) V_T e^{-kT r^2} + 1/2(1-Ps) V_S e^{-kS r^2})(1 - Ps Pt).
+ * V in MeV, kappa in fm^-2, hbar2_2m in MeV fm^2.  The paper prints magnitudes; the
+ * attractive terms take V_T, V_S < 0. */
+typedef struct {
+    double VR, kR, VT, kT, VS, kS, hbar2_2m;
+} pnm_minnesota;
+
+#define PNM_PREC_FP64 0   /* every step in FP64 */
+#define PNM_PREC_BF16X3 2 /* pp ladder as hi/lo BF16 products on tcgen05 (FP32 accumulate),
+                             other contractions in FP32, denominators/energy/residual FP64,
+                             then `refine_sweeps` FP64 iterations */
+
+#define PNM_INIT_MBPT2 0  /* t = <ab|v|ij> / eps_ij^ab, Eq. (ccdGuess) */
+#define PNM_INIT_ZERO 1   /* t = 0 (the first update then gives MBPT2) */
+#define PNM_INIT_KEEP 2   /* start from the amplitudes currently held (pnm_set_amplitudes) */
+
+/* Options of the CCD iteration (Eq. ccd3 with mixing and the stopping rule of Sec.
+ * "Developing a numerical project"). */
+typedef struct {
+    int precision;        /* PNM_PREC_* */
+    double mix_alpha;     /* t = alpha t_new + (1-alpha) t_old, alpha in (0,1] */
+    double tol_dE;        /* stop when |dE^(n+1) - dE^(n)| < tol_dE (total, MeV) */
+    double tol_dE_per_N;  /* and/or when |dE^(n+1) - dE^(n)| / N < tol_dE_per_N (<= 0: unused) */
+    int max_iter;         /* iteration cap (PNM_ENOTCONV when reached) */
+    int refine_sweeps;    /* FP64 sweeps after a mixed-precision solve */
+    int init;             /* PNM_INIT_* */
+    int host_loop;        /* 0: device-side loop in one CUDA graph; 1: host checks each iteration */
+} pnm_solve_opts;
+
+/* Fills the defaults of the small FP64 workload: FP64, alpha 0.5, tol 1e-10 MeV,
+ * max_iter 500, no refinement, MBPT2 start, device-side loop. */
+void pnm_default_opts(pnm_solve_opts *opts);
+
+/* Build one system: the basis of Sec. "Single-particle basis for infinite matter" (k =
+ * 2 pi n/L, L^3 = N/rho, n^2 <= n2max, shell order of the state loop in Sec. "Developing a
+ * CCD code", first N states are holes), its direct (P, S_z) and cross channels, the
+ * antisymmetrized Minnesota blocks and the HF energies eps_p = f_pp (Eq. Hnormalorder).
+ * Runs on the GPU.  PNM_EINVAL if N does not close a shell or leaves no particle state.
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out receives the context. */
+int pnm_create(int N, double rho, int n2max, const pnm_minnesota *params, void *stream,
+               pnm_ctx **out);
+
+/* Build n independent systems in one context; their channels are grouped so every
+ * iteration kernel covers all systems in one launch.  Arrays have n entries. */
+int pnm_create_batch(int n, const int *N, const double *rho, const int *n2max,
+                     const pnm_minnesota *params, void *stream, pnm_ctx **out);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+int pnm_destroy(pnm_ctx *ctx);
+
+/* Number of systems held by the context. */
+int pnm_num_systems(const pnm_ctx *ctx, int *n);
+
+/* Single-particle basis of system `sys`: sizes, and (nullable) n_x, n_y, n_z, s per state
+ * (4 int8 per state, state-major) and the HF energies (n_sp doubles). */
+int pnm_basis(const pnm_ctx *ctx, int sys, int *n_sp, int *n_holes, int8_t *nxyzs,
+              double *eps_hf);
+
+/* Channel tables of system `sys` as built on the GPU.
+ * kind 0: direct channels (P = n_p + n_q, S_z = s_p + s_q) holding restricted hh pairs
+ *         i<j and pp pairs a<b (both non-empty); per channel keys[c], sizes[2c] = n_hh,
+ *         sizes[2c+1] = n_pp; pairs = all hh pairs then all pp pairs, 2 ints each,
+ *         channel-major, lexicographic inside a channel.
+ * kind 1: cross channels (n_p - n_q, s_p - s_q) with ordered ph rows (a,i) and hp columns
+ *         (k,c); sizes[2x] = n_ph, sizes[2x+1] = n_hp; pairs = all (a,i) then all (k,c).
+ * key = (((Px+m)*M + (Py+m))*M + (Pz+m))*3 + (Sz+2)/2, m = 2 floor(sqrt(n2max)), M = 2m+1.
+ * Sec. "Developing a CCD code" (direct T and cross X channels).  Any output may be NULL;
+ * *n_chan and *n_pairs (total pair count) are always written. */
+int pnm_channels(const pnm_ctx *ctx, int sys, int kind, int *n_chan, int *n_pairs,
+                 int32_t *keys, int32_t *sizes, int32_t *pairs);
+
+/* Antisymmetrized <pq|v|rs> of system `sys` (MeV), evaluated by the same device code
+ * that fills the blocks.  Sec. "Two-body interaction". */
+int pnm_v_element(const pnm_ctx *ctx, int sys, int p, int q, int r, int s, double *out);
+
+/* Reference energy E_ref = sum_i h0_ii + 1/2 sum_ij <ij|v|ij> (Sec. "Normal-ordered
+ * Hamiltonian", the E_Ref expression).  One value per system (e_ref[n_systems]). */
+int pnm_eref(const pnm_ctx *ctx, double *e_ref);
+
+/* Second-order correlation energy, Eq. (ccdGuess) and the energy below it, computed as a
+ * fused pass over the direct channels.  One value per system. */
+int pnm_mbpt2(pnm_ctx *ctx, double *dE);
+
+/* Solve the CCD equations (Eq. ccd3 in the intermediate form of Sec. "Developing a CCD
+ * code", energy Eq. ccdcorr).  Per system outputs (nullable): dE (correlation energy),
+ * iters (updates made), resid (2-norm of the last residual over restricted amplitudes).
+ * Returns PNM_ENOTCONV / PNM_EDIVERGED as described above; outputs are still written. */
+int pnm_ccd_solve(pnm_ctx *ctx, const pnm_solve_opts *opts, double *dE, int *iters,
+                  double *resid);
+
+/* Energy after each update of the last solve: hist[0] is the start, hist[k] after k
+ * updates.  *n receives the number of entries (<= cap) for system `sys`. */
+int pnm_energy_history(const pnm_ctx *ctx, int sys, double *hist, int cap, int *n);
+
+/* Number of restricted amplitudes (a<b, i<j, both pairs in one direct channel) of
+ * system `sys`, and (nullable) their labels a, b, i, j in the library's order. */
+int pnm_amplitude_labels(const pnm_ctx *ctx, int sys, size_t *n, int32_t *abij);
+
+/* Copy restricted amplitudes (FP64, library order) of system `sys` to / from the host.
+ * n must equal the count of pnm_amplitude_labels.  Checkpoint and training-data path. */
+int pnm_get_amplitudes(const pnm_ctx *ctx, int sys, double *t, size_t n);
+int pnm_set_amplitudes(pnm_ctx *ctx, int sys, const double *t, size_t n);
+
+/* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
+ * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement. */
+int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
+
+/* Thread-local text describing the last failure of a pnm_* call on this thread. */
+const char *pnm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNMCC_H */

@@ -1,0 +1,147 @@
+"""GB300-native coupled-cluster doubles for pure neutron matter (arXiv:1611.06765).
+
+``Context`` wraps one ``pnm_ctx`` of the C library: it marshals arguments to the
+``pnm_*`` calls of ``include/pnmcc.h`` and returns numpy arrays.  All work happens in the
+library's CUDA kernels; importing this package does not need a GPU, calling it does.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PNM_EDIVERGED, PNM_ENOTCONV, PNM_INIT_KEEP, PNM_INIT_MBPT2, PNM_INIT_ZERO,
+                   PNM_PREC_BF16X3, PNM_PREC_FP64, PnmError)
+
+__all__ = ["Context", "MINNESOTA", "PnmError", "PNM_PREC_FP64", "PNM_PREC_BF16X3",
+           "PNM_INIT_MBPT2", "PNM_INIT_ZERO", "PNM_INIT_KEEP", "PNM_ENOTCONV", "PNM_EDIVERGED"]
+
+# V_R, kappa_R, V_T, kappa_T, V_S, kappa_S (Table tab:minnesotatab, attractive T and S) and
+# hbar^2/2m in MeV fm^2.
+MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Context:
+    """One or more (N, rho, n2max) systems built on the GPU by ``pnm_create_batch``."""
+
+    def __init__(self, N, rho, n2max, params=MINNESOTA, stream=None):
+        L = _lib.load()
+        Ns = np.atleast_1d(np.asarray(N, dtype=np.int32))
+        rhos = np.atleast_1d(np.asarray(rho, dtype=np.float64))
+        n2 = np.atleast_1d(np.asarray(n2max, dtype=np.int32))
+        n = max(len(Ns), len(rhos), len(n2))
+        Ns, rhos, n2 = (np.ascontiguousarray(np.broadcast_to(a, (n,))) for a in (Ns, rhos, n2))
+        self.N, self.rho, self.n2max = Ns.copy(), rhos.copy(), n2.copy()
+        p = _lib.pnm_minnesota(*[float(x) for x in params])
+        h = C.c_void_p()
+        _lib.check(L.pnm_create_batch(n, Ns.ctypes.data_as(C.POINTER(C.c_int)),
+                                      rhos.ctypes.data_as(C.POINTER(C.c_double)),
+                                      n2.ctypes.data_as(C.POINTER(C.c_int)), C.byref(p),
+                                      C.c_void_p(stream) if stream else None, C.byref(h)))
+        self._h = h
+        self.nsys = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().pnm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ queries
+    def basis(self, sys=0):
+        L = _lib.load()
+        nsp, nh = C.c_int(), C.c_int()
+        _lib.check(L.pnm_basis(self._h, sys, C.byref(nsp), C.byref(nh), None, None))
+        nv = np.zeros((nsp.value, 4), np.int8)
+        eps = np.zeros(nsp.value)
+        _lib.check(L.pnm_basis(self._h, sys, C.byref(nsp), C.byref(nh), _ptr(nv), _ptr(eps)))
+        return nv, eps, nh.value
+
+    def channels(self, sys=0, kind=0):
+        L = _lib.load()
+        nc, npairs = C.c_int(), C.c_int()
+        _lib.check(L.pnm_channels(self._h, sys, kind, C.byref(nc), C.byref(npairs), None, None, None))
+        keys = np.zeros(nc.value, np.int32)
+        sizes = np.zeros((nc.value, 2), np.int32)
+        pairs = np.zeros((npairs.value, 2), np.int32)
+        _lib.check(L.pnm_channels(self._h, sys, kind, C.byref(nc), C.byref(npairs), _ptr(keys),
+                                  _ptr(sizes), _ptr(pairs)))
+        return keys, sizes, pairs
+
+    def v(self, p, q, r, s, sys=0):
+        out = C.c_double()
+        _lib.check(_lib.load().pnm_v_element(self._h, sys, p, q, r, s, C.byref(out)))
+        return out.value
+
+    def eref(self):
+        out = np.zeros(self.nsys)
+        _lib.check(_lib.load().pnm_eref(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def mbpt2(self):
+        out = np.zeros(self.nsys)
+        _lib.check(_lib.load().pnm_mbpt2(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    # -------------------------------------------------------------------- solve
+    def solve(self, precision=PNM_PREC_FP64, alpha=0.5, tol=1e-10, tol_per_N=0.0, max_iter=500,
+              refine_sweeps=0, init=PNM_INIT_MBPT2, host_loop=False, allow=()):
+        """pnm_ccd_solve; returns (dE[nsys], iters[nsys], resid[nsys], rc)."""
+        L = _lib.load()
+        o = _lib.pnm_solve_opts()
+        L.pnm_default_opts(C.byref(o))
+        o.precision, o.mix_alpha, o.tol_dE, o.tol_dE_per_N = precision, alpha, tol, tol_per_N
+        o.max_iter, o.refine_sweeps, o.init, o.host_loop = max_iter, refine_sweeps, init, int(host_loop)
+        dE = np.zeros(self.nsys)
+        it = np.zeros(self.nsys, np.int32)
+        res = np.zeros(self.nsys)
+        rc = L.pnm_ccd_solve(self._h, C.byref(o), dE.ctypes.data_as(C.POINTER(C.c_double)),
+                             it.ctypes.data_as(C.POINTER(C.c_int)),
+                             res.ctypes.data_as(C.POINTER(C.c_double)))
+        _lib.check(rc, allow=allow)
+        return dE, it, res, rc
+
+    def history(self, sys=0, cap=100000):
+        n = C.c_int()
+        buf = np.zeros(cap)
+        _lib.check(_lib.load().pnm_energy_history(self._h, sys, buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                                  cap, C.byref(n)))
+        return buf[: n.value].copy()
+
+    def amplitude_labels(self, sys=0):
+        L = _lib.load()
+        n = C.c_size_t()
+        _lib.check(L.pnm_amplitude_labels(self._h, sys, C.byref(n), None))
+        out = np.zeros((n.value, 4), np.int32)
+        _lib.check(L.pnm_amplitude_labels(self._h, sys, C.byref(n), _ptr(out)))
+        return out
+
+    def get_amplitudes(self, sys=0):
+        n = C.c_size_t()
+        _lib.check(_lib.load().pnm_amplitude_labels(self._h, sys, C.byref(n), None))
+        t = np.zeros(n.value)
+        _lib.check(_lib.load().pnm_get_amplitudes(self._h, sys, _ptr(t), n.value))
+        return t
+
+    def set_amplitudes(self, t, sys=0):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        _lib.check(_lib.load().pnm_set_amplitudes(self._h, sys, _ptr(t), t.size))
+
+    def timings(self):
+        ms = np.zeros(5)
+        _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 5))
+        return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4])

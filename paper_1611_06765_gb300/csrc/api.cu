@@ -1,0 +1,336 @@
+// api.cu -- the extern "C" entry points declared in include/pnmcc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "pnm_context.cuh"
+
+static thread_local std::string g_last_error;
+
+void pnm_set_error(int code, const std::string& msg) {
+  g_last_error = "pnmcc error " + std::to_string(code) + ": " + msg;
+}
+
+template <typename F>
+static int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pnm_set_error(PNM_ENOMEM, "host allocation failed");
+    return PNM_ENOMEM;
+  } catch (...) {
+    pnm_set_error(PNM_EINVAL, "unexpected failure");
+    return PNM_EINVAL;
+  }
+}
+
+static void release(pnm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+  for (auto& g : ctx->graph_defs) cudaGraphDestroy(g.second);
+  pnm_free_mixed(ctx);
+  for (void* p : ctx->owned) cudaFree(p);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+static void check_sys(const pnm_ctx* ctx, int sys) {
+  if (!ctx) throw PnmError{PNM_EINVAL, "null context"};
+  if (sys < 0 || sys >= (int)ctx->sys.size()) throw PnmError{PNM_EINVAL, "system index out of range"};
+}
+
+extern "C" {
+
+void pnm_default_opts(pnm_solve_opts* o) {
+  if (!o) return;
+  o->precision = PNM_PREC_FP64;
+  o->mix_alpha = 0.5;
+  o->tol_dE = 1e-10;
+  o->tol_dE_per_N = 0.0;
+  o->max_iter = 500;
+  o->refine_sweeps = 0;
+  o->init = PNM_INIT_MBPT2;
+  o->host_loop = 0;
+}
+
+const char* pnm_last_error(void) { return g_last_error.c_str(); }
+
+int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
+                     const pnm_minnesota* params, void* stream, pnm_ctx** out) {
+  return guarded([&]() {
+    if (!out || !N || !rho || !n2max || !params || n <= 0)
+      throw PnmError{PNM_EINVAL, "null argument or empty batch"};
+    *out = nullptr;
+    pnm_ctx* ctx = new pnm_ctx();
+    try {
+      if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+      } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+      }
+      for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
+      CUDA_TRY(cudaEventRecord(ctx->ev[2], ctx->stream));
+      pnm_build(ctx, n, N, rho, n2max, *params);
+      pnm_prepare_iteration(ctx);
+      pnm_eref_all(ctx);
+      CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
+      CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+      ctx->t_setup = ms;
+    } catch (...) {
+      release(ctx);
+      throw;
+    }
+    *out = ctx;
+    return PNM_OK;
+  });
+}
+
+int pnm_create(int N, double rho, int n2max, const pnm_minnesota* params, void* stream,
+               pnm_ctx** out) {
+  return pnm_create_batch(1, &N, &rho, &n2max, params, stream, out);
+}
+
+int pnm_destroy(pnm_ctx* ctx) {
+  return guarded([&]() {
+    release(ctx);
+    return PNM_OK;
+  });
+}
+
+int pnm_num_systems(const pnm_ctx* ctx, int* n) {
+  return guarded([&]() {
+    if (!ctx || !n) throw PnmError{PNM_EINVAL, "null argument"};
+    *n = (int)ctx->sys.size();
+    return PNM_OK;
+  });
+}
+
+int pnm_basis(const pnm_ctx* ctx, int sys, int* n_sp, int* n_holes, int8_t* nxyzs,
+              double* eps_hf) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    if (n_sp) *n_sp = S.nsp;
+    if (n_holes) *n_holes = S.N;
+    if (nxyzs)
+      CUDA_TRY(cudaMemcpyAsync(nxyzs, ctx->d.nvec + S.sp_off, sizeof(char4) * S.nsp,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    if (eps_hf)
+      CUDA_TRY(cudaMemcpyAsync(eps_hf, ctx->d.eps + S.sp_off, sizeof(double) * S.nsp,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  });
+}
+
+int pnm_channels(const pnm_ctx* ctx, int sys, int kind, int* n_chan, int* n_pairs, int32_t* keys,
+                 int32_t* sizes, int32_t* pairs) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    cudaStream_t s = ctx->stream;
+    if (kind == 0) {
+      int c0 = S.ch_begin, c1 = S.ch_end;
+      int nh = 0, np = 0;
+      for (int c = c0; c < c1; c++) {
+        nh += ctx->h_nhh[c];
+        np += ctx->h_npp[c];
+      }
+      if (n_chan) *n_chan = c1 - c0;
+      if (n_pairs) *n_pairs = nh + np;
+      for (int c = c0; c < c1; c++) {
+        if (keys) keys[c - c0] = ctx->h_key[c];
+        if (sizes) {
+          sizes[2 * (c - c0)] = ctx->h_nhh[c];
+          sizes[2 * (c - c0) + 1] = ctx->h_npp[c];
+        }
+      }
+      if (pairs && c1 > c0) {
+        std::vector<int2> hh(nh), pp(np);
+        CUDA_TRY(cudaMemcpyAsync(hh.data(), ctx->d.hh_pair + ctx->h_hh_off[c0], sizeof(int2) * nh,
+                                 cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(pp.data(), ctx->d.pp_pair + ctx->h_pp_off[c0], sizeof(int2) * np,
+                                 cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < nh; k++) {
+          pairs[2 * k] = hh[k].x - S.sp_off;
+          pairs[2 * k + 1] = hh[k].y - S.sp_off;
+        }
+        for (int k = 0; k < np; k++) {
+          pairs[2 * (nh + k)] = pp[k].x - S.sp_off;
+          pairs[2 * (nh + k) + 1] = pp[k].y - S.sp_off;
+        }
+      }
+    } else if (kind == 1) {
+      int x0 = S.x_begin, x1 = S.x_end;
+      int nph = 0, nhp = 0;
+      for (int x = x0; x < x1; x++) {
+        nph += ctx->h_x_nph[x];
+        nhp += ctx->h_x_nhp[x];
+      }
+      if (n_chan) *n_chan = x1 - x0;
+      if (n_pairs) *n_pairs = nph + nhp;
+      if (keys && x1 > x0) {
+        // keys are recomputed from the first row of each channel: key(n_a - n_i, s_a - s_i)
+        std::vector<int2> ph(nph);
+        CUDA_TRY(cudaMemcpyAsync(ph.data(), ctx->d.ph_pair + ctx->h_x_ph_off[x0],
+                                 sizeof(int2) * nph, cudaMemcpyDeviceToHost, s));
+        std::vector<char4> nv(S.nsp);
+        CUDA_TRY(cudaMemcpyAsync(nv.data(), ctx->d.nvec + S.sp_off, sizeof(char4) * S.nsp,
+                                 cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (int x = x0; x < x1; x++) {
+          int2 pr = ph[ctx->h_x_ph_off[x] - ctx->h_x_ph_off[x0]];
+          char4 a = nv[pr.x - S.sp_off], i = nv[pr.y - S.sp_off];
+          keys[x - x0] = (((a.x - i.x + S.m) * S.M + (a.y - i.y + S.m)) * S.M + (a.z - i.z + S.m)) * 3 +
+                         (a.w - i.w + 2) / 2;
+        }
+      }
+      if (sizes)
+        for (int x = x0; x < x1; x++) {
+          sizes[2 * (x - x0)] = ctx->h_x_nph[x];
+          sizes[2 * (x - x0) + 1] = ctx->h_x_nhp[x];
+        }
+      if (pairs && x1 > x0) {
+        std::vector<int2> ph(nph), hp(nhp);
+        CUDA_TRY(cudaMemcpyAsync(ph.data(), ctx->d.ph_pair + ctx->h_x_ph_off[x0],
+                                 sizeof(int2) * nph, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), ctx->d.hp_pair + ctx->h_x_hp_off[x0],
+                                 sizeof(int2) * nhp, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < nph; k++) {
+          pairs[2 * k] = ph[k].x - S.sp_off;
+          pairs[2 * k + 1] = ph[k].y - S.sp_off;
+        }
+        for (int k = 0; k < nhp; k++) {
+          pairs[2 * (nph + k)] = hp[k].x - S.sp_off;
+          pairs[2 * (nph + k) + 1] = hp[k].y - S.sp_off;
+        }
+      }
+    } else {
+      throw PnmError{PNM_EINVAL, "kind must be 0 (direct) or 1 (cross)"};
+    }
+    return PNM_OK;
+  });
+}
+
+int pnm_eref(const pnm_ctx* ctx, double* e_ref) {
+  return guarded([&]() {
+    if (!ctx || !e_ref) throw PnmError{PNM_EINVAL, "null argument"};
+    for (size_t k = 0; k < ctx->sys.size(); k++) e_ref[k] = ctx->sys[k].eref;
+    return PNM_OK;
+  });
+}
+
+int pnm_mbpt2(pnm_ctx* ctx, double* dE) {
+  return guarded([&]() {
+    if (!ctx || !dE) throw PnmError{PNM_EINVAL, "null argument"};
+    pnm_mbpt2_all(ctx, dE);
+    return PNM_OK;
+  });
+}
+
+int pnm_ccd_solve(pnm_ctx* ctx, const pnm_solve_opts* opts, double* dE, int* iters,
+                  double* resid) {
+  return guarded([&]() {
+    if (!ctx || !opts) throw PnmError{PNM_EINVAL, "null argument"};
+    return pnm_solve(ctx, *opts, dE, iters, resid);
+  });
+}
+
+int pnm_energy_history(const pnm_ctx* ctx, int sys, double* hist, int cap, int* n) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    if (!ctx->hist) throw PnmError{PNM_EINVAL, "no solve has run"};
+    SysCtl sc;
+    CUDA_TRY(cudaMemcpyAsync(&sc, ctx->sysctl + sys, sizeof(SysCtl), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    int cnt = std::min(sc.iters + 1, ctx->hist_cap);
+    cnt = std::min(cnt, cap);
+    if (n) *n = cnt;
+    if (hist && cnt > 0)
+      CUDA_TRY(cudaMemcpyAsync(hist, ctx->hist + (long)sys * ctx->hist_cap, sizeof(double) * cnt,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  });
+}
+
+int pnm_amplitude_labels(const pnm_ctx* ctx, int sys, size_t* n, int32_t* abij) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    if (n) *n = (size_t)(S.t_end - S.t_begin);
+    if (abij) {
+      int c0 = S.ch_begin, c1 = S.ch_end;
+      if (c1 == c0) return PNM_OK;
+      int nh = ctx->h_hh_off[c1 - 1] + ctx->h_nhh[c1 - 1] - ctx->h_hh_off[c0];
+      int np = ctx->h_pp_off[c1 - 1] + ctx->h_npp[c1 - 1] - ctx->h_pp_off[c0];
+      std::vector<int2> hh(nh), pp(np);
+      CUDA_TRY(cudaMemcpyAsync(hh.data(), ctx->d.hh_pair + ctx->h_hh_off[c0], sizeof(int2) * nh,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(cudaMemcpyAsync(pp.data(), ctx->d.pp_pair + ctx->h_pp_off[c0], sizeof(int2) * np,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+      CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      size_t z = 0;
+      for (int c = c0; c < c1; c++) {
+        int hb = ctx->h_hh_off[c] - ctx->h_hh_off[c0], pb = ctx->h_pp_off[c] - ctx->h_pp_off[c0];
+        for (int ij = 0; ij < ctx->h_nhh[c]; ij++)
+          for (int ab = 0; ab < ctx->h_npp[c]; ab++, z++) {
+            abij[4 * z + 0] = pp[pb + ab].x - S.sp_off;
+            abij[4 * z + 1] = pp[pb + ab].y - S.sp_off;
+            abij[4 * z + 2] = hh[hb + ij].x - S.sp_off;
+            abij[4 * z + 3] = hh[hb + ij].y - S.sp_off;
+          }
+      }
+    }
+    return PNM_OK;
+  });
+}
+
+int pnm_get_amplitudes(const pnm_ctx* ctx, int sys, double* t, size_t n) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    if (!t || n != (size_t)(S.t_end - S.t_begin)) throw PnmError{PNM_EINVAL, "size mismatch"};
+    CUDA_TRY(cudaMemcpyAsync(t, ctx->d.t0 + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  });
+}
+
+int pnm_set_amplitudes(pnm_ctx* ctx, int sys, const double* t, size_t n) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    if (!t || n != (size_t)(S.t_end - S.t_begin)) throw PnmError{PNM_EINVAL, "size mismatch"};
+    CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  });
+}
+
+int pnm_get_timings(const pnm_ctx* ctx, double* ms, int n) {
+  return guarded([&]() {
+    if (!ctx || !ms) throw PnmError{PNM_EINVAL, "null argument"};
+    double v[5] = {ctx->t_setup, ctx->t_mbpt2, ctx->t_solve, ctx->t_mixed, ctx->t_refine};
+    for (int k = 0; k < n && k < 5; k++) ms[k] = v[k];
+    return PNM_OK;
+  });
+}
+
+int pnm_v_element(const pnm_ctx* ctx, int sys, int p, int q, int r, int s, double* out);
+
+}  // extern "C"

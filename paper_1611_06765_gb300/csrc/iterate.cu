@@ -1,0 +1,603 @@
+// iterate.cu -- one CCD update, Eq. (ccd3) of arXiv:1611.06765 written with the
+// intermediates of Sec. "Developing a CCD code":
+//
+//   0 = v_ab^ij + P(ab) chi_b^c t_ac^ij - P(ij) chi_k^j t_ab^ik + 1/2 <ab|chi|cd> t_cd^ij
+//       + 1/2 t_ab^kl <kl|chi|ij> + P(ij)P(ab) t_ik^ac <kb|chi|cj>
+//
+// with chi_b^c, chi_k^j diagonal here (momentum and S_z conservation), blocked per direct
+// channel (restricted pairs) and per cross channel (ordered ph/hp pairs).  Kernels:
+//   k_tstats   row and column sums of t o v (one-body intermediates) and
+//              <kl|chi|ij> = <kl|v|ij> + 1/2 <kl|v|cd> t_ij^cd per direct channel
+//   k_dchi     chi_p - eps_p per state, gathered over the pairs holding p
+//   k_ph       T_x = remap(t); C_x = V1_x + 1/2 W_x T_x; Q_x = T_x C_x per cross channel
+//   k_pp64     1/2 sum_cd <ab|v|cd> t_cd^ij, grouped over all S_z = 0 channels (FP64)
+//   k_update   Jacobi step t_new = (v + rest) / eps_ij^ab, mixing, energy/residual partials
+//   k_finalize Eq. (ccdcorr) energy per system, |dE| test, device-side loop condition
+#include <cmath>
+#include <cstdio>
+
+#include "pnm_context.cuh"
+
+__device__ __forceinline__ const double* cur_t(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t1 : D.t0;
+}
+__device__ __forceinline__ double* next_t(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t0 : D.t1;
+}
+
+// ----------------------------------------------------------------------------- stats
+// Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for all ij.
+// Blocks [nrows, ...): column chunk (c, ab0): sab[ab] = sum_ij t v.
+__global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __restrict__ ctl,
+                                                int nrows, const int2* __restrict__ ab_items) {
+  __shared__ double sh32[32];
+  const double* __restrict__ t = cur_t(D, ctl);
+  if ((int)blockIdx.x < nrows) {
+    int2 it = D.row_item[blockIdx.x];
+    int c = it.x, kl = it.y;
+    int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+    long base = D.ch_t_off[c];
+    const double* tr = t + base + (long)kl * npp;
+    const double* vr = D.v_pphh + base + (long)kl * npp;
+    double s = 0.0;
+    for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) s += tr[ab] * vr[ab];
+    s = block_sum(s, sh32);
+    if (threadIdx.x == 0) D.sij[D.ch_hh_off[c] + kl] = s;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ij = warp; ij < nh; ij += blockDim.x >> 5) {
+      const double* tj = t + base + (long)ij * npp;
+      double acc = 0.0;
+      for (int cd = lane; cd < npp; cd += 32) acc += vr[cd] * tj[cd];
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        long e = D.ch_vhh_off[c] + (long)kl * nh + ij;
+        D.chi_hh[e] = D.v_hhhh[e] + acc;
+      }
+    }
+  } else {
+    int2 it = ab_items[blockIdx.x - nrows];
+    int c = it.x, ab = it.y + threadIdx.x;
+    int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+    if (ab < npp) {
+      long base = D.ch_t_off[c] + ab;
+      double s = 0.0;
+      for (int ij = 0; ij < nh; ij++) s += t[base + (long)ij * npp] * D.v_pphh[base + (long)ij * npp];
+      D.sab[D.ch_pp_off[c] + ab] = s;
+    }
+  }
+}
+
+// chi_b - eps_b = -sum_d sum_{k<l} t_kl^bd v_kl^bd   (particles)
+// chi_j - eps_j = +sum_l sum_{c<d} v_jl^cd t_jl^cd   (holes)
+__global__ void k_dchi(DevState D, int nsp_total) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nsp_total) return;
+  int lo = D.occ_off[p], hi = D.occ_off[p + 1];
+  double s = 0.0;
+  if (D.sp_hole[p]) {
+    for (int k = lo; k < hi; k++) s += D.sij[D.occ_idx[k]];
+    D.dchi[p] = s;
+  } else {
+    for (int k = lo; k < hi; k++) s += D.sab[D.occ_idx[k]];
+    D.dchi[p] = -s;
+  }
+}
+
+// ------------------------------------------------------------------------ ph term FP64
+// One CTA per cross channel.  Shared: T (nph x nhp), W (nhp x nph), C (nhp x nhp).
+__global__ void __launch_bounds__(256) k_ph64(DevState D, const LoopCtl* __restrict__ ctl) {
+  extern __shared__ double sm[];
+  int x = blockIdx.x;
+  int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  const double* __restrict__ t = cur_t(D, ctl);
+  double* T = sm;
+  double* W = T + nph * nhp;
+  double* Cm = W + nhp * nph;
+  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+    int code = D.xmap[to + e];
+    double v = 0.0;
+    if (code > 0) v = t[code - 1];
+    else if (code < 0) v = -t[-code - 1];
+    T[e] = v;
+    W[e] = D.x_w[wo + e];
+  }
+  __syncthreads();
+  // C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
+  for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
+    int r = e / nhp, s = e % nhp;
+    double acc = 0.0;
+    for (int u = 0; u < nph; u++) acc += W[r * nph + u] * T[u * nhp + s];
+    Cm[e] = D.x_v1[co + e] + 0.5 * acc;
+  }
+  __syncthreads();
+  // Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
+  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+    int r = e / nhp, s = e % nhp;
+    double acc = 0.0;
+    for (int u = 0; u < nhp; u++) acc += T[r * nhp + u] * Cm[u * nhp + s];
+    D.xq[to + e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------- pp ladder FP64
+// R^T(ij, ab) = sum_cd t(ij, cd) <cd|v|ab>, restricted pairs (1/2 sum over ordered cd of a
+// pair-antisymmetric product = sum over c<d).  One CTA per work item (channel, 128 pp
+// columns, up to 8 hh rows); the item's t rows are staged in shared memory, each thread
+// streams one column of the symmetric V block.
+constexpr int PP64_COLS = 128, PP64_ROWS = 8;
+
+__global__ void __launch_bounds__(PP64_COLS) k_pp64(DevState D, const LoopCtl* __restrict__ ctl,
+                                                    const PPItem* __restrict__ items) {
+  extern __shared__ double ts[];  // PP64_ROWS x npp
+  PPItem it = items[blockIdx.x];
+  int c = it.ch;
+  int npp = D.ch_npp[c];
+  long tb = D.ch_t_off[c];
+  const double* __restrict__ t = cur_t(D, ctl);
+  for (int e = threadIdx.x; e < it.nij * npp; e += blockDim.x)
+    ts[e] = t[tb + (long)(it.ij0 + e / npp) * npp + e % npp];
+  __syncthreads();
+  int ab = it.ab0 + threadIdx.x;
+  if (ab >= npp) return;
+  const double* __restrict__ V = D.v_pppp + D.ch_vpp_off[c] + ab;
+  double acc[PP64_ROWS];
+#pragma unroll
+  for (int r = 0; r < PP64_ROWS; r++) acc[r] = 0.0;
+  int cd = 0;
+  for (; cd + 4 <= npp; cd += 4) {
+    double v0 = V[(long)cd * npp], v1 = V[(long)(cd + 1) * npp];
+    double v2 = V[(long)(cd + 2) * npp], v3 = V[(long)(cd + 3) * npp];
+#pragma unroll
+    for (int r = 0; r < PP64_ROWS; r++) {
+      if (r < it.nij) {
+        const double* tr = ts + r * npp + cd;
+        acc[r] = fma(tr[0], v0, acc[r]);
+        acc[r] = fma(tr[1], v1, acc[r]);
+        acc[r] = fma(tr[2], v2, acc[r]);
+        acc[r] = fma(tr[3], v3, acc[r]);
+      }
+    }
+  }
+  for (; cd < npp; cd++) {
+    double v0 = V[(long)cd * npp];
+#pragma unroll
+    for (int r = 0; r < PP64_ROWS; r++)
+      if (r < it.nij) acc[r] = fma(ts[r * npp + cd], v0, acc[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < PP64_ROWS; r++)
+    if (r < it.nij) D.rpp[tb + (long)(it.ij0 + r) * npp + ab] = acc[r];
+}
+
+// ---------------------------------------------------------------------------- update
+// One CTA per row (channel, ij).  Jacobi step of Eq. (ccd3): the bracket collects v, the
+// non-eps parts of the one-body terms, the pp and hh ladders and P(ij)P(ab) Q; then
+// t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.  The residual of the
+// amplitude equation is R = bracket - eps_ij^ab t.
+__global__ void __launch_bounds__(128) k_update(DevState D, const LoopCtl* __restrict__ ctl,
+                                                const SysCtl* __restrict__ sc) {
+  __shared__ double sh32[32];
+  int2 it = D.row_item[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  int sys = D.ch_sys[c];
+  bool frozen = sc[sys].done != 0;
+  bool szero = D.ch_szero[c] != 0;
+  double alpha = ctl->alpha;
+  const double* __restrict__ t = cur_t(D, ctl);
+  double* __restrict__ tn = next_t(D, ctl);
+  long base = D.ch_t_off[c];
+  long row = base + (long)ij * npp;
+  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+  double ei = D.eps[h.x], ej = D.eps[h.y];
+  double di = D.dchi[h.x], dj = D.dchi[h.y];
+  const double* chi = D.chi_hh + D.ch_vhh_off[c] + ij;  // chi[kl * nh]
+  double esum = 0.0, rsum = 0.0;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    long z = row + ab;
+    double tz = t[z];
+    double out = tz;
+    double v = D.v_pphh[z];
+    if (!frozen) {
+      int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+      double num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
+      if (szero) num += D.rpp[z];
+      double hh = 0.0;
+      for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
+      num += hh;
+      int4 q = D.qmap[z];
+      double ph = 0.0;
+      if (q.x >= 0) ph += D.xq[q.x];
+      if (q.y >= 0) ph -= D.xq[q.y];
+      if (q.z >= 0) ph -= D.xq[q.z];
+      if (q.w >= 0) ph += D.xq[q.w];
+      num += ph;
+      double den = ei + ej - D.eps[p.x] - D.eps[p.y];
+      double tnew = num / den;
+      double R = num - den * tz;
+      rsum += R * R;
+      out = alpha * tnew + (1.0 - alpha) * tz;
+    }
+    tn[z] = out;
+    esum += v * out;
+  }
+  esum = block_sum(esum, sh32);
+  rsum = block_sum(rsum, sh32);
+  if (threadIdx.x == 0) {
+    D.eparts[blockIdx.x] = esum;
+    D.rparts[blockIdx.x] = rsum;
+  }
+}
+
+// Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
+__global__ void __launch_bounds__(128) k_init(DevState D, int init) {
+  __shared__ double sh32[32];
+  int2 it = D.row_item[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  long row = D.ch_t_off[c] + (long)ij * npp;
+  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+  double ei = D.eps[h.x], ej = D.eps[h.y];
+  double esum = 0.0;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    long z = row + ab;
+    double v = D.v_pphh[z];
+    double t;
+    if (init == PNM_INIT_MBPT2) {
+      int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+      t = v / (ei + ej - D.eps[p.x] - D.eps[p.y]);
+      D.t0[z] = t;
+    } else if (init == PNM_INIT_ZERO) {
+      t = 0.0;
+      D.t0[z] = t;
+    } else {
+      t = D.t0[z];
+    }
+    esum += v * t;
+  }
+  esum = block_sum(esum, sh32);
+  if (threadIdx.x == 0) {
+    D.eparts[blockIdx.x] = esum;
+    D.rparts[blockIdx.x] = 0.0;
+  }
+}
+
+// MBPT2 with v generated on the fly: sum over restricted pairs of v^2 / eps_ij^ab.
+__global__ void __launch_bounds__(128) k_mbpt2(DevState D, const int* __restrict__ row_lut_off) {
+  __shared__ double sh32[32];
+  int2 it = D.row_item[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  const double* lut = D.lut + row_lut_off[D.ch_sys[c]];
+  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+  char4 si = D.nvec[h.x], sj = D.nvec[h.y];
+  double ei = D.eps[h.x], ej = D.eps[h.y];
+  double s = 0.0;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+    double v = v_minnesota_as(D.nvec[p.x], D.nvec[p.y], si, sj, lut);
+    s += v * v / (ei + ej - D.eps[p.x] - D.eps[p.y]);
+  }
+  s = block_sum(s, sh32);
+  if (threadIdx.x == 0) D.eparts[blockIdx.x] = s;
+}
+
+// Sum of row partials per system (fixed order), into out[sys].
+__global__ void k_reduce_rows(const double* __restrict__ parts, const int* __restrict__ row_lo,
+                              const int* __restrict__ row_hi, double* __restrict__ out) {
+  __shared__ double sh32[32];
+  int s = blockIdx.x;
+  double acc = 0.0;
+  for (int r = row_lo[s] + threadIdx.x; r < row_hi[s]; r += blockDim.x) acc += parts[r];
+  acc = block_sum(acc, sh32);
+  if (threadIdx.x == 0) out[s] = acc;
+}
+
+// Energy of the start amplitudes: history[0] per system, reset of the loop state.
+__global__ void k_start(const double* __restrict__ parts, const int* __restrict__ row_lo,
+                        const int* __restrict__ row_hi, int nsys, SysCtl* __restrict__ sc,
+                        LoopCtl* __restrict__ ctl, double* __restrict__ hist, int hist_cap) {
+  __shared__ double sh32[32];
+  for (int s = 0; s < nsys; s++) {
+    double acc = 0.0;
+    for (int r = row_lo[s] + threadIdx.x; r < row_hi[s]; r += blockDim.x) acc += parts[r];
+    acc = block_sum(acc, sh32);
+    if (threadIdx.x == 0) {
+      sc[s].e_old = acc;
+      sc[s].e_new = acc;
+      sc[s].resid = 0.0;
+      sc[s].done = 0;
+      sc[s].iters = 0;
+      hist[(long)s * hist_cap] = acc;
+    }
+  }
+  if (threadIdx.x == 0) {
+    ctl->iter = 0;
+    ctl->status = 0;
+  }
+}
+
+// End of one update: energies, convergence per system, loop condition.
+__global__ void k_finalize(const double* __restrict__ eparts, const double* __restrict__ rparts,
+                           const int* __restrict__ row_lo, const int* __restrict__ row_hi,
+                           int nsys, SysCtl* __restrict__ sc, LoopCtl* __restrict__ ctl,
+                           double* __restrict__ hist, int hist_cap, int use_cond,
+                           cudaGraphConditionalHandle handle) {
+  __shared__ double sh32[32];
+  __shared__ int all_done, bad;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int s = 0; s < nsys; s++) {
+    double e = 0.0, r = 0.0;
+    for (int k = row_lo[s] + threadIdx.x; k < row_hi[s]; k += blockDim.x) {
+      e += eparts[k];
+      r += rparts[k];
+    }
+    e = block_sum(e, sh32);
+    r = block_sum(r, sh32);
+    if (threadIdx.x == 0) {
+      SysCtl& S = sc[s];
+      if (!S.done) {
+        S.iters += 1;
+        S.e_new = e;
+        S.resid = sqrt(r);
+        if (S.iters < hist_cap) hist[(long)s * hist_cap + S.iters] = e;
+        double diff = fabs(e - S.e_old);
+        S.e_old = e;
+        if (!isfinite(e) || !isfinite(r)) bad = 1;
+        if (diff < S.tol) S.done = 1;
+      }
+      if (!S.done) all_done = 0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ctl->iter += 1;
+    int cont = 1;
+    if (bad) {
+      ctl->status = PNM_EDIVERGED;
+      cont = 0;
+    } else if (all_done) {
+      ctl->status = 1;
+      cont = 0;
+    } else if (ctl->iter >= ctl->max_iter) {
+      ctl->status = PNM_ENOTCONV;
+      cont = 0;
+    }
+    if (use_cond) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+  }
+}
+
+// ------------------------------------------------------------------------- host side
+
+static void* dmalloc(pnm_ctx* ctx, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) {
+    cudaGetLastError();
+    throw PnmError{PNM_ENOMEM, "cudaMalloc failed"};
+  }
+  ctx->owned.push_back(p);
+  return p;
+}
+
+void pnm_prepare_iteration(pnm_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  // per-system row ranges and LUT offsets
+  std::vector<int> lo(nsys), hi(nsys), lut(nsys);
+  for (int k = 0; k < nsys; k++) {
+    lo[k] = ctx->sys[k].row_begin;
+    hi[k] = ctx->sys[k].row_end;
+    lut[k] = ctx->sys[k].lut_off;
+  }
+  int* d = (int*)dmalloc(ctx, sizeof(int) * 3 * nsys);
+  CUDA_TRY(cudaMemcpyAsync(d, lo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d + nsys, hi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d + 2 * nsys, lut.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  ctx->row_lo_d = d;
+  ctx->row_hi_d = d + nsys;
+  ctx->lut_off_d = d + 2 * nsys;
+  // pp work list (S_z = 0 channels): 128 columns x up to 8 rows
+  std::vector<PPItem> items;
+  std::vector<int2> abit;
+  int max_npp = 0;
+  for (int c = 0; c < ctx->nch; c++) {
+    int npp = ctx->h_npp[c], nh = ctx->h_nhh[c];
+    max_npp = std::max(max_npp, npp);
+    for (int ab0 = 0; ab0 < npp; ab0 += 128) abit.push_back(make_int2(c, ab0));
+    if (!ctx->h_szero[c]) continue;
+    for (int ij0 = 0; ij0 < nh; ij0 += PP64_ROWS)
+      for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS)
+        items.push_back(PPItem{c, ab0, ij0, std::min(PP64_ROWS, nh - ij0)});
+  }
+  ctx->max_npp = max_npp;
+  ctx->n_pp_items = (int)items.size();
+  ctx->pp_items = (PPItem*)dmalloc(ctx, sizeof(PPItem) * std::max<size_t>(1, items.size()));
+  if (!items.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->pp_items, items.data(), sizeof(PPItem) * items.size(),
+                             cudaMemcpyHostToDevice, s));
+  ctx->n_ab_items = (int)abit.size();
+  ctx->ab_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, abit.size()));
+  if (!abit.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->ab_items, abit.data(), sizeof(int2) * abit.size(),
+                             cudaMemcpyHostToDevice, s));
+  int mx = 0;
+  for (int x = 0; x < ctx->nx; x++) mx = std::max(mx, std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]));
+  ctx->max_x_dim = mx;
+  ctx->ctl = (LoopCtl*)dmalloc(ctx, sizeof(LoopCtl));
+  ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
+  ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
+  size_t ph_smem = sizeof(double) * 3 * (size_t)mx * mx;
+  size_t pp_smem = sizeof(double) * PP64_ROWS * (size_t)max_npp;
+  if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
+    throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
+  CUDA_TRY(cudaFuncSetAttribute(k_ph64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_pp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp_smem));
+  CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void pnm_eref_all(pnm_ctx* ctx) {
+  // E_ref = sum_i h0_ii + 1/2 sum_ij <ij|v|ij>, from the HF energies:
+  // sum_i eps_i = sum_i h0_ii + sum_ij <ij|v|ij>, so E_ref = 1/2 (sum_i h0_ii + sum_i eps_i).
+  cudaStream_t s = ctx->stream;
+  std::vector<double> ekin(ctx->nsp_total), eps(ctx->nsp_total);
+  CUDA_TRY(cudaMemcpyAsync(ekin.data(), ctx->d.ekin, sizeof(double) * ctx->nsp_total,
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(eps.data(), ctx->d.eps, sizeof(double) * ctx->nsp_total,
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (auto& S : ctx->sys) {
+    double a = 0, b = 0;
+    for (int i = 0; i < S.N; i++) {
+      a += ekin[S.sp_off + i];
+      b += eps[S.sp_off + i];
+    }
+    S.eref = 0.5 * (a + b);
+  }
+}
+
+void pnm_mbpt2_all(pnm_ctx* ctx, double* out) {
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
+  k_mbpt2<<<ctx->nrows, 128, 0, s>>>(ctx->d, ctx->lut_off_d);
+  k_reduce_rows<<<nsys, 256, 0, s>>>(ctx->d.eparts, ctx->row_lo_d, ctx->row_hi_d,
+                                     ctx->d.rparts);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecord(ctx->ev[1], s));
+  CUDA_TRY(cudaMemcpyAsync(out, ctx->d.rparts, sizeof(double) * nsys, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+  ctx->t_mbpt2 = ms;
+}
+
+// The body of one update, enqueued on the context stream (FP64 path).
+static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
+  cudaStream_t s = ctx->stream;
+  DevState& D = ctx->d;
+  int nsys = (int)ctx->sys.size();
+  k_tstats<<<ctx->nrows + ctx->n_ab_items, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
+  k_dchi<<<(ctx->nsp_total + 127) / 128, 128, 0, s>>>(D, ctx->nsp_total);
+  if (ctx->nx > 0)
+    k_ph64<<<ctx->nx, 256, sizeof(double) * 3 * ctx->max_x_dim * ctx->max_x_dim, s>>>(D, ctx->ctl);
+  if (ctx->n_pp_items > 0)
+    k_pp64<<<ctx->n_pp_items, PP64_COLS, sizeof(double) * PP64_ROWS * ctx->max_npp, s>>>(
+        D, ctx->ctl, ctx->pp_items);
+  k_update<<<ctx->nrows, 128, 0, s>>>(D, ctx->ctl, ctx->sysctl);
+  k_finalize<<<1, 256, 0, s>>>(D.eparts, D.rparts, ctx->row_lo_d, ctx->row_hi_d, nsys,
+                               ctx->sysctl, ctx->ctl, ctx->hist, ctx->hist_cap, use_cond, h);
+}
+
+void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
+  if (mode == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h);
+  else pnm_enqueue_body_mixed(ctx, use_cond, h);
+}
+
+// Build (once per mode) a graph whose single node is a WHILE conditional looping the body.
+static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
+  auto f = ctx->graphs.find(mode);
+  if (f != ctx->graphs.end()) return f->second;
+  cudaGraph_t g;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+  try {
+    pnm_enqueue_body(ctx, mode, 1, h);
+  } catch (...) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(ctx->stream, &dummy);
+    throw;
+  }
+  cudaGraph_t captured;
+  CUDA_TRY(cudaStreamEndCapture(ctx->stream, &captured));
+  cudaGraphExec_t ge;
+  CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));
+  ctx->graphs[mode] = ge;
+  ctx->graph_defs[mode] = g;
+  return ge;
+}
+
+// Runs updates until every system meets its tolerance or the cap is hit.  Returns the
+// loop status (1 converged, PNM_ENOTCONV, PNM_EDIVERGED).
+int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alpha) {
+  cudaStream_t s = ctx->stream;
+  LoopCtl hc{};
+  // keep iteration parity: ctl->iter is reset by k_start; only max_iter/alpha/mode set here
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->max_iter, &max_iter, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->mode, &mode, sizeof(int), cudaMemcpyHostToDevice, s));
+  if (max_iter <= 0) return PNM_ENOTCONV;
+  if (!host_loop) {
+    cudaGraphExec_t ge = graph_for(ctx, mode);
+    CUDA_TRY(cudaGraphLaunch(ge, s));
+  } else {
+    for (;;) {
+      pnm_enqueue_body(ctx, mode, 0, 0);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hc.status != 0) break;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return hc.status;
+}
+
+// Initial amplitudes and their energy; resets iteration counters.
+void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol) {
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  std::vector<SysCtl> hs(nsys);
+  for (int k = 0; k < nsys; k++) {
+    hs[k] = SysCtl{};
+    hs[k].tol = tol[k];
+  }
+  CUDA_TRY(cudaMemcpyAsync(ctx->sysctl, hs.data(), sizeof(SysCtl) * nsys, cudaMemcpyHostToDevice, s));
+  k_init<<<ctx->nrows, 128, 0, s>>>(ctx->d, init);
+  k_start<<<1, 256, 0, s>>>(ctx->d.eparts, ctx->row_lo_d, ctx->row_hi_d, nsys, ctx->sysctl,
+                            ctx->ctl, ctx->hist, ctx->hist_cap);
+  CUDA_TRY(cudaGetLastError());
+}
+
+// Reopen the convergence test of every system for a further phase (refinement), keeping
+// amplitudes, energies and iteration counts.
+__global__ void k_reopen(SysCtl* sc, int nsys, LoopCtl* ctl) {
+  for (int s = 0; s < nsys; s++) sc[s].done = 0;
+  ctl->status = 0;
+}
+
+void pnm_reopen(pnm_ctx* ctx) {
+  k_reopen<<<1, 1, 0, ctx->stream>>>(ctx->sysctl, (int)ctx->sys.size(), ctx->ctl);
+  CUDA_TRY(cudaGetLastError());
+}
+
+// Make t0 hold the latest amplitudes (the loop leaves them in t[iter & 1]).
+void pnm_settle_amplitudes(pnm_ctx* ctx) {
+  int it = 0;
+  CUDA_TRY(cudaMemcpyAsync(&it, &ctx->ctl->iter, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (it & 1) {
+    CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, ctx->d.t1, sizeof(double) * ctx->nt,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+    int zero = 0;
+    CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  ctx->last_iters_host = it;
+}

@@ -1,0 +1,143 @@
+// pnm_internal.cuh -- device data layout of a pnmcc context and shared helpers.
+//
+// Layout in HBM (all systems of a context concatenated; every index below is global):
+//   states       char4 nvec[n_sp_total] = (n_x, n_y, n_z, s); double eps[], ekin[]
+//   direct chans per channel c: sys, key, n_hh, n_pp, hh_off, pp_off, t_off, vpp_off, vhh_off
+//                int2 hh_pair[], pp_pair[] (global state indices, lexicographic per channel)
+//   amplitudes   t[c] is an n_hh x n_pp row-major block (hh rows, pp contiguous): element
+//                (ij, ab) at t_off[c] + ij * n_pp + ab.  v_pphh has the same layout.
+//   V_pppp       only for S_z = 0 channels (same-spin pairs do not interact): n_pp x n_pp,
+//                symmetric, row-major at vpp_off[c].
+//   cross chans  per channel x: n_ph rows (a,i), n_hp columns (k,c); T_x/Q_x are
+//                n_ph x n_hp at xt_off[x]; V1_x (<kb|v|cj>) n_hp x n_hp at xc_off[x];
+//                W_x (<kl|v|ce>) n_hp x n_ph at xw_off[x].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pnmcc.h"
+
+#define PNM_PI 3.14159265358979323846
+
+struct PnmError {
+  int code;
+  std::string msg;
+};
+
+void pnm_set_error(int code, const std::string& msg);
+
+#define CUDA_TRY(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw PnmError{PNM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// One system (N, rho, n2max) of a context.
+struct SysInfo {
+  int N, n2max, r, m, M, nkeys;
+  double rho, L;
+  int nsp, sp_off;        // states [sp_off, sp_off + nsp)
+  int ch_begin, ch_end;   // direct channels
+  int x_begin, x_end;     // cross channels
+  long t_begin, t_end;    // restricted amplitudes
+  int row_begin, row_end; // (channel, ij) rows
+  int lut_off, lut_len;
+  double eref;
+};
+
+// Device arena pointers; all arrays are global over the systems of the context.
+struct DevState {
+  // states
+  char4* nvec;
+  double *eps, *ekin, *lut;
+  int* sp_sys;           // state -> system
+  int* sp_hole;          // 1 for hole states
+  // direct channels
+  int *ch_sys, *ch_key, *ch_nhh, *ch_npp, *ch_hh_off, *ch_pp_off, *ch_szero;
+  long *ch_t_off, *ch_vpp_off, *ch_vhh_off;
+  int2 *hh_pair, *pp_pair;
+  // rows (channel, ij) for the update and energy partials
+  int2* row_item;        // (channel, ij)
+  // cross channels
+  int *x_nph, *x_nhp;
+  long *x_t_off, *x_c_off, *x_w_off;
+  int2 *ph_pair, *hp_pair;
+  int* x_ph_off;
+  int* x_hp_off;
+  // maps
+  int* xmap;             // per T element: sign * (t index + 1), 0 = structurally zero
+  int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q
+  int *occ_off, *occ_idx; // per state: pair indices (pp for particles, hh for holes)
+  // blocks
+  double *v_pphh, *v_pppp, *v_hhhh, *x_v1, *x_w;
+  // iteration state
+  double *t0, *t1;       // double buffer, parity = iteration & 1
+  double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;
+  double *eparts, *rparts;
+};
+
+// Work-list items for the grouped pp-ladder launch (FP64 path).
+struct PPItem {
+  int ch;      // direct channel
+  int ab0;     // first pp column of the tile
+  int ij0;     // first hh row of the tile
+  int nij;     // rows in the tile
+};
+
+// Solve-loop control block in device memory (one per context).
+struct LoopCtl {
+  int iter;          // updates made in the current solve
+  int max_iter;
+  int status;        // 0 running, 1 converged, PNM_ENOTCONV, PNM_EDIVERGED
+  int mode;          // 0 FP64 iteration, 1 mixed iteration
+  double alpha;
+};
+
+struct SysCtl {
+  double e_old, e_new, resid;
+  double tol;
+  int done;       // 1 once converged
+  int iters;
+};
+
+// --------------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ int dot3(int x, int y, int z) { return x * x + y * y + z * z; }
+
+// Antisymmetrized Minnesota element for two neutrons.  With P_tau = 1 the exchange form
+// reduces to 1/2 (V_R + V_S)(1 - P_sigma) (the V_T term cancels), whose antisymmetrized
+// plane-wave element is 1/2 [Vt(n_p - n_r) + Vt(n_p - n_s)] times the spin factor
+// d(s_p,s_r) d(s_q,s_s) - d(s_p,s_s) d(s_q,s_r), with momentum conservation.
+// lut[m] = Vt at |dn|^2 = m for this system.
+__device__ __forceinline__ double v_minnesota_as(char4 p, char4 q, char4 r, char4 s,
+                                                 const double* __restrict__ lut) {
+  if (p.x + q.x != r.x + s.x || p.y + q.y != r.y + s.y || p.z + q.z != r.z + s.z) return 0.0;
+  int sf = (p.w == r.w && q.w == s.w) - (p.w == s.w && q.w == r.w);
+  if (sf == 0) return 0.0;
+  int m1 = dot3(p.x - r.x, p.y - r.y, p.z - r.z);
+  int m2 = dot3(p.x - s.x, p.y - s.y, p.z - s.z);
+  return 0.5 * (lut[m1] + lut[m2]) * (double)sf;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum for blockDim.x a multiple of 32 (<= 1024); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh32) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh32[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh32[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  __syncthreads();
+  return v;
+}

@@ -1,0 +1,839 @@
+// setup.cu -- GPU construction of the basis, the channel tables, the index maps and the
+// antisymmetrized Minnesota blocks of a pnmcc context.
+//
+//   basis     Sec. "Single-particle basis for infinite matter": k = 2 pi n / L, L^3 = N/rho,
+//             closed shells; state order of the shell loop in Sec. "Developing a CCD code"
+//             (shell, then n_x, n_y, n_z ascending, then s = -1 before +1).
+//   channels  Sec. "Developing a CCD code": direct channels T (quantum numbers added) and
+//             cross channels X (subtracted).  One warp per channel key walks the rows in
+//             ascending state order; in a row every partner is unique for a given key, so a
+//             ballot/popc prefix gives each pair its lexicographic position with no sort.
+//   blocks    Sec. "Two-body interaction" (Minnesota in momentum space) and the particle-hole
+//             character blocks t_pphh, v_pphh, v_pppp, v_hhhh, v_hpph of the channel mapping.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "pnm_context.cuh"
+
+namespace {
+
+__device__ __forceinline__ int cube_index(int x, int y, int z, int r) {
+  if (x < -r || x > r || y < -r || y > r || z < -r || z > r) return -1;
+  int w = 2 * r + 1;
+  return ((x + r) * w + (y + r)) * w + (z + r);
+}
+
+// State index of (n, s) in a system, or -1.
+__device__ __forceinline__ int lookup_state(const int* __restrict__ idx3, int r, int x, int y,
+                                            int z, int s) {
+  int c = cube_index(x, y, z, r);
+  if (c < 0 || (s != -1 && s != 1)) return -1;
+  return idx3[2 * c + ((s + 1) >> 1)];
+}
+
+__device__ __forceinline__ void decode_key(int K, int m, int M, int& Px, int& Py, int& Pz,
+                                           int& Sz) {
+  Sz = 2 * (K % 3) - 2;
+  int rest = K / 3;
+  Pz = rest % M - m;
+  rest /= M;
+  Py = rest % M - m;
+  Px = rest / M - m;
+}
+
+__device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int Sz, int m, int M) {
+  return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * 3 + (Sz + 2) / 2;
+}
+
+// ---------------------------------------------------------------------------- basis
+// One CTA.  Cube points c = ((x+r)w + (y+r))w + (z+r) are in (n_x, n_y, n_z) lexicographic
+// order, so a point's slot in the shell-ordered list is (points in lower shells) + (points
+// of the same shell with a smaller cube index).
+__global__ void k_basis(int n2max, int r, char4* __restrict__ nvec, int* __restrict__ idx3,
+                        int* __restrict__ nsp_out) {
+  extern __shared__ int sh[];  // shell counts [n2max + 1], then shell starts [n2max + 1]
+  int* cnt = sh;
+  int* start = sh + (n2max + 1);
+  int w = 2 * r + 1, ncube = w * w * w;
+  for (int k = threadIdx.x; k <= n2max; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncube; c += blockDim.x) {
+    int x = c / (w * w) - r, y = (c / w) % w - r, z = c % w - r;
+    int n2 = dot3(x, y, z);
+    if (n2 <= n2max) atomicAdd(&cnt[n2], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k <= n2max; k++) {
+      start[k] = acc;
+      acc += cnt[k];
+    }
+    *nsp_out = 2 * acc;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncube; c += blockDim.x) {
+    int x = c / (w * w) - r, y = (c / w) % w - r, z = c % w - r;
+    int n2 = dot3(x, y, z);
+    if (n2 > n2max) {
+      idx3[2 * c] = idx3[2 * c + 1] = -1;
+      continue;
+    }
+    int rank = 0;
+    for (int c2 = 0; c2 < c; c2++) {
+      int x2 = c2 / (w * w) - r, y2 = (c2 / w) % w - r, z2 = c2 % w - r;
+      rank += (dot3(x2, y2, z2) == n2);
+    }
+    int slot = start[n2] + rank;
+    nvec[2 * slot] = make_char4((char)x, (char)y, (char)z, (char)-1);
+    nvec[2 * slot + 1] = make_char4((char)x, (char)y, (char)z, (char)1);
+    idx3[2 * c] = 2 * slot;
+    idx3[2 * c + 1] = 2 * slot + 1;
+  }
+}
+
+// lut[m] = sum_{a=R,S} (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)).
+__global__ void k_lut(double* __restrict__ lut, int len, double L, double VR, double kR,
+                      double VS, double kS) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= len) return;
+  double L3 = L * L * L;
+  double q2 = (2.0 * PNM_PI / L) * (2.0 * PNM_PI / L) * (double)m;
+  lut[m] = VR / L3 * pow(PNM_PI / kR, 1.5) * exp(-q2 / (4.0 * kR)) +
+           VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS));
+}
+
+// eps_p = h0_pp + sum_i <pi|v|pi>  (holes are the first N states of the system).
+__global__ void k_eps(const char4* __restrict__ nvec, const double* __restrict__ lut, int nsp,
+                      int N, double L, double hbar2_2m, double* __restrict__ ekin,
+                      double* __restrict__ eps, int* __restrict__ sp_sys,
+                      int* __restrict__ sp_hole, int sys) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nsp) return;
+  char4 sp = nvec[p];
+  double k0 = 2.0 * PNM_PI / L;
+  double ek = hbar2_2m * k0 * k0 * (double)dot3(sp.x, sp.y, sp.z);
+  double acc = 0.0;
+  for (int i = 0; i < N; i++) {
+    char4 si = nvec[i];
+    acc += v_minnesota_as(sp, si, sp, si, lut);
+  }
+  ekin[p] = ek;
+  eps[p] = ek + acc;
+  sp_sys[p] = sys;
+  sp_hole[p] = p < N;
+}
+
+// ---------------------------------------------------------------------- channel counts
+// One warp per direct key: count restricted hh pairs (i<j<N) and pp pairs (N<=a<b).
+__global__ void k_count_direct(const char4* __restrict__ nvec, const int* __restrict__ idx3,
+                               int r, int m, int M, int nkeys, int N, int nsp,
+                               int* __restrict__ cnt_hh, int* __restrict__ cnt_pp) {
+  int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (K >= nkeys) return;
+  int Px, Py, Pz, Sz;
+  decode_key(K, m, M, Px, Py, Pz, Sz);
+  int nh = 0, np = 0;
+  for (int p0 = 0; p0 < nsp; p0 += 32) {
+    int p = p0 + lane;
+    bool v = false;
+    if (p < nsp) {
+      char4 s = nvec[p];
+      int q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w);
+      v = (q > p) && ((p < N) == (q < N));
+      if (v && p < N) {
+        nh++;
+        v = false;
+      }
+    }
+    np += v;
+  }
+  nh = __reduce_add_sync(0xffffffffu, nh);
+  np = __reduce_add_sync(0xffffffffu, np);
+  if (lane == 0) {
+    cnt_hh[K] = nh;
+    cnt_pp[K] = np;
+  }
+}
+
+// One warp per cross key D: count ph rows (a >= N, i < N, n_a - n_i = D) and hp columns.
+__global__ void k_count_cross(const char4* __restrict__ nvec, const int* __restrict__ idx3,
+                              int r, int m, int M, int nkeys, int N, int nsp,
+                              int* __restrict__ cnt_ph, int* __restrict__ cnt_hp) {
+  int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (K >= nkeys) return;
+  int Dx, Dy, Dz, Ds;
+  decode_key(K, m, M, Dx, Dy, Dz, Ds);
+  int nph = 0, nhp = 0;
+  for (int p0 = 0; p0 < nsp; p0 += 32) {
+    int p = p0 + lane;
+    if (p < nsp) {
+      char4 s = nvec[p];
+      int q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds);
+      if (q >= 0) {
+        if (p >= N && q < N) nph++;
+        if (p < N && q >= N) nhp++;
+      }
+    }
+  }
+  nph = __reduce_add_sync(0xffffffffu, nph);
+  nhp = __reduce_add_sync(0xffffffffu, nhp);
+  if (lane == 0) {
+    cnt_ph[K] = nph;
+    cnt_hp[K] = nhp;
+  }
+}
+
+// ------------------------------------------------------------------------ channel fill
+// One warp per direct channel.  Writes pairs (global state indices) in lexicographic order
+// and the pair -> position tables used by the index maps.
+__global__ void k_fill_direct(const char4* __restrict__ nvec, const int* __restrict__ idx3,
+                              int r, int m, int M, int N, int nsp, int sp_off, int nch_sys,
+                              const int* __restrict__ key, const int* __restrict__ hh_off,
+                              const int* __restrict__ pp_off, int2* __restrict__ hh_pair,
+                              int2* __restrict__ pp_pair, int* __restrict__ pos_hh,
+                              int* __restrict__ pos_pp) {
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= nch_sys) return;
+  int Px, Py, Pz, Sz;
+  decode_key(key[c], m, M, Px, Py, Pz, Sz);
+  int np = nsp - N;
+  int nh_fill = 0, np_fill = 0;
+  unsigned lt = (1u << lane) - 1u;
+  for (int p0 = 0; p0 < nsp; p0 += 32) {
+    int p = p0 + lane;
+    int q = -1;
+    bool vh = false, vp = false;
+    if (p < nsp) {
+      char4 s = nvec[p];
+      q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w);
+      bool v = (q > p) && ((p < N) == (q < N));
+      vh = v && p < N;
+      vp = v && p >= N;
+    }
+    unsigned bh = __ballot_sync(0xffffffffu, vh);
+    unsigned bp = __ballot_sync(0xffffffffu, vp);
+    if (vh) {
+      int pos = nh_fill + __popc(bh & lt);
+      hh_pair[hh_off[c] + pos] = make_int2(p + sp_off, q + sp_off);
+      pos_hh[p * N + q] = pos;
+    }
+    if (vp) {
+      int pos = np_fill + __popc(bp & lt);
+      pp_pair[pp_off[c] + pos] = make_int2(p + sp_off, q + sp_off);
+      pos_pp[(size_t)(p - N) * np + (q - N)] = pos;
+    }
+    nh_fill += __popc(bh);
+    np_fill += __popc(bp);
+  }
+}
+
+// One warp per cross channel: rows (a,i) and columns (k,c) in lexicographic order.
+__global__ void k_fill_cross(const char4* __restrict__ nvec, const int* __restrict__ idx3,
+                             int r, int m, int M, int N, int nsp, int sp_off, int nx_sys,
+                             const int* __restrict__ key, const int* __restrict__ ph_off,
+                             const int* __restrict__ hp_off, int2* __restrict__ ph_pair,
+                             int2* __restrict__ hp_pair, int* __restrict__ phpos,
+                             int* __restrict__ phch, int* __restrict__ hppos) {
+  int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (x >= nx_sys) return;
+  int Dx, Dy, Dz, Ds;
+  decode_key(key[x], m, M, Dx, Dy, Dz, Ds);
+  int np = nsp - N;
+  int f_ph = 0, f_hp = 0;
+  unsigned lt = (1u << lane) - 1u;
+  for (int p0 = 0; p0 < nsp; p0 += 32) {
+    int p = p0 + lane;
+    int q = -1;
+    bool vph = false, vhp = false;
+    if (p < nsp) {
+      char4 s = nvec[p];
+      q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds);
+      vph = (q >= 0) && p >= N && q < N;
+      vhp = (q >= 0) && p < N && q >= N;
+    }
+    unsigned b1 = __ballot_sync(0xffffffffu, vph);
+    unsigned b2 = __ballot_sync(0xffffffffu, vhp);
+    if (vph) {
+      int pos = f_ph + __popc(b1 & lt);
+      ph_pair[ph_off[x] + pos] = make_int2(p + sp_off, q + sp_off);
+      phpos[(size_t)(p - N) * N + q] = pos;
+      phch[(size_t)(p - N) * N + q] = x;
+    }
+    if (vhp) {
+      int pos = f_hp + __popc(b2 & lt);
+      hp_pair[hp_off[x] + pos] = make_int2(p + sp_off, q + sp_off);
+      hppos[(size_t)p * np + (q - N)] = pos;
+    }
+    f_ph += __popc(b1);
+    f_hp += __popc(b2);
+  }
+}
+
+// ------------------------------------------------------------------------- index maps
+// T_x[(a,i)][(k,c)] = t_ik^ac, read from the restricted direct block with its sign.
+// Encoded as sign * (t index + 1); 0 where the element vanishes (a = c or i = k).
+__global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
+                       const long* __restrict__ x_t_off, const int* __restrict__ x_ph_off,
+                       const int* __restrict__ x_hp_off, const int2* __restrict__ ph_pair,
+                       const int2* __restrict__ hp_pair, const char4* __restrict__ nvec,
+                       int sp_off, int N, int nsp, int m, int M, const int* __restrict__ key2ch,
+                       int ch0, const long* __restrict__ ch_t_off,
+                       const int* __restrict__ ch_npp, const int* __restrict__ pos_hh,
+                       const int* __restrict__ pos_pp, int* __restrict__ xmap) {
+  int x = x0 + blockIdx.x;
+  int nph = x_nph[x], nhp = x_nhp[x];
+  int np = nsp - N;
+  long base = x_t_off[x];
+  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+    int rr = e / nhp, ss = e % nhp;
+    int2 ai = ph_pair[x_ph_off[x] + rr], kc = hp_pair[x_hp_off[x] + ss];
+    int a = ai.x - sp_off, i = ai.y - sp_off, k = kc.x - sp_off, c = kc.y - sp_off;
+    int code = 0;
+    if (a != c && i != k) {
+      int sgn = 1;
+      int p1 = a, p2 = c, h1 = i, h2 = k;
+      if (p1 > p2) { int z = p1; p1 = p2; p2 = z; sgn = -sgn; }
+      if (h1 > h2) { int z = h1; h1 = h2; h2 = z; sgn = -sgn; }
+      char4 s1 = nvec[sp_off + p1], s2 = nvec[sp_off + p2];
+      int K = encode_key(s1.x + s2.x, s1.y + s2.y, s1.z + s2.z, s1.w + s2.w, m, M);
+      int ch = key2ch[K];
+      if (ch >= 0) {
+        int g = ch0 + ch;
+        long idx = ch_t_off[g] + (long)pos_hh[h1 * N + h2] * ch_npp[g] +
+                   pos_pp[(size_t)(p1 - N) * np + (p2 - N)];
+        code = sgn * (int)(idx + 1);
+      }
+    }
+    xmap[base + e] = code;
+  }
+}
+
+// For every restricted t element (ij, ab) of a row: the positions of
+// Q_ij^ab, Q_ji^ab, Q_ij^ba, Q_ji^ba with Q_ij^ab = Q_x[(a,i)][(j,b)].
+__device__ __forceinline__ int qpos(int p, int h, int h2, int p2, int N, int np,
+                                    const int* __restrict__ phch, const int* __restrict__ phpos,
+                                    const int* __restrict__ hppos, int x0,
+                                    const long* __restrict__ x_t_off,
+                                    const int* __restrict__ x_nhp) {
+  size_t u = (size_t)(p - N) * N + h;
+  int x = phch[u];
+  if (x < 0) return -1;
+  int g = x0 + x;
+  return (int)(x_t_off[g] + (long)phpos[u] * x_nhp[g] + hppos[(size_t)h2 * np + (p2 - N)]);
+}
+
+__global__ void k_qmap(int row0, const int2* __restrict__ row_item,
+                       const int* __restrict__ ch_hh_off, const int* __restrict__ ch_pp_off,
+                       const int* __restrict__ ch_npp, const long* __restrict__ ch_t_off,
+                       const int2* __restrict__ hh_pair, const int2* __restrict__ pp_pair,
+                       int sp_off, int N, int nsp, const int* __restrict__ phch,
+                       const int* __restrict__ phpos, const int* __restrict__ hppos, int x0,
+                       const long* __restrict__ x_t_off, const int* __restrict__ x_nhp,
+                       int4* __restrict__ qmap) {
+  int2 it = row_item[row0 + blockIdx.x];
+  int c = it.x, ij = it.y;
+  int np = nsp - N;
+  int2 h = hh_pair[ch_hh_off[c] + ij];
+  int i = h.x - sp_off, j = h.y - sp_off;
+  int npp = ch_npp[c];
+  long base = ch_t_off[c] + (long)ij * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 pb = pp_pair[ch_pp_off[c] + ab];
+    int a = pb.x - sp_off, b = pb.y - sp_off;
+    int4 q;
+    q.x = qpos(a, i, j, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
+    q.y = qpos(a, j, i, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
+    q.z = qpos(b, i, j, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
+    q.w = qpos(b, j, i, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
+    qmap[base + ab] = q;
+  }
+}
+
+// Pairs containing each state (for the one-body intermediates): count then fill.
+// One warp per state p of the system; partners d of the same class.
+__global__ void k_occ(int fill, const char4* __restrict__ nvec, int sp_off, int N, int nsp,
+                      int m, int M, const int* __restrict__ key2ch, int ch0,
+                      const int* __restrict__ ch_hh_off, const int* __restrict__ ch_pp_off,
+                      const int* __restrict__ pos_hh, const int* __restrict__ pos_pp,
+                      int* __restrict__ occ_cnt, const int* __restrict__ occ_off,
+                      int* __restrict__ occ_idx) {
+  int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (p >= nsp) return;
+  int np = nsp - N;
+  bool hole = p < N;
+  int lo = hole ? 0 : N, hi = hole ? N : nsp;
+  char4 sp = nvec[sp_off + p];
+  int n = 0;
+  unsigned lt = (1u << lane) - 1u;
+  for (int d0 = lo; d0 < hi; d0 += 32) {
+    int d = d0 + lane;
+    int gidx = -1;
+    if (d < hi && d != p) {
+      char4 sd = nvec[sp_off + d];
+      int K = encode_key(sp.x + sd.x, sp.y + sd.y, sp.z + sd.z, sp.w + sd.w, m, M);
+      int ch = key2ch[K];
+      if (ch >= 0) {
+        int p1 = min(p, d), p2 = max(p, d);
+        int g = ch0 + ch;
+        gidx = hole ? ch_hh_off[g] + pos_hh[p1 * N + p2]
+                    : ch_pp_off[g] + pos_pp[(size_t)(p1 - N) * np + (p2 - N)];
+      }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, gidx >= 0);
+    if (fill && gidx >= 0) occ_idx[occ_off[sp_off + p] + n + __popc(b & lt)] = gidx;
+    n += __popc(b);
+  }
+  if (!fill && lane == 0) occ_cnt[p] = n;
+}
+
+// -------------------------------------------------------------------------- V blocks
+__global__ void k_v_pphh(int row0, const int2* __restrict__ row_item,
+                         const int* __restrict__ ch_hh_off, const int* __restrict__ ch_pp_off,
+                         const int* __restrict__ ch_npp, const long* __restrict__ ch_t_off,
+                         const int2* __restrict__ hh_pair, const int2* __restrict__ pp_pair,
+                         const char4* __restrict__ nvec, const double* __restrict__ lut,
+                         double* __restrict__ v_pphh) {
+  int2 it = row_item[row0 + blockIdx.x];
+  int c = it.x, ij = it.y;
+  int2 h = hh_pair[ch_hh_off[c] + ij];
+  char4 si = nvec[h.x], sj = nvec[h.y];
+  int npp = ch_npp[c];
+  long base = ch_t_off[c] + (long)ij * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 pb = pp_pair[ch_pp_off[c] + ab];
+    v_pphh[base + ab] = v_minnesota_as(nvec[pb.x], nvec[pb.y], si, sj, lut);
+  }
+}
+
+// <ab|v|cd> for S_z = 0 channels; one CTA per (channel, row cd).
+__global__ void k_v_pppp(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
+                         const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
+                         const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
+                         const double* __restrict__ lut, double* __restrict__ v_pppp) {
+  int2 it = items[blockIdx.x];
+  int c = it.x, cd = it.y;
+  int npp = ch_npp[c];
+  int2 pc = pp_pair[ch_pp_off[c] + cd];
+  char4 sc = nvec[pc.x], sd = nvec[pc.y];
+  long base = ch_vpp_off[c] + (long)cd * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 pb = pp_pair[ch_pp_off[c] + ab];
+    v_pppp[base + ab] = v_minnesota_as(nvec[pb.x], nvec[pb.y], sc, sd, lut);
+  }
+}
+
+__global__ void k_v_hhhh(int c0, const int* __restrict__ ch_hh_off,
+                         const int* __restrict__ ch_nhh, const long* __restrict__ ch_vhh_off,
+                         const int2* __restrict__ hh_pair, const char4* __restrict__ nvec,
+                         const double* __restrict__ lut, double* __restrict__ v_hhhh) {
+  int c = c0 + blockIdx.x;
+  int nh = ch_nhh[c];
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) {
+    int kl = e / nh, ij = e % nh;
+    int2 a = hh_pair[ch_hh_off[c] + kl], b = hh_pair[ch_hh_off[c] + ij];
+    v_hhhh[ch_vhh_off[c] + e] = v_minnesota_as(nvec[a.x], nvec[a.y], nvec[b.x], nvec[b.y], lut);
+  }
+}
+
+// V1_x[(k,c)][(j,b)] = <kb|v|cj>,  W_x[(k,c)][(e,l)] = <kl|v|ce>.
+__global__ void k_v_cross(int x0, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
+                          const long* __restrict__ x_c_off, const long* __restrict__ x_w_off,
+                          const int* __restrict__ x_ph_off, const int* __restrict__ x_hp_off,
+                          const int2* __restrict__ ph_pair, const int2* __restrict__ hp_pair,
+                          const char4* __restrict__ nvec, const double* __restrict__ lut,
+                          double* __restrict__ x_v1, double* __restrict__ x_w) {
+  int x = x0 + blockIdx.x;
+  int nph = x_nph[x], nhp = x_nhp[x];
+  for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
+    int2 kc = hp_pair[x_hp_off[x] + e / nhp], jb = hp_pair[x_hp_off[x] + e % nhp];
+    x_v1[x_c_off[x] + e] = v_minnesota_as(nvec[kc.x], nvec[jb.y], nvec[kc.y], nvec[jb.x], lut);
+  }
+  for (int e = threadIdx.x; e < nhp * nph; e += blockDim.x) {
+    int2 kc = hp_pair[x_hp_off[x] + e / nph], el = ph_pair[x_ph_off[x] + e % nph];
+    x_w[x_w_off[x] + e] = v_minnesota_as(nvec[kc.x], nvec[el.y], nvec[kc.y], nvec[el.x], lut);
+  }
+}
+
+template <typename T>
+T* dalloc(size_t n, std::vector<void*>& owned) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw PnmError{PNM_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+  }
+  owned.push_back(p);
+  return (T*)p;
+}
+
+template <typename T>
+void h2d(T* d, const std::vector<T>& h, cudaStream_t s) {
+  if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+template <typename T>
+std::vector<T> d2h(const T* d, size_t n, cudaStream_t s) {
+  std::vector<T> h(n);
+  if (n) {
+    CUDA_TRY(cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return h;
+}
+
+int isqrt_floor(int x) {
+  int r = (int)std::floor(std::sqrt((double)x));
+  while (r * r > x) r--;
+  while ((r + 1) * (r + 1) <= x) r++;
+  return r;
+}
+
+}  // namespace
+
+// Per-system scratch that lives only during setup.
+struct SysScratch {
+  int* idx3 = nullptr;
+  int *key2ch = nullptr, *key2x = nullptr;
+  int *pos_hh = nullptr, *pos_pp = nullptr, *phpos = nullptr, *phch = nullptr, *hppos = nullptr;
+  std::vector<int> dkeys, dnhh, dnpp, xkeys, xnph, xnhp;
+  std::vector<void*> owned;
+  ~SysScratch() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
+               const pnm_minnesota& P) {
+  cudaStream_t s = ctx->stream;
+  DevState& D = ctx->d;
+  std::vector<SysInfo>& sys = ctx->sys;
+  sys.resize(nsys);
+  std::vector<SysScratch> scr(nsys);
+
+  // ---- basis per system (into scratch), closed-shell check on the host
+  std::vector<std::vector<char4>> hvec(nsys);
+  int nsp_total = 0, lut_total = 0;
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    S.N = Ns[k];
+    S.rho = rhos[k];
+    S.n2max = n2maxs[k];
+    if (S.N <= 0 || !(S.rho > 0.0) || S.n2max < 0 || S.n2max > 400)
+      throw PnmError{PNM_EINVAL, "invalid N, rho or n2max"};
+    S.r = isqrt_floor(S.n2max);
+    S.m = 2 * S.r;
+    S.M = 2 * S.m + 1;
+    S.nkeys = S.M * S.M * S.M * 3;
+    S.L = std::cbrt((double)S.N / S.rho);
+    int w = 2 * S.r + 1, ncube = w * w * w;
+    char4* tvec = dalloc<char4>(2 * ncube, scr[k].owned);
+    scr[k].idx3 = dalloc<int>(2 * ncube, scr[k].owned);
+    int* dnsp = dalloc<int>(1, scr[k].owned);
+    k_basis<<<1, 512, 2 * (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, tvec, scr[k].idx3, dnsp);
+    CUDA_TRY(cudaGetLastError());
+    S.nsp = d2h(dnsp, 1, s)[0];
+    hvec[k] = d2h(tvec, S.nsp, s);
+    if (S.N >= S.nsp) throw PnmError{PNM_EINVAL, "no particle states: n2max too small for N"};
+    auto sh = [&](const char4& c) { return c.x * c.x + c.y * c.y + c.z * c.z; };
+    if (sh(hvec[k][S.N - 1]) == sh(hvec[k][S.N]))
+      throw PnmError{PNM_EINVAL, "N = " + std::to_string(S.N) + " does not close a shell"};
+    S.sp_off = nsp_total;
+    nsp_total += S.nsp;
+    S.lut_off = lut_total;
+    S.lut_len = 4 * S.n2max + 1;
+    lut_total += S.lut_len;
+  }
+  ctx->nsp_total = nsp_total;
+  D.nvec = dalloc<char4>(nsp_total, ctx->owned);
+  D.eps = dalloc<double>(nsp_total, ctx->owned);
+  D.ekin = dalloc<double>(nsp_total, ctx->owned);
+  D.sp_sys = dalloc<int>(nsp_total, ctx->owned);
+  D.sp_hole = dalloc<int>(nsp_total, ctx->owned);
+  D.lut = dalloc<double>(lut_total, ctx->owned);
+  D.dchi = dalloc<double>(nsp_total, ctx->owned);
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    h2d(D.nvec + S.sp_off, hvec[k], s);
+    k_lut<<<(S.lut_len + 127) / 128, 128, 0, s>>>(D.lut + S.lut_off, S.lut_len, S.L, P.VR, P.kR,
+                                                 P.VS, P.kS);
+    k_eps<<<(S.nsp + 127) / 128, 128, 0, s>>>(D.nvec + S.sp_off, D.lut + S.lut_off, S.nsp, S.N,
+                                             S.L, P.hbar2_2m, D.ekin + S.sp_off,
+                                             D.eps + S.sp_off, D.sp_sys + S.sp_off,
+                                             D.sp_hole + S.sp_off, k);
+    CUDA_TRY(cudaGetLastError());
+  }
+
+  // ---- channel counts (GPU) and selection (host: keys with both classes, ascending)
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    int* c1 = dalloc<int>(S.nkeys, scr[k].owned);
+    int* c2 = dalloc<int>(S.nkeys, scr[k].owned);
+    int* c3 = dalloc<int>(S.nkeys, scr[k].owned);
+    int* c4 = dalloc<int>(S.nkeys, scr[k].owned);
+    int blocks = (S.nkeys * 32 + 255) / 256;
+    k_count_direct<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.nkeys,
+                                          S.N, S.nsp, c1, c2);
+    k_count_cross<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.nkeys,
+                                         S.N, S.nsp, c3, c4);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<int> hh = d2h(c1, S.nkeys, s), pp = d2h(c2, S.nkeys, s);
+    std::vector<int> ph = d2h(c3, S.nkeys, s), hp = d2h(c4, S.nkeys, s);
+    std::vector<int> key2ch(S.nkeys, -1), key2x(S.nkeys, -1);
+    for (int K = 0; K < S.nkeys; K++) {
+      if (hh[K] > 0 && pp[K] > 0) {
+        key2ch[K] = (int)scr[k].dkeys.size();
+        scr[k].dkeys.push_back(K);
+        scr[k].dnhh.push_back(hh[K]);
+        scr[k].dnpp.push_back(pp[K]);
+      }
+      if (ph[K] > 0 && hp[K] > 0) {
+        key2x[K] = (int)scr[k].xkeys.size();
+        scr[k].xkeys.push_back(K);
+        scr[k].xnph.push_back(ph[K]);
+        scr[k].xnhp.push_back(hp[K]);
+      }
+    }
+    scr[k].key2ch = dalloc<int>(S.nkeys, scr[k].owned);
+    scr[k].key2x = dalloc<int>(S.nkeys, scr[k].owned);
+    h2d(scr[k].key2ch, key2ch, s);
+    h2d(scr[k].key2x, key2x, s);
+  }
+
+  // ---- channel metadata and offsets (host prefix sums over channels)
+  std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_szero;
+  std::vector<long> h_t_off, h_vpp_off, h_vhh_off;
+  std::vector<int2> h_rows, h_vpp_items;
+  std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
+  std::vector<long> h_x_t_off, h_x_c_off, h_x_w_off;
+  long t_acc = 0, vpp_acc = 0, vhh_acc = 0, xt_acc = 0, xc_acc = 0;
+  int hh_acc = 0, pp_acc = 0, ph_acc = 0, hp_acc = 0;
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    SysScratch& X = scr[k];
+    S.ch_begin = (int)h_key.size();
+    S.t_begin = t_acc;
+    S.row_begin = (int)h_rows.size();
+    for (size_t c = 0; c < X.dkeys.size(); c++) {
+      int g = (int)h_key.size();
+      int K = X.dkeys[c];
+      h_ch_sys.push_back(k);
+      h_key.push_back(K);
+      h_nhh.push_back(X.dnhh[c]);
+      h_npp.push_back(X.dnpp[c]);
+      h_hh_off.push_back(hh_acc);
+      h_pp_off.push_back(pp_acc);
+      h_t_off.push_back(t_acc);
+      h_vhh_off.push_back(vhh_acc);
+      bool szero = (K % 3) == 1;  // S_z = 0: the only spin class with nonzero <ab|v|cd>
+      h_szero.push_back(szero ? 1 : 0);
+      h_vpp_off.push_back(szero ? vpp_acc : -1);
+      if (szero) {
+        for (int cd = 0; cd < X.dnpp[c]; cd++) h_vpp_items.push_back(make_int2(g, cd));
+        vpp_acc += (long)X.dnpp[c] * X.dnpp[c];
+      }
+      for (int ij = 0; ij < X.dnhh[c]; ij++) h_rows.push_back(make_int2(g, ij));
+      hh_acc += X.dnhh[c];
+      pp_acc += X.dnpp[c];
+      t_acc += (long)X.dnhh[c] * X.dnpp[c];
+      vhh_acc += (long)X.dnhh[c] * X.dnhh[c];
+    }
+    S.ch_end = (int)h_key.size();
+    S.t_end = t_acc;
+    S.row_end = (int)h_rows.size();
+    S.x_begin = (int)h_x_nph.size();
+    for (size_t x = 0; x < X.xkeys.size(); x++) {
+      h_x_nph.push_back(X.xnph[x]);
+      h_x_nhp.push_back(X.xnhp[x]);
+      h_x_ph_off.push_back(ph_acc);
+      h_x_hp_off.push_back(hp_acc);
+      h_x_t_off.push_back(xt_acc);
+      h_x_c_off.push_back(xc_acc);
+      h_x_w_off.push_back(xt_acc);  // W_x has n_hp x n_ph entries, as many as T_x
+      ph_acc += X.xnph[x];
+      hp_acc += X.xnhp[x];
+      xt_acc += (long)X.xnph[x] * X.xnhp[x];
+      xc_acc += (long)X.xnhp[x] * X.xnhp[x];
+    }
+    S.x_end = (int)h_x_nph.size();
+  }
+  if (t_acc >= (1L << 31) - 2 || xt_acc >= (1L << 31) - 2)
+    throw PnmError{PNM_EINVAL, "problem too large for 32-bit element maps"};
+  ctx->nch = (int)h_key.size();
+  ctx->nx = (int)h_x_nph.size();
+  ctx->nt = t_acc;
+  ctx->nvpp = vpp_acc;
+  ctx->nvhh = vhh_acc;
+  ctx->nxt = xt_acc;
+  ctx->nxc = xc_acc;
+  ctx->nrows = (int)h_rows.size();
+  ctx->n_hh_pairs = hh_acc;
+  ctx->n_pp_pairs = pp_acc;
+  ctx->h_ch_sys = h_ch_sys;
+  ctx->h_key = h_key;
+  ctx->h_nhh = h_nhh;
+  ctx->h_npp = h_npp;
+  ctx->h_t_off = h_t_off;
+  ctx->h_vpp_off = h_vpp_off;
+  ctx->h_szero = h_szero;
+  ctx->h_rows = h_rows;
+  ctx->h_x_nph = h_x_nph;
+  ctx->h_x_nhp = h_x_nhp;
+  ctx->h_x_t_off = h_x_t_off;
+  ctx->h_x_ph_off = h_x_ph_off;
+  ctx->h_x_hp_off = h_x_hp_off;
+  ctx->h_hh_off = h_hh_off;
+  ctx->h_pp_off = h_pp_off;
+
+  int C = ctx->nch, NX = ctx->nx;
+  D.ch_sys = dalloc<int>(C, ctx->owned);
+  D.ch_key = dalloc<int>(C, ctx->owned);
+  D.ch_nhh = dalloc<int>(C, ctx->owned);
+  D.ch_npp = dalloc<int>(C, ctx->owned);
+  D.ch_hh_off = dalloc<int>(C, ctx->owned);
+  D.ch_pp_off = dalloc<int>(C, ctx->owned);
+  D.ch_szero = dalloc<int>(C, ctx->owned);
+  D.ch_t_off = dalloc<long>(C, ctx->owned);
+  D.ch_vpp_off = dalloc<long>(C, ctx->owned);
+  D.ch_vhh_off = dalloc<long>(C, ctx->owned);
+  D.row_item = dalloc<int2>(ctx->nrows, ctx->owned);
+  D.x_nph = dalloc<int>(NX, ctx->owned);
+  D.x_nhp = dalloc<int>(NX, ctx->owned);
+  D.x_ph_off = dalloc<int>(NX, ctx->owned);
+  D.x_hp_off = dalloc<int>(NX, ctx->owned);
+  D.x_t_off = dalloc<long>(NX, ctx->owned);
+  D.x_c_off = dalloc<long>(NX, ctx->owned);
+  D.x_w_off = dalloc<long>(NX, ctx->owned);
+  h2d(D.ch_sys, h_ch_sys, s);
+  h2d(D.ch_key, h_key, s);
+  h2d(D.ch_nhh, h_nhh, s);
+  h2d(D.ch_npp, h_npp, s);
+  h2d(D.ch_hh_off, h_hh_off, s);
+  h2d(D.ch_pp_off, h_pp_off, s);
+  h2d(D.ch_szero, h_szero, s);
+  h2d(D.ch_t_off, h_t_off, s);
+  h2d(D.ch_vpp_off, h_vpp_off, s);
+  h2d(D.ch_vhh_off, h_vhh_off, s);
+  h2d(D.row_item, h_rows, s);
+  h2d(D.x_nph, h_x_nph, s);
+  h2d(D.x_nhp, h_x_nhp, s);
+  h2d(D.x_ph_off, h_x_ph_off, s);
+  h2d(D.x_hp_off, h_x_hp_off, s);
+  h2d(D.x_t_off, h_x_t_off, s);
+  h2d(D.x_c_off, h_x_c_off, s);
+  h2d(D.x_w_off, h_x_w_off, s);
+
+  D.hh_pair = dalloc<int2>(hh_acc, ctx->owned);
+  D.pp_pair = dalloc<int2>(pp_acc, ctx->owned);
+  D.ph_pair = dalloc<int2>(ph_acc, ctx->owned);
+  D.hp_pair = dalloc<int2>(hp_acc, ctx->owned);
+  D.xmap = dalloc<int>(xt_acc, ctx->owned);
+  D.qmap = dalloc<int4>(t_acc, ctx->owned);
+  D.v_pphh = dalloc<double>(t_acc, ctx->owned);
+  D.v_pppp = dalloc<double>(vpp_acc, ctx->owned);
+  D.v_hhhh = dalloc<double>(vhh_acc, ctx->owned);
+  D.x_v1 = dalloc<double>(xc_acc, ctx->owned);
+  D.x_w = dalloc<double>(xt_acc, ctx->owned);
+  D.t0 = dalloc<double>(t_acc, ctx->owned);
+  D.t1 = dalloc<double>(t_acc, ctx->owned);
+  D.rpp = dalloc<double>(t_acc, ctx->owned);
+  D.chi_hh = dalloc<double>(vhh_acc, ctx->owned);
+  D.sab = dalloc<double>(pp_acc, ctx->owned);
+  D.sij = dalloc<double>(hh_acc, ctx->owned);
+  D.xq = dalloc<double>(xt_acc, ctx->owned);
+  D.eparts = dalloc<double>(ctx->nrows, ctx->owned);
+  D.rparts = dalloc<double>(ctx->nrows, ctx->owned);
+  D.occ_off = dalloc<int>(nsp_total + 1, ctx->owned);
+
+  // ---- pair lists, maps, V blocks per system
+  std::vector<int> h_occ_off(nsp_total + 1, 0);
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    SysScratch& X = scr[k];
+    int np = S.nsp - S.N;
+    X.pos_hh = dalloc<int>((size_t)S.N * S.N, X.owned);
+    X.pos_pp = dalloc<int>((size_t)np * np, X.owned);
+    X.phpos = dalloc<int>((size_t)np * S.N, X.owned);
+    X.phch = dalloc<int>((size_t)np * S.N, X.owned);
+    X.hppos = dalloc<int>((size_t)S.N * np, X.owned);
+    CUDA_TRY(cudaMemsetAsync(X.phch, 0xff, sizeof(int) * (size_t)np * S.N, s));
+    int nchs = S.ch_end - S.ch_begin, nxs = S.x_end - S.x_begin;
+    if (nchs > 0)
+      k_fill_direct<<<(nchs * 32 + 255) / 256, 256, 0, s>>>(
+          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.N, S.nsp, S.sp_off, nchs,
+          D.ch_key + S.ch_begin, D.ch_hh_off + S.ch_begin, D.ch_pp_off + S.ch_begin, D.hh_pair,
+          D.pp_pair, X.pos_hh, X.pos_pp);
+    if (nxs > 0) {
+      int* xk = dalloc<int>(nxs, X.owned);
+      h2d(xk, X.xkeys, s);
+      k_fill_cross<<<(nxs * 32 + 255) / 256, 256, 0, s>>>(
+          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.N, S.nsp, S.sp_off, nxs, xk,
+          D.x_ph_off + S.x_begin, D.x_hp_off + S.x_begin, D.ph_pair, D.hp_pair, X.phpos, X.phch,
+          X.hppos);
+      k_xmap<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_t_off, D.x_ph_off, D.x_hp_off,
+                                 D.ph_pair, D.hp_pair, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M,
+                                 X.key2ch, S.ch_begin, D.ch_t_off, D.ch_npp, X.pos_hh, X.pos_pp,
+                                 D.xmap);
+      k_v_cross<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_c_off, D.x_w_off,
+                                    D.x_ph_off, D.x_hp_off, D.ph_pair, D.hp_pair, D.nvec,
+                                    D.lut + S.lut_off, D.x_v1, D.x_w);
+    }
+    int nrows = S.row_end - S.row_begin;
+    if (nrows > 0) {
+      k_qmap<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
+                                   D.ch_t_off, D.hh_pair, D.pp_pair, S.sp_off, S.N, S.nsp,
+                                   X.phch, X.phpos, X.hppos, S.x_begin, D.x_t_off, D.x_nhp,
+                                   D.qmap);
+      k_v_pphh<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
+                                     D.ch_t_off, D.hh_pair, D.pp_pair, D.nvec, D.lut + S.lut_off,
+                                     D.v_pphh);
+    }
+    if (nchs > 0)
+      k_v_hhhh<<<nchs, 128, 0, s>>>(S.ch_begin, D.ch_hh_off, D.ch_nhh, D.ch_vhh_off, D.hh_pair,
+                                    D.nvec, D.lut + S.lut_off, D.v_hhhh);
+    CUDA_TRY(cudaGetLastError());
+    // pairs containing each state
+    int* cnt = dalloc<int>(S.nsp, X.owned);
+    int ob = (S.nsp * 32 + 255) / 256;
+    k_occ<<<ob, 256, 0, s>>>(0, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, X.key2ch, S.ch_begin,
+                             D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, cnt, nullptr, nullptr);
+    std::vector<int> hc = d2h(cnt, S.nsp, s);
+    for (int p = 0; p < S.nsp; p++) h_occ_off[S.sp_off + p + 1] = h_occ_off[S.sp_off + p] + hc[p];
+  }
+  h2d(D.occ_off, h_occ_off, s);
+  D.occ_idx = dalloc<int>(h_occ_off[nsp_total], ctx->owned);
+  for (int k = 0; k < nsys; k++) {
+    SysInfo& S = sys[k];
+    SysScratch& X = scr[k];
+    int ob = (S.nsp * 32 + 255) / 256;
+    k_occ<<<ob, 256, 0, s>>>(1, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, X.key2ch, S.ch_begin,
+                             D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, nullptr, D.occ_off,
+                             D.occ_idx);
+  }
+  // V_pppp for S_z = 0 channels, all systems in one launch
+  if (!h_vpp_items.empty()) {
+    int2* items = dalloc<int2>(h_vpp_items.size(), scr[0].owned);
+    h2d(items, h_vpp_items, s);
+    // the LUT differs per system: launch per system over its item range
+    size_t lo = 0;
+    for (int k = 0; k < nsys; k++) {
+      size_t hi = lo;
+      while (hi < h_vpp_items.size() && h_ch_sys[h_vpp_items[hi].x] == k) hi++;
+      if (hi > lo)
+        k_v_pppp<<<(unsigned)(hi - lo), 256, 0, s>>>(items + lo, D.ch_pp_off, D.ch_npp,
+                                                    D.ch_vpp_off, D.pp_pair, D.nvec,
+                                                    D.lut + sys[k].lut_off, D.v_pppp);
+      lo = hi;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+}

@@ -1,0 +1,104 @@
+// solve.cu -- the CCD driver (Sec. "Developing a CCD code": MBPT2 start, Jacobi updates of
+// Eq. ccd3, mixing, stop on |dE^(n+1) - dE^(n)| < eta) and single-element V access.
+#include <algorithm>
+#include <cmath>
+
+#include "pnm_context.cuh"
+
+__global__ void k_v_one(const char4* __restrict__ nvec, const double* __restrict__ lut, int p,
+                        int q, int r, int s, double* out) {
+  *out = v_minnesota_as(nvec[p], nvec[q], nvec[r], nvec[s], lut);
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, double* resid) {
+  if (!(o.mix_alpha > 0.0 && o.mix_alpha <= 1.0)) throw PnmError{PNM_EINVAL, "mix_alpha must be in (0,1]"};
+  if (o.max_iter < 1) throw PnmError{PNM_EINVAL, "max_iter must be >= 1"};
+  if (o.precision != PNM_PREC_FP64 && o.precision != PNM_PREC_BF16X3)
+    throw PnmError{PNM_EINVAL, "unknown precision mode"};
+  if (o.init < PNM_INIT_MBPT2 || o.init > PNM_INIT_KEEP) throw PnmError{PNM_EINVAL, "unknown init"};
+  if (o.refine_sweeps < 0) throw PnmError{PNM_EINVAL, "refine_sweeps must be >= 0"};
+  if (!(o.tol_dE > 0.0) && !(o.tol_dE_per_N > 0.0)) throw PnmError{PNM_EINVAL, "no tolerance given"};
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  std::vector<double> tol(nsys);
+  for (int k = 0; k < nsys; k++)
+    tol[k] = o.tol_dE_per_N > 0.0 ? o.tol_dE_per_N * ctx->sys[k].N : o.tol_dE;
+  int cap = o.max_iter + o.refine_sweeps + 2;
+  if (cap > ctx->hist_cap) {
+    if (ctx->hist) {
+      // the old buffer stays owned by the context until destroy
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * (size_t)cap * nsys) != cudaSuccess) {
+      cudaGetLastError();
+      throw PnmError{PNM_ENOMEM, "history buffer"};
+    }
+    ctx->owned.push_back(p);
+    ctx->hist = (double*)p;
+    ctx->hist_cap = cap;
+    // graphs capture hist pointer and capacity: rebuild them
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : ctx->graph_defs) cudaGraphDestroy(g.second);
+    ctx->graphs.clear();
+    ctx->graph_defs.clear();
+  }
+  bool mixed = o.precision != PNM_PREC_FP64;
+  if (mixed) pnm_prepare_mixed(ctx);
+
+  cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
+  CUDA_TRY(cudaEventRecord(e0, s));
+  pnm_start(ctx, o.init, tol);
+  int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : PNM_PREC_FP64, o.max_iter, o.host_loop,
+                            o.mix_alpha);
+  CUDA_TRY(cudaEventRecord(e1, s));
+  if (mixed && status == 1 && o.refine_sweeps > 0) {
+    int it0 = 0;
+    CUDA_TRY(cudaMemcpyAsync(&it0, &ctx->ctl->iter, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    pnm_reopen(ctx);
+    status = pnm_run_loop(ctx, PNM_PREC_FP64, it0 + o.refine_sweeps, o.host_loop, o.mix_alpha);
+  }
+  CUDA_TRY(cudaEventRecord(e2, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ctx->t_solve = elapsed(e0, e2);
+  ctx->t_mixed = mixed ? elapsed(e0, e1) : 0.0;
+  ctx->t_refine = mixed ? elapsed(e1, e2) : 0.0;
+  pnm_settle_amplitudes(ctx);
+  std::vector<SysCtl> hs(nsys);
+  CUDA_TRY(cudaMemcpyAsync(hs.data(), ctx->sysctl, sizeof(SysCtl) * nsys, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < nsys; k++) {
+    if (dE) dE[k] = hs[k].e_new;
+    if (iters) iters[k] = hs[k].iters;
+    if (resid) resid[k] = hs[k].resid;
+  }
+  if (status == 1) return PNM_OK;
+  if (status == PNM_ENOTCONV) pnm_set_error(status, "iteration cap reached before convergence");
+  if (status == PNM_EDIVERGED) pnm_set_error(status, "NaN or Inf in the energy or residual");
+  return status;
+}
+
+extern "C" int pnm_v_element(const pnm_ctx* ctx, int sys, int p, int q, int r, int s, double* out) {
+  try {
+    if (!ctx || !out || sys < 0 || sys >= (int)ctx->sys.size())
+      throw PnmError{PNM_EINVAL, "bad argument"};
+    const SysInfo& S = ctx->sys[sys];
+    for (int x : {p, q, r, s})
+      if (x < 0 || x >= S.nsp) throw PnmError{PNM_EINVAL, "state index out of range"};
+    double* d = ctx->small;
+    k_v_one<<<1, 1, 0, ctx->stream>>>(ctx->d.nvec + S.sp_off, ctx->d.lut + S.lut_off, p, q, r, s, d);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
