@@ -144,9 +144,28 @@ int pnm_amplitude_labels(const pnm_ctx *ctx, int sys, size_t *n, int32_t *abij);
 int pnm_get_amplitudes(const pnm_ctx *ctx, int sys, double *t, size_t n);
 int pnm_set_amplitudes(pnm_ctx *ctx, int sys, const double *t, size_t n);
 
+/* The particle-particle ladder alone, as an operator on amplitudes:
+ * r_ij^ab = 1/2 sum_cd <ab|v|cd> t_ij^cd = sum_{c<d} <ab|v|cd> t_ij^cd (the pp-ladder term of
+ * Eq. ccd3, with <ab|chi|cd> = <ab|v|cd> of Sec. "Developing a CCD code"), evaluated by the
+ * FP64 kernel or by the BF16x3 tensor-core kernel (precision).  t and r hold n restricted
+ * amplitudes of system `sys` in library order; r is 0 on channels whose V block vanishes
+ * (S_z != 0 for neutrons).  Resets the solver's iteration state. */
+int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, double *r,
+                        size_t n);
+
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
  * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
+
+/* Per-kernel device time of host-driven solves (opts.host_loop = 1): while profiling is on,
+ * every kernel launch of the update is bracketed by CUDA events on the context stream.
+ * pnm_set_profiling also clears the counters.  pnm_kernel_stats returns, for kernel id
+ * (0, 1, ... until the call returns PNM_EINVAL), its name (static string), total
+ * milliseconds and launch count.
+ * Not from the paper: this is the library's own instrumentation. */
+int pnm_set_profiling(pnm_ctx *ctx, int on);
+int pnm_kernel_stats(const pnm_ctx *ctx, int id, const char **name, double *total_ms,
+                     int *launches);
 
 /* Thread-local text describing the last failure of a pnm_* call on this thread. */
 const char *pnm_last_error(void);

@@ -44,6 +44,8 @@ def lib():
         L.om_t_get.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.om_t_gather.argtypes = [vp, C.c_long, vp, vp]
         L.om_t_dump.argtypes = [vp, vp, vp]
+        L.om_vpp_block.restype = C.c_long
+        L.om_vpp_block.argtypes = [vp, C.c_int, vp]
         L.om_threads.restype = C.c_int
         L.om_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -141,6 +143,14 @@ class OracleSystem:
         t = np.zeros(n)
         lib().om_t_dump(self._h, _ptr(abij), _ptr(t))
         return abij, t
+
+    def vpp_block(self, c):
+        """<ab|v|cd> block of direct channel c (restricted pairs, oracle pair order)."""
+        n = lib().om_vpp_block(self._h, int(c), None)
+        out = np.zeros(n)
+        lib().om_vpp_block(self._h, int(c), _ptr(out))
+        m = int(round(np.sqrt(n)))
+        return out.reshape(m, m)
 
     def t_gather(self, abij):
         abij = np.ascontiguousarray(abij, dtype=np.int32)

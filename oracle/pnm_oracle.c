@@ -793,3 +793,12 @@ void om_set_threads(int n) {
     (void)n;
 #endif
 }
+
+/* <ab|v|cd> block of direct channel c (restricted pairs, npp x npp row-major) and its size. */
+long om_vpp_block(om_sys *S, int c, double *out) {
+    if (c < 0 || c >= S->nch) return -1;
+    build_ccd_blocks(S);
+    long n = (long)S->npp[c] * S->npp[c];
+    if (out) memcpy(out, S->v_pppp + S->vpp_off[c], sizeof(double) * n);
+    return n;
+}

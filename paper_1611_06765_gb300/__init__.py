@@ -141,6 +141,30 @@ class Context:
         t = np.ascontiguousarray(t, dtype=np.float64)
         _lib.check(_lib.load().pnm_set_amplitudes(self._h, sys, _ptr(t), t.size))
 
+    def apply_pp_ladder(self, t, precision=PNM_PREC_FP64, sys=0):
+        """pnm_apply_pp_ladder: the pp-ladder term alone applied to amplitudes t."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        r = np.zeros_like(t)
+        _lib.check(_lib.load().pnm_apply_pp_ladder(self._h, sys, precision, _ptr(t), _ptr(r), t.size))
+        return r
+
+    def set_profiling(self, on=True):
+        _lib.check(_lib.load().pnm_set_profiling(self._h, int(on)))
+
+    def kernel_stats(self):
+        """{name: (total_ms, launches)} of the last profiled host-loop solves."""
+        out = {}
+        k = 0
+        L = _lib.load()
+        while True:
+            name, ms, n = C.c_char_p(), C.c_double(), C.c_int()
+            if L.pnm_kernel_stats(self._h, k, C.byref(name), C.byref(ms), C.byref(n)) != 0:
+                break
+            if n.value:
+                out[name.value.decode()] = (ms.value, n.value)
+            k += 1
+        return out
+
     def timings(self):
         ms = np.zeros(5)
         _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 5))

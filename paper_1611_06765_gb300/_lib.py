@@ -28,7 +28,7 @@ EXPORTS = (
     "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_destroy", "pnm_num_systems",
     "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
-    "pnm_get_timings", "pnm_last_error",
+    "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_set_profiling", "pnm_kernel_stats", "pnm_last_error",
 )
 
 
@@ -78,6 +78,9 @@ def load(path=None):
     L.pnm_get_amplitudes.argtypes = [vp, C.c_int, vp, C.c_size_t]
     L.pnm_set_amplitudes.argtypes = [vp, C.c_int, vp, C.c_size_t]
     L.pnm_get_timings.argtypes = [vp, dp, C.c_int]
+    L.pnm_apply_pp_ladder.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_size_t]
+    L.pnm_set_profiling.argtypes = [vp, C.c_int]
+    L.pnm_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), dp, ip]
     L.pnm_last_error.restype = C.c_char_p
     L.pnm_last_error.argtypes = []
     for name in EXPORTS:

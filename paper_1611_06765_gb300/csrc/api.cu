@@ -36,6 +36,10 @@ static void release(pnm_ctx* ctx) {
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& pr : ctx->prof_ev) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -332,5 +336,39 @@ int pnm_get_timings(const pnm_ctx* ctx, double* ms, int n) {
 }
 
 int pnm_v_element(const pnm_ctx* ctx, int sys, int p, int q, int r, int s, double* out);
+
+int pnm_apply_pp_ladder(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    if (!t || !r) throw PnmError{PNM_EINVAL, "null argument"};
+    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3)
+      throw PnmError{PNM_EINVAL, "unknown precision mode"};
+    pnm_apply_pp(ctx, sys, precision, t, r, n);
+    return PNM_OK;
+  });
+}
+
+int pnm_set_profiling(pnm_ctx* ctx, int on) {
+  return guarded([&]() {
+    if (!ctx) throw PnmError{PNM_EINVAL, "null context"};
+    ctx->prof_on = on != 0;
+    for (int k = 0; k < PNM_NKERNELS; k++) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_n[k] = 0;
+    }
+    return PNM_OK;
+  });
+}
+
+int pnm_kernel_stats(const pnm_ctx* ctx, int id, const char** name, double* total_ms, int* launches) {
+  return guarded([&]() {
+    if (!ctx) throw PnmError{PNM_EINVAL, "null context"};
+    if (id < 0 || id >= PNM_NKERNELS) throw PnmError{PNM_EINVAL, "kernel id out of range"};
+    if (name) *name = pnm_kernel_names[id];
+    if (total_ms) *total_ms = ctx->prof_ms[id];
+    if (launches) *launches = ctx->prof_n[id];
+    return PNM_OK;
+  });
+}
 
 }  // extern "C"

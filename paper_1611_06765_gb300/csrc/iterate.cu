@@ -12,18 +12,13 @@
 //   k_ph       T_x = remap(t); C_x = V1_x + 1/2 W_x T_x; Q_x = T_x C_x per cross channel
 //   k_pp64     1/2 sum_cd <ab|v|cd> t_cd^ij, grouped over all S_z = 0 channels (FP64)
 //   k_update   Jacobi step t_new = (v + rest) / eps_ij^ab, mixing, energy/residual partials
-//   k_finalize Eq. (ccdcorr) energy per system, |dE| test, device-side loop condition
+//   finalize   (last block of k_update) Eq. (ccdcorr) energy per system, |dE| test,
+//              device-side loop condition
 #include <cmath>
 #include <cstdio>
 
 #include "pnm_context.cuh"
 
-__device__ __forceinline__ const double* cur_t(const DevState& D, const LoopCtl* ctl) {
-  return (ctl->iter & 1) ? D.t1 : D.t0;
-}
-__device__ __forceinline__ double* next_t(const DevState& D, const LoopCtl* ctl) {
-  return (ctl->iter & 1) ? D.t0 : D.t1;
-}
 
 // ----------------------------------------------------------------------------- stats
 // Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for all ij.
@@ -70,117 +65,226 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
 // chi_b - eps_b = -sum_d sum_{k<l} t_kl^bd v_kl^bd   (particles)
 // chi_j - eps_j = +sum_l sum_{c<d} v_jl^cd t_jl^cd   (holes)
 __global__ void k_dchi(DevState D, int nsp_total) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
   if (p >= nsp_total) return;
   int lo = D.occ_off[p], hi = D.occ_off[p + 1];
+  bool hole = D.sp_hole[p] != 0;
+  const double* src = hole ? D.sij : D.sab;
   double s = 0.0;
-  if (D.sp_hole[p]) {
-    for (int k = lo; k < hi; k++) s += D.sij[D.occ_idx[k]];
-    D.dchi[p] = s;
-  } else {
-    for (int k = lo; k < hi; k++) s += D.sab[D.occ_idx[k]];
-    D.dchi[p] = -s;
-  }
+  for (int k = lo + lane; k < hi; k += 32) s += src[D.occ_idx[k]];
+  s = warp_sum(s);
+  if (lane == 0) D.dchi[p] = hole ? s : -s;
 }
 
-// ------------------------------------------------------------------------ ph term FP64
-// One CTA per cross channel.  Shared: T (nph x nhp), W (nhp x nph), C (nhp x nhp).
-__global__ void __launch_bounds__(256) k_ph64(DevState D, const LoopCtl* __restrict__ ctl) {
-  extern __shared__ double sm[];
+// ----------------------------------------------------------------------------- ph term
+// One CTA per cross channel.  Shared: T (nph x nhp), W (nhp x nph), C (nhp x nhp), in the
+// element type T_ of the precision mode (double for FP64, float for the mixed mode).
+template <typename T_>
+__global__ void __launch_bounds__(256) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
+                                            const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                            T_* __restrict__ xq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T_* sm = reinterpret_cast<T_*>(smraw);
   int x = blockIdx.x;
   int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const double* __restrict__ t = cur_t(D, ctl);
-  double* T = sm;
-  double* W = T + nph * nhp;
-  double* Cm = W + nhp * nph;
+  T_* T = sm;
+  T_* W = T + nph * nhp;
+  T_* Cm = W + nhp * nph;
   long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
   for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
     int code = D.xmap[to + e];
     double v = 0.0;
     if (code > 0) v = t[code - 1];
     else if (code < 0) v = -t[-code - 1];
-    T[e] = v;
-    W[e] = D.x_w[wo + e];
+    T[e] = (T_)v;
+    W[e] = xw[wo + e];
   }
   __syncthreads();
   // C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
   for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
     int r = e / nhp, s = e % nhp;
-    double acc = 0.0;
+    T_ acc = 0;
     for (int u = 0; u < nph; u++) acc += W[r * nph + u] * T[u * nhp + s];
-    Cm[e] = D.x_v1[co + e] + 0.5 * acc;
+    Cm[e] = xv1[co + e] + (T_)0.5 * acc;
   }
   __syncthreads();
   // Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
   for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
     int r = e / nhp, s = e % nhp;
-    double acc = 0.0;
+    T_ acc = 0;
     for (int u = 0; u < nhp; u++) acc += T[r * nhp + u] * Cm[u * nhp + s];
-    D.xq[to + e] = acc;
+    xq[to + e] = acc;
   }
 }
+
+template <typename T_>
+void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq) {
+  size_t smem = sizeof(T_) * 3 * (size_t)ctx->max_x_dim * ctx->max_x_dim;
+  k_ph<T_><<<ctx->nx, 256, smem, ctx->stream>>>(ctx->d, ctx->ctl, xw, xv1, xq);
+}
+template void launch_ph<double>(pnm_ctx*, const double*, const double*, double*);
+template void launch_ph<float>(pnm_ctx*, const float*, const float*, float*);
 
 // ---------------------------------------------------------------------- pp ladder FP64
 // R^T(ij, ab) = sum_cd t(ij, cd) <cd|v|ab>, restricted pairs (1/2 sum over ordered cd of a
-// pair-antisymmetric product = sum over c<d).  One CTA per work item (channel, 128 pp
-// columns, up to 8 hh rows); the item's t rows are staged in shared memory, each thread
-// streams one column of the symmetric V block.
-constexpr int PP64_COLS = 128, PP64_ROWS = 8;
+// pair-antisymmetric product = sum over c<d).  One CTA per work item (channel, 32 pp
+// columns); its 8 warps split the cd range, lane = column, so each warp streams coalesced
+// 256-byte rows of the symmetric V block.  hh rows go in groups of 8 staged in shared
+// memory; the 8 partial sums per output are added in a fixed order (deterministic).
+constexpr int PP64_COLS = 32, PP64_WARPS = 8, PP64_ROWS = 8;
+static size_t pp64_smem(int npp) {
+  return sizeof(double) * ((size_t)PP64_ROWS * npp + PP64_WARPS * PP64_ROWS * 32);
+}
 
-__global__ void __launch_bounds__(PP64_COLS) k_pp64(DevState D, const LoopCtl* __restrict__ ctl,
-                                                    const PPItem* __restrict__ items) {
-  extern __shared__ double ts[];  // PP64_ROWS x npp
-  PPItem it = items[blockIdx.x];
-  int c = it.ch;
-  int npp = D.ch_npp[c];
+__global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const LoopCtl* __restrict__ ctl,
+                                                          const int2* __restrict__ items) {
+  extern __shared__ double sm[];  // ts[PP64_ROWS][npp], red[PP64_WARPS][PP64_ROWS][32]
+  int2 it = items[blockIdx.x];
+  int c = it.x, ab0 = it.y;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   long tb = D.ch_t_off[c];
   const double* __restrict__ t = cur_t(D, ctl);
-  for (int e = threadIdx.x; e < it.nij * npp; e += blockDim.x)
-    ts[e] = t[tb + (long)(it.ij0 + e / npp) * npp + e % npp];
-  __syncthreads();
-  int ab = it.ab0 + threadIdx.x;
-  if (ab >= npp) return;
-  const double* __restrict__ V = D.v_pppp + D.ch_vpp_off[c] + ab;
-  double acc[PP64_ROWS];
+  double* ts = sm;
+  double* red = sm + PP64_ROWS * npp;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ab = ab0 + lane;
+  bool col = ab < npp;
+  int chunk = (npp + PP64_WARPS - 1) / PP64_WARPS;
+  int lo = warp * chunk, hi = min(npp, lo + chunk);
+  const double* __restrict__ V = D.v_pppp + D.ch_vpp_off[c] + (col ? ab : 0);
+  for (int g0 = 0; g0 < nh; g0 += PP64_ROWS) {
+    int nr = min(PP64_ROWS, nh - g0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * npp; e += blockDim.x)
+      ts[e] = t[tb + (long)(g0 + e / npp) * npp + e % npp];
+    __syncthreads();
+    double acc[PP64_ROWS];
 #pragma unroll
-  for (int r = 0; r < PP64_ROWS; r++) acc[r] = 0.0;
-  int cd = 0;
-  for (; cd + 4 <= npp; cd += 4) {
-    double v0 = V[(long)cd * npp], v1 = V[(long)(cd + 1) * npp];
-    double v2 = V[(long)(cd + 2) * npp], v3 = V[(long)(cd + 3) * npp];
+    for (int r = 0; r < PP64_ROWS; r++) acc[r] = 0.0;
+    if (col) {
+      int cd = lo;
+      for (; cd + 4 <= hi; cd += 4) {
+        double v0 = V[(long)cd * npp], v1 = V[(long)(cd + 1) * npp];
+        double v2 = V[(long)(cd + 2) * npp], v3 = V[(long)(cd + 3) * npp];
 #pragma unroll
-    for (int r = 0; r < PP64_ROWS; r++) {
-      if (r < it.nij) {
-        const double* tr = ts + r * npp + cd;
-        acc[r] = fma(tr[0], v0, acc[r]);
-        acc[r] = fma(tr[1], v1, acc[r]);
-        acc[r] = fma(tr[2], v2, acc[r]);
-        acc[r] = fma(tr[3], v3, acc[r]);
+        for (int r = 0; r < PP64_ROWS; r++) {
+          if (r < nr) {
+            const double* tr = ts + r * npp + cd;
+            acc[r] = fma(tr[0], v0, acc[r]);
+            acc[r] = fma(tr[1], v1, acc[r]);
+            acc[r] = fma(tr[2], v2, acc[r]);
+            acc[r] = fma(tr[3], v3, acc[r]);
+          }
+        }
+      }
+      for (; cd < hi; cd++) {
+        double v0 = V[(long)cd * npp];
+#pragma unroll
+        for (int r = 0; r < PP64_ROWS; r++)
+          if (r < nr) acc[r] = fma(ts[r * npp + cd], v0, acc[r]);
       }
     }
-  }
-  for (; cd < npp; cd++) {
-    double v0 = V[(long)cd * npp];
 #pragma unroll
-    for (int r = 0; r < PP64_ROWS; r++)
-      if (r < it.nij) acc[r] = fma(ts[r * npp + cd], v0, acc[r]);
-  }
+    for (int r = 0; r < PP64_ROWS; r++) red[(warp * PP64_ROWS + r) * 32 + lane] = acc[r];
+    __syncthreads();
+    if ((int)threadIdx.x < nr * 32) {
+      int r = threadIdx.x >> 5, l = threadIdx.x & 31;
+      double s = 0.0;
 #pragma unroll
-  for (int r = 0; r < PP64_ROWS; r++)
-    if (r < it.nij) D.rpp[tb + (long)(it.ij0 + r) * npp + ab] = acc[r];
+      for (int w = 0; w < PP64_WARPS; w++) s += red[(w * PP64_ROWS + r) * 32 + l];
+      if (ab0 + l < npp) D.rpp[tb + (long)(g0 + r) * npp + ab0 + l] = s;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------- finalize
+// End of one update: energy (Eq. ccdcorr, sum of v t over restricted amplitudes) and
+// residual norm per system from the block partials in a fixed order, the |dE| test, the
+// energy history, and the loop condition of the device-side loop.
+__device__ void finalize_systems(const FinArgs& f, LoopCtl* ctl) {
+  __shared__ double sh32f[32];
+  __shared__ int all_done, bad;
+  if (threadIdx.x == 0) {
+    all_done = 1;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int s = 0; s < f.nsys; s++) {
+    double e = 0.0, r = 0.0;
+    for (int k = f.lo[s] + threadIdx.x; k < f.hi[s]; k += blockDim.x) {
+      e += __ldcg(f.eparts + k);
+      r += __ldcg(f.rparts + k);
+    }
+    e = block_sum(e, sh32f);
+    r = block_sum(r, sh32f);
+    if (threadIdx.x == 0) {
+      SysCtl& S = f.sc[s];
+      if (!S.done) {
+        S.iters += 1;
+        S.e_new = e;
+        S.resid = sqrt(r);
+        if (S.iters < f.hist_cap) f.hist[(long)s * f.hist_cap + S.iters] = e;
+        double diff = fabs(e - S.e_old);
+        S.e_old = e;
+        if (!isfinite(e) || !isfinite(r)) bad = 1;
+        if (diff < S.tol) S.done = 1;
+      }
+      if (!S.done) all_done = 0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ctl->iter += 1;
+    int cont = 1;
+    if (ctl->dev_error) {
+      ctl->status = PNM_ETIMEOUT;
+      cont = 0;
+    } else if (bad) {
+      ctl->status = PNM_EDIVERGED;
+      cont = 0;
+    } else if (all_done) {
+      ctl->status = 1;
+      cont = 0;
+    } else if (ctl->iter >= ctl->max_iter) {
+      ctl->status = PNM_ENOTCONV;
+      cont = 0;
+    }
+    if (f.use_cond) cudaGraphSetConditional(f.handle, cont ? 1u : 0u);
+  }
+}
+
+// The last block of a grid to finish runs the finalize step (no waiting: the blocks count
+// themselves out with an atomic after a fence, as in the CUDA threadfence reduction).
+__device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&ctl->blocks_done, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  finalize_systems(f, ctl);
+  if (threadIdx.x == 0) ctl->blocks_done = 0;
 }
 
 // ---------------------------------------------------------------------------- update
-// One CTA per row (channel, ij).  Jacobi step of Eq. (ccd3): the bracket collects v, the
-// non-eps parts of the one-body terms, the pp and hh ladders and P(ij)P(ab) Q; then
-// t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.  The residual of the
-// amplitude equation is R = bracket - eps_ij^ab t.
-__global__ void __launch_bounds__(128) k_update(DevState D, const LoopCtl* __restrict__ ctl,
-                                                const SysCtl* __restrict__ sc) {
+// One CTA per item (channel, ij, 128 pp columns).  Jacobi step of Eq. (ccd3): the bracket
+// collects v, the non-eps parts of the one-body terms, the pp and hh ladders and
+// P(ij)P(ab) Q; then t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.
+// The residual of the amplitude equation is R = bracket - eps_ij^ab t.
+template <typename RT, typename QT>
+__global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
+                                                const int4* __restrict__ items, FinArgs fa,
+                                                const RT* __restrict__ rpp,
+                                                const QT* __restrict__ xq) {
   __shared__ double sh32[32];
-  int2 it = D.row_item[blockIdx.x];
+  int4 it = items[blockIdx.x];
   int c = it.x, ij = it.y;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  int ab_end = min(npp, it.z + (int)blockDim.x);
+  const SysCtl* __restrict__ sc = fa.sc;
   int sys = D.ch_sys[c];
   bool frozen = sc[sys].done != 0;
   bool szero = D.ch_szero[c] != 0;
@@ -194,7 +298,7 @@ __global__ void __launch_bounds__(128) k_update(DevState D, const LoopCtl* __res
   double di = D.dchi[h.x], dj = D.dchi[h.y];
   const double* chi = D.chi_hh + D.ch_vhh_off[c] + ij;  // chi[kl * nh]
   double esum = 0.0, rsum = 0.0;
-  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+  for (int ab = it.z + threadIdx.x; ab < ab_end; ab += blockDim.x) {
     long z = row + ab;
     double tz = t[z];
     double out = tz;
@@ -202,16 +306,16 @@ __global__ void __launch_bounds__(128) k_update(DevState D, const LoopCtl* __res
     if (!frozen) {
       int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
       double num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
-      if (szero) num += D.rpp[z];
+      if (szero) num += (double)rpp[z];
       double hh = 0.0;
       for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
       num += hh;
       int4 q = D.qmap[z];
       double ph = 0.0;
-      if (q.x >= 0) ph += D.xq[q.x];
-      if (q.y >= 0) ph -= D.xq[q.y];
-      if (q.z >= 0) ph -= D.xq[q.z];
-      if (q.w >= 0) ph += D.xq[q.w];
+      if (q.x >= 0) ph += (double)xq[q.x];
+      if (q.y >= 0) ph -= (double)xq[q.y];
+      if (q.z >= 0) ph -= (double)xq[q.z];
+      if (q.w >= 0) ph += (double)xq[q.w];
       num += ph;
       double den = ei + ej - D.eps[p.x] - D.eps[p.y];
       double tnew = num / den;
@@ -228,7 +332,19 @@ __global__ void __launch_bounds__(128) k_update(DevState D, const LoopCtl* __res
     D.eparts[blockIdx.x] = esum;
     D.rparts[blockIdx.x] = rsum;
   }
+  last_block_finalize(fa, ctl);
 }
+
+template <typename RT, typename QT>
+void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
+                   cudaGraphConditionalHandle h) {
+  k_update<RT, QT><<<ctx->n_upd_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->upd_items,
+                                                               fin_args(ctx, use_cond, h), rpp, xq);
+}
+template void launch_update<double, double>(pnm_ctx*, const double*, const double*, int,
+                                            cudaGraphConditionalHandle);
+template void launch_update<float, float>(pnm_ctx*, const float*, const float*, int,
+                                          cudaGraphConditionalHandle);
 
 // Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
 __global__ void __launch_bounds__(128) k_init(DevState D, int init) {
@@ -315,60 +431,8 @@ __global__ void k_start(const double* __restrict__ parts, const int* __restrict_
   if (threadIdx.x == 0) {
     ctl->iter = 0;
     ctl->status = 0;
-  }
-}
-
-// End of one update: energies, convergence per system, loop condition.
-__global__ void k_finalize(const double* __restrict__ eparts, const double* __restrict__ rparts,
-                           const int* __restrict__ row_lo, const int* __restrict__ row_hi,
-                           int nsys, SysCtl* __restrict__ sc, LoopCtl* __restrict__ ctl,
-                           double* __restrict__ hist, int hist_cap, int use_cond,
-                           cudaGraphConditionalHandle handle) {
-  __shared__ double sh32[32];
-  __shared__ int all_done, bad;
-  if (threadIdx.x == 0) {
-    all_done = 1;
-    bad = 0;
-  }
-  __syncthreads();
-  for (int s = 0; s < nsys; s++) {
-    double e = 0.0, r = 0.0;
-    for (int k = row_lo[s] + threadIdx.x; k < row_hi[s]; k += blockDim.x) {
-      e += eparts[k];
-      r += rparts[k];
-    }
-    e = block_sum(e, sh32);
-    r = block_sum(r, sh32);
-    if (threadIdx.x == 0) {
-      SysCtl& S = sc[s];
-      if (!S.done) {
-        S.iters += 1;
-        S.e_new = e;
-        S.resid = sqrt(r);
-        if (S.iters < hist_cap) hist[(long)s * hist_cap + S.iters] = e;
-        double diff = fabs(e - S.e_old);
-        S.e_old = e;
-        if (!isfinite(e) || !isfinite(r)) bad = 1;
-        if (diff < S.tol) S.done = 1;
-      }
-      if (!S.done) all_done = 0;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    ctl->iter += 1;
-    int cont = 1;
-    if (bad) {
-      ctl->status = PNM_EDIVERGED;
-      cont = 0;
-    } else if (all_done) {
-      ctl->status = 1;
-      cont = 0;
-    } else if (ctl->iter >= ctl->max_iter) {
-      ctl->status = PNM_ENOTCONV;
-      cont = 0;
-    }
-    if (use_cond) cudaGraphSetConditional(handle, cont ? 1u : 0u);
+    ctl->blocks_done = 0;
+    ctl->dev_error = 0;
   }
 }
 
@@ -401,30 +465,52 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->row_lo_d = d;
   ctx->row_hi_d = d + nsys;
   ctx->lut_off_d = d + 2 * nsys;
-  // pp work list (S_z = 0 channels): 128 columns x up to 8 rows
-  std::vector<PPItem> items;
-  std::vector<int2> abit;
+  // pp work list (S_z = 0 channels): one item per 32 pp columns
+  std::vector<int2> items, abit;
+  std::vector<int4> upd;
+  std::vector<int> ulo(nsys), uhi(nsys);
   int max_npp = 0;
   for (int c = 0; c < ctx->nch; c++) {
-    int npp = ctx->h_npp[c], nh = ctx->h_nhh[c];
+    int npp = ctx->h_npp[c];
     max_npp = std::max(max_npp, npp);
     for (int ab0 = 0; ab0 < npp; ab0 += 128) abit.push_back(make_int2(c, ab0));
     if (!ctx->h_szero[c]) continue;
-    for (int ij0 = 0; ij0 < nh; ij0 += PP64_ROWS)
-      for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS)
-        items.push_back(PPItem{c, ab0, ij0, std::min(PP64_ROWS, nh - ij0)});
+    for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS) items.push_back(make_int2(c, ab0));
+  }
+  // update items (channel, ij, first column), 128 columns each, grouped by system
+  for (int k = 0; k < nsys; k++) {
+    ulo[k] = (int)upd.size();
+    for (int r = ctx->sys[k].row_begin; r < ctx->sys[k].row_end; r++) {
+      int2 row = ctx->h_rows[r];
+      for (int ab0 = 0; ab0 < ctx->h_npp[row.x]; ab0 += 128) upd.push_back(make_int4(row.x, row.y, ab0, 0));
+    }
+    uhi[k] = (int)upd.size();
   }
   ctx->max_npp = max_npp;
   ctx->n_pp_items = (int)items.size();
-  ctx->pp_items = (PPItem*)dmalloc(ctx, sizeof(PPItem) * std::max<size_t>(1, items.size()));
+  ctx->pp_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, items.size()));
   if (!items.empty())
-    CUDA_TRY(cudaMemcpyAsync(ctx->pp_items, items.data(), sizeof(PPItem) * items.size(),
+    CUDA_TRY(cudaMemcpyAsync(ctx->pp_items, items.data(), sizeof(int2) * items.size(),
                              cudaMemcpyHostToDevice, s));
   ctx->n_ab_items = (int)abit.size();
   ctx->ab_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, abit.size()));
   if (!abit.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->ab_items, abit.data(), sizeof(int2) * abit.size(),
                              cudaMemcpyHostToDevice, s));
+  ctx->n_upd_items = (int)upd.size();
+  ctx->upd_items = (int4*)dmalloc(ctx, sizeof(int4) * std::max<size_t>(1, upd.size()));
+  if (!upd.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->upd_items, upd.data(), sizeof(int4) * upd.size(),
+                             cudaMemcpyHostToDevice, s));
+  int* ud = (int*)dmalloc(ctx, sizeof(int) * 2 * nsys);
+  CUDA_TRY(cudaMemcpyAsync(ud, ulo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(ud + nsys, uhi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  ctx->upd_lo_d = ud;
+  ctx->upd_hi_d = ud + nsys;
+  // partial sums: one per update item (at least one per row for init/MBPT2)
+  size_t nparts = std::max<size_t>(upd.size(), (size_t)ctx->nrows);
+  ctx->d.eparts = (double*)dmalloc(ctx, sizeof(double) * nparts);
+  ctx->d.rparts = (double*)dmalloc(ctx, sizeof(double) * nparts);
   int mx = 0;
   for (int x = 0; x < ctx->nx; x++) mx = std::max(mx, std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]));
   ctx->max_x_dim = mx;
@@ -432,10 +518,11 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
   size_t ph_smem = sizeof(double) * 3 * (size_t)mx * mx;
-  size_t pp_smem = sizeof(double) * PP64_ROWS * (size_t)max_npp;
+  size_t pp_smem = pp64_smem(max_npp);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
-  CUDA_TRY(cudaFuncSetAttribute(k_ph64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
   CUDA_TRY(cudaFuncSetAttribute(k_pp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp_smem));
   CUDA_TRY(cudaStreamSynchronize(s));
 }
@@ -477,20 +564,89 @@ void pnm_mbpt2_all(pnm_ctx* ctx, double* out) {
 }
 
 // The body of one update, enqueued on the context stream (FP64 path).
+FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
+  FinArgs f;
+  f.eparts = ctx->d.eparts;
+  f.rparts = ctx->d.rparts;
+  f.lo = ctx->upd_lo_d;
+  f.hi = ctx->upd_hi_d;
+  f.nsys = (int)ctx->sys.size();
+  f.sc = ctx->sysctl;
+  f.hist = ctx->hist;
+  f.hist_cap = ctx->hist_cap;
+  f.use_cond = use_cond;
+  f.handle = h;
+  return f;
+}
+
+void pnm_launch_pp64(pnm_ctx* ctx) {
+  if (ctx->n_pp_items > 0)
+    k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_npp), ctx->stream>>>(
+        ctx->d, ctx->ctl, ctx->pp_items);
+}
+
+// One-body intermediates and <kl|chi|ij> (shared by both precision modes, FP64).
+void pnm_enqueue_stats(pnm_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  DevState& D = ctx->d;
+  prof_begin(ctx, KID_TSTATS);
+  k_tstats<<<ctx->nrows + ctx->n_ab_items, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
+  prof_end(ctx);
+  prof_begin(ctx, KID_DCHI);
+  k_dchi<<<(ctx->nsp_total * 32 + 255) / 256, 256, 0, s>>>(D, ctx->nsp_total);
+  prof_end(ctx);
+}
+
 static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
-  int nsys = (int)ctx->sys.size();
-  k_tstats<<<ctx->nrows + ctx->n_ab_items, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
-  k_dchi<<<(ctx->nsp_total + 127) / 128, 128, 0, s>>>(D, ctx->nsp_total);
-  if (ctx->nx > 0)
-    k_ph64<<<ctx->nx, 256, sizeof(double) * 3 * ctx->max_x_dim * ctx->max_x_dim, s>>>(D, ctx->ctl);
-  if (ctx->n_pp_items > 0)
-    k_pp64<<<ctx->n_pp_items, PP64_COLS, sizeof(double) * PP64_ROWS * ctx->max_npp, s>>>(
-        D, ctx->ctl, ctx->pp_items);
-  k_update<<<ctx->nrows, 128, 0, s>>>(D, ctx->ctl, ctx->sysctl);
-  k_finalize<<<1, 256, 0, s>>>(D.eparts, D.rparts, ctx->row_lo_d, ctx->row_hi_d, nsys,
-                               ctx->sysctl, ctx->ctl, ctx->hist, ctx->hist_cap, use_cond, h);
+  pnm_enqueue_stats(ctx);
+  if (ctx->nx > 0) {
+    prof_begin(ctx, KID_PH64);
+    launch_ph<double>(ctx, D.x_w, D.x_v1, D.xq);
+    prof_end(ctx);
+  }
+  if (ctx->n_pp_items > 0) {
+    prof_begin(ctx, KID_PP64);
+    pnm_launch_pp64(ctx);
+    prof_end(ctx);
+  }
+  prof_begin(ctx, KID_UPDATE);
+  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h);
+  prof_end(ctx);
+}
+
+const char* const pnm_kernel_names[PNM_NKERNELS] = {
+    "k_tstats", "k_dchi", "k_ph64", "k_pp64", "k_update", "k_finalize(unused)",
+    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack"};
+
+void prof_begin(pnm_ctx* ctx, int kid) {
+  if (!ctx->prof_live) return;
+  size_t k = ctx->prof_pending.size();
+  if (k >= ctx->prof_ev.size()) {
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    ctx->prof_ev.push_back({a, b});
+  }
+  ctx->prof_pending.push_back(kid);
+  CUDA_TRY(cudaEventRecord(ctx->prof_ev[k].first, ctx->stream));
+}
+
+void prof_end(pnm_ctx* ctx) {
+  if (!ctx->prof_live) return;
+  CUDA_TRY(cudaEventRecord(ctx->prof_ev[ctx->prof_pending.size() - 1].second, ctx->stream));
+}
+
+void prof_collect(pnm_ctx* ctx) {
+  for (size_t k = 0; k < ctx->prof_pending.size(); k++) {
+    float ms = 0;
+    CUDA_TRY(cudaEventSynchronize(ctx->prof_ev[k].second));
+    CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_ev[k].first, ctx->prof_ev[k].second));
+    ctx->prof_ms[ctx->prof_pending[k]] += ms;
+    ctx->prof_n[ctx->prof_pending[k]] += 1;
+  }
+  ctx->prof_pending.clear();
 }
 
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
@@ -546,13 +702,16 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alp
     cudaGraphExec_t ge = graph_for(ctx, mode);
     CUDA_TRY(cudaGraphLaunch(ge, s));
   } else {
+    ctx->prof_live = ctx->prof_on;
     for (;;) {
       pnm_enqueue_body(ctx, mode, 0, 0);
       CUDA_TRY(cudaGetLastError());
       CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
+      if (ctx->prof_live) prof_collect(ctx);
       if (hc.status != 0) break;
     }
+    ctx->prof_live = false;
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));

@@ -1,12 +1,469 @@
-// mixed.cu -- mixed-precision iteration body (filled in with the tcgen05 pp ladder).
+// mixed.cu -- mixed-precision CCD update.
+//
+// The particle-particle ladder 1/2 sum_cd <ab|v|cd> t_cd^ij (Eq. ccd3 with the
+// intermediate <ab|chi|cd> = <ab|v|cd> of Sec. "Developing a CCD code") is the dense
+// per-channel contraction of the method.  Here it runs on the 5th-generation tensor cores:
+//
+//   D(ab, ij) = sum_cd V(ab, cd) t(ij, cd)          (M = ab tile of 128, N = n_hh padded
+//                                                    to 16/32/48, K = cd)
+//   with V = V_hi + V_lo and t = t_hi + t_lo split into BF16 pairs, and
+//   D = V_hi t_hi + V_hi t_lo + V_lo t_hi accumulated in FP32 in tensor memory (TMEM).
+//
+// V is written once per context into HBM already in the UMMA canonical K-major layout
+// (8-row x 16-byte core matrices, no swizzle), one 32 KB chunk (hi, lo) per 128 x 64 tile,
+// so each tile moves with one bulk asynchronous copy (the TMA engine) into a 3-stage
+// shared-memory ring guarded by mbarriers.  Warp 0 lane 0 issues the copies, warp 1 lane 0
+// issues tcgen05.mma and commits each stage back to the producer, all four warps read the
+// accumulator with tcgen05.ld.  The other contractions of the mixed update run in FP32 on
+// the CUDA cores; denominators, mixing, energy and residual stay in FP64.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
 #include "pnm_context.cuh"
 
-void pnm_prepare_mixed(pnm_ctx*) {
-  throw PnmError{PNM_EINVAL, "mixed precision is not available in this build"};
+namespace {
+
+constexpr int TC_M = 128;        // ab rows per tile (one TMEM lane per row)
+constexpr int TC_BK = 64;        // cd elements per k-block
+constexpr int TC_STAGES = 3;
+constexpr uint32_t A_PLANE = TC_M * TC_BK * 2;  // bytes of one BF16 plane of a V tile
+constexpr uint32_t CORE_LBO = 128;              // next core matrix along K
+constexpr uint32_t CORE_SBO = (TC_BK / 8) * 128;  // next 8-row group along M/N
+
+struct TCItem {
+  int ch, mt, nkb, npad;
+  int npp, nhh, pad0, pad1;
+  long voff;   // element offset of tile (mt, 0) in the V tile arena
+  long boff;   // element offset of k-block 0 in the t tile arena
+  long toff;   // element offset of the channel in the t layout
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after 2^22 polls (of the order of a second) and reports failure.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-void pnm_enqueue_body_mixed(pnm_ctx*, int, cudaGraphConditionalHandle) {
-  throw PnmError{PNM_EINVAL, "mixed precision is not available in this build"};
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
+  d |= (uint64_t)((CORE_LBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((CORE_SBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;               // base offset 0, layout type 0 (no swizzle)
 }
 
-void pnm_free_mixed(pnm_ctx*) {}
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Element offset inside a (rows x 64) BF16 plane laid out as core matrices.
+__device__ __forceinline__ int core_off(int r, int k) {
+  return (((r >> 3) * (TC_BK / 8) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn((float)x);
+  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+}
+
+// ------------------------------------------------------------------------ kernels
+// V tiles of the S_z = 0 channels (setup): one CTA per (item, k-block).
+__global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restrict__ v_pppp,
+                         const long* __restrict__ ch_vpp_off, __nv_bfloat16* __restrict__ vt) {
+  TCItem it = items[blockIdx.x];
+  int kb = blockIdx.y;
+  if (kb >= it.nkb) return;
+  const double* V = v_pppp + ch_vpp_off[it.ch];
+  __nv_bfloat16* hi = vt + it.voff + (long)kb * 2 * (TC_M * TC_BK);
+  __nv_bfloat16* lo = hi + TC_M * TC_BK;
+  for (int e = threadIdx.x; e < TC_M * TC_BK; e += blockDim.x) {
+    int r = e / TC_BK, k = e % TC_BK;
+    int ab = it.mt * TC_M + r, cd = kb * TC_BK + k;
+    double x = (ab < it.npp && cd < it.npp) ? V[(long)cd * it.npp + ab] : 0.0;
+    __nv_bfloat16 h, l;
+    split_bf16(x, h, l);
+    hi[core_off(r, k)] = h;
+    lo[core_off(r, k)] = l;
+  }
+}
+
+// t tiles of the S_z = 0 channels (every update): one CTA per (channel, k-block).
+__global__ void k_pack_t(const int4* __restrict__ pk, const long* __restrict__ pk_boff,
+                         DevState D, const LoopCtl* __restrict__ ctl, __nv_bfloat16* __restrict__ bt) {
+  int4 p = pk[blockIdx.x];  // (channel, k-block, npad, 0)
+  int c = p.x, kb = p.y, npad = p.z;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  const double* t = cur_t(D, ctl) + D.ch_t_off[c];
+  __nv_bfloat16* hi = bt + pk_boff[blockIdx.x];
+  __nv_bfloat16* lo = hi + npad * TC_BK;
+  for (int e = threadIdx.x; e < npad * TC_BK; e += blockDim.x) {
+    int n = e / TC_BK, k = e % TC_BK;
+    int cd = kb * TC_BK + k;
+    double x = (n < nh && cd < npp) ? t[(long)n * npp + cd] : 0.0;
+    __nv_bfloat16 h, l;
+    split_bf16(x, h, l);
+    hi[core_off(n, k)] = h;
+    lo[core_off(n, k)] = l;
+  }
+}
+
+// The grouped tensor-core pp ladder: one CTA (4 warps) per (channel, 128-row ab tile).
+__global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ items,
+                                                  const __nv_bfloat16* __restrict__ vt,
+                                                  const __nv_bfloat16* __restrict__ bt,
+                                                  float* __restrict__ rpp32, LoopCtl* __restrict__ ctl,
+                                                  uint32_t stage_bytes) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const TCItem it = items[blockIdx.x];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  unsigned char* stage0 = smem + 1024;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
+  const uint32_t ncols = it.npad <= 32 ? 32u : 64u;
+  __shared__ int err;
+
+  if (threadIdx.x == 0) {
+    err = 0;
+    for (int s = 0; s < TC_STAGES; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    mbar_fence_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(tslot, ncols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: one 32 KB copy of the V tile (hi, lo) and one of the t tile per stage
+    const __nv_bfloat16* va = vt + it.voff;
+    const __nv_bfloat16* tb = bt + it.boff;
+    int issued = 0;
+    for (int kb = 0; kb < it.nkb; kb++) {
+      int s = kb % TC_STAGES, use = kb / TC_STAGES;
+      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+        err = 1;
+        break;
+      }
+      unsigned char* st = stage0 + s * stage_bytes;
+      mbar_expect_tx(&full[s], 2 * A_PLANE + 2 * b_plane);
+      bulk_g2s(st, va + (long)kb * 2 * (TC_M * TC_BK), 2 * A_PLANE, &full[s]);
+      bulk_g2s(st + 2 * A_PLANE, tb + (long)kb * 2 * (it.npad * TC_BK), 2 * b_plane, &full[s]);
+      issued = kb + 1;
+    }
+    // every copy this thread started has landed before the CTA may retire
+    for (int kb = max(0, issued - TC_STAGES); kb < issued; kb++)
+      if (!mbar_wait(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1)) err = 1;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_bf16(TC_M, it.npad);
+    for (int kb = 0; kb < it.nkb; kb++) {
+      int s = kb % TC_STAGES, use = kb / TC_STAGES;
+      if (!mbar_wait(&full[s], use & 1)) {
+        err = 1;
+        break;
+      }
+      tc_fence_after();
+      unsigned char* a_hi = stage0 + s * stage_bytes;
+      unsigned char* a_lo = a_hi + A_PLANE;
+      unsigned char* b_hi = a_hi + 2 * A_PLANE;
+      unsigned char* b_lo = b_hi + b_plane;
+#pragma unroll
+      for (int ks = 0; ks < TC_BK / 16; ks++) {
+        uint32_t o = ks * 2 * 128;  // two core matrices of K per MMA
+        uint64_t ah = smem_desc(a_hi + o), al = smem_desc(a_lo + o);
+        uint64_t bh = smem_desc(b_hi + o), bl = smem_desc(b_lo + o);
+        umma_bf16(tbase, ah, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+        umma_bf16(tbase, ah, bl, idesc, 1u);
+        umma_bf16(tbase, al, bh, idesc, 1u);
+      }
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  // epilogue: TMEM lane = ab row, column = ij
+  bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  const int row = warp * 32 + lane;
+  const int ab = it.mt * TC_M + row;
+  for (int c0 = 0; c0 < it.npad; c0 += 16) {
+    uint32_t r[16];
+    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    if (ok && ab < it.npp) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        int ij = c0 + j;
+        if (ij < it.nhh) rpp32[it.toff + (long)ij * it.npp + ab] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) tmem_dealloc(tbase, ncols);
+  if (threadIdx.x == 0 && (err || !ok)) atomicExch(&ctl->dev_error, 1);
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+template <typename T>
+T* mdalloc(pnm_ctx* ctx, size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    throw PnmError{PNM_ENOMEM, "cudaMalloc (mixed precision arenas) failed"};
+  }
+  ctx->owned.push_back(p);
+  return (T*)p;
+}
+
+}  // namespace
+
+struct MixedState {
+  __nv_bfloat16* vt = nullptr;
+  __nv_bfloat16* bt = nullptr;
+  float *rpp32 = nullptr, *xw32 = nullptr, *xv132 = nullptr, *xq32 = nullptr;
+  TCItem* items = nullptr;
+  int nitems = 0;
+  int4* pk = nullptr;
+  long* pk_boff = nullptr;
+  int npk = 0;
+  uint32_t stage_bytes = 0;
+  size_t smem = 0;
+};
+
+void pnm_prepare_mixed(pnm_ctx* ctx) {
+  if (ctx->mixed) return;
+  cudaStream_t s = ctx->stream;
+  MixedState* M = new MixedState();
+  try {
+    std::vector<TCItem> items;
+    std::vector<int4> pk;
+    std::vector<long> pk_boff;
+    long voff = 0, boff = 0;
+    int max_npad = 16, max_nkb = 1;
+    for (int c = 0; c < ctx->nch; c++) {
+      if (!ctx->h_szero[c]) continue;
+      int npp = ctx->h_npp[c], nh = ctx->h_nhh[c];
+      int npad = std::max(16, (nh + 15) / 16 * 16);
+      if (npad > 64) throw PnmError{PNM_EINVAL, "n_hh > 64 in one channel: tensor-core tile too small"};
+      int nmt = (npp + TC_M - 1) / TC_M, nkb = (npp + TC_BK - 1) / TC_BK;
+      max_npad = std::max(max_npad, npad);
+      max_nkb = std::max(max_nkb, nkb);
+      for (int mt = 0; mt < nmt; mt++) {
+        TCItem t{};
+        t.ch = c;
+        t.mt = mt;
+        t.nkb = nkb;
+        t.npad = npad;
+        t.npp = npp;
+        t.nhh = nh;
+        t.voff = voff + (long)mt * nkb * 2 * (TC_M * TC_BK);
+        t.boff = boff;
+        t.toff = ctx->h_t_off[c];
+        items.push_back(t);
+      }
+      for (int kb = 0; kb < nkb; kb++) {
+        pk.push_back(make_int4(c, kb, npad, 0));
+        pk_boff.push_back(boff + (long)kb * 2 * npad * TC_BK);
+      }
+      voff += (long)nmt * nkb * 2 * (TC_M * TC_BK);
+      boff += (long)nkb * 2 * npad * TC_BK;
+    }
+    M->nitems = (int)items.size();
+    M->npk = (int)pk.size();
+    M->vt = mdalloc<__nv_bfloat16>(ctx, voff);
+    M->bt = mdalloc<__nv_bfloat16>(ctx, boff);
+    M->items = mdalloc<TCItem>(ctx, items.size());
+    M->pk = mdalloc<int4>(ctx, pk.size());
+    M->pk_boff = mdalloc<long>(ctx, pk_boff.size());
+    if (!items.empty())
+      CUDA_TRY(cudaMemcpyAsync(M->items, items.data(), sizeof(TCItem) * items.size(), cudaMemcpyHostToDevice, s));
+    if (!pk.empty()) {
+      CUDA_TRY(cudaMemcpyAsync(M->pk, pk.data(), sizeof(int4) * pk.size(), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(M->pk_boff, pk_boff.data(), sizeof(long) * pk_boff.size(),
+                               cudaMemcpyHostToDevice, s));
+    }
+    M->rpp32 = mdalloc<float>(ctx, ctx->nt);
+    M->xw32 = mdalloc<float>(ctx, ctx->nxt);
+    M->xv132 = mdalloc<float>(ctx, ctx->nxc);
+    M->xq32 = mdalloc<float>(ctx, ctx->nxt);
+    if (ctx->nxt > 0)
+      k_to_float<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, s>>>(ctx->d.x_w, M->xw32, ctx->nxt);
+    if (ctx->nxc > 0)
+      k_to_float<<<(unsigned)((ctx->nxc + 255) / 256), 256, 0, s>>>(ctx->d.x_v1, M->xv132, ctx->nxc);
+    if (M->nitems > 0)
+      k_pack_v<<<dim3(M->nitems, max_nkb), 256, 0, s>>>(M->items, ctx->d.v_pppp, ctx->d.ch_vpp_off, M->vt);
+    CUDA_TRY(cudaGetLastError());
+    M->stage_bytes = (2 * A_PLANE + 2 * (uint32_t)max_npad * TC_BK * 2 + 1023) / 1024 * 1024;
+    M->smem = 1024 + (size_t)TC_STAGES * M->stage_bytes + 8192;  // tail guard
+    if (M->smem > 227 * 1024) throw PnmError{PNM_EINVAL, "tensor-core stage ring exceeds shared memory"};
+    CUDA_TRY(cudaFuncSetAttribute(k_pp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M->smem));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete M;
+    throw;
+  }
+  ctx->mixed = M;
+}
+
+void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
+  cudaStream_t s = ctx->stream;
+  MixedState* M = ctx->mixed;
+  DevState& D = ctx->d;
+  if (M->npk > 0) {
+    prof_begin(ctx, KID_PACK);
+    k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, D, ctx->ctl, M->bt);
+    prof_end(ctx);
+  }
+  pnm_enqueue_stats(ctx);
+  if (ctx->nx > 0) {
+    prof_begin(ctx, KID_PH32);
+    launch_ph<float>(ctx, M->xw32, M->xv132, M->xq32);
+    prof_end(ctx);
+  }
+  if (M->nitems > 0) {
+    prof_begin(ctx, KID_PP_TC);
+    k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
+    prof_end(ctx);
+  }
+  prof_begin(ctx, KID_UPDATE_MIX);
+  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h);
+  prof_end(ctx);
+}
+
+void pnm_free_mixed(pnm_ctx* ctx) {
+  delete ctx->mixed;  // device arenas are in ctx->owned
+  ctx->mixed = nullptr;
+}
+
+// Apply only the particle-particle ladder to amplitudes t (library order, system `sys`):
+// r = sum_{c<d} <ab|v|cd> t_cd^ij on S_z = 0 channels, 0 elsewhere.  Uses the solver's
+// buffers (the iteration state is reset).
+void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n) {
+  const SysInfo& S = ctx->sys[sys];
+  cudaStream_t s = ctx->stream;
+  if (n != (size_t)(S.t_end - S.t_begin)) throw PnmError{PNM_EINVAL, "size mismatch"};
+  if (precision == PNM_PREC_BF16X3) pnm_prepare_mixed(ctx);
+  int zero = 0;
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  std::vector<double> out(ctx->nt, 0.0);
+  if (precision == PNM_PREC_BF16X3) {
+    MixedState* M = ctx->mixed;
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * ctx->nt, s));
+    if (M->npk > 0) k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
+    if (M->nitems > 0)
+      k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<float> f(ctx->nt);
+    CUDA_TRY(cudaMemcpyAsync(f.data(), M->rpp32, sizeof(float) * ctx->nt, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (long z = 0; z < ctx->nt; z++) out[z] = f[z];
+  } else {
+    CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * ctx->nt, s));
+    pnm_launch_pp64(ctx);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out.data(), ctx->d.rpp, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget"};
+  for (int c = S.ch_begin; c < S.ch_end; c++) {
+    long o = ctx->h_t_off[c], len = (long)ctx->h_nhh[c] * ctx->h_npp[c];
+    for (long z = 0; z < len; z++) r[o - S.t_begin + z] = ctx->h_szero[c] ? out[o + z] : 0.0;
+  }
+}

@@ -7,6 +7,13 @@
 
 struct MixedState;  // mixed-precision operand arenas (mixed.cu)
 
+// Kernel ids of the per-kernel profiler.
+enum {
+  KID_TSTATS = 0, KID_DCHI, KID_PH64, KID_PP64, KID_UPDATE, KID_FINALIZE,
+  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, PNM_NKERNELS
+};
+extern const char* const pnm_kernel_names[PNM_NKERNELS];
+
 struct pnm_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -26,8 +33,11 @@ struct pnm_ctx {
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
 
   // work lists
-  PPItem* pp_items = nullptr;
+  int2* pp_items = nullptr;   // (channel, first pp column) of the FP64 pp ladder
   int n_pp_items = 0;
+  int4* upd_items = nullptr;  // (channel, ij, first pp column) of the update
+  int n_upd_items = 0;
+  int *upd_lo_d = nullptr, *upd_hi_d = nullptr;  // per system update-item ranges
   int2* ab_items = nullptr;
   int n_ab_items = 0;
 
@@ -46,6 +56,13 @@ struct pnm_ctx {
   unsigned long long cond_handle_for_mode[4] = {0, 0, 0, 0};
 
   MixedState* mixed = nullptr;
+
+  // per-kernel CUDA-event profiling of host-driven solves (never active during capture)
+  bool prof_on = false, prof_live = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+  std::vector<int> prof_pending;  // kernel id per used event pair
+  double prof_ms[PNM_NKERNELS] = {};
+  int prof_n[PNM_NKERNELS] = {};
 
   // timings (ms)
   double t_setup = 0, t_mbpt2 = 0, t_solve = 0, t_mixed = 0, t_refine = 0;
@@ -66,3 +83,15 @@ void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);
 int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alpha);
 void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
+void prof_begin(pnm_ctx* ctx, int kid);
+void prof_end(pnm_ctx* ctx);
+void prof_collect(pnm_ctx* ctx);
+FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
+void pnm_enqueue_stats(pnm_ctx* ctx);
+void pnm_launch_pp64(pnm_ctx* ctx);
+void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
+template <typename T_>
+void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq);
+template <typename RT, typename QT>
+void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
+                   cudaGraphConditionalHandle h);

@@ -91,6 +91,8 @@ struct PPItem {
 // Solve-loop control block in device memory (one per context).
 struct LoopCtl {
   int iter;          // updates made in the current solve
+  int blocks_done;   // blocks of the current update that have finished (last-block finalize)
+  int dev_error;     // set by a kernel whose bounded wait ran out (the loop then stops)
   int max_iter;
   int status;        // 0 running, 1 converged, PNM_ENOTCONV, PNM_EDIVERGED
   int mode;          // 0 FP64 iteration, 1 mixed iteration
@@ -104,9 +106,31 @@ struct SysCtl {
   int iters;
 };
 
+// Arguments of the end-of-update step (energy, convergence test, loop condition).
+struct FinArgs {
+  const double* eparts;
+  const double* rparts;
+  const int* lo;        // per system: first partial
+  const int* hi;        // per system: one past the last partial
+  int nsys;
+  SysCtl* sc;
+  double* hist;
+  int hist_cap;
+  int use_cond;
+  cudaGraphConditionalHandle handle;
+};
+
 // --------------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ int dot3(int x, int y, int z) { return x * x + y * y + z * z; }
+
+// Double-buffered amplitudes: an update reads t[iter & 1] and writes the other buffer.
+__device__ __forceinline__ const double* cur_t(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t1 : D.t0;
+}
+__device__ __forceinline__ double* next_t(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t0 : D.t1;
+}
 
 // Antisymmetrized Minnesota element for two neutrons.  With P_tau = 1 the exchange form
 // reduces to 1/2 (V_R + V_S)(1 - P_sigma) (the V_T term cancels), whose antisymmetrized

@@ -749,8 +749,6 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   D.sab = dalloc<double>(pp_acc, ctx->owned);
   D.sij = dalloc<double>(hh_acc, ctx->owned);
   D.xq = dalloc<double>(xt_acc, ctx->owned);
-  D.eparts = dalloc<double>(ctx->nrows, ctx->owned);
-  D.rparts = dalloc<double>(ctx->nrows, ctx->owned);
   D.occ_off = dalloc<int>(nsp_total + 1, ctx->owned);
 
   // ---- pair lists, maps, V blocks per system

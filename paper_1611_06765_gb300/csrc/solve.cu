@@ -81,6 +81,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   if (status == 1) return PNM_OK;
   if (status == PNM_ENOTCONV) pnm_set_error(status, "iteration cap reached before convergence");
   if (status == PNM_EDIVERGED) pnm_set_error(status, "NaN or Inf in the energy or residual");
+  if (status == PNM_ETIMEOUT) pnm_set_error(status, "a device-side wait ran out of its budget");
   return status;
 }
 

@@ -1,0 +1,81 @@
+"""Mixed-precision path (BF16x3 tensor-core pp ladder, FP32 contractions, FP64
+denominators/energy) against the FP64 oracle, through the C ABI.
+
+Error bound of one BF16x3 product: with x = hi + lo + d, |hi - x| <= 2^-9 |x|,
+|lo| <= 2^-9 |x| and |d| <= 2^-18 |x|, the dropped and rounding terms sum to at most
+3 * 2^-18 |V||t| (about 1.2e-5); FP32 accumulation over K <= 1200 terms adds at most
+K * 2^-24 relative in the worst case.  The tests use 5e-5 * sum_cd |V||t| per element.
+"""
+import numpy as np
+import pytest
+
+from conftest import minnesota_params
+from inputs import random_amplitudes
+from oracle import channel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1611_06765_gb300 import build
+    build.build()
+    import paper_1611_06765_gb300 as P
+    return P
+
+
+def _blocks(o, t):
+    """Per-channel (offset, nhh, npp) of the library layout (hh rows, pp contiguous)."""
+    tab = o.channel_tables()
+    off = 0
+    for c, (nh, np_) in enumerate(zip(tab["nhh"], tab["npp"])):
+        yield c, off, int(nh), int(np_)
+        off += int(nh) * int(np_)
+
+
+@pytest.mark.parametrize("N,rho,n2", [(14, 0.08, 4), (14, 0.08, 20), (66, 0.16, 36)])
+def test_pp_ladder_operator(pkg, N, rho, n2):
+    g = pkg.Context(N, rho, n2, params=minnesota_params())
+    o = channel.OracleSystem(N, rho, n2, minnesota_params())
+    n = len(g.amplitude_labels())
+    t = random_amplitudes(n, seed=7)
+    r64 = g.apply_pp_ladder(t, precision=pkg.PNM_PREC_FP64)
+    r16 = g.apply_pp_ladder(t, precision=pkg.PNM_PREC_BF16X3)
+    ref = np.zeros(n)
+    bound = np.zeros(n)
+    for c, off, nh, npp in _blocks(o, t):
+        V = o.vpp_block(c)
+        tb = t[off:off + nh * npp].reshape(nh, npp)
+        ref[off:off + nh * npp] = (tb @ V).ravel()
+        bound[off:off + nh * npp] = (np.abs(tb) @ np.abs(V)).ravel()
+    scale = np.max(np.abs(ref))
+    assert scale > 0
+    assert np.max(np.abs(r64 - ref)) <= 1e-12 * scale
+    assert np.all(np.abs(r16 - ref) <= 5e-5 * bound + 1e-30)
+    g.close()
+
+
+@pytest.mark.parametrize("N,rho,n2", [(14, 0.08, 4), (14, 0.08, 20), (66, 0.16, 36)])
+def test_mixed_solve_within_target(pkg, N, rho, n2):
+    """E_corr/N of the mixed path after two FP64 refinement sweeps within 1e-6 MeV of the
+    FP64 oracle."""
+    g = pkg.Context(N, rho, n2, params=minnesota_params())
+    o = channel.OracleSystem(N, rho, n2, minnesota_params())
+    dE_o, _, _, _ = o.ccd(alpha=0.5, tol=1e-10 * N, maxit=300)
+    dE, it, _, rc = g.solve(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-7,
+                            max_iter=300, refine_sweeps=2, allow=(pkg.PNM_ENOTCONV,))
+    assert abs(dE[0] - dE_o) / N < 1e-6
+    g.close()
+
+
+def test_mixed_then_fp64_agree_on_fixed_point(pkg):
+    """Without refinement the mixed fixed point is already within the target; FP64 sweeps
+    from it move the energy by less than 1e-6 MeV per particle."""
+    N = 14
+    g = pkg.Context(N, 0.08, 20, params=minnesota_params())
+    dEm, _, _, _ = g.solve(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-8,
+                           max_iter=300)
+    dE64, _, _, _ = g.solve(precision=pkg.PNM_PREC_FP64, alpha=0.5, tol=1e-30, tol_per_N=1e-8,
+                            max_iter=300)
+    assert abs(dEm[0] - dE64[0]) / N < 1e-6
+    g.close()
