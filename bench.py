@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x3"])
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / N=66 comparison runs")
     return ap.parse_args()
 
 
@@ -207,6 +208,43 @@ def run_reference(a):
     return 0
 
 
+def timed_solves(ctx, solve_kw, steps, flush, stream, torch):
+    """Per-solve device times (ms) with an L2 flush outside each timed region."""
+    evs, iters, dEs = [], [], []
+    for _ in range(steps):
+        flush.zero_()  # 512 MB write > 129 MB L2, outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dE, it, _, _ = ctx.solve(**solve_kw)
+        e1.record(stream)
+        evs.append((e0, e1))
+        iters.append(int(it[0]))
+        dEs.append(float(dE[0]))
+    torch.cuda.synchronize()
+    return [e0.elapsed_time(e1) for e0, e1 in evs], iters, dEs
+
+
+def solve_kwargs(P, prec, refine):
+    return dict(precision=prec, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
+                refine_sweeps=refine if prec == P.PNM_PREC_BF16X3 else 0)
+
+
+def measure_other(P, torch, stream, flush, workload, prec, refine, steps):
+    """Mean time-to-converge (ms) and iterations of another workload/precision."""
+    N, rho, n2max = WORKLOADS[workload]
+    ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream)
+    kw = solve_kwargs(P, prec, refine)
+    for _ in range(3):
+        ctx.solve(**kw)
+    torch.cuda.synchronize()
+    ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
+    tim = ctx.timings()
+    ctx.close()
+    return {"ms": statistics.mean(ms), "iters": statistics.mean(iters), "dE_per_N": statistics.mean(dEs) / N,
+            "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"]}
+
+
 def run_ours(a):
     world, rank, local = dist_setup()
     import torch
@@ -221,15 +259,12 @@ def run_ours(a):
     pb.build()
     import paper_1611_06765_gb300 as P
     N, rho, n2max = WORKLOADS[a.workload]
-    prec_name = a.precision
-    if prec_name == "auto":
-        prec_name = "bf16x3" if _mixed_available(P) else "fp64"
+    prec_name = "bf16x3" if a.precision == "auto" else a.precision
     prec = P.PNM_PREC_BF16X3 if prec_name == "bf16x3" else P.PNM_PREC_FP64
     refine = a.refine if prec == P.PNM_PREC_BF16X3 else 0
     stream = torch.cuda.current_stream()
     ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream)
-    solve_kw = dict(precision=prec, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
-                    refine_sweeps=refine)
+    solve_kw = solve_kwargs(P, prec, a.refine)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(max(3, a.warmup)):
         flush.zero_()
@@ -237,25 +272,11 @@ def run_ours(a):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    iters = []
-    dEs = []
-    evs = []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
-        for _ in range(a.steps):
-            flush.zero_()  # 512 MB write > 129 MB L2, outside the timed events
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            dE, it, _, _ = ctx.solve(**solve_kw)
-            e1.record(stream)
-            evs.append((e0, e1))
-            iters.append(int(it[0]))
-            dEs.append(float(dE[0]))
-        torch.cuda.synchronize()
+        step_ms, iters, dEs = timed_solves(ctx, solve_kw, a.steps, flush, stream, torch)
         wall = time.perf_counter() - wall0
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     ms = statistics.mean(step_ms)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -299,8 +320,19 @@ def run_ours(a):
     roof["kernel_avg_us"] = kavg_s * 1e6
     roof["algorithmic_bytes"] = byts
     roof["algorithmic_flops"] = flops
+    body = 6 if prec == P.PNM_PREC_BF16X3 else 5
+    launches_per_solve = 2 + body * statistics.mean(iters) + (1 if refine else 0)
 
-    launches_per_solve = 2 + 6 * statistics.mean(iters) + (2 if refine else 0)
+    comparison = None
+    if rank == 0 and not a.no_extra:
+        comparison = {}
+        other = P.PNM_PREC_FP64 if prec == P.PNM_PREC_BF16X3 else P.PNM_PREC_BF16X3
+        comparison[a.workload + ("_fp64" if other == P.PNM_PREC_FP64 else "_bf16x3")] = measure_other(
+            P, torch, stream, flush, a.workload, other, a.refine, max(5, a.steps // 2))
+        if a.workload != "pnm_N66_rho0.16_n2max36":
+            for pn, pv in (("bf16x3", P.PNM_PREC_BF16X3), ("fp64", P.PNM_PREC_FP64)):
+                comparison["pnm_N66_rho0.16_n2max36_" + pn] = measure_other(
+                    P, torch, stream, flush, "pnm_N66_rho0.16_n2max36", pv, a.refine, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -329,9 +361,11 @@ def run_ours(a):
             "gpu_launches": int(round(launches_per_solve * a.steps)),
             "roofline": roof,
             "cpu_baseline": cpu,
+            "comparison": comparison,
             "result": {"dE_per_N": statistics.mean(dEs) / N, "iters": statistics.mean(iters),
                        "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                        "wall_ms_per_step": wall * 1e3 / a.steps, "setup_ms": tim["setup"],
+                       "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"],
                        "kernels_ms_per_solve": {k: v[0] for k, v in stats.items()}},
         }
         print(json.dumps(line), flush=True)
@@ -340,16 +374,6 @@ def run_ours(a):
         dist.barrier()
         dist.destroy_process_group()
     return 0
-
-
-def _mixed_available(P):
-    try:
-        c = P.Context(14, 0.08, 4, params=MINNESOTA)
-        c.solve(precision=P.PNM_PREC_BF16X3, alpha=ALPHA, tol=1e-8, max_iter=200, refine_sweeps=1)
-        c.close()
-        return True
-    except P.PnmError:
-        return False
 
 
 def main():
