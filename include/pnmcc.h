@@ -124,6 +124,22 @@ int pnm_eref(const pnm_ctx *ctx, double *e_ref);
  * fused pass over the direct channels.  One value per system. */
 int pnm_mbpt2(pnm_ctx *ctx, double *dE);
 
+/* The same second-order energy as pnm_mbpt2, for callers that must not allocate device
+ * memory at the time of the call: code running while a CUDA graph is being captured
+ * (cudaMalloc is not allowed there), loops with a fixed memory budget, or hosts whose
+ * device allocator belongs to another framework.  This call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  Its scratch is a file-scope device
+ * array of (65536 + 64) doubles, about 513 KB, which every GPU that loads this library holds
+ * until the process exits.  Limits: at most 65536 (channel, hole-pair) rows and 64 systems
+ * per context, else PNM_EINVAL with a message.  The first call on a device looks up the
+ * array's device address for that device (done once per device); make that first call
+ * before any stream capture.  All calls on a device share the one array: every slot used is
+ * rewritten by each call, so nothing carries over, but calls that overlap on the GPU (from
+ * several host threads or streams) race on it.  dE receives one value per system; the call
+ * synchronises the context stream.  The paper has no counterpart: this is the library's
+ * own calling convention. */
+int pnm_mbpt2_noalloc(const pnm_ctx *ctx, double *dE);
+
 /* Solve the CCD equations (Eq. ccd3 in the intermediate form of Sec. "Developing a CCD
  * code", energy Eq. ccdcorr).  Per system outputs (nullable): dE (correlation energy),
  * iters (updates made), resid (2-norm of the last residual over restricted amplitudes).

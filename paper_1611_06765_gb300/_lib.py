@@ -26,7 +26,8 @@ PNM_INIT_KEEP = 2
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
     "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_destroy", "pnm_num_systems",
-    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_ccd_solve",
+    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc",
+    "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_set_profiling", "pnm_kernel_stats", "pnm_last_error",
 )
@@ -72,6 +73,7 @@ def load(path=None):
     L.pnm_v_element.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]
     L.pnm_eref.argtypes = [vp, dp]
     L.pnm_mbpt2.argtypes = [vp, dp]
+    L.pnm_mbpt2_noalloc.argtypes = [vp, dp]
     L.pnm_ccd_solve.argtypes = [vp, C.POINTER(pnm_solve_opts), dp, ip, dp]
     L.pnm_energy_history.argtypes = [vp, C.c_int, dp, C.c_int, ip]
     L.pnm_amplitude_labels.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t), vp]

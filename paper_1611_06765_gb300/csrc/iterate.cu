@@ -563,6 +563,16 @@ void pnm_mbpt2_all(pnm_ctx* ctx, double* out) {
   ctx->t_mbpt2 = ms;
 }
 
+// The MBPT2 kernels of pnm_mbpt2_all with caller-chosen device buffers for the per-row
+// partial sums (nrows doubles) and the per-system results (nsys doubles).
+void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results) {
+  DevState d = ctx->d;
+  d.eparts = partials;
+  k_mbpt2<<<ctx->nrows, 128, 0, ctx->stream>>>(d, ctx->lut_off_d);
+  k_reduce_rows<<<(int)ctx->sys.size(), 256, 0, ctx->stream>>>(partials, ctx->row_lo_d,
+                                                                ctx->row_hi_d, results);
+}
+
 // The body of one update, enqueued on the context stream (FP64 path).
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   FinArgs f;

@@ -89,6 +89,7 @@ void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_enqueue_stats(pnm_ctx* ctx);
 void pnm_launch_pp64(pnm_ctx* ctx);
+void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 template <typename T_>
 void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq);
