@@ -36,6 +36,11 @@ static void release(pnm_ctx* ctx) {
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < 2; k++) {
+    if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   for (auto& pr : ctx->prof_ev) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);

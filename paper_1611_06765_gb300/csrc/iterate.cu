@@ -78,54 +78,121 @@ __global__ void k_dchi(DevState D, int nsp_total) {
 }
 
 // ----------------------------------------------------------------------------- ph term
-// One CTA per cross channel.  Shared: T (nph x nhp), W (nhp x nph), C (nhp x nhp), in the
-// element type T_ of the precision mode (double for FP64, float for the mixed mode).
+// One CTA per cross channel, element type T_ of the precision mode (double for FP64, float
+// for the mixed mode).  Shared buffers, dimensions padded to multiples of 4 with zeros:
+//   Ts[u][s] = T[(a,i)=u][(k,c)=s]          (P4 x H4)
+//   Xt[u][r] = W[r][u] for GEMM 1, then T[r][u] transposed (T rows as columns) for GEMM 2
+//   Cs[r][s] = C[r][s]                       (H4 x H4)
+// Each thread accumulates 4 x 4 outputs; per k step it reads two 4-vectors from shared.
 template <typename T_>
-__global__ void __launch_bounds__(256) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ __forceinline__ static void ld(const double* p, double (&v)[4]) {
+    double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+template <typename T_>
+__global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
                                             const T_* __restrict__ xw, const T_* __restrict__ xv1,
                                             T_* __restrict__ xq) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T_* sm = reinterpret_cast<T_*>(smraw);
   int x = blockIdx.x;
   int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
   const double* __restrict__ t = cur_t(D, ctl);
-  T_* T = sm;
-  T_* W = T + nph * nhp;
-  T_* Cm = W + nhp * nph;
+  T_* Ts = sm;
+  T_* Xt = Ts + P4 * H4;
+  T_* Cs = Xt + P4 * H4;
   long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
-    int code = D.xmap[to + e];
-    double v = 0.0;
-    if (code > 0) v = t[code - 1];
-    else if (code < 0) v = -t[-code - 1];
-    T[e] = (T_)v;
-    W[e] = xw[wo + e];
+  // T[(a,i)][(k,c)] = t_ik^ac through the signed index map; W transposed into Xt
+  for (int e = threadIdx.x; e < P4 * H4; e += blockDim.x) {
+    int u = e / H4, s = e % H4;
+    T_ tv = 0, wv = 0;
+    if (u < nph && s < nhp) {
+      int code = D.xmap[to + (long)u * nhp + s];
+      if (code > 0) tv = (T_)t[code - 1];
+      else if (code < 0) tv = -(T_)t[-code - 1];
+      wv = xw[wo + (long)s * nph + u];
+    }
+    Ts[e] = tv;
+    Xt[e] = wv;  // Xt[u][s] = W[s][u]
   }
   __syncthreads();
   // C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
-  for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
-    int r = e / nhp, s = e % nhp;
-    T_ acc = 0;
-    for (int u = 0; u < nph; u++) acc += W[r * nph + u] * T[u * nhp + s];
-    Cm[e] = xv1[co + e] + (T_)0.5 * acc;
+  int th = H4 >> 2;
+  for (int tile = threadIdx.x; tile < th * th; tile += blockDim.x) {
+    int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
+    T_ acc[4][4] = {};
+    for (int u = 0; u < nph; u++) {
+      T_ a[4], b[4];
+      Vec4<T_>::ld(Xt + u * H4 + r0, a);
+      Vec4<T_>::ld(Ts + u * H4 + s0, b);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        int r = r0 + i, s = s0 + j;
+        Cs[r * H4 + s] = (r < nhp && s < nhp) ? xv1[co + (long)r * nhp + s] + (T_)0.5 * acc[i][j] : (T_)0;
+      }
+  }
+  __syncthreads();
+  // T transposed into Xt: Xt[u][r] = T[r][u]  (u over hp, r over ph)
+  for (int e = threadIdx.x; e < P4 * H4; e += blockDim.x) {
+    int r = e / H4, u = e % H4;
+    Xt[u * P4 + r] = Ts[e];
   }
   __syncthreads();
   // Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
-  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
-    int r = e / nhp, s = e % nhp;
-    T_ acc = 0;
-    for (int u = 0; u < nhp; u++) acc += T[r * nhp + u] * Cm[u * nhp + s];
-    xq[to + e] = acc;
+  int tp = P4 >> 2;
+  for (int tile = threadIdx.x; tile < tp * th; tile += blockDim.x) {
+    int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
+    T_ acc[4][4] = {};
+    for (int u = 0; u < nhp; u++) {
+      T_ a[4], b[4];
+      Vec4<T_>::ld(Xt + u * P4 + r0, a);
+      Vec4<T_>::ld(Cs + u * H4 + s0, b);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        int r = r0 + i, s = s0 + j;
+        if (r < nph && s < nhp) xq[to + (long)r * nhp + s] = acc[i][j];
+      }
   }
 }
 
-template <typename T_>
-void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq) {
-  size_t smem = sizeof(T_) * 3 * (size_t)ctx->max_x_dim * ctx->max_x_dim;
-  k_ph<T_><<<ctx->nx, 256, smem, ctx->stream>>>(ctx->d, ctx->ctl, xw, xv1, xq);
+size_t ph_smem_bytes(const pnm_ctx* ctx, size_t elem) {
+  size_t m4 = (size_t)((ctx->max_x_dim + 3) & ~3);
+  return elem * 3 * m4 * m4;
 }
-template void launch_ph<double>(pnm_ctx*, const double*, const double*, double*);
-template void launch_ph<float>(pnm_ctx*, const float*, const float*, float*);
+
+template <typename T_>
+void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
+  k_ph<T_><<<ctx->nx, 128, ph_smem_bytes(ctx, sizeof(T_)), s>>>(ctx->d, ctx->ctl, xw, xv1, xq);
+}
+template void launch_ph<double>(pnm_ctx*, const double*, const double*, double*, cudaStream_t);
+template void launch_ph<float>(pnm_ctx*, const float*, const float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------- pp ladder FP64
 // R^T(ij, ab) = sum_cd t(ij, cd) <cd|v|ab>, restricted pairs (1/2 sum over ordered cd of a
@@ -278,7 +345,7 @@ template <typename RT, typename QT>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
                                                 const int4* __restrict__ items, FinArgs fa,
                                                 const RT* __restrict__ rpp,
-                                                const QT* __restrict__ xq) {
+                                                const QT* __restrict__ xq, PackArgs pk) {
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
   int c = it.x, ij = it.y;
@@ -325,6 +392,16 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
     }
     tn[z] = out;
     esum += v * out;
+    if (pk.bt && szero) {
+      // BF16 hi/lo copy of the new amplitude for the next tensor-core pp ladder
+      int npad = pk.ch_npad[c];
+      long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
+      __nv_bfloat16 hi, lo;
+      split_bf16(out, hi, lo);
+      int o = tile_core_off(ij, ab & 63);
+      pk.bt[tb + o] = hi;
+      pk.bt[tb + (long)npad * 64 + o] = lo;
+    }
   }
   esum = block_sum(esum, sh32);
   rsum = block_sum(rsum, sh32);
@@ -337,14 +414,14 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
 
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h) {
+                   cudaGraphConditionalHandle h, PackArgs pk) {
   k_update<RT, QT><<<ctx->n_upd_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->upd_items,
-                                                               fin_args(ctx, use_cond, h), rpp, xq);
+                                                               fin_args(ctx, use_cond, h), rpp, xq, pk);
 }
 template void launch_update<double, double>(pnm_ctx*, const double*, const double*, int,
-                                            cudaGraphConditionalHandle);
+                                            cudaGraphConditionalHandle, PackArgs);
 template void launch_update<float, float>(pnm_ctx*, const float*, const float*, int,
-                                          cudaGraphConditionalHandle);
+                                          cudaGraphConditionalHandle, PackArgs);
 
 // Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
 __global__ void __launch_bounds__(128) k_init(DevState D, int init) {
@@ -517,12 +594,18 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->ctl = (LoopCtl*)dmalloc(ctx, sizeof(LoopCtl));
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
-  size_t ph_smem = sizeof(double) * 3 * (size_t)mx * mx;
+  size_t ph_smem = ph_smem_bytes(ctx, sizeof(double));
   size_t pp_smem = pp64_smem(max_npp);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
   CUDA_TRY(cudaFuncSetAttribute(k_ph<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_smem_bytes(ctx, sizeof(float))));
+  for (int k = 0; k < 2; k++) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
+  }
+  CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   CUDA_TRY(cudaFuncSetAttribute(k_pp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp_smem));
   CUDA_TRY(cudaStreamSynchronize(s));
 }
@@ -589,10 +672,27 @@ FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   return f;
 }
 
-void pnm_launch_pp64(pnm_ctx* ctx) {
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s) {
   if (ctx->n_pp_items > 0)
-    k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_npp), ctx->stream>>>(
-        ctx->d, ctx->ctl, ctx->pp_items);
+    k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_npp), s>>>(ctx->d, ctx->ctl,
+                                                                             ctx->pp_items);
+}
+
+// The ph term and the pp ladder do not depend on each other nor on the one-body sums: in a
+// captured update they run on two side streams next to the stats kernels.  While kernels are
+// being profiled one by one everything stays on the context stream.
+void pnm_fork(pnm_ctx* ctx) {
+  if (ctx->prof_live) return;
+  CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  for (int k = 0; k < 2; k++) CUDA_TRY(cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0));
+}
+
+void pnm_join(pnm_ctx* ctx) {
+  if (ctx->prof_live) return;
+  for (int k = 0; k < 2; k++) {
+    CUDA_TRY(cudaEventRecord(ctx->ev_join[k], ctx->side[k]));
+    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[k], 0));
+  }
 }
 
 // One-body intermediates and <kl|chi|ij> (shared by both precision modes, FP64).
@@ -608,21 +708,24 @@ void pnm_enqueue_stats(pnm_ctx* ctx) {
 }
 
 static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
-  cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
-  pnm_enqueue_stats(ctx);
+  cudaStream_t s_ph = ctx->prof_live ? ctx->stream : ctx->side[0];
+  cudaStream_t s_pp = ctx->prof_live ? ctx->stream : ctx->side[1];
+  pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH64);
-    launch_ph<double>(ctx, D.x_w, D.x_v1, D.xq);
+    launch_ph<double>(ctx, D.x_w, D.x_v1, D.xq, s_ph);
     prof_end(ctx);
   }
   if (ctx->n_pp_items > 0) {
     prof_begin(ctx, KID_PP64);
-    pnm_launch_pp64(ctx);
+    pnm_launch_pp64(ctx, s_pp);
     prof_end(ctx);
   }
+  pnm_enqueue_stats(ctx);
+  pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
-  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h);
+  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr});
   prof_end(ctx);
 }
 

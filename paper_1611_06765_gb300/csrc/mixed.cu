@@ -135,15 +135,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Element offset inside a (rows x 64) BF16 plane laid out as core matrices.
-__device__ __forceinline__ int core_off(int r, int k) {
-  return (((r >> 3) * (TC_BK / 8) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
-}
-
-__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn((float)x);
-  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
-}
+static_assert(TC_BK == 64, "tile_core_off assumes 64-element k-blocks");
+__device__ __forceinline__ int core_off(int r, int k) { return tile_core_off(r, k); }
 
 // ------------------------------------------------------------------------ kernels
 // V tiles of the S_z = 0 channels (setup): one CTA per (item, k-block).
@@ -319,6 +312,8 @@ struct MixedState {
   int4* pk = nullptr;
   long* pk_boff = nullptr;
   int npk = 0;
+  long* ch_boff = nullptr;  // per channel: k-block 0 of its t tiles (-1: not an S_z = 0 channel)
+  int* ch_npad = nullptr;
   uint32_t stage_bytes = 0;
   size_t smem = 0;
 };
@@ -330,7 +325,8 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
   try {
     std::vector<TCItem> items;
     std::vector<int4> pk;
-    std::vector<long> pk_boff;
+    std::vector<long> pk_boff, ch_boff(ctx->nch, -1);
+    std::vector<int> ch_npad(ctx->nch, 0);
     long voff = 0, boff = 0;
     int max_npad = 16, max_nkb = 1;
     for (int c = 0; c < ctx->nch; c++) {
@@ -341,6 +337,8 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       int nmt = (npp + TC_M - 1) / TC_M, nkb = (npp + TC_BK - 1) / TC_BK;
       max_npad = std::max(max_npad, npad);
       max_nkb = std::max(max_nkb, nkb);
+      ch_boff[c] = boff;
+      ch_npad[c] = npad;
       for (int mt = 0; mt < nmt; mt++) {
         TCItem t{};
         t.ch = c;
@@ -375,6 +373,12 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       CUDA_TRY(cudaMemcpyAsync(M->pk_boff, pk_boff.data(), sizeof(long) * pk_boff.size(),
                                cudaMemcpyHostToDevice, s));
     }
+    M->ch_boff = mdalloc<long>(ctx, ctx->nch);
+    M->ch_npad = mdalloc<int>(ctx, ctx->nch);
+    CUDA_TRY(cudaMemcpyAsync(M->ch_boff, ch_boff.data(), sizeof(long) * ctx->nch, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(M->ch_npad, ch_npad.data(), sizeof(int) * ctx->nch, cudaMemcpyHostToDevice, s));
+    // padding rows/columns of the t tiles are never written again: they stay zero
+    CUDA_TRY(cudaMemsetAsync(M->bt, 0, sizeof(__nv_bfloat16) * std::max<long>(boff, 1), s));
     M->rpp32 = mdalloc<float>(ctx, ctx->nt);
     M->xw32 = mdalloc<float>(ctx, ctx->nxt);
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
@@ -399,28 +403,37 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
 }
 
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
-  cudaStream_t s = ctx->stream;
   MixedState* M = ctx->mixed;
-  DevState& D = ctx->d;
-  if (M->npk > 0) {
-    prof_begin(ctx, KID_PACK);
-    k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, D, ctx->ctl, M->bt);
-    prof_end(ctx);
-  }
-  pnm_enqueue_stats(ctx);
+  cudaStream_t s_ph = ctx->prof_live ? ctx->stream : ctx->side[0];
+  cudaStream_t s_pp = ctx->prof_live ? ctx->stream : ctx->side[1];
+  pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH32);
-    launch_ph<float>(ctx, M->xw32, M->xv132, M->xq32);
+    launch_ph<float>(ctx, M->xw32, M->xv132, M->xq32, s_ph);
     prof_end(ctx);
   }
   if (M->nitems > 0) {
     prof_begin(ctx, KID_PP_TC);
-    k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
+    k_pp_tc<<<M->nitems, 128, M->smem, s_pp>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
     prof_end(ctx);
   }
+  pnm_enqueue_stats(ctx);
+  pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
-  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h);
+  // the update also writes the BF16 hi/lo tiles of the new amplitudes for the next ladder
+  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->ch_boff, M->ch_npad});
   prof_end(ctx);
+}
+
+// BF16 tiles of the start amplitudes (before the first mixed update).
+void pnm_mixed_pack_initial(pnm_ctx* ctx) {
+  MixedState* M = ctx->mixed;
+  if (M->npk > 0) {
+    prof_begin(ctx, KID_PACK);
+    k_pack_t<<<M->npk, 256, 0, ctx->stream>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
+    prof_end(ctx);
+  }
+  CUDA_TRY(cudaGetLastError());
 }
 
 void pnm_free_mixed(pnm_ctx* ctx) {
@@ -454,7 +467,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     for (long z = 0; z < ctx->nt; z++) out[z] = f[z];
   } else {
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * ctx->nt, s));
-    pnm_launch_pp64(ctx);
+    pnm_launch_pp64(ctx, s);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(out.data(), ctx->d.rpp, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));

@@ -57,6 +57,10 @@ struct pnm_ctx {
 
   MixedState* mixed = nullptr;
 
+  // side streams for the independent parts of an update (ph term, pp ladder), joined by events
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+
   // per-kernel CUDA-event profiling of host-driven solves (never active during capture)
   bool prof_on = false, prof_live = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
@@ -88,11 +92,15 @@ void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_enqueue_stats(pnm_ctx* ctx);
-void pnm_launch_pp64(pnm_ctx* ctx);
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s);
+size_t ph_smem_bytes(const pnm_ctx* ctx, size_t elem);
+void pnm_mixed_pack_initial(pnm_ctx* ctx);
+void pnm_fork(pnm_ctx* ctx);
+void pnm_join(pnm_ctx* ctx);
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 template <typename T_>
-void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq);
+void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s);
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h);
+                   cudaGraphConditionalHandle h, PackArgs pk);

@@ -12,6 +12,7 @@
 //                n_ph x n_hp at xt_off[x]; V1_x (<kb|v|cj>) n_hp x n_hp at xc_off[x];
 //                W_x (<kl|v|ce>) n_hp x n_ph at xw_off[x].
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -120,6 +121,14 @@ struct FinArgs {
   cudaGraphConditionalHandle handle;
 };
 
+// Where the mixed update writes the BF16 hi/lo copy of the new amplitudes (the B operand
+// tiles of the tensor-core pp ladder).  bt == nullptr: no copy.
+struct PackArgs {
+  __nv_bfloat16* bt;
+  const long* ch_boff;  // per channel: element offset of its k-block 0, -1 if not packed
+  const int* ch_npad;   // per channel: n_hh padded to the MMA N
+};
+
 // --------------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ int dot3(int x, int y, int z) { return x * x + y * y + z * z; }
@@ -145,6 +154,18 @@ __device__ __forceinline__ double v_minnesota_as(char4 p, char4 q, char4 r, char
   int m1 = dot3(p.x - r.x, p.y - r.y, p.z - r.z);
   int m2 = dot3(p.x - s.x, p.y - s.y, p.z - s.z);
   return 0.5 * (lut[m1] + lut[m2]) * (double)sf;
+}
+
+// Element offset inside a (rows x 64) BF16 plane stored as 8-row x 16-byte core matrices
+// (K-major canonical layout of the tensor-core operands, no swizzle).
+__device__ __forceinline__ int tile_core_off(int r, int k) {
+  return (((r >> 3) * 8 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// x = hi + lo with hi, lo in BF16 (hi = round(x), lo = round(x - hi)).
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn((float)x);
+  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

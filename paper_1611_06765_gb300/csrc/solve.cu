@@ -54,6 +54,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
   CUDA_TRY(cudaEventRecord(e0, s));
   pnm_start(ctx, o.init, tol);
+  if (mixed) pnm_mixed_pack_initial(ctx);
   int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : PNM_PREC_FP64, o.max_iter, o.host_loop,
                             o.mix_alpha);
   CUDA_TRY(cudaEventRecord(e1, s));

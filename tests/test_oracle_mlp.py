@@ -1,0 +1,45 @@
+"""Pins of the FP64 warm-start network reference: analytic gradient vs central finite
+differences (without BF16 rounding, where the loss is smooth), the BF16 rounding against
+known values, and GELU against its textbook values."""
+import numpy as np
+
+from inputs import random_mlp
+from oracle import mlp
+
+
+def test_bf16_rounding_known_values():
+    vals = np.array([1.0, 1.00390625, 1.005859375, -3.140625, 65504.0, 1e-3], np.float32)
+    got = mlp.bf16(vals)
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7 -> even (1.0); 1.005859375 rounds up
+    assert got[0] == 1.0 and got[1] == 1.0 and got[2] == 1.0078125
+    assert got[3] == -3.140625
+    assert got[4] == 65536.0
+    assert abs(got[5] - 1e-3) <= 2 ** -9 * 1e-3
+
+
+def test_gelu_values():
+    z = np.array([0.0, 1.0, -1.0, 3.0])
+    # x Phi(x) with the tabulated normal CDF Phi(1) = 0.8413447460685429, Phi(3) = 0.9986501019683699
+    expect = np.array([0.0, 0.8413447460685429, -0.15865525393145707, 3 * 0.9986501019683699])
+    assert np.allclose(mlp.gelu(z), expect, rtol=1e-12, atol=1e-15)
+    h = 1e-6
+    assert np.allclose(mlp.gelu_prime(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), rtol=1e-8)
+
+
+def test_analytic_gradient_matches_finite_differences():
+    blob, X, T = random_mlp(n=16, seed=3)
+    loss, g = mlp.loss_and_grad(blob, X, T, round_bf16=False)
+    rng = np.random.default_rng(5)
+    off = mlp.offsets()
+    picks = []
+    for name, (o, k) in off.items():
+        picks += list(o + rng.choice(k, size=min(k, 6), replace=False))
+    b64 = blob.astype(np.float64)
+    for idx in picks:
+        h = 1e-5 * max(1.0, abs(b64[idx]))
+        bp = b64.copy(); bp[idx] += h
+        bm = b64.copy(); bm[idx] -= h
+        lp, _ = mlp.loss_and_grad(bp, X, T, round_bf16=False)
+        lm, _ = mlp.loss_and_grad(bm, X, T, round_bf16=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-10, (idx, fd, g[idx])
