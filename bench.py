@@ -245,6 +245,67 @@ def measure_other(P, torch, stream, flush, workload, prec, refine, steps):
             "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"]}
 
 
+def measure_batch(P, torch, stream, flush, refine, steps):
+    """16 densities (0.02..0.32) of N=14, n^2<=20 solved together in one context: every kernel
+    launch covers all systems; the loop ends when all have converged."""
+    rhos = [0.02 * k for k in range(1, 17)]
+    ctx = P.Context(14, rhos, 20, params=MINNESOTA, stream=stream.cuda_stream)
+    out = {}
+    for pn, pv in (("bf16x3", P.PNM_PREC_BF16X3), ("fp64", P.PNM_PREC_FP64)):
+        kw = solve_kwargs(P, pv, refine)
+        for _ in range(3):
+            ctx.solve(**kw)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dE, it, _, _ = ctx.solve(**kw)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        out[pn] = {"ms": statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs),
+                   "iters_max": int(max(it)), "dE_per_N": [float(x) / 14 for x in dE]}
+    ctx.close()
+    return out
+
+
+def measure_learned(P, torch, stream, flush, refine, steps):
+    """Learned warm start: train on solver amplitudes of N=14 (n^2<=20, 16 densities) and
+    N=66 (n^2<=36, rho=0.16), then time N=66 solves at held-out densities from the learned
+    start, from the MBPT2 start (both mixed precision) and in FP64."""
+    kw64 = dict(precision=P.PNM_PREC_FP64, alpha=ALPHA, tol=1e-30, tol_per_N=1e-8, max_iter=500)
+    t0 = time.perf_counter()
+    tr14 = P.Context(14, [0.02 * k for k in range(1, 17)], 20, params=MINNESOTA, stream=stream.cuda_stream)
+    tr14.solve(**kw64)
+    tr66 = P.Context(66, 0.16, 36, params=MINNESOTA, stream=stream.cuda_stream)
+    tr66.solve(**kw64)
+    blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=12, batch=4096, lr=1e-3, seed=2)
+    train_s = time.perf_counter() - t0
+    tr14.close()
+    tr66.close()
+    res = {"train_s": train_s, "train_loss_first_last": [float(hist[0]), float(hist[-1])], "rho": {}}
+    for rho in (0.05, 0.11, 0.17):
+        ctx = P.Context(66, rho, 36, params=MINNESOTA, stream=stream.cuda_stream)
+        ctx.mlp_set_model(blob)
+        row = {}
+        for name, prec, init in (("bf16x3_learned", P.PNM_PREC_BF16X3, P.PNM_INIT_MLP),
+                                 ("bf16x3_mbpt2", P.PNM_PREC_BF16X3, P.PNM_INIT_MBPT2),
+                                 ("fp64_mbpt2", P.PNM_PREC_FP64, P.PNM_INIT_MBPT2)):
+            kw = solve_kwargs(P, prec, refine)
+            kw["init"] = init
+            for _ in range(3):
+                ctx.solve(**kw)
+            ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
+            row[name] = {"ms": statistics.mean(ms), "iters": statistics.mean(iters),
+                         "dE_per_N": statistics.mean(dEs) / 66}
+        ctx.close()
+        res["rho"][str(rho)] = row
+    return res
+
+
 def run_ours(a):
     world, rank, local = dist_setup()
     import torch
@@ -333,6 +394,8 @@ def run_ours(a):
             for pn, pv in (("bf16x3", P.PNM_PREC_BF16X3), ("fp64", P.PNM_PREC_FP64)):
                 comparison["pnm_N66_rho0.16_n2max36_" + pn] = measure_other(
                     P, torch, stream, flush, "pnm_N66_rho0.16_n2max36", pv, a.refine, 3)
+        comparison["density_batch_N14_n2max20_16rho"] = measure_batch(P, torch, stream, flush, a.refine, 3)
+        comparison["learned_start_N66_n2max36_heldout"] = measure_learned(P, torch, stream, flush, a.refine, 3)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -56,6 +56,8 @@ typedef struct {
 #define PNM_INIT_MBPT2 0  /* t = <ab|v|ij> / eps_ij^ab, Eq. (ccdGuess) */
 #define PNM_INIT_ZERO 1   /* t = 0 (the first update then gives MBPT2) */
 #define PNM_INIT_KEEP 2   /* start from the amplitudes currently held (pnm_set_amplitudes) */
+#define PNM_INIT_MLP 3    /* learned start (pnm_mlp_set_model); falls back to MBPT2 if the
+                             iteration from it does not converge */
 
 /* Options of the CCD iteration (Eq. ccd3 with mixing and the stopping rule of Sec.
  * "Developing a numerical project"). */
@@ -172,6 +174,55 @@ int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, d
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
  * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
+
+/* ---------------------------------------------------------------- learned warm start
+ * Not in the paper: a network predicts the converged amplitudes so the Jacobi iteration of
+ * Eq. (ccd3) starts closer to its fixed point than the MBPT2 guess of Eq. (ccdGuess); the
+ * iteration itself still decides the result.  Network: 32 features -> 128 -> 128 -> 128
+ * (GELU) -> 1, weights and layer inputs rounded to BF16, FP32 accumulation;
+ *   t_start = t_MBPT2 + sigma_sys * y_scale * net(features),
+ * sigma_sys = RMS of the system's MBPT2 amplitudes.  Features per restricted amplitude:
+ * k_a, k_b, k_i, k_j / k_F (12), spins (4), eps_ij^ab / eps_F, N <ab|v|ij> / eps_F,
+ * t_MBPT2 / sigma_sys, rho / 0.16, k_F, N / 66, then 10 zeros.
+ * Parameter blob (pnm_mlp_num_params floats): mu[32], inv_std[32], y_scale, pad[3],
+ * W1[128][32], b1[128], W2[128][128], b2[128], W3[128][128], b3[128], w4[128], b4. */
+typedef struct {
+    int epochs;               /* passes over the training amplitudes */
+    int batch;                /* samples per Adam step */
+    double lr;                /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8) */
+    unsigned long long seed;  /* shuffling */
+} pnm_mlp_opts;
+
+/* Number of floats in a parameter blob. */
+int pnm_mlp_num_params(int *n);
+
+/* Initial parameters (host): unit feature normalisation, He-normal weights, zero biases. */
+int pnm_mlp_init(float *blob, unsigned long long seed);
+
+/* Features (n x 32 floats), MBPT2 amplitudes (n doubles) and sigma_sys of system `sys`
+ * in library amplitude order (any output may be NULL).  Computed on the GPU once per context. */
+int pnm_mlp_features(pnm_ctx *ctx, int sys, float *X, double *t_mbpt2, double *sigma);
+
+/* Train on the amplitudes currently held by the given contexts (after converged solves):
+ * target (t - t_MBPT2) / sigma_sys.  Sets the blob's normalisation header from the data,
+ * then runs Adam on the GPU (the library's forward/backward kernels).  blob: in = initial
+ * parameters, out = trained.  loss_hist (nullable, cap entries) gets the mean loss per
+ * epoch (in units of y_scale^2); *n_hist the number of epochs. */
+int pnm_mlp_train(pnm_ctx *const *ctxs, int nctx, const pnm_mlp_opts *opts, float *blob,
+                  float *loss_hist, int cap, int *n_hist);
+
+/* Install a trained blob in a context for solves with init = PNM_INIT_MLP. */
+int pnm_mlp_set_model(pnm_ctx *ctx, const float *blob);
+
+/* Network output for n feature rows (host arrays): use_tensor_cores = 1 runs the fused
+ * tcgen05 inference kernel, 0 the SIMT training forward.  stream: NULL = legacy stream. */
+int pnm_mlp_forward(const float *blob, const float *X, long n, float *Y, int use_tensor_cores,
+                    void *stream);
+
+/* Mean squared error over n samples and its gradient (NPARAM floats, header entries 0)
+ * from the library's GPU forward/backward kernels, for gradient checks. */
+int pnm_mlp_loss_grad(const float *blob, const float *X, const float *T, int n, float *loss,
+                      float *grad, void *stream);
 
 /* Per-kernel device time of host-driven solves (opts.host_loop = 1): while profiling is on,
  * every kernel launch of the update is bracketed by CUDA events on the context stream.

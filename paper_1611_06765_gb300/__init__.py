@@ -9,11 +9,12 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (PNM_EDIVERGED, PNM_ENOTCONV, PNM_INIT_KEEP, PNM_INIT_MBPT2, PNM_INIT_ZERO,
-                   PNM_PREC_BF16X3, PNM_PREC_FP64, PnmError)
+from ._lib import (PNM_EDIVERGED, PNM_ENOTCONV, PNM_INIT_KEEP, PNM_INIT_MBPT2, PNM_INIT_MLP,
+                   PNM_INIT_ZERO, PNM_PREC_BF16X3, PNM_PREC_FP64, PnmError)
 
 __all__ = ["Context", "MINNESOTA", "PnmError", "PNM_PREC_FP64", "PNM_PREC_BF16X3",
-           "PNM_INIT_MBPT2", "PNM_INIT_ZERO", "PNM_INIT_KEEP", "PNM_ENOTCONV", "PNM_EDIVERGED"]
+           "PNM_INIT_MBPT2", "PNM_INIT_ZERO", "PNM_INIT_KEEP", "PNM_INIT_MLP", "PNM_ENOTCONV",
+           "PNM_EDIVERGED", "mlp_num_params", "mlp_init", "mlp_train", "mlp_forward", "mlp_loss_grad"]
 
 # V_R, kappa_R, V_T, kappa_T, V_S, kappa_S (Table tab:minnesotatab, attractive T and S) and
 # hbar^2/2m in MeV fm^2.
@@ -148,6 +149,19 @@ class Context:
         _lib.check(_lib.load().pnm_apply_pp_ladder(self._h, sys, precision, _ptr(t), _ptr(r), t.size))
         return r
 
+    def mlp_features(self, sys=0):
+        """(X[n,32], t_MBPT2[n], sigma_sys) of system sys in library order."""
+        n = len(self.amplitude_labels(sys))
+        X = np.zeros((n, 32), np.float32)
+        tm2 = np.zeros(n)
+        sig = np.zeros(1)
+        _lib.check(_lib.load().pnm_mlp_features(self._h, sys, _ptr(X), _ptr(tm2), _ptr(sig)))
+        return X, tm2, float(sig[0])
+
+    def mlp_set_model(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.float32)
+        _lib.check(_lib.load().pnm_mlp_set_model(self._h, blob.ctypes.data_as(C.POINTER(C.c_float))))
+
     def set_profiling(self, on=True):
         _lib.check(_lib.load().pnm_set_profiling(self._h, int(on)))
 
@@ -169,3 +183,50 @@ class Context:
         ms = np.zeros(5)
         _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 5))
         return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4])
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def mlp_num_params():
+    n = C.c_int()
+    _lib.check(_lib.load().pnm_mlp_num_params(C.byref(n)))
+    return n.value
+
+
+def mlp_init(seed=0):
+    blob = np.zeros(mlp_num_params(), np.float32)
+    _lib.check(_lib.load().pnm_mlp_init(_fptr(blob), seed))
+    return blob
+
+
+def mlp_train(contexts, blob, epochs=20, batch=4096, lr=1e-3, seed=0):
+    """pnm_mlp_train on the amplitudes held by the contexts; returns (blob, loss history)."""
+    blob = np.ascontiguousarray(blob, dtype=np.float32).copy()
+    o = _lib.pnm_mlp_opts(epochs, batch, lr, seed)
+    handles = (C.c_void_p * len(contexts))(*[c._h.value for c in contexts])
+    hist = np.zeros(max(1, epochs), np.float32)
+    nh = C.c_int()
+    _lib.check(_lib.load().pnm_mlp_train(handles, len(contexts), C.byref(o), _fptr(blob), _fptr(hist),
+                                         hist.size, C.byref(nh)))
+    return blob, hist[: nh.value].copy()
+
+
+def mlp_forward(blob, X, tensor_cores=True):
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.zeros(X.shape[0], np.float32)
+    _lib.check(_lib.load().pnm_mlp_forward(_fptr(blob), _fptr(X), X.shape[0], _fptr(Y), int(tensor_cores), None))
+    return Y
+
+
+def mlp_loss_grad(blob, X, T):
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    g = np.zeros_like(blob)
+    loss = C.c_float()
+    _lib.check(_lib.load().pnm_mlp_loss_grad(_fptr(blob), _fptr(X), _fptr(T), X.shape[0], C.byref(loss),
+                                             _fptr(g), None))
+    return float(loss.value), g

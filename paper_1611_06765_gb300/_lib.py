@@ -22,6 +22,7 @@ PNM_PREC_BF16X3 = 2
 PNM_INIT_MBPT2 = 0
 PNM_INIT_ZERO = 1
 PNM_INIT_KEEP = 2
+PNM_INIT_MLP = 3
 
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
@@ -29,7 +30,8 @@ EXPORTS = (
     "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc",
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
-    "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_set_profiling", "pnm_kernel_stats", "pnm_last_error",
+    "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_mlp_num_params", "pnm_mlp_init",
+    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_last_error",
 )
 
 
@@ -41,6 +43,10 @@ class pnm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("mix_alpha", C.c_double), ("tol_dE", C.c_double),
                 ("tol_dE_per_N", C.c_double), ("max_iter", C.c_int), ("refine_sweeps", C.c_int),
                 ("init", C.c_int), ("host_loop", C.c_int)]
+
+
+class pnm_mlp_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("seed", C.c_ulonglong)]
 
 
 class PnmError(RuntimeError):
@@ -81,6 +87,14 @@ def load(path=None):
     L.pnm_set_amplitudes.argtypes = [vp, C.c_int, vp, C.c_size_t]
     L.pnm_get_timings.argtypes = [vp, dp, C.c_int]
     L.pnm_apply_pp_ladder.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_size_t]
+    fp = C.POINTER(C.c_float)
+    L.pnm_mlp_num_params.argtypes = [ip]
+    L.pnm_mlp_init.argtypes = [fp, C.c_ulonglong]
+    L.pnm_mlp_features.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.pnm_mlp_train.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(pnm_mlp_opts), fp, fp, C.c_int, ip]
+    L.pnm_mlp_set_model.argtypes = [vp, fp]
+    L.pnm_mlp_forward.argtypes = [fp, fp, C.c_long, fp, C.c_int, vp]
+    L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, vp]
     L.pnm_set_profiling.argtypes = [vp, C.c_int]
     L.pnm_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), dp, ip]
     L.pnm_last_error.restype = C.c_char_p

@@ -33,6 +33,7 @@ static void release(pnm_ctx* ctx) {
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
   for (auto& g : ctx->graph_defs) cudaGraphDestroy(g.second);
   pnm_free_mixed(ctx);
+  pnm_free_mlp(ctx);
   for (void* p : ctx->owned) cudaFree(p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "pnm_context.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -40,100 +41,7 @@ struct TCItem {
   long toff;   // element offset of the channel in the t layout
 };
 
-// ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after 2^22 polls (of the order of a second) and reports failure.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); i++)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
-  uint64_t d = 0;
-  d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
-  d |= (uint64_t)((CORE_LBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((CORE_SBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  return d;               // base offset 0, layout type 0 (no swizzle)
-}
-
-// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+using namespace tc;
 
 static_assert(TC_BK == 64, "tile_core_off assumes 64-element k-blocks");
 __device__ __forceinline__ int core_off(int r, int k) { return tile_core_off(r, k); }
@@ -210,9 +118,9 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
     tmem_alloc(tslot, ncols);
     tmem_relinquish();
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tbase = *tslot;
 
   if (warp == 0 && lane == 0) {
@@ -244,7 +152,7 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
         err = 1;
         break;
       }
-      tc_fence_after();
+      fence_after();
       unsigned char* a_hi = stage0 + s * stage_bytes;
       unsigned char* a_lo = a_hi + A_PLANE;
       unsigned char* b_hi = a_hi + 2 * A_PLANE;
@@ -252,20 +160,20 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
 #pragma unroll
       for (int ks = 0; ks < TC_BK / 16; ks++) {
         uint32_t o = ks * 2 * 128;  // two core matrices of K per MMA
-        uint64_t ah = smem_desc(a_hi + o), al = smem_desc(a_lo + o);
-        uint64_t bh = smem_desc(b_hi + o), bl = smem_desc(b_lo + o);
-        umma_bf16(tbase, ah, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-        umma_bf16(tbase, ah, bl, idesc, 1u);
-        umma_bf16(tbase, al, bh, idesc, 1u);
+        uint64_t ah = smem_desc(a_hi + o, CORE_LBO, CORE_SBO), al = smem_desc(a_lo + o, CORE_LBO, CORE_SBO);
+        uint64_t bh = smem_desc(b_hi + o, CORE_LBO, CORE_SBO), bl = smem_desc(b_lo + o, CORE_LBO, CORE_SBO);
+        mma_bf16(tbase, ah, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+        mma_bf16(tbase, ah, bl, idesc, 1u);
+        mma_bf16(tbase, al, bh, idesc, 1u);
       }
-      umma_commit(&empty[s]);
+      commit(&empty[s]);
     }
-    umma_commit(done);
+    commit(done);
   }
   __syncwarp();
   // epilogue: TMEM lane = ab row, column = ij
   bool ok = mbar_wait(done, 0);
-  tc_fence_after();
+  fence_after();
   const int row = warp * 32 + lane;
   const int ab = it.mt * TC_M + row;
   for (int c0 = 0; c0 < it.npad; c0 += 16) {
@@ -279,7 +187,7 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
       }
     }
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (warp == 2) tmem_dealloc(tbase, ncols);
   if (threadIdx.x == 0 && (err || !ok)) atomicExch(&ctl->dev_error, 1);

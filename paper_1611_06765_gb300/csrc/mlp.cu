@@ -1,0 +1,849 @@
+// mlp.cu -- learned warm start for the CCD iteration (not in the paper; it starts the
+// Jacobi iteration of Eq. ccd3 from a prediction instead of the MBPT2 guess of Eq. ccdGuess).
+//
+// Network: 32 features -> 128 -> 128 -> 128 (GELU) -> 1, weights and layer inputs in BF16,
+// FP32 accumulation.  Prediction per restricted amplitude:
+//   t_start = t_MBPT2 + sigma_sys * y_scale * net(features),
+// with sigma_sys the RMS of the system's MBPT2 amplitudes.  Features are dimensionless:
+// momenta in units of k_F, spins, eps_ij^ab / eps_F, N <ab|v|ij> / eps_F, t_MBPT2 / sigma_sys,
+// rho, k_F, N.  Training (SIMT kernels, Adam) uses amplitudes the solver itself converged;
+// inference is one fused tcgen05 kernel: the four layers of a 128-sample tile run back to
+// back with the weights resident in shared memory and the accumulator in tensor memory.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <random>
+
+#include "pnm_context.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int MF = 32, MH = 128, MHEADER = 2 * MF + 4;
+constexpr int O_MU = 0, O_IS = MF, O_YS = 2 * MF;
+constexpr int O_W1 = MHEADER, O_B1 = O_W1 + MH * MF, O_W2 = O_B1 + MH, O_B2 = O_W2 + MH * MH;
+constexpr int O_W3 = O_B2 + MH, O_B3 = O_W3 + MH * MH, O_W4 = O_B3 + MH, O_B4 = O_W4 + MH;
+constexpr int NPARAM = O_B4 + 1;
+constexpr int NFEAT = 22;  // real features; columns NFEAT..MF-1 are zero
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_prime_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// ------------------------------------------------------------------------ features
+struct FeatSys {
+  double kscale;  // (2 pi / L) / k_F
+  double epsF;    // hbar^2 k_F^2 / 2m
+  double rho, kF;
+  int N;
+};
+
+// t_MBPT2 per amplitude and partial sums of its square (one per update item).
+__global__ void k_tm2(DevState D, const int4* __restrict__ items, double* __restrict__ tm2,
+                      double* __restrict__ parts) {
+  __shared__ double sh32[32];
+  int4 it = items[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  int ab = it.z + threadIdx.x;
+  double s = 0.0;
+  if (ab < npp && threadIdx.x < 128) {
+    long z = D.ch_t_off[c] + (long)ij * npp + ab;
+    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+    double den = D.eps[h.x] + D.eps[h.y] - D.eps[p.x] - D.eps[p.y];
+    double t = D.v_pphh[z] / den;
+    tm2[z] = t;
+    s = t * t;
+  }
+  s = block_sum(s, sh32);
+  if (threadIdx.x == 0) parts[blockIdx.x] = s;
+}
+
+__global__ void k_sigma(const double* __restrict__ parts, const int* __restrict__ lo,
+                        const int* __restrict__ hi, const long* __restrict__ count,
+                        double* __restrict__ sigma) {
+  __shared__ double sh32[32];
+  int s = blockIdx.x;
+  double acc = 0.0;
+  for (int k = lo[s] + threadIdx.x; k < hi[s]; k += blockDim.x) acc += parts[k];
+  acc = block_sum(acc, sh32);
+  if (threadIdx.x == 0) sigma[s] = sqrt(acc / (double)max(1L, count[s]));
+}
+
+__global__ void k_features(DevState D, const int4* __restrict__ items, const FeatSys* __restrict__ fs,
+                           const double* __restrict__ tm2, const double* __restrict__ sigma,
+                           float* __restrict__ X) {
+  int4 it = items[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  int ab = it.z + threadIdx.x;
+  if (ab >= npp || threadIdx.x >= 128) return;
+  int sys = D.ch_sys[c];
+  FeatSys f = fs[sys];
+  long z = D.ch_t_off[c] + (long)ij * npp + ab;
+  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+  int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+  char4 sa = D.nvec[p.x], sb = D.nvec[p.y], si = D.nvec[h.x], sj = D.nvec[h.y];
+  float* x = X + z * MF;
+  float k = (float)f.kscale;
+  x[0] = k * sa.x; x[1] = k * sa.y; x[2] = k * sa.z;
+  x[3] = k * sb.x; x[4] = k * sb.y; x[5] = k * sb.z;
+  x[6] = k * si.x; x[7] = k * si.y; x[8] = k * si.z;
+  x[9] = k * sj.x; x[10] = k * sj.y; x[11] = k * sj.z;
+  x[12] = sa.w; x[13] = sb.w; x[14] = si.w; x[15] = sj.w;
+  double den = D.eps[h.x] + D.eps[h.y] - D.eps[p.x] - D.eps[p.y];
+  x[16] = (float)(den / f.epsF);
+  x[17] = (float)(D.v_pphh[z] * f.N / f.epsF);
+  x[18] = (float)(tm2[z] / sigma[sys]);
+  x[19] = (float)(f.rho / 0.16);
+  x[20] = (float)f.kF;
+  x[21] = (float)(f.N / 66.0);
+#pragma unroll
+  for (int q = NFEAT; q < MF; q++) x[q] = 0.0f;
+}
+
+// Training targets y = (t - t_MBPT2) / sigma_sys from the held amplitudes t0.
+__global__ void k_targets(DevState D, const int4* __restrict__ items, const double* __restrict__ tm2,
+                          const double* __restrict__ sigma, float* __restrict__ T) {
+  int4 it = items[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  int ab = it.z + threadIdx.x;
+  if (ab >= npp || threadIdx.x >= 128) return;
+  long z = D.ch_t_off[c] + (long)ij * npp + ab;
+  T[z] = (float)((D.t0[z] - tm2[z]) / sigma[D.ch_sys[c]]);
+}
+
+// t0 = t_MBPT2 + sigma_sys * y_scale * y  (the learned start).
+__global__ void k_apply_start(DevState D, const int4* __restrict__ items, const double* __restrict__ tm2,
+                              const double* __restrict__ sigma, const float* __restrict__ Y, float y_scale) {
+  int4 it = items[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  int ab = it.z + threadIdx.x;
+  if (ab >= npp || threadIdx.x >= 128) return;
+  long z = D.ch_t_off[c] + (long)ij * npp + ab;
+  float y = Y[z];
+  double t = tm2[z];
+  if (isfinite(y)) t += sigma[D.ch_sys[c]] * (double)y_scale * (double)y;
+  D.t0[z] = t;
+}
+
+// ------------------------------------------------------------------- SIMT training
+// C[M][N] (+)= op(A)[M][K] op(B)[K][N], row-major; op(A)(m,k) = tA ? A[k lda + m] : A[m lda + k].
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                               int tA, const float* __restrict__ B, int ldb, int tB,
+                                               float* __restrict__ C, int ldc, int acc) {
+  __shared__ float As[16][68], Bs[16][68];
+  int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float c[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int kk = e >> 6, mm = e & 63;
+      int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? (tA ? A[(long)k * lda + m] : A[(long)m * lda + k]) : 0.0f;
+      int n = n0 + mm;
+      Bs[kk][mm] = (n < N && k < K) ? (tB ? B[(long)n * ldb + k] : B[(long)k * ldb + n]) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) c[i][j] = fmaf(a[i], b[j], c[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+      if (m < M && n < N) C[(long)m * ldc + n] = (acc ? C[(long)m * ldc + n] : 0.0f) + c[i][j];
+    }
+}
+
+void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, int tA, const float* B, int ldb,
+           int tB, float* C, int ldc, int acc) {
+  dim3 g((N + 63) / 64, (M + 63) / 64);
+  k_sgemm<<<g, 256, 0, s>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, acc);
+}
+
+// h0 = bf16((x - mu) * inv_std) for the rows idx[0..B) of X.
+__global__ void k_prep(const float* __restrict__ X, const int* __restrict__ idx, int B,
+                       const float* __restrict__ blob, float* __restrict__ H0) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * MF) return;
+  int r = e / MF, q = e % MF;
+  long row = idx ? idx[r] : r;
+  H0[e] = bf16r((X[row * MF + q] - blob[O_MU + q]) * blob[O_IS + q]);
+}
+
+// z = acc + b; keep z; h = bf16(gelu(z)).
+__global__ void k_bias_gelu(float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ Hn, int B) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * MH) return;
+  float z = Z[e] + b[e % MH];
+  Z[e] = z;
+  Hn[e] = bf16r(gelu_f(z));
+}
+
+// y = h3 . w4 + b4, residual, loss partial and dy = 2 (y - t) / B.  One warp per row.
+__global__ void k_out(const float* __restrict__ H3, const float* __restrict__ w4q, const float* __restrict__ b4,
+                      const float* __restrict__ T, const int* __restrict__ idx, int B, float* __restrict__ Y,
+                      float* __restrict__ dY, double* __restrict__ loss_acc) {
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= B) return;
+  float s = 0.0f;
+  for (int q = lane; q < MH; q += 32) s += H3[(long)r * MH + q] * w4q[q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    float y = s + b4[0];
+    if (Y) Y[r] = y;
+    if (T) {
+      float t = T[idx ? idx[r] : r];
+      float d = y - t;
+      dY[r] = 2.0f * d / (float)B;
+      atomicAdd(loss_acc, (double)d * d);
+    }
+  }
+}
+
+__global__ void k_dz(const float* __restrict__ dH, const float* __restrict__ Z, float* __restrict__ dZ, int n) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dZ[e] = dH[e] * gelu_prime_f(Z[e]);
+}
+
+// Column sums of a (B x ncol) matrix into g (fixed order per column).
+__global__ void k_colsum(const float* __restrict__ A, int B, int ncol, float* __restrict__ g) {
+  __shared__ float sh[256];
+  int col = blockIdx.x;
+  float s = 0.0f;
+  for (int r = threadIdx.x; r < B; r += blockDim.x) s += A[(long)r * ncol + col];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) g[col] = sh[0];
+}
+
+// Adam on the parameters (header entries are constants); q = BF16-rounded copy of weights.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float* __restrict__ q, float lr, float b1, float b2,
+                       float c1, float c2, float eps) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < MHEADER || e >= NPARAM) return;
+  float ge = g[e];
+  float me = b1 * m[e] + (1.0f - b1) * ge;
+  float ve = b2 * v[e] + (1.0f - b2) * ge * ge;
+  m[e] = me;
+  v[e] = ve;
+  float we = w[e] - lr * (me / c1) / (sqrtf(ve / c2) + eps);
+  w[e] = we;
+  bool is_w = (e >= O_W1 && e < O_B1) || (e >= O_W2 && e < O_B2) || (e >= O_W3 && e < O_B3) ||
+              (e >= O_W4 && e < O_B4);
+  q[e] = is_w ? bf16r(we) : we;
+}
+
+__global__ void k_quantize(const float* __restrict__ w, float* __restrict__ q) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NPARAM) return;
+  bool is_w = (e >= O_W1 && e < O_B1) || (e >= O_W2 && e < O_B2) || (e >= O_W3 && e < O_B3) ||
+              (e >= O_W4 && e < O_B4);
+  q[e] = is_w ? bf16r(w[e]) : w[e];
+}
+
+// Per-column sums and squares of X (n x 32) for the feature normalisation.
+__global__ void k_featstats(const float* __restrict__ X, long n, double* __restrict__ out) {
+  __shared__ double s1[256], s2[256];
+  int q = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (long r = threadIdx.x; r < n; r += blockDim.x) {
+    double x = X[r * MF + q];
+    a += x;
+    b += x * x;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s1[threadIdx.x] += s1[threadIdx.x + w];
+      s2[threadIdx.x] += s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * q] = s1[0];
+    out[2 * q + 1] = s2[0];
+  }
+}
+
+__global__ void k_scale(float* __restrict__ T, long n, float s) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) T[e] *= s;
+}
+
+// ------------------------------------------------------------- tensor-core inference
+// Packed BF16 weights in the K-major core-matrix layout: W1 (128 x 32), W2, W3 (128 x 128),
+// W4 (16 x 128, rows 1..15 zero).
+constexpr int PW1 = MH * MF, PW2 = MH * MH, PW4 = 16 * MH;
+constexpr int PW_TOTAL = PW1 + 2 * PW2 + PW4;
+
+__global__ void k_pack_weights(const float* __restrict__ q, __nv_bfloat16* __restrict__ pw) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < PW1) {
+    int r = e / MF, k = e % MF;
+    pw[tc::core_off(r, k, MF / 8)] = __float2bfloat16_rn(q[O_W1 + e]);
+  } else if (e < PW1 + PW2) {
+    int f = e - PW1, r = f / MH, k = f % MH;
+    pw[PW1 + tc::core_off(r, k, MH / 8)] = __float2bfloat16_rn(q[O_W2 + f]);
+  } else if (e < PW1 + 2 * PW2) {
+    int f = e - PW1 - PW2, r = f / MH, k = f % MH;
+    pw[PW1 + PW2 + tc::core_off(r, k, MH / 8)] = __float2bfloat16_rn(q[O_W3 + f]);
+  } else if (e < PW_TOTAL) {
+    int f = e - PW1 - 2 * PW2, r = f / MH, k = f % MH;
+    float w = (r == 0) ? q[O_W4 + k] : 0.0f;
+    pw[PW1 + 2 * PW2 + tc::core_off(r, k, MH / 8)] = __float2bfloat16_rn(w);
+  }
+}
+
+constexpr uint32_t MLP_SMEM = 1024 + PW_TOTAL * 2 + MH * MH * 2 + 4 * MH * 4 + 1024;
+
+// One CTA (4 warps) loops over 128-sample tiles.  Warp w reads TMEM lanes 32w..32w+31;
+// thread (w, lane) owns sample row 32w + lane of the tile.
+__global__ void __launch_bounds__(128, 1) k_mlp_tc(const float* __restrict__ X, long n,
+                                                   const float* __restrict__ q,
+                                                   const __nv_bfloat16* __restrict__ pw,
+                                                   float* __restrict__ Y, int* __restrict__ err_flag) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar_w = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* bar_mma = bar_w + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_w + 2);
+  __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(smem + 1024);
+  __nv_bfloat16* A = W + PW_TOTAL;
+  float* bias = reinterpret_cast<float*>(A + MH * MH);  // b1, b2, b3 (then b4 at [3*MH])
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = threadIdx.x;
+  __shared__ int bad;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    tc::mbar_init(bar_w, 1);
+    tc::mbar_init(bar_mma, 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 2) {
+    tc::tmem_alloc(tslot, MH);
+    tc::tmem_relinquish();
+  }
+  for (int k = threadIdx.x; k < MH; k += blockDim.x) {
+    bias[k] = q[O_B1 + k];
+    bias[MH + k] = q[O_B2 + k];
+    bias[2 * MH + k] = q[O_B3 + k];
+  }
+  if (threadIdx.x == 0) bias[3 * MH] = q[O_B4];
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  if (threadIdx.x == 0) {
+    tc::mbar_expect_tx(bar_w, PW_TOTAL * 2);
+    tc::bulk_g2s(W, pw, PW_TOTAL * 2, bar_w);
+  }
+  if (!tc::mbar_wait(bar_w, 0)) bad = 1;
+  uint32_t phase = 0;
+  const long ntiles = (n + MH - 1) / MH;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // every thread leaves together after a failed wait (no thread may skip a barrier)
+    __syncthreads();
+    const int stop = bad;
+    __syncthreads();
+    if (stop) break;
+    long r_glob = tile * MH + row;
+    // layer-1 input: normalised, BF16, K = 32 layout
+    {
+      float xv[MF];
+      bool ok = r_glob < n;
+#pragma unroll
+      for (int k = 0; k < MF; k++)
+        xv[k] = ok ? (X[r_glob * MF + k] - q[O_MU + k]) * q[O_IS + k] : 0.0f;
+#pragma unroll
+      for (int k0 = 0; k0 < MF; k0 += 8) {
+        __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) v8[j] = __float2bfloat16_rn(xv[k0 + j]);
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, k0, MF / 8)) = *reinterpret_cast<uint4*>(v8);
+      }
+    }
+    for (int layer = 0; layer < 4; layer++) {
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      const int K = layer == 0 ? MF : MH;
+      const int N = layer == 3 ? 16 : MH;
+      if (threadIdx.x == 0) {
+        const __nv_bfloat16* Wl = W + (layer == 0 ? 0 : layer == 1 ? PW1 : layer == 2 ? PW1 + PW2 : PW1 + 2 * PW2);
+        const uint32_t sbo = (K / 8) * 128;
+        const uint32_t idesc = tc::idesc_bf16(MH, N);
+        for (int ks = 0; ks < K / 16; ks++) {
+          uint64_t ad = tc::smem_desc(reinterpret_cast<const unsigned char*>(A) + ks * 256, 128, sbo);
+          uint64_t bd = tc::smem_desc(reinterpret_cast<const unsigned char*>(Wl) + ks * 256, 128, sbo);
+          tc::mma_bf16(tbase, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+        tc::commit(bar_mma);
+      }
+      __syncwarp();
+      if (!tc::mbar_wait(bar_mma, phase & 1)) bad = 1;
+      phase++;
+      tc::fence_after();
+      const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+      if (layer < 3) {
+        const float* b = bias + layer * MH;
+        for (int c0 = 0; c0 < MH; c0 += 16) {
+          uint32_t r[16];
+          tc::tmem_ld16(lane_addr + c0, r);
+#pragma unroll
+          for (int h = 0; h < 16; h += 8) {
+            __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v8[j] = __float2bfloat16_rn(gelu_f(__uint_as_float(r[h + j]) + b[c0 + h + j]));
+            *reinterpret_cast<uint4*>(A + tc::core_off(row, c0 + h, MH / 8)) = *reinterpret_cast<uint4*>(v8);
+          }
+        }
+      } else {
+        uint32_t r[16];
+        tc::tmem_ld16(lane_addr, r);
+        if (r_glob < n) Y[r_glob] = __uint_as_float(r[0]) + bias[3 * MH];
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 2) tc::tmem_dealloc(tbase, MH);
+  if (threadIdx.x == 0 && bad) atomicExch(err_flag, 1);
+}
+
+template <typename T>
+T* xalloc(size_t n, std::vector<void*>& owned) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    throw PnmError{PNM_ENOMEM, "cudaMalloc (warm-start network) failed"};
+  }
+  owned.push_back(p);
+  return (T*)p;
+}
+
+struct Scratch {
+  std::vector<void*> owned;
+  ~Scratch() {
+    for (void* p : owned) cudaFree(p);
+  }
+};
+
+// Training/inference buffers for a batch of B rows.
+struct Net {
+  float *w, *q, *g, *m, *v;  // parameters, BF16-rounded copy, gradient, Adam moments
+  float *H0, *Z1, *H1, *Z2, *H2, *Z3, *H3, *Y, *dY, *dA, *dB;
+  int B;
+  void alloc(int b, Scratch& s) {
+    B = b;
+    w = xalloc<float>(NPARAM, s.owned);
+    q = xalloc<float>(NPARAM, s.owned);
+    g = xalloc<float>(NPARAM, s.owned);
+    m = xalloc<float>(NPARAM, s.owned);
+    v = xalloc<float>(NPARAM, s.owned);
+    H0 = xalloc<float>((size_t)b * MF, s.owned);
+    Z1 = xalloc<float>((size_t)b * MH, s.owned);
+    H1 = xalloc<float>((size_t)b * MH, s.owned);
+    Z2 = xalloc<float>((size_t)b * MH, s.owned);
+    H2 = xalloc<float>((size_t)b * MH, s.owned);
+    Z3 = xalloc<float>((size_t)b * MH, s.owned);
+    H3 = xalloc<float>((size_t)b * MH, s.owned);
+    Y = xalloc<float>(b, s.owned);
+    dY = xalloc<float>(b, s.owned);
+    dA = xalloc<float>((size_t)b * MH, s.owned);
+    dB = xalloc<float>((size_t)b * MH, s.owned);
+  }
+};
+
+void net_forward(cudaStream_t s, Net& nt, const float* X, const int* idx, int B) {
+  k_prep<<<(B * MF + 255) / 256, 256, 0, s>>>(X, idx, B, nt.q, nt.H0);
+  sgemm(s, B, MH, MF, nt.H0, MF, 0, nt.q + O_W1, MF, 1, nt.Z1, MH, 0);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z1, nt.q + O_B1, nt.H1, B);
+  sgemm(s, B, MH, MH, nt.H1, MH, 0, nt.q + O_W2, MH, 1, nt.Z2, MH, 0);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z2, nt.q + O_B2, nt.H2, B);
+  sgemm(s, B, MH, MH, nt.H2, MH, 0, nt.q + O_W3, MH, 1, nt.Z3, MH, 0);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z3, nt.q + O_B3, nt.H3, B);
+}
+
+// Backward pass from dY; writes the gradient blob nt.g (header entries zero).
+void net_backward(cudaStream_t s, Net& nt, int B) {
+  CUDA_TRY(cudaMemsetAsync(nt.g, 0, sizeof(float) * NPARAM, s));
+  // output layer: dw4 = dY^T H3, db4 = sum dY, dH3 = dY w4
+  sgemm(s, 1, MH, B, nt.dY, 1, 1, nt.H3, MH, 0, nt.g + O_W4, MH, 0);
+  k_colsum<<<1, 256, 0, s>>>(nt.dY, B, 1, nt.g + O_B4);
+  sgemm(s, B, MH, 1, nt.dY, 1, 0, nt.q + O_W4, MH, 0, nt.dA, MH, 0);
+  const float* Zs[3] = {nt.Z1, nt.Z2, nt.Z3};
+  const float* Hin[3] = {nt.H0, nt.H1, nt.H2};
+  const int Ow[3] = {O_W1, O_W2, O_W3}, Ob[3] = {O_B1, O_B2, O_B3}, Kin[3] = {MF, MH, MH};
+  for (int l = 2; l >= 0; l--) {
+    k_dz<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.dA, Zs[l], nt.dB, B * MH);
+    sgemm(s, MH, Kin[l], B, nt.dB, MH, 1, Hin[l], Kin[l], 0, nt.g + Ow[l], Kin[l], 0);
+    k_colsum<<<MH, 256, 0, s>>>(nt.dB, B, MH, nt.g + Ob[l]);
+    if (l > 0) sgemm(s, B, MH, MH, nt.dB, MH, 0, nt.q + Ow[l], MH, 0, nt.dA, MH, 0);
+  }
+}
+
+unsigned long long g_seed_mix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- context glue
+struct MlpState {
+  float* X = nullptr;       // features of every amplitude (library order)
+  double* tm2 = nullptr;    // MBPT2 amplitudes
+  double* sigma = nullptr;  // per system
+  float* Y = nullptr;       // network output
+  float* q = nullptr;       // model parameters (BF16-rounded weights)
+  __nv_bfloat16* pw = nullptr;
+  int* err = nullptr;
+  float y_scale = 1.0f;
+  bool have_model = false;
+};
+
+static void mlp_features(pnm_ctx* ctx) {
+  if (!ctx->mlp) ctx->mlp = new MlpState();
+  MlpState* M = ctx->mlp;
+  if (M->X) return;
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  M->X = xalloc<float>((size_t)ctx->nt * MF, ctx->owned);
+  M->tm2 = xalloc<double>(ctx->nt, ctx->owned);
+  M->sigma = xalloc<double>(nsys, ctx->owned);
+  M->Y = xalloc<float>(ctx->nt, ctx->owned);
+  double* parts = xalloc<double>(ctx->n_upd_items, ctx->owned);
+  std::vector<long> cnt(nsys);
+  std::vector<FeatSys> fs(nsys);
+  for (int k = 0; k < nsys; k++) {
+    const SysInfo& S = ctx->sys[k];
+    cnt[k] = S.t_end - S.t_begin;
+    double kF = std::cbrt(3.0 * PNM_PI * PNM_PI * S.rho);
+    fs[k].kF = kF;
+    fs[k].rho = S.rho;
+    fs[k].N = S.N;
+    fs[k].kscale = (2.0 * PNM_PI / S.L) / kF;
+    fs[k].epsF = ctx->hbar2_2m * kF * kF;
+  }
+  long* dcnt = xalloc<long>(nsys, ctx->owned);
+  FeatSys* dfs = xalloc<FeatSys>(nsys, ctx->owned);
+  CUDA_TRY(cudaMemcpyAsync(dcnt, cnt.data(), sizeof(long) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(dfs, fs.data(), sizeof(FeatSys) * nsys, cudaMemcpyHostToDevice, s));
+  k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, parts);
+  k_sigma<<<nsys, 256, 0, s>>>(parts, ctx->upd_lo_d, ctx->upd_hi_d, dcnt, M->sigma);
+  k_features<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, dfs, M->tm2, M->sigma, M->X);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+static void check_blob_header(const float* blob) {
+  for (int k = 0; k < NPARAM; k++)
+    if (!std::isfinite(blob[k])) throw PnmError{PNM_EINVAL, "non-finite parameter"};
+}
+
+static void set_model(pnm_ctx* ctx, const float* blob) {
+  check_blob_header(blob);
+  if (!ctx->mlp) ctx->mlp = new MlpState();
+  MlpState* M = ctx->mlp;
+  cudaStream_t s = ctx->stream;
+  if (!M->q) {
+    M->q = xalloc<float>(NPARAM, ctx->owned);
+    M->pw = xalloc<__nv_bfloat16>(PW_TOTAL, ctx->owned);
+    M->err = xalloc<int>(1, ctx->owned);
+    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+  }
+  float* w = xalloc<float>(NPARAM, ctx->owned);
+  CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
+  k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, M->q);
+  k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(M->q, M->pw);
+  CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
+  M->y_scale = blob[O_YS];
+  M->have_model = true;
+}
+
+static void tc_infer(cudaStream_t s, const float* X, long n, const float* q, const __nv_bfloat16* pw, float* Y,
+                     int* err) {
+  long ntiles = (n + MH - 1) / MH;
+  int grid = (int)std::min<long>(ntiles, 152 * 2);
+  if (grid > 0) k_mlp_tc<<<grid, 128, MLP_SMEM, s>>>(X, n, q, pw, Y, err);
+}
+
+// Learned start into t0 (every system), used by the solver for PNM_INIT_MLP.
+void pnm_mlp_start(pnm_ctx* ctx) {
+  if (!ctx->mlp || !ctx->mlp->have_model) throw PnmError{PNM_EINVAL, "no warm-start model set (pnm_mlp_set_model)"};
+  mlp_features(ctx);
+  MlpState* M = ctx->mlp;
+  cudaStream_t s = ctx->stream;
+  tc_infer(s, M->X, ctx->nt, M->q, M->pw, M->Y, M->err);
+  k_apply_start<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, M->sigma, M->Y, M->y_scale);
+  CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_free_mlp(pnm_ctx* ctx) {
+  delete ctx->mlp;
+  ctx->mlp = nullptr;
+}
+
+// -------------------------------------------------------------------------- C ABI
+extern "C" {
+
+int pnm_mlp_num_params(int* n) {
+  if (!n) return PNM_EINVAL;
+  *n = NPARAM;
+  return PNM_OK;
+}
+
+int pnm_mlp_init(float* blob, unsigned long long seed) {
+  if (!blob) return PNM_EINVAL;
+  std::mt19937_64 rng(g_seed_mix(seed));
+  std::normal_distribution<double> nd(0.0, 1.0);
+  std::memset(blob, 0, sizeof(float) * NPARAM);
+  for (int k = 0; k < MF; k++) blob[O_IS + k] = 1.0f;
+  blob[O_YS] = 1.0f;
+  for (int k = 0; k < MH * MF; k++) blob[O_W1 + k] = (float)(nd(rng) * std::sqrt(2.0 / NFEAT));
+  for (int k = 0; k < MH * MH; k++) blob[O_W2 + k] = (float)(nd(rng) * std::sqrt(2.0 / MH));
+  for (int k = 0; k < MH * MH; k++) blob[O_W3 + k] = (float)(nd(rng) * std::sqrt(2.0 / MH));
+  for (int k = 0; k < MH; k++) blob[O_W4 + k] = (float)(nd(rng) * std::sqrt(1.0 / MH));
+  return PNM_OK;
+}
+
+int pnm_mlp_features(pnm_ctx* ctx, int sys, float* X, double* t_mbpt2, double* sigma) {
+  try {
+    if (!ctx || sys < 0 || sys >= (int)ctx->sys.size()) throw PnmError{PNM_EINVAL, "bad argument"};
+    mlp_features(ctx);
+    const SysInfo& S = ctx->sys[sys];
+    long n = S.t_end - S.t_begin;
+    cudaStream_t s = ctx->stream;
+    if (X) CUDA_TRY(cudaMemcpyAsync(X, ctx->mlp->X + S.t_begin * MF, sizeof(float) * n * MF, cudaMemcpyDeviceToHost, s));
+    if (t_mbpt2) CUDA_TRY(cudaMemcpyAsync(t_mbpt2, ctx->mlp->tm2 + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (sigma) CUDA_TRY(cudaMemcpyAsync(sigma, ctx->mlp->sigma + sys, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
+int pnm_mlp_set_model(pnm_ctx* ctx, const float* blob) {
+  try {
+    if (!ctx || !blob) throw PnmError{PNM_EINVAL, "null argument"};
+    set_model(ctx, blob);
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
+int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use_tensor_cores, void* stream) {
+  try {
+    if (!blob || !X || !Y || n < 0) throw PnmError{PNM_EINVAL, "bad argument"};
+    check_blob_header(blob);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc;
+    float* w = xalloc<float>(NPARAM, sc.owned);
+    float* q = xalloc<float>(NPARAM, sc.owned);
+    float* dX = xalloc<float>((size_t)n * MF, sc.owned);
+    float* dY = xalloc<float>(n, sc.owned);
+    CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dX, X, sizeof(float) * n * MF, cudaMemcpyHostToDevice, s));
+    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, q);
+    if (use_tensor_cores) {
+      __nv_bfloat16* pw = xalloc<__nv_bfloat16>(PW_TOTAL, sc.owned);
+      int* err = xalloc<int>(1, sc.owned);
+      CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+      CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+      k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(q, pw);
+      tc_infer(s, dX, n, q, pw, dY, err);
+      int h_err = 0;
+      CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (h_err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget"};
+    } else {
+      const long chunk = 8192;
+      Net nt;
+      nt.alloc((int)std::min(chunk, std::max(1L, n)), sc);
+      CUDA_TRY(cudaMemcpyAsync(nt.q, q, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s));
+      for (long r0 = 0; r0 < n; r0 += chunk) {
+        int B = (int)std::min(chunk, n - r0);
+        net_forward(s, nt, dX + r0 * MF, nullptr, B);
+        k_out<<<(B * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, nullptr, nullptr, B,
+                                                   dY + r0, nullptr, nullptr);
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(Y, dY, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
+int pnm_mlp_loss_grad(const float* blob, const float* X, const float* T, int n, float* loss, float* grad,
+                      void* stream) {
+  try {
+    if (!blob || !X || !T || n <= 0) throw PnmError{PNM_EINVAL, "bad argument"};
+    check_blob_header(blob);
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc;
+    Net nt;
+    nt.alloc(n, sc);
+    float* dX = xalloc<float>((size_t)n * MF, sc.owned);
+    float* dT = xalloc<float>(n, sc.owned);
+    double* lacc = xalloc<double>(1, sc.owned);
+    CUDA_TRY(cudaMemcpyAsync(nt.w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)n * MF, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dT, T, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(lacc, 0, sizeof(double), s));
+    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.q);
+    net_forward(s, nt, dX, nullptr, n);
+    k_out<<<(n * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, dT, nullptr, n, nt.Y, nt.dY, lacc);
+    net_backward(s, nt, n);
+    CUDA_TRY(cudaGetLastError());
+    double l = 0;
+    CUDA_TRY(cudaMemcpyAsync(&l, lacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (grad) CUDA_TRY(cudaMemcpyAsync(grad, nt.g, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (loss) *loss = (float)(l / n);
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
+int pnm_mlp_train(pnm_ctx* const* ctxs, int nctx, const pnm_mlp_opts* o, float* blob, float* loss_hist,
+                  int cap, int* n_hist) {
+  try {
+    if (!ctxs || nctx <= 0 || !o || !blob) throw PnmError{PNM_EINVAL, "bad argument"};
+    if (o->epochs < 0 || o->batch <= 0 || !(o->lr > 0)) throw PnmError{PNM_EINVAL, "bad options"};
+    check_blob_header(blob);
+    cudaStream_t s = ctxs[0]->stream;
+    long ntot = 0;
+    for (int k = 0; k < nctx; k++) {
+      if (!ctxs[k]) throw PnmError{PNM_EINVAL, "null context"};
+      ntot += ctxs[k]->nt;
+    }
+    Scratch sc;
+    float* X = xalloc<float>((size_t)ntot * MF, sc.owned);
+    float* T = xalloc<float>(ntot, sc.owned);
+    long off = 0;
+    for (int k = 0; k < nctx; k++) {
+      pnm_ctx* c = ctxs[k];
+      mlp_features(c);
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+      k_targets<<<c->n_upd_items, 128, 0, c->stream>>>(c->d, c->upd_items, c->mlp->tm2, c->mlp->sigma, T + off);
+      CUDA_TRY(cudaMemcpyAsync(X + off * MF, c->mlp->X, sizeof(float) * c->nt * MF, cudaMemcpyDeviceToDevice,
+                               c->stream));
+      CUDA_TRY(cudaStreamSynchronize(c->stream));
+      off += c->nt;
+    }
+    // normalisation from the training data
+    double* st = xalloc<double>(2 * MF + 2, sc.owned);
+    k_featstats<<<MF, 256, 0, s>>>(X, ntot, st);
+    std::vector<double> hs(2 * MF + 2);
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), st, sizeof(double) * 2 * MF, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int q = 0; q < MF; q++) {
+      double mu = hs[2 * q] / ntot, var = hs[2 * q + 1] / ntot - mu * mu;
+      blob[O_MU + q] = (float)mu;
+      blob[O_IS + q] = var > 1e-12 ? (float)(1.0 / std::sqrt(var)) : 0.0f;
+    }
+    {
+      std::vector<float> ht(ntot);
+      CUDA_TRY(cudaMemcpyAsync(ht.data(), T, sizeof(float) * ntot, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      double a = 0, b = 0;
+      for (float v : ht) {
+        a += v;
+        b += (double)v * v;
+      }
+      double var = b / ntot - (a / ntot) * (a / ntot);
+      double ys = var > 1e-30 ? std::sqrt(var) : 1.0;
+      blob[O_YS] = (float)ys;
+      k_scale<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(T, ntot, (float)(1.0 / ys));
+    }
+    int B = (int)std::min<long>(o->batch, ntot);
+    Net nt;
+    nt.alloc(B, sc);
+    int* idx = xalloc<int>(ntot, sc.owned);
+    double* lacc = xalloc<double>(1, sc.owned);
+    CUDA_TRY(cudaMemcpyAsync(nt.w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(nt.m, 0, sizeof(float) * NPARAM, s));
+    CUDA_TRY(cudaMemsetAsync(nt.v, 0, sizeof(float) * NPARAM, s));
+    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.q);
+    std::vector<int> perm(ntot);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::mt19937_64 rng(g_seed_mix(o->seed));
+    long step = 0;
+    int nh = 0;
+    const float b1 = 0.9f, b2 = 0.999f;
+    for (int ep = 0; ep < o->epochs; ep++) {
+      std::shuffle(perm.begin(), perm.end(), rng);
+      CUDA_TRY(cudaMemcpyAsync(idx, perm.data(), sizeof(int) * ntot, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemsetAsync(lacc, 0, sizeof(double), s));
+      long nb = 0;
+      for (long r0 = 0; r0 + B <= ntot; r0 += B, nb++) {
+        net_forward(s, nt, X, idx + r0, B);
+        k_out<<<(B * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, T, idx + r0, B, nt.Y, nt.dY,
+                                                   lacc);
+        net_backward(s, nt, B);
+        step++;
+        float c1 = 1.0f - std::pow(b1, (float)step), c2 = 1.0f - std::pow(b2, (float)step);
+        k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.g, nt.m, nt.v, nt.q, (float)o->lr, b1, b2, c1, c2,
+                                                    1e-8f);
+      }
+      CUDA_TRY(cudaGetLastError());
+      double l = 0;
+      CUDA_TRY(cudaMemcpyAsync(&l, lacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (loss_hist && nh < cap) loss_hist[nh] = (float)(l / std::max(1L, nb * B));
+      nh++;
+    }
+    std::vector<float> w(NPARAM);
+    CUDA_TRY(cudaMemcpyAsync(w.data(), nt.w, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = MHEADER; k < NPARAM; k++) blob[k] = w[k];
+    if (n_hist) *n_hist = nh;
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
+}  // extern "C"

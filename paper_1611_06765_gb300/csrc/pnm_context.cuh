@@ -6,6 +6,7 @@
 #include "pnm_internal.cuh"
 
 struct MixedState;  // mixed-precision operand arenas (mixed.cu)
+struct MlpState;    // learned warm start (mlp.cu)
 
 // Kernel ids of the per-kernel profiler.
 enum {
@@ -56,6 +57,9 @@ struct pnm_ctx {
   unsigned long long cond_handle_for_mode[4] = {0, 0, 0, 0};
 
   MixedState* mixed = nullptr;
+  MlpState* mlp = nullptr;
+  double hbar2_2m = 0.0;
+  int mlp_fallback = 0;  // 1 when the last learned start was replaced by the MBPT2 start
 
   // side streams for the independent parts of an update (ph term, pp ladder), joined by events
   cudaStream_t side[2] = {nullptr, nullptr};
@@ -87,6 +91,8 @@ void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);
 int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alpha);
 void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
+void pnm_mlp_start(pnm_ctx* ctx);
+void pnm_free_mlp(pnm_ctx* ctx);
 void prof_begin(pnm_ctx* ctx, int kid);
 void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);

@@ -518,6 +518,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   std::vector<SysInfo>& sys = ctx->sys;
   sys.resize(nsys);
   std::vector<SysScratch> scr(nsys);
+  ctx->hbar2_2m = P.hbar2_2m;
 
   // ---- basis per system (into scratch), closed-shell check on the host
   std::vector<std::vector<char4>> hvec(nsys);

@@ -21,7 +21,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   if (o.max_iter < 1) throw PnmError{PNM_EINVAL, "max_iter must be >= 1"};
   if (o.precision != PNM_PREC_FP64 && o.precision != PNM_PREC_BF16X3)
     throw PnmError{PNM_EINVAL, "unknown precision mode"};
-  if (o.init < PNM_INIT_MBPT2 || o.init > PNM_INIT_KEEP) throw PnmError{PNM_EINVAL, "unknown init"};
+  if (o.init < PNM_INIT_MBPT2 || o.init > PNM_INIT_MLP) throw PnmError{PNM_EINVAL, "unknown init"};
   if (o.refine_sweeps < 0) throw PnmError{PNM_EINVAL, "refine_sweeps must be >= 0"};
   if (!(o.tol_dE > 0.0) && !(o.tol_dE_per_N > 0.0)) throw PnmError{PNM_EINVAL, "no tolerance given"};
   cudaStream_t s = ctx->stream;
@@ -53,7 +53,12 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
 
   cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
   CUDA_TRY(cudaEventRecord(e0, s));
-  pnm_start(ctx, o.init, tol);
+  int init = o.init;
+  if (init == PNM_INIT_MLP) {
+    pnm_mlp_start(ctx);  // t0 = learned start; its energy is taken below as for a kept start
+    init = PNM_INIT_KEEP;
+  }
+  pnm_start(ctx, init, tol);
   if (mixed) pnm_mixed_pack_initial(ctx);
   int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : PNM_PREC_FP64, o.max_iter, o.host_loop,
                             o.mix_alpha);
@@ -78,6 +83,18 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     if (dE) dE[k] = hs[k].e_new;
     if (iters) iters[k] = hs[k].iters;
     if (resid) resid[k] = hs[k].resid;
+  }
+  if (o.init == PNM_INIT_MLP) ctx->mlp_fallback = 0;
+  if (o.init == PNM_INIT_MLP && (status == PNM_ENOTCONV || status == PNM_EDIVERGED)) {
+    // the CCD iteration judges the learned start: if it does not lead to convergence,
+    // solve again from the MBPT2 guess
+    pnm_solve_opts o2 = o;
+    o2.init = PNM_INIT_MBPT2;
+    float t_first = (float)ctx->t_solve;
+    int rc = pnm_solve(ctx, o2, dE, iters, resid);
+    ctx->t_solve += t_first;
+    ctx->mlp_fallback = 1;
+    return rc;
   }
   if (status == 1) return PNM_OK;
   if (status == PNM_ENOTCONV) pnm_set_error(status, "iteration cap reached before convergence");
