@@ -425,6 +425,8 @@ def run_ours(a):
             "roofline": roof,
             "cpu_baseline": cpu,
             "comparison": comparison,
+            "tuning": (dict(zip(("k_splits", "stages", "pp_tc_us", "serial_mask"), ctx.tuning()))
+                       if prec == P.PNM_PREC_BF16X3 else None),
             "result": {"dE_per_N": statistics.mean(dEs) / N, "iters": statistics.mean(iters),
                        "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
                        "wall_ms_per_step": wall * 1e3 / a.steps, "setup_ms": tim["setup"],

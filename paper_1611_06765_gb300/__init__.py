@@ -162,6 +162,12 @@ class Context:
         blob = np.ascontiguousarray(blob, dtype=np.float32)
         _lib.check(_lib.load().pnm_mlp_set_model(self._h, blob.ctypes.data_as(C.POINTER(C.c_float))))
 
+    def tuning(self):
+        """Autotuner choices: (k-range splits, ring stages, us per ladder launch, serial mask)."""
+        a, b, us, m = C.c_int(), C.c_int(), C.c_float(), C.c_int()
+        _lib.check(_lib.load().pnm_get_tuning(self._h, C.byref(a), C.byref(b), C.byref(us), C.byref(m)))
+        return a.value, b.value, us.value, m.value
+
     def set_profiling(self, on=True):
         _lib.check(_lib.load().pnm_set_profiling(self._h, int(on)))
 

@@ -354,6 +354,14 @@ int pnm_apply_pp_ladder(pnm_ctx* ctx, int sys, int precision, const double* t, d
   });
 }
 
+int pnm_get_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask) {
+  return guarded([&]() {
+    if (!ctx) throw PnmError{PNM_EINVAL, "null context"};
+    pnm_mixed_tuning(ctx, ksplit, stages, us, serial_mask);
+    return PNM_OK;
+  });
+}
+
 int pnm_set_profiling(pnm_ctx* ctx, int on) {
   return guarded([&]() {
     if (!ctx) throw PnmError{PNM_EINVAL, "null context"};

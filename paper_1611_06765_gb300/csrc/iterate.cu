@@ -129,6 +129,25 @@ __global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restric
     Xt[e] = wv;  // Xt[u][s] = W[s][u]
   }
   __syncthreads();
+  // Small channels: one output per thread (more threads busy, shorter chains); large
+  // channels: 4 x 4 register tiles.
+  const bool small = (nph * nhp <= 2 * (int)blockDim.x) && (nhp * nhp <= 2 * (int)blockDim.x);
+  if (small) {
+    for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
+      int r = e / nhp, c2 = e % nhp;
+      T_ acc = 0;
+      for (int u = 0; u < nph; u++) acc += Xt[u * H4 + r] * Ts[u * H4 + c2];
+      Cs[r * H4 + c2] = xv1[co + (long)r * nhp + c2] + (T_)0.5 * acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+      int r = e / nhp, c2 = e % nhp;
+      T_ acc = 0;
+      for (int u = 0; u < nhp; u++) acc += Ts[r * H4 + u] * Cs[u * H4 + c2];
+      xq[to + (long)r * nhp + c2] = acc;
+    }
+    return;
+  }
   // C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
   int th = H4 >> 2;
   for (int tile = threadIdx.x; tile < th * th; tile += blockDim.x) {
@@ -345,7 +364,8 @@ template <typename RT, typename QT>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
                                                 const int4* __restrict__ items, FinArgs fa,
                                                 const RT* __restrict__ rpp,
-                                                const QT* __restrict__ xq, PackArgs pk) {
+                                                const QT* __restrict__ xq, PackArgs pk, int nplanes,
+                                                long pstride) {
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
   int c = it.x, ij = it.y;
@@ -373,7 +393,8 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
     if (!frozen) {
       int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
       double num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
-      if (szero) num += (double)rpp[z];
+      if (szero)
+        for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
       double hh = 0.0;
       for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
       num += hh;
@@ -412,16 +433,20 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   last_block_finalize(fa, ctl);
 }
 
+size_t upd_smem_bytes(const pnm_ctx* ctx) {
+  return sizeof(double) * ((size_t)ctx->max_nhh * 128 + (size_t)ctx->max_nhh * ctx->max_nhh);
+}
+
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h, PackArgs pk) {
-  k_update<RT, QT><<<ctx->n_upd_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->upd_items,
-                                                               fin_args(ctx, use_cond, h), rpp, xq, pk);
+                   cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride) {
+  k_update<RT, QT><<<ctx->n_upd_items, 128, 0, ctx->stream>>>(
+      ctx->d, ctx->ctl, ctx->upd_items, fin_args(ctx, use_cond, h), rpp, xq, pk, nplanes, pstride);
 }
 template void launch_update<double, double>(pnm_ctx*, const double*, const double*, int,
-                                            cudaGraphConditionalHandle, PackArgs);
+                                            cudaGraphConditionalHandle, PackArgs, int, long);
 template void launch_update<float, float>(pnm_ctx*, const float*, const float*, int,
-                                          cudaGraphConditionalHandle, PackArgs);
+                                          cudaGraphConditionalHandle, PackArgs, int, long);
 
 // Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
 __global__ void __launch_bounds__(128) k_init(DevState D, int init) {
@@ -569,6 +594,26 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   if (!items.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->pp_items, items.data(), sizeof(int2) * items.size(),
                              cudaMemcpyHostToDevice, s));
+  std::vector<int> alo(nsys), ahi(nsys);
+  int max_nhh = 1;
+  for (size_t k = 0; k < abit.size(); k++) max_nhh = std::max(max_nhh, ctx->h_nhh[abit[k].x]);
+  for (int k = 0; k < nsys; k++) {
+    alo[k] = (int)abit.size();
+    ahi[k] = 0;
+  }
+  for (size_t k = 0; k < abit.size(); k++) {
+    int sy = ctx->h_ch_sys[abit[k].x];
+    alo[sy] = std::min(alo[sy], (int)k);
+    ahi[sy] = std::max(ahi[sy], (int)k + 1);
+  }
+  for (int k = 0; k < nsys; k++)
+    if (ahi[k] == 0) alo[k] = 0;
+  ctx->max_nhh = max_nhh;
+  int* ad = (int*)dmalloc(ctx, sizeof(int) * 2 * nsys);
+  CUDA_TRY(cudaMemcpyAsync(ad, alo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(ad + nsys, ahi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  ctx->ab_lo_d = ad;
+  ctx->ab_hi_d = ad + nsys;
   ctx->n_ab_items = (int)abit.size();
   ctx->ab_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, abit.size()));
   if (!abit.empty())
@@ -592,6 +637,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   for (int x = 0; x < ctx->nx; x++) mx = std::max(mx, std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]));
   ctx->max_x_dim = mx;
   ctx->ctl = (LoopCtl*)dmalloc(ctx, sizeof(LoopCtl));
+  CUDA_TRY(cudaMemsetAsync(ctx->ctl, 0, sizeof(LoopCtl), s));
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
   size_t ph_smem = ph_smem_bytes(ctx, sizeof(double));
@@ -681,14 +727,18 @@ void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s) {
 // The ph term and the pp ladder do not depend on each other nor on the one-body sums: in a
 // captured update they run on two side streams next to the stats kernels.  While kernels are
 // being profiled one by one everything stays on the context stream.
+bool pnm_concurrent(const pnm_ctx* ctx) {
+  return !ctx->prof_live && !ctx->serial_sched[ctx->cur_mode];
+}
+
 void pnm_fork(pnm_ctx* ctx) {
-  if (ctx->prof_live) return;
+  if (!pnm_concurrent(ctx)) return;
   CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
   for (int k = 0; k < 2; k++) CUDA_TRY(cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0));
 }
 
 void pnm_join(pnm_ctx* ctx) {
-  if (ctx->prof_live) return;
+  if (!pnm_concurrent(ctx)) return;
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaEventRecord(ctx->ev_join[k], ctx->side[k]));
     CUDA_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[k], 0));
@@ -709,8 +759,8 @@ void pnm_enqueue_stats(pnm_ctx* ctx) {
 
 static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   DevState& D = ctx->d;
-  cudaStream_t s_ph = ctx->prof_live ? ctx->stream : ctx->side[0];
-  cudaStream_t s_pp = ctx->prof_live ? ctx->stream : ctx->side[1];
+  cudaStream_t s_ph = pnm_concurrent(ctx) ? ctx->side[0] : ctx->stream;
+  cudaStream_t s_pp = pnm_concurrent(ctx) ? ctx->side[1] : ctx->stream;
   pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH64);
@@ -725,7 +775,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
   pnm_enqueue_stats(ctx);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
-  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr});
+  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr}, 1, 0);
   prof_end(ctx);
 }
 
@@ -763,6 +813,7 @@ void prof_collect(pnm_ctx* ctx) {
 }
 
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
+  ctx->cur_mode = mode == PNM_PREC_FP64 ? 0 : 1;
   if (mode == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h);
   else pnm_enqueue_body_mixed(ctx, use_cond, h);
 }
@@ -872,4 +923,47 @@ void pnm_settle_amplitudes(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   }
   ctx->last_iters_host = it;
+}
+
+// Schedule tuning: time a few updates with the ph term and the pp ladder on side streams
+// (concurrent with the one-body kernels) and a few with everything on one stream; keep the
+// faster for this precision mode.  The held amplitudes are saved and restored.
+void pnm_tune_schedule(pnm_ctx* ctx, int mode) {
+  int m = mode == PNM_PREC_FP64 ? 0 : 1;
+  if (ctx->sched_tuned[m]) return;
+  cudaStream_t s = ctx->stream;
+  double* save = (double*)dmalloc(ctx, sizeof(double) * std::max<long>(ctx->nt, 1));
+  CUDA_TRY(cudaMemcpyAsync(save, ctx->d.t0, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> never(ctx->sys.size(), 0.0);
+  int big = 1 << 30;
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->max_iter, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_serial = 0;
+  for (int serial = 0; serial < 2; serial++) {
+    ctx->serial_sched[m] = serial != 0;
+    CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, save, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
+    pnm_start(ctx, PNM_INIT_KEEP, never);
+    if (m == 1) pnm_mixed_pack_initial(ctx);
+    pnm_enqueue_body(ctx, mode, 0, 0);
+    CUDA_TRY(cudaEventRecord(e0, s));
+    for (int k = 0; k < 4; k++) pnm_enqueue_body(ctx, mode, 0, 0);
+    CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_serial = serial;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->serial_sched[m] = best_serial != 0;
+  ctx->sched_tuned[m] = true;
+  CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, save, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
 }

@@ -28,14 +28,15 @@ namespace {
 
 constexpr int TC_M = 128;        // ab rows per tile (one TMEM lane per row)
 constexpr int TC_BK = 64;        // cd elements per k-block
-constexpr int TC_STAGES = 3;
+constexpr int TC_MAX_STAGES = 4;  // the ring depth is chosen per context by the autotuner
+constexpr int TC_MAX_SPLIT = 4;   // k-range splits of one (channel, ab tile), also autotuned
 constexpr uint32_t A_PLANE = TC_M * TC_BK * 2;  // bytes of one BF16 plane of a V tile
 constexpr uint32_t CORE_LBO = 128;              // next core matrix along K
 constexpr uint32_t CORE_SBO = (TC_BK / 8) * 128;  // next 8-row group along M/N
 
 struct TCItem {
-  int ch, mt, nkb, npad;
-  int npp, nhh, pad0, pad1;
+  int ch, mt, kb0, nkb;  // channel, ab tile, first k-block and number of k-blocks of this item
+  int npad, npp, nhh, plane;  // padded N, sizes, output plane (k-range split index)
   long voff;   // element offset of tile (mt, 0) in the V tile arena
   long boff;   // element offset of k-block 0 in the t tile arena
   long toff;   // element offset of the channel in the t layout
@@ -50,7 +51,7 @@ __device__ __forceinline__ int core_off(int r, int k) { return tile_core_off(r, 
 // V tiles of the S_z = 0 channels (setup): one CTA per (item, k-block).
 __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restrict__ v_pppp,
                          const long* __restrict__ ch_vpp_off, __nv_bfloat16* __restrict__ vt) {
-  TCItem it = items[blockIdx.x];
+  TCItem it = items[blockIdx.x];  // an unsplit item: kb0 = 0, nkb = all k-blocks
   int kb = blockIdx.y;
   if (kb >= it.nkb) return;
   const double* V = v_pppp + ch_vpp_off[it.ch];
@@ -92,12 +93,12 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
                                                   const __nv_bfloat16* __restrict__ vt,
                                                   const __nv_bfloat16* __restrict__ bt,
                                                   float* __restrict__ rpp32, LoopCtl* __restrict__ ctl,
-                                                  uint32_t stage_bytes) {
+                                                  uint32_t stage_bytes, int nst, long plane_stride) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const TCItem it = items[blockIdx.x];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
+  uint64_t* empty = full + TC_MAX_STAGES;
+  uint64_t* done = empty + TC_MAX_STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   unsigned char* stage0 = smem + 1024;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
 
   if (threadIdx.x == 0) {
     err = 0;
-    for (int s = 0; s < TC_STAGES; s++) {
+    for (int s = 0; s < nst; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -125,11 +126,11 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
 
   if (warp == 0 && lane == 0) {
     // producer: one 32 KB copy of the V tile (hi, lo) and one of the t tile per stage
-    const __nv_bfloat16* va = vt + it.voff;
-    const __nv_bfloat16* tb = bt + it.boff;
+    const __nv_bfloat16* va = vt + it.voff + (long)it.kb0 * 2 * (TC_M * TC_BK);
+    const __nv_bfloat16* tb = bt + it.boff + (long)it.kb0 * 2 * (it.npad * TC_BK);
     int issued = 0;
     for (int kb = 0; kb < it.nkb; kb++) {
-      int s = kb % TC_STAGES, use = kb / TC_STAGES;
+      int s = kb % nst, use = kb / nst;
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
         err = 1;
         break;
@@ -141,13 +142,13 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
       issued = kb + 1;
     }
     // every copy this thread started has landed before the CTA may retire
-    for (int kb = max(0, issued - TC_STAGES); kb < issued; kb++)
-      if (!mbar_wait(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1)) err = 1;
+    for (int kb = max(0, issued - nst); kb < issued; kb++)
+      if (!mbar_wait(&full[kb % nst], (kb / nst) & 1)) err = 1;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     const uint32_t idesc = idesc_bf16(TC_M, it.npad);
     for (int kb = 0; kb < it.nkb; kb++) {
-      int s = kb % TC_STAGES, use = kb / TC_STAGES;
+      int s = kb % nst, use = kb / nst;
       if (!mbar_wait(&full[s], use & 1)) {
         err = 1;
         break;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
 #pragma unroll
       for (int j = 0; j < 16; j++) {
         int ij = c0 + j;
-        if (ij < it.nhh) rpp32[it.toff + (long)ij * it.npp + ab] = __uint_as_float(r[j]);
+        if (ij < it.nhh) rpp32[it.plane * plane_stride + it.toff + (long)ij * it.npp + ab] = __uint_as_float(r[j]);
       }
     }
   }
@@ -224,7 +225,26 @@ struct MixedState {
   int* ch_npad = nullptr;
   uint32_t stage_bytes = 0;
   size_t smem = 0;
+  int nst = 3, ksplit = 1;  // chosen by the autotuner
+  float tuned_us = 0.0f;
 };
+
+// Items of the tensor-core ladder for one k-range split factor: each (channel, ab tile)
+// becomes up to `split` items over consecutive k-block ranges (never empty).
+static std::vector<TCItem> split_items(const std::vector<TCItem>& base, int split) {
+  std::vector<TCItem> out;
+  for (const TCItem& b : base) {
+    int parts = std::min(split, b.nkb);
+    for (int p = 0; p < parts; p++) {
+      TCItem t = b;
+      t.kb0 = (int)((long)b.nkb * p / parts);
+      t.nkb = (int)((long)b.nkb * (p + 1) / parts) - t.kb0;
+      t.plane = p;
+      out.push_back(t);
+    }
+  }
+  return out;
+}
 
 void pnm_prepare_mixed(pnm_ctx* ctx) {
   if (ctx->mixed) return;
@@ -251,6 +271,8 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
         TCItem t{};
         t.ch = c;
         t.mt = mt;
+        t.kb0 = 0;
+        t.plane = 0;
         t.nkb = nkb;
         t.npad = npad;
         t.npp = npp;
@@ -271,7 +293,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     M->npk = (int)pk.size();
     M->vt = mdalloc<__nv_bfloat16>(ctx, voff);
     M->bt = mdalloc<__nv_bfloat16>(ctx, boff);
-    M->items = mdalloc<TCItem>(ctx, items.size());
+    M->items = mdalloc<TCItem>(ctx, split_items(items, TC_MAX_SPLIT).size());
     M->pk = mdalloc<int4>(ctx, pk.size());
     M->pk_boff = mdalloc<long>(ctx, pk_boff.size());
     if (!items.empty())
@@ -287,7 +309,9 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpyAsync(M->ch_npad, ch_npad.data(), sizeof(int) * ctx->nch, cudaMemcpyHostToDevice, s));
     // padding rows/columns of the t tiles are never written again: they stay zero
     CUDA_TRY(cudaMemsetAsync(M->bt, 0, sizeof(__nv_bfloat16) * std::max<long>(boff, 1), s));
-    M->rpp32 = mdalloc<float>(ctx, ctx->nt);
+    M->rpp32 = mdalloc<float>(ctx, (size_t)TC_MAX_SPLIT * ctx->nt);
+    // planes a channel with fewer k-blocks than the split never writes stay zero
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
     M->xw32 = mdalloc<float>(ctx, ctx->nxt);
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
     M->xq32 = mdalloc<float>(ctx, ctx->nxt);
@@ -299,9 +323,57 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       k_pack_v<<<dim3(M->nitems, max_nkb), 256, 0, s>>>(M->items, ctx->d.v_pppp, ctx->d.ch_vpp_off, M->vt);
     CUDA_TRY(cudaGetLastError());
     M->stage_bytes = (2 * A_PLANE + 2 * (uint32_t)max_npad * TC_BK * 2 + 1023) / 1024 * 1024;
-    M->smem = 1024 + (size_t)TC_STAGES * M->stage_bytes + 8192;  // tail guard
-    if (M->smem > 227 * 1024) throw PnmError{PNM_EINVAL, "tensor-core stage ring exceeds shared memory"};
-    CUDA_TRY(cudaFuncSetAttribute(k_pp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M->smem));
+    auto smem_for = [&](int nst) { return 1024 + (size_t)nst * M->stage_bytes + 8192; };  // tail guard
+    if (smem_for(2) > 227 * 1024) throw PnmError{PNM_EINVAL, "tensor-core stage ring exceeds shared memory"};
+    int max_st = TC_MAX_STAGES;
+    while (smem_for(max_st) > 227 * 1024) max_st--;
+    CUDA_TRY(cudaFuncSetAttribute(k_pp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(max_st)));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    // Autotuner: time every (k-range split, ring depth) on this context's channels and keep
+    // the fastest.  The ladder's cost does not depend on the amplitude values.
+    CUDA_TRY(cudaMemsetAsync(&ctx->ctl->dev_error, 0, sizeof(int), s));
+    float best = 1e30f;
+    std::vector<TCItem> best_items = items;
+    TCItem* trial = mdalloc<TCItem>(ctx, split_items(items, TC_MAX_SPLIT).size());
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    for (int split : {1, 2, 4}) {
+      std::vector<TCItem> its = split_items(items, split);
+      if (its.empty()) break;
+      CUDA_TRY(cudaMemcpyAsync(trial, its.data(), sizeof(TCItem) * its.size(), cudaMemcpyHostToDevice, s));
+      for (int nst = 2; nst <= max_st; nst++) {
+        for (int w = 0; w < 2; w++)
+          k_pp_tc<<<(int)its.size(), 128, smem_for(nst), s>>>(trial, M->vt, M->bt, M->rpp32, ctx->ctl,
+                                                               M->stage_bytes, nst, ctx->nt);
+        CUDA_TRY(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 5; rep++)
+          k_pp_tc<<<(int)its.size(), 128, smem_for(nst), s>>>(trial, M->vt, M->bt, M->rpp32, ctx->ctl,
+                                                               M->stage_bytes, nst, ctx->nt);
+        CUDA_TRY(cudaEventRecord(e1, s));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          best_items = its;
+          M->nst = nst;
+          M->ksplit = split;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(cudaGetLastError());
+    int dev_err = 0;
+    CUDA_TRY(cudaMemcpy(&dev_err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget while tuning"};
+    M->tuned_us = best / 5 * 1000.0f;
+    M->smem = smem_for(M->nst);
+    M->nitems = (int)best_items.size();
+    CUDA_TRY(cudaMemcpyAsync(M->items, best_items.data(), sizeof(TCItem) * best_items.size(),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
     CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
     delete M;
@@ -312,8 +384,8 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
 
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   MixedState* M = ctx->mixed;
-  cudaStream_t s_ph = ctx->prof_live ? ctx->stream : ctx->side[0];
-  cudaStream_t s_pp = ctx->prof_live ? ctx->stream : ctx->side[1];
+  cudaStream_t s_ph = pnm_concurrent(ctx) ? ctx->side[0] : ctx->stream;
+  cudaStream_t s_pp = pnm_concurrent(ctx) ? ctx->side[1] : ctx->stream;
   pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH32);
@@ -322,14 +394,16 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
   }
   if (M->nitems > 0) {
     prof_begin(ctx, KID_PP_TC);
-    k_pp_tc<<<M->nitems, 128, M->smem, s_pp>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
+    k_pp_tc<<<M->nitems, 128, M->smem, s_pp>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes,
+                                                M->nst, ctx->nt);
     prof_end(ctx);
   }
   pnm_enqueue_stats(ctx);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
   // the update also writes the BF16 hi/lo tiles of the new amplitudes for the next ladder
-  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->ch_boff, M->ch_npad});
+  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->ch_boff, M->ch_npad},
+                              M->ksplit, ctx->nt);
   prof_end(ctx);
 }
 
@@ -342,6 +416,16 @@ void pnm_mixed_pack_initial(pnm_ctx* ctx) {
     prof_end(ctx);
   }
   CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask) {
+  if (serial_mask)
+    *serial_mask = (ctx->sched_tuned[0] ? (ctx->serial_sched[0] ? 1 : 0) : 4) |
+                   (ctx->sched_tuned[1] ? (ctx->serial_sched[1] ? 2 : 0) : 8);
+  if (!ctx->mixed) throw PnmError{PNM_EINVAL, "the mixed-precision path has not been prepared"};
+  if (ksplit) *ksplit = ctx->mixed->ksplit;
+  if (stages) *stages = ctx->mixed->nst;
+  if (us) *us = ctx->mixed->tuned_us;
 }
 
 void pnm_free_mixed(pnm_ctx* ctx) {
@@ -364,15 +448,20 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   std::vector<double> out(ctx->nt, 0.0);
   if (precision == PNM_PREC_BF16X3) {
     MixedState* M = ctx->mixed;
-    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * ctx->nt, s));
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * ctx->nt, s));
     if (M->npk > 0) k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
     if (M->nitems > 0)
-      k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes);
+      k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes,
+                                              M->nst, ctx->nt);
     CUDA_TRY(cudaGetLastError());
-    std::vector<float> f(ctx->nt);
-    CUDA_TRY(cudaMemcpyAsync(f.data(), M->rpp32, sizeof(float) * ctx->nt, cudaMemcpyDeviceToHost, s));
+    std::vector<float> f((size_t)TC_MAX_SPLIT * ctx->nt);
+    CUDA_TRY(cudaMemcpyAsync(f.data(), M->rpp32, sizeof(float) * f.size(), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    for (long z = 0; z < ctx->nt; z++) out[z] = f[z];
+    for (long z = 0; z < ctx->nt; z++) {
+      float acc = 0.0f;
+      for (int p = 0; p < M->ksplit; p++) acc += f[(size_t)p * ctx->nt + z];
+      out[z] = acc;
+    }
   } else {
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * ctx->nt, s));
     pnm_launch_pp64(ctx, s);

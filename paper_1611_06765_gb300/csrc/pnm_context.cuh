@@ -38,7 +38,9 @@ struct pnm_ctx {
   int n_pp_items = 0;
   int4* upd_items = nullptr;  // (channel, ij, first pp column) of the update
   int n_upd_items = 0;
-  int *upd_lo_d = nullptr, *upd_hi_d = nullptr;  // per system update-item ranges
+  int *upd_lo_d = nullptr, *upd_hi_d = nullptr;  // per system ranges of the (row, column) items
+  int *ab_lo_d = nullptr, *ab_hi_d = nullptr;    // per system ranges of the column items
+  int max_nhh = 1;
   int2* ab_items = nullptr;
   int n_ab_items = 0;
 
@@ -64,6 +66,9 @@ struct pnm_ctx {
   // side streams for the independent parts of an update (ph term, pp ladder), joined by events
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  bool serial_sched[2] = {false, false};  // per mode (0 FP64, 1 mixed): one stream only
+  bool sched_tuned[2] = {false, false};
+  int cur_mode = 0;
 
   // per-kernel CUDA-event profiling of host-driven solves (never active during capture)
   bool prof_on = false, prof_live = false;
@@ -109,4 +114,7 @@ template <typename T_>
 void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s);
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h, PackArgs pk);
+                   cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride);
+void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask);
+bool pnm_concurrent(const pnm_ctx* ctx);
+void pnm_tune_schedule(pnm_ctx* ctx, int mode);

@@ -50,6 +50,8 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   }
   bool mixed = o.precision != PNM_PREC_FP64;
   if (mixed) pnm_prepare_mixed(ctx);
+  pnm_tune_schedule(ctx, PNM_PREC_FP64);
+  if (mixed) pnm_tune_schedule(ctx, PNM_PREC_BF16X3);
 
   cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
   CUDA_TRY(cudaEventRecord(e0, s));
