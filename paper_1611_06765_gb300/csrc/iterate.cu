@@ -16,6 +16,9 @@
 //              device-side loop condition
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <type_traits>
 
 #include "pnm_context.cuh"
 
@@ -381,7 +384,6 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   long base = D.ch_t_off[c];
   long row = base + (long)ij * npp;
   int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-  double ei = D.eps[h.x], ej = D.eps[h.y];
   double di = D.dchi[h.x], dj = D.dchi[h.y];
   const double* chi = D.chi_hh + D.ch_vhh_off[c] + ij;  // chi[kl * nh]
   double esum = 0.0, rsum = 0.0;
@@ -392,22 +394,39 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
     double v = D.v_pphh[z];
     if (!frozen) {
       int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
-      double num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
-      if (szero)
-        for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
-      double hh = 0.0;
-      for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
-      num += hh;
-      int4 q = D.qmap[z];
-      double ph = 0.0;
-      if (q.x >= 0) ph += (double)xq[q.x];
-      if (q.y >= 0) ph -= (double)xq[q.y];
-      if (q.z >= 0) ph -= (double)xq[q.z];
-      if (q.w >= 0) ph += (double)xq[q.w];
-      num += ph;
-      double den = ei + ej - D.eps[p.x] - D.eps[p.y];
-      double tnew = num / den;
-      double R = num - den * tz;
+      double num;
+      if constexpr (std::is_same<QT, float>::value) {
+        // mixed precision: the correction terms (one-body, ladders, ph) in FP32; the
+        // denominator, the Jacobi step, mixing, energy and residual stay FP64
+        float corr = (float)(D.dchi[p.x] + D.dchi[p.y] - di - dj) * (float)tz;
+        if (szero)
+          for (int pl = 0; pl < nplanes; pl++) corr += (float)rpp[pl * pstride + z];
+        for (int kl = 0; kl < nh; kl++)
+          corr = fmaf((float)t[base + (long)kl * npp + ab], (float)chi[(long)kl * nh], corr);
+        int4 q = D.qmap[z];
+        if (q.x >= 0) corr += (float)xq[q.x];
+        if (q.y >= 0) corr -= (float)xq[q.y];
+        if (q.z >= 0) corr -= (float)xq[q.z];
+        if (q.w >= 0) corr += (float)xq[q.w];
+        num = v + (double)corr;
+      } else {
+        num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
+        if (szero)
+          for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
+        double hh = 0.0;
+        for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
+        num += hh;
+        int4 q = D.qmap[z];
+        double ph = 0.0;
+        if (q.x >= 0) ph += (double)xq[q.x];
+        if (q.y >= 0) ph -= (double)xq[q.y];
+        if (q.z >= 0) ph -= (double)xq[q.z];
+        if (q.w >= 0) ph += (double)xq[q.w];
+        num += ph;
+      }
+      // eps_ij^ab and its reciprocal are fixed per context (no divide per iteration)
+      double tnew = num * D.inv_den[z];
+      double R = num - D.den[z] * tz;
       rsum += R * R;
       out = alpha * tnew + (1.0 - alpha) * tz;
     }
@@ -928,9 +947,22 @@ void pnm_settle_amplitudes(pnm_ctx* ctx) {
 // Schedule tuning: time a few updates with the ph term and the pp ladder on side streams
 // (concurrent with the one-body kernels) and a few with everything on one stream; keep the
 // faster for this precision mode.  The held amplitudes are saved and restored.
+static std::mutex g_sched_mu;
+static std::map<std::string, bool> g_sched_cache;  // (shape key, mode) -> one stream
+
 void pnm_tune_schedule(pnm_ctx* ctx, int mode) {
   int m = mode == PNM_PREC_FP64 ? 0 : 1;
   if (ctx->sched_tuned[m]) return;
+  const std::string key = pnm_shape_key(ctx) + (m ? "|mixed" : "|fp64");
+  {
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    auto f = g_sched_cache.find(key);
+    if (f != g_sched_cache.end()) {
+      ctx->serial_sched[m] = f->second;
+      ctx->sched_tuned[m] = true;
+      return;
+    }
+  }
   cudaStream_t s = ctx->stream;
   double* save = (double*)dmalloc(ctx, sizeof(double) * std::max<long>(ctx->nt, 1));
   CUDA_TRY(cudaMemcpyAsync(save, ctx->d.t0, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
@@ -963,6 +995,10 @@ void pnm_tune_schedule(pnm_ctx* ctx, int mode) {
   cudaEventDestroy(e1);
   ctx->serial_sched[m] = best_serial != 0;
   ctx->sched_tuned[m] = true;
+  {
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    g_sched_cache[key] = ctx->serial_sched[m];
+  }
   CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, save, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));

@@ -20,6 +20,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "pnm_context.cuh"
 #include "tc_ptx.cuh"
@@ -246,6 +249,10 @@ static std::vector<TCItem> split_items(const std::vector<TCItem>& base, int spli
   return out;
 }
 
+// Tile choices already measured in this process, per channel-size signature.
+static std::mutex g_tile_mu;
+static std::map<std::string, std::tuple<int, int, float>> g_tile_cache;
+
 void pnm_prepare_mixed(pnm_ctx* ctx) {
   if (ctx->mixed) return;
   cudaStream_t s = ctx->stream;
@@ -334,11 +341,25 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemsetAsync(&ctx->ctl->dev_error, 0, sizeof(int), s));
     float best = 1e30f;
     std::vector<TCItem> best_items = items;
+    const std::string key = pnm_shape_key(ctx);
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tile_mu);
+      auto f = g_tile_cache.find(key);
+      if (f != g_tile_cache.end()) {
+        M->ksplit = std::get<0>(f->second);
+        M->nst = std::min(std::get<1>(f->second), max_st);
+        best = std::get<2>(f->second) * 5 / 1000.0f;
+        best_items = split_items(items, M->ksplit);
+        cached = true;
+      }
+    }
     TCItem* trial = mdalloc<TCItem>(ctx, split_items(items, TC_MAX_SPLIT).size());
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     for (int split : {1, 2, 4}) {
+      if (cached) break;
       std::vector<TCItem> its = split_items(items, split);
       if (its.empty()) break;
       CUDA_TRY(cudaMemcpyAsync(trial, its.data(), sizeof(TCItem) * its.size(), cudaMemcpyHostToDevice, s));
@@ -369,6 +390,10 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpy(&dev_err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
     if (dev_err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget while tuning"};
     M->tuned_us = best / 5 * 1000.0f;
+    if (!cached) {
+      std::lock_guard<std::mutex> lock(g_tile_mu);
+      g_tile_cache[key] = std::make_tuple(M->ksplit, M->nst, M->tuned_us);
+    }
     M->smem = smem_for(M->nst);
     M->nitems = (int)best_items.size();
     CUDA_TRY(cudaMemcpyAsync(M->items, best_items.data(), sizeof(TCItem) * best_items.size(),

@@ -82,6 +82,16 @@ struct pnm_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// Autotuner cache key: device and the (N, n2max) of every system, which fix all channel
+// sizes (the density only rescales values).
+inline std::string pnm_shape_key(const pnm_ctx* ctx) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string k = "dev" + std::to_string(dev);
+  for (const SysInfo& S : ctx->sys) k += ";" + std::to_string(S.N) + "," + std::to_string(S.n2max);
+  return k;
+}
+
 void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
                const pnm_minnesota& P);
 void pnm_prepare_iteration(pnm_ctx* ctx);

@@ -75,6 +75,7 @@ struct DevState {
   int *occ_off, *occ_idx; // per state: pair indices (pp for particles, hh for holes)
   // blocks
   double *v_pphh, *v_pppp, *v_hhhh, *x_v1, *x_w;
+  double *den, *inv_den;  // eps_i + eps_j - eps_a - eps_b per amplitude, and its reciprocal
   // iteration state
   double *t0, *t1;       // double buffer, parity = iteration & 1
   double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;

@@ -413,6 +413,26 @@ __global__ void k_v_pphh(int row0, const int2* __restrict__ row_item,
   }
 }
 
+// Denominators eps_ij^ab = e_i + e_j - e_a - e_b (HF energies) and their reciprocals.
+__global__ void k_den(int row0, const int2* __restrict__ row_item, const int* __restrict__ ch_hh_off,
+                      const int* __restrict__ ch_pp_off, const int* __restrict__ ch_npp,
+                      const long* __restrict__ ch_t_off, const int2* __restrict__ hh_pair,
+                      const int2* __restrict__ pp_pair, const double* __restrict__ eps,
+                      double* __restrict__ den, double* __restrict__ inv_den) {
+  int2 it = row_item[row0 + blockIdx.x];
+  int c = it.x, ij = it.y;
+  int2 h = hh_pair[ch_hh_off[c] + ij];
+  double eij = eps[h.x] + eps[h.y];
+  int npp = ch_npp[c];
+  long base = ch_t_off[c] + (long)ij * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 pb = pp_pair[ch_pp_off[c] + ab];
+    double d = eij - eps[pb.x] - eps[pb.y];
+    den[base + ab] = d;
+    inv_den[base + ab] = 1.0 / d;
+  }
+}
+
 // <ab|v|cd> for S_z = 0 channels; one CTA per (channel, row cd).
 __global__ void k_v_pppp(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
                          const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
@@ -739,6 +759,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   D.xmap = dalloc<int>(xt_acc, ctx->owned);
   D.qmap = dalloc<int4>(t_acc, ctx->owned);
   D.v_pphh = dalloc<double>(t_acc, ctx->owned);
+  D.den = dalloc<double>(t_acc, ctx->owned);
+  D.inv_den = dalloc<double>(t_acc, ctx->owned);
   D.v_pppp = dalloc<double>(vpp_acc, ctx->owned);
   D.v_hhhh = dalloc<double>(vhh_acc, ctx->owned);
   D.x_v1 = dalloc<double>(xc_acc, ctx->owned);
@@ -794,6 +816,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       k_v_pphh<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
                                      D.ch_t_off, D.hh_pair, D.pp_pair, D.nvec, D.lut + S.lut_off,
                                      D.v_pphh);
+      k_den<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp, D.ch_t_off,
+                                  D.hh_pair, D.pp_pair, D.eps, D.den, D.inv_den);
     }
     if (nchs > 0)
       k_v_hhhh<<<nchs, 128, 0, s>>>(S.ch_begin, D.ch_hh_off, D.ch_nhh, D.ch_vhh_off, D.hh_pair,
