@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
       if (lane == 0) {
         long e = D.ch_vhh_off[c] + (long)kl * nh + ij;
         D.chi_hh[e] = D.v_hhhh[e] + acc;
+        if (D.chi32) D.chi32[e] = (float)(D.v_hhhh[e] + acc);
       }
     }
   } else {
@@ -118,18 +119,33 @@ __global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restric
   T_* Xt = Ts + P4 * H4;
   T_* Cs = Xt + P4 * H4;
   long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  // T[(a,i)][(k,c)] = t_ik^ac through the signed index map; W transposed into Xt
-  for (int e = threadIdx.x; e < P4 * H4; e += blockDim.x) {
-    int u = e / H4, s = e % H4;
-    T_ tv = 0, wv = 0;
-    if (u < nph && s < nhp) {
-      int code = D.xmap[to + (long)u * nhp + s];
-      if (code > 0) tv = (T_)t[code - 1];
-      else if (code < 0) tv = -(T_)t[-code - 1];
-      wv = xw[wo + (long)s * nph + u];
+  // T[(a,i)][(k,c)] = t_ik^ac through the signed index map; W transposed into Xt.
+  // Four elements per thread per step so that four independent gathers are in flight.
+  const bool f32 = std::is_same<T_, float>::value && D.t32_0 != nullptr;
+  const float* __restrict__ t32 = f32 ? cur_t32(D, ctl) : nullptr;
+  for (int e0 = threadIdx.x; e0 < P4 * H4; e0 += 4 * blockDim.x) {
+    int code[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int e = e0 + q * blockDim.x;
+      int u = e / H4, s = e % H4;
+      code[q] = (e < P4 * H4 && u < nph && s < nhp) ? D.xmap[to + (long)u * nhp + s] : 0;
     }
-    Ts[e] = tv;
-    Xt[e] = wv;  // Xt[u][s] = W[s][u]
+    T_ tv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int cd = code[q], a = cd > 0 ? cd - 1 : -cd - 1;
+      T_ g = cd == 0 ? (T_)0 : (f32 ? (T_)t32[a] : (T_)t[a]);
+      tv[q] = cd < 0 ? -g : g;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int e = e0 + q * blockDim.x;
+      if (e >= P4 * H4) continue;
+      int u = e / H4, s = e % H4;
+      Ts[e] = tv[q];
+      Xt[e] = (u < nph && s < nhp) ? xw[wo + (long)u * nhp + s] : (T_)0;  // W^T[u][s] = W[s][u]
+    }
   }
   __syncthreads();
   // Small channels: one output per thread (more threads busy, shorter chains); large
@@ -401,8 +417,14 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
         float corr = (float)(D.dchi[p.x] + D.dchi[p.y] - di - dj) * (float)tz;
         if (szero)
           for (int pl = 0; pl < nplanes; pl++) corr += (float)rpp[pl * pstride + z];
-        for (int kl = 0; kl < nh; kl++)
-          corr = fmaf((float)t[base + (long)kl * npp + ab], (float)chi[(long)kl * nh], corr);
+        if (D.t32_0) {
+          const float* t32 = cur_t32(D, ctl);
+          const float* chi32 = D.chi32 + D.ch_vhh_off[c] + ij;
+          for (int kl = 0; kl < nh; kl++) corr = fmaf(t32[base + (long)kl * npp + ab], chi32[(long)kl * nh], corr);
+        } else {
+          for (int kl = 0; kl < nh; kl++)
+            corr = fmaf((float)t[base + (long)kl * npp + ab], (float)chi[(long)kl * nh], corr);
+        }
         int4 q = D.qmap[z];
         if (q.x >= 0) corr += (float)xq[q.x];
         if (q.y >= 0) corr -= (float)xq[q.y];
@@ -431,6 +453,7 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
       out = alpha * tnew + (1.0 - alpha) * tz;
     }
     tn[z] = out;
+    if (std::is_same<QT, float>::value && D.t32_0) next_t32(D, ctl)[z] = (float)out;
     esum += v * out;
     if (pk.bt && szero) {
       // BF16 hi/lo copy of the new amplitude for the next tensor-core pp ladder

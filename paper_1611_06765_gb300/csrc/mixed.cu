@@ -197,6 +197,14 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
   if (threadIdx.x == 0 && (err || !ok)) atomicExch(&ctl->dev_error, 1);
 }
 
+// FP32 copy of the current amplitudes.
+__global__ void k_to_float_cur(DevState D, const LoopCtl* __restrict__ ctl, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float* dst = (ctl->iter & 1) ? D.t32_1 : D.t32_0;
+  dst[i] = (float)cur_t(D, ctl)[i];
+}
+
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -316,6 +324,9 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpyAsync(M->ch_npad, ch_npad.data(), sizeof(int) * ctx->nch, cudaMemcpyHostToDevice, s));
     // padding rows/columns of the t tiles are never written again: they stay zero
     CUDA_TRY(cudaMemsetAsync(M->bt, 0, sizeof(__nv_bfloat16) * std::max<long>(boff, 1), s));
+    ctx->d.t32_0 = mdalloc<float>(ctx, ctx->nt);
+    ctx->d.t32_1 = mdalloc<float>(ctx, ctx->nt);
+    ctx->d.chi32 = mdalloc<float>(ctx, ctx->nvhh);
     M->rpp32 = mdalloc<float>(ctx, (size_t)TC_MAX_SPLIT * ctx->nt);
     // planes a channel with fewer k-blocks than the split never writes stay zero
     CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
@@ -432,9 +443,11 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
   prof_end(ctx);
 }
 
-// BF16 tiles of the start amplitudes (before the first mixed update).
+// BF16 tiles and the FP32 copy of the start amplitudes (before the first mixed update).
 void pnm_mixed_pack_initial(pnm_ctx* ctx) {
   MixedState* M = ctx->mixed;
+  if (ctx->nt > 0)
+    k_to_float_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
   if (M->npk > 0) {
     prof_begin(ctx, KID_PACK);
     k_pack_t<<<M->npk, 256, 0, ctx->stream>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);

@@ -10,7 +10,7 @@
 //                symmetric, row-major at vpp_off[c].
 //   cross chans  per channel x: n_ph rows (a,i), n_hp columns (k,c); T_x/Q_x are
 //                n_ph x n_hp at xt_off[x]; V1_x (<kb|v|cj>) n_hp x n_hp at xc_off[x];
-//                W_x (<kl|v|ce>) n_hp x n_ph at xw_off[x].
+//                W_x (<kl|v|ce>, n_hp x n_ph) stored transposed (n_ph x n_hp) at xw_off[x].
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -78,6 +78,8 @@ struct DevState {
   double *den, *inv_den;  // eps_i + eps_j - eps_a - eps_b per amplitude, and its reciprocal
   // iteration state
   double *t0, *t1;       // double buffer, parity = iteration & 1
+  float *t32_0, *t32_1;  // FP32 copies of t0/t1 kept by the mixed-precision update (else null)
+  float* chi32;          // FP32 copy of chi_hh written by the stats kernel when t32 is used
   double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;
   double *eparts, *rparts;
 };
@@ -140,6 +142,12 @@ __device__ __forceinline__ const double* cur_t(const DevState& D, const LoopCtl*
 }
 __device__ __forceinline__ double* next_t(const DevState& D, const LoopCtl* ctl) {
   return (ctl->iter & 1) ? D.t0 : D.t1;
+}
+__device__ __forceinline__ const float* cur_t32(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t32_1 : D.t32_0;
+}
+__device__ __forceinline__ float* next_t32(const DevState& D, const LoopCtl* ctl) {
+  return (ctl->iter & 1) ? D.t32_0 : D.t32_1;
 }
 
 // Antisymmetrized Minnesota element for two neutrons.  With P_tau = 1 the exchange form

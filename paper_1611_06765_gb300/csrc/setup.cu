@@ -463,7 +463,7 @@ __global__ void k_v_hhhh(int c0, const int* __restrict__ ch_hh_off,
   }
 }
 
-// V1_x[(k,c)][(j,b)] = <kb|v|cj>,  W_x[(k,c)][(e,l)] = <kl|v|ce>.
+// V1_x[(k,c)][(j,b)] = <kb|v|cj>,  W_x[(k,c)][(e,l)] = <kl|v|ce> (stored as W_x^T).
 __global__ void k_v_cross(int x0, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
                           const long* __restrict__ x_c_off, const long* __restrict__ x_w_off,
                           const int* __restrict__ x_ph_off, const int* __restrict__ x_hp_off,
@@ -476,8 +476,9 @@ __global__ void k_v_cross(int x0, const int* __restrict__ x_nph, const int* __re
     int2 kc = hp_pair[x_hp_off[x] + e / nhp], jb = hp_pair[x_hp_off[x] + e % nhp];
     x_v1[x_c_off[x] + e] = v_minnesota_as(nvec[kc.x], nvec[jb.y], nvec[kc.y], nvec[jb.x], lut);
   }
-  for (int e = threadIdx.x; e < nhp * nph; e += blockDim.x) {
-    int2 kc = hp_pair[x_hp_off[x] + e / nph], el = ph_pair[x_ph_off[x] + e % nph];
+  // stored transposed, W^T[(e,l)][(k,c)], so the ph kernel stages it with coalesced loads
+  for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+    int2 el = ph_pair[x_ph_off[x] + e / nhp], kc = hp_pair[x_hp_off[x] + e % nhp];
     x_w[x_w_off[x] + e] = v_minnesota_as(nvec[kc.x], nvec[el.y], nvec[kc.y], nvec[el.x], lut);
   }
 }
