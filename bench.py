@@ -106,6 +106,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value, dist, device="cpu"):
+    """Largest value over all ranks (the slowest rank sets the job time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -340,9 +348,7 @@ def run_ours(a):
         wall = time.perf_counter() - wall0
     ms = statistics.mean(step_ms)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, device="cuda")
     tim = ctx.timings()
 
     # e2e through the public API from host inputs

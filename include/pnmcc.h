@@ -244,6 +244,11 @@ int pnm_kernel_stats(const pnm_ctx *ctx, int id, const char **name, double *tota
  * mixed-precision solve. */
 int pnm_get_tuning(const pnm_ctx *ctx, int *ksplit, int *stages, float *us, int *serial_mask);
 
+/* Failure-path self test (not from the paper): a one-thread kernel waits, with the bounded
+ * wait the tensor-core kernels use, on an mbarrier nothing arrives on.  Expected result:
+ * PNM_ETIMEOUT after about a second, the context still usable.  Nothing traps or hangs. */
+int pnm_selftest_timeout(pnm_ctx *ctx);
+
 /* Thread-local text describing the last failure of a pnm_* call on this thread. */
 const char *pnm_last_error(void);
 

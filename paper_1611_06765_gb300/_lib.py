@@ -31,7 +31,7 @@ EXPORTS = (
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_mlp_num_params", "pnm_mlp_init",
-    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_last_error",
+    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout", "pnm_last_error",
 )
 
 
@@ -96,6 +96,7 @@ def load(path=None):
     L.pnm_mlp_forward.argtypes = [fp, fp, C.c_long, fp, C.c_int, vp]
     L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, vp]
     L.pnm_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_float), ip]
+    L.pnm_selftest_timeout.argtypes = [vp]
     L.pnm_set_profiling.argtypes = [vp, C.c_int]
     L.pnm_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), dp, ip]
     L.pnm_last_error.restype = C.c_char_p

@@ -362,6 +362,14 @@ int pnm_get_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int*
   });
 }
 
+int pnm_selftest_timeout(pnm_ctx* ctx) {
+  return guarded([&]() {
+    if (!ctx) throw PnmError{PNM_EINVAL, "null context"};
+    pnm_selftest_wait(ctx);
+    return PNM_OK;
+  });
+}
+
 int pnm_set_profiling(pnm_ctx* ctx, int on) {
   return guarded([&]() {
     if (!ctx) throw PnmError{PNM_EINVAL, "null context"};

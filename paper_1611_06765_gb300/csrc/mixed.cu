@@ -515,3 +515,28 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     for (long z = 0; z < len; z++) r[o - S.t_begin + z] = ctx->h_szero[c] ? out[o + z] : 0.0;
   }
 }
+
+// Failure-path self test: one thread waits, with the bounded wait of the tensor-core
+// kernels, on an mbarrier that nothing ever arrives on.  The wait gives up, the kernel
+// records the failure in the context's device flag and returns; nothing traps or hangs.
+__global__ void k_wait_selftest(LoopCtl* __restrict__ ctl) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicExch(&ctl->dev_error, 1);
+}
+
+void pnm_selftest_wait(pnm_ctx* ctx) {
+  int zero = 0, err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->ctl);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (err) throw PnmError{PNM_ETIMEOUT, "device-side wait ran out of its budget (self test)"};
+}

@@ -128,3 +128,4 @@ void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
 void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask);
 bool pnm_concurrent(const pnm_ctx* ctx);
 void pnm_tune_schedule(pnm_ctx* ctx, int mode);
+void pnm_selftest_wait(pnm_ctx* ctx);
