@@ -1,16 +1,25 @@
 #!/usr/bin/env python
 """Time-to-converge of coupled-cluster doubles for pure neutron matter on one GB300.
 
-A step is one complete CCD solve (MBPT2 start, updates until |dE^(n+1) - dE^(n)| / N <
-1e-6 MeV) of the workload N = 14 neutrons, rho = 0.08 fm^-3, plane waves with n^2 <= 20
-(778 states), Minnesota interaction, mixing alpha = 0.5.  The channel tables and the
-interaction blocks are resident in HBM before the timed region (built by the context); the
-timed region covers the solve.  ``e2e`` repeats the measurement through the public API
-from host inputs: context creation (basis, channels and V built on the GPU), solve, and the
-converged amplitudes copied back to the host.
+Metric: device time for the CCD iteration to reach |dE^(n+1) - dE^(n)| / N < 1e-6 MeV.
 
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the only reference
-implementation of this method) on the same workload and metric.
+Default workload, the one the metric's "mixed + learned" is defined on: N = 66 neutrons,
+plane waves with n^2 <= 36 (1850 states), Minnesota interaction, mixing 0.5, at the three
+held-out densities rho = 0.05, 0.11, 0.17 fm^-3, solved together in one batched context
+(every kernel launch covers the three systems).  A step is one converged solve of that batch
+from the learned start (feature kernel + tensor-core inference inside the timed region), the
+pp ladder in BF16x3 on the tensor cores, FP64 denominators / residual / energies, and two
+FP64 refinement sweeps at the end.  The network is trained before timing, by the library's
+own GPU kernels, on amplitudes the solver converges for N = 14 (n^2 <= 20, 16 densities
+0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16).  Channel tables, interaction blocks and
+the model are resident in HBM before the timed region; L2 is flushed before every step.
+
+``e2e`` times the public API from host inputs: context creation (basis, channels and V built
+on the GPU), model upload, solve, converged amplitudes copied back.  ``comparison`` holds the
+same batch from the MBPT2 start (mixed and FP64) and the other configurations, each with its
+dE/N error against the FP64 oracle.  ``--impl reference`` times the FP64 CPU oracle.
+
+Prints one JSON line.
 """
 import argparse
 import json
@@ -25,13 +34,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PNM CCD time-to-converge (ΔE/N<1e-6 MeV), mixed+learned vs FP64, one GB300"
+HELDOUT = (0.05, 0.11, 0.17)
+SWEEP16 = tuple(round(0.02 * k, 2) for k in range(1, 17))
 WORKLOADS = {
-    # name: (N, rho, n2max)
-    "pnm_N14_rho0.08_n2max20": (14, 0.08, 20),
-    "pnm_N14_rho0.08_n2max4": (14, 0.08, 4),
-    "pnm_N66_rho0.16_n2max36": (66, 0.16, 36),
+    # name: (N, densities, n2max, start, precision)
+    "pnm_N66_n2max36_heldout3_learned_bf16x3": (66, HELDOUT, 36, "mlp", "bf16x3"),
+    "pnm_N66_n2max36_heldout3_mbpt2_bf16x3": (66, HELDOUT, 36, "mbpt2", "bf16x3"),
+    "pnm_N66_n2max36_heldout3_mbpt2_fp64": (66, HELDOUT, 36, "mbpt2", "fp64"),
+    "pnm_N14_rho0.08_n2max20_bf16x3": (14, (0.08,), 20, "mbpt2", "bf16x3"),
+    "pnm_N14_rho0.08_n2max20_fp64": (14, (0.08,), 20, "mbpt2", "fp64"),
+    "pnm_N66_rho0.16_n2max36_bf16x3": (66, (0.16,), 36, "mbpt2", "bf16x3"),
+    "pnm_N66_rho0.16_n2max36_fp64": (66, (0.16,), 36, "mbpt2", "fp64"),
+    "pnm_N14_n2max20_16rho_bf16x3": (14, SWEEP16, 20, "mbpt2", "bf16x3"),
+    "pnm_N14_n2max20_16rho_fp64": (14, SWEEP16, 20, "mbpt2", "fp64"),
+    "pnm_N14_rho0.08_n2max4_fp64": (14, (0.08,), 4, "mbpt2", "fp64"),
 }
-DEFAULT_WORKLOAD = "pnm_N14_rho0.08_n2max20"
+DEFAULT_WORKLOAD = "pnm_N66_n2max36_heldout3_learned_bf16x3"
+COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
+           "pnm_N66_n2max36_heldout3_mbpt2_fp64", "pnm_N14_rho0.08_n2max20_bf16x3",
+           "pnm_N14_rho0.08_n2max20_fp64", "pnm_N66_rho0.16_n2max36_bf16x3", "pnm_N66_rho0.16_n2max36_fp64",
+           "pnm_N14_n2max20_16rho_bf16x3", "pnm_N14_n2max20_16rho_fp64"]
 MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 ALPHA = 0.5
@@ -44,10 +66,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "bf16x3"])
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / N=66 comparison runs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
+    ap.add_argument("--model", default=None, help="load the warm-start network (.npy) instead of training it")
+    ap.add_argument("--save-model", default=None, help="write the trained warm-start network (.npy)")
     return ap.parse_args()
 
 
@@ -121,16 +144,25 @@ def dist_setup():
     return world, rank, local
 
 
-def chan_sizes(ctx, sys_=0):
-    keys, sizes, _ = ctx.channels(sys_, 0)
-    xk, xs, _ = ctx.channels(sys_, 1)
-    szero = (keys % 3) == 1
-    return sizes[:, 0].astype(float), sizes[:, 1].astype(float), szero, xs[:, 0].astype(float), xs[:, 1].astype(float)
+def chan_sizes(ctx):
+    """Channel sizes of every system of a context, concatenated."""
+    import numpy as np
+    nhh, npp, sz, nph, nhp = [], [], [], [], []
+    for s in range(ctx.nsys):
+        keys, sizes, _ = ctx.channels(s, 0)
+        _, xs, _ = ctx.channels(s, 1)
+        nhh.append(sizes[:, 0])
+        npp.append(sizes[:, 1])
+        sz.append((keys % 3) == 1)
+        nph.append(xs[:, 0])
+        nhp.append(xs[:, 1])
+    cat = lambda v: np.concatenate(v).astype(float)
+    return cat(nhh), cat(npp), np.concatenate(sz), cat(nph), cat(nhp)
 
 
-def algorithmic_cost(ctx, kernel, prec):
-    """(bytes, flops) per launch of a kernel, from the channel sizes: each array the kernel
-    must touch, counted once."""
+def algorithmic_cost(ctx, kernel):
+    """(bytes, flops) per launch of a kernel, from the channel sizes of all systems of the
+    context: every array the kernel must touch, counted once."""
     nhh, npp, szero, nph, nhp = chan_sizes(ctx)
     nt = float((nhh * npp).sum())
     if kernel in ("k_pp64", "k_pp_tc"):
@@ -164,53 +196,51 @@ def read_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def oracle_time(N, rho, n2max, budget_s=8.0, max_runs=50):
-    """Median wall time (ms) of full oracle solves, repeated within a time budget."""
+def oracle_solve(N, rho, n2max):
+    """One full FP64 oracle solve (setup + MBPT2 start + iterations); (ms, dE, iterations)."""
     from oracle import channel
-    times = []
-    t_start = time.perf_counter()
-    dE = it = None
-    while len(times) < max_runs and (time.perf_counter() - t_start) < budget_s or len(times) < 1:
-        t0 = time.perf_counter()
-        o = channel.OracleSystem(N, rho, n2max, MINNESOTA)
-        dE, it, _, _ = o.ccd(alpha=ALPHA, tol=TOL_PER_N * N, maxit=500)
-        times.append((time.perf_counter() - t0) * 1e3)
-        del o
-    return statistics.median(times), len(times), channel.threads(), dE, it
+    t0 = time.perf_counter()
+    o = channel.OracleSystem(N, rho, n2max, MINNESOTA)
+    dE, it, _, _ = o.ccd(alpha=ALPHA, tol=TOL_PER_N * N, maxit=500)
+    ms = (time.perf_counter() - t0) * 1e3
+    del o
+    return ms, dE, it
 
 
 # ------------------------------------------------------------------------------ arms
 
 def run_reference(a):
+    """The FP64 oracle on the host cores, same workload and metric.  One step is a bounded
+    sample: one full solve of one system of the workload (the systems taken in turn), scaled
+    to the number of systems in the workload."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    N, rho, n2max = WORKLOADS[a.workload]
+    N, rhos, n2max, _, _ = WORKLOADS[a.workload]
     from oracle import build as ob
     ob.build()
     from oracle import channel
-    for _ in range(max(0, min(a.warmup, 1))):
-        oracle_time(N, rho, n2max, budget_s=0.0, max_runs=1)
-    times = []
-    dE = it = None
-    for _ in range(a.steps):
-        t0 = time.perf_counter()
-        o = channel.OracleSystem(N, rho, n2max, MINNESOTA)
-        dE, it, _, _ = o.ccd(alpha=ALPHA, tol=TOL_PER_N * N, maxit=500)
-        times.append((time.perf_counter() - t0) * 1e3)
-        del o
+    if a.warmup:
+        oracle_solve(N, rhos[0], n2max)  # pages in the library and starts the thread pool
+    times, dEs = [], {}
+    for k in range(a.steps):
+        rho = rhos[k % len(rhos)]
+        ms, dE, it = oracle_solve(N, rho, n2max)
+        times.append(ms * len(rhos))
+        dEs[str(rho)] = dE / N
     ms = statistics.mean(times)
     cores = channel.threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": a.workload, "N": N, "rho": rho, "n2max": n2max,
+        "config": {"workload": a.workload, "N": N, "rho": list(rhos), "n2max": n2max, "start": "mbpt2",
                    "tol_dE_per_N": TOL_PER_N, "mix_alpha": ALPHA, "l2": "host"},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": "%d full FP64 solves of the workload (setup + iterations) on the host" % a.steps},
+                         "sample": "each step: one full FP64 oracle solve (MBPT2 start) of one system of the "
+                                   "%d-system workload, systems in turn, time x %d" % (len(rhos), len(rhos))},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "result": {"dE_per_N": dE / N, "iters": it},
+        "result": {"dE_per_N": dEs},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -227,91 +257,94 @@ def timed_solves(ctx, solve_kw, steps, flush, stream, torch):
         dE, it, _, _ = ctx.solve(**solve_kw)
         e1.record(stream)
         evs.append((e0, e1))
-        iters.append(int(it[0]))
-        dEs.append(float(dE[0]))
+        iters.append([int(x) for x in it])
+        dEs.append([float(x) for x in dE])
     torch.cuda.synchronize()
     return [e0.elapsed_time(e1) for e0, e1 in evs], iters, dEs
 
 
-def solve_kwargs(P, prec, refine):
-    return dict(precision=prec, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
-                refine_sweeps=refine if prec == P.PNM_PREC_BF16X3 else 0)
+def solve_kwargs(P, workload, refine):
+    _, _, _, start, prec = WORKLOADS[workload]
+    p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
+    return dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
+                refine_sweeps=refine if p == P.PNM_PREC_BF16X3 else 0,
+                init=P.PNM_INIT_MLP if start == "mlp" else P.PNM_INIT_MBPT2)
 
 
-def measure_other(P, torch, stream, flush, workload, prec, refine, steps):
-    """Mean time-to-converge (ms) and iterations of another workload/precision."""
-    N, rho, n2max = WORKLOADS[workload]
-    ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream)
-    kw = solve_kwargs(P, prec, refine)
+_model = {}
+
+
+def trained_model(P, stream):
+    """Warm-start network trained by the library's GPU kernels on converged amplitudes of
+    N = 14 (n^2 <= 20, 16 densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16), or
+    the one given with --model."""
+    if "blob" not in _model and _model.get("path"):
+        import numpy as np
+        _model["blob"] = np.load(_model["path"]).astype(np.float32)
+    if "blob" not in _model:
+        kw64 = dict(precision=P.PNM_PREC_FP64, alpha=ALPHA, tol=1e-30, tol_per_N=1e-8, max_iter=500)
+        t0 = time.perf_counter()
+        tr14 = P.Context(14, list(SWEEP16), 20, params=MINNESOTA, stream=stream.cuda_stream)
+        tr14.solve(**kw64)
+        tr66 = P.Context(66, 0.16, 36, params=MINNESOTA, stream=stream.cuda_stream)
+        tr66.solve(**kw64)
+        blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=12, batch=4096, lr=1e-3, seed=2)
+        tr14.close()
+        tr66.close()
+        _model.update(blob=blob, train_s=time.perf_counter() - t0, loss=[float(hist[0]), float(hist[-1])])
+    return _model["blob"]
+
+
+def make_context(P, workload, stream):
+    N, rhos, n2max, start, _ = WORKLOADS[workload]
+    ctx = P.Context(N, list(rhos), n2max, params=MINNESOTA, stream=stream.cuda_stream)
+    if start == "mlp":
+        ctx.mlp_set_model(trained_model(P, stream))
+    return ctx
+
+
+def measure(P, torch, stream, flush, workload, refine, steps):
+    """Mean time-to-converge (ms), per-system iterations and dE/N of another workload."""
+    N = WORKLOADS[workload][0]
+    ctx = make_context(P, workload, stream)
+    kw = solve_kwargs(P, workload, refine)
     for _ in range(3):
         ctx.solve(**kw)
     torch.cuda.synchronize()
     ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
-    tim = ctx.timings()
     ctx.close()
-    return {"ms": statistics.mean(ms), "iters": statistics.mean(iters), "dE_per_N": statistics.mean(dEs) / N,
-            "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"]}
+    return {"ms": statistics.mean(ms), "iters": iters[-1], "dE_per_N": [x / N for x in dEs[-1]]}
 
 
-def measure_batch(P, torch, stream, flush, refine, steps):
-    """16 densities (0.02..0.32) of N=14, n^2<=20 solved together in one context: every kernel
-    launch covers all systems; the loop ends when all have converged."""
-    rhos = [0.02 * k for k in range(1, 17)]
-    ctx = P.Context(14, rhos, 20, params=MINNESOTA, stream=stream.cuda_stream)
+def oracle_leg(workloads, budget_s=45.0):
+    """cpu_baseline leg: FP64 oracle solves of the systems of the given workloads (each
+    distinct (N, rho, n2max) once, within a time budget, largest first). Returns
+    {(N, rho, n2max): (ms, dE/N, iterations)}."""
+    from oracle import build as ob
+    ob.build()
+    seen = []
+    for w in workloads:
+        N, rhos, n2max, _, _ = WORKLOADS[w]
+        for r in rhos:
+            if (N, r, n2max) not in seen:
+                seen.append((N, r, n2max))
     out = {}
-    for pn, pv in (("bf16x3", P.PNM_PREC_BF16X3), ("fp64", P.PNM_PREC_FP64)):
-        kw = solve_kwargs(P, pv, refine)
-        for _ in range(3):
-            ctx.solve(**kw)
-        torch.cuda.synchronize()
-        evs = []
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            dE, it, _, _ = ctx.solve(**kw)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        out[pn] = {"ms": statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs),
-                   "iters_max": int(max(it)), "dE_per_N": [float(x) / 14 for x in dE]}
-    ctx.close()
+    t0 = time.perf_counter()
+    for key in seen:
+        if out and time.perf_counter() - t0 > budget_s:
+            break
+        ms, dE, it = oracle_solve(*key)
+        out[key] = (ms, dE / key[0], it)
     return out
 
 
-def measure_learned(P, torch, stream, flush, refine, steps):
-    """Learned warm start: train on solver amplitudes of N=14 (n^2<=20, 16 densities) and
-    N=66 (n^2<=36, rho=0.16), then time N=66 solves at held-out densities from the learned
-    start, from the MBPT2 start (both mixed precision) and in FP64."""
-    kw64 = dict(precision=P.PNM_PREC_FP64, alpha=ALPHA, tol=1e-30, tol_per_N=1e-8, max_iter=500)
-    t0 = time.perf_counter()
-    tr14 = P.Context(14, [0.02 * k for k in range(1, 17)], 20, params=MINNESOTA, stream=stream.cuda_stream)
-    tr14.solve(**kw64)
-    tr66 = P.Context(66, 0.16, 36, params=MINNESOTA, stream=stream.cuda_stream)
-    tr66.solve(**kw64)
-    blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=12, batch=4096, lr=1e-3, seed=2)
-    train_s = time.perf_counter() - t0
-    tr14.close()
-    tr66.close()
-    res = {"train_s": train_s, "train_loss_first_last": [float(hist[0]), float(hist[-1])], "rho": {}}
-    for rho in (0.05, 0.11, 0.17):
-        ctx = P.Context(66, rho, 36, params=MINNESOTA, stream=stream.cuda_stream)
-        ctx.mlp_set_model(blob)
-        row = {}
-        for name, prec, init in (("bf16x3_learned", P.PNM_PREC_BF16X3, P.PNM_INIT_MLP),
-                                 ("bf16x3_mbpt2", P.PNM_PREC_BF16X3, P.PNM_INIT_MBPT2),
-                                 ("fp64_mbpt2", P.PNM_PREC_FP64, P.PNM_INIT_MBPT2)):
-            kw = solve_kwargs(P, prec, refine)
-            kw["init"] = init
-            for _ in range(3):
-                ctx.solve(**kw)
-            ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
-            row[name] = {"ms": statistics.mean(ms), "iters": statistics.mean(iters),
-                         "dE_per_N": statistics.mean(dEs) / 66}
-        ctx.close()
-        res["rho"][str(rho)] = row
-    return res
+def oracle_errors(res, workload, ora):
+    N, rhos, n2max, _, _ = WORKLOADS[workload]
+    err = {}
+    for r, e in zip(rhos, res["dE_per_N"]):
+        if (N, r, n2max) in ora:
+            err[str(r)] = e - ora[(N, r, n2max)][1]
+    return err
 
 
 def run_ours(a):
@@ -327,14 +360,12 @@ def run_ours(a):
     from paper_1611_06765_gb300 import build as pb
     pb.build()
     import paper_1611_06765_gb300 as P
-    N, rho, n2max = WORKLOADS[a.workload]
-    prec_name = "bf16x3" if a.precision == "auto" else a.precision
-    prec = P.PNM_PREC_BF16X3 if prec_name == "bf16x3" else P.PNM_PREC_FP64
-    refine = a.refine if prec == P.PNM_PREC_BF16X3 else 0
+    N, rhos, n2max, start, prec_name = WORKLOADS[a.workload]
+    _model["path"] = a.model
     stream = torch.cuda.current_stream()
-    ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream)
-    solve_kw = solve_kwargs(P, prec, a.refine)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctx = make_context(P, a.workload, stream)
+    solve_kw = solve_kwargs(P, a.workload, a.refine)
     for _ in range(max(3, a.warmup)):
         flush.zero_()
         ctx.solve(**solve_kw)
@@ -350,94 +381,108 @@ def run_ours(a):
     if dist:
         ms = max_over_ranks(ms, dist, device="cuda")
     tim = ctx.timings()
+    if a.save_model and rank == 0 and "blob" in _model:
+        import numpy as np
+        np.save(a.save_model, _model["blob"])
 
-    # e2e through the public API from host inputs
+    # e2e through the public API from host inputs (the trained model is an input, like V's parameters)
     e2e_ms = []
-    n_t = None
-    for k in range(max(1, min(a.steps, 10))):
+    n_t = 0
+    for _ in range(max(1, min(a.steps, 10))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream)
+        c2 = make_context(P, a.workload, stream)
         c2.solve(**solve_kw)
-        amps = c2.get_amplitudes()
+        n_t = sum(c2.get_amplitudes(s).size for s in range(c2.nsys))
         c2.close()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        n_t = amps.size
 
     # per-kernel durations from one profiled host-driven solve of the same work
     ctx.set_profiling(True)
     ctx.solve(host_loop=True, **solve_kw)
     stats = ctx.kernel_stats()
     ctx.set_profiling(False)
-    dom = max(stats.items(), key=lambda kv: kv[1][0])
-    kname, (ktot, kn) = dom
+    kname, (ktot, kn) = max(stats.items(), key=lambda kv: kv[1][0])
     kavg_s = ktot / kn / 1e3
-    byts, flops = algorithmic_cost(ctx, kname, prec)
+    byts, flops = algorithmic_cost(ctx, kname)
     hbm, bf16, src = read_peaks()
-    if kname == "k_pp64":
+    if kname in ("k_pp64", "k_ph64"):
         roof = {"bound": "alu", "achieved": flops / kavg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 DFMA rate derived from SM count and clock"}
+                "unit": "TFLOP/s", "peak_source": "FP64 FMA rate from SM count and clock"}
     else:
         roof = {"bound": "hbm", "achieved": byts / kavg_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "%s hbm_gbs" % src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = kname
-    roof["kernel_avg_us"] = kavg_s * 1e6
-    roof["algorithmic_bytes"] = byts
-    roof["algorithmic_flops"] = flops
-    body = 6 if prec == P.PNM_PREC_BF16X3 else 5
-    launches_per_solve = 2 + body * statistics.mean(iters) + (1 if refine else 0)
+    roof.update(frac=roof["achieved"] / roof["peak"], traffic=None, kernel=kname, kernel_avg_us=kavg_s * 1e6,
+                algorithmic_bytes=byts, algorithmic_flops=flops)
+    if "k_pp_tc" in stats and kname != "k_pp_tc":
+        t_tc = stats["k_pp_tc"][0] / stats["k_pp_tc"][1] / 1e3
+        b_tc, f_tc = algorithmic_cost(ctx, "k_pp_tc")
+        roof["k_pp_tc"] = {"bound": "hbm", "achieved": b_tc / t_tc / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": b_tc / t_tc / 1e9 / hbm, "kernel_avg_us": t_tc * 1e6,
+                           "tensor_tflops": f_tc / t_tc / 1e12, "tensor_frac_of_bf16_peak": f_tc / t_tc / 1e12 / bf16}
+    # kernels of one solve: the loop bodies and refinement sweeps counted by the profiler, plus
+    # the start (MBPT2: init + energy; learned: features, inference, apply, energy)
+    launches_per_solve = sum(n for _, n in stats.values()) + (4 if start == "mlp" else 2)
 
     comparison = None
     if rank == 0 and not a.no_extra:
         comparison = {}
-        other = P.PNM_PREC_FP64 if prec == P.PNM_PREC_BF16X3 else P.PNM_PREC_BF16X3
-        comparison[a.workload + ("_fp64" if other == P.PNM_PREC_FP64 else "_bf16x3")] = measure_other(
-            P, torch, stream, flush, a.workload, other, a.refine, max(5, a.steps // 2))
-        if a.workload != "pnm_N66_rho0.16_n2max36":
-            for pn, pv in (("bf16x3", P.PNM_PREC_BF16X3), ("fp64", P.PNM_PREC_FP64)):
-                comparison["pnm_N66_rho0.16_n2max36_" + pn] = measure_other(
-                    P, torch, stream, flush, "pnm_N66_rho0.16_n2max36", pv, a.refine, 3)
-        comparison["density_batch_N14_n2max20_16rho"] = measure_batch(P, torch, stream, flush, a.refine, 3)
-        comparison["learned_start_N66_n2max36_heldout"] = measure_learned(P, torch, stream, flush, a.refine, 3)
+        for w in COMPARE:
+            if w != a.workload:
+                comparison[w] = measure(P, torch, stream, flush, w, a.refine, 5)
+        if "train_s" in _model:
+            comparison["training"] = {"seconds": _model["train_s"], "loss_first_last": _model["loss"],
+                                      "data": "FP64-converged amplitudes, N=14 n2max=20 16 densities "
+                                              "and N=66 n2max=36 rho=0.16"}
+
+    result = {"dE_per_N": [x / N for x in dEs[-1]], "iters": iters[-1], "step_ms_min": min(step_ms),
+              "step_ms_median": statistics.median(step_ms), "wall_ms_per_step": wall * 1e3 / a.steps,
+              "setup_ms": tim["setup"], "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"],
+              "kernels_ms_per_solve": {k: v[0] for k, v in stats.items()}}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        from oracle import build as ob
-        ob.build()
-        cms, runs, cores, dE_o, it_o = oracle_time(N, rho, n2max)
-        cpu = {"value": cms, "unit": "ms", "cores": cores, "kind": "oracle",
-               "sample": "median of %d full FP64 oracle solves of the workload (setup + %d iterations)" % (runs, it_o),
-               "dE_per_N": dE_o / N, "gpu_minus_oracle_dE_per_N": statistics.mean(dEs) / N - dE_o / N}
+        from oracle import channel
+        ora = oracle_leg([a.workload] + (COMPARE if comparison is not None else []))
+        own = [ora[(N, r, n2max)] for r in rhos if (N, r, n2max) in ora]
+        cpu = {"value": sum(x[0] for x in own) * len(rhos) / len(own), "unit": "ms",
+               "cores": channel.threads(), "kind": "oracle",
+               "sample": "%d of %d systems of the workload, one full FP64 oracle solve each (setup, MBPT2 "
+                         "start, iterations to the same stopping rule), summed and scaled to all systems"
+                         % (len(own), len(rhos)),
+               "oracle_dE_per_N": {str(k[1]): v[1] for k, v in ora.items() if k[0] == N and k[2] == n2max
+                                   and k[1] in rhos},
+               "oracle_iters": {str(k[1]): v[2] for k, v in ora.items() if k[0] == N and k[2] == n2max
+                                and k[1] in rhos}}
+        result["dE_per_N_minus_oracle"] = oracle_errors(result, a.workload, ora)
+        if comparison:
+            for w, r in comparison.items():
+                if w in WORKLOADS:
+                    r["dE_per_N_minus_oracle"] = oracle_errors(r, w, ora)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": a.steps,
             "warmup": max(3, a.warmup), "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == P.PNM_PREC_FP64 else "bf16x3+f32+f64",
+            "dtype": "f64" if prec_name == "fp64" else "bf16x3+f32+f64",
             "data": "synthetic",
-            "config": {"workload": a.workload, "N": N, "rho": rho, "n2max": n2max,
-                       "precision": prec_name, "refine_sweeps": refine, "mix_alpha": ALPHA,
+            "config": {"workload": a.workload, "N": N, "rho": list(rhos), "n2max": n2max, "start": start,
+                       "precision": prec_name, "refine_sweeps": solve_kw["refine_sweeps"], "mix_alpha": ALPHA,
                        "tol_dE_per_N": TOL_PER_N, "l2": "flushed (512 MB write) before every step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clk.summary(),
             "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms",
-                    "h2d_bytes_per_step": 4 + 8 + 4 + 7 * 8,
-                    "d2h_bytes_per_step": 8 * (n_t or 0) + 8 + 4 + 8},
-            "gpu_launches": int(round(launches_per_solve * a.steps)),
+                    "h2d_bytes_per_step": 8 * len(rhos) + 7 * 8 + 8 + (4 * len(_model.get("blob", ()))),
+                    "d2h_bytes_per_step": 8 * n_t + len(rhos) * 20},
+            "gpu_launches": int(launches_per_solve * a.steps),
             "roofline": roof,
             "cpu_baseline": cpu,
-            "comparison": comparison,
             "tuning": (dict(zip(("k_splits", "stages", "pp_tc_us", "serial_mask"), ctx.tuning()))
-                       if prec == P.PNM_PREC_BF16X3 else None),
-            "result": {"dE_per_N": statistics.mean(dEs) / N, "iters": statistics.mean(iters),
-                       "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
-                       "wall_ms_per_step": wall * 1e3 / a.steps, "setup_ms": tim["setup"],
-                       "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"],
-                       "kernels_ms_per_solve": {k: v[0] for k, v in stats.items()}},
+                       if prec_name == "bf16x3" else None),
+            "comparison": comparison,
+            "result": result,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
