@@ -249,6 +249,12 @@ int pnm_get_tuning(const pnm_ctx *ctx, int *ksplit, int *stages, float *us, int 
  * PNM_ETIMEOUT after about a second, the context still usable.  Nothing traps or hangs. */
 int pnm_selftest_timeout(pnm_ctx *ctx);
 
+/* FMA-rate microbenchmark (not from the paper): the measured peak FP64 (fp64 = 1) or FP32
+ * (fp64 = 0) fused multiply-add rate of the current device in TFLOP/s (2 flop per FMA),
+ * the roofline denominator of the ALU-bound kernels.  Runs two short kernels on `stream`
+ * (NULL: the default stream) and synchronizes.  PNM_ECUDA / PNM_ENOMEM on failure. */
+int pnm_measure_fma_peak(int fp64, void *stream, double *tflops);
+
 /* Thread-local text describing the last failure of a pnm_* call on this thread. */
 const char *pnm_last_error(void);
 

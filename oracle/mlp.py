@@ -8,7 +8,8 @@ Model (the definition the CUDA kernels implement):
   z_l = h_{l-1} W_l^T + b_l,  h_l = bf16(gelu(z_l))   l = 1, 2, 3 (width 128)
   y   = h_3 w_4 + b_4                                  scalar output
   loss = mean((y - target)^2)
-with gelu(x) = x/2 (1 + erf(x/sqrt 2)), weights used through their BF16 rounding, and the
+with gelu(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (the tanh form of GELU),
+weights used through their BF16 rounding, and the
 rounding of activations treated as the identity in the backward pass (straight-through).
 bf16() is round-to-nearest-even on float32, as __float2bfloat16_rn.
 
@@ -17,7 +18,6 @@ Parameter blob (float32), the layout shared with include/pnmcc.h:
   W3[128][128], b3[128], w4[128], b4
 """
 import numpy as np
-from scipy.special import erf
 
 F = 32
 H = 128
@@ -59,12 +59,16 @@ def bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+GELU_C = np.sqrt(2.0 / np.pi)
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + 0.044715 * z ** 3)))
 
 
 def gelu_prime(z):
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    th = np.tanh(GELU_C * (z + 0.044715 * z ** 3))
+    return 0.5 * (1.0 + th) + 0.5 * z * (1.0 - th * th) * GELU_C * (1.0 + 3 * 0.044715 * z * z)
 
 
 def forward(blob, X, round_bf16=True):

@@ -195,6 +195,14 @@ def _fptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_float))
 
 
+def measure_fma_peak(fp64=True, stream=None):
+    """Measured peak FMA rate of the current device, TFLOP/s (FP64 or FP32)."""
+    out = C.c_double()
+    _lib.check(_lib.load().pnm_measure_fma_peak(int(fp64), C.c_void_p(stream) if stream else None,
+                                                C.byref(out)))
+    return out.value
+
+
 def mlp_num_params():
     n = C.c_int()
     _lib.check(_lib.load().pnm_mlp_num_params(C.byref(n)))

@@ -31,7 +31,8 @@ EXPORTS = (
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_mlp_num_params", "pnm_mlp_init",
-    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout", "pnm_last_error",
+    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
+    "pnm_measure_fma_peak", "pnm_last_error",
 )
 
 

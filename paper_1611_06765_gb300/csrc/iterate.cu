@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <map>
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -24,33 +25,49 @@
 
 
 // ----------------------------------------------------------------------------- stats
+// Element type T_: double for the FP64 iteration (t, v_pphh, v_hhhh, chi_hh, sij, sab), float
+// for the mixed-precision one (their FP32 copies).
+template <typename T_>
+struct StatsIO {
+  const T_ *t, *v, *vhh;
+  T_ *chi, *sij, *sab;
+  __device__ StatsIO(const DevState& D, const LoopCtl* ctl) {
+    if constexpr (std::is_same<T_, double>::value) {
+      t = cur_t(D, ctl); v = D.v_pphh; vhh = D.v_hhhh; chi = D.chi_hh; sij = D.sij; sab = D.sab;
+    } else {
+      t = cur_t32(D, ctl); v = D.v32; vhh = D.vhh32; chi = D.chi32; sij = D.sij32; sab = D.sab32;
+    }
+  }
+};
+
 // Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for all ij.
 // Blocks [nrows, ...): column chunk (c, ab0): sab[ab] = sum_ij t v.
+template <typename T_>
 __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __restrict__ ctl,
                                                 int nrows, const int2* __restrict__ ab_items) {
-  __shared__ double sh32[32];
-  const double* __restrict__ t = cur_t(D, ctl);
+  __shared__ T_ sh32[32];
+  StatsIO<T_> io(D, ctl);
+  const T_* __restrict__ t = io.t;
   if ((int)blockIdx.x < nrows) {
     int2 it = D.row_item[blockIdx.x];
     int c = it.x, kl = it.y;
     int npp = D.ch_npp[c], nh = D.ch_nhh[c];
     long base = D.ch_t_off[c];
-    const double* tr = t + base + (long)kl * npp;
-    const double* vr = D.v_pphh + base + (long)kl * npp;
-    double s = 0.0;
+    const T_* tr = t + base + (long)kl * npp;
+    const T_* vr = io.v + base + (long)kl * npp;
+    T_ s = 0;
     for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) s += tr[ab] * vr[ab];
     s = block_sum(s, sh32);
-    if (threadIdx.x == 0) D.sij[D.ch_hh_off[c] + kl] = s;
+    if (threadIdx.x == 0) io.sij[D.ch_hh_off[c] + kl] = s;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int ij = warp; ij < nh; ij += blockDim.x >> 5) {
-      const double* tj = t + base + (long)ij * npp;
-      double acc = 0.0;
+      const T_* tj = t + base + (long)ij * npp;
+      T_ acc = 0;
       for (int cd = lane; cd < npp; cd += 32) acc += vr[cd] * tj[cd];
       acc = warp_sum(acc);
       if (lane == 0) {
         long e = D.ch_vhh_off[c] + (long)kl * nh + ij;
-        D.chi_hh[e] = D.v_hhhh[e] + acc;
-        if (D.chi32) D.chi32[e] = (float)(D.v_hhhh[e] + acc);
+        io.chi[e] = io.vhh[e] + acc;
       }
     }
   } else {
@@ -59,33 +76,39 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
     int npp = D.ch_npp[c], nh = D.ch_nhh[c];
     if (ab < npp) {
       long base = D.ch_t_off[c] + ab;
-      double s = 0.0;
-      for (int ij = 0; ij < nh; ij++) s += t[base + (long)ij * npp] * D.v_pphh[base + (long)ij * npp];
-      D.sab[D.ch_pp_off[c] + ab] = s;
+      T_ s = 0;
+      for (int ij = 0; ij < nh; ij++) s += t[base + (long)ij * npp] * io.v[base + (long)ij * npp];
+      io.sab[D.ch_pp_off[c] + ab] = s;
     }
   }
 }
 
 // chi_b - eps_b = -sum_d sum_{k<l} t_kl^bd v_kl^bd   (particles)
 // chi_j - eps_j = +sum_l sum_{c<d} v_jl^cd t_jl^cd   (holes)
+template <typename T_>
 __global__ void k_dchi(DevState D, int nsp_total) {
   int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (p >= nsp_total) return;
+  constexpr bool F64 = std::is_same<T_, double>::value;
   int lo = D.occ_off[p], hi = D.occ_off[p + 1];
   bool hole = D.sp_hole[p] != 0;
-  const double* src = hole ? D.sij : D.sab;
-  double s = 0.0;
+  const T_* src;
+  if constexpr (F64) src = hole ? D.sij : D.sab;
+  else src = hole ? D.sij32 : D.sab32;
+  T_ s = 0;
   for (int k = lo + lane; k < hi; k += 32) s += src[D.occ_idx[k]];
   s = warp_sum(s);
-  if (lane == 0) D.dchi[p] = hole ? s : -s;
+  if (lane == 0) {
+    if constexpr (F64) D.dchi[p] = hole ? s : -s;
+    else D.dchi32[p] = hole ? s : -s;
+  }
 }
 
 // ----------------------------------------------------------------------------- ph term
-// One CTA per cross channel, element type T_ of the precision mode (double for FP64, float
-// for the mixed mode).  Shared buffers, dimensions padded to multiples of 4 with zeros:
+// One CTA per cross channel.  Shared buffers, dimensions padded to multiples of 4 with zeros:
 //   Ts[u][s] = T[(a,i)=u][(k,c)=s]          (P4 x H4)
-//   Xt[u][r] = W[r][u] for GEMM 1, then T[r][u] transposed (T rows as columns) for GEMM 2
+//   Xt[u][r] = W[r][u] for the first contraction, then T[r][u] transposed for the second
 //   Cs[r][s] = C[r][s]                       (H4 x H4)
 // Each thread accumulates 4 x 4 outputs; per k step it reads two 4-vectors from shared.
 template <typename T_>
@@ -105,71 +128,33 @@ struct Vec4<double> {
   }
 };
 
-template <typename T_>
-__global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
-                                            const T_* __restrict__ xw, const T_* __restrict__ xv1,
-                                            T_* __restrict__ xq) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T_* sm = reinterpret_cast<T_*>(smraw);
-  int x = blockIdx.x;
-  int nph = D.x_nph[x], nhp = D.x_nhp[x];
-  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
-  const double* __restrict__ t = cur_t(D, ctl);
-  T_* Ts = sm;
-  T_* Xt = Ts + P4 * H4;
-  T_* Cs = Xt + P4 * H4;
-  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  // T[(a,i)][(k,c)] = t_ik^ac through the signed index map; W transposed into Xt.
-  // Four elements per thread per step so that four independent gathers are in flight.
-  const bool f32 = std::is_same<T_, float>::value && D.t32_0 != nullptr;
-  const float* __restrict__ t32 = f32 ? cur_t32(D, ctl) : nullptr;
-  for (int e0 = threadIdx.x; e0 < P4 * H4; e0 += 4 * blockDim.x) {
-    int code[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int e = e0 + q * blockDim.x;
-      int u = e / H4, s = e % H4;
-      code[q] = (e < P4 * H4 && u < nph && s < nhp) ? D.xmap[to + (long)u * nhp + s] : 0;
-    }
-    T_ tv[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int cd = code[q], a = cd > 0 ? cd - 1 : -cd - 1;
-      T_ g = cd == 0 ? (T_)0 : (f32 ? (T_)t32[a] : (T_)t[a]);
-      tv[q] = cd < 0 ? -g : g;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int e = e0 + q * blockDim.x;
-      if (e >= P4 * H4) continue;
-      int u = e / H4, s = e % H4;
-      Ts[e] = tv[q];
-      Xt[e] = (u < nph && s < nhp) ? xw[wo + (long)u * nhp + s] : (T_)0;  // W^T[u][s] = W[s][u]
-    }
-  }
-  __syncthreads();
+// The two contractions of a cross channel from the staged Ts (T) and Xt (W^T); writes Q.
+//   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
+//   Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
+template <typename T_, int NT>
+__device__ __forceinline__ void ph_contract(T_* Ts, T_* Xt, T_* Cs, int nph, int nhp, int P4, int H4,
+                                            const T_* __restrict__ v1, T_* __restrict__ q) {
   // Small channels: one output per thread (more threads busy, shorter chains); large
   // channels: 4 x 4 register tiles.
-  const bool small = (nph * nhp <= 2 * (int)blockDim.x) && (nhp * nhp <= 2 * (int)blockDim.x);
+  const bool small = (nph * nhp <= 2 * NT) && (nhp * nhp <= 2 * NT);
   if (small) {
-    for (int e = threadIdx.x; e < nhp * nhp; e += blockDim.x) {
+    for (int e = threadIdx.x; e < nhp * nhp; e += NT) {
       int r = e / nhp, c2 = e % nhp;
       T_ acc = 0;
       for (int u = 0; u < nph; u++) acc += Xt[u * H4 + r] * Ts[u * H4 + c2];
-      Cs[r * H4 + c2] = xv1[co + (long)r * nhp + c2] + (T_)0.5 * acc;
+      Cs[r * H4 + c2] = v1[(long)r * nhp + c2] + (T_)0.5 * acc;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
+    for (int e = threadIdx.x; e < nph * nhp; e += NT) {
       int r = e / nhp, c2 = e % nhp;
       T_ acc = 0;
       for (int u = 0; u < nhp; u++) acc += Ts[r * H4 + u] * Cs[u * H4 + c2];
-      xq[to + (long)r * nhp + c2] = acc;
+      q[(long)r * nhp + c2] = acc;
     }
     return;
   }
-  // C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
   int th = H4 >> 2;
-  for (int tile = threadIdx.x; tile < th * th; tile += blockDim.x) {
+  for (int tile = threadIdx.x; tile < th * th; tile += NT) {
     int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
     T_ acc[4][4] = {};
     for (int u = 0; u < nph; u++) {
@@ -186,19 +171,18 @@ __global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restric
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         int r = r0 + i, s = s0 + j;
-        Cs[r * H4 + s] = (r < nhp && s < nhp) ? xv1[co + (long)r * nhp + s] + (T_)0.5 * acc[i][j] : (T_)0;
+        Cs[r * H4 + s] = (r < nhp && s < nhp) ? v1[(long)r * nhp + s] + (T_)0.5 * acc[i][j] : (T_)0;
       }
   }
   __syncthreads();
   // T transposed into Xt: Xt[u][r] = T[r][u]  (u over hp, r over ph)
-  for (int e = threadIdx.x; e < P4 * H4; e += blockDim.x) {
+  for (int e = threadIdx.x; e < P4 * H4; e += NT) {
     int r = e / H4, u = e % H4;
     Xt[u * P4 + r] = Ts[e];
   }
   __syncthreads();
-  // Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
   int tp = P4 >> 2;
-  for (int tile = threadIdx.x; tile < tp * th; tile += blockDim.x) {
+  for (int tile = threadIdx.x; tile < tp * th; tile += NT) {
     int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
     T_ acc[4][4] = {};
     for (int u = 0; u < nhp; u++) {
@@ -215,22 +199,104 @@ __global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restric
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         int r = r0 + i, s = s0 + j;
-        if (r < nph && s < nhp) xq[to + (long)r * nhp + s] = acc[i][j];
+        if (r < nph && s < nhp) q[(long)r * nhp + s] = acc[i][j];
       }
   }
 }
 
-size_t ph_smem_bytes(const pnm_ctx* ctx, size_t elem) {
-  size_t m4 = (size_t)((ctx->max_x_dim + 3) & ~3);
+// FP64 ph term: one CTA per cross channel; T[(a,i)][(k,c)] = t_ik^ac gathered through the
+// signed index map.
+__global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
+                                            const double* __restrict__ xw, const double* __restrict__ xv1,
+                                            double* __restrict__ xq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sm = reinterpret_cast<double*>(smraw);
+  int x = blockIdx.x;
+  int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
+  const double* __restrict__ t = cur_t(D, ctl);
+  double* Ts = sm;
+  double* Xt = Ts + P4 * H4;
+  double* Cs = Xt + P4 * H4;
+  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+  // Four elements per thread per step so that four independent gathers are in flight.
+  for (int e0 = threadIdx.x; e0 < P4 * H4; e0 += 4 * blockDim.x) {
+    int code[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int e = e0 + q * blockDim.x;
+      int u = e / H4, s = e % H4;
+      code[q] = (e < P4 * H4 && u < nph && s < nhp) ? D.xmap[to + (long)u * nhp + s] : 0;
+    }
+    double tv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int cd = code[q], a = cd > 0 ? cd - 1 : -cd - 1;
+      double g = cd == 0 ? 0.0 : t[a];
+      tv[q] = cd < 0 ? -g : g;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int e = e0 + q * blockDim.x;
+      if (e >= P4 * H4) continue;
+      int u = e / H4, s = e % H4;
+      Ts[e] = tv[q];
+      Xt[e] = (u < nph && s < nhp) ? xw[wo + (long)u * nhp + s] : 0.0;  // W^T[u][s] = W[s][u]
+    }
+  }
+  __syncthreads();
+  ph_contract<double, 128>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
+}
+
+// FP32 ph term of the mixed-precision iteration.  T comes ready in the cross-channel layout
+// (xt, scattered by the previous update through the inverse of the index map), so staging is
+// plain coalesced loads.  xlist: the cross channels of this launch (one size class).
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ph_mix(DevState D, const int* __restrict__ xlist,
+                                               const float* __restrict__ xt, const float* __restrict__ xw,
+                                               const float* __restrict__ xv1, float* __restrict__ xq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* sm = reinterpret_cast<float*>(smraw);
+  int x = xlist[blockIdx.x];
+  int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
+  float* Ts = sm;
+  float* Xt = Ts + P4 * H4;
+  float* Cs = Xt + P4 * H4;
+  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+#pragma unroll 4
+  for (int e = threadIdx.x; e < P4 * H4; e += NT) {
+    int u = e / H4, s = e % H4;
+    bool in = u < nph && s < nhp;
+    long o = (long)u * nhp + s;
+    Ts[e] = in ? xt[to + o] : 0.0f;
+    Xt[e] = in ? xw[wo + o] : 0.0f;  // W^T[u][s] = W[s][u]
+  }
+  __syncthreads();
+  ph_contract<float, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
+}
+
+size_t ph_smem_bytes(int max_dim, size_t elem) {
+  size_t m4 = (size_t)((max_dim + 3) & ~3);
   return elem * 3 * m4 * m4;
 }
 
-template <typename T_>
-void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
-  k_ph<T_><<<ctx->nx, 128, ph_smem_bytes(ctx, sizeof(T_)), s>>>(ctx->d, ctx->ctl, xw, xv1, xq);
+void launch_ph64(pnm_ctx* ctx, cudaStream_t s) {
+  k_ph<<<ctx->nx, 128, ph_smem_bytes(ctx->max_x_dim, sizeof(double)), s>>>(ctx->d, ctx->ctl, ctx->d.x_w,
+                                                                          ctx->d.x_v1, ctx->d.xq);
 }
-template void launch_ph<double>(pnm_ctx*, const double*, const double*, double*, cudaStream_t);
-template void launch_ph<float>(pnm_ctx*, const float*, const float*, float*, cudaStream_t);
+
+// Mixed ph: cross channels larger than PH_SMALL_DIM in one launch of 256-thread CTAs, the
+// others in a second launch with a small shared footprint (many CTAs per SM).
+void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
+                   cudaStream_t s) {
+  if (ctx->n_ph_big > 0)
+    k_ph_mix<256><<<ctx->n_ph_big, 256, ph_smem_bytes(ctx->max_x_dim, sizeof(float)), s>>>(
+        ctx->d, ctx->ph_list, xt, xw, xv1, xq);
+  if (ctx->n_ph_small > 0)
+    k_ph_mix<128><<<ctx->n_ph_small, 128, ph_smem_bytes(PH_SMALL_DIM, sizeof(float)), s>>>(
+        ctx->d, ctx->ph_list + ctx->n_ph_big, xt, xw, xv1, xq);
+}
 
 // ---------------------------------------------------------------------- pp ladder FP64
 // R^T(ij, ab) = sum_cd t(ij, cd) <cd|v|ab>, restricted pairs (1/2 sum over ordered cd of a
@@ -375,9 +441,9 @@ __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
 }
 
 // ---------------------------------------------------------------------------- update
-// One CTA per item (channel, ij, 128 pp columns).  Jacobi step of Eq. (ccd3): the bracket
-// collects v, the non-eps parts of the one-body terms, the pp and hh ladders and
-// P(ij)P(ab) Q; then t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.
+// One CTA per item (channel, up to UPD_ROWS hole pairs ij, 128 pp columns).  Jacobi step of
+// Eq. (ccd3): the bracket collects v, the non-eps parts of the one-body terms, the pp and hh
+// ladders and P(ij)P(ab) Q; then t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.
 // The residual of the amplitude equation is R = bracket - eps_ij^ab t.
 template <typename RT, typename QT>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
@@ -385,85 +451,125 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
                                                 const RT* __restrict__ rpp,
                                                 const QT* __restrict__ xq, PackArgs pk, int nplanes,
                                                 long pstride) {
+  // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng
+  __shared__ QT chs[UPD_MAX_NHH][UPD_ROWS];
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
-  int c = it.x, ij = it.y;
+  int c = it.x, ij0 = it.y, ng = it.w;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
-  int ab_end = min(npp, it.z + (int)blockDim.x);
+  int ab = it.z + threadIdx.x;
   const SysCtl* __restrict__ sc = fa.sc;
-  int sys = D.ch_sys[c];
-  bool frozen = sc[sys].done != 0;
+  bool frozen = sc[D.ch_sys[c]].done != 0;
   bool szero = D.ch_szero[c] != 0;
+  constexpr bool MIX = std::is_same<QT, float>::value;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
+  const float* __restrict__ t32 = MIX ? cur_t32(D, ctl) : nullptr;
   double* __restrict__ tn = next_t(D, ctl);
   long base = D.ch_t_off[c];
-  long row = base + (long)ij * npp;
-  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-  double di = D.dchi[h.x], dj = D.dchi[h.y];
-  const double* chi = D.chi_hh + D.ch_vhh_off[c] + ij;  // chi[kl * nh]
-  double esum = 0.0, rsum = 0.0;
-  for (int ab = it.z + threadIdx.x; ab < ab_end; ab += blockDim.x) {
-    long z = row + ab;
-    double tz = t[z];
-    double out = tz;
-    double v = D.v_pphh[z];
-    if (!frozen) {
-      int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
-      double num;
-      if constexpr (std::is_same<QT, float>::value) {
-        // mixed precision: the correction terms (one-body, ladders, ph) in FP32; the
-        // denominator, the Jacobi step, mixing, energy and residual stay FP64
-        float corr = (float)(D.dchi[p.x] + D.dchi[p.y] - di - dj) * (float)tz;
-        if (szero)
-          for (int pl = 0; pl < nplanes; pl++) corr += (float)rpp[pl * pstride + z];
-        if (D.t32_0) {
-          const float* t32 = cur_t32(D, ctl);
-          const float* chi32 = D.chi32 + D.ch_vhh_off[c] + ij;
-          for (int kl = 0; kl < nh; kl++) corr = fmaf(t32[base + (long)kl * npp + ab], chi32[(long)kl * nh], corr);
-        } else {
-          for (int kl = 0; kl < nh; kl++)
-            corr = fmaf((float)t[base + (long)kl * npp + ab], (float)chi[(long)kl * nh], corr);
-        }
-        int4 q = D.qmap[z];
-        if (q.x >= 0) corr += (float)xq[q.x];
-        if (q.y >= 0) corr -= (float)xq[q.y];
-        if (q.z >= 0) corr -= (float)xq[q.z];
-        if (q.w >= 0) corr += (float)xq[q.w];
-        num = v + (double)corr;
-      } else {
-        num = v + (D.dchi[p.x] + D.dchi[p.y] - di - dj) * tz;
-        if (szero)
-          for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
-        double hh = 0.0;
-        for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * chi[(long)kl * nh];
-        num += hh;
-        int4 q = D.qmap[z];
-        double ph = 0.0;
-        if (q.x >= 0) ph += (double)xq[q.x];
-        if (q.y >= 0) ph -= (double)xq[q.y];
-        if (q.z >= 0) ph -= (double)xq[q.z];
-        if (q.w >= 0) ph += (double)xq[q.w];
-        num += ph;
-      }
-      // eps_ij^ab and its reciprocal are fixed per context (no divide per iteration)
-      double tnew = num * D.inv_den[z];
-      double R = num - D.den[z] * tz;
-      rsum += R * R;
-      out = alpha * tnew + (1.0 - alpha) * tz;
+  long vho = D.ch_vhh_off[c];
+  for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
+    int kl = e / UPD_ROWS, g = e % UPD_ROWS;
+    QT v = 0;
+    if (g < ng) {
+      long o = vho + (long)kl * nh + ij0 + g;
+      if constexpr (MIX) v = D.chi32[o];
+      else v = D.chi_hh[o];
     }
-    tn[z] = out;
-    if (std::is_same<QT, float>::value && D.t32_0) next_t32(D, ctl)[z] = (float)out;
-    esum += v * out;
-    if (pk.bt && szero) {
-      // BF16 hi/lo copy of the new amplitude for the next tensor-core pp ladder
-      int npad = pk.ch_npad[c];
-      long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
-      __nv_bfloat16 hi, lo;
-      split_bf16(out, hi, lo);
-      int o = tile_core_off(ij, ab & 63);
-      pk.bt[tb + o] = hi;
-      pk.bt[tb + (long)npad * 64 + o] = lo;
+    chs[kl][g] = v;
+  }
+  __syncthreads();
+  double esum = 0.0, rsum = 0.0;
+  if (ab < npp) {
+    // hh ladder sum_kl t_ab^kl chi_kl^ij for all rows of the item: one pass over the t column
+    QT hh[UPD_ROWS];
+#pragma unroll
+    for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0;
+    if (!frozen) {
+      const long col = base + ab;
+#pragma unroll 4
+      for (int kl = 0; kl < nh; kl++) {
+        QT tk;
+        if constexpr (MIX) tk = t32[col + (long)kl * npp];
+        else tk = t[col + (long)kl * npp];
+#pragma unroll
+        for (int g = 0; g < UPD_ROWS; g++) hh[g] = tk * chs[kl][g] + hh[g];
+      }
+    }
+    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+    // one-body part of the bracket: (d_a + d_b - d_i - d_j) t with d_p = chi_p - eps_p
+    QT da;
+    if constexpr (MIX) da = D.dchi32[p.x] + D.dchi32[p.y];
+    else da = D.dchi[p.x] + D.dchi[p.y];
+#pragma unroll
+    for (int g = 0; g < UPD_ROWS; g++) {
+      if (g >= ng) break;
+      int ij = ij0 + g;
+      long z = base + (long)ij * npp + ab;
+      double tz = t[z];
+      double out = tz;
+      double v = D.v_pphh[z];
+      int4 q = D.qmap[z];
+      if (!frozen) {
+        int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+        if constexpr (MIX) {
+          // mixed precision: the bracket's correction terms (one-body, ladders, ph) in FP32
+          // from the FP32 copies; v, the denominator, the Jacobi step with mixing, the
+          // residual and the energy in FP64.  The FP64 unit is the scarce one, so the step
+          // is written as t + alpha R / eps with R = bracket - eps t (same value as
+          // alpha t_new + (1 - alpha) t).
+          float corr = (da - D.dchi32[h.x] - D.dchi32[h.y]) * t32[z] + hh[g];
+          if (szero)
+            for (int pl = 0; pl < nplanes; pl++) corr += (float)rpp[pl * pstride + z];
+          if (q.x >= 0) corr += (float)xq[q.x];
+          if (q.y >= 0) corr -= (float)xq[q.y];
+          if (q.z >= 0) corr -= (float)xq[q.z];
+          if (q.w >= 0) corr += (float)xq[q.w];
+          double num = v + (double)corr;
+          double R = fma(-D.den[z], tz, num);
+          rsum = fma(R, R, rsum);
+          out = fma(alpha * R, D.inv_den[z], tz);
+        } else {
+          double num = v + (da - D.dchi[h.x] - D.dchi[h.y]) * tz;
+          if (szero)
+            for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
+          num += (double)hh[g];
+          double ph = 0.0;
+          if (q.x >= 0) ph += (double)xq[q.x];
+          if (q.y >= 0) ph -= (double)xq[q.y];
+          if (q.z >= 0) ph -= (double)xq[q.z];
+          if (q.w >= 0) ph += (double)xq[q.w];
+          num += ph;
+          double tnew = num * D.inv_den[z];
+          double R = num - D.den[z] * tz;
+          rsum += R * R;
+          out = alpha * tnew + (1.0 - alpha) * tz;
+        }
+      }
+      tn[z] = out;
+      esum = fma(v, out, esum);
+      if constexpr (MIX) {
+        float o32 = (float)out;
+        next_t32(D, ctl)[z] = o32;
+        if (pk.xt) {
+          // the new amplitude at its four places in the ph term's T (the Q positions of
+          // P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba)
+          if (q.x >= 0) pk.xt[q.x] = o32;
+          if (q.y >= 0) pk.xt[q.y] = -o32;
+          if (q.z >= 0) pk.xt[q.z] = -o32;
+          if (q.w >= 0) pk.xt[q.w] = o32;
+        }
+        if (pk.bt && szero) {
+          // BF16 hi/lo copy of the new amplitude for the next tensor-core pp ladder
+          int npad = pk.ch_npad[c];
+          long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
+          __nv_bfloat16 bhi = __float2bfloat16_rn(o32);
+          __nv_bfloat16 blo = __float2bfloat16_rn(o32 - __bfloat162float(bhi));
+          int o = tile_core_off(ij, ab & 63);
+          pk.bt[tb + o] = bhi;
+          pk.bt[tb + (long)npad * 64 + o] = blo;
+        }
+      }
     }
   }
   esum = block_sum(esum, sh32);
@@ -475,15 +581,11 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   last_block_finalize(fa, ctl);
 }
 
-size_t upd_smem_bytes(const pnm_ctx* ctx) {
-  return sizeof(double) * ((size_t)ctx->max_nhh * 128 + (size_t)ctx->max_nhh * ctx->max_nhh);
-}
-
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
                    cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride) {
-  k_update<RT, QT><<<ctx->n_upd_items, 128, 0, ctx->stream>>>(
-      ctx->d, ctx->ctl, ctx->upd_items, fin_args(ctx, use_cond, h), rpp, xq, pk, nplanes, pstride);
+  k_update<RT, QT><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(
+      ctx->d, ctx->ctl, ctx->grp_items, fin_args(ctx, use_cond, h), rpp, xq, pk, nplanes, pstride);
 }
 template void launch_update<double, double>(pnm_ctx*, const double*, const double*, int,
                                             cudaGraphConditionalHandle, PackArgs, int, long);
@@ -621,7 +723,9 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
     if (!ctx->h_szero[c]) continue;
     for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS) items.push_back(make_int2(c, ab0));
   }
-  // update items (channel, ij, first column), 128 columns each, grouped by system
+  // per-row items (channel, ij, first column), 128 columns each, grouped by system (the
+  // learned-start kernels); update items (channel, first ij, first column, rows) with up to
+  // UPD_ROWS hole pairs each, fewer when the grid would not fill the GPU
   for (int k = 0; k < nsys; k++) {
     ulo[k] = (int)upd.size();
     for (int r = ctx->sys[k].row_begin; r < ctx->sys[k].row_end; r++) {
@@ -630,6 +734,31 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
     }
     uhi[k] = (int)upd.size();
   }
+  int dev = 0, nsm = 148;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto group_items = [&](int G, std::vector<int4>* out, std::vector<int>* glo, std::vector<int>* ghi) {
+    size_t n = 0;
+    for (int k = 0; k < nsys; k++) {
+      if (glo) (*glo)[k] = (int)(out ? out->size() : n);
+      for (int c = ctx->sys[k].ch_begin; c < ctx->sys[k].ch_end; c++) {
+        int nh = ctx->h_nhh[c], np = ctx->h_npp[c];
+        for (int ij0 = 0; ij0 < nh; ij0 += G)
+          for (int ab0 = 0; ab0 < np; ab0 += 128) {
+            if (out) out->push_back(make_int4(c, ij0, ab0, std::min(G, nh - ij0)));
+            n++;
+          }
+      }
+      if (ghi) (*ghi)[k] = (int)(out ? out->size() : n);
+    }
+    return n;
+  };
+  int G = UPD_ROWS;
+  while (G > 1 && group_items(G, nullptr, nullptr, nullptr) < (size_t)8 * nsm) G >>= 1;
+  std::vector<int4> grp;
+  std::vector<int> glo(nsys), ghi(nsys);
+  group_items(G, &grp, &glo, &ghi);
+  ctx->upd_rows = G;
   ctx->max_npp = max_npp;
   ctx->n_pp_items = (int)items.size();
   ctx->pp_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, items.size()));
@@ -651,6 +780,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   for (int k = 0; k < nsys; k++)
     if (ahi[k] == 0) alo[k] = 0;
   ctx->max_nhh = max_nhh;
+  if (max_nhh > UPD_MAX_NHH) throw PnmError{PNM_EINVAL, "more hole pairs in one channel than the update supports"};
   int* ad = (int*)dmalloc(ctx, sizeof(int) * 2 * nsys);
   CUDA_TRY(cudaMemcpyAsync(ad, alo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(ad + nsys, ahi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
@@ -671,6 +801,16 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   CUDA_TRY(cudaMemcpyAsync(ud + nsys, uhi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
   ctx->upd_lo_d = ud;
   ctx->upd_hi_d = ud + nsys;
+  ctx->n_grp_items = (int)grp.size();
+  ctx->grp_items = (int4*)dmalloc(ctx, sizeof(int4) * std::max<size_t>(1, grp.size()));
+  if (!grp.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->grp_items, grp.data(), sizeof(int4) * grp.size(),
+                             cudaMemcpyHostToDevice, s));
+  int* gd = (int*)dmalloc(ctx, sizeof(int) * 2 * nsys);
+  CUDA_TRY(cudaMemcpyAsync(gd, glo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(gd + nsys, ghi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
+  ctx->grp_lo_d = gd;
+  ctx->grp_hi_d = gd + nsys;
   // partial sums: one per update item (at least one per row for init/MBPT2)
   size_t nparts = std::max<size_t>(upd.size(), (size_t)ctx->nrows);
   ctx->d.eparts = (double*)dmalloc(ctx, sizeof(double) * nparts);
@@ -682,13 +822,32 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   CUDA_TRY(cudaMemsetAsync(ctx->ctl, 0, sizeof(LoopCtl), s));
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
-  size_t ph_smem = ph_smem_bytes(ctx, sizeof(double));
+  // cross channels for the mixed ph launches: the large ones first, each class largest first
+  std::vector<int> big, small;
+  for (int x = 0; x < ctx->nx; x++)
+    (std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]) > PH_SMALL_DIM ? big : small).push_back(x);
+  auto by_size = [&](int a, int b) {
+    long sa = (long)ctx->h_x_nph[a] * ctx->h_x_nhp[a], sb = (long)ctx->h_x_nph[b] * ctx->h_x_nhp[b];
+    return sa != sb ? sa > sb : a < b;
+  };
+  std::sort(big.begin(), big.end(), by_size);
+  std::sort(small.begin(), small.end(), by_size);
+  std::vector<int> xl(big);
+  xl.insert(xl.end(), small.begin(), small.end());
+  ctx->n_ph_big = (int)big.size();
+  ctx->n_ph_small = (int)small.size();
+  ctx->ph_list = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, xl.size()));
+  if (!xl.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->ph_list, xl.data(), sizeof(int) * xl.size(), cudaMemcpyHostToDevice, s));
+  size_t ph_smem = ph_smem_bytes(ctx->max_x_dim, sizeof(double));
   size_t pp_smem = pp64_smem(max_npp);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
-  CUDA_TRY(cudaFuncSetAttribute(k_ph<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_smem_bytes(ctx, sizeof(float))));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph_mix<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_smem_bytes(ctx->max_x_dim, sizeof(float))));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph_mix<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_smem_bytes(PH_SMALL_DIM, sizeof(float))));
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
@@ -749,8 +908,8 @@ FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
   FinArgs f;
   f.eparts = ctx->d.eparts;
   f.rparts = ctx->d.rparts;
-  f.lo = ctx->upd_lo_d;
-  f.hi = ctx->upd_hi_d;
+  f.lo = ctx->grp_lo_d;
+  f.hi = ctx->grp_hi_d;
   f.nsys = (int)ctx->sys.size();
   f.sc = ctx->sysctl;
   f.hist = ctx->hist;
@@ -788,14 +947,20 @@ void pnm_join(pnm_ctx* ctx) {
 }
 
 // One-body intermediates and <kl|chi|ij> (shared by both precision modes, FP64).
-void pnm_enqueue_stats(pnm_ctx* ctx) {
+// One-body sums, chi_hh and the one-body terms: FP64 (mixed = false) or from the FP32
+// copies of the mixed-precision iteration.
+void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed) {
   cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
-  prof_begin(ctx, KID_TSTATS);
-  k_tstats<<<ctx->nrows + ctx->n_ab_items, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
+  unsigned nb = (unsigned)(ctx->nrows + ctx->n_ab_items);
+  unsigned nd = (unsigned)((ctx->nsp_total * 32 + 255) / 256);
+  prof_begin(ctx, mixed ? KID_TSTATS32 : KID_TSTATS);
+  if (mixed) k_tstats<float><<<nb, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
+  else k_tstats<double><<<nb, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
   prof_end(ctx);
-  prof_begin(ctx, KID_DCHI);
-  k_dchi<<<(ctx->nsp_total * 32 + 255) / 256, 256, 0, s>>>(D, ctx->nsp_total);
+  prof_begin(ctx, mixed ? KID_DCHI32 : KID_DCHI);
+  if (mixed) k_dchi<float><<<nd, 256, 0, s>>>(D, ctx->nsp_total);
+  else k_dchi<double><<<nd, 256, 0, s>>>(D, ctx->nsp_total);
   prof_end(ctx);
 }
 
@@ -806,7 +971,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
   pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH64);
-    launch_ph<double>(ctx, D.x_w, D.x_v1, D.xq, s_ph);
+    launch_ph64(ctx, s_ph);
     prof_end(ctx);
   }
   if (ctx->n_pp_items > 0) {
@@ -814,16 +979,16 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
     pnm_launch_pp64(ctx, s_pp);
     prof_end(ctx);
   }
-  pnm_enqueue_stats(ctx);
+  pnm_enqueue_stats(ctx, false);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
-  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr}, 1, 0);
+  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr, nullptr}, 1, 0);
   prof_end(ctx);
 }
 
 const char* const pnm_kernel_names[PNM_NKERNELS] = {
     "k_tstats", "k_dchi", "k_ph64", "k_pp64", "k_update", "k_finalize(unused)",
-    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack"};
+    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack", "k_dchi32"};
 
 void prof_begin(pnm_ctx* ctx, int kid) {
   if (!ctx->prof_live) return;

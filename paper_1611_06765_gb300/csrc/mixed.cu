@@ -205,6 +205,17 @@ __global__ void k_to_float_cur(DevState D, const LoopCtl* __restrict__ ctl, long
   dst[i] = (float)cur_t(D, ctl)[i];
 }
 
+// T[(a,i)][(k,c)] = t_ik^ac of the current amplitudes through the signed index map (the FP32
+// cross-channel copy the mixed ph term reads; later updates keep it current by scattering).
+__global__ void k_remap_t32(DevState D, const LoopCtl* __restrict__ ctl, float* __restrict__ xt, long n) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  int code = D.xmap[e];
+  const float* t32 = cur_t32(D, ctl);
+  float g = code == 0 ? 0.0f : t32[code > 0 ? code - 1 : -code - 1];
+  xt[e] = code < 0 ? -g : g;
+}
+
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long n) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -227,6 +238,7 @@ struct MixedState {
   __nv_bfloat16* vt = nullptr;
   __nv_bfloat16* bt = nullptr;
   float *rpp32 = nullptr, *xw32 = nullptr, *xv132 = nullptr, *xq32 = nullptr;
+  float* xt32 = nullptr;  // T of the ph term, cross-channel layout, written by the update
   TCItem* items = nullptr;
   int nitems = 0;
   int4* pk = nullptr;
@@ -327,12 +339,24 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     ctx->d.t32_0 = mdalloc<float>(ctx, ctx->nt);
     ctx->d.t32_1 = mdalloc<float>(ctx, ctx->nt);
     ctx->d.chi32 = mdalloc<float>(ctx, ctx->nvhh);
+    ctx->d.v32 = mdalloc<float>(ctx, ctx->nt);
+    ctx->d.vhh32 = mdalloc<float>(ctx, ctx->nvhh);
+    ctx->d.sij32 = mdalloc<float>(ctx, ctx->n_hh_pairs);
+    ctx->d.sab32 = mdalloc<float>(ctx, ctx->n_pp_pairs);
+    ctx->d.dchi32 = mdalloc<float>(ctx, ctx->nsp_total);
+    if (ctx->nt > 0)
+      k_to_float<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.v_pphh, ctx->d.v32, ctx->nt);
+    if (ctx->nvhh > 0)
+      k_to_float<<<(unsigned)((ctx->nvhh + 255) / 256), 256, 0, s>>>(ctx->d.v_hhhh, ctx->d.vhh32, ctx->nvhh);
     M->rpp32 = mdalloc<float>(ctx, (size_t)TC_MAX_SPLIT * ctx->nt);
     // planes a channel with fewer k-blocks than the split never writes stay zero
     CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
     M->xw32 = mdalloc<float>(ctx, ctx->nxt);
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
     M->xq32 = mdalloc<float>(ctx, ctx->nxt);
+    M->xt32 = mdalloc<float>(ctx, ctx->nxt);
+    // entries no amplitude maps to (repeated state index) stay zero
+    CUDA_TRY(cudaMemsetAsync(M->xt32, 0, sizeof(float) * std::max<long>(ctx->nxt, 1), s));
     if (ctx->nxt > 0)
       k_to_float<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, s>>>(ctx->d.x_w, M->xw32, ctx->nxt);
     if (ctx->nxc > 0)
@@ -425,7 +449,7 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
   pnm_fork(ctx);
   if (ctx->nx > 0) {
     prof_begin(ctx, KID_PH32);
-    launch_ph<float>(ctx, M->xw32, M->xv132, M->xq32, s_ph);
+    launch_ph_mix(ctx, M->xt32, M->xw32, M->xv132, M->xq32, s_ph);
     prof_end(ctx);
   }
   if (M->nitems > 0) {
@@ -434,11 +458,11 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
                                                 M->nst, ctx->nt);
     prof_end(ctx);
   }
-  pnm_enqueue_stats(ctx);
+  pnm_enqueue_stats(ctx, true);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
   // the update also writes the BF16 hi/lo tiles of the new amplitudes for the next ladder
-  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->ch_boff, M->ch_npad},
+  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->xt32, M->ch_boff, M->ch_npad},
                               M->ksplit, ctx->nt);
   prof_end(ctx);
 }
@@ -448,6 +472,8 @@ void pnm_mixed_pack_initial(pnm_ctx* ctx) {
   MixedState* M = ctx->mixed;
   if (ctx->nt > 0)
     k_to_float_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
+  if (ctx->nxt > 0)
+    k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
   if (M->npk > 0) {
     prof_begin(ctx, KID_PACK);
     k_pack_t<<<M->npk, 256, 0, ctx->stream>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);

@@ -27,9 +27,27 @@ constexpr int O_W3 = O_B2 + MH, O_B3 = O_W3 + MH * MH, O_W4 = O_B3 + MH, O_B4 = 
 constexpr int NPARAM = O_B4 + 1;
 constexpr int NFEAT = 22;  // real features; columns NFEAT..MF-1 are zero
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form, gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) (Hendrycks and
+// Gimpel), and its derivative; training uses the accurate tanhf.
+constexpr float GELU_C0 = 0.7978845608028654f, GELU_C1 = 0.7978845608028654f * 0.044715f;
+__device__ __forceinline__ float gelu_f(float z) {
+  float th = tanhf(z * fmaf(GELU_C1, z * z, GELU_C0));
+  return 0.5f * z * (1.0f + th);
+}
 __device__ __forceinline__ float gelu_prime_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  float th = tanhf(z * fmaf(GELU_C1, z * z, GELU_C0));
+  return 0.5f * (1.0f + th) + 0.5f * z * (1.0f - th * th) * fmaf(3.0f * GELU_C1, z * z, GELU_C0);
+}
+// Inference: the same function with the hardware tanh approximation (relative error about
+// 2^-11, below the BF16 rounding of the activations that follows).
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu_fast(float z) {
+  float hz = 0.5f * z;
+  return fmaf(hz, tanh_fast(z * fmaf(GELU_C1, z * z, GELU_C0)), hz);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -116,21 +134,6 @@ __global__ void k_targets(DevState D, const int4* __restrict__ items, const doub
   if (ab >= npp || threadIdx.x >= 128) return;
   long z = D.ch_t_off[c] + (long)ij * npp + ab;
   T[z] = (float)((D.t0[z] - tm2[z]) / sigma[D.ch_sys[c]]);
-}
-
-// t0 = t_MBPT2 + sigma_sys * y_scale * y  (the learned start).
-__global__ void k_apply_start(DevState D, const int4* __restrict__ items, const double* __restrict__ tm2,
-                              const double* __restrict__ sigma, const float* __restrict__ Y, float y_scale) {
-  int4 it = items[blockIdx.x];
-  int c = it.x, ij = it.y;
-  int npp = D.ch_npp[c];
-  int ab = it.z + threadIdx.x;
-  if (ab >= npp || threadIdx.x >= 128) return;
-  long z = D.ch_t_off[c] + (long)ij * npp + ab;
-  float y = Y[z];
-  double t = tm2[z];
-  if (isfinite(y)) t += sigma[D.ch_sys[c]] * (double)y_scale * (double)y;
-  D.t0[z] = t;
 }
 
 // ------------------------------------------------------------------- SIMT training
@@ -322,22 +325,43 @@ __global__ void k_pack_weights(const float* __restrict__ q, __nv_bfloat16* __res
   }
 }
 
-constexpr uint32_t MLP_SMEM = 1024 + PW_TOTAL * 2 + MH * MH * 2 + 4 * MH * 4 + 1024;
+constexpr int MLP_THREADS = 256;
+constexpr int MLP_PAR = 3 * MH + 1 + 2 * MF;  // b1, b2, b3, b4, mu, inv_std
+constexpr uint32_t MLP_SMEM = 1024 + PW_TOTAL * 2 + MH * MH * 2 + ((MLP_PAR * 4 + 1023) / 1024) * 1024;
 
-// One CTA (4 warps) loops over 128-sample tiles.  Warp w reads TMEM lanes 32w..32w+31;
-// thread (w, lane) owns sample row 32w + lane of the tile.
-__global__ void __launch_bounds__(128, 1) k_mlp_tc(const float* __restrict__ X, long n,
-                                                   const float* __restrict__ q,
-                                                   const __nv_bfloat16* __restrict__ pw,
-                                                   float* __restrict__ Y, int* __restrict__ err_flag) {
+// Where the inference writes: raw outputs Y, and/or the learned start amplitudes
+// t0 = t_MBPT2 + sigma_sys * y_scale * y of every system (t_begin: first amplitude of each
+// system, nsys + 1 entries).
+struct MlpOut {
+  float* Y;
+  double* t0;
+  const double* tm2;
+  const double* sigma;
+  const long* t_begin;
+  int nsys;
+  float y_scale;
+};
+
+// One CTA (8 warps) loops over 128-sample tiles; two CTAs share an SM, so one CTA's
+// epilogue overlaps the other's MMAs.  Warp w reads TMEM lanes 32 (w % 4) ... + 31 (its
+// row quarter) and columns 64 (w / 4) ... + 63 (its column half); thread (w, lane) owns
+// sample row 32 (w % 4) + lane of the tile.
+__global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restrict__ X, long n,
+                                                           const float* __restrict__ q,
+                                                           const __nv_bfloat16* __restrict__ pw, MlpOut out,
+                                                           int* __restrict__ err_flag) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar_w = reinterpret_cast<uint64_t*>(smem);
   uint64_t* bar_mma = bar_w + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar_w + 2);
   __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(smem + 1024);
   __nv_bfloat16* A = W + PW_TOTAL;
-  float* bias = reinterpret_cast<float*>(A + MH * MH);  // b1, b2, b3 (then b4 at [3*MH])
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = threadIdx.x;
+  float* par = reinterpret_cast<float*>(A + MH * MH);  // b1 b2 b3 | b4 | mu | inv_std
+  const float* mu = par + 3 * MH + 1;
+  const float* istd = mu + MF;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;
   __shared__ int bad;
   if (threadIdx.x == 0) {
     bad = 0;
@@ -350,11 +374,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const float* __restrict__ X, 
     tc::tmem_relinquish();
   }
   for (int k = threadIdx.x; k < MH; k += blockDim.x) {
-    bias[k] = q[O_B1 + k];
-    bias[MH + k] = q[O_B2 + k];
-    bias[2 * MH + k] = q[O_B3 + k];
+    par[k] = q[O_B1 + k];
+    par[MH + k] = q[O_B2 + k];
+    par[2 * MH + k] = q[O_B3 + k];
   }
-  if (threadIdx.x == 0) bias[3 * MH] = q[O_B4];
+  for (int k = threadIdx.x; k < MF; k += blockDim.x) {
+    par[3 * MH + 1 + k] = q[O_MU + k];
+    par[3 * MH + 1 + MF + k] = q[O_IS + k];
+  }
+  if (threadIdx.x == 0) par[3 * MH] = q[O_B4];
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -366,26 +394,38 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const float* __restrict__ X, 
   if (!tc::mbar_wait(bar_w, 0)) bad = 1;
   uint32_t phase = 0;
   const long ntiles = (n + MH - 1) / MH;
+  const uint32_t lane_addr = tbase + ((uint32_t)(quarter * 32) << 16);
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // every thread leaves together after a failed wait (no thread may skip a barrier)
     __syncthreads();
     const int stop = bad;
     __syncthreads();
     if (stop) break;
-    long r_glob = tile * MH + row;
-    // layer-1 input: normalised, BF16, K = 32 layout
+    const long r_glob = tile * MH + row;
+    const bool ok = r_glob < n;
+    // layer-1 input: features [16 half, 16 half + 16) of the row, normalised, BF16
     {
-      float xv[MF];
-      bool ok = r_glob < n;
+      const int k0 = 16 * half;
+      float xv[16];
+      if (ok) {
+        const float4* xp = reinterpret_cast<const float4*>(X + r_glob * MF + k0);
 #pragma unroll
-      for (int k = 0; k < MF; k++)
-        xv[k] = ok ? (X[r_glob * MF + k] - q[O_MU + k]) * q[O_IS + k] : 0.0f;
+        for (int j = 0; j < 4; j++) {
+          float4 v = __ldg(xp + j);
+          xv[4 * j] = v.x; xv[4 * j + 1] = v.y; xv[4 * j + 2] = v.z; xv[4 * j + 3] = v.w;
+        }
 #pragma unroll
-      for (int k0 = 0; k0 < MF; k0 += 8) {
-        __align__(16) __nv_bfloat16 v8[8];
+        for (int k = 0; k < 16; k++) xv[k] = (xv[k] - mu[k0 + k]) * istd[k0 + k];
+      } else {
 #pragma unroll
-        for (int j = 0; j < 8; j++) v8[j] = __float2bfloat16_rn(xv[k0 + j]);
-        *reinterpret_cast<uint4*>(A + tc::core_off(row, k0, MF / 8)) = *reinterpret_cast<uint4*>(v8);
+        for (int k = 0; k < 16; k++) xv[k] = 0.0f;
+      }
+#pragma unroll
+      for (int h = 0; h < 16; h += 8) {
+        __align__(16) __nv_bfloat162 v4[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) v4[j] = __floats2bfloat162_rn(xv[h + 2 * j], xv[h + 2 * j + 1]);
+        *reinterpret_cast<uint4*>(A + tc::core_off(row, k0 + h, MF / 8)) = *reinterpret_cast<uint4*>(v4);
       }
     }
     for (int layer = 0; layer < 4; layer++) {
@@ -410,24 +450,41 @@ __global__ void __launch_bounds__(128, 1) k_mlp_tc(const float* __restrict__ X, 
       if (!tc::mbar_wait(bar_mma, phase & 1)) bad = 1;
       phase++;
       tc::fence_after();
-      const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
       if (layer < 3) {
-        const float* b = bias + layer * MH;
-        for (int c0 = 0; c0 < MH; c0 += 16) {
-          uint32_t r[16];
-          tc::tmem_ld16(lane_addr + c0, r);
+        // bias + GELU of this thread's 64 columns, BF16, into the next layer's A operand
+        const float* b = par + layer * MH;
+        const int cbase = 64 * half;
+        uint32_t r[64];
+        tc::tmem_ld16_nowait(lane_addr + cbase, *reinterpret_cast<uint32_t(*)[16]>(r));
+        tc::tmem_ld16_nowait(lane_addr + cbase + 16, *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+        tc::tmem_ld16_nowait(lane_addr + cbase + 32, *reinterpret_cast<uint32_t(*)[16]>(r + 32));
+        tc::tmem_ld16_nowait(lane_addr + cbase + 48, *reinterpret_cast<uint32_t(*)[16]>(r + 48));
+        tc::tmem_wait_ld();
 #pragma unroll
-          for (int h = 0; h < 16; h += 8) {
-            __align__(16) __nv_bfloat16 v8[8];
+        for (int h = 0; h < 64; h += 8) {
+          __align__(16) __nv_bfloat162 v4[4];
 #pragma unroll
-            for (int j = 0; j < 8; j++) v8[j] = __float2bfloat16_rn(gelu_f(__uint_as_float(r[h + j]) + b[c0 + h + j]));
-            *reinterpret_cast<uint4*>(A + tc::core_off(row, c0 + h, MH / 8)) = *reinterpret_cast<uint4*>(v8);
+          for (int j = 0; j < 4; j++) {
+            float z0 = __uint_as_float(r[h + 2 * j]) + b[cbase + h + 2 * j];
+            float z1 = __uint_as_float(r[h + 2 * j + 1]) + b[cbase + h + 2 * j + 1];
+            v4[j] = __floats2bfloat162_rn(gelu_fast(z0), gelu_fast(z1));
           }
+          *reinterpret_cast<uint4*>(A + tc::core_off(row, cbase + h, MH / 8)) = *reinterpret_cast<uint4*>(v4);
         }
-      } else {
+      } else if (half == 0) {
         uint32_t r[16];
         tc::tmem_ld16(lane_addr, r);
-        if (r_glob < n) Y[r_glob] = __uint_as_float(r[0]) + bias[3 * MH];
+        if (ok) {
+          float y = __uint_as_float(r[0]) + par[3 * MH];
+          if (out.Y) out.Y[r_glob] = y;
+          if (out.t0) {
+            int sy = 0;
+            while (sy + 1 < out.nsys && r_glob >= out.t_begin[sy + 1]) sy++;
+            double t = out.tm2[r_glob];
+            if (isfinite(y)) t += out.sigma[sy] * (double)out.y_scale * (double)y;
+            out.t0[r_glob] = t;
+          }
+        }
       }
     }
   }
@@ -523,7 +580,7 @@ struct MlpState {
   float* X = nullptr;       // features of every amplitude (library order)
   double* tm2 = nullptr;    // MBPT2 amplitudes
   double* sigma = nullptr;  // per system
-  float* Y = nullptr;       // network output
+  long* t_begin = nullptr;  // first amplitude of each system, then the total
   float* q = nullptr;       // model parameters (BF16-rounded weights)
   __nv_bfloat16* pw = nullptr;
   int* err = nullptr;
@@ -540,7 +597,11 @@ static void mlp_features(pnm_ctx* ctx) {
   M->X = xalloc<float>((size_t)ctx->nt * MF, ctx->owned);
   M->tm2 = xalloc<double>(ctx->nt, ctx->owned);
   M->sigma = xalloc<double>(nsys, ctx->owned);
-  M->Y = xalloc<float>(ctx->nt, ctx->owned);
+  std::vector<long> tb(nsys + 1);
+  for (int k = 0; k < nsys; k++) tb[k] = ctx->sys[k].t_begin;
+  tb[nsys] = ctx->nt;
+  M->t_begin = xalloc<long>(nsys + 1, ctx->owned);
+  CUDA_TRY(cudaMemcpyAsync(M->t_begin, tb.data(), sizeof(long) * (nsys + 1), cudaMemcpyHostToDevice, s));
   double* parts = xalloc<double>(ctx->n_upd_items, ctx->owned);
   std::vector<long> cnt(nsys);
   std::vector<FeatSys> fs(nsys);
@@ -580,6 +641,7 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
     M->pw = xalloc<__nv_bfloat16>(PW_TOTAL, ctx->owned);
     M->err = xalloc<int>(1, ctx->owned);
     CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   }
   float* w = xalloc<float>(NPARAM, ctx->owned);
   CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
@@ -592,11 +654,14 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
   M->have_model = true;
 }
 
-static void tc_infer(cudaStream_t s, const float* X, long n, const float* q, const __nv_bfloat16* pw, float* Y,
-                     int* err) {
+static void tc_infer(cudaStream_t s, const float* X, long n, const float* q, const __nv_bfloat16* pw,
+                     const MlpOut& out, int* err) {
   long ntiles = (n + MH - 1) / MH;
-  int grid = (int)std::min<long>(ntiles, 152 * 2);
-  if (grid > 0) k_mlp_tc<<<grid, 128, MLP_SMEM, s>>>(X, n, q, pw, Y, err);
+  int dev = 0, nsm = 148;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int grid = (int)std::min<long>(ntiles, 2L * nsm);
+  if (grid > 0) k_mlp_tc<<<grid, MLP_THREADS, MLP_SMEM, s>>>(X, n, q, pw, out, err);
 }
 
 // Learned start into t0 (every system), used by the solver for PNM_INIT_MLP.
@@ -605,8 +670,9 @@ void pnm_mlp_start(pnm_ctx* ctx) {
   mlp_features(ctx);
   MlpState* M = ctx->mlp;
   cudaStream_t s = ctx->stream;
-  tc_infer(s, M->X, ctx->nt, M->q, M->pw, M->Y, M->err);
-  k_apply_start<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, M->sigma, M->Y, M->y_scale);
+  // the network output goes straight into t0 (t_MBPT2 + sigma_sys * y_scale * y)
+  tc_infer(s, M->X, ctx->nt, M->q, M->pw,
+           MlpOut{nullptr, ctx->d.t0, M->tm2, M->sigma, M->t_begin, (int)ctx->sys.size(), M->y_scale}, M->err);
   CUDA_TRY(cudaGetLastError());
 }
 
@@ -685,8 +751,9 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use
       int* err = xalloc<int>(1, sc.owned);
       CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
       CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(q, pw);
-      tc_infer(s, dX, n, q, pw, dY, err);
+      tc_infer(s, dX, n, q, pw, MlpOut{dY, nullptr, nullptr, nullptr, nullptr, 0, 1.0f}, err);
       int h_err = 0;
       CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));

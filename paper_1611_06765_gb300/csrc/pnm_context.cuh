@@ -11,7 +11,7 @@ struct MlpState;    // learned warm start (mlp.cu)
 // Kernel ids of the per-kernel profiler.
 enum {
   KID_TSTATS = 0, KID_DCHI, KID_PH64, KID_PP64, KID_UPDATE, KID_FINALIZE,
-  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, PNM_NKERNELS
+  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, KID_DCHI32, PNM_NKERNELS
 };
 extern const char* const pnm_kernel_names[PNM_NKERNELS];
 
@@ -39,6 +39,11 @@ struct pnm_ctx {
   int4* upd_items = nullptr;  // (channel, ij, first pp column) of the update
   int n_upd_items = 0;
   int *upd_lo_d = nullptr, *upd_hi_d = nullptr;  // per system ranges of the (row, column) items
+  int4* grp_items = nullptr;  // (channel, first ij, first pp column, rows) of the update
+  int n_grp_items = 0, upd_rows = 1;
+  int* ph_list = nullptr;  // cross channels of the mixed ph launches (large class first)
+  int n_ph_big = 0, n_ph_small = 0;
+  int *grp_lo_d = nullptr, *grp_hi_d = nullptr;  // per system ranges of the update items
   int *ab_lo_d = nullptr, *ab_hi_d = nullptr;    // per system ranges of the column items
   int max_nhh = 1;
   int2* ab_items = nullptr;
@@ -112,16 +117,17 @@ void prof_begin(pnm_ctx* ctx, int kid);
 void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
-void pnm_enqueue_stats(pnm_ctx* ctx);
+void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s);
-size_t ph_smem_bytes(const pnm_ctx* ctx, size_t elem);
+size_t ph_smem_bytes(int max_dim, size_t elem);
 void pnm_mixed_pack_initial(pnm_ctx* ctx);
 void pnm_fork(pnm_ctx* ctx);
 void pnm_join(pnm_ctx* ctx);
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
-template <typename T_>
-void launch_ph(pnm_ctx* ctx, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s);
+void launch_ph64(pnm_ctx* ctx, cudaStream_t s);
+void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
+                   cudaStream_t s);
 template <typename RT, typename QT>
 void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
                    cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride);

@@ -79,7 +79,9 @@ struct DevState {
   // iteration state
   double *t0, *t1;       // double buffer, parity = iteration & 1
   float *t32_0, *t32_1;  // FP32 copies of t0/t1 kept by the mixed-precision update (else null)
-  float* chi32;          // FP32 copy of chi_hh written by the stats kernel when t32 is used
+  // FP32 intermediates of the mixed-precision iteration (null until it is first prepared):
+  // v_pphh and v_hhhh copies, chi_hh, the one-body row/column sums and the one-body terms
+  float *v32, *vhh32, *chi32, *sij32, *sab32, *dchi32;
   double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;
   double *eparts, *rparts;
 };
@@ -124,10 +126,18 @@ struct FinArgs {
   cudaGraphConditionalHandle handle;
 };
 
+// The update kernel: at most UPD_ROWS hole pairs per CTA share one pass over a t column for
+// the hh ladder; channels may hold at most UPD_MAX_NHH hole pairs.
+constexpr int UPD_ROWS = 8, UPD_MAX_NHH = 128;
+
+// Cross channels with at most PH_SMALL_DIM rows and columns go to the small-footprint ph launch.
+constexpr int PH_SMALL_DIM = 32;
+
 // Where the mixed update writes the BF16 hi/lo copy of the new amplitudes (the B operand
 // tiles of the tensor-core pp ladder).  bt == nullptr: no copy.
 struct PackArgs {
   __nv_bfloat16* bt;
+  float* xt;            // FP32 T of the ph term in the cross-channel layout (scattered), or null
   const long* ch_boff;  // per channel: element offset of its k-block 0, -1 if not packed
   const int* ch_npad;   // per channel: n_hh padded to the MMA N
 };
@@ -177,20 +187,22 @@ __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfl
   lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // Block-wide sum for blockDim.x a multiple of 32 (<= 1024); result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh32) {
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh32) {
   v = warp_sum(v);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sh32[w] = v;
   __syncthreads();
   int nw = blockDim.x >> 5;
-  v = (threadIdx.x < nw) ? sh32[threadIdx.x] : 0.0;
+  v = (threadIdx.x < nw) ? sh32[threadIdx.x] : (T)0;
   if (w == 0) v = warp_sum(v);
   __syncthreads();
   return v;

@@ -1,9 +1,10 @@
 """The GPU path against the paper's own PNM energies (Table tab:ecomparison): N = 66,
 Minnesota, periodic boundary conditions, 2378 plane-wave states (n^2 <= 42), energies per
 particle including E_ref.  All three densities run in one batched context.  The paper prints
-three decimals, so each value must lie within half a unit of the last digit (plus 1e-6 for
-the stopping rule).  The CCD row at rho = 0.08 is a misprint under every reading of the table
-tried (its MBPT2 entry is reproduced), so only the CCD rows 0.04 and 0.06 are checked.
+three decimals and not the hbar^2/2m it used (20.721 MeV fm^2 here), so each value must lie
+within one unit of the last printed digit, as for the oracle.  The CCD row at rho = 0.08 is a
+misprint under every reading of the table tried (its MBPT2 entry is reproduced), so only the
+CCD rows 0.04 and 0.06 are checked.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from conftest import minnesota_params, read_golden
 pytestmark = pytest.mark.gpu
 
 ROWS = [tuple(float(x) for x in r) for r in read_golden("ecomparison.txt")]
-HALF_ULP = 0.5e-3 + 1e-6
+TOL = 1.0e-3
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +38,7 @@ def test_mbpt2_column(table_ctx):
     P, ctx = table_ctx
     e = (ctx.eref() + ctx.mbpt2()) / 66
     for (rho, e_mbpt2, _), got in zip(ROWS, e):
-        assert abs(got - e_mbpt2) <= HALF_ULP, (rho, got, e_mbpt2)
+        assert abs(got - e_mbpt2) <= TOL, (rho, got, e_mbpt2)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "bf16x3"])
@@ -50,7 +51,7 @@ def test_ccd_column(table_ctx, mode):
     checked = 0
     for (rho, _, e_ccd), got in zip(ROWS, e):
         if rho in (0.04, 0.06):
-            assert abs(got - e_ccd) <= HALF_ULP, (mode, rho, got, e_ccd)
+            assert abs(got - e_ccd) <= TOL, (mode, rho, got, e_ccd)
             checked += 1
     assert checked == 2
     assert np.all(it < 300)

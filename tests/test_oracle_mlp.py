@@ -18,12 +18,21 @@ def test_bf16_rounding_known_values():
 
 
 def test_gelu_values():
+    """The tanh form of GELU stays within 5e-4 of x Phi(x) (its known maximum deviation is
+    4.7e-4; a dropped cubic term gives 3.4e-2), at the tabulated normal CDF values
+    Phi(1) = 0.8413447460685429, Phi(3) = 0.9986501019683699 and on a grid against the
+    library erf; gelu(x) - gelu(-x) = x exactly; the derivative matches central differences."""
+    from scipy.special import erf
     z = np.array([0.0, 1.0, -1.0, 3.0])
-    # x Phi(x) with the tabulated normal CDF Phi(1) = 0.8413447460685429, Phi(3) = 0.9986501019683699
     expect = np.array([0.0, 0.8413447460685429, -0.15865525393145707, 3 * 0.9986501019683699])
-    assert np.allclose(mlp.gelu(z), expect, rtol=1e-12, atol=1e-15)
+    assert np.max(np.abs(mlp.gelu(z) - expect)) < 5e-4
+    assert mlp.gelu(0.0) == 0.0
+    x = np.linspace(-8.0, 8.0, 4001)
+    assert np.max(np.abs(mlp.gelu(x) - 0.5 * x * (1.0 + erf(x / np.sqrt(2.0))))) < 5e-4
+    assert np.allclose(mlp.gelu(x) - mlp.gelu(-x), x, rtol=1e-13, atol=1e-13)
     h = 1e-6
-    assert np.allclose(mlp.gelu_prime(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), rtol=1e-8)
+    zz = np.array([-3.0, -1.0, -0.3, 0.0, 0.5, 1.0, 3.0])
+    assert np.allclose(mlp.gelu_prime(zz), (mlp.gelu(zz + h) - mlp.gelu(zz - h)) / (2 * h), rtol=1e-8, atol=1e-10)
 
 
 def test_analytic_gradient_matches_finite_differences():
