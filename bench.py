@@ -171,13 +171,22 @@ def algorithmic_cost(ctx, kernel):
         byts = float((npp[szero] ** 2).sum()) * vb + float((nhh[szero] * npp[szero]).sum()) * (tb + 8.0)
         flops = 2.0 * float((nhh[szero] * npp[szero] ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
         return byts, flops
-    if kernel in ("k_ph64", "k_ph32"):
-        eb = 8.0 if kernel == "k_ph64" else 4.0
-        byts = float((nph * nhp).sum()) * (4 + eb + eb) + float((nhp * nhp).sum()) * eb + nt * eb
+    if kernel == "k_ph64":
+        # index map and gathered t, W, V1, Q
+        byts = float((nph * nhp).sum()) * (4 + 8 + 8 + 8) + float((nhp * nhp).sum()) * 8
         flops = 2.0 * float((nhp * nhp * nph + nph * nhp * nhp).sum())
         return byts, flops
-    if kernel in ("k_update", "k_update_mix"):
-        return nt * (8 + 8 + 8 + 16 + 4 * 8 + 8 + 8), nt * 20.0
+    if kernel == "k_ph32":
+        # T (scattered by the update), W, V1 read; Q written
+        byts = float((nph * nhp).sum()) * (4 + 4 + 4) + float((nhp * nhp).sum()) * 4
+        flops = 2.0 * float((nhp * nhp * nph + nph * nhp * nhp).sum())
+        return byts, flops
+    if kernel == "k_update":
+        # t, v, eps, 1/eps, qmap, rpp, four Q values, t_next
+        return nt * (8 + 8 + 8 + 8 + 16 + 8 + 4 * 8 + 8), nt * 20.0
+    if kernel == "k_update_mix":
+        # t, v, 1/eps, qmap, t32, rpp32, four Q values read; t, t32, BF16 hi/lo, four T entries written
+        return nt * (8 + 8 + 8 + 16 + 4 + 4 + 4 * 4 + 8 + 4 + 4 + 4 * 4), nt * 20.0
     if kernel in ("k_tstats", "k_tstats32"):
         return nt * 8 * 2 + float((nhh * nhh).sum()) * 16, nt * 2.0 * (2 + nhh.mean())
     return nt * 8.0, 0.0
@@ -192,8 +201,6 @@ def read_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-# FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def oracle_solve(N, rho, n2max):
@@ -407,14 +414,25 @@ def run_ours(a):
     kavg_s = ktot / kn / 1e3
     byts, flops = algorithmic_cost(ctx, kname)
     hbm, bf16, src = read_peaks()
+    fp64_peak = P.measure_fma_peak(True, stream.cuda_stream)
+    fp32_peak = P.measure_fma_peak(False, stream.cuda_stream)
     if kname in ("k_pp64", "k_ph64"):
-        roof = {"bound": "alu", "achieved": flops / kavg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 FMA rate from SM count and clock"}
+        roof = {"bound": "alu", "achieved": flops / kavg_s / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "peak_source": "measured FP64 FMA rate (pnm_measure_fma_peak)"}
     else:
         roof = {"bound": "hbm", "achieved": byts / kavg_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "%s hbm_gbs" % src}
     roof.update(frac=roof["achieved"] / roof["peak"], traffic=None, kernel=kname, kernel_avg_us=kavg_s * 1e6,
-                algorithmic_bytes=byts, algorithmic_flops=flops)
+                algorithmic_bytes=byts, algorithmic_flops=flops,
+                measured_fma_peaks_tflops={"fp64": fp64_peak, "fp32": fp32_peak})
+    # the FP64 refinement contractions against the measured FP64 FMA rate
+    for k in ("k_pp64", "k_ph64", "k_ph32"):
+        if k in stats and k != kname:
+            tk = stats[k][0] / stats[k][1] / 1e3
+            bk, fk = algorithmic_cost(ctx, k)
+            pk = fp64_peak if k != "k_ph32" else fp32_peak
+            roof[k] = {"bound": "alu", "achieved": fk / tk / 1e12, "peak": pk, "unit": "TFLOP/s",
+                       "frac": fk / tk / 1e12 / pk, "kernel_avg_us": tk * 1e6}
     if "k_pp_tc" in stats and kname != "k_pp_tc":
         t_tc = stats["k_pp_tc"][0] / stats["k_pp_tc"][1] / 1e3
         b_tc, f_tc = algorithmic_cost(ctx, "k_pp_tc")

@@ -67,7 +67,10 @@ typedef struct {
     double tol_dE;        /* stop when |dE^(n+1) - dE^(n)| < tol_dE (total, MeV) */
     double tol_dE_per_N;  /* and/or when |dE^(n+1) - dE^(n)| / N < tol_dE_per_N (<= 0: unused) */
     int max_iter;         /* iteration cap (PNM_ENOTCONV when reached) */
-    int refine_sweeps;    /* FP64 sweeps after a mixed-precision solve */
+    int refine_sweeps;    /* FP64 sweeps after a mixed-precision solve has converged: exactly
+                             this many FP64 updates, the FP64 stopping test applied from the
+                             last of them on (further FP64 updates, at most max_iter, until it
+                             passes) */
     int init;             /* PNM_INIT_* */
     int host_loop;        /* 0: device-side loop in one CUDA graph; 1: host checks each iteration */
 } pnm_solve_opts;

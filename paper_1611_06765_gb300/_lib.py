@@ -98,6 +98,7 @@ def load(path=None):
     L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, vp]
     L.pnm_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_float), ip]
     L.pnm_selftest_timeout.argtypes = [vp]
+    L.pnm_measure_fma_peak.argtypes = [C.c_int, vp, dp]
     L.pnm_set_profiling.argtypes = [vp, C.c_int]
     L.pnm_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_char_p), dp, ip]
     L.pnm_last_error.restype = C.c_char_p

@@ -204,76 +204,88 @@ __device__ __forceinline__ void ph_contract(T_* Ts, T_* Xt, T_* Cs, int nph, int
   }
 }
 
-// FP64 ph term: one CTA per cross channel; T[(a,i)][(k,c)] = t_ik^ac gathered through the
-// signed index map.
-__global__ void __launch_bounds__(128) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
-                                            const double* __restrict__ xw, const double* __restrict__ xv1,
-                                            double* __restrict__ xq) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double* sm = reinterpret_cast<double*>(smraw);
-  int x = blockIdx.x;
-  int nph = D.x_nph[x], nhp = D.x_nhp[x];
-  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
-  const double* __restrict__ t = cur_t(D, ctl);
-  double* Ts = sm;
-  double* Xt = Ts + P4 * H4;
-  double* Cs = Xt + P4 * H4;
-  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  // Four elements per thread per step so that four independent gathers are in flight.
-  for (int e0 = threadIdx.x; e0 < P4 * H4; e0 += 4 * blockDim.x) {
-    int code[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int e = e0 + q * blockDim.x;
-      int u = e / H4, s = e % H4;
-      code[q] = (e < P4 * H4 && u < nph && s < nhp) ? D.xmap[to + (long)u * nhp + s] : 0;
-    }
-    double tv[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int cd = code[q], a = cd > 0 ? cd - 1 : -cd - 1;
-      double g = cd == 0 ? 0.0 : t[a];
-      tv[q] = cd < 0 ? -g : g;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int e = e0 + q * blockDim.x;
-      if (e >= P4 * H4) continue;
-      int u = e / H4, s = e % H4;
-      Ts[e] = tv[q];
-      Xt[e] = (u < nph && s < nhp) ? xw[wo + (long)u * nhp + s] : 0.0;  // W^T[u][s] = W[s][u]
-    }
+// Element e of a cross channel's T: gathered from the current amplitudes through the signed
+// index map (GATHER: FP64 iteration) or read from the copy the update scatters (mixed).
+template <typename T_, bool GATHER>
+__device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__ tcur,
+                                   const T_* __restrict__ xt, long e) {
+  if constexpr (GATHER) {
+    int cd = D.xmap[e];
+    T_ g = cd == 0 ? (T_)0 : (T_)tcur[cd > 0 ? cd - 1 : -cd - 1];
+    return cd < 0 ? -g : g;
+  } else {
+    return xt[e];
   }
-  __syncthreads();
-  ph_contract<double, 128>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
 }
 
-// FP32 ph term of the mixed-precision iteration.  T comes ready in the cross-channel layout
-// (xt, scattered by the previous update through the inverse of the index map), so staging is
-// plain coalesced loads.  xlist: the cross channels of this launch (one size class).
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ph_mix(DevState D, const int* __restrict__ xlist,
-                                               const float* __restrict__ xt, const float* __restrict__ xw,
-                                               const float* __restrict__ xv1, float* __restrict__ xq) {
+// One CTA (NT threads) per cross channel of the launch's size class.  Staging: Ts = T,
+// Xt = W^T (W is stored transposed), both zero-padded to multiples of 4.
+template <typename T_, int NT, bool GATHER>
+__global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
+                                           const int* __restrict__ xlist, const T_* __restrict__ xt,
+                                           const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                           T_* __restrict__ xq) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* sm = reinterpret_cast<float*>(smraw);
+  T_* sm = reinterpret_cast<T_*>(smraw);
   int x = xlist[blockIdx.x];
   int nph = D.x_nph[x], nhp = D.x_nhp[x];
   int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
-  float* Ts = sm;
-  float* Xt = Ts + P4 * H4;
-  float* Cs = Xt + P4 * H4;
+  T_* Ts = sm;
+  T_* Xt = Ts + P4 * H4;
+  T_* Cs = Xt + P4 * H4;
   long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
 #pragma unroll 4
   for (int e = threadIdx.x; e < P4 * H4; e += NT) {
     int u = e / H4, s = e % H4;
     bool in = u < nph && s < nhp;
     long o = (long)u * nhp + s;
-    Ts[e] = in ? xt[to + o] : 0.0f;
-    Xt[e] = in ? xw[wo + o] : 0.0f;  // W^T[u][s] = W[s][u]
+    Ts[e] = in ? ph_t<T_, GATHER>(D, tcur, xt, to + o) : (T_)0;
+    Xt[e] = in ? xw[wo + o] : (T_)0;  // W^T[u][s] = W[s][u]
   }
   __syncthreads();
-  ph_contract<float, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
+  ph_contract<T_, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
+}
+
+// Cross channels of at most PH_WARP_DIM rows/columns: one warp per channel with its own
+// shared buffers (stride PH_WARP_DIM), no block-wide synchronisation.
+constexpr int PH_WARPS = 8;
+template <typename T_, bool GATHER>
+__global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const LoopCtl* __restrict__ ctl,
+                                                           const int* __restrict__ xlist, int nlist,
+                                                           const T_* __restrict__ xt, const T_* __restrict__ xw,
+                                                           const T_* __restrict__ xv1, T_* __restrict__ xq) {
+  constexpr int S = PH_WARP_DIM;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * PH_WARPS + w;
+  if (idx >= nlist) return;  // whole warps leave; nothing below synchronises the block
+  const int x = xlist[idx];
+  const int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+  T_* Ts = reinterpret_cast<T_*>(smraw) + (size_t)w * 3 * S * S;  // T[u][s]
+  T_* Ws = Ts + S * S;                                             // W^T[u][r] = W[r][u]
+  T_* Cs = Ws + S * S;                                             // C[r][s]
+  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
+  for (int e = lane; e < nph * nhp; e += 32) {
+    int u = e / nhp, c = e % nhp;
+    Ts[u * S + c] = ph_t<T_, GATHER>(D, tcur, xt, to + e);
+    Ws[u * S + c] = xw[wo + e];
+  }
+  __syncwarp();
+  for (int e = lane; e < nhp * nhp; e += 32) {
+    int r = e / nhp, c = e % nhp;
+    T_ acc = 0;
+    for (int u = 0; u < nph; u++) acc += Ws[u * S + r] * Ts[u * S + c];
+    Cs[r * S + c] = xv1[co + e] + (T_)0.5 * acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < nph * nhp; e += 32) {
+    int r = e / nhp, c = e % nhp;
+    T_ acc = 0;
+    for (int u = 0; u < nhp; u++) acc += Ts[r * S + u] * Cs[u * S + c];
+    xq[to + e] = acc;
+  }
 }
 
 size_t ph_smem_bytes(int max_dim, size_t elem) {
@@ -281,21 +293,49 @@ size_t ph_smem_bytes(int max_dim, size_t elem) {
   return elem * 3 * m4 * m4;
 }
 
-void launch_ph64(pnm_ctx* ctx, cudaStream_t s) {
-  k_ph<<<ctx->nx, 128, ph_smem_bytes(ctx->max_x_dim, sizeof(double)), s>>>(ctx->d, ctx->ctl, ctx->d.x_w,
-                                                                          ctx->d.x_v1, ctx->d.xq);
+static size_t ph_warp_smem(size_t elem) { return elem * PH_WARPS * 3 * PH_WARP_DIM * PH_WARP_DIM; }
+
+// The ph term in three size classes: cross channels larger than PH_SMALL_DIM (256-thread
+// CTAs), those larger than PH_WARP_DIM (128-thread CTAs, small shared footprint) and the rest
+// (one warp each).
+template <typename T_, bool GATHER>
+static void launch_ph_classes(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
+  if (ctx->n_ph_big > 0)
+    k_ph<T_, 256, GATHER><<<ctx->n_ph_big, 256, ph_smem_bytes(ctx->max_x_dim, sizeof(T_)), s>>>(
+        ctx->d, ctx->ctl, ctx->ph_list, xt, xw, xv1, xq);
+  if (ctx->n_ph_mid > 0)
+    k_ph<T_, 128, GATHER><<<ctx->n_ph_mid, 128, ph_smem_bytes(PH_SMALL_DIM, sizeof(T_)), s>>>(
+        ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph_big, xt, xw, xv1, xq);
+  if (ctx->n_ph_small > 0)
+    k_ph_warp<T_, GATHER><<<(ctx->n_ph_small + PH_WARPS - 1) / PH_WARPS, PH_WARPS * 32, ph_warp_smem(sizeof(T_)),
+                            s>>>(ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph_big + ctx->n_ph_mid, ctx->n_ph_small,
+                                 xt, xw, xv1, xq);
 }
 
-// Mixed ph: cross channels larger than PH_SMALL_DIM in one launch of 256-thread CTAs, the
-// others in a second launch with a small shared footprint (many CTAs per SM).
+template <typename T_, bool GATHER>
+static void ph_attributes(const pnm_ctx* ctx) {
+  CUDA_TRY(cudaFuncSetAttribute(k_ph<T_, 256, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_smem_bytes(ctx->max_x_dim, sizeof(T_))));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph<T_, 128, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_smem_bytes(PH_SMALL_DIM, sizeof(T_))));
+  CUDA_TRY(cudaFuncSetAttribute(k_ph_warp<T_, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ph_warp_smem(sizeof(T_))));
+}
+
+// FP64 ph: T gathered from the current FP64 amplitudes.
+void launch_ph64(pnm_ctx* ctx, cudaStream_t s) {
+  launch_ph_classes<double, true>(ctx, nullptr, ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
+}
+
+// Mixed ph: T read from the copy the update scatters.
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s) {
-  if (ctx->n_ph_big > 0)
-    k_ph_mix<256><<<ctx->n_ph_big, 256, ph_smem_bytes(ctx->max_x_dim, sizeof(float)), s>>>(
-        ctx->d, ctx->ph_list, xt, xw, xv1, xq);
-  if (ctx->n_ph_small > 0)
-    k_ph_mix<128><<<ctx->n_ph_small, 128, ph_smem_bytes(PH_SMALL_DIM, sizeof(float)), s>>>(
-        ctx->d, ctx->ph_list + ctx->n_ph_big, xt, xw, xv1, xq);
+  launch_ph_classes<float, false>(ctx, xt, xw, xv1, xq, s);
+}
+
+void pnm_ph_attributes(const pnm_ctx* ctx) {
+  ph_attributes<double, true>(ctx);
+  ph_attributes<float, false>(ctx);
 }
 
 // ---------------------------------------------------------------------- pp ladder FP64
@@ -400,7 +440,7 @@ __device__ void finalize_systems(const FinArgs& f, LoopCtl* ctl) {
         double diff = fabs(e - S.e_old);
         S.e_old = e;
         if (!isfinite(e) || !isfinite(r)) bad = 1;
-        if (diff < S.tol) S.done = 1;
+        if (diff < S.tol && ctl->iter + 1 >= ctl->min_iter) S.done = 1;
       }
       if (!S.done) all_done = 0;
     }
@@ -445,127 +485,226 @@ __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
 // Eq. (ccd3): the bracket collects v, the non-eps parts of the one-body terms, the pp and hh
 // ladders and P(ij)P(ab) Q; then t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.
 // The residual of the amplitude equation is R = bracket - eps_ij^ab t.
-template <typename RT, typename QT>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
-                                                const int4* __restrict__ items, FinArgs fa,
-                                                const RT* __restrict__ rpp,
-                                                const QT* __restrict__ xq, PackArgs pk, int nplanes,
-                                                long pstride) {
-  // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng
-  __shared__ QT chs[UPD_MAX_NHH][UPD_ROWS];
+                                                const int4* __restrict__ items, FinArgs fa) {
+  // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng;
+  // per row: d_i + d_j of the one-body term
+  __shared__ double chs[UPD_MAX_NHH][UPD_ROWS];
+  __shared__ double row_dij[UPD_ROWS];
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
   int c = it.x, ij0 = it.y, ng = it.w;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   int ab = it.z + threadIdx.x;
-  const SysCtl* __restrict__ sc = fa.sc;
-  bool frozen = sc[D.ch_sys[c]].done != 0;
+  bool frozen = fa.sc[D.ch_sys[c]].done != 0;
   bool szero = D.ch_szero[c] != 0;
-  constexpr bool MIX = std::is_same<QT, float>::value;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
-  const float* __restrict__ t32 = MIX ? cur_t32(D, ctl) : nullptr;
   double* __restrict__ tn = next_t(D, ctl);
   long base = D.ch_t_off[c];
   long vho = D.ch_vhh_off[c];
   for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
     int kl = e / UPD_ROWS, g = e % UPD_ROWS;
-    QT v = 0;
-    if (g < ng) {
-      long o = vho + (long)kl * nh + ij0 + g;
-      if constexpr (MIX) v = D.chi32[o];
-      else v = D.chi_hh[o];
-    }
-    chs[kl][g] = v;
+    chs[kl][g] = g < ng ? D.chi_hh[vho + (long)kl * nh + ij0 + g] : 0.0;
+  }
+  if ((int)threadIdx.x < UPD_ROWS) {
+    int g = min((int)threadIdx.x, ng - 1);
+    int2 h = D.hh_pair[D.ch_hh_off[c] + ij0 + g];
+    row_dij[threadIdx.x] = D.dchi[h.x] + D.dchi[h.y];
   }
   __syncthreads();
   double esum = 0.0, rsum = 0.0;
   if (ab < npp) {
     // hh ladder sum_kl t_ab^kl chi_kl^ij for all rows of the item: one pass over the t column
-    QT hh[UPD_ROWS];
+    double hh[UPD_ROWS];
 #pragma unroll
-    for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0;
+    for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0.0;
     if (!frozen) {
       const long col = base + ab;
 #pragma unroll 4
       for (int kl = 0; kl < nh; kl++) {
-        QT tk;
-        if constexpr (MIX) tk = t32[col + (long)kl * npp];
-        else tk = t[col + (long)kl * npp];
+        double tk = t[col + (long)kl * npp];
 #pragma unroll
         for (int g = 0; g < UPD_ROWS; g++) hh[g] = tk * chs[kl][g] + hh[g];
       }
     }
     int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
     // one-body part of the bracket: (d_a + d_b - d_i - d_j) t with d_p = chi_p - eps_p
-    QT da;
-    if constexpr (MIX) da = D.dchi32[p.x] + D.dchi32[p.y];
-    else da = D.dchi[p.x] + D.dchi[p.y];
+    double da = D.dchi[p.x] + D.dchi[p.y];
 #pragma unroll
     for (int g = 0; g < UPD_ROWS; g++) {
       if (g >= ng) break;
-      int ij = ij0 + g;
-      long z = base + (long)ij * npp + ab;
+      long z = base + (long)(ij0 + g) * npp + ab;
       double tz = t[z];
       double out = tz;
       double v = D.v_pphh[z];
-      int4 q = D.qmap[z];
       if (!frozen) {
-        int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-        if constexpr (MIX) {
-          // mixed precision: the bracket's correction terms (one-body, ladders, ph) in FP32
-          // from the FP32 copies; v, the denominator, the Jacobi step with mixing, the
-          // residual and the energy in FP64.  The FP64 unit is the scarce one, so the step
-          // is written as t + alpha R / eps with R = bracket - eps t (same value as
-          // alpha t_new + (1 - alpha) t).
-          float corr = (da - D.dchi32[h.x] - D.dchi32[h.y]) * t32[z] + hh[g];
-          if (szero)
-            for (int pl = 0; pl < nplanes; pl++) corr += (float)rpp[pl * pstride + z];
-          if (q.x >= 0) corr += (float)xq[q.x];
-          if (q.y >= 0) corr -= (float)xq[q.y];
-          if (q.z >= 0) corr -= (float)xq[q.z];
-          if (q.w >= 0) corr += (float)xq[q.w];
-          double num = v + (double)corr;
-          double R = fma(-D.den[z], tz, num);
-          rsum = fma(R, R, rsum);
-          out = fma(alpha * R, D.inv_den[z], tz);
-        } else {
-          double num = v + (da - D.dchi[h.x] - D.dchi[h.y]) * tz;
-          if (szero)
-            for (int pl = 0; pl < nplanes; pl++) num += (double)rpp[pl * pstride + z];
-          num += (double)hh[g];
-          double ph = 0.0;
-          if (q.x >= 0) ph += (double)xq[q.x];
-          if (q.y >= 0) ph -= (double)xq[q.y];
-          if (q.z >= 0) ph -= (double)xq[q.z];
-          if (q.w >= 0) ph += (double)xq[q.w];
-          num += ph;
-          double tnew = num * D.inv_den[z];
-          double R = num - D.den[z] * tz;
-          rsum += R * R;
-          out = alpha * tnew + (1.0 - alpha) * tz;
-        }
+        int4 q = D.qmap[z];
+        double num = v + (da - row_dij[g]) * tz;
+        if (szero) num += D.rpp[z];
+        num += hh[g];
+        double ph = 0.0;
+        if (q.x >= 0) ph += D.xq[q.x];
+        if (q.y >= 0) ph -= D.xq[q.y];
+        if (q.z >= 0) ph -= D.xq[q.z];
+        if (q.w >= 0) ph += D.xq[q.w];
+        num += ph;
+        double tnew = num * D.inv_den[z];
+        double R = num - D.den[z] * tz;
+        rsum += R * R;
+        out = alpha * tnew + (1.0 - alpha) * tz;
       }
       tn[z] = out;
       esum = fma(v, out, esum);
-      if constexpr (MIX) {
+    }
+  }
+  esum = block_sum(esum, sh32);
+  rsum = block_sum(rsum, sh32);
+  if (threadIdx.x == 0) {
+    D.eparts[blockIdx.x] = esum;
+    D.rparts[blockIdx.x] = rsum;
+  }
+  last_block_finalize(fa, ctl);
+}
+
+void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
+  k_update<<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
+                                                      fin_args(ctx, use_cond, h, false));
+}
+
+// hh ladder of the mixed iteration, sum_kl t_ab^kl chi_kl^ij in FP32 for every (ij, ab): one
+// CTA per (channel, 128 pp columns); the chi block and the t columns are staged in shared
+// memory (thread = column), rows in groups of 8 accumulated in registers.
+__global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restrict__ ctl,
+                                              const int2* __restrict__ ab_items, float* __restrict__ hh) {
+  extern __shared__ __align__(16) float hsm[];
+  int2 it = ab_items[blockIdx.x];
+  int c = it.x, ab = it.y + threadIdx.x;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  const float* __restrict__ t32 = cur_t32(D, ctl);
+  float* chs = hsm;            // chi[kl][ij], nh x nh
+  float* ts = hsm + nh * nh;   // t[kl][column], nh x 128
+  long base = D.ch_t_off[c];
+  const float* chi = D.chi32 + D.ch_vhh_off[c];
+  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) chs[e] = chi[e];
+  bool ok = ab < npp;
+  for (int kl = 0; kl < nh; kl++) ts[kl * 128 + threadIdx.x] = ok ? t32[base + (long)kl * npp + ab] : 0.0f;
+  __syncthreads();
+  if (!ok) return;
+  for (int ij0 = 0; ij0 < nh; ij0 += 8) {
+    float acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; g++) acc[g] = 0.0f;
+    for (int kl = 0; kl < nh; kl++) {
+      float tk = ts[kl * 128 + threadIdx.x];
+      const float* cr = chs + kl * nh + ij0;
+#pragma unroll
+      for (int g = 0; g < 8; g++)
+        if (ij0 + g < nh) acc[g] = fmaf(tk, cr[g], acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; g++)
+      if (ij0 + g < nh) hh[base + (long)(ij0 + g) * npp + ab] = acc[g];
+  }
+}
+
+// Mixed-precision update.  One CTA per item (channel, up to UPD_ROWS hole pairs ij, 128 pp
+// columns); each thread owns one column ab and the item's rows, so the block reductions of
+// the energy and residual are shared by up to UPD_ROWS amplitudes.  The bracket's correction
+// terms (one-body, pp and hh ladders, ph) are taken in FP32 from the FP32 copies; v, the
+// denominator, the Jacobi step with mixing, the residual and the energy in FP64.  The FP64
+// unit is the scarce one, so the step is written as t + alpha R / eps with R = bracket -
+// eps t (the value of alpha t_new + (1 - alpha) t).  Rows go in batches of UPD_BATCH: all
+// loads of a batch are issued before any store (rows past ng repeat the last row and are
+// discarded).  Writes the new amplitude in FP64, FP32, as BF16 hi/lo tiles of the next
+// tensor-core pp ladder and at its four places in the ph term's T.
+__global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, LoopCtl* __restrict__ ctl,
+                                                    const int4* __restrict__ items, FinArgs fa,
+                                                    const float* __restrict__ rpp, const float* __restrict__ hh,
+                                                    const float* __restrict__ xq, PackArgs pk, int nplanes,
+                                                    long pstride) {
+  __shared__ float row_dij[UPD_ROWS];
+  __shared__ double row_eij[UPD_ROWS];
+  __shared__ double sh32[32];
+  int4 it = items[blockIdx.x];
+  int c = it.x, ij0 = it.y, ng = it.w;
+  int npp = D.ch_npp[c];
+  int ab = it.z + threadIdx.x;
+  if ((int)threadIdx.x < UPD_ROWS) {
+    int g = min((int)threadIdx.x, ng - 1);
+    int2 h = D.hh_pair[D.ch_hh_off[c] + ij0 + g];
+    row_dij[threadIdx.x] = D.dchi32[h.x] + D.dchi32[h.y];
+    row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
+  }
+  bool frozen = fa.sc[D.ch_sys[c]].done != 0;
+  bool szero = D.ch_szero[c] != 0;
+  double alpha = ctl->alpha;
+  const double* __restrict__ t = cur_t(D, ctl);
+  const float* __restrict__ t32 = cur_t32(D, ctl);
+  double* __restrict__ tn = next_t(D, ctl);
+  float* __restrict__ t32n = next_t32(D, ctl);
+  long base = D.ch_t_off[c];
+  __syncthreads();
+  double esum = 0.0, rsum = 0.0;
+  if (ab < npp) {
+    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+    const float dab = D.dchi32[p.x] + D.dchi32[p.y];
+    const double eab = D.eps[p.x] + D.eps[p.y];
+#pragma unroll
+    for (int gb = 0; gb < UPD_ROWS; gb += UPD_BATCH) {
+      if (gb >= ng) break;
+      long z[UPD_BATCH];
+      double tz[UPD_BATCH], v[UPD_BATCH], idn[UPD_BATCH];
+      int4 q[UPD_BATCH];
+      float t32z[UPD_BATCH], part[UPD_BATCH], qs[UPD_BATCH];
+#pragma unroll
+      for (int j = 0; j < UPD_BATCH; j++) {
+        int g = min(gb + j, ng - 1);
+        z[j] = base + (long)(ij0 + g) * npp + ab;
+        tz[j] = t[z[j]];
+        v[j] = D.v_pphh[z[j]];
+        q[j] = D.qmap[z[j]];
+        t32z[j] = t32[z[j]];
+        idn[j] = D.inv_den[z[j]];
+        part[j] = hh[z[j]];
+        if (szero)
+          for (int pl = 0; pl < nplanes; pl++) part[j] += rpp[pl * pstride + z[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < UPD_BATCH; j++) {
+        float a0 = q[j].x >= 0 ? xq[q[j].x] : 0.0f, a1 = q[j].y >= 0 ? xq[q[j].y] : 0.0f;
+        float a2 = q[j].z >= 0 ? xq[q[j].z] : 0.0f, a3 = q[j].w >= 0 ? xq[q[j].w] : 0.0f;
+        qs[j] = (a0 - a1) - (a2 - a3);
+      }
+#pragma unroll
+      for (int j = 0; j < UPD_BATCH; j++) {
+        int g = gb + j;
+        if (g >= ng) break;
+        double out = tz[j];
+        if (!frozen) {
+          float corr = (dab - row_dij[g]) * t32z[j] + part[j] + qs[j];
+          double num = v[j] + (double)corr;
+          double R = fma(eab - row_eij[g], tz[j], num);  // bracket - eps_ij^ab t
+          rsum = fma(R, R, rsum);
+          out = fma(alpha * R, idn[j], tz[j]);
+        }
+        tn[z[j]] = out;
+        esum = fma(v[j], out, esum);
         float o32 = (float)out;
-        next_t32(D, ctl)[z] = o32;
+        t32n[z[j]] = o32;
         if (pk.xt) {
-          // the new amplitude at its four places in the ph term's T (the Q positions of
-          // P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba)
-          if (q.x >= 0) pk.xt[q.x] = o32;
-          if (q.y >= 0) pk.xt[q.y] = -o32;
-          if (q.z >= 0) pk.xt[q.z] = -o32;
-          if (q.w >= 0) pk.xt[q.w] = o32;
+          // the Q positions of P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba
+          if (q[j].x >= 0) pk.xt[q[j].x] = o32;
+          if (q[j].y >= 0) pk.xt[q[j].y] = -o32;
+          if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
+          if (q[j].w >= 0) pk.xt[q[j].w] = o32;
         }
         if (pk.bt && szero) {
-          // BF16 hi/lo copy of the new amplitude for the next tensor-core pp ladder
           int npad = pk.ch_npad[c];
           long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
           __nv_bfloat16 bhi = __float2bfloat16_rn(o32);
           __nv_bfloat16 blo = __float2bfloat16_rn(o32 - __bfloat162float(bhi));
-          int o = tile_core_off(ij, ab & 63);
+          int o = tile_core_off(ij0 + g, ab & 63);
           pk.bt[tb + o] = bhi;
           pk.bt[tb + (long)npad * 64 + o] = blo;
         }
@@ -581,16 +720,21 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   last_block_finalize(fa, ctl);
 }
 
-template <typename RT, typename QT>
-void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride) {
-  k_update<RT, QT><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(
-      ctx->d, ctx->ctl, ctx->grp_items, fin_args(ctx, use_cond, h), rpp, xq, pk, nplanes, pstride);
+size_t hh32_smem_bytes(const pnm_ctx* ctx) {
+  return sizeof(float) * ((size_t)ctx->max_nhh * ctx->max_nhh + (size_t)ctx->max_nhh * 128);
 }
-template void launch_update<double, double>(pnm_ctx*, const double*, const double*, int,
-                                            cudaGraphConditionalHandle, PackArgs, int, long);
-template void launch_update<float, float>(pnm_ctx*, const float*, const float*, int,
-                                          cudaGraphConditionalHandle, PackArgs, int, long);
+
+void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const float* xq, int use_cond,
+                       cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride) {
+  k_update_mix<<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
+                                                         fin_args(ctx, use_cond, h, false), rpp, hh, xq, pk,
+                                                         nplanes, pstride);
+}
+
+void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s) {
+  if (ctx->n_ab_items > 0)
+    k_hh32<<<ctx->n_ab_items, 128, hh32_smem_bytes(ctx), s>>>(ctx->d, ctx->ctl, ctx->ab_items, hh);
+}
 
 // Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
 __global__ void __launch_bounds__(128) k_init(DevState D, int init) {
@@ -823,18 +967,23 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
   // cross channels for the mixed ph launches: the large ones first, each class largest first
-  std::vector<int> big, small;
-  for (int x = 0; x < ctx->nx; x++)
-    (std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]) > PH_SMALL_DIM ? big : small).push_back(x);
+  std::vector<int> big, mid, small;
+  for (int x = 0; x < ctx->nx; x++) {
+    int d = std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]);
+    (d > PH_SMALL_DIM ? big : d > PH_WARP_DIM ? mid : small).push_back(x);
+  }
   auto by_size = [&](int a, int b) {
     long sa = (long)ctx->h_x_nph[a] * ctx->h_x_nhp[a], sb = (long)ctx->h_x_nph[b] * ctx->h_x_nhp[b];
     return sa != sb ? sa > sb : a < b;
   };
   std::sort(big.begin(), big.end(), by_size);
+  std::sort(mid.begin(), mid.end(), by_size);
   std::sort(small.begin(), small.end(), by_size);
   std::vector<int> xl(big);
+  xl.insert(xl.end(), mid.begin(), mid.end());
   xl.insert(xl.end(), small.begin(), small.end());
   ctx->n_ph_big = (int)big.size();
+  ctx->n_ph_mid = (int)mid.size();
   ctx->n_ph_small = (int)small.size();
   ctx->ph_list = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, xl.size()));
   if (!xl.empty())
@@ -843,11 +992,8 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   size_t pp_smem = pp64_smem(max_npp);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
-  CUDA_TRY(cudaFuncSetAttribute(k_ph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ph_smem));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph_mix<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_smem_bytes(ctx->max_x_dim, sizeof(float))));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph_mix<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_smem_bytes(PH_SMALL_DIM, sizeof(float))));
+  pnm_ph_attributes(ctx);
+  CUDA_TRY(cudaFuncSetAttribute(k_hh32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh32_smem_bytes(ctx)));
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
@@ -904,12 +1050,13 @@ void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results
 }
 
 // The body of one update, enqueued on the context stream (FP64 path).
-FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
+// per_row: partials of the per-row mixed update (items upd_items), else of the grouped update.
+FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row) {
   FinArgs f;
   f.eparts = ctx->d.eparts;
   f.rparts = ctx->d.rparts;
-  f.lo = ctx->grp_lo_d;
-  f.hi = ctx->grp_hi_d;
+  f.lo = per_row ? ctx->upd_lo_d : ctx->grp_lo_d;
+  f.hi = per_row ? ctx->upd_hi_d : ctx->grp_hi_d;
   f.nsys = (int)ctx->sys.size();
   f.sc = ctx->sysctl;
   f.hist = ctx->hist;
@@ -982,13 +1129,13 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
   pnm_enqueue_stats(ctx, false);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
-  launch_update<double, double>(ctx, D.rpp, D.xq, use_cond, h, PackArgs{nullptr, nullptr, nullptr, nullptr}, 1, 0);
+  launch_update64(ctx, use_cond, h);
   prof_end(ctx);
 }
 
 const char* const pnm_kernel_names[PNM_NKERNELS] = {
     "k_tstats", "k_dchi", "k_ph64", "k_pp64", "k_update", "k_finalize(unused)",
-    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack", "k_dchi32"};
+    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack", "k_dchi32", "k_hh32"};
 
 void prof_begin(pnm_ctx* ctx, int kid) {
   if (!ctx->prof_live) return;
@@ -1061,11 +1208,13 @@ static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
 
 // Runs updates until every system meets its tolerance or the cap is hit.  Returns the
 // loop status (1 converged, PNM_ENOTCONV, PNM_EDIVERGED).
-int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alpha) {
+int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha) {
   cudaStream_t s = ctx->stream;
   LoopCtl hc{};
-  // keep iteration parity: ctl->iter is reset by k_start; only max_iter/alpha/mode set here
+  // keep iteration parity: ctl->iter is reset by k_start; only the limits, alpha and mode
+  // are set here
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->max_iter, &max_iter, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->min_iter, &min_iter, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->mode, &mode, sizeof(int), cudaMemcpyHostToDevice, s));
   if (max_iter <= 0) return PNM_ENOTCONV;

@@ -239,6 +239,7 @@ struct MixedState {
   __nv_bfloat16* bt = nullptr;
   float *rpp32 = nullptr, *xw32 = nullptr, *xv132 = nullptr, *xq32 = nullptr;
   float* xt32 = nullptr;  // T of the ph term, cross-channel layout, written by the update
+  float* hh32 = nullptr;  // hh ladder of the current amplitudes (FP32, t layout)
   TCItem* items = nullptr;
   int nitems = 0;
   int4* pk = nullptr;
@@ -355,6 +356,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
     M->xq32 = mdalloc<float>(ctx, ctx->nxt);
     M->xt32 = mdalloc<float>(ctx, ctx->nxt);
+    M->hh32 = mdalloc<float>(ctx, ctx->nt);
     // entries no amplitude maps to (repeated state index) stay zero
     CUDA_TRY(cudaMemsetAsync(M->xt32, 0, sizeof(float) * std::max<long>(ctx->nxt, 1), s));
     if (ctx->nxt > 0)
@@ -459,11 +461,14 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
     prof_end(ctx);
   }
   pnm_enqueue_stats(ctx, true);
+  prof_begin(ctx, KID_HH32);
+  launch_hh32(ctx, M->hh32, ctx->stream);
+  prof_end(ctx);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
   // the update also writes the BF16 hi/lo tiles of the new amplitudes for the next ladder
-  launch_update<float, float>(ctx, M->rpp32, M->xq32, use_cond, h, PackArgs{M->bt, M->xt32, M->ch_boff, M->ch_npad},
-                              M->ksplit, ctx->nt);
+  launch_update_mix(ctx, M->rpp32, M->hh32, M->xq32, use_cond, h, PackArgs{M->bt, M->xt32, M->ch_boff, M->ch_npad},
+                    M->ksplit, ctx->nt);
   prof_end(ctx);
 }
 

@@ -11,7 +11,7 @@ struct MlpState;    // learned warm start (mlp.cu)
 // Kernel ids of the per-kernel profiler.
 enum {
   KID_TSTATS = 0, KID_DCHI, KID_PH64, KID_PP64, KID_UPDATE, KID_FINALIZE,
-  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, KID_DCHI32, PNM_NKERNELS
+  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, KID_DCHI32, KID_HH32, PNM_NKERNELS
 };
 extern const char* const pnm_kernel_names[PNM_NKERNELS];
 
@@ -42,7 +42,7 @@ struct pnm_ctx {
   int4* grp_items = nullptr;  // (channel, first ij, first pp column, rows) of the update
   int n_grp_items = 0, upd_rows = 1;
   int* ph_list = nullptr;  // cross channels of the mixed ph launches (large class first)
-  int n_ph_big = 0, n_ph_small = 0;
+  int n_ph_big = 0, n_ph_mid = 0, n_ph_small = 0;
   int *grp_lo_d = nullptr, *grp_hi_d = nullptr;  // per system ranges of the update items
   int *ab_lo_d = nullptr, *ab_hi_d = nullptr;    // per system ranges of the column items
   int max_nhh = 1;
@@ -108,7 +108,7 @@ void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditional
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_mixed(pnm_ctx* ctx);
 void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);
-int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int host_loop, double alpha);
+int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha);
 void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
 void pnm_mlp_start(pnm_ctx* ctx);
@@ -116,7 +116,7 @@ void pnm_free_mlp(pnm_ctx* ctx);
 void prof_begin(pnm_ctx* ctx, int kid);
 void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
-FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
+FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
 void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s);
 size_t ph_smem_bytes(int max_dim, size_t elem);
@@ -128,9 +128,11 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s);
-template <typename RT, typename QT>
-void launch_update(pnm_ctx* ctx, const RT* rpp, const QT* xq, int use_cond,
-                   cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride);
+void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
+void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const float* xq, int use_cond,
+                       cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride);
+void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s);
+size_t hh32_smem_bytes(const pnm_ctx* ctx);
 void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask);
 bool pnm_concurrent(const pnm_ctx* ctx);
 void pnm_tune_schedule(pnm_ctx* ctx, int mode);

@@ -102,6 +102,7 @@ struct LoopCtl {
   int max_iter;
   int status;        // 0 running, 1 converged, PNM_ENOTCONV, PNM_EDIVERGED
   int mode;          // 0 FP64 iteration, 1 mixed iteration
+  int min_iter;      // no system counts as converged before this many updates
   double alpha;
 };
 
@@ -126,12 +127,25 @@ struct FinArgs {
   cudaGraphConditionalHandle handle;
 };
 
-// The update kernel: at most UPD_ROWS hole pairs per CTA share one pass over a t column for
-// the hh ladder; channels may hold at most UPD_MAX_NHH hole pairs.
-constexpr int UPD_ROWS = 8, UPD_MAX_NHH = 128;
+// The update kernels: at most UPD_ROWS hole pairs per CTA (the FP64 update shares one pass
+// over a t column for the hh ladder among them), loads issued in batches of UPD_BATCH rows,
+// at least UPD_MIN_BLOCKS CTAs of the mixed update per SM; channels may hold at most
+// UPD_MAX_NHH hole pairs.  The PNM_UPD_* macros override the tuning constants at build time.
+#ifndef PNM_UPD_ROWS
+#define PNM_UPD_ROWS 8
+#endif
+#ifndef PNM_UPD_BATCH
+#define PNM_UPD_BATCH 4
+#endif
+#ifndef PNM_UPD_MIN_BLOCKS
+#define PNM_UPD_MIN_BLOCKS 1
+#endif
+constexpr int UPD_ROWS = PNM_UPD_ROWS, UPD_MAX_NHH = 128, UPD_BATCH = PNM_UPD_BATCH;
+constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
 
-// Cross channels with at most PH_SMALL_DIM rows and columns go to the small-footprint ph launch.
-constexpr int PH_SMALL_DIM = 32;
+// Size classes of the mixed ph launches: cross channels with at most PH_WARP_DIM rows and
+// columns get one warp each, those with at most PH_SMALL_DIM a 128-thread CTA each.
+constexpr int PH_SMALL_DIM = 32, PH_WARP_DIM = 16;
 
 // Where the mixed update writes the BF16 hi/lo copy of the new amplitudes (the B operand
 // tiles of the tensor-core pp ladder).  bt == nullptr: no copy.

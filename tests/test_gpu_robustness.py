@@ -76,3 +76,24 @@ def test_mixed_precision_batch(pkg):
         dE_o, _, _, _ = o.ccd(alpha=0.5, tol=1e-10 * 14, maxit=300)
         assert abs(dE[k] - dE_o) / 14 < 1e-6
     g.close()
+
+
+def test_fma_peak_measurement(pkg):
+    """The FMA-rate microbenchmark returns a finite rate, FP32 above FP64."""
+    fp64 = pkg.measure_fma_peak(True)
+    fp32 = pkg.measure_fma_peak(False)
+    assert 0.1 < fp64 < 1000.0 and 1.0 < fp32 < 1000.0
+    assert fp32 > fp64
+
+
+def test_refinement_runs_exactly_the_requested_sweeps(pkg):
+    """refine_sweeps FP64 updates always follow the converged mixed phase (the FP64 stopping
+    test only counts from the last of them on)."""
+    g = pkg.Context(14, 0.08, 20, params=minnesota_params())
+    kw = dict(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-6, max_iter=300)
+    _, it0, _, _ = g.solve(refine_sweeps=0, **kw)
+    for k in (1, 2, 3):
+        _, itk, _, rc = g.solve(refine_sweeps=k, **kw)
+        assert rc == 0
+        assert itk[0] >= it0[0] + k, (k, it0, itk)
+    g.close()
