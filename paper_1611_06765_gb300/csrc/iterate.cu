@@ -469,10 +469,13 @@ __device__ void finalize_systems(const FinArgs& f, LoopCtl* ctl) {
 // The last block of a grid to finish runs the finalize step (no waiting: the blocks count
 // themselves out with an atomic after a fence, as in the CUDA threadfence reduction).
 __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
+  // only thread 0 wrote the block's partials: its fence orders them before the count
   __shared__ int is_last;
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(&ctl->blocks_done, 1) == (int)gridDim.x - 1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = (atomicAdd(&ctl->blocks_done, 1) == (int)gridDim.x - 1);
+  }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -558,8 +561,7 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
       esum = fma(v, out, esum);
     }
   }
-  esum = block_sum(esum, sh32);
-  rsum = block_sum(rsum, sh32);
+  block_sum2(esum, rsum, sh32);
   if (threadIdx.x == 0) {
     D.eparts[blockIdx.x] = esum;
     D.rparts[blockIdx.x] = rsum;
@@ -672,6 +674,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
       }
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
+        // P(ij)P(ab) Q: Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba from the cross-channel layout
         float a0 = q[j].x >= 0 ? xq[q[j].x] : 0.0f, a1 = q[j].y >= 0 ? xq[q[j].y] : 0.0f;
         float a2 = q[j].z >= 0 ? xq[q[j].z] : 0.0f, a3 = q[j].w >= 0 ? xq[q[j].w] : 0.0f;
         qs[j] = (a0 - a1) - (a2 - a3);
@@ -711,8 +714,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
       }
     }
   }
-  esum = block_sum(esum, sh32);
-  rsum = block_sum(rsum, sh32);
+  block_sum2(esum, rsum, sh32);
   if (threadIdx.x == 0) {
     D.eparts[blockIdx.x] = esum;
     D.rparts[blockIdx.x] = rsum;

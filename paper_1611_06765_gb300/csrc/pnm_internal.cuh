@@ -135,10 +135,10 @@ struct FinArgs {
 #define PNM_UPD_ROWS 8
 #endif
 #ifndef PNM_UPD_BATCH
-#define PNM_UPD_BATCH 4
+#define PNM_UPD_BATCH 2
 #endif
 #ifndef PNM_UPD_MIN_BLOCKS
-#define PNM_UPD_MIN_BLOCKS 1
+#define PNM_UPD_MIN_BLOCKS 8
 #endif
 constexpr int UPD_ROWS = PNM_UPD_ROWS, UPD_MAX_NHH = 128, UPD_BATCH = PNM_UPD_BATCH;
 constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
@@ -220,4 +220,24 @@ __device__ __forceinline__ T block_sum(T v, T* sh32) {
   if (w == 0) v = warp_sum(v);
   __syncthreads();
   return v;
+}
+
+// Two block-wide sums at once (sh32: 32 doubles); results valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh32) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh32[w] = a;
+    sh32[16 + w] = b;
+  }
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  a = (threadIdx.x < nw) ? sh32[threadIdx.x] : 0.0;
+  b = (threadIdx.x < nw) ? sh32[16 + threadIdx.x] : 0.0;
+  if (w == 0) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
 }
