@@ -174,6 +174,14 @@ int pnm_set_amplitudes(pnm_ctx *ctx, int sys, const double *t, size_t n);
 int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, double *r,
                         size_t n);
 
+/* The particle-hole term alone, as an operator on amplitudes: r_ij^ab =
+ * P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj with chi_kb^cj = <kb|v|cj> + 1/2 sum_dl <kl|v|cd> t_lj^db
+ * (the linear ph term and the quadratic ph term of Eq. ccd3 through the intermediate of Sec.
+ * "Developing a CCD code"), computed in the cross-coupled channels (n_a - n_i, s_a - s_i):
+ * FP64 kernels, or the mixed-precision ones (FP32 operands and products).  t and r hold n restricted
+ * amplitudes of system `sys` in library order.  Resets the solver's iteration state. */
+int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, double *r, size_t n);
+
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
  * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);

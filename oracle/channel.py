@@ -46,6 +46,8 @@ def lib():
         L.om_t_dump.argtypes = [vp, vp, vp]
         L.om_vpp_block.restype = C.c_long
         L.om_vpp_block.argtypes = [vp, C.c_int, vp]
+        L.om_ph_apply.restype = C.c_int
+        L.om_ph_apply.argtypes = [vp, vp, vp, C.c_int]
         L.om_threads.restype = C.c_int
         L.om_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -151,6 +153,29 @@ class OracleSystem:
         lib().om_vpp_block(self._h, int(c), _ptr(out))
         m = int(round(np.sqrt(n)))
         return out.reshape(m, m)
+
+    def ph_apply(self, t_lib, absval=False):
+        """P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj of Eq. (ccd3) for restricted amplitudes given in
+        the library layout (per channel n_hh x n_pp, hh rows); result in the same layout.
+        absval: the same with |t|, |v| and + signs (an error bound)."""
+        tab = self.channel_tables()
+        t_lib = np.asarray(t_lib, dtype=np.float64)
+        t_or = np.zeros_like(t_lib)
+        off = 0
+        for nh, npp in zip(tab["nhh"], tab["npp"]):
+            k = int(nh) * int(npp)
+            t_or[off:off + k] = t_lib[off:off + k].reshape(int(nh), int(npp)).T.ravel()
+            off += k
+        out = np.zeros_like(t_or)
+        if lib().om_ph_apply(self._h, _ptr(t_or), _ptr(out), int(bool(absval))) != 0:
+            raise MemoryError("oracle: out of memory")
+        res = np.zeros_like(out)
+        off = 0
+        for nh, npp in zip(tab["nhh"], tab["npp"]):
+            k = int(nh) * int(npp)
+            res[off:off + k] = out[off:off + k].reshape(int(npp), int(nh)).T.ravel()
+            off += k
+        return res
 
     def t_gather(self, abij):
         abij = np.ascontiguousarray(abij, dtype=np.int32)

@@ -607,10 +607,67 @@ static double ccd_energy(const om_sys *S, const double *t) {
     return e;
 }
 
+/* Particle-hole term in cross channels (the intermediate chi_kb^cj of Sec. "Developing a
+ * CCD code", in the cross-coupled (a-i) channels):
+ *   T[(a,i)][(k,c)] = t_ik^ac
+ *   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
+ *   Q[(a,i)][(j,b)] = sum_{(k,c)} T C = sum_kc t_ik^ac chi_kb^cj
+ * absval != 0: the same with |t|, |v| everywhere (a bound for rounding-error tests). */
+static void ph_cross(const om_sys *S, const double *t, double *xT, double *xC, double *xQ, int absval) {
+#pragma omp parallel for schedule(dynamic)
+    for (int x = 0; x < S->nx_ch; x++) {
+        int nph = S->nph[x], nhp = S->nhp[x];
+        const int *pa = S->ph_a + S->ph_off[x], *pi = S->ph_i + S->ph_off[x];
+        const int *hk = S->hp_k + S->hp_off[x], *hc = S->hp_c + S->hp_off[x];
+        double *T = xT + S->xt_off[x], *Cm = xC + S->xc_off[x], *Q = xQ + S->xt_off[x];
+        const double *V1 = S->x_v1 + S->xc_off[x], *W = S->x_w + S->xw_off[x];
+        for (int r = 0; r < nph; r++)
+            for (int s = 0; s < nhp; s++) {
+                double v = t_get(S, t, pa[r], hc[s], pi[r], hk[s]);
+                T[(size_t)r * nhp + s] = absval ? fabs(v) : v;
+            }
+        for (int r = 0; r < nhp; r++)
+            for (int s = 0; s < nhp; s++) {
+                double acc = 0.0;
+                for (int u = 0; u < nph; u++) {
+                    double w = W[(size_t)r * nph + u];
+                    acc += (absval ? fabs(w) : w) * T[(size_t)u * nhp + s];
+                }
+                double v1 = V1[(size_t)r * nhp + s];
+                Cm[(size_t)r * nhp + s] = (absval ? fabs(v1) : v1) + 0.5 * acc;
+            }
+        for (int r = 0; r < nph; r++)
+            for (int s = 0; s < nhp; s++) {
+                double acc = 0.0;
+                for (int u = 0; u < nhp; u++) acc += T[(size_t)r * nhp + u] * Cm[(size_t)u * nhp + s];
+                Q[(size_t)r * nhp + s] = acc;
+            }
+    }
+}
+
+/* P(ij)P(ab) Q: Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba with Q_ij^ab = Q[(a,i)][(j,b)]
+ * (absval != 0: all four with + signs). */
+static double ph_combine(const om_sys *S, const double *xQ, int a, int b, int i, int j, int absval) {
+    int n = S->nsp, N = S->N;
+    int h1[4] = {i, j, i, j}, h2[4] = {j, i, j, i};
+    int p1[4] = {a, a, b, b}, p2[4] = {b, b, a, a};
+    double sg[4] = {1.0, -1.0, -1.0, 1.0};
+    double out = 0.0;
+    for (int u = 0; u < 4; u++) {
+        int xr = S->phx_ch[(size_t)p1[u] * N + h1[u]];
+        int xc = S->hpx_ch[(size_t)h2[u] * n + p2[u]];
+        if (xr < 0 || xr != xc) continue;
+        int r = S->phx_pos[(size_t)p1[u] * N + h1[u]];
+        int s = S->hpx_pos[(size_t)h2[u] * n + p2[u]];
+        out += (absval ? 1.0 : sg[u]) * xQ[S->xt_off[xr] + (size_t)r * S->nhp[xr] + s];
+    }
+    return out;
+}
+
 /* One Jacobi step of Eq. (ccd3) with the intermediates; writes t_new (restricted). */
 static void ccd_step(const om_sys *S, const double *t, double *t_new, double *chi1,
                      double *chi_hh, double *xT, double *xC, double *xQ) {
-    int n = S->nsp, N = S->N;
+    int n = S->nsp;
     /* one-body intermediates.  Momentum and S_z conservation make them diagonal:
      *   chi_b = f_bb - 1/2 sum_{kld} t_kl^bd <kl|v|bd>  = f_bb - sum_d sum_{k<l} t v
      *   chi_j = f_jj + 1/2 sum_{cdl} <jl|v|cd> t_jl^cd  = f_jj + sum_l sum_{c<d} v t   */
@@ -646,33 +703,7 @@ static void ccd_step(const om_sys *S, const double *t, double *t_new, double *ch
                 ch[(size_t)kl * nh + ij] = s;
             }
     }
-    /* particle-hole term in cross channels:
-     *   T[(a,i)][(k,c)] = t_ik^ac
-     *   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
-     *   Q[(a,i)][(j,b)] = sum_{(k,c)} T C = sum_kc t_ik^ac chi_kb^cj                  */
-#pragma omp parallel for schedule(dynamic)
-    for (int x = 0; x < S->nx_ch; x++) {
-        int nph = S->nph[x], nhp = S->nhp[x];
-        const int *pa = S->ph_a + S->ph_off[x], *pi = S->ph_i + S->ph_off[x];
-        const int *hk = S->hp_k + S->hp_off[x], *hc = S->hp_c + S->hp_off[x];
-        double *T = xT + S->xt_off[x], *Cm = xC + S->xc_off[x], *Q = xQ + S->xt_off[x];
-        const double *V1 = S->x_v1 + S->xc_off[x], *W = S->x_w + S->xw_off[x];
-        for (int r = 0; r < nph; r++)
-            for (int s = 0; s < nhp; s++)
-                T[(size_t)r * nhp + s] = t_get(S, t, pa[r], hc[s], pi[r], hk[s]);
-        for (int r = 0; r < nhp; r++)
-            for (int s = 0; s < nhp; s++) {
-                double acc = 0.0;
-                for (int u = 0; u < nph; u++) acc += W[(size_t)r * nph + u] * T[(size_t)u * nhp + s];
-                Cm[(size_t)r * nhp + s] = V1[(size_t)r * nhp + s] + 0.5 * acc;
-            }
-        for (int r = 0; r < nph; r++)
-            for (int s = 0; s < nhp; s++) {
-                double acc = 0.0;
-                for (int u = 0; u < nhp; u++) acc += T[(size_t)r * nhp + u] * Cm[(size_t)u * nhp + s];
-                Q[(size_t)r * nhp + s] = acc;
-            }
-    }
+    ph_cross(S, t, xT, xC, xQ, 0);
     /* assemble Eq. (ccd3) with the intermediates, for restricted a<b, i<j */
 #pragma omp parallel for schedule(dynamic)
     for (int c = 0; c < S->nch; c++) {
@@ -700,17 +731,7 @@ static void ccd_step(const om_sys *S, const double *t, double *t_new, double *ch
                 for (int kl = 0; kl < nh; kl++) hh += tb[(size_t)x * nh + kl] * ch[(size_t)kl * nh + y];
                 num += hh;
                 /* P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj = Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba */
-                int h1[4] = {i, j, i, j}, h2[4] = {j, i, j, i};
-                int p1[4] = {a, a, b, b}, p2[4] = {b, b, a, a};
-                double sg[4] = {1.0, -1.0, -1.0, 1.0};
-                for (int u = 0; u < 4; u++) {
-                    int xr = S->phx_ch[(size_t)p1[u] * N + h1[u]];
-                    int xc = S->hpx_ch[(size_t)h2[u] * n + p2[u]];
-                    if (xr < 0 || xr != xc) continue;
-                    int r = S->phx_pos[(size_t)p1[u] * N + h1[u]];
-                    int s = S->hpx_pos[(size_t)h2[u] * n + p2[u]];
-                    num += sg[u] * xQ[S->xt_off[xr] + (size_t)r * S->nhp[xr] + s];
-                }
+                num += ph_combine(S, xQ, a, b, i, j, 0);
                 double D = S->eps[i] + S->eps[j] - S->eps[a] - S->eps[b];
                 tn[(size_t)x * nh + y] = num / D;
             }
@@ -776,6 +797,32 @@ int om_ccd(om_sys *S, double alpha, double tol, int maxit, int init, double *dE_
     if (timings) { timings[0] = t1 - t0; timings[1] = t2 - t1; }
     free(t_new); free(chi1); free(chi_hh); free(xT); free(xC); free(xQ);
     return it;
+}
+
+/* The P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj part of Eq. (ccd3) for the restricted amplitudes t
+ * (oracle layout), into out (same layout); absval != 0 gives the absolute-value bound. */
+int om_ph_apply(om_sys *S, const double *t, double *out, int absval) {
+    build_ccd_blocks(S);
+    double *xT = malloc(sizeof(double) * (S->nxt + 1));
+    double *xC = malloc(sizeof(double) * (S->nxc + 1));
+    double *xQ = malloc(sizeof(double) * (S->nxt + 1));
+    if (!xT || !xC || !xQ) {
+        free(xT); free(xC); free(xQ);
+        return -1;
+    }
+    ph_cross(S, t, xT, xC, xQ, absval);
+    for (int c = 0; c < S->nch; c++) {
+        int np = S->npp[c], nh = S->nhh[c];
+        for (int x = 0; x < np; x++) {
+            int a = S->pp_p[S->pp_off[c] + x], b = S->pp_q[S->pp_off[c] + x];
+            for (int y = 0; y < nh; y++) {
+                int i = S->hh_p[S->hh_off[c] + y], j = S->hh_q[S->hh_off[c] + y];
+                out[S->t_off[c] + (size_t)x * nh + y] = ph_combine(S, xQ, a, b, i, j, absval);
+            }
+        }
+    }
+    free(xT); free(xC); free(xQ);
+    return 0;
 }
 
 int om_threads(void) {

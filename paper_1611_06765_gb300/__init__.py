@@ -149,6 +149,13 @@ class Context:
         _lib.check(_lib.load().pnm_apply_pp_ladder(self._h, sys, precision, _ptr(t), _ptr(r), t.size))
         return r
 
+    def apply_ph_term(self, t, precision=PNM_PREC_FP64, sys=0):
+        """pnm_apply_ph_term: the ph term (linear and quadratic) alone applied to amplitudes t."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        r = np.zeros_like(t)
+        _lib.check(_lib.load().pnm_apply_ph_term(self._h, sys, precision, _ptr(t), _ptr(r), t.size))
+        return r
+
     def mlp_features(self, sys=0):
         """(X[n,32], t_MBPT2[n], sigma_sys) of system sys in library order."""
         n = len(self.amplitude_labels(sys))

@@ -30,7 +30,7 @@ EXPORTS = (
     "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc",
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
-    "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_mlp_num_params", "pnm_mlp_init",
+    "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_apply_ph_term", "pnm_mlp_num_params", "pnm_mlp_init",
     "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
     "pnm_measure_fma_peak", "pnm_last_error",
 )
@@ -88,6 +88,7 @@ def load(path=None):
     L.pnm_set_amplitudes.argtypes = [vp, C.c_int, vp, C.c_size_t]
     L.pnm_get_timings.argtypes = [vp, dp, C.c_int]
     L.pnm_apply_pp_ladder.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_size_t]
+    L.pnm_apply_ph_term.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_size_t]
     fp = C.POINTER(C.c_float)
     L.pnm_mlp_num_params.argtypes = [ip]
     L.pnm_mlp_init.argtypes = [fp, C.c_ulonglong]

@@ -354,6 +354,17 @@ int pnm_apply_pp_ladder(pnm_ctx* ctx, int sys, int precision, const double* t, d
   });
 }
 
+int pnm_apply_ph_term(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    if (!t || !r) throw PnmError{PNM_EINVAL, "null argument"};
+    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3)
+      throw PnmError{PNM_EINVAL, "unknown precision mode"};
+    pnm_apply_ph(ctx, sys, precision, t, r, n);
+    return PNM_OK;
+  });
+}
+
 int pnm_get_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask) {
   return guarded([&]() {
     if (!ctx) throw PnmError{PNM_EINVAL, "null context"};

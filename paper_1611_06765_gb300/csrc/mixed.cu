@@ -547,6 +547,49 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   }
 }
 
+// out[z] = Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba of amplitude z from the cross-channel Q.
+template <typename T>
+__global__ void k_ph_assemble(DevState D, const T* __restrict__ xq, long nt, double* __restrict__ out) {
+  long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nt) return;
+  int4 q = D.qmap[z];
+  double a0 = q.x >= 0 ? (double)xq[q.x] : 0.0, a1 = q.y >= 0 ? (double)xq[q.y] : 0.0;
+  double a2 = q.z >= 0 ? (double)xq[q.z] : 0.0, a3 = q.w >= 0 ? (double)xq[q.w] : 0.0;
+  out[z] = (a0 - a1) - (a2 - a3);
+}
+
+// The ph term P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj as an operator on the amplitudes of one
+// system (FP64 kernels, or the mixed-precision ones: FP32 T copy, tensor-core or CUDA-core
+// contractions by channel size).
+void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n) {
+  const SysInfo& S = ctx->sys[sys];
+  cudaStream_t s = ctx->stream;
+  if (n != (size_t)(S.t_end - S.t_begin)) throw PnmError{PNM_EINVAL, "size mismatch"};
+  if (precision == PNM_PREC_BF16X3) pnm_prepare_mixed(ctx);
+  int zero = 0;
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  unsigned nb = (unsigned)((ctx->nt + 255) / 256);
+  if (precision == PNM_PREC_BF16X3) {
+    MixedState* M = ctx->mixed;
+    k_to_float_cur<<<nb, 256, 0, s>>>(ctx->d, ctx->ctl, ctx->nt);
+    if (ctx->nxt > 0)
+      k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, s>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
+    if (ctx->nx > 0) launch_ph_mix(ctx, M->xt32, M->xw32, M->xv132, M->xq32, s);
+    k_ph_assemble<float><<<nb, 256, 0, s>>>(ctx->d, M->xq32, ctx->nt, ctx->d.rpp);
+  } else {
+    if (ctx->nx > 0) launch_ph64(ctx, s);
+    k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->d.rpp);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(r, ctx->d.rpp + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget"};
+}
+
 // Failure-path self test: one thread waits, with the bounded wait of the tensor-core
 // kernels, on an mbarrier that nothing ever arrives on.  The wait gives up, the kernel
 // records the failure in the context's device flag and returns; nothing traps or hangs.

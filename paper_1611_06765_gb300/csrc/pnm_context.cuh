@@ -124,6 +124,7 @@ void pnm_mixed_pack_initial(pnm_ctx* ctx);
 void pnm_fork(pnm_ctx* ctx);
 void pnm_join(pnm_ctx* ctx);
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
+void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,

@@ -79,3 +79,24 @@ def test_mixed_then_fp64_agree_on_fixed_point(pkg):
                             max_iter=300)
     assert abs(dEm[0] - dE64[0]) / N < 1e-6
     g.close()
+
+
+@pytest.mark.parametrize("N,rho,n2", [(14, 0.08, 4), (14, 0.08, 20), (66, 0.16, 36)])
+def test_ph_term_operator(pkg, N, rho, n2):
+    """The ph term (cross-channel T, chi_kb^cj, Q and P(ij)P(ab)) against the oracle's, on
+    seeded amplitudes: FP64 kernels to 1e-12 of the largest element; the mixed kernels (FP32
+    operands and accumulation) within 2e-5 of the oracle's absolute-value bound per element
+    (two chained FP32 products over at most 66 terms each: at most 2 * 66 * 2^-24 of it)."""
+    g = pkg.Context(N, rho, n2, params=minnesota_params())
+    o = channel.OracleSystem(N, rho, n2, minnesota_params())
+    n = len(g.amplitude_labels())
+    t = random_amplitudes(n, seed=9)
+    ref = o.ph_apply(t)
+    bound = o.ph_apply(t, absval=True)
+    r64 = g.apply_ph_term(t, precision=pkg.PNM_PREC_FP64)
+    r16 = g.apply_ph_term(t, precision=pkg.PNM_PREC_BF16X3)
+    scale = np.max(np.abs(ref))
+    assert scale > 0
+    assert np.max(np.abs(r64 - ref)) <= 1e-12 * scale
+    assert np.all(np.abs(r16 - ref) <= 2e-5 * bound + 1e-30)
+    g.close()

@@ -123,3 +123,44 @@ def test_ccd_matches_ecomparison(rho, e_mbpt2, e_ccd):
     dE, it, _, _ = S.ccd(alpha=0.5, tol=1e-8, maxit=200)
     assert it < 200
     assert abs((er + dE) / 66 - e_ccd) < 1.0e-3
+
+
+def _library_labels(S):
+    """(a, b, i, j) of each restricted amplitude in the library layout (per channel n_hh x
+    n_pp, hh rows, pp contiguous)."""
+    tab = S.channel_tables()
+    out = []
+    ho = po = 0
+    for nh, npp in zip(tab["nhh"], tab["npp"]):
+        hh = tab["hh"][ho:ho + nh]
+        pp = tab["pp"][po:po + npp]
+        for i, j in hh:
+            for a, b in pp:
+                out.append((a, b, i, j))
+        ho += nh
+        po += npp
+    return np.array(out, dtype=np.int64).reshape(-1, 4)
+
+
+def test_ph_term_matches_dense(cfg0):
+    """The channel engine's P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj (cross-channel T, C, Q) equals
+    the dense Eq. (ccd3) terms it stands for, P(ij)P(ab) sum_kc <kb|v|cj> t_ik^ac +
+    P(ij) sum_klcd <kl|v|cd> t_ik^ac t_jl^bd, on random antisymmetric amplitudes."""
+    D, S = cfg0
+    N = 14
+    lab = _library_labels(S)
+    rng = np.random.default_rng(21)
+    t = rng.normal(0.0, 0.05, len(lab))
+    td = np.zeros_like(D.D)
+    a, b, i, j = lab[:, 0] - N, lab[:, 1] - N, lab[:, 2], lab[:, 3]
+    td[a, b, i, j] = t
+    td[b, a, i, j] = -t
+    td[a, b, j, i] = -t
+    td[b, a, j, i] = t
+    lin = dense.P_ij(dense.P_ab(np.einsum("kbcj,acik->abij", D.v_kbcj, td)))
+    quad = dense.P_ij(np.einsum("klcd,acik,bdjl->abij", D.v_klcd, td, td, optimize=True))
+    ref = (lin + quad)[a, b, i, j]
+    got = S.ph_apply(t)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    bound = S.ph_apply(t, absval=True)
+    assert np.all(bound >= np.abs(got) - 1e-15)
