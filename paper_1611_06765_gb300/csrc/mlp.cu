@@ -395,6 +395,22 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
   uint32_t phase = 0;
   const long ntiles = (n + MH - 1) / MH;
   const uint32_t lane_addr = tbase + ((uint32_t)(quarter * 32) << 16);
+  // features [16 half, 16 half + 16) of this thread's row of a tile (zeros past n); the next
+  // tile's are loaded while the current one runs through the layers
+  const int k0 = 16 * half;
+  auto load_x = [&](long tile, float4 (&xr)[4]) {
+    long rg = tile * MH + row;
+    if (tile < ntiles && rg < n) {
+      const float4* xp = reinterpret_cast<const float4*>(X + rg * MF + k0);
+#pragma unroll
+      for (int j = 0; j < 4; j++) xr[j] = __ldg(xp + j);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; j++) xr[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  };
+  float4 xnext[4];
+  load_x(blockIdx.x, xnext);
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // every thread leaves together after a failed wait (no thread may skip a barrier)
     __syncthreads();
@@ -403,23 +419,16 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
     if (stop) break;
     const long r_glob = tile * MH + row;
     const bool ok = r_glob < n;
-    // layer-1 input: features [16 half, 16 half + 16) of the row, normalised, BF16
+    float xv[16];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      xv[4 * j] = xnext[j].x; xv[4 * j + 1] = xnext[j].y; xv[4 * j + 2] = xnext[j].z; xv[4 * j + 3] = xnext[j].w;
+    }
+    load_x(tile + gridDim.x, xnext);
+    // layer-1 input: normalised, BF16
     {
-      const int k0 = 16 * half;
-      float xv[16];
-      if (ok) {
-        const float4* xp = reinterpret_cast<const float4*>(X + r_glob * MF + k0);
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-          float4 v = __ldg(xp + j);
-          xv[4 * j] = v.x; xv[4 * j + 1] = v.y; xv[4 * j + 2] = v.z; xv[4 * j + 3] = v.w;
-        }
-#pragma unroll
-        for (int k = 0; k < 16; k++) xv[k] = (xv[k] - mu[k0 + k]) * istd[k0 + k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 16; k++) xv[k] = 0.0f;
-      }
+      for (int k = 0; k < 16; k++) xv[k] = ok ? (xv[k] - mu[k0 + k]) * istd[k0 + k] : 0.0f;
 #pragma unroll
       for (int h = 0; h < 16; h += 8) {
         __align__(16) __nv_bfloat162 v4[4];
