@@ -91,23 +91,32 @@ __global__ void k_pack_t(const int4* __restrict__ pk, const long* __restrict__ p
   }
 }
 
-// The grouped tensor-core pp ladder: one CTA (4 warps) per (channel, 128-row ab tile).
-__global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ items,
-                                                  const __nv_bfloat16* __restrict__ vt,
-                                                  const __nv_bfloat16* __restrict__ bt,
-                                                  float* __restrict__ rpp32, LoopCtl* __restrict__ ctl,
-                                                  uint32_t stage_bytes, int nst, long plane_stride) {
+// Persistent grouped pp ladder: R^T(ij, ab) = sum_cd t(ij, cd) V(cd, ab) for every (channel,
+// ab tile, k-range) item of every system in one launch.  CTA c takes items cta_off[c] ...
+// cta_off[c+1] - 1 (a longest-first greedy plan of the host balances the CTAs); warp 0 streams the V and t tiles of
+// its items through an mbarrier ring of bulk-async copies without a break between items,
+// warp 1 issues the BF16x3 MMAs (hi*hi + hi*lo + lo*hi, FP32 accumulator in tensor memory)
+// into one of two accumulator buffers, and warps 2-5 drain the other buffer (item j-1) while
+// item j accumulates.  Every wait is bounded; a wait that runs out sets ctl->dev_error and
+// the CTA winds down (its own copies waited for, tensor memory freed).
+constexpr int PP_THREADS = 192;
+
+__global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const TCItem* __restrict__ items,
+                                                         const int* __restrict__ cta_off,
+                                                         const __nv_bfloat16* __restrict__ vt,
+                                                         const __nv_bfloat16* __restrict__ bt,
+                                                         float* __restrict__ rpp32, LoopCtl* __restrict__ ctl,
+                                                         uint32_t stage_bytes, int nst, long plane_stride) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TCItem it = items[blockIdx.x];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + TC_MAX_STAGES;
-  uint64_t* done = empty + TC_MAX_STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = empty + TC_MAX_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
   unsigned char* stage0 = smem + 1024;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
-  const uint32_t ncols = it.npad <= 32 ? 32u : 64u;
   __shared__ int err;
+  const int i_begin = cta_off[blockIdx.x], i_end = cta_off[blockIdx.x + 1];
 
   if (threadIdx.x == 0) {
     err = 0;
@@ -115,11 +124,14 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+    }
     mbar_fence_init();
   }
-  if (warp == 2) {
-    tmem_alloc(tslot, ncols);
+  if (warp == 0) {
+    tmem_alloc(tslot, 128);
     tmem_relinquish();
   }
   fence_before();
@@ -127,74 +139,115 @@ __global__ void __launch_bounds__(128, 1) k_pp_tc(const TCItem* __restrict__ ite
   fence_after();
   const uint32_t tbase = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    // producer: one 32 KB copy of the V tile (hi, lo) and one of the t tile per stage
-    const __nv_bfloat16* va = vt + it.voff + (long)it.kb0 * 2 * (TC_M * TC_BK);
-    const __nv_bfloat16* tb = bt + it.boff + (long)it.kb0 * 2 * (it.npad * TC_BK);
-    int issued = 0;
-    for (int kb = 0; kb < it.nkb; kb++) {
-      int s = kb % nst, use = kb / nst;
-      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
-        err = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: one 32 KB copy of the V tile (hi, lo) and one of the t tile per stage
+      long g = 0;
+      bool ok = true;
+      for (int i = i_begin; i < i_end && ok; i++) {
+        const TCItem it = items[i];
+        const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
+        const __nv_bfloat16* va = vt + it.voff + (long)it.kb0 * 2 * (TC_M * TC_BK);
+        const __nv_bfloat16* tb = bt + it.boff + (long)it.kb0 * 2 * (it.npad * TC_BK);
+        for (int kb = 0; kb < it.nkb; kb++) {
+          int s = (int)(g % nst);
+          long use = g / nst;
+          if (use > 0 && !mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+            err = 1;
+            ok = false;
+            break;
+          }
+          unsigned char* st = stage0 + s * stage_bytes;
+          mbar_expect_tx(&full[s], 2 * A_PLANE + 2 * b_plane);
+          bulk_g2s(st, va + (long)kb * 2 * (TC_M * TC_BK), 2 * A_PLANE, &full[s]);
+          bulk_g2s(st + 2 * A_PLANE, tb + (long)kb * 2 * (it.npad * TC_BK), 2 * b_plane, &full[s]);
+          g++;
+        }
       }
-      unsigned char* st = stage0 + s * stage_bytes;
-      mbar_expect_tx(&full[s], 2 * A_PLANE + 2 * b_plane);
-      bulk_g2s(st, va + (long)kb * 2 * (TC_M * TC_BK), 2 * A_PLANE, &full[s]);
-      bulk_g2s(st + 2 * A_PLANE, tb + (long)kb * 2 * (it.npad * TC_BK), 2 * b_plane, &full[s]);
-      issued = kb + 1;
+      // every copy this thread started has landed before the CTA may retire
+      for (long k = (g > nst ? g - nst : 0); k < g; k++)
+        if (!mbar_wait(&full[k % nst], (uint32_t)((k / nst) & 1))) err = 1;
     }
-    // every copy this thread started has landed before the CTA may retire
-    for (int kb = max(0, issued - nst); kb < issued; kb++)
-      if (!mbar_wait(&full[kb % nst], (kb / nst) & 1)) err = 1;
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = idesc_bf16(TC_M, it.npad);
-    for (int kb = 0; kb < it.nkb; kb++) {
-      int s = kb % nst, use = kb / nst;
-      if (!mbar_wait(&full[s], use & 1)) {
-        err = 1;
-        break;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      long g = 0;
+      int j = 0;
+      bool ok = true;
+      for (int i = i_begin; i < i_end && ok; i++, j++) {
+        const TCItem it = items[i];
+        const int buf = j & 1;
+        if (j >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((j >> 1) - 1) & 1))) {
+          err = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t dt = tbase + (uint32_t)(buf * 64);
+        const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
+        const uint32_t idesc = idesc_bf16(TC_M, it.npad);
+        for (int kb = 0; kb < it.nkb; kb++) {
+          int s = (int)(g % nst);
+          long use = g / nst;
+          if (!mbar_wait(&full[s], (uint32_t)(use & 1))) {
+            err = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          unsigned char* a_hi = stage0 + s * stage_bytes;
+          unsigned char* a_lo = a_hi + A_PLANE;
+          unsigned char* b_hi = a_hi + 2 * A_PLANE;
+          unsigned char* b_lo = b_hi + b_plane;
+#pragma unroll
+          for (int ks = 0; ks < TC_BK / 16; ks++) {
+            uint32_t o = ks * 2 * 128;  // two core matrices of K per MMA
+            uint64_t ah = smem_desc(a_hi + o, CORE_LBO, CORE_SBO), al = smem_desc(a_lo + o, CORE_LBO, CORE_SBO);
+            uint64_t bh = smem_desc(b_hi + o, CORE_LBO, CORE_SBO), bl = smem_desc(b_lo + o, CORE_LBO, CORE_SBO);
+            mma_bf16(dt, ah, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+            mma_bf16(dt, ah, bl, idesc, 1u);
+            mma_bf16(dt, al, bh, idesc, 1u);
+          }
+          commit(&empty[s]);
+          g++;
+        }
+        if (ok) commit(&tfull[buf]);
       }
+    }
+  } else {
+    // epilogue warps 2-5: TMEM lane = ab row (quarter warp % 4), column = ij
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int j = 0;
+    for (int i = i_begin; i < i_end; i++, j++) {
+      const TCItem it = items[i];
+      const int buf = j & 1;
+      const bool ok = mbar_wait(&tfull[buf], (uint32_t)((j >> 1) & 1));
       fence_after();
-      unsigned char* a_hi = stage0 + s * stage_bytes;
-      unsigned char* a_lo = a_hi + A_PLANE;
-      unsigned char* b_hi = a_hi + 2 * A_PLANE;
-      unsigned char* b_lo = b_hi + b_plane;
-#pragma unroll
-      for (int ks = 0; ks < TC_BK / 16; ks++) {
-        uint32_t o = ks * 2 * 128;  // two core matrices of K per MMA
-        uint64_t ah = smem_desc(a_hi + o, CORE_LBO, CORE_SBO), al = smem_desc(a_lo + o, CORE_LBO, CORE_SBO);
-        uint64_t bh = smem_desc(b_hi + o, CORE_LBO, CORE_SBO), bl = smem_desc(b_lo + o, CORE_LBO, CORE_SBO);
-        mma_bf16(tbase, ah, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-        mma_bf16(tbase, ah, bl, idesc, 1u);
-        mma_bf16(tbase, al, bh, idesc, 1u);
+      if (!ok) {
+        if (lane == 0) err = 1;
+        break;
       }
-      commit(&empty[s]);
-    }
-    commit(done);
-  }
-  __syncwarp();
-  // epilogue: TMEM lane = ab row, column = ij
-  bool ok = mbar_wait(done, 0);
-  fence_after();
-  const int row = warp * 32 + lane;
-  const int ab = it.mt * TC_M + row;
-  for (int c0 = 0; c0 < it.npad; c0 += 16) {
-    uint32_t r[16];
-    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-    if (ok && ab < it.npp) {
+      const int ab = it.mt * TC_M + row;
+      for (int c0 = 0; c0 < it.npad; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tbase + (uint32_t)(buf * 64) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        if (ab < it.npp) {
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        int ij = c0 + j;
-        if (ij < it.nhh) rpp32[it.plane * plane_stride + it.toff + (long)ij * it.npp + ab] = __uint_as_float(r[j]);
+          for (int jj = 0; jj < 16; jj++) {
+            int ij = c0 + jj;
+            if (ij < it.nhh) rpp32[it.plane * plane_stride + it.toff + (long)ij * it.npp + ab] = __uint_as_float(r[jj]);
+          }
+        }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 2) tmem_dealloc(tbase, ncols);
-  if (threadIdx.x == 0 && (err || !ok)) atomicExch(&ctl->dev_error, 1);
+  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (threadIdx.x == 0 && err) atomicExch(&ctl->dev_error, 1);
 }
 
 // FP32 copy of the current amplitudes.
@@ -250,11 +303,15 @@ struct MixedState {
   uint32_t stage_bytes = 0;
   size_t smem = 0;
   int nst = 3, ksplit = 1;  // chosen by the autotuner
+  int grid = 1;             // CTAs of the persistent ladder
+  int* cta_off = nullptr;   // per CTA: first item (items grouped by CTA), then the total
   float tuned_us = 0.0f;
 };
 
 // Items of the tensor-core ladder for one k-range split factor: each (channel, ab tile)
 // becomes up to `split` items over consecutive k-block ranges (never empty).
+// Sorted by decreasing k-block count, so that the persistent kernel's round robin over CTAs
+// balances.
 static std::vector<TCItem> split_items(const std::vector<TCItem>& base, int split) {
   std::vector<TCItem> out;
   for (const TCItem& b : base) {
@@ -267,7 +324,49 @@ static std::vector<TCItem> split_items(const std::vector<TCItem>& base, int spli
       out.push_back(t);
     }
   }
+  std::stable_sort(out.begin(), out.end(), [](const TCItem& x, const TCItem& y) { return x.nkb > y.nkb; });
   return out;
+}
+
+// Grid of the persistent ladder: every CTA that fits on the GPU at this shared-memory size.
+static int pp_grid(size_t smem, int nitems) {
+  int dev = 0, nsm = 1, per_sm = 1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pp_tc, PP_THREADS, smem));
+  // at most 4 CTAs per SM: 4 x 128 tensor-memory columns fill the SM's 512
+  return std::max(1, std::min(nitems, nsm * std::min(4, std::max(1, per_sm))));
+}
+
+// Longest-first greedy plan: items (in decreasing cost) go one by one to the least loaded CTA
+// (cost = k-blocks + 1 for the epilogue); returns the items grouped by CTA and the CTA offsets.
+static void plan_items(const std::vector<TCItem>& its, int grid, std::vector<TCItem>* order, std::vector<int>* off) {
+  std::vector<std::vector<int>> per(grid);
+  std::vector<std::pair<long, int>> heap;
+  for (int c = 0; c < grid; c++) heap.push_back({0L, c});
+  auto cmp = [](const std::pair<long, int>& a, const std::pair<long, int>& b) {
+    return a.first != b.first ? a.first > b.first : a.second > b.second;
+  };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  for (int i = 0; i < (int)its.size(); i++) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    auto& h = heap.back();
+    per[h.second].push_back(i);
+    h.first += its[i].nkb + 1;
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  order->clear();
+  off->assign(grid + 1, 0);
+  for (int c = 0; c < grid; c++) {
+    for (int i : per[c]) order->push_back(its[i]);
+    (*off)[c + 1] = (int)order->size();
+  }
+}
+
+static void launch_pp_tc(const TCItem* items, const int* cta_off, int grid, const MixedState* M, size_t smem,
+                         int nst, LoopCtl* ctl, long nt, cudaStream_t s) {
+  if (grid > 0)
+    k_pp_tc<<<grid, PP_THREADS, smem, s>>>(items, cta_off, M->vt, M->bt, M->rpp32, ctl, M->stage_bytes, nst, nt);
 }
 
 // Tile choices already measured in this process, per channel-size signature.
@@ -392,6 +491,13 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       }
     }
     TCItem* trial = mdalloc<TCItem>(ctx, split_items(items, TC_MAX_SPLIT).size());
+    int dev = 0, nsm = 1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int* trial_off = mdalloc<int>(ctx, 4 * (size_t)nsm + 1);
+    M->cta_off = mdalloc<int>(ctx, 4 * (size_t)nsm + 1);
+    std::vector<TCItem> order;
+    std::vector<int> off;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -399,15 +505,16 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       if (cached) break;
       std::vector<TCItem> its = split_items(items, split);
       if (its.empty()) break;
-      CUDA_TRY(cudaMemcpyAsync(trial, its.data(), sizeof(TCItem) * its.size(), cudaMemcpyHostToDevice, s));
       for (int nst = 2; nst <= max_st; nst++) {
+        int grid = pp_grid(smem_for(nst), (int)its.size());
+        plan_items(its, grid, &order, &off);
+        CUDA_TRY(cudaMemcpyAsync(trial, order.data(), sizeof(TCItem) * order.size(), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(trial_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
         for (int w = 0; w < 2; w++)
-          k_pp_tc<<<(int)its.size(), 128, smem_for(nst), s>>>(trial, M->vt, M->bt, M->rpp32, ctx->ctl,
-                                                               M->stage_bytes, nst, ctx->nt);
+          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->nt, s);
         CUDA_TRY(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 5; rep++)
-          k_pp_tc<<<(int)its.size(), 128, smem_for(nst), s>>>(trial, M->vt, M->bt, M->rpp32, ctx->ctl,
-                                                               M->stage_bytes, nst, ctx->nt);
+          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->nt, s);
         CUDA_TRY(cudaEventRecord(e1, s));
         CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0;
@@ -433,8 +540,10 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     }
     M->smem = smem_for(M->nst);
     M->nitems = (int)best_items.size();
-    CUDA_TRY(cudaMemcpyAsync(M->items, best_items.data(), sizeof(TCItem) * best_items.size(),
-                             cudaMemcpyHostToDevice, s));
+    M->grid = pp_grid(M->smem, M->nitems);
+    plan_items(best_items, M->grid, &order, &off);
+    CUDA_TRY(cudaMemcpyAsync(M->items, order.data(), sizeof(TCItem) * order.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(M->cta_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
     CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
@@ -456,8 +565,7 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
   }
   if (M->nitems > 0) {
     prof_begin(ctx, KID_PP_TC);
-    k_pp_tc<<<M->nitems, 128, M->smem, s_pp>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes,
-                                                M->nst, ctx->nt);
+    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->nt, s_pp);
     prof_end(ctx);
   }
   pnm_enqueue_stats(ctx, true);
@@ -519,9 +627,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     MixedState* M = ctx->mixed;
     CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * ctx->nt, s));
     if (M->npk > 0) k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
-    if (M->nitems > 0)
-      k_pp_tc<<<M->nitems, 128, M->smem, s>>>(M->items, M->vt, M->bt, M->rpp32, ctx->ctl, M->stage_bytes,
-                                              M->nst, ctx->nt);
+    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->nt, s);
     CUDA_TRY(cudaGetLastError());
     std::vector<float> f((size_t)TC_MAX_SPLIT * ctx->nt);
     CUDA_TRY(cudaMemcpyAsync(f.data(), M->rpp32, sizeof(float) * f.size(), cudaMemcpyDeviceToHost, s));
