@@ -24,6 +24,9 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched through the runtime)
+#include <cudaTypedefs.h>
+
 #include "pnm_context.cuh"
 #include "tc_ptx.cuh"
 
@@ -101,7 +104,8 @@ __global__ void k_pack_t(const int4* __restrict__ pk, const long* __restrict__ p
 // the CTA winds down (its own copies waited for, tensor memory freed).
 constexpr int PP_THREADS = 192;
 
-__global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const TCItem* __restrict__ items,
+__global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__ CUtensorMap tmap_v,
+                                                         const TCItem* __restrict__ items,
                                                          const int* __restrict__ cta_off,
                                                          const __nv_bfloat16* __restrict__ vt,
                                                          const __nv_bfloat16* __restrict__ bt,
@@ -141,13 +145,13 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const TCItem* __restric
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: one 32 KB copy of the V tile (hi, lo) and one of the t tile per stage
+      // producer: per stage one tiled tensor copy of the V tile (hi, lo planes: 256 rows of 64
+      // BF16) and one bulk copy of the t tile
       long g = 0;
       bool ok = true;
       for (int i = i_begin; i < i_end && ok; i++) {
         const TCItem it = items[i];
         const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
-        const __nv_bfloat16* va = vt + it.voff + (long)it.kb0 * 2 * (TC_M * TC_BK);
         const __nv_bfloat16* tb = bt + it.boff + (long)it.kb0 * 2 * (it.npad * TC_BK);
         for (int kb = 0; kb < it.nkb; kb++) {
           int s = (int)(g % nst);
@@ -159,7 +163,8 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const TCItem* __restric
           }
           unsigned char* st = stage0 + s * stage_bytes;
           mbar_expect_tx(&full[s], 2 * A_PLANE + 2 * b_plane);
-          bulk_g2s(st, va + (long)kb * 2 * (TC_M * TC_BK), 2 * A_PLANE, &full[s]);
+          tma_load_2d(st, &tmap_v, 0, (int)((it.voff + (long)(it.kb0 + kb) * 2 * (TC_M * TC_BK)) / TC_BK),
+                      &full[s]);
           bulk_g2s(st + 2 * A_PLANE, tb + (long)kb * 2 * (it.npad * TC_BK), 2 * b_plane, &full[s]);
           g++;
         }
@@ -305,6 +310,7 @@ struct MixedState {
   int nst = 3, ksplit = 1;  // chosen by the autotuner
   int grid = 1;             // CTAs of the persistent ladder
   int* cta_off = nullptr;   // per CTA: first item (items grouped by CTA), then the total
+  CUtensorMap tmap_v;       // the V tile arena for the tiled tensor copies
   float tuned_us = 0.0f;
 };
 
@@ -366,7 +372,35 @@ static void plan_items(const std::vector<TCItem>& its, int grid, std::vector<TCI
 static void launch_pp_tc(const TCItem* items, const int* cta_off, int grid, const MixedState* M, size_t smem,
                          int nst, LoopCtl* ctl, long nt, cudaStream_t s) {
   if (grid > 0)
-    k_pp_tc<<<grid, PP_THREADS, smem, s>>>(items, cta_off, M->vt, M->bt, M->rpp32, ctl, M->stage_bytes, nst, nt);
+    k_pp_tc<<<grid, PP_THREADS, smem, s>>>(M->tmap_v, items, cta_off, M->vt, M->bt, M->rpp32, ctl,
+                                           M->stage_bytes, nst, nt);
+}
+
+// Tensor map of the V tile arena as a 2-D BF16 tensor of rows x 64 (128-byte rows); one box
+// is a whole tile (hi and lo planes, 256 rows).
+static CUtensorMap v_tensor_map(__nv_bfloat16* vt, long elems) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+      CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+      if (q != cudaDriverEntryPointSuccess || !fn) throw PnmError{PNM_ECUDA, "cuTensorMapEncodeTiled not available"};
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  CUtensorMap map;
+  cuuint64_t dims[2] = {(cuuint64_t)TC_BK, (cuuint64_t)(elems / TC_BK)};
+  cuuint64_t strides[1] = {(cuuint64_t)TC_BK * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)(2 * TC_M)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, vt, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw PnmError{PNM_ECUDA, "cuTensorMapEncodeTiled failed for the V tiles"};
+  return map;
 }
 
 // Tile choices already measured in this process, per channel-size signature.
@@ -418,7 +452,9 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     }
     M->nitems = (int)items.size();
     M->npk = (int)pk.size();
-    M->vt = mdalloc<__nv_bfloat16>(ctx, voff);
+    const long vt_elems = std::max<long>(voff, 2L * TC_M * TC_BK);  // at least one whole box
+    M->vt = mdalloc<__nv_bfloat16>(ctx, vt_elems);
+    M->tmap_v = v_tensor_map(M->vt, vt_elems);
     M->bt = mdalloc<__nv_bfloat16>(ctx, boff);
     M->items = mdalloc<TCItem>(ctx, split_items(items, TC_MAX_SPLIT).size());
     M->pk = mdalloc<int4>(ctx, pk.size());
