@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--model", default=None, help="load the warm-start network (.npy) instead of training it")
     ap.add_argument("--save-model", default=None, help="write the trained warm-start network (.npy)")
+    ap.add_argument("--train-epochs", type=int, default=20, help="warm-start training epochs")
+    ap.add_argument("--train-batch", type=int, default=1024, help="warm-start training batch")
     return ap.parse_args()
 
 
@@ -298,7 +300,8 @@ def trained_model(P, stream):
         tr14.solve(**kw64)
         tr66 = P.Context(66, 0.16, 36, params=MINNESOTA, stream=stream.cuda_stream)
         tr66.solve(**kw64)
-        blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=12, batch=4096, lr=1e-3, seed=2)
+        blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=_model.get("epochs", 20),
+                                 batch=_model.get("batch", 1024), lr=1e-3, seed=2)
         tr14.close()
         tr66.close()
         _model.update(blob=blob, train_s=time.perf_counter() - t0, loss=[float(hist[0]), float(hist[-1])])
@@ -353,6 +356,21 @@ def oracle_leg(workloads, budget_s=60.0):
     return out
 
 
+def oracle_one_thread():
+    """The oracle on one host thread, full solve of N = 14, rho = 0.08, n^2 <= 20 (ms), beside
+    the all-core figure of the same solve."""
+    from oracle import channel
+    n = channel.threads()
+    ms_all, _, _ = oracle_solve(14, 0.08, 20)
+    channel.set_threads(1)
+    try:
+        ms_one, _, it = oracle_solve(14, 0.08, 20)
+    finally:
+        channel.set_threads(n)
+    return {"workload": "pnm_N14_rho0.08_n2max20", "ms_1_thread": ms_one, "ms_all_threads": ms_all,
+            "threads": n, "iterations": it}
+
+
 def oracle_errors(res, workload, ora):
     N, rhos, n2max, _, _ = WORKLOADS[workload]
     err = {}
@@ -377,6 +395,7 @@ def run_ours(a):
     import paper_1611_06765_gb300 as P
     N, rhos, n2max, start, prec_name = WORKLOADS[a.workload]
     _model["path"] = a.model
+    _model["epochs"], _model["batch"] = a.train_epochs, a.train_batch
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ctx = make_context(P, a.workload, stream)
@@ -461,6 +480,7 @@ def run_ours(a):
                 comparison[w] = measure(P, torch, stream, flush, w, a.refine, 5)
         if "train_s" in _model:
             comparison["training"] = {"seconds": _model["train_s"], "loss_first_last": _model["loss"],
+                                      "epochs": _model["epochs"], "batch": _model["batch"],
                                       "data": "FP64-converged amplitudes, N=14 n2max=20 16 densities "
                                               "and N=66 n2max=36 rho=0.16"}
 
@@ -486,7 +506,8 @@ def run_ours(a):
                "errors": "dE_per_N_minus_oracle fields: GPU dE/N minus the oracle's fixed point "
                          "(converged to 1e-10 MeV per neutron)",
                "oracle_iters": {str(k[1]): v[2] for k, v in ora.items() if k[0] == N and k[2] == n2max
-                                and k[1] in rhos}}
+                                and k[1] in rhos},
+               "one_thread": oracle_one_thread()}
         result["dE_per_N_minus_oracle"] = oracle_errors(result, a.workload, ora)
         if comparison:
             for w, r in comparison.items():

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
   if ((int)blockIdx.x < nrows) {
     int2 it = D.row_item[blockIdx.x];
     int c = it.x, kl = it.y;
+    if (sys_done(D, ctl, D.ch_sys[c])) return;
     int npp = D.ch_npp[c], nh = D.ch_nhh[c];
     long base = D.ch_t_off[c];
     const T_* tr = t + base + (long)kl * npp;
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
   } else {
     int2 it = ab_items[blockIdx.x - nrows];
     int c = it.x, ab = it.y + threadIdx.x;
+    if (sys_done(D, ctl, D.ch_sys[c])) return;
     int npp = D.ch_npp[c], nh = D.ch_nhh[c];
     if (ab < npp) {
       long base = D.ch_t_off[c] + ab;
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict
   extern __shared__ __align__(16) unsigned char smraw[];
   T_* sm = reinterpret_cast<T_*>(smraw);
   int x = xlist[blockIdx.x];
+  if (sys_done(D, ctl, D.x_sys[x])) return;
   int nph = D.x_nph[x], nhp = D.x_nhp[x];
   int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
   T_* Ts = sm;
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const Loo
   const int idx = blockIdx.x * PH_WARPS + w;
   if (idx >= nlist) return;  // whole warps leave; nothing below synchronises the block
   const int x = xlist[idx];
+  if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
   T_* Ts = reinterpret_cast<T_*>(smraw) + (size_t)w * 3 * S * S;  // T[u][s]
@@ -354,6 +358,7 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const Loop
   extern __shared__ double sm[];  // ts[PP64_ROWS][npp], red[PP64_WARPS][PP64_ROWS][32]
   int2 it = items[blockIdx.x];
   int c = it.x, ab0 = it.y;
+  if (sys_done(D, ctl, D.ch_sys[c])) return;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   long tb = D.ch_t_off[c];
   const double* __restrict__ t = cur_t(D, ctl);
@@ -440,7 +445,10 @@ __device__ void finalize_systems(const FinArgs& f, LoopCtl* ctl) {
         double diff = fabs(e - S.e_old);
         S.e_old = e;
         if (!isfinite(e) || !isfinite(r)) bad = 1;
-        if (diff < S.tol && ctl->iter + 1 >= ctl->min_iter) S.done = 1;
+        if (diff < S.tol && ctl->iter + 1 >= ctl->min_iter) {
+          S.done = 1;
+          S.frozen_at = ctl->iter;
+        }
       }
       if (!S.done) all_done = 0;
     }
@@ -500,6 +508,15 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   int ab = it.z + threadIdx.x;
   bool frozen = fa.sc[D.ch_sys[c]].done != 0;
+  if (sys_settled(fa.sc[D.ch_sys[c]], ctl)) {
+    // converged at least two steps ago: both amplitude buffers already hold its values
+    if (threadIdx.x == 0) {
+      D.eparts[blockIdx.x] = 0.0;
+      D.rparts[blockIdx.x] = 0.0;
+    }
+    last_block_finalize(fa, ctl);
+    return;
+  }
   bool szero = D.ch_szero[c] != 0;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
@@ -582,6 +599,7 @@ __global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restr
   extern __shared__ __align__(16) float hsm[];
   int2 it = ab_items[blockIdx.x];
   int c = it.x, ab = it.y + threadIdx.x;
+  if (sys_done(D, ctl, D.ch_sys[c])) return;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   const float* __restrict__ t32 = cur_t32(D, ctl);
   float* chs = hsm;            // chi[kl][ij], nh x nh
@@ -639,6 +657,15 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
   }
   bool frozen = fa.sc[D.ch_sys[c]].done != 0;
+  if (sys_settled(fa.sc[D.ch_sys[c]], ctl)) {
+    // converged at least two steps ago: both amplitude buffers already hold its values
+    if (threadIdx.x == 0) {
+      D.eparts[blockIdx.x] = 0.0;
+      D.rparts[blockIdx.x] = 0.0;
+    }
+    last_block_finalize(fa, ctl);
+    return;
+  }
   bool szero = D.ch_szero[c] != 0;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
@@ -968,6 +995,8 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   CUDA_TRY(cudaMemsetAsync(ctx->ctl, 0, sizeof(LoopCtl), s));
   ctx->small = (double*)dmalloc(ctx, sizeof(double) * 8);
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
+  CUDA_TRY(cudaMemsetAsync(ctx->sysctl, 0, sizeof(SysCtl) * nsys, s));
+  ctx->d.sysctl = ctx->sysctl;
   // cross channels for the mixed ph launches: the large ones first, each class largest first
   std::vector<int> big, mid, small;
   for (int x = 0; x < ctx->nx; x++) {
@@ -1217,9 +1246,11 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_lo
   // are set here
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->max_iter, &max_iter, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->min_iter, &min_iter, sizeof(int), cudaMemcpyHostToDevice, s));
+  static const int kOne = 1, kZero = 0;
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->mode, &mode, sizeof(int), cudaMemcpyHostToDevice, s));
   if (max_iter <= 0) return PNM_ENOTCONV;
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &kOne, sizeof(int), cudaMemcpyHostToDevice, s));
   if (!host_loop) {
     cudaGraphExec_t ge = graph_for(ctx, mode);
     CUDA_TRY(cudaGraphLaunch(ge, s));
@@ -1236,6 +1267,7 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_lo
     ctx->prof_live = false;
   }
   CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &kZero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return hc.status;

@@ -42,6 +42,7 @@ constexpr uint32_t CORE_SBO = (TC_BK / 8) * 128;  // next 8-row group along M/N
 
 struct TCItem {
   int ch, mt, kb0, nkb;  // channel, ab tile, first k-block and number of k-blocks of this item
+  int sys;               // system of the channel
   int npad, npp, nhh, plane;  // padded N, sizes, output plane (k-range split index)
   long voff;   // element offset of tile (mt, 0) in the V tile arena
   long boff;   // element offset of k-block 0 in the t tile arena
@@ -107,6 +108,7 @@ constexpr int PP_THREADS = 192;
 __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__ CUtensorMap tmap_v,
                                                          const TCItem* __restrict__ items,
                                                          const int* __restrict__ cta_off,
+                                                         const SysCtl* __restrict__ sc,
                                                          const __nv_bfloat16* __restrict__ vt,
                                                          const __nv_bfloat16* __restrict__ bt,
                                                          float* __restrict__ rpp32, LoopCtl* __restrict__ ctl,
@@ -121,6 +123,9 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ int err;
   const int i_begin = cta_off[blockIdx.x], i_end = cta_off[blockIdx.x + 1];
+  // items of converged systems are skipped by all three roles alike (the flags do not change
+  // during a launch)
+  const bool skip = ctl->skip_done != 0;
 
   if (threadIdx.x == 0) {
     err = 0;
@@ -151,6 +156,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
       bool ok = true;
       for (int i = i_begin; i < i_end && ok; i++) {
         const TCItem it = items[i];
+        if (skip && sc[it.sys].done) continue;
         const uint32_t b_plane = (uint32_t)it.npad * TC_BK * 2;
         const __nv_bfloat16* tb = bt + it.boff + (long)it.kb0 * 2 * (it.npad * TC_BK);
         for (int kb = 0; kb < it.nkb; kb++) {
@@ -179,8 +185,9 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
       long g = 0;
       int j = 0;
       bool ok = true;
-      for (int i = i_begin; i < i_end && ok; i++, j++) {
+      for (int i = i_begin; i < i_end && ok; i++) {
         const TCItem it = items[i];
+        if (skip && sc[it.sys].done) continue;
         const int buf = j & 1;
         if (j >= 2 && !mbar_wait(&tempty[buf], (uint32_t)(((j >> 1) - 1) & 1))) {
           err = 1;
@@ -216,6 +223,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
           g++;
         }
         if (ok) commit(&tfull[buf]);
+        j++;
       }
     }
   } else {
@@ -223,8 +231,9 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
     const int q = warp & 3;
     const int row = q * 32 + lane;
     int j = 0;
-    for (int i = i_begin; i < i_end; i++, j++) {
+    for (int i = i_begin; i < i_end; i++) {
       const TCItem it = items[i];
+      if (skip && sc[it.sys].done) continue;
       const int buf = j & 1;
       const bool ok = mbar_wait(&tfull[buf], (uint32_t)((j >> 1) & 1));
       fence_after();
@@ -247,6 +256,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
+      j++;
     }
   }
   fence_before();
@@ -311,6 +321,7 @@ struct MixedState {
   int grid = 1;             // CTAs of the persistent ladder
   int* cta_off = nullptr;   // per CTA: first item (items grouped by CTA), then the total
   CUtensorMap tmap_v;       // the V tile arena for the tiled tensor copies
+  const SysCtl* sysctl = nullptr;  // the context's per-system loop state
   float tuned_us = 0.0f;
 };
 
@@ -372,7 +383,7 @@ static void plan_items(const std::vector<TCItem>& its, int grid, std::vector<TCI
 static void launch_pp_tc(const TCItem* items, const int* cta_off, int grid, const MixedState* M, size_t smem,
                          int nst, LoopCtl* ctl, long nt, cudaStream_t s) {
   if (grid > 0)
-    k_pp_tc<<<grid, PP_THREADS, smem, s>>>(M->tmap_v, items, cta_off, M->vt, M->bt, M->rpp32, ctl,
+    k_pp_tc<<<grid, PP_THREADS, smem, s>>>(M->tmap_v, items, cta_off, M->sysctl, M->vt, M->bt, M->rpp32, ctl,
                                            M->stage_bytes, nst, nt);
 }
 
@@ -411,6 +422,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
   if (ctx->mixed) return;
   cudaStream_t s = ctx->stream;
   MixedState* M = new MixedState();
+  M->sysctl = ctx->sysctl;
   try {
     std::vector<TCItem> items;
     std::vector<int4> pk;
@@ -441,6 +453,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
         t.voff = voff + (long)mt * nkb * 2 * (TC_M * TC_BK);
         t.boff = boff;
         t.toff = ctx->h_t_off[c];
+        t.sys = ctx->h_ch_sys[c];
         items.push_back(t);
       }
       for (int kb = 0; kb < nkb; kb++) {
@@ -657,6 +670,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   int zero = 0;
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   std::vector<double> out(ctx->nt, 0.0);
   if (precision == PNM_PREC_BF16X3) {
@@ -711,6 +725,7 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   int zero = 0;
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   unsigned nb = (unsigned)((ctx->nt + 255) / 256);
   if (precision == PNM_PREC_BF16X3) {

@@ -65,6 +65,7 @@ struct DevState {
   int2* row_item;        // (channel, ij)
   // cross channels
   int *x_nph, *x_nhp;
+  int* x_sys;            // cross channel -> system
   long *x_t_off, *x_c_off, *x_w_off;
   int2 *ph_pair, *hp_pair;
   int* x_ph_off;
@@ -84,6 +85,8 @@ struct DevState {
   float *v32, *vhh32, *chi32, *sij32, *sab32, *dchi32;
   double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;
   double *eparts, *rparts;
+  // per-system loop state (converged systems are frozen: later steps skip their work)
+  const struct SysCtl* sysctl;
 };
 
 // Work-list items for the grouped pp-ladder launch (FP64 path).
@@ -103,6 +106,7 @@ struct LoopCtl {
   int status;        // 0 running, 1 converged, PNM_ENOTCONV, PNM_EDIVERGED
   int mode;          // 0 FP64 iteration, 1 mixed iteration
   int min_iter;      // no system counts as converged before this many updates
+  int skip_done;     // 1 inside the solve loop: kernels skip the work of converged systems
   double alpha;
 };
 
@@ -111,7 +115,19 @@ struct SysCtl {
   double tol;
   int done;       // 1 once converged
   int iters;
+  int frozen_at;  // index of the update after which it converged (valid while done)
 };
+
+// True inside the solve loop once system `sys` has met its stopping rule (its amplitudes are
+// frozen): the contraction kernels of later steps skip its work, and the update skips it too
+// from the second step on (the first one copies the amplitudes into the other buffer, after
+// which both buffers hold them).
+__device__ __forceinline__ bool sys_done(const DevState& D, const LoopCtl* ctl, int sys) {
+  return ctl->skip_done != 0 && D.sysctl != nullptr && D.sysctl[sys].done != 0;
+}
+__device__ __forceinline__ bool sys_settled(const SysCtl& S, const LoopCtl* ctl) {
+  return ctl->skip_done != 0 && S.done != 0 && ctl->iter >= S.frozen_at + 2;
+}
 
 // Arguments of the end-of-update step (energy, convergence test, loop condition).
 struct FinArgs {

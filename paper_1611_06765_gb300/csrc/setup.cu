@@ -728,6 +728,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   D.ch_vhh_off = dalloc<long>(C, ctx->owned);
   D.row_item = dalloc<int2>(ctx->nrows, ctx->owned);
   D.x_nph = dalloc<int>(NX, ctx->owned);
+  D.x_sys = dalloc<int>(NX, ctx->owned);
   D.x_nhp = dalloc<int>(NX, ctx->owned);
   D.x_ph_off = dalloc<int>(NX, ctx->owned);
   D.x_hp_off = dalloc<int>(NX, ctx->owned);
@@ -735,6 +736,12 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   D.x_c_off = dalloc<long>(NX, ctx->owned);
   D.x_w_off = dalloc<long>(NX, ctx->owned);
   h2d(D.ch_sys, h_ch_sys, s);
+  {
+    std::vector<int> h_x_sys(NX);
+    for (int k = 0; k < nsys; k++)
+      for (int x = ctx->sys[k].x_begin; x < ctx->sys[k].x_end; x++) h_x_sys[x] = k;
+    h2d(D.x_sys, h_x_sys, s);
+  }
   h2d(D.ch_key, h_key, s);
   h2d(D.ch_nhh, h_nhh, s);
   h2d(D.ch_npp, h_npp, s);

@@ -26,6 +26,8 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   if (!(o.tol_dE > 0.0) && !(o.tol_dE_per_N > 0.0)) throw PnmError{PNM_EINVAL, "no tolerance given"};
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
+  // work skipping for converged systems is scoped to the solve loops
+  CUDA_TRY(cudaMemsetAsync(&ctx->ctl->skip_done, 0, sizeof(int), s));
   std::vector<double> tol(nsys);
   for (int k = 0; k < nsys; k++)
     tol[k] = o.tol_dE_per_N > 0.0 ? o.tol_dE_per_N * ctx->sys[k].N : o.tol_dE;
