@@ -58,7 +58,7 @@ MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload
 # (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {"k_pp64": 1.820785e9, "k_pp_tc": 0.876272e9, "k_update_mix": 0.341905e9}
+TRAFFIC = {"k_pp64": 1.820952e9, "k_pp_tc": 0.876660e9, "k_update_mix": 0.341421e9}
 ALPHA = 0.5
 
 
@@ -485,6 +485,7 @@ def run_ours(a):
                                               "and N=66 n2max=36 rho=0.16"}
 
     result = {"dE_per_N": [x / N for x in dEs[-1]], "iters": iters[-1], "step_ms_min": min(step_ms),
+              "step_ms_max": max(step_ms), "step_ms": [round(x, 4) for x in step_ms],
               "step_ms_median": statistics.median(step_ms), "wall_ms_per_step": wall * 1e3 / a.steps,
               "setup_ms": tim["setup"], "mixed_phase_ms": tim["mixed"], "refine_ms": tim["refine"],
               "kernels_ms_per_solve": {k: v[0] for k, v in stats.items()}}

@@ -1239,7 +1239,7 @@ static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
 
 // Runs updates until every system meets its tolerance or the cap is hit.  Returns the
 // loop status (1 converged, PNM_ENOTCONV, PNM_EDIVERGED).
-int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha) {
+int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha, int* iter_out) {
   cudaStream_t s = ctx->stream;
   LoopCtl hc{};
   // keep iteration parity: ctl->iter is reset by k_start; only the limits, alpha and mode
@@ -1270,6 +1270,7 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_lo
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &kZero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&hc, ctx->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (iter_out) *iter_out = hc.iter;
   return hc.status;
 }
 

@@ -108,7 +108,8 @@ void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditional
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_mixed(pnm_ctx* ctx);
 void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);
-int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha);
+int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_loop, double alpha,
+                 int* iter_out = nullptr);
 void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
 void pnm_mlp_start(pnm_ctx* ctx);

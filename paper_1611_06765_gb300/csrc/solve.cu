@@ -64,13 +64,11 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   }
   pnm_start(ctx, init, tol);
   if (mixed) pnm_mixed_pack_initial(ctx);
+  int it0 = 0;
   int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : PNM_PREC_FP64, o.max_iter, 0, o.host_loop,
-                            o.mix_alpha);
+                            o.mix_alpha, &it0);
   CUDA_TRY(cudaEventRecord(e1, s));
   if (mixed && status == 1 && o.refine_sweeps > 0) {
-    int it0 = 0;
-    CUDA_TRY(cudaMemcpyAsync(&it0, &ctx->ctl->iter, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
     // exactly refine_sweeps FP64 updates, then (if the FP64 test has not passed by then)
     // further FP64 updates until it does, within max_iter more
     pnm_reopen(ctx);
