@@ -1,4 +1,4 @@
-"""FP64 reference of the learned warm-start network (not part of the paper: BASELINE config 4).
+"""FP64 reference of the learned warm-start network (not part of the paper: the warm start of the CCD iteration).
 
 TEST INFRASTRUCTURE ONLY.
 

@@ -187,13 +187,19 @@ def test_open_shell_rejected(pkg):
 
 
 def test_batch_matches_single_systems(pkg):
+    """Densities of one batch converge after different numbers of updates; a converged one is
+    frozen and its work skipped while the others go on.  Each must still follow the oracle's
+    own iteration: same count, history, energy and final amplitudes."""
     rhos = [0.04, 0.08, 0.12]
     g = pkg.Context(14, rhos, 20, params=minnesota_params())
     dE, it, _, _ = g.solve(alpha=0.5, tol=1e-10, max_iter=300)
+    assert len(set(int(x) for x in it)) > 1
     for k, rho in enumerate(rhos):
         o = orc_of(14, rho, 20)
         dE_o, it_o, h_o, _ = o.ccd(alpha=0.5, tol=1e-10, maxit=300)
         assert it[k] == it_o
         assert abs(dE[k] - dE_o) <= 1e-10 * abs(dE_o)
         assert np.max(np.abs(g.history(k) - h_o) / np.abs(h_o)) < 1e-10
+        t_o = o.t_gather(g.amplitude_labels(k))
+        assert np.max(np.abs(g.get_amplitudes(k) - t_o)) <= 1e-10 * np.max(np.abs(t_o))
     g.close()
