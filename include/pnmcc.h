@@ -93,6 +93,29 @@ int pnm_create(int N, double rho, int n2max, const pnm_minnesota *params, void *
 int pnm_create_batch(int n, const int *N, const double *rho, const int *n2max,
                      const pnm_minnesota *params, void *stream, pnm_ctx **out);
 
+/* Twisted boundary conditions (Sec. "Twist-averaged boundary conditions"): as
+ * pnm_create_batch, with system k's single-particle momenta k = (2 pi n + theta_k)/L.
+ * theta: 3n doubles (radians, x y z per system), NULL for periodic boundaries; host memory,
+ * read during the call.  The model space stays n^2 <= n2max; the states are reordered by
+ * |n + theta/2pi|^2 (equal values keep the shell order) and the lowest N are the holes.  The
+ * three axis terms of |n + theta/2pi|^2 are rounded one by one and added smallest first, so
+ * twists with equal components give equal energies to states that differ by a permutation.
+ * PNM_EINVAL (message naming the system) if a twist leaves no gap between state N-1 and
+ * state N (a degenerate Fermi level: the reference is not unique), or a twist is not finite. */
+int pnm_create_twisted(int n, const int *N, const double *rho, const int *n2max,
+                       const double *theta, const pnm_minnesota *params, void *stream,
+                       pnm_ctx **out);
+
+/* Product Gauss-Legendre twist mesh of the twist-averaging loop (Sec. "Twist-averaged
+ * boundary conditions"): nx, ny, nz nodes (1..64) on [0, pi] per axis, points in x-major
+ * order (m = (i ny + j) nz + k).  theta: 3 nx ny nz doubles (radians); weight: nx ny nz
+ * doubles, w_x w_y w_z / pi^3 with w the Gauss-Legendre weights on [0, pi], so they sum to 1
+ * and the twist average of E is sum_m weight[m] E(theta_m).  Host memory owned by the caller;
+ * pure host computation.  Equal node counts on two axes put mesh points on the planes
+ * theta_x = theta_y (and so on), where the Fermi level can be degenerate; distinct counts
+ * with at most one odd count avoid equal components altogether.  PNM_EINVAL on bad sizes. */
+int pnm_twist_mesh(int nx, int ny, int nz, double *theta, double *weight);
+
 /* Release the context and all its device memory.  NULL is accepted. */
 int pnm_destroy(pnm_ctx *ctx);
 

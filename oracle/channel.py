@@ -20,6 +20,9 @@ def lib():
         vp = C.c_void_p
         L.om_create.restype = vp
         L.om_create.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.om_create_twisted.restype = vp
+        L.om_create_twisted.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_int)]
         L.om_destroy.argtypes = [vp]
         for name in ("om_nsp", "om_nchan", "om_nxchan"):
             getattr(L, name).restype = C.c_int
@@ -61,14 +64,21 @@ def _ptr(a):
 class OracleSystem:
     """One (N, rho, n2max) pure-neutron-matter system in the C oracle."""
 
-    def __init__(self, N, rho, n2max, params):
-        """params: (V_R, kappa_R, V_T, kappa_T, V_S, kappa_S, hbar^2/2m)."""
+    def __init__(self, N, rho, n2max, params, theta=None):
+        """params: (V_R, kappa_R, V_T, kappa_T, V_S, kappa_S, hbar^2/2m); theta: twist angles
+        (radians, one per axis) or None for periodic boundary conditions."""
         L = lib()
         p = (C.c_double * 7)(*[float(x) for x in params])
         err = C.c_int(0)
-        h = L.om_create(int(N), float(rho), int(n2max), p, C.byref(err))
+        if theta is None:
+            h = L.om_create(int(N), float(rho), int(n2max), p, C.byref(err))
+        else:
+            th = (C.c_double * 3)(*[float(x) for x in theta])
+            h = L.om_create_twisted(int(N), float(rho), int(n2max), p, th, C.byref(err))
         if not h:
-            raise ValueError("oracle: invalid system (N=%d is not a closed shell of n2max=%d?)" % (N, n2max))
+            raise ValueError("oracle: invalid system (N=%d is not a closed shell of n2max=%d "
+                             "at twist %s?)" % (N, n2max, theta))
+        self.theta = None if theta is None else tuple(float(x) for x in theta)
         self._h = C.c_void_p(h)
         self.N, self.rho, self.n2max = int(N), float(rho), int(n2max)
         self.nsp = L.om_nsp(self._h)

@@ -4,20 +4,22 @@ TEST INFRASTRUCTURE ONLY.  For two particles the CCD wave function exp(T2)|Phi_0
 (1 + T2)|Phi_0> spans the whole two-body sector of the reference (singles vanish by
 momentum conservation), so converged CCD equals the exact ground-state energy.  This
 module diagonalises H = sum_p h0_p a+_p a_p + 1/4 sum <pq|v|rs> a+_p a+_q a_s a_r in the
-sector of two-particle states |pq>, p < q, with total momentum 0 and S_z = 0, where
+sector of two-particle states |pq>, p < q, with the reference pair's total momentum and
+S_z (zero for periodic boundary conditions; a twist can move the lowest pair), where
 <pq|H|rs> = (h0_p + h0_q) delta_{pq,rs} + <pq|v|rs>.  The matrix elements come from the
 caller (``velem(p, q, r, s)`` and the kinetic energies), so this file holds no force.
 """
 import numpy as np
 
 
-def sector_pairs(states):
-    """Pairs p<q with n_p + n_q = 0 and s_p + s_q = 0."""
+def sector_pairs(states, P=(0, 0, 0), Sz=0):
+    """Pairs p<q with n_p + n_q = P and s_p + s_q = Sz."""
     n = len(states)
+    P = np.asarray(P)
     out = []
     for p in range(n):
         for q in range(p + 1, n):
-            if np.all(states[p, :3] + states[q, :3] == 0) and states[p, 3] + states[q, 3] == 0:
+            if np.all(states[p, :3] + states[q, :3] == P) and states[p, 3] + states[q, 3] == Sz:
                 out.append((p, q))
     return out
 
@@ -26,7 +28,8 @@ def ground_state(states, ekin, velem, ref_pair):
     """Eigenvalue of the state with the largest overlap with the reference pair.
 
     Returns (E0, E_ref) where E_ref = <ref|H|ref>."""
-    pairs = sector_pairs(states)
+    i, j = ref_pair
+    pairs = sector_pairs(states, states[i, :3] + states[j, :3], states[i, 3] + states[j, 3])
     dim = len(pairs)
     H = np.zeros((dim, dim))
     for x, (p, q) in enumerate(pairs):

@@ -31,6 +31,14 @@
  *     m = 2 floor(sqrt(n2max)), M = 2m+1 and spins in units of hbar/2.
  *   - State order: shells ascending, then nx, ny, nz ascending, then s = -1 before +1;
  *     the first N states are holes.  Pairs inside a channel are in lexicographic order.
+ *   - Twisted boundary conditions (Sec. "Twist-averaged boundary conditions"): k = (2 pi n +
+ *     theta)/L, so eps_kin = hbar^2/2m (2 pi/L)^2 |n + phi|^2 with phi = theta/(2 pi) per axis
+ *     (the paper's printed shift of eps_k is garbled; this is |k + theta/L|^2 written out).
+ *     The model space stays n^2 <= n2max.  States are reordered by |n + phi|^2 (ties kept in
+ *     the order above) and the first N are the holes, as the paper's "order states by energy
+ *     and fill holes".  |n + phi|^2 is summed over the three axes in ascending order of the
+ *     axis terms, so twists with equal components give bit-identical energies to states that
+ *     differ by a permutation; N must leave a gap: |n + phi|^2 of state N-1 below that of N.
  *   - Direct-channel blocks of t and v are stored for restricted pairs (p<q); a sum
  *     1/2 sum_{cd} over ordered pairs of a pair-antisymmetric product equals sum_{c<d}.
  *     Cross-channel blocks use ordered pairs, as the paper's X channels do.
@@ -53,6 +61,7 @@ typedef struct {
 typedef struct om_sys {
     int N, nsp, n2max, m, M;
     double rho, L;
+    double phi[3];                   /* twist theta / (2 pi) per axis; 0 = periodic */
     om_minnesota P;
     int *nx, *ny, *nz, *sz;          /* sz in units of hbar/2: -1 or +1 */
     double *ekin, *eps;              /* kinetic and HF single-particle energies */
@@ -112,6 +121,49 @@ static int build_basis(om_sys *S) {
                         }
     S->nsp = n;
     return n;
+}
+
+/* |n + phi|^2 with the three axis terms added in ascending order. */
+static double twisted_n2(const om_sys *S, int p) {
+    double a[3] = {(S->nx[p] + S->phi[0]) * (S->nx[p] + S->phi[0]),
+                   (S->ny[p] + S->phi[1]) * (S->ny[p] + S->phi[1]),
+                   (S->nz[p] + S->phi[2]) * (S->nz[p] + S->phi[2])};
+    for (int i = 0; i < 3; i++)
+        for (int j = i + 1; j < 3; j++)
+            if (a[j] < a[i]) { double x = a[i]; a[i] = a[j]; a[j] = x; }
+    return (a[0] + a[1]) + a[2];
+}
+
+typedef struct { double key; int idx; } om_rank;
+
+static int rank_cmp(const void *x, const void *y) {
+    const om_rank *a = x, *b = y;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* Stable reorder of the shell-ordered states by |n + phi|^2; returns the sorted keys. */
+static double *order_by_energy(om_sys *S) {
+    int n = S->nsp;
+    om_rank *r = malloc(sizeof(om_rank) * n);
+    for (int p = 0; p < n; p++) { r[p].key = twisted_n2(S, p); r[p].idx = p; }
+    qsort(r, n, sizeof(om_rank), rank_cmp);
+    int *tmp = malloc(sizeof(int) * 4 * n);
+    for (int p = 0; p < n; p++) {
+        int q = r[p].idx;
+        tmp[4 * p] = S->nx[q]; tmp[4 * p + 1] = S->ny[q];
+        tmp[4 * p + 2] = S->nz[q]; tmp[4 * p + 3] = S->sz[q];
+    }
+    double *key = malloc(sizeof(double) * n);
+    for (int p = 0; p < n; p++) {
+        S->nx[p] = tmp[4 * p]; S->ny[p] = tmp[4 * p + 1];
+        S->nz[p] = tmp[4 * p + 2]; S->sz[p] = tmp[4 * p + 3];
+        key[p] = r[p].key;
+    }
+    free(tmp);
+    free(r);
+    return key;
 }
 
 /* ------------------------------------------------------------- Minnesota force */
@@ -378,8 +430,10 @@ void om_destroy(om_sys *S) {
     free(S);
 }
 
-/* Error codes: 0 ok, -1 invalid argument (N not a closed shell, no particle states). */
-om_sys *om_create(int N, double rho, int n2max, const double *params7, int *err) {
+/* Error codes: 0 ok, -1 invalid argument (N not a closed shell, no particle states).
+ * theta3: twist angles (radians) per axis, NULL for periodic boundary conditions. */
+om_sys *om_create_twisted(int N, double rho, int n2max, const double *params7,
+                          const double *theta3, int *err) {
     *err = -1;
     if (N <= 0 || rho <= 0.0 || n2max < 0) return NULL;
     om_sys *S = calloc(1, sizeof(om_sys));
@@ -388,24 +442,22 @@ om_sys *om_create(int N, double rho, int n2max, const double *params7, int *err)
     S->P.VT = params7[2]; S->P.kT = params7[3];
     S->P.VS = params7[4]; S->P.kS = params7[5];
     S->P.hbar2_2m = params7[6];
+    for (int a = 0; a < 3; a++) S->phi[a] = theta3 ? theta3[a] / (2.0 * OM_PI) : 0.0;
     S->m = 2 * isqrt_floor(n2max);
     S->M = 2 * S->m + 1;
     S->L = cbrt((double)N / rho);
     build_basis(S);
     int n = S->nsp;
-    /* closed shell: N states fill whole shells and at least one particle state exists */
     if (N >= n) { om_destroy(S); return NULL; }
-    int shN1 = S->nx[N - 1] * S->nx[N - 1] + S->ny[N - 1] * S->ny[N - 1] + S->nz[N - 1] * S->nz[N - 1];
-    int shN = S->nx[N] * S->nx[N] + S->ny[N] * S->ny[N] + S->nz[N] * S->nz[N];
-    if (shN == shN1) { om_destroy(S); return NULL; }
+    double *key = order_by_energy(S);
+    /* closed shell: a gap in |n + phi|^2 between the last hole and the first particle */
+    if (!(key[N - 1] < key[N])) { free(key); om_destroy(S); return NULL; }
     build_spin_ops(S);
     S->ekin = malloc(sizeof(double) * n);
     S->eps = malloc(sizeof(double) * n);
     double k0 = 2.0 * OM_PI / S->L;
-    for (int p = 0; p < n; p++) {
-        double n2 = (double)(S->nx[p] * S->nx[p] + S->ny[p] * S->ny[p] + S->nz[p] * S->nz[p]);
-        S->ekin[p] = S->P.hbar2_2m * k0 * k0 * n2;
-    }
+    for (int p = 0; p < n; p++) S->ekin[p] = S->P.hbar2_2m * k0 * k0 * key[p];
+    free(key);
     /* f_pp = h0_pp + sum_i <pi|v|pi> */
     for (int p = 0; p < n; p++) {
         double acc = 0.0;
@@ -416,6 +468,10 @@ om_sys *om_create(int N, double rho, int n2max, const double *params7, int *err)
     build_cross_channels(S);
     *err = 0;
     return S;
+}
+
+om_sys *om_create(int N, double rho, int n2max, const double *params7, int *err) {
+    return om_create_twisted(N, rho, n2max, params7, NULL, err);
 }
 
 /* ------------------------------------------------------------------ accessors */

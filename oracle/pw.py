@@ -15,8 +15,12 @@ import math
 import numpy as np
 
 
-def basis(n2max):
-    """States (nx, ny, nz, s) in the shell-ordered loop order, s in units of hbar/2."""
+def basis(n2max, theta=None):
+    """States (nx, ny, nz, s) in the shell-ordered loop order, s in units of hbar/2.
+
+    With twist angles theta (Sec. "Twist-averaged boundary conditions", k = (2 pi n +
+    theta)/L) the same states are reordered by |n + theta/2pi|^2, equal values keeping the
+    shell order, so that the lowest N are the holes."""
     r = math.isqrt(n2max)
     out = []
     for shell in range(n2max + 1):
@@ -27,7 +31,19 @@ def basis(n2max):
                         continue
                     for s in (-1, 1):
                         out.append((x, y, z, s))
-    return np.array(out, dtype=np.int64)
+    st = np.array(out, dtype=np.int64)
+    if theta is not None:
+        st = st[np.argsort(twisted_n2(st, theta), kind="stable")]
+    return st
+
+
+def twisted_n2(states, theta):
+    """|n + theta/2pi|^2 per state, the axis terms added smallest first."""
+    if theta is None:
+        theta = (0.0, 0.0, 0.0)
+    phi = np.asarray(theta, float) / (2 * math.pi)
+    terms = np.sort((states[:, :3] + phi[None, :]) ** 2, axis=1)
+    return (terms[:, 0] + terms[:, 1]) + terms[:, 2]
 
 
 def box_length(N, rho):
@@ -63,6 +79,7 @@ def v_dense(states, L, params):
     return v
 
 
-def kinetic(states, L, hbar2_2m):
-    n2 = np.sum(states[:, :3] ** 2, axis=1).astype(float)
-    return hbar2_2m * (2 * math.pi / L) ** 2 * n2
+def kinetic(states, L, hbar2_2m, theta=None):
+    """hbar^2/2m |k|^2 with k = (2 pi n + theta)/L."""
+    k0 = 2 * math.pi / L
+    return hbar2_2m * k0 * k0 * twisted_n2(states, theta)

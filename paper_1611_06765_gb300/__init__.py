@@ -28,20 +28,30 @@ def _ptr(a):
 class Context:
     """One or more (N, rho, n2max) systems built on the GPU by ``pnm_create_batch``."""
 
-    def __init__(self, N, rho, n2max, params=MINNESOTA, stream=None):
+    def __init__(self, N, rho, n2max, params=MINNESOTA, stream=None, theta=None):
+        """theta: twist angles, shape (3,) or (n, 3) radians (``pnm_create_twisted``); None
+        for periodic boundaries."""
         L = _lib.load()
         Ns = np.atleast_1d(np.asarray(N, dtype=np.int32))
         rhos = np.atleast_1d(np.asarray(rho, dtype=np.float64))
         n2 = np.atleast_1d(np.asarray(n2max, dtype=np.int32))
-        n = max(len(Ns), len(rhos), len(n2))
+        th = None if theta is None else np.atleast_2d(np.asarray(theta, dtype=np.float64))
+        n = max(len(Ns), len(rhos), len(n2), 0 if th is None else len(th))
         Ns, rhos, n2 = (np.ascontiguousarray(np.broadcast_to(a, (n,))) for a in (Ns, rhos, n2))
         self.N, self.rho, self.n2max = Ns.copy(), rhos.copy(), n2.copy()
         p = _lib.pnm_minnesota(*[float(x) for x in params])
         h = C.c_void_p()
-        _lib.check(L.pnm_create_batch(n, Ns.ctypes.data_as(C.POINTER(C.c_int)),
-                                      rhos.ctypes.data_as(C.POINTER(C.c_double)),
-                                      n2.ctypes.data_as(C.POINTER(C.c_int)), C.byref(p),
-                                      C.c_void_p(stream) if stream else None, C.byref(h)))
+        args = (Ns.ctypes.data_as(C.POINTER(C.c_int)), rhos.ctypes.data_as(C.POINTER(C.c_double)),
+                n2.ctypes.data_as(C.POINTER(C.c_int)))
+        st = C.c_void_p(stream) if stream else None
+        if th is None:
+            self.theta = None
+            _lib.check(L.pnm_create_batch(n, *args, C.byref(p), st, C.byref(h)))
+        else:
+            th = np.ascontiguousarray(np.broadcast_to(th, (n, 3)))
+            self.theta = th.copy()
+            _lib.check(L.pnm_create_twisted(n, *args, th.ctypes.data_as(C.POINTER(C.c_double)),
+                                            C.byref(p), st, C.byref(h)))
         self._h = h
         self.nsys = n
 
@@ -200,6 +210,18 @@ class Context:
 
 def _fptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def twist_mesh(nx, ny=None, nz=None):
+    """Product Gauss-Legendre twist mesh (``pnm_twist_mesh``): theta (M, 3), weight (M,)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    m = nx * ny * nz
+    theta = np.zeros((m, 3))
+    w = np.zeros(m)
+    _lib.check(_lib.load().pnm_twist_mesh(nx, ny, nz, theta.ctypes.data_as(C.POINTER(C.c_double)),
+                                          w.ctypes.data_as(C.POINTER(C.c_double))))
+    return theta, w
 
 
 def measure_fma_peak(fp64=True, stream=None):

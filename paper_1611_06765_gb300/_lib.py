@@ -26,7 +26,8 @@ PNM_INIT_MLP = 3
 
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
-    "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_destroy", "pnm_num_systems",
+    "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_twist_mesh",
+    "pnm_destroy", "pnm_num_systems",
     "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc",
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
@@ -73,6 +74,9 @@ def load(path=None):
     L.pnm_default_opts.argtypes = [C.POINTER(pnm_solve_opts)]
     L.pnm_create.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(pnm_minnesota), vp, C.POINTER(vp)]
     L.pnm_create_batch.argtypes = [C.c_int, ip, dp, ip, C.POINTER(pnm_minnesota), vp, C.POINTER(vp)]
+    L.pnm_create_twisted.argtypes = [C.c_int, ip, dp, ip, dp, C.POINTER(pnm_minnesota), vp,
+                                     C.POINTER(vp)]
+    L.pnm_twist_mesh.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
     L.pnm_destroy.argtypes = [vp]
     L.pnm_num_systems.argtypes = [vp, ip]
     L.pnm_basis.argtypes = [vp, C.c_int, ip, ip, vp, vp]

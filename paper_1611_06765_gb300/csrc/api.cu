@@ -71,8 +71,9 @@ void pnm_default_opts(pnm_solve_opts* o) {
 
 const char* pnm_last_error(void) { return g_last_error.c_str(); }
 
-int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
-                     const pnm_minnesota* params, void* stream, pnm_ctx** out) {
+int pnm_create_twisted(int n, const int* N, const double* rho, const int* n2max,
+                       const double* theta, const pnm_minnesota* params, void* stream,
+                       pnm_ctx** out) {
   return guarded([&]() {
     if (!out || !N || !rho || !n2max || !params || n <= 0)
       throw PnmError{PNM_EINVAL, "null argument or empty batch"};
@@ -87,7 +88,7 @@ int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
       }
       for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
       CUDA_TRY(cudaEventRecord(ctx->ev[2], ctx->stream));
-      pnm_build(ctx, n, N, rho, n2max, *params);
+      pnm_build(ctx, n, N, rho, n2max, theta, *params);
       pnm_prepare_iteration(ctx);
       pnm_eref_all(ctx);
       CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -100,6 +101,74 @@ int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
       throw;
     }
     *out = ctx;
+    return PNM_OK;
+  });
+}
+
+int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
+                     const pnm_minnesota* params, void* stream, pnm_ctx** out) {
+  return pnm_create_twisted(n, N, rho, n2max, nullptr, params, stream, out);
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_n from the Chebyshev-like
+// first guess cos(pi (i + 3/4) / (n + 1/2)); P_n and P_n' from the three-term recurrence
+// (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}; w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; i++) {
+    double z = std::cos(PNM_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; it++) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int k = 0; k < n; k++) {
+        double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * k + 1.0) * z * p1 - k * p2) / (k + 1.0);
+      }
+      dp = n * (z * p0 - p1) / (z * z - 1.0);
+      double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = 0.0;
+    for (int k = 0; k < n; k++) {
+      double p2 = p1;
+      p1 = p0;
+      p0 = ((2.0 * k + 1.0) * z * p1 - k * p2) / (k + 1.0);
+    }
+    dp = n * (z * p0 - p1) / (z * z - 1.0);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+int pnm_twist_mesh(int nx, int ny, int nz, double* theta, double* weight) {
+  return guarded([&]() {
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 64 || ny > 64 || nz > 64 || !theta || !weight)
+      throw PnmError{PNM_EINVAL, "mesh sizes must be 1..64 per axis and outputs non-null"};
+    int n3[3] = {nx, ny, nz};
+    std::vector<double> th[3], wt[3];
+    for (int a = 0; a < 3; a++) {
+      std::vector<double> x, w;
+      gauss_legendre(n3[a], x, w);
+      th[a].resize(n3[a]);
+      wt[a].resize(n3[a]);
+      for (int i = 0; i < n3[a]; i++) {
+        th[a][i] = 0.5 * PNM_PI * (x[i] + 1.0);
+        wt[a][i] = 0.5 * w[i];  // (pi/2) w_i / pi: the 1/pi^3 of the average taken per axis
+      }
+    }
+    long m = 0;
+    for (int i = 0; i < nx; i++)
+      for (int j = 0; j < ny; j++)
+        for (int k = 0; k < nz; k++, m++) {
+          theta[3 * m] = th[0][i];
+          theta[3 * m + 1] = th[1][j];
+          theta[3 * m + 2] = th[2][k];
+          weight[m] = wt[0][i] * wt[1][j] * wt[2][k];
+        }
     return PNM_OK;
   });
 }

@@ -98,7 +98,7 @@ inline std::string pnm_shape_key(const pnm_ctx* ctx) {
 }
 
 void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
-               const pnm_minnesota& P);
+               const double* thetas, const pnm_minnesota& P);
 void pnm_prepare_iteration(pnm_ctx* ctx);
 void pnm_eref_all(pnm_ctx* ctx);
 void pnm_mbpt2_all(pnm_ctx* ctx, double* out);

@@ -48,6 +48,7 @@ struct SysInfo {
   int row_begin, row_end; // (channel, ij) rows
   int lut_off, lut_len;
   double eref;
+  double phi[3];          // twist theta / (2 pi) per axis; all zero = periodic
 };
 
 // Device arena pointers; all arrays are global over the systems of the context.

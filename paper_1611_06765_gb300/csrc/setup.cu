@@ -105,16 +105,76 @@ __global__ void k_lut(double* __restrict__ lut, int len, double L, double VR, do
            VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS));
 }
 
+// ------------------------------------------------------------------ twisted boundaries
+// Sec. "Twist-averaged boundary conditions": k = (2 pi n + theta)/L, so the kinetic energy is
+// hbar^2/2m (2 pi/L)^2 |n + phi|^2 with phi = theta/(2 pi).  The three axis terms are added
+// smallest first and every step is rounded on its own (no fused multiply-add), so that states
+// related by a permutation of axes with equal twist components get bit-identical values; with
+// phi = 0 the result is the integer n^2.
+__device__ __forceinline__ double twisted_n2(char4 sp, double px, double py, double pz) {
+  double a = __dadd_rn((double)sp.x, px), b = __dadd_rn((double)sp.y, py);
+  double c = __dadd_rn((double)sp.z, pz);
+  a = __dmul_rn(a, a);
+  b = __dmul_rn(b, b);
+  c = __dmul_rn(c, c);
+  double lo = fmin(a, b), hi = fmax(a, b);
+  double x0 = fmin(lo, c), mid = fmax(lo, c);
+  double x1 = fmin(mid, hi), x2 = fmax(mid, hi);
+  return __dadd_rn(__dadd_rn(x0, x1), x2);
+}
+
+__global__ void k_twist_keys(const char4* __restrict__ nvec, int nsp, double px, double py,
+                             double pz, double* __restrict__ key) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nsp) key[p] = twisted_n2(nvec[p], px, py, pz);
+}
+
+// Stable reorder by key ("order states by energy and fill holes"): a state's new slot is the
+// number of states with a smaller key, or an equal key and a smaller shell-order index.
+// Keys are staged through shared memory in tiles of the block size.
+constexpr int TWIST_THREADS = 256;
+__global__ void __launch_bounds__(TWIST_THREADS)
+k_twist_rank(const double* __restrict__ key, int nsp, const char4* __restrict__ nvec_in,
+             char4* __restrict__ nvec_out, double* __restrict__ key_out, int* __restrict__ perm) {
+  __shared__ double sk[TWIST_THREADS];
+  int p = blockIdx.x * TWIST_THREADS + threadIdx.x;
+  double kp = p < nsp ? key[p] : 0.0;
+  int rank = 0;
+  for (int q0 = 0; q0 < nsp; q0 += TWIST_THREADS) {
+    int q = q0 + threadIdx.x;
+    sk[threadIdx.x] = q < nsp ? key[q] : 0.0;
+    __syncthreads();
+    int lim = min(TWIST_THREADS, nsp - q0);
+    if (p < nsp)
+      for (int u = 0; u < lim; u++) {
+        double kq = sk[u];
+        rank += (kq < kp) || (kq == kp && q0 + u < p);
+      }
+    __syncthreads();
+  }
+  if (p < nsp) {
+    nvec_out[rank] = nvec_in[p];
+    key_out[rank] = kp;
+    perm[p] = rank;
+  }
+}
+
+// Cube point -> state index map follows the reorder.
+__global__ void k_twist_idx3(int* __restrict__ idx3, int n, const int* __restrict__ perm) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n && idx3[c] >= 0) idx3[c] = perm[idx3[c]];
+}
+
 // eps_p = h0_pp + sum_i <pi|v|pi>  (holes are the first N states of the system).
 __global__ void k_eps(const char4* __restrict__ nvec, const double* __restrict__ lut, int nsp,
-                      int N, double L, double hbar2_2m, double* __restrict__ ekin,
-                      double* __restrict__ eps, int* __restrict__ sp_sys,
-                      int* __restrict__ sp_hole, int sys) {
+                      int N, double L, double hbar2_2m, double px, double py, double pz,
+                      double* __restrict__ ekin, double* __restrict__ eps,
+                      int* __restrict__ sp_sys, int* __restrict__ sp_hole, int sys) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nsp) return;
   char4 sp = nvec[p];
   double k0 = 2.0 * PNM_PI / L;
-  double ek = hbar2_2m * k0 * k0 * (double)dot3(sp.x, sp.y, sp.z);
+  double ek = hbar2_2m * k0 * k0 * twisted_n2(sp, px, py, pz);
   double acc = 0.0;
   for (int i = 0; i < N; i++) {
     char4 si = nvec[i];
@@ -533,7 +593,7 @@ struct SysScratch {
 };
 
 void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
-               const pnm_minnesota& P) {
+               const double* thetas, const pnm_minnesota& P) {
   cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
   std::vector<SysInfo>& sys = ctx->sys;
@@ -556,6 +616,13 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     S.M = 2 * S.m + 1;
     S.nkeys = S.M * S.M * S.M * 3;
     S.L = std::cbrt((double)S.N / S.rho);
+    bool twisted = false;
+    for (int a = 0; a < 3; a++) {
+      double th = thetas ? thetas[3 * k + a] : 0.0;
+      if (!std::isfinite(th)) throw PnmError{PNM_EINVAL, "twist angle is not finite"};
+      S.phi[a] = th / (2.0 * PNM_PI);
+      twisted = twisted || S.phi[a] != 0.0;
+    }
     int w = 2 * S.r + 1, ncube = w * w * w;
     char4* tvec = dalloc<char4>(2 * ncube, scr[k].owned);
     scr[k].idx3 = dalloc<int>(2 * ncube, scr[k].owned);
@@ -563,11 +630,28 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     k_basis<<<1, 512, 2 * (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, tvec, scr[k].idx3, dnsp);
     CUDA_TRY(cudaGetLastError());
     S.nsp = d2h(dnsp, 1, s)[0];
-    hvec[k] = d2h(tvec, S.nsp, s);
     if (S.N >= S.nsp) throw PnmError{PNM_EINVAL, "no particle states: n2max too small for N"};
-    auto sh = [&](const char4& c) { return c.x * c.x + c.y * c.y + c.z * c.z; };
-    if (sh(hvec[k][S.N - 1]) == sh(hvec[k][S.N]))
-      throw PnmError{PNM_EINVAL, "N = " + std::to_string(S.N) + " does not close a shell"};
+    if (!twisted) {
+      hvec[k] = d2h(tvec, S.nsp, s);
+      auto sh = [&](const char4& c) { return c.x * c.x + c.y * c.y + c.z * c.z; };
+      if (sh(hvec[k][S.N - 1]) == sh(hvec[k][S.N]))
+        throw PnmError{PNM_EINVAL, "N = " + std::to_string(S.N) + " does not close a shell"};
+    } else {
+      double* key = dalloc<double>(S.nsp, scr[k].owned);
+      double* skey = dalloc<double>(S.nsp, scr[k].owned);
+      int* perm = dalloc<int>(S.nsp, scr[k].owned);
+      char4* tv2 = dalloc<char4>(S.nsp, scr[k].owned);
+      int nb = (S.nsp + TWIST_THREADS - 1) / TWIST_THREADS;
+      k_twist_keys<<<nb, TWIST_THREADS, 0, s>>>(tvec, S.nsp, S.phi[0], S.phi[1], S.phi[2], key);
+      k_twist_rank<<<nb, TWIST_THREADS, 0, s>>>(key, S.nsp, tvec, tv2, skey, perm);
+      k_twist_idx3<<<(2 * ncube + 255) / 256, 256, 0, s>>>(scr[k].idx3, 2 * ncube, perm);
+      CUDA_TRY(cudaGetLastError());
+      hvec[k] = d2h(tv2, S.nsp, s);
+      std::vector<double> hk = d2h(skey, S.nsp, s);
+      if (!(hk[S.N - 1] < hk[S.N]))
+        throw PnmError{PNM_EINVAL, "system " + std::to_string(k) + ": N = " + std::to_string(S.N) +
+                                       " leaves no gap at this twist (degenerate Fermi level)"};
+    }
     S.sp_off = nsp_total;
     nsp_total += S.nsp;
     S.lut_off = lut_total;
@@ -588,7 +672,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     k_lut<<<(S.lut_len + 127) / 128, 128, 0, s>>>(D.lut + S.lut_off, S.lut_len, S.L, P.VR, P.kR,
                                                  P.VS, P.kS);
     k_eps<<<(S.nsp + 127) / 128, 128, 0, s>>>(D.nvec + S.sp_off, D.lut + S.lut_off, S.nsp, S.N,
-                                             S.L, P.hbar2_2m, D.ekin + S.sp_off,
+                                             S.L, P.hbar2_2m, S.phi[0], S.phi[1], S.phi[2],
+                                             D.ekin + S.sp_off,
                                              D.eps + S.sp_off, D.sp_sys + S.sp_off,
                                              D.sp_hole + S.sp_off, k);
     CUDA_TRY(cudaGetLastError());
