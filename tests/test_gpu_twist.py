@@ -13,7 +13,7 @@ from oracle import channel, exact2
 
 pytestmark = pytest.mark.gpu
 
-TWISTS = [(0.4, 1.3, 2.6), (2.9, 0.5, 1.7), (1.0, 1.0, 2.2)]
+TWISTS = [(0.4, 1.3, 2.6), (2.9, 0.5, 1.7), (2.0, 2.0, 0.7)]
 
 
 @pytest.fixture(scope="module")
@@ -77,11 +77,14 @@ def test_twisted_two_neutrons_exact(pkg):
 
 
 def test_degenerate_twist_rejected(pkg):
+    """Twists whose Fermi level is degenerate for N = 14 (the oracle rejects them too)."""
     nodes = pkg.twist_mesh(5, 1, 1)[0][:, 0]
-    bad = (nodes[0], nodes[0], nodes[2])      # equal x and y components: degenerate for N=14
-    with pytest.raises(pkg.PnmError) as e:
-        pkg.Context([14, 14], 0.08, 20, params=minnesota_params(), theta=[TWISTS[0], bad])
-    assert e.value.code == -1 and "system 1" in str(e.value)
+    for bad in [(nodes[0], nodes[0], nodes[2]), (1.0, 1.0, 2.2), (0.5, 0.5, 2.0)]:
+        with pytest.raises(ValueError):
+            channel.OracleSystem(14, 0.08, 20, minnesota_params(), theta=bad)
+        with pytest.raises(pkg.PnmError) as e:
+            pkg.Context([14, 14], 0.08, 20, params=minnesota_params(), theta=[TWISTS[0], bad])
+        assert e.value.code == -1 and "system 1" in str(e.value)
 
 
 @pytest.fixture(scope="module")
