@@ -17,7 +17,8 @@ the model are resident in HBM before the timed region; L2 is flushed before ever
 ``e2e`` times the public API from host inputs: context creation (basis, channels and V built
 on the GPU), model upload, solve, converged amplitudes copied back.  ``comparison`` holds the
 same batch from the MBPT2 start (mixed and FP64) and the other configurations, each with its
-dE/N error against the FP64 oracle.  ``--impl reference`` times the FP64 CPU oracle.
+dE/N error against the FP64 oracle, and a twist-averaged batch (N = 14, n^2 <= 20, rho = 0.08,
+120 twists of a 4 x 5 x 6 Gauss-Legendre mesh in one context) in both precisions.  ``--impl reference`` times the FP64 CPU oracle.
 
 Prints one JSON line.
 """
@@ -48,6 +49,13 @@ WORKLOADS = {
     "pnm_N14_n2max20_16rho_bf16x3": (14, SWEEP16, 20, "mbpt2", "bf16x3"),
     "pnm_N14_n2max20_16rho_fp64": (14, SWEEP16, 20, "mbpt2", "fp64"),
     "pnm_N14_rho0.08_n2max4_fp64": (14, (0.08,), 4, "mbpt2", "fp64"),
+}
+# Twist-averaged boundary conditions: one system per point of a product Gauss-Legendre twist
+# mesh (4 x 5 x 6 nodes on [0, pi]: no two equal components, so no mesh point has a
+# degenerate Fermi level), all in one batched context.  name: (N, rho, n2max, mesh, precision)
+TWIST_WORKLOADS = {
+    "pnm_N14_rho0.08_n2max20_tabc4x5x6_bf16x3": (14, 0.08, 20, (4, 5, 6), "bf16x3"),
+    "pnm_N14_rho0.08_n2max20_tabc4x5x6_fp64": (14, 0.08, 20, (4, 5, 6), "fp64"),
 }
 DEFAULT_WORKLOAD = "pnm_N66_n2max36_heldout3_learned_bf16x3"
 COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
@@ -329,6 +337,56 @@ def measure(P, torch, stream, flush, workload, refine, steps):
     return {"ms": statistics.mean(ms), "iters": iters[-1], "dE_per_N": [x / N for x in dEs[-1]]}
 
 
+def measure_twist(P, torch, stream, flush, workload, refine, steps):
+    """Mean time-to-converge (ms) of a twist-averaged batch, with its twist-averaged energies."""
+    import numpy as np
+    N, rho, n2max, mesh, prec = TWIST_WORKLOADS[workload]
+    theta, w = P.twist_mesh(*mesh)
+    ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream, theta=theta)
+    p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
+    kw = dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
+              refine_sweeps=refine if prec == "bf16x3" else 0)
+    for _ in range(3):
+        ctx.solve(**kw)
+    torch.cuda.synchronize()
+    ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
+    eref = ctx.eref()
+    ctx.close()
+    dE = np.array(dEs[-1])
+    return {"ms": statistics.mean(ms), "systems": len(w), "mesh": list(mesh), "N": N, "rho": rho,
+            "n2max": n2max, "iters_min": min(iters[-1]), "iters_max": max(iters[-1]),
+            "E_per_N_twist_avg": float(np.sum(w * (eref + dE)) / N),
+            "Eref_per_N_twist_avg": float(np.sum(w * eref) / N),
+            "dE_per_N_twist_avg": float(np.sum(w * dE) / N),
+            "_theta": theta, "_w": w, "_dE_per_N": dE / N}
+
+
+_twist_fixed = {}
+
+
+def oracle_twist(P, r, budget_s=60.0):
+    """The oracle's fixed points (|dE change| / N < 1e-10 MeV) at every twist of a measured
+    twist batch, within a time budget; fills the error fields of r."""
+    import numpy as np
+    from oracle import channel
+    theta, w, dE = r.pop("_theta"), r.pop("_w"), r.pop("_dE_per_N")
+    err = []
+    t0 = time.perf_counter()
+    for th, d in zip(theta, dE):
+        key = (r["N"], r["rho"], r["n2max"], tuple(th))
+        if key not in _twist_fixed:
+            if time.perf_counter() - t0 > budget_s:
+                break
+            o = channel.OracleSystem(r["N"], r["rho"], r["n2max"], MINNESOTA, theta=th)
+            _twist_fixed[key] = o.ccd(alpha=ALPHA, tol=1e-10 * r["N"], maxit=1000)[0] / r["N"]
+        err.append(d - _twist_fixed[key])
+    r["oracle_systems"] = len(err)
+    if err:
+        r["max_abs_dE_per_N_minus_oracle"] = float(np.max(np.abs(err)))
+        if len(err) == len(w):
+            r["twist_avg_dE_per_N_minus_oracle"] = float(np.sum(w * np.array(err)))
+
+
 def oracle_leg(workloads, budget_s=60.0):
     """cpu_baseline leg: FP64 oracle solves of the systems of the given workloads (each
     distinct (N, rho, n2max) once, within a time budget, in the order given): one at the
@@ -478,6 +536,8 @@ def run_ours(a):
         for w in COMPARE:
             if w != a.workload:
                 comparison[w] = measure(P, torch, stream, flush, w, a.refine, 5)
+        for w in TWIST_WORKLOADS:
+            comparison[w] = measure_twist(P, torch, stream, flush, w, a.refine, 5)
         if "train_s" in _model:
             comparison["training"] = {"seconds": _model["train_s"], "loss_first_last": _model["loss"],
                                       "epochs": _model["epochs"], "batch": _model["batch"],
@@ -514,6 +574,8 @@ def run_ours(a):
             for w, r in comparison.items():
                 if w in WORKLOADS:
                     r["dE_per_N_minus_oracle"] = oracle_errors(r, w, ora)
+                elif w in TWIST_WORKLOADS:
+                    oracle_twist(P, r)
 
     if rank == 0:
         line = {
@@ -535,7 +597,8 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "tuning": (dict(zip(("k_splits", "stages", "pp_tc_us", "serial_mask"), ctx.tuning()))
                        if prec_name == "bf16x3" else None),
-            "comparison": comparison,
+            "comparison": ({k: {f: v for f, v in r.items() if not f.startswith("_")}
+                            for k, r in comparison.items()} if comparison else comparison),
             "result": result,
         }
         print(json.dumps(line), flush=True)
