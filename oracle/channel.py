@@ -43,6 +43,10 @@ def lib():
         L.om_mbpt2.argtypes = [vp]
         L.om_ccd.restype = C.c_int
         L.om_ccd.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, vp, vp, vp]
+        L.om_ccd_terms.restype = C.c_int
+        L.om_ccd_terms.argtypes = [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+        L.om_mbpt3.restype = C.c_int
+        L.om_mbpt3.argtypes = [vp, vp]
         L.om_t_get.restype = C.c_double
         L.om_t_get.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.om_t_gather.argtypes = [vp, C.c_long, vp, vp]
@@ -137,16 +141,29 @@ class OracleSystem:
         return dict(keys=keys, nph=nph, nhp=nhp, ph=ph, hp=hp)
 
     # ---- CCD
-    def ccd(self, alpha=0.5, tol=1e-10, maxit=200, init="mbpt2"):
-        """Returns (dE, iterations, energy history, (setup_s, iterate_s))."""
+    TERMS = {"full": 0, "pp": 1, "pphh": 2, "linear": 3}
+
+    def ccd(self, alpha=0.5, tol=1e-10, maxit=200, init="mbpt2", terms="full"):
+        """Returns (dE, iterations, energy history, (setup_s, iterate_s)).  terms: "full"
+        (Eq. ccd3), "pp" (Eq. ccd1), "pphh" (Eq. ccd2) or "linear" (the terms of Eq. ccd3
+        linear in t)."""
         hist = np.zeros(maxit + 1)
         dE = C.c_double(0.0)
         tim = np.zeros(2)
-        it = lib().om_ccd(self._h, float(alpha), float(tol), int(maxit),
-                          0 if init == "mbpt2" else 1, C.byref(dE), _ptr(hist), _ptr(tim))
+        it = lib().om_ccd_terms(self._h, float(alpha), float(tol), int(maxit),
+                                0 if init == "mbpt2" else 1, self.TERMS[terms], C.byref(dE),
+                                _ptr(hist), _ptr(tim))
         if it < 0:
             raise ValueError("oracle: zero energy denominator")
         return dE.value, it, hist[: it + 1].copy(), (tim[0], tim[1])
+
+    def mbpt3(self):
+        """Third-order diagrams (4) pp ladder, (5) hh ladder, (3) ph ring, from the MBPT2
+        amplitudes (see om_mbpt3)."""
+        out = np.zeros(3)
+        if lib().om_mbpt3(self._h, _ptr(out)) != 0:
+            raise ValueError("oracle: zero energy denominator")
+        return out
 
     def amplitudes(self):
         """Restricted amplitudes (a<b, i<j) and their labels, oracle layout."""

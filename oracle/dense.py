@@ -57,24 +57,42 @@ class DenseCCD:
         """Eq. (ccdGuess): t0 = <ab|v|ij> / eps_ij^ab."""
         return self.v_abij / self.D
 
-    def rhs(self, t):
-        """The bracket of Eq. (ccd3): everything except the eps_ij^ab t term."""
+    def rhs(self, t, terms="full"):
+        """The bracket of Eq. (ccd3): everything except the eps_ij^ab t term.  terms: "full";
+        "pp" (Eq. ccd1: v and the pp ladder); "pphh" (Eq. ccd2: and the hh ladder); "linear"
+        (every term of Eq. ccd3 linear in t)."""
         v = self
         r = v.v_abij.copy()
         r += 0.5 * _es("abcd,cdij->abij", v.v_abcd, t)
+        if terms == "pp":
+            return r
         r += 0.5 * _es("klij,abkl->abij", v.v_klij, t)
+        if terms == "pphh":
+            return r
         r += P_ij(P_ab(_es("kbcj,acik->abij", v.v_kbcj, t)))
+        if terms == "linear":
+            return r
         r += 0.25 * _es("klcd,cdij,abkl->abij", v.v_klcd, t, t)
         r += P_ij(_es("klcd,acik,bdjl->abij", v.v_klcd, t, t))
         r -= 0.5 * P_ij(_es("klcd,dcik,ablj->abij", v.v_klcd, t, t))
         r -= 0.5 * P_ab(_es("klcd,aclk,dbij->abij", v.v_klcd, t, t))
         return r
 
-    def step(self, t):
-        """t^(n+1) of Eq. (ccd3), before mixing."""
-        return self.rhs(t) / self.D
+    def step(self, t, terms="full"):
+        """t^(n+1) of Eq. (ccd3) (or of its truncation), before mixing."""
+        return self.rhs(t, terms) / self.D
 
-    def solve(self, alpha=1.0, tol=1e-10, maxit=500, init="mbpt2"):
+    def mbpt3(self):
+        """Eqs. (diag4), (diag5) and (diag3) written out over the dense arrays, with
+        t0_ij^ab = <ij|v|ab> / eps_ij^ab.  Eq. (diag3) is read with <kb|v|cj> where the paper
+        prints <bk|v|ic> (= <kb|v|ci>)."""
+        t0 = self.mbpt2_guess()                              # [a, b, i, j]
+        d4 = 0.125 * _es("cdij,abcd,abij->", t0, self.v_abcd, t0)
+        d5 = 0.125 * _es("abkl,klij,abij->", t0, self.v_klij, t0)
+        d3 = _es("abij,kbcj,acik->", t0, self.v_kbcj, t0)
+        return np.array([d4, d5, d3])
+
+    def solve(self, alpha=1.0, tol=1e-10, maxit=500, init="mbpt2", terms="full"):
         """Iterate with mixing t = alpha t_new + (1 - alpha) t_old until the energy change
         is below tol.  Returns (dE, updates, energy history, t)."""
         t = self.mbpt2_guess() if init == "mbpt2" else np.zeros_like(self.D)
@@ -82,7 +100,7 @@ class DenseCCD:
         hist = [e_old]
         it = 0
         while it < maxit:
-            t = alpha * self.step(t) + (1.0 - alpha) * t
+            t = alpha * self.step(t, terms) + (1.0 - alpha) * t
             e = self.energy(t)
             it += 1
             hist.append(e)

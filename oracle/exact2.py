@@ -40,3 +40,29 @@ def ground_state(states, ekin, velem, ref_pair):
     ref = pairs.index(tuple(sorted(ref_pair)))
     k = int(np.argmax(np.abs(U[ref, :])))
     return float(w[k]), float(H[ref, ref]), float(w[0])
+
+
+def rs_third_order(states, ekin, eps, velem, ref_pair):
+    """Rayleigh-Schroedinger perturbation theory in the same two-body sector with the
+    Moller-Plesset split H = H0 + W, H0 = diag(eps_p + eps_q) (HF energies), reference |ij>:
+      E^(2) = sum_k W_0k W_k0 / (E0_0 - E0_k)
+      E^(3) = sum_{k,l} W_0k W_kl W_l0 / ((E0_0 - E0_k)(E0_0 - E0_l))
+              - W_00 sum_k W_0k W_k0 / (E0_0 - E0_k)^2,   k, l over the other pairs.
+    Returns (E^(2), E^(3))."""
+    i, j = ref_pair
+    pairs = sector_pairs(states, states[i, :3] + states[j, :3], states[i, 3] + states[j, 3])
+    dim = len(pairs)
+    H = np.zeros((dim, dim))
+    for x, (p, q) in enumerate(pairs):
+        for y, (r, s) in enumerate(pairs):
+            H[x, y] = velem(p, q, r, s)
+        H[x, x] += ekin[p] + ekin[q]
+    H0 = np.array([eps[p] + eps[q] for p, q in pairs])
+    W = H - np.diag(H0)
+    k0 = pairs.index(tuple(sorted(ref_pair)))
+    rest = [k for k in range(dim) if k != k0]
+    d = H0[k0] - H0[rest]
+    w = W[k0, rest]
+    e2 = float(np.sum(w * w / d))
+    e3 = float((w / d) @ W[np.ix_(rest, rest)] @ (w / d) - W[k0, k0] * np.sum(w * w / d ** 2))
+    return e2, e3

@@ -21,6 +21,9 @@
  *                code", blocked in direct (T) and cross (X) channels as in the channel
  *                mapping that follows them; energy Eq. (ccdcorr); mixing
  *                t = alpha t_new + (1-alpha) t_old; stop when |dE^(n+1) - dE^(n)| < eta.
+ *   truncations  Eq. (ccd1) (pp ladder only) and Eq. (ccd2) (pp and hh ladders) of Sec.
+ *                "Coupled cluster theory", and the terms of Eq. (ccd3) linear in t.
+ *   MBPT3        diagrams (3), (4), (5) of Fig. goldstone, Eqs. (diag3)-(diag5).
  *
  * Readings of the paper taken here (each one is listed with its evidence in the design notes):
  *   - Minnesota signs: V_R = +200 MeV, V_T = -178 MeV, V_S = -91.85 MeV (the table prints
@@ -666,10 +669,11 @@ static double ccd_energy(const om_sys *S, const double *t) {
 /* Particle-hole term in cross channels (the intermediate chi_kb^cj of Sec. "Developing a
  * CCD code", in the cross-coupled (a-i) channels):
  *   T[(a,i)][(k,c)] = t_ik^ac
- *   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
+ *   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb   (quad = 0: <kb|v|cj> only)
  *   Q[(a,i)][(j,b)] = sum_{(k,c)} T C = sum_kc t_ik^ac chi_kb^cj
  * absval != 0: the same with |t|, |v| everywhere (a bound for rounding-error tests). */
-static void ph_cross(const om_sys *S, const double *t, double *xT, double *xC, double *xQ, int absval) {
+static void ph_cross(const om_sys *S, const double *t, double *xT, double *xC, double *xQ, int absval,
+                     int quad) {
 #pragma omp parallel for schedule(dynamic)
     for (int x = 0; x < S->nx_ch; x++) {
         int nph = S->nph[x], nhp = S->nhp[x];
@@ -690,7 +694,7 @@ static void ph_cross(const om_sys *S, const double *t, double *xT, double *xC, d
                     acc += (absval ? fabs(w) : w) * T[(size_t)u * nhp + s];
                 }
                 double v1 = V1[(size_t)r * nhp + s];
-                Cm[(size_t)r * nhp + s] = (absval ? fabs(v1) : v1) + 0.5 * acc;
+                Cm[(size_t)r * nhp + s] = (absval ? fabs(v1) : v1) + (quad ? 0.5 * acc : 0.0);
             }
         for (int r = 0; r < nph; r++)
             for (int s = 0; s < nhp; s++) {
@@ -720,15 +724,25 @@ static double ph_combine(const om_sys *S, const double *xQ, int a, int b, int i,
     return out;
 }
 
+/* Which terms of Eq. (ccd3) an iteration keeps (Sec. "Coupled cluster theory" truncations):
+ *   OM_FULL    every term of Eq. (ccd3);
+ *   OM_PP      Eq. (ccd1): v and the pp ladder with the bare interaction;
+ *   OM_PPHH    Eq. (ccd2): v, the pp ladder and the hh ladder with the bare interaction;
+ *   OM_LINEAR  every term linear in t (pp and hh ladders, the ph term with <kb|v|cj>), none of
+ *              the quadratic ones.  One unmixed step of it from the MBPT2 amplitudes gives the
+ *              third-order energy: E = E2 + the diagrams (3), (4), (5). */
+enum { OM_FULL = 0, OM_PP = 1, OM_PPHH = 2, OM_LINEAR = 3 };
+
 /* One Jacobi step of Eq. (ccd3) with the intermediates; writes t_new (restricted). */
 static void ccd_step(const om_sys *S, const double *t, double *t_new, double *chi1,
-                     double *chi_hh, double *xT, double *xC, double *xQ) {
+                     double *chi_hh, double *xT, double *xC, double *xQ, int terms) {
     int n = S->nsp;
+    int quad = terms == OM_FULL, hh_on = terms != OM_PP, ph_on = terms == OM_FULL || terms == OM_LINEAR;
     /* one-body intermediates.  Momentum and S_z conservation make them diagonal:
      *   chi_b = f_bb - 1/2 sum_{kld} t_kl^bd <kl|v|bd>  = f_bb - sum_d sum_{k<l} t v
      *   chi_j = f_jj + 1/2 sum_{cdl} <jl|v|cd> t_jl^cd  = f_jj + sum_l sum_{c<d} v t   */
     for (int p = 0; p < n; p++) chi1[p] = S->eps[p];
-    for (int c = 0; c < S->nch; c++) {
+    for (int c = 0; c < S->nch && quad; c++) {
         int np = S->npp[c], nh = S->nhh[c];
         const double *tb = t + S->t_off[c], *vb = S->v_pphh + S->t_off[c];
         for (int x = 0; x < np; x++) {
@@ -754,12 +768,12 @@ static void ccd_step(const om_sys *S, const double *t, double *t_new, double *ch
         for (int kl = 0; kl < nh; kl++)
             for (int ij = 0; ij < nh; ij++) {
                 double s = vh[(size_t)kl * nh + ij];
-                for (int cd = 0; cd < np; cd++)
+                for (int cd = 0; cd < np && quad; cd++)
                     s += vb[(size_t)cd * nh + kl] * tb[(size_t)cd * nh + ij];
                 ch[(size_t)kl * nh + ij] = s;
             }
     }
-    ph_cross(S, t, xT, xC, xQ, 0);
+    if (ph_on) ph_cross(S, t, xT, xC, xQ, 0, quad);
     /* assemble Eq. (ccd3) with the intermediates, for restricted a<b, i<j */
 #pragma omp parallel for schedule(dynamic)
     for (int c = 0; c < S->nch; c++) {
@@ -784,10 +798,10 @@ static void ccd_step(const om_sys *S, const double *t, double *t_new, double *ch
                 num += pp;
                 /* 1/2 sum_kl t_kl^ab chi_kl^ij */
                 double hh = 0.0;
-                for (int kl = 0; kl < nh; kl++) hh += tb[(size_t)x * nh + kl] * ch[(size_t)kl * nh + y];
+                for (int kl = 0; kl < nh && hh_on; kl++) hh += tb[(size_t)x * nh + kl] * ch[(size_t)kl * nh + y];
                 num += hh;
                 /* P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj = Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba */
-                num += ph_combine(S, xQ, a, b, i, j, 0);
+                if (ph_on) num += ph_combine(S, xQ, a, b, i, j, 0);
                 double D = S->eps[i] + S->eps[j] - S->eps[a] - S->eps[b];
                 tn[(size_t)x * nh + y] = num / D;
             }
@@ -808,8 +822,9 @@ static double now_s(void) {
  * Returns the number of updates made, or -1 on a zero denominator.
  * timings (nullable, 2 doubles): setup seconds, iteration seconds.
  */
-int om_ccd(om_sys *S, double alpha, double tol, int maxit, int init, double *dE_out,
-           double *e_hist, double *timings) {
+int om_ccd_terms(om_sys *S, double alpha, double tol, int maxit, int init, int terms,
+                 double *dE_out, double *e_hist, double *timings) {
+    if (terms < OM_FULL || terms > OM_LINEAR) return -2;
     double t0 = now_s();
     build_ccd_blocks(S);
     int n = S->nsp;
@@ -839,7 +854,7 @@ int om_ccd(om_sys *S, double alpha, double tol, int maxit, int init, double *dE_
     if (e_hist) e_hist[0] = e_old;
     int it = 0;
     while (it < maxit) {
-        ccd_step(S, S->t, t_new, chi1, chi_hh, xT, xC, xQ);
+        ccd_step(S, S->t, t_new, chi1, chi_hh, xT, xC, xQ, terms);
         for (size_t z = 0; z < S->nt; z++) S->t[z] = alpha * t_new[z] + (1.0 - alpha) * S->t[z];
         double e = ccd_energy(S, S->t);
         it++;
@@ -855,6 +870,75 @@ int om_ccd(om_sys *S, double alpha, double tol, int maxit, int init, double *dE_
     return it;
 }
 
+int om_ccd(om_sys *S, double alpha, double tol, int maxit, int init, double *dE_out,
+           double *e_hist, double *timings) {
+    return om_ccd_terms(S, alpha, tol, maxit, init, OM_FULL, dE_out, e_hist, timings);
+}
+
+/* Third-order energy diagrams of Sec. "Many-body perturbation theory" (Fig. goldstone), with
+ * the MBPT2 amplitudes t0 = <ab|v|ij> / eps_ij^ab and restricted sums (a<b, i<j):
+ *   out[0] = (4) = 1/8 sum <ij|v|cd><cd|v|ab><ab|v|ij> / (eps_ij^cd eps_ij^ab)
+ *          = sum t0_ab^ij sum_{c<d} <ab|v|cd> t0_cd^ij                      (pp ladder)
+ *   out[1] = (5) = 1/8 sum <ab|v|kl><kl|v|ij><ij|v|ab> / (eps_ij^ab eps_kl^ab)
+ *          = sum t0_ab^ij sum_{k<l} t0_ab^kl <kl|v|ij>                      (hh ladder)
+ *   out[2] = (3) = sum_{ijkabc} t0_ab^ij <kb|v|cj> t0_ac^ik                 (ph ring)
+ *          = sum t0_ab^ij [P(ij)P(ab) sum_kc <kb|v|cj> t0_ik^ac]_restricted.
+ * Eq. (diag3) is printed with <bk|v|ic> = <kb|v|ci>; read with <kb|v|cj> (i and j of that
+ * factor swapped): as printed it vanishes for two particles and misses third-order
+ * Rayleigh-Schroedinger perturbation theory, which the form used here reproduces.
+ * Returns 0, or -1 on a zero denominator or no memory. */
+int om_mbpt3(om_sys *S, double *out) {
+    build_ccd_blocks(S);
+    double *t0 = malloc(sizeof(double) * (S->nt + 1));
+    double *xT = malloc(sizeof(double) * (S->nxt + 1));
+    double *xC = malloc(sizeof(double) * (S->nxc + 1));
+    double *xQ = malloc(sizeof(double) * (S->nxt + 1));
+    if (!t0 || !xT || !xC || !xQ) {
+        free(t0); free(xT); free(xC); free(xQ);
+        return -1;
+    }
+    int bad = 0;
+    for (int c = 0; c < S->nch; c++)
+        for (int x = 0; x < S->npp[c]; x++)
+            for (int y = 0; y < S->nhh[c]; y++) {
+                int a = S->pp_p[S->pp_off[c] + x], b = S->pp_q[S->pp_off[c] + x];
+                int i = S->hh_p[S->hh_off[c] + y], j = S->hh_q[S->hh_off[c] + y];
+                double D = S->eps[i] + S->eps[j] - S->eps[a] - S->eps[b];
+                size_t z = S->t_off[c] + (size_t)x * S->nhh[c] + y;
+                if (D == 0.0) bad = 1;
+                t0[z] = D != 0.0 ? S->v_pphh[z] / D : 0.0;
+            }
+    if (bad) {
+        free(t0); free(xT); free(xC); free(xQ);
+        return -1;
+    }
+    ph_cross(S, t0, xT, xC, xQ, 0, 0);
+    double e4 = 0.0, e5 = 0.0, e3 = 0.0;
+    for (int c = 0; c < S->nch; c++) {
+        int np = S->npp[c], nh = S->nhh[c];
+        const double *tb = t0 + S->t_off[c];
+        const double *vp = S->v_pppp + S->vpp_off[c], *vh = S->v_hhhh + S->vhh_off[c];
+        for (int x = 0; x < np; x++) {
+            int a = S->pp_p[S->pp_off[c] + x], b = S->pp_q[S->pp_off[c] + x];
+            for (int y = 0; y < nh; y++) {
+                int i = S->hh_p[S->hh_off[c] + y], j = S->hh_q[S->hh_off[c] + y];
+                double tz = tb[(size_t)x * nh + y];
+                double pp = 0.0, hh = 0.0;
+                for (int cd = 0; cd < np; cd++) pp += vp[(size_t)x * np + cd] * tb[(size_t)cd * nh + y];
+                for (int kl = 0; kl < nh; kl++) hh += tb[(size_t)x * nh + kl] * vh[(size_t)kl * nh + y];
+                e4 += tz * pp;
+                e5 += tz * hh;
+                e3 += tz * ph_combine(S, xQ, a, b, i, j, 0);
+            }
+        }
+    }
+    out[0] = e4;
+    out[1] = e5;
+    out[2] = e3;
+    free(t0); free(xT); free(xC); free(xQ);
+    return 0;
+}
+
 /* The P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj part of Eq. (ccd3) for the restricted amplitudes t
  * (oracle layout), into out (same layout); absval != 0 gives the absolute-value bound. */
 int om_ph_apply(om_sys *S, const double *t, double *out, int absval) {
@@ -866,7 +950,7 @@ int om_ph_apply(om_sys *S, const double *t, double *out, int absval) {
         free(xT); free(xC); free(xQ);
         return -1;
     }
-    ph_cross(S, t, xT, xC, xQ, absval);
+    ph_cross(S, t, xT, xC, xQ, absval, 1);
     for (int c = 0; c < S->nch; c++) {
         int np = S->npp[c], nh = S->nhh[c];
         for (int x = 0; x < np; x++) {
