@@ -59,6 +59,19 @@ typedef struct {
 #define PNM_INIT_MLP 3    /* learned start (pnm_mlp_set_model); falls back to MBPT2 if the
                              iteration from it does not converge */
 
+/* Terms the iteration keeps (Sec. "Coupled cluster theory"):
+ *   PNM_TERMS_FULL    Eq. (ccd3);
+ *   PNM_TERMS_PP      Eq. (ccd1): <ab|v|ij>, the energy denominator and the pp ladder with the
+ *                     bare interaction (the G-matrix equation at omega = eps_i + eps_j);
+ *   PNM_TERMS_PPHH    Eq. (ccd2): and the hh ladder 1/2 sum_kl <kl|v|ij> t_kl^ab;
+ *   PNM_TERMS_LINEAR  every term of Eq. (ccd3) linear in t (both ladders and the ph term with
+ *                     <kb|v|cj>), none of the quadratic ones.
+ * The truncations are linear in t; they run in FP64 (precision PNM_PREC_FP64). */
+#define PNM_TERMS_FULL 0
+#define PNM_TERMS_PP 1
+#define PNM_TERMS_PPHH 2
+#define PNM_TERMS_LINEAR 3
+
 /* Options of the CCD iteration (Eq. ccd3 with mixing and the stopping rule of Sec.
  * "Developing a numerical project"). */
 typedef struct {
@@ -73,10 +86,11 @@ typedef struct {
                              passes) */
     int init;             /* PNM_INIT_* */
     int host_loop;        /* 0: device-side loop in one CUDA graph; 1: host checks each iteration */
+    int terms;            /* PNM_TERMS_*: the full Eq. (ccd3) or a truncation (FP64 only) */
 } pnm_solve_opts;
 
 /* Fills the defaults of the small FP64 workload: FP64, alpha 0.5, tol 1e-10 MeV,
- * max_iter 500, no refinement, MBPT2 start, device-side loop. */
+ * max_iter 500, no refinement, MBPT2 start, device-side loop, full Eq. (ccd3). */
 void pnm_default_opts(pnm_solve_opts *opts);
 
 /* Build one system: the basis of Sec. "Single-particle basis for infinite matter" (k =
@@ -151,6 +165,17 @@ int pnm_eref(const pnm_ctx *ctx, double *e_ref);
 /* Second-order correlation energy, Eq. (ccdGuess) and the energy below it, computed as a
  * fused pass over the direct channels.  One value per system. */
 int pnm_mbpt2(pnm_ctx *ctx, double *dE);
+
+/* Third-order correlation energy (Sec. "Many-body perturbation theory", Fig. goldstone):
+ * e3[3 s + 0] = diagram (4), the pp ladder (Eq. diag4); e3[3 s + 1] = diagram (5), the hh
+ * ladder (Eq. diag5); e3[3 s + 2] = diagram (3), the particle-hole ring (Eq. diag3, read with
+ * <kb|v|cj> where the paper prints <bk|v|ic>; that reading is the third order of
+ * Rayleigh-Schroedinger perturbation theory with HF energies).  Their sum is the MBPT3
+ * correction; diagrams with HF insertions vanish in this basis.  Computed on the GPU in FP64
+ * from the MBPT2 amplitudes t0 = <ab|v|ij>/eps_ij^ab: one pp-ladder launch, one linear ph
+ * launch and a fused row pass with the hh ladder and the three dot products.  e3: host,
+ * 3 n_systems doubles.  The context's amplitudes afterwards hold the MBPT2 guess. */
+int pnm_mbpt3(pnm_ctx *ctx, double *e3);
 
 /* The same second-order energy as pnm_mbpt2, for callers that must not allocate device
  * memory at the time of the call: code running while a CUDA graph is being captured

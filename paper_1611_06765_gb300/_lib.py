@@ -24,11 +24,16 @@ PNM_INIT_ZERO = 1
 PNM_INIT_KEEP = 2
 PNM_INIT_MLP = 3
 
+PNM_TERMS_FULL = 0
+PNM_TERMS_PP = 1
+PNM_TERMS_PPHH = 2
+PNM_TERMS_LINEAR = 3
+
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
     "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_twist_mesh",
     "pnm_destroy", "pnm_num_systems",
-    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc",
+    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc", "pnm_mbpt3",
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_apply_ph_term", "pnm_mlp_num_params", "pnm_mlp_init",
@@ -44,7 +49,7 @@ class pnm_minnesota(C.Structure):
 class pnm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("mix_alpha", C.c_double), ("tol_dE", C.c_double),
                 ("tol_dE_per_N", C.c_double), ("max_iter", C.c_int), ("refine_sweeps", C.c_int),
-                ("init", C.c_int), ("host_loop", C.c_int)]
+                ("init", C.c_int), ("host_loop", C.c_int), ("terms", C.c_int)]
 
 
 class pnm_mlp_opts(C.Structure):
@@ -85,6 +90,7 @@ def load(path=None):
     L.pnm_eref.argtypes = [vp, dp]
     L.pnm_mbpt2.argtypes = [vp, dp]
     L.pnm_mbpt2_noalloc.argtypes = [vp, dp]
+    L.pnm_mbpt3.argtypes = [vp, dp]
     L.pnm_ccd_solve.argtypes = [vp, C.POINTER(pnm_solve_opts), dp, ip, dp]
     L.pnm_energy_history.argtypes = [vp, C.c_int, dp, C.c_int, ip]
     L.pnm_amplitude_labels.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t), vp]

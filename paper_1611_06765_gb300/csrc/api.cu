@@ -67,6 +67,7 @@ void pnm_default_opts(pnm_solve_opts* o) {
   o->refine_sweeps = 0;
   o->init = PNM_INIT_MBPT2;
   o->host_loop = 0;
+  o->terms = PNM_TERMS_FULL;
 }
 
 const char* pnm_last_error(void) { return g_last_error.c_str(); }
@@ -314,6 +315,14 @@ int pnm_mbpt2(pnm_ctx* ctx, double* dE) {
   return guarded([&]() {
     if (!ctx || !dE) throw PnmError{PNM_EINVAL, "null argument"};
     pnm_mbpt2_all(ctx, dE);
+    return PNM_OK;
+  });
+}
+
+int pnm_mbpt3(pnm_ctx* ctx, double* e3) {
+  return guarded([&]() {
+    if (!ctx || !e3) throw PnmError{PNM_EINVAL, "null argument"};
+    pnm_mbpt3_all(ctx, e3);
     return PNM_OK;
   });
 }

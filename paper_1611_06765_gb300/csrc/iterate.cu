@@ -131,16 +131,24 @@ struct Vec4<double> {
 };
 
 // The two contractions of a cross channel from the staged Ts (T) and Xt (W^T); writes Q.
-//   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb
+//   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb   (quad false: <kb|v|cj>)
 //   Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
 template <typename T_, int NT>
 __device__ __forceinline__ void ph_contract(T_* Ts, T_* Xt, T_* Cs, int nph, int nhp, int P4, int H4,
-                                            const T_* __restrict__ v1, T_* __restrict__ q) {
+                                            const T_* __restrict__ v1, T_* __restrict__ q, bool quad) {
+  if (!quad) {
+    // linear term only: C = <kb|v|cj>, zero-padded
+    for (int e = threadIdx.x; e < H4 * H4; e += NT) {
+      int r = e / H4, c2 = e % H4;
+      Cs[e] = (r < nhp && c2 < nhp) ? v1[(long)r * nhp + c2] : (T_)0;
+    }
+    __syncthreads();
+  }
   // Small channels: one output per thread (more threads busy, shorter chains); large
   // channels: 4 x 4 register tiles.
   const bool small = (nph * nhp <= 2 * NT) && (nhp * nhp <= 2 * NT);
   if (small) {
-    for (int e = threadIdx.x; e < nhp * nhp; e += NT) {
+    for (int e = threadIdx.x; e < nhp * nhp && quad; e += NT) {
       int r = e / nhp, c2 = e % nhp;
       T_ acc = 0;
       for (int u = 0; u < nph; u++) acc += Xt[u * H4 + r] * Ts[u * H4 + c2];
@@ -156,7 +164,7 @@ __device__ __forceinline__ void ph_contract(T_* Ts, T_* Xt, T_* Cs, int nph, int
     return;
   }
   int th = H4 >> 2;
-  for (int tile = threadIdx.x; tile < th * th; tile += NT) {
+  for (int tile = threadIdx.x; tile < th * th && quad; tile += NT) {
     int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
     T_ acc[4][4] = {};
     for (int u = 0; u < nph; u++) {
@@ -221,7 +229,8 @@ __device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__
 }
 
 // One CTA (NT threads) per cross channel of the launch's size class.  Staging: Ts = T,
-// Xt = W^T (W is stored transposed), both zero-padded to multiples of 4.
+// Xt = W^T (W is stored transposed), both zero-padded to multiples of 4.  xw == nullptr: the
+// term linear in t only (C = <kb|v|cj>).
 template <typename T_, int NT, bool GATHER>
 __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
                                            const int* __restrict__ xlist, const T_* __restrict__ xt,
@@ -244,10 +253,10 @@ __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict
     bool in = u < nph && s < nhp;
     long o = (long)u * nhp + s;
     Ts[e] = in ? ph_t<T_, GATHER>(D, tcur, xt, to + o) : (T_)0;
-    Xt[e] = in ? xw[wo + o] : (T_)0;  // W^T[u][s] = W[s][u]
+    Xt[e] = in && xw ? xw[wo + o] : (T_)0;  // W^T[u][s] = W[s][u]
   }
   __syncthreads();
-  ph_contract<T_, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to);
+  ph_contract<T_, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to, xw != nullptr);
 }
 
 // Cross channels of at most PH_WARP_DIM rows/columns: one warp per channel with its own
@@ -274,14 +283,14 @@ __global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const Loo
   for (int e = lane; e < nph * nhp; e += 32) {
     int u = e / nhp, c = e % nhp;
     Ts[u * S + c] = ph_t<T_, GATHER>(D, tcur, xt, to + e);
-    Ws[u * S + c] = xw[wo + e];
+    Ws[u * S + c] = xw ? xw[wo + e] : (T_)0;
   }
   __syncwarp();
   for (int e = lane; e < nhp * nhp; e += 32) {
     int r = e / nhp, c = e % nhp;
     T_ acc = 0;
-    for (int u = 0; u < nph; u++) acc += Ws[u * S + r] * Ts[u * S + c];
-    Cs[r * S + c] = xv1[co + e] + (T_)0.5 * acc;
+    for (int u = 0; u < nph && xw; u++) acc += Ws[u * S + r] * Ts[u * S + c];
+    Cs[r * S + c] = xw ? xv1[co + e] + (T_)0.5 * acc : xv1[co + e];
   }
   __syncwarp();
   for (int e = lane; e < nph * nhp; e += 32) {
@@ -326,9 +335,9 @@ static void ph_attributes(const pnm_ctx* ctx) {
                                 (int)ph_warp_smem(sizeof(T_))));
 }
 
-// FP64 ph: T gathered from the current FP64 amplitudes.
-void launch_ph64(pnm_ctx* ctx, cudaStream_t s) {
-  launch_ph_classes<double, true>(ctx, nullptr, ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
+// FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
+void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear) {
+  launch_ph_classes<double, true>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
 }
 
 // Mixed ph: T read from the copy the update scatters.
@@ -1070,6 +1079,80 @@ void pnm_mbpt2_all(pnm_ctx* ctx, double* out) {
   ctx->t_mbpt2 = ms;
 }
 
+// Third-order diagrams (Fig. goldstone, Eqs. diag3-diag5) from the MBPT2 amplitudes t0 held in
+// D.t0, the pp ladder of t0 in D.rpp (S_z = 0 channels) and the linear ph term of t0 in D.xq:
+// per row (channel, ij) the partial sums over ab of
+//   (4)  t0_ab^ij sum_{c<d} <ab|v|cd> t0_cd^ij,
+//   (5)  t0_ab^ij sum_{k<l} t0_ab^kl <kl|v|ij>,
+//   (3)  t0_ab^ij [P(ij)P(ab) sum_kc <kb|v|cj> t0_ik^ac],
+// into parts[0..3) x nrows.
+__global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restrict__ parts, int nrows) {
+  __shared__ double sh32[32];
+  int2 it = D.row_item[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  long base = D.ch_t_off[c], row = base + (long)ij * npp;
+  const double* __restrict__ vh = D.v_hhhh + D.ch_vhh_off[c];
+  const double* __restrict__ t = D.t0;
+  bool szero = D.ch_szero[c] != 0;
+  double e4 = 0.0, e5 = 0.0, e3 = 0.0;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    long z = row + ab;
+    double tz = t[z];
+    if (szero) e4 += tz * D.rpp[z];
+    double hh = 0.0;
+    for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * vh[(long)kl * nh + ij];
+    e5 += tz * hh;
+    int4 q = D.qmap[z];
+    double ph = 0.0;
+    if (q.x >= 0) ph += D.xq[q.x];
+    if (q.y >= 0) ph -= D.xq[q.y];
+    if (q.z >= 0) ph -= D.xq[q.z];
+    if (q.w >= 0) ph += D.xq[q.w];
+    e3 += tz * ph;
+  }
+  e4 = block_sum(e4, sh32);
+  e5 = block_sum(e5, sh32);
+  e3 = block_sum(e3, sh32);
+  if (threadIdx.x == 0) {
+    parts[blockIdx.x] = e4;
+    parts[nrows + blockIdx.x] = e5;
+    parts[2 * nrows + blockIdx.x] = e3;
+  }
+}
+
+// out[3 s + {0, 1, 2}] = diagrams (4), (5), (3) of system s.  Replaces the context's
+// amplitudes by the MBPT2 guess.
+void pnm_mbpt3_all(pnm_ctx* ctx, double* out) {
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  if (!ctx->mbpt3_buf) ctx->mbpt3_buf = (double*)dmalloc(ctx, sizeof(double) * (3 * (size_t)ctx->nrows + 3 * nsys));
+  double* parts = ctx->mbpt3_buf;
+  double* res = parts + 3 * (size_t)ctx->nrows;
+  CUDA_TRY(cudaEventRecord(ctx->ev[0], s));
+  // amplitudes of the start in t0, read by the contraction kernels (iteration parity 0, no
+  // system frozen)
+  CUDA_TRY(cudaMemsetAsync(&ctx->ctl->iter, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(&ctx->ctl->skip_done, 0, sizeof(int), s));
+  k_init<<<ctx->nrows, 128, 0, s>>>(ctx->d, PNM_INIT_MBPT2);
+  pnm_launch_pp64(ctx, s);
+  if (ctx->nx > 0) launch_ph64(ctx, s, true);  // without cross channels no Q is read
+  k_mbpt3_rows<<<ctx->nrows, 128, 0, s>>>(ctx->d, parts, ctx->nrows);
+  for (int k = 0; k < 3; k++)
+    k_reduce_rows<<<nsys, 256, 0, s>>>(parts + (size_t)k * ctx->nrows, ctx->row_lo_d, ctx->row_hi_d,
+                                       res + (size_t)k * nsys);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecord(ctx->ev[1], s));
+  std::vector<double> h(3 * (size_t)nsys);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), res, sizeof(double) * 3 * nsys, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < 3; k++)
+    for (int y = 0; y < nsys; y++) out[3 * y + k] = h[(size_t)k * nsys + y];
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+  ctx->t_mbpt3 = ms;
+}
+
 // The MBPT2 kernels of pnm_mbpt2_all with caller-chosen device buffers for the per-row
 // partial sums (nrows doubles) and the per-system results (nsys doubles).
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results) {
@@ -1142,14 +1225,17 @@ void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed) {
   prof_end(ctx);
 }
 
-static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
-  DevState& D = ctx->d;
+// One FP64 update.  terms (PNM_TERMS_*): the full Eq. (ccd3), or a truncation whose
+// intermediates were fixed by pnm_prepare_terms (one-body terms zero, chi_kl^ij = <kl|v|ij>
+// or zero, the ph term zero unless the linear ph term is launched here).
+static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, int terms) {
   cudaStream_t s_ph = pnm_concurrent(ctx) ? ctx->side[0] : ctx->stream;
   cudaStream_t s_pp = pnm_concurrent(ctx) ? ctx->side[1] : ctx->stream;
+  bool ph_on = terms == PNM_TERMS_FULL || terms == PNM_TERMS_LINEAR;
   pnm_fork(ctx);
-  if (ctx->nx > 0) {
+  if (ctx->nx > 0 && ph_on) {
     prof_begin(ctx, KID_PH64);
-    launch_ph64(ctx, s_ph);
+    launch_ph64(ctx, s_ph, terms == PNM_TERMS_LINEAR);
     prof_end(ctx);
   }
   if (ctx->n_pp_items > 0) {
@@ -1157,7 +1243,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
     pnm_launch_pp64(ctx, s_pp);
     prof_end(ctx);
   }
-  pnm_enqueue_stats(ctx, false);
+  if (terms == PNM_TERMS_FULL) pnm_enqueue_stats(ctx, false);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
   launch_update64(ctx, use_cond, h);
@@ -1197,10 +1283,26 @@ void prof_collect(pnm_ctx* ctx) {
   ctx->prof_pending.clear();
 }
 
+// mode = precision | (terms << 4); truncations (terms != 0) are FP64 only.
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
-  ctx->cur_mode = mode == PNM_PREC_FP64 ? 0 : 1;
-  if (mode == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h);
+  int prec = mode & 15, terms = mode >> 4;
+  ctx->cur_mode = prec == PNM_PREC_FP64 ? 0 : 1;
+  if (prec == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h, terms);
   else pnm_enqueue_body_mixed(ctx, use_cond, h);
+}
+
+// Fixed intermediates of a truncated iteration: no one-body terms, chi_kl^ij = <kl|v|ij>
+// (hh ladder with the bare interaction) or zero (no hh ladder), and no ph term unless the
+// linear one is recomputed every step.
+void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
+  if (terms == PNM_TERMS_FULL) return;
+  cudaStream_t s = ctx->stream;
+  CUDA_TRY(cudaMemsetAsync(ctx->d.dchi, 0, sizeof(double) * ctx->nsp_total, s));
+  if (terms == PNM_TERMS_PP) CUDA_TRY(cudaMemsetAsync(ctx->d.chi_hh, 0, sizeof(double) * ctx->nvhh, s));
+  else CUDA_TRY(cudaMemcpyAsync(ctx->d.chi_hh, ctx->d.v_hhhh, sizeof(double) * ctx->nvhh,
+                                cudaMemcpyDeviceToDevice, s));
+  if (terms != PNM_TERMS_LINEAR && ctx->nxt > 0)
+    CUDA_TRY(cudaMemsetAsync(ctx->d.xq, 0, sizeof(double) * ctx->nxt, s));
 }
 
 // Build (once per mode) a graph whose single node is a WHILE conditional looping the body.
@@ -1248,7 +1350,9 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_lo
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->min_iter, &min_iter, sizeof(int), cudaMemcpyHostToDevice, s));
   static const int kOne = 1, kZero = 0;
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->mode, &mode, sizeof(int), cudaMemcpyHostToDevice, s));
+  static const int kMode[2] = {0, 1};
+  CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->mode, &kMode[(mode & 15) == PNM_PREC_FP64 ? 0 : 1], sizeof(int),
+                           cudaMemcpyHostToDevice, s));
   if (max_iter <= 0) return PNM_ENOTCONV;
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &kOne, sizeof(int), cudaMemcpyHostToDevice, s));
   if (!host_loop) {

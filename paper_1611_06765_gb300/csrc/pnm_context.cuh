@@ -53,6 +53,7 @@ struct pnm_ctx {
   int *row_lo_d = nullptr, *row_hi_d = nullptr, *lut_off_d = nullptr;  // per system
   LoopCtl* ctl = nullptr;     // device
   double* small = nullptr;    // device scratch for single-value queries
+  double* mbpt3_buf = nullptr;  // per-row partials and per-system results of pnm_mbpt3
   SysCtl* sysctl = nullptr;   // device, one per system
   double* hist = nullptr;     // device, (hist_cap) per system
   int hist_cap = 0;
@@ -83,7 +84,7 @@ struct pnm_ctx {
   int prof_n[PNM_NKERNELS] = {};
 
   // timings (ms)
-  double t_setup = 0, t_mbpt2 = 0, t_solve = 0, t_mixed = 0, t_refine = 0;
+  double t_setup = 0, t_mbpt2 = 0, t_solve = 0, t_mixed = 0, t_refine = 0, t_mbpt3 = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -105,6 +106,8 @@ void pnm_mbpt2_all(pnm_ctx* ctx, double* out);
 int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, double* resid);
 void pnm_free_mixed(pnm_ctx* ctx);
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h);
+void pnm_prepare_terms(pnm_ctx* ctx, int terms);
+void pnm_mbpt3_all(pnm_ctx* ctx, double* out);
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_mixed(pnm_ctx* ctx);
 void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);
@@ -127,7 +130,7 @@ void pnm_join(pnm_ctx* ctx);
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
 void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
-void launch_ph64(pnm_ctx* ctx, cudaStream_t s);
+void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s);
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);

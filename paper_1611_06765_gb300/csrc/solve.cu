@@ -24,6 +24,9 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   if (o.init < PNM_INIT_MBPT2 || o.init > PNM_INIT_MLP) throw PnmError{PNM_EINVAL, "unknown init"};
   if (o.refine_sweeps < 0) throw PnmError{PNM_EINVAL, "refine_sweeps must be >= 0"};
   if (!(o.tol_dE > 0.0) && !(o.tol_dE_per_N > 0.0)) throw PnmError{PNM_EINVAL, "no tolerance given"};
+  if (o.terms < PNM_TERMS_FULL || o.terms > PNM_TERMS_LINEAR) throw PnmError{PNM_EINVAL, "unknown terms"};
+  if (o.terms != PNM_TERMS_FULL && o.precision != PNM_PREC_FP64)
+    throw PnmError{PNM_EINVAL, "truncated iterations run in FP64 only"};
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
   // work skipping for converged systems is scoped to the solve loops
@@ -64,9 +67,10 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   }
   pnm_start(ctx, init, tol);
   if (mixed) pnm_mixed_pack_initial(ctx);
+  pnm_prepare_terms(ctx, o.terms);
   int it0 = 0;
-  int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : PNM_PREC_FP64, o.max_iter, 0, o.host_loop,
-                            o.mix_alpha, &it0);
+  int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : (PNM_PREC_FP64 | (o.terms << 4)), o.max_iter, 0,
+                            o.host_loop, o.mix_alpha, &it0);
   CUDA_TRY(cudaEventRecord(e1, s));
   if (mixed && status == 1 && o.refine_sweeps > 0) {
     // exactly refine_sweeps FP64 updates, then (if the FP64 test has not passed by then)

@@ -36,6 +36,7 @@ def test_default_opts_and_errors_without_gpu(lib):
     o = _lib.pnm_solve_opts()
     lib.pnm_default_opts(C.byref(o))
     assert o.precision == 0 and o.mix_alpha == 0.5 and o.tol_dE == 1e-10 and o.max_iter == 500
+    assert o.terms == _lib.PNM_TERMS_FULL and C.sizeof(o) == 56
     # a null context is rejected before any CUDA call
     n = C.c_int()
     assert lib.pnm_num_systems(None, C.byref(n)) == _lib.PNM_EINVAL
