@@ -17,8 +17,10 @@ the model are resident in HBM before the timed region; L2 is flushed before ever
 ``e2e`` times the public API from host inputs: context creation (basis, channels and V built
 on the GPU), model upload, solve, converged amplitudes copied back.  ``comparison`` holds the
 same batch from the MBPT2 start (mixed and FP64) and the other configurations, each with its
-dE/N error against the FP64 oracle, and a twist-averaged batch (N = 14, n^2 <= 20, rho = 0.08,
-120 twists of a 4 x 5 x 6 Gauss-Legendre mesh in one context) in both precisions.  ``--impl reference`` times the FP64 CPU oracle.
+dE/N error against the FP64 oracle, a twist-averaged batch (N = 14, n^2 <= 20, rho = 0.08,
+120 twists of a 4 x 5 x 6 Gauss-Legendre mesh in one context) in both precisions, the ladder
+truncations of Eqs. ccd1 and ccd2 (N = 66, n^2 <= 36, rho = 0.16, FP64) and the third-order
+diagrams of the held-out batch (pnm_mbpt3, with the oracle's time and values).  ``--impl reference`` times the FP64 CPU oracle.
 
 Prints one JSON line.
 """
@@ -57,6 +59,13 @@ TWIST_WORKLOADS = {
     "pnm_N14_rho0.08_n2max20_tabc4x5x6_bf16x3": (14, 0.08, 20, (4, 5, 6), "bf16x3"),
     "pnm_N14_rho0.08_n2max20_tabc4x5x6_fp64": (14, 0.08, 20, (4, 5, 6), "fp64"),
 }
+# Truncated iterations (Eq. ccd1: pp ladder; Eq. ccd2: pp and hh ladders), FP64, and the
+# third-order diagrams.  name: (N, densities, n2max, terms)
+TRUNC_WORKLOADS = {
+    "pnm_N66_rho0.16_n2max36_ccd1_pp_fp64": (66, (0.16,), 36, "pp"),
+    "pnm_N66_rho0.16_n2max36_ccd2_pphh_fp64": (66, (0.16,), 36, "pphh"),
+}
+MBPT3_WORKLOAD = ("pnm_N66_n2max36_heldout3_mbpt3_fp64", 66, HELDOUT, 36)
 DEFAULT_WORKLOAD = "pnm_N66_n2max36_heldout3_learned_bf16x3"
 COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
            "pnm_N66_n2max36_heldout3_mbpt2_fp64", "pnm_N14_rho0.08_n2max20_bf16x3",
@@ -361,6 +370,77 @@ def measure_twist(P, torch, stream, flush, workload, refine, steps):
             "_theta": theta, "_w": w, "_dE_per_N": dE / N}
 
 
+def measure_trunc(P, torch, stream, flush, workload, steps):
+    """Mean time-to-converge (ms) of a truncated FP64 iteration at the metric's stopping rule,
+    with the oracle's fixed point of the same truncation (|dE change| / N < 1e-10 MeV)."""
+    N, rhos, n2max, terms = TRUNC_WORKLOADS[workload]
+    code = {"pp": P.PNM_TERMS_PP, "pphh": P.PNM_TERMS_PPHH}[terms]
+    ctx = P.Context(N, list(rhos), n2max, params=MINNESOTA, stream=stream.cuda_stream)
+    kw = dict(precision=P.PNM_PREC_FP64, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500, terms=code)
+    for _ in range(3):
+        ctx.solve(**kw)
+    torch.cuda.synchronize()
+    ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
+    ctx.close()
+    return {"ms": statistics.mean(ms), "iters": iters[-1], "terms": terms,
+            "dE_per_N": [x / N for x in dEs[-1]], "_key": (N, rhos, n2max, terms)}
+
+
+def oracle_trunc(r, budget_s=60.0):
+    from oracle import channel
+    N, rhos, n2max, terms = r.pop("_key")
+    err = {}
+    t0 = time.perf_counter()
+    for rho, d in zip(rhos, r["dE_per_N"]):
+        if time.perf_counter() - t0 > budget_s:
+            break
+        o = channel.OracleSystem(N, rho, n2max, MINNESOTA)
+        e, _, _, _ = o.ccd(alpha=ALPHA, tol=1e-10 * N, maxit=2000, terms=terms)
+        err[str(rho)] = d - e / N
+    r["dE_per_N_minus_oracle"] = err
+
+
+def measure_mbpt3(P, torch, stream, steps):
+    """Device time (ms) of pnm_mbpt3 on the held-out batch and its three diagrams per system."""
+    name, N, rhos, n2max = MBPT3_WORKLOAD
+    ctx = P.Context(N, list(rhos), n2max, params=MINNESOTA, stream=stream.cuda_stream)
+    for _ in range(3):
+        e3 = ctx.mbpt3()
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e3 = ctx.mbpt3()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    return {"ms": statistics.mean(ms), "N": N, "rho": list(rhos), "n2max": n2max,
+            "diagrams_per_N": {str(r): {"pp_ladder_4": e[0] / N, "hh_ladder_5": e[1] / N, "ph_ring_3": e[2] / N}
+                               for r, e in zip(rhos, e3.tolist())}}
+
+
+def oracle_mbpt3(r, budget_s=60.0):
+    """The oracle's diagrams for each system (timed) and the GPU's relative error."""
+    from oracle import channel
+    errs, tms = [], []
+    t0 = time.perf_counter()
+    for rho in r["rho"]:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        o = channel.OracleSystem(r["N"], rho, r["n2max"], MINNESOTA)
+        o.mbpt3()  # the first call builds the interaction blocks; the timed one reuses them
+        t1 = time.perf_counter()
+        ref = o.mbpt3()
+        tms.append((time.perf_counter() - t1) * 1e3)
+        got = r["diagrams_per_N"][str(rho)]
+        g = [got["pp_ladder_4"], got["hh_ladder_5"], got["ph_ring_3"]]
+        errs.append(max(abs(a * r["N"] - b) / abs(b) for a, b in zip(g, ref)))
+    r["max_rel_err_vs_oracle"] = max(errs) if errs else None
+    r["oracle_ms_per_system"] = statistics.mean(tms) if tms else None
+
+
 _twist_fixed = {}
 
 
@@ -538,6 +618,9 @@ def run_ours(a):
                 comparison[w] = measure(P, torch, stream, flush, w, a.refine, 5)
         for w in TWIST_WORKLOADS:
             comparison[w] = measure_twist(P, torch, stream, flush, w, a.refine, 5)
+        for w in TRUNC_WORKLOADS:
+            comparison[w] = measure_trunc(P, torch, stream, flush, w, 5)
+        comparison[MBPT3_WORKLOAD[0]] = measure_mbpt3(P, torch, stream, 5)
         if "train_s" in _model:
             comparison["training"] = {"seconds": _model["train_s"], "loss_first_last": _model["loss"],
                                       "epochs": _model["epochs"], "batch": _model["batch"],
@@ -576,6 +659,10 @@ def run_ours(a):
                     r["dE_per_N_minus_oracle"] = oracle_errors(r, w, ora)
                 elif w in TWIST_WORKLOADS:
                     oracle_twist(P, r)
+                elif w in TRUNC_WORKLOADS:
+                    oracle_trunc(r)
+                elif w == MBPT3_WORKLOAD[0]:
+                    oracle_mbpt3(r)
 
     if rank == 0:
         line = {
