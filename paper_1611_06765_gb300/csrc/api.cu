@@ -1,5 +1,8 @@
 // api.cu -- the extern "C" entry points declared in include/pnmcc.h.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 #include <cmath>
 #include <cstring>
 
@@ -27,6 +30,45 @@ static int guarded(F&& f) {
   }
 }
 
+static cudaMemPool_t library_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto f = pools.find(dev);
+  if (f != pools.end()) return f->second;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+  uint64_t keep = ~0ull;  // freed blocks stay in the pool for reuse until the process ends
+  CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pools[dev] = pool;
+  return pool;
+}
+
+void* pnm_pool_alloc(cudaStream_t s, size_t bytes) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  void* p = nullptr;
+  if (cudaMallocFromPoolAsync(&p, bytes ? bytes : 1, library_pool(dev), s) != cudaSuccess) {
+    cudaGetLastError();
+    throw PnmError{PNM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+  }
+  return p;
+}
+
+void pnm_pool_free(cudaStream_t s, void* p) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+void* pnm_ctx_alloc(pnm_ctx* ctx, size_t bytes) {
+  void* p = pnm_pool_alloc(ctx->stream, bytes);
+  ctx->owned.push_back(p);
+  return p;
+}
+
 static void release(pnm_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -34,7 +76,8 @@ static void release(pnm_ctx* ctx) {
   for (auto& g : ctx->graph_defs) cudaGraphDestroy(g.second);
   pnm_free_mixed(ctx);
   pnm_free_mlp(ctx);
-  for (void* p : ctx->owned) cudaFree(p);
+  for (void* p : ctx->owned) pnm_pool_free(ctx->stream, p);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (int k = 0; k < 2; k++) {

@@ -866,15 +866,7 @@ __global__ void k_start(const double* __restrict__ parts, const int* __restrict_
 
 // ------------------------------------------------------------------------- host side
 
-static void* dmalloc(pnm_ctx* ctx, size_t bytes) {
-  void* p = nullptr;
-  if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) {
-    cudaGetLastError();
-    throw PnmError{PNM_ENOMEM, "cudaMalloc failed"};
-  }
-  ctx->owned.push_back(p);
-  return p;
-}
+static void* dmalloc(pnm_ctx* ctx, size_t bytes) { return pnm_ctx_alloc(ctx, bytes); }
 
 void pnm_prepare_iteration(pnm_ctx* ctx) {
   cudaStream_t s = ctx->stream;

@@ -64,10 +64,13 @@ __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restr
   const double* V = v_pppp + ch_vpp_off[it.ch];
   __nv_bfloat16* hi = vt + it.voff + (long)kb * 2 * (TC_M * TC_BK);
   __nv_bfloat16* lo = hi + TC_M * TC_BK;
+  // V is symmetric (bit for bit: <ab|v|cd> and <cd|v|ab> are evaluated by the same
+  // arithmetic), so the element (cd, ab) is read as (ab, cd): consecutive threads then read
+  // consecutive doubles of one row.
   for (int e = threadIdx.x; e < TC_M * TC_BK; e += blockDim.x) {
     int r = e / TC_BK, k = e % TC_BK;
     int ab = it.mt * TC_M + r, cd = kb * TC_BK + k;
-    double x = (ab < it.npp && cd < it.npp) ? V[(long)cd * it.npp + ab] : 0.0;
+    double x = (ab < it.npp && cd < it.npp) ? V[(long)ab * it.npp + cd] : 0.0;
     __nv_bfloat16 h, l;
     split_bf16(x, h, l);
     hi[core_off(r, k)] = h;
@@ -291,13 +294,7 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 
 template <typename T>
 T* mdalloc(pnm_ctx* ctx, size_t n) {
-  void* p = nullptr;
-  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    throw PnmError{PNM_ENOMEM, "cudaMalloc (mixed precision arenas) failed"};
-  }
-  ctx->owned.push_back(p);
-  return (T*)p;
+  return ctx_alloc<T>(ctx, n);
 }
 
 }  // namespace

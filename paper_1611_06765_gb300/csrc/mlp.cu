@@ -603,15 +603,15 @@ static void mlp_features(pnm_ctx* ctx) {
   if (M->X) return;
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
-  M->X = xalloc<float>((size_t)ctx->nt * MF, ctx->owned);
-  M->tm2 = xalloc<double>(ctx->nt, ctx->owned);
-  M->sigma = xalloc<double>(nsys, ctx->owned);
+  M->X = ctx_alloc<float>(ctx, (size_t)ctx->nt * MF);
+  M->tm2 = ctx_alloc<double>(ctx, ctx->nt);
+  M->sigma = ctx_alloc<double>(ctx, nsys);
   std::vector<long> tb(nsys + 1);
   for (int k = 0; k < nsys; k++) tb[k] = ctx->sys[k].t_begin;
   tb[nsys] = ctx->nt;
-  M->t_begin = xalloc<long>(nsys + 1, ctx->owned);
+  M->t_begin = ctx_alloc<long>(ctx, nsys + 1);
   CUDA_TRY(cudaMemcpyAsync(M->t_begin, tb.data(), sizeof(long) * (nsys + 1), cudaMemcpyHostToDevice, s));
-  double* parts = xalloc<double>(ctx->n_upd_items, ctx->owned);
+  double* parts = ctx_alloc<double>(ctx, ctx->n_upd_items);
   std::vector<long> cnt(nsys);
   std::vector<FeatSys> fs(nsys);
   for (int k = 0; k < nsys; k++) {
@@ -624,8 +624,8 @@ static void mlp_features(pnm_ctx* ctx) {
     fs[k].kscale = (2.0 * PNM_PI / S.L) / kF;
     fs[k].epsF = ctx->hbar2_2m * kF * kF;
   }
-  long* dcnt = xalloc<long>(nsys, ctx->owned);
-  FeatSys* dfs = xalloc<FeatSys>(nsys, ctx->owned);
+  long* dcnt = ctx_alloc<long>(ctx, nsys);
+  FeatSys* dfs = ctx_alloc<FeatSys>(ctx, nsys);
   CUDA_TRY(cudaMemcpyAsync(dcnt, cnt.data(), sizeof(long) * nsys, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(dfs, fs.data(), sizeof(FeatSys) * nsys, cudaMemcpyHostToDevice, s));
   k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, parts);
@@ -646,13 +646,13 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
   MlpState* M = ctx->mlp;
   cudaStream_t s = ctx->stream;
   if (!M->q) {
-    M->q = xalloc<float>(NPARAM, ctx->owned);
-    M->pw = xalloc<__nv_bfloat16>(PW_TOTAL, ctx->owned);
-    M->err = xalloc<int>(1, ctx->owned);
+    M->q = ctx_alloc<float>(ctx, NPARAM);
+    M->pw = ctx_alloc<__nv_bfloat16>(ctx, PW_TOTAL);
+    M->err = ctx_alloc<int>(ctx, 1);
     CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
     CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   }
-  float* w = xalloc<float>(NPARAM, ctx->owned);
+  float* w = ctx_alloc<float>(ctx, NPARAM);
   CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
   k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, M->q);
   k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(M->q, M->pw);

@@ -98,6 +98,17 @@ inline std::string pnm_shape_key(const pnm_ctx* ctx) {
   return k;
 }
 
+// Device memory of contexts: stream-ordered allocations from one memory pool per device, owned
+// by the library, whose freed blocks stay cached for the next context (a create/solve/destroy
+// loop then maps no new memory).  pnm_pool_alloc throws PNM_ENOMEM.
+void* pnm_pool_alloc(cudaStream_t s, size_t bytes);
+void pnm_pool_free(cudaStream_t s, void* p);
+// An allocation on the context stream recorded in ctx->owned (released by pnm_destroy).
+void* pnm_ctx_alloc(pnm_ctx* ctx, size_t bytes);
+template <typename T>
+T* ctx_alloc(pnm_ctx* ctx, size_t n) {
+  return (T*)pnm_ctx_alloc(ctx, (n ? n : 1) * sizeof(T));
+}
 void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
                const double* thetas, const pnm_minnesota& P);
 void pnm_prepare_iteration(pnm_ctx* ctx);

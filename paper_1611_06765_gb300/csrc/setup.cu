@@ -48,14 +48,13 @@ __device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int Sz, int m,
 }
 
 // ---------------------------------------------------------------------------- basis
-// One CTA.  Cube points c = ((x+r)w + (y+r))w + (z+r) are in (n_x, n_y, n_z) lexicographic
-// order, so a point's slot in the shell-ordered list is (points in lower shells) + (points
-// of the same shell with a smaller cube index).
-__global__ void k_basis(int n2max, int r, char4* __restrict__ nvec, int* __restrict__ idx3,
-                        int* __restrict__ nsp_out) {
-  extern __shared__ int sh[];  // shell counts [n2max + 1], then shell starts [n2max + 1]
-  int* cnt = sh;
-  int* start = sh + (n2max + 1);
+// Cube points c = ((x+r)w + (y+r))w + (z+r) are in (n_x, n_y, n_z) lexicographic order, so a
+// point's slot in the shell-ordered list is (points in lower shells) + (points of the same
+// shell with a smaller cube index).  k_basis_count: one CTA counts the shells (shared-memory
+// atomics) and writes the shell starts; k_basis_place: one thread per cube point counts the
+// same-shell points before it and writes the two spin states.
+__global__ void k_basis_count(int n2max, int r, int* __restrict__ start, int* __restrict__ nsp_out) {
+  extern __shared__ int cnt[];  // [n2max + 1]
   int w = 2 * r + 1, ncube = w * w * w;
   for (int k = threadIdx.x; k <= n2max; k += blockDim.x) cnt[k] = 0;
   __syncthreads();
@@ -73,25 +72,29 @@ __global__ void k_basis(int n2max, int r, char4* __restrict__ nvec, int* __restr
     }
     *nsp_out = 2 * acc;
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < ncube; c += blockDim.x) {
-    int x = c / (w * w) - r, y = (c / w) % w - r, z = c % w - r;
-    int n2 = dot3(x, y, z);
-    if (n2 > n2max) {
-      idx3[2 * c] = idx3[2 * c + 1] = -1;
-      continue;
-    }
-    int rank = 0;
-    for (int c2 = 0; c2 < c; c2++) {
-      int x2 = c2 / (w * w) - r, y2 = (c2 / w) % w - r, z2 = c2 % w - r;
-      rank += (dot3(x2, y2, z2) == n2);
-    }
-    int slot = start[n2] + rank;
-    nvec[2 * slot] = make_char4((char)x, (char)y, (char)z, (char)-1);
-    nvec[2 * slot + 1] = make_char4((char)x, (char)y, (char)z, (char)1);
-    idx3[2 * c] = 2 * slot;
-    idx3[2 * c + 1] = 2 * slot + 1;
+}
+
+__global__ void k_basis_place(int n2max, int r, const int* __restrict__ start, char4* __restrict__ nvec,
+                              int* __restrict__ idx3) {
+  int w = 2 * r + 1, ncube = w * w * w;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncube) return;
+  int x = c / (w * w) - r, y = (c / w) % w - r, z = c % w - r;
+  int n2 = dot3(x, y, z);
+  if (n2 > n2max) {
+    idx3[2 * c] = idx3[2 * c + 1] = -1;
+    return;
   }
+  int rank = 0;
+  for (int c2 = 0; c2 < c; c2++) {
+    int x2 = c2 / (w * w) - r, y2 = (c2 / w) % w - r, z2 = c2 % w - r;
+    rank += (dot3(x2, y2, z2) == n2);
+  }
+  int slot = start[n2] + rank;
+  nvec[2 * slot] = make_char4((char)x, (char)y, (char)z, (char)-1);
+  nvec[2 * slot + 1] = make_char4((char)x, (char)y, (char)z, (char)1);
+  idx3[2 * c] = 2 * slot;
+  idx3[2 * c + 1] = 2 * slot + 1;
 }
 
 // lut[m] = sum_{a=R,S} (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)).
@@ -510,6 +513,38 @@ __global__ void k_v_pppp(const int2* __restrict__ items, const int* __restrict__
   }
 }
 
+// The same elements, VPP_ROWS rows of one channel per CTA: the channel's pair states and the
+// LUT are staged in shared memory once, so the inner loop gathers from shared memory only.
+constexpr int VPP_ROWS = 16;
+__global__ void __launch_bounds__(256) k_v_pppp_rows(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
+                                                     const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
+                                                     const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
+                                                     const double* __restrict__ lut, int lut_len,
+                                                     double* __restrict__ v_pppp) {
+  extern __shared__ __align__(16) unsigned char vsm[];
+  double* slut = reinterpret_cast<double*>(vsm);
+  char4* sa = reinterpret_cast<char4*>(slut + lut_len);
+  int2 it = items[blockIdx.x];
+  int c = it.x, cd0 = it.y;
+  int npp = ch_npp[c];
+  char4* sb = sa + npp;
+  const int2* pairs = pp_pair + ch_pp_off[c];
+  for (int m = threadIdx.x; m < lut_len; m += blockDim.x) slut[m] = lut[m];
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 p = pairs[ab];
+    sa[ab] = nvec[p.x];
+    sb[ab] = nvec[p.y];
+  }
+  __syncthreads();
+  int cd1 = min(cd0 + VPP_ROWS, npp);
+  for (int cd = cd0; cd < cd1; cd++) {
+    char4 sc = sa[cd], sd = sb[cd];
+    double* out = v_pppp + ch_vpp_off[c] + (long)cd * npp;
+    for (int ab = threadIdx.x; ab < npp; ab += blockDim.x)
+      out[ab] = v_minnesota_as(sa[ab], sb[ab], sc, sd, slut);
+  }
+}
+
 __global__ void k_v_hhhh(int c0, const int* __restrict__ ch_hh_off,
                          const int* __restrict__ ch_nhh, const long* __restrict__ ch_vhh_off,
                          const int2* __restrict__ hh_pair, const char4* __restrict__ nvec,
@@ -544,14 +579,8 @@ __global__ void k_v_cross(int x0, const int* __restrict__ x_nph, const int* __re
 }
 
 template <typename T>
-T* dalloc(size_t n, std::vector<void*>& owned) {
-  void* p = nullptr;
-  size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    throw PnmError{PNM_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
-  }
+T* dalloc(size_t n, std::vector<void*>& owned, cudaStream_t s) {
+  void* p = pnm_pool_alloc(s, std::max<size_t>(n, 1) * sizeof(T));
   owned.push_back(p);
   return (T*)p;
 }
@@ -582,13 +611,14 @@ int isqrt_floor(int x) {
 
 // Per-system scratch that lives only during setup.
 struct SysScratch {
+  cudaStream_t stream = nullptr;  // allocations and their release are ordered on it
   int* idx3 = nullptr;
   int *key2ch = nullptr, *key2x = nullptr;
   int *pos_hh = nullptr, *pos_pp = nullptr, *phpos = nullptr, *phch = nullptr, *hppos = nullptr;
   std::vector<int> dkeys, dnhh, dnpp, xkeys, xnph, xnhp;
   std::vector<void*> owned;
   ~SysScratch() {
-    for (void* p : owned) cudaFree(p);
+    for (void* p : owned) pnm_pool_free(stream, p);
   }
 };
 
@@ -599,6 +629,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   std::vector<SysInfo>& sys = ctx->sys;
   sys.resize(nsys);
   std::vector<SysScratch> scr(nsys);
+  for (auto& x : scr) x.stream = s;
   ctx->hbar2_2m = P.hbar2_2m;
 
   // ---- basis per system (into scratch), closed-shell check on the host
@@ -624,10 +655,12 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       twisted = twisted || S.phi[a] != 0.0;
     }
     int w = 2 * S.r + 1, ncube = w * w * w;
-    char4* tvec = dalloc<char4>(2 * ncube, scr[k].owned);
-    scr[k].idx3 = dalloc<int>(2 * ncube, scr[k].owned);
-    int* dnsp = dalloc<int>(1, scr[k].owned);
-    k_basis<<<1, 512, 2 * (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, tvec, scr[k].idx3, dnsp);
+    char4* tvec = dalloc<char4>(2 * ncube, scr[k].owned, s);
+    scr[k].idx3 = dalloc<int>(2 * ncube, scr[k].owned, s);
+    int* dnsp = dalloc<int>(1, scr[k].owned, s);
+    int* shell_start = dalloc<int>(S.n2max + 1, scr[k].owned, s);
+    k_basis_count<<<1, 512, (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, shell_start, dnsp);
+    k_basis_place<<<(ncube + 127) / 128, 128, 0, s>>>(S.n2max, S.r, shell_start, tvec, scr[k].idx3);
     CUDA_TRY(cudaGetLastError());
     S.nsp = d2h(dnsp, 1, s)[0];
     if (S.N >= S.nsp) throw PnmError{PNM_EINVAL, "no particle states: n2max too small for N"};
@@ -637,10 +670,10 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       if (sh(hvec[k][S.N - 1]) == sh(hvec[k][S.N]))
         throw PnmError{PNM_EINVAL, "N = " + std::to_string(S.N) + " does not close a shell"};
     } else {
-      double* key = dalloc<double>(S.nsp, scr[k].owned);
-      double* skey = dalloc<double>(S.nsp, scr[k].owned);
-      int* perm = dalloc<int>(S.nsp, scr[k].owned);
-      char4* tv2 = dalloc<char4>(S.nsp, scr[k].owned);
+      double* key = dalloc<double>(S.nsp, scr[k].owned, s);
+      double* skey = dalloc<double>(S.nsp, scr[k].owned, s);
+      int* perm = dalloc<int>(S.nsp, scr[k].owned, s);
+      char4* tv2 = dalloc<char4>(S.nsp, scr[k].owned, s);
       int nb = (S.nsp + TWIST_THREADS - 1) / TWIST_THREADS;
       k_twist_keys<<<nb, TWIST_THREADS, 0, s>>>(tvec, S.nsp, S.phi[0], S.phi[1], S.phi[2], key);
       k_twist_rank<<<nb, TWIST_THREADS, 0, s>>>(key, S.nsp, tvec, tv2, skey, perm);
@@ -659,13 +692,13 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     lut_total += S.lut_len;
   }
   ctx->nsp_total = nsp_total;
-  D.nvec = dalloc<char4>(nsp_total, ctx->owned);
-  D.eps = dalloc<double>(nsp_total, ctx->owned);
-  D.ekin = dalloc<double>(nsp_total, ctx->owned);
-  D.sp_sys = dalloc<int>(nsp_total, ctx->owned);
-  D.sp_hole = dalloc<int>(nsp_total, ctx->owned);
-  D.lut = dalloc<double>(lut_total, ctx->owned);
-  D.dchi = dalloc<double>(nsp_total, ctx->owned);
+  D.nvec = dalloc<char4>(nsp_total, ctx->owned, s);
+  D.eps = dalloc<double>(nsp_total, ctx->owned, s);
+  D.ekin = dalloc<double>(nsp_total, ctx->owned, s);
+  D.sp_sys = dalloc<int>(nsp_total, ctx->owned, s);
+  D.sp_hole = dalloc<int>(nsp_total, ctx->owned, s);
+  D.lut = dalloc<double>(lut_total, ctx->owned, s);
+  D.dchi = dalloc<double>(nsp_total, ctx->owned, s);
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
     h2d(D.nvec + S.sp_off, hvec[k], s);
@@ -682,10 +715,10 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   // ---- channel counts (GPU) and selection (host: keys with both classes, ascending)
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
-    int* c1 = dalloc<int>(S.nkeys, scr[k].owned);
-    int* c2 = dalloc<int>(S.nkeys, scr[k].owned);
-    int* c3 = dalloc<int>(S.nkeys, scr[k].owned);
-    int* c4 = dalloc<int>(S.nkeys, scr[k].owned);
+    int* c1 = dalloc<int>(S.nkeys, scr[k].owned, s);
+    int* c2 = dalloc<int>(S.nkeys, scr[k].owned, s);
+    int* c3 = dalloc<int>(S.nkeys, scr[k].owned, s);
+    int* c4 = dalloc<int>(S.nkeys, scr[k].owned, s);
     int blocks = (S.nkeys * 32 + 255) / 256;
     k_count_direct<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.nkeys,
                                           S.N, S.nsp, c1, c2);
@@ -709,8 +742,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
         scr[k].xnhp.push_back(hp[K]);
       }
     }
-    scr[k].key2ch = dalloc<int>(S.nkeys, scr[k].owned);
-    scr[k].key2x = dalloc<int>(S.nkeys, scr[k].owned);
+    scr[k].key2ch = dalloc<int>(S.nkeys, scr[k].owned, s);
+    scr[k].key2x = dalloc<int>(S.nkeys, scr[k].owned, s);
     h2d(scr[k].key2ch, key2ch, s);
     h2d(scr[k].key2x, key2x, s);
   }
@@ -718,7 +751,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   // ---- channel metadata and offsets (host prefix sums over channels)
   std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_szero;
   std::vector<long> h_t_off, h_vpp_off, h_vhh_off;
-  std::vector<int2> h_rows, h_vpp_items;
+  std::vector<int2> h_rows, h_vpp_items, h_vpp_chunks;
+  int vpp_max_npp = 0;
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
   std::vector<long> h_x_t_off, h_x_c_off, h_x_w_off;
   long t_acc = 0, vpp_acc = 0, vhh_acc = 0, xt_acc = 0, xc_acc = 0;
@@ -745,6 +779,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       h_vpp_off.push_back(szero ? vpp_acc : -1);
       if (szero) {
         for (int cd = 0; cd < X.dnpp[c]; cd++) h_vpp_items.push_back(make_int2(g, cd));
+        for (int cd = 0; cd < X.dnpp[c]; cd += VPP_ROWS) h_vpp_chunks.push_back(make_int2(g, cd));
+        vpp_max_npp = std::max(vpp_max_npp, X.dnpp[c]);
         vpp_acc += (long)X.dnpp[c] * X.dnpp[c];
       }
       for (int ij = 0; ij < X.dnhh[c]; ij++) h_rows.push_back(make_int2(g, ij));
@@ -801,25 +837,25 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   ctx->h_pp_off = h_pp_off;
 
   int C = ctx->nch, NX = ctx->nx;
-  D.ch_sys = dalloc<int>(C, ctx->owned);
-  D.ch_key = dalloc<int>(C, ctx->owned);
-  D.ch_nhh = dalloc<int>(C, ctx->owned);
-  D.ch_npp = dalloc<int>(C, ctx->owned);
-  D.ch_hh_off = dalloc<int>(C, ctx->owned);
-  D.ch_pp_off = dalloc<int>(C, ctx->owned);
-  D.ch_szero = dalloc<int>(C, ctx->owned);
-  D.ch_t_off = dalloc<long>(C, ctx->owned);
-  D.ch_vpp_off = dalloc<long>(C, ctx->owned);
-  D.ch_vhh_off = dalloc<long>(C, ctx->owned);
-  D.row_item = dalloc<int2>(ctx->nrows, ctx->owned);
-  D.x_nph = dalloc<int>(NX, ctx->owned);
-  D.x_sys = dalloc<int>(NX, ctx->owned);
-  D.x_nhp = dalloc<int>(NX, ctx->owned);
-  D.x_ph_off = dalloc<int>(NX, ctx->owned);
-  D.x_hp_off = dalloc<int>(NX, ctx->owned);
-  D.x_t_off = dalloc<long>(NX, ctx->owned);
-  D.x_c_off = dalloc<long>(NX, ctx->owned);
-  D.x_w_off = dalloc<long>(NX, ctx->owned);
+  D.ch_sys = dalloc<int>(C, ctx->owned, s);
+  D.ch_key = dalloc<int>(C, ctx->owned, s);
+  D.ch_nhh = dalloc<int>(C, ctx->owned, s);
+  D.ch_npp = dalloc<int>(C, ctx->owned, s);
+  D.ch_hh_off = dalloc<int>(C, ctx->owned, s);
+  D.ch_pp_off = dalloc<int>(C, ctx->owned, s);
+  D.ch_szero = dalloc<int>(C, ctx->owned, s);
+  D.ch_t_off = dalloc<long>(C, ctx->owned, s);
+  D.ch_vpp_off = dalloc<long>(C, ctx->owned, s);
+  D.ch_vhh_off = dalloc<long>(C, ctx->owned, s);
+  D.row_item = dalloc<int2>(ctx->nrows, ctx->owned, s);
+  D.x_nph = dalloc<int>(NX, ctx->owned, s);
+  D.x_sys = dalloc<int>(NX, ctx->owned, s);
+  D.x_nhp = dalloc<int>(NX, ctx->owned, s);
+  D.x_ph_off = dalloc<int>(NX, ctx->owned, s);
+  D.x_hp_off = dalloc<int>(NX, ctx->owned, s);
+  D.x_t_off = dalloc<long>(NX, ctx->owned, s);
+  D.x_c_off = dalloc<long>(NX, ctx->owned, s);
+  D.x_w_off = dalloc<long>(NX, ctx->owned, s);
   h2d(D.ch_sys, h_ch_sys, s);
   {
     std::vector<int> h_x_sys(NX);
@@ -845,27 +881,27 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   h2d(D.x_c_off, h_x_c_off, s);
   h2d(D.x_w_off, h_x_w_off, s);
 
-  D.hh_pair = dalloc<int2>(hh_acc, ctx->owned);
-  D.pp_pair = dalloc<int2>(pp_acc, ctx->owned);
-  D.ph_pair = dalloc<int2>(ph_acc, ctx->owned);
-  D.hp_pair = dalloc<int2>(hp_acc, ctx->owned);
-  D.xmap = dalloc<int>(xt_acc, ctx->owned);
-  D.qmap = dalloc<int4>(t_acc, ctx->owned);
-  D.v_pphh = dalloc<double>(t_acc, ctx->owned);
-  D.den = dalloc<double>(t_acc, ctx->owned);
-  D.inv_den = dalloc<double>(t_acc, ctx->owned);
-  D.v_pppp = dalloc<double>(vpp_acc, ctx->owned);
-  D.v_hhhh = dalloc<double>(vhh_acc, ctx->owned);
-  D.x_v1 = dalloc<double>(xc_acc, ctx->owned);
-  D.x_w = dalloc<double>(xt_acc, ctx->owned);
-  D.t0 = dalloc<double>(t_acc, ctx->owned);
-  D.t1 = dalloc<double>(t_acc, ctx->owned);
-  D.rpp = dalloc<double>(t_acc, ctx->owned);
-  D.chi_hh = dalloc<double>(vhh_acc, ctx->owned);
-  D.sab = dalloc<double>(pp_acc, ctx->owned);
-  D.sij = dalloc<double>(hh_acc, ctx->owned);
-  D.xq = dalloc<double>(xt_acc, ctx->owned);
-  D.occ_off = dalloc<int>(nsp_total + 1, ctx->owned);
+  D.hh_pair = dalloc<int2>(hh_acc, ctx->owned, s);
+  D.pp_pair = dalloc<int2>(pp_acc, ctx->owned, s);
+  D.ph_pair = dalloc<int2>(ph_acc, ctx->owned, s);
+  D.hp_pair = dalloc<int2>(hp_acc, ctx->owned, s);
+  D.xmap = dalloc<int>(xt_acc, ctx->owned, s);
+  D.qmap = dalloc<int4>(t_acc, ctx->owned, s);
+  D.v_pphh = dalloc<double>(t_acc, ctx->owned, s);
+  D.den = dalloc<double>(t_acc, ctx->owned, s);
+  D.inv_den = dalloc<double>(t_acc, ctx->owned, s);
+  D.v_pppp = dalloc<double>(vpp_acc, ctx->owned, s);
+  D.v_hhhh = dalloc<double>(vhh_acc, ctx->owned, s);
+  D.x_v1 = dalloc<double>(xc_acc, ctx->owned, s);
+  D.x_w = dalloc<double>(xt_acc, ctx->owned, s);
+  D.t0 = dalloc<double>(t_acc, ctx->owned, s);
+  D.t1 = dalloc<double>(t_acc, ctx->owned, s);
+  D.rpp = dalloc<double>(t_acc, ctx->owned, s);
+  D.chi_hh = dalloc<double>(vhh_acc, ctx->owned, s);
+  D.sab = dalloc<double>(pp_acc, ctx->owned, s);
+  D.sij = dalloc<double>(hh_acc, ctx->owned, s);
+  D.xq = dalloc<double>(xt_acc, ctx->owned, s);
+  D.occ_off = dalloc<int>(nsp_total + 1, ctx->owned, s);
 
   // ---- pair lists, maps, V blocks per system
   std::vector<int> h_occ_off(nsp_total + 1, 0);
@@ -873,11 +909,11 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     SysInfo& S = sys[k];
     SysScratch& X = scr[k];
     int np = S.nsp - S.N;
-    X.pos_hh = dalloc<int>((size_t)S.N * S.N, X.owned);
-    X.pos_pp = dalloc<int>((size_t)np * np, X.owned);
-    X.phpos = dalloc<int>((size_t)np * S.N, X.owned);
-    X.phch = dalloc<int>((size_t)np * S.N, X.owned);
-    X.hppos = dalloc<int>((size_t)S.N * np, X.owned);
+    X.pos_hh = dalloc<int>((size_t)S.N * S.N, X.owned, s);
+    X.pos_pp = dalloc<int>((size_t)np * np, X.owned, s);
+    X.phpos = dalloc<int>((size_t)np * S.N, X.owned, s);
+    X.phch = dalloc<int>((size_t)np * S.N, X.owned, s);
+    X.hppos = dalloc<int>((size_t)S.N * np, X.owned, s);
     CUDA_TRY(cudaMemsetAsync(X.phch, 0xff, sizeof(int) * (size_t)np * S.N, s));
     int nchs = S.ch_end - S.ch_begin, nxs = S.x_end - S.x_begin;
     if (nchs > 0)
@@ -886,7 +922,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
           D.ch_key + S.ch_begin, D.ch_hh_off + S.ch_begin, D.ch_pp_off + S.ch_begin, D.hh_pair,
           D.pp_pair, X.pos_hh, X.pos_pp);
     if (nxs > 0) {
-      int* xk = dalloc<int>(nxs, X.owned);
+      int* xk = dalloc<int>(nxs, X.owned, s);
       h2d(xk, X.xkeys, s);
       k_fill_cross<<<(nxs * 32 + 255) / 256, 256, 0, s>>>(
           D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.N, S.nsp, S.sp_off, nxs, xk,
@@ -917,7 +953,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
                                     D.nvec, D.lut + S.lut_off, D.v_hhhh);
     CUDA_TRY(cudaGetLastError());
     // pairs containing each state
-    int* cnt = dalloc<int>(S.nsp, X.owned);
+    int* cnt = dalloc<int>(S.nsp, X.owned, s);
     int ob = (S.nsp * 32 + 255) / 256;
     k_occ<<<ob, 256, 0, s>>>(0, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, X.key2ch, S.ch_begin,
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, cnt, nullptr, nullptr);
@@ -925,7 +961,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     for (int p = 0; p < S.nsp; p++) h_occ_off[S.sp_off + p + 1] = h_occ_off[S.sp_off + p] + hc[p];
   }
   h2d(D.occ_off, h_occ_off, s);
-  D.occ_idx = dalloc<int>(h_occ_off[nsp_total], ctx->owned);
+  D.occ_idx = dalloc<int>(h_occ_off[nsp_total], ctx->owned, s);
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
     SysScratch& X = scr[k];
@@ -934,19 +970,32 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, nullptr, D.occ_off,
                              D.occ_idx);
   }
-  // V_pppp for S_z = 0 channels, all systems in one launch
+  // V_pppp for S_z = 0 channels, one launch per system (the LUT differs per system): chunks of
+  // VPP_ROWS rows with the channel staged in shared memory, or one row per CTA when a channel
+  // does not fit
   if (!h_vpp_items.empty()) {
-    int2* items = dalloc<int2>(h_vpp_items.size(), scr[0].owned);
-    h2d(items, h_vpp_items, s);
-    // the LUT differs per system: launch per system over its item range
+    int max_lut = 0;
+    for (const SysInfo& S : sys) max_lut = std::max(max_lut, S.lut_len);
+    size_t smem = sizeof(double) * max_lut + 2 * sizeof(char4) * (size_t)vpp_max_npp;
+    bool staged = smem <= 200 * 1024;
+    const std::vector<int2>& hv = staged ? h_vpp_chunks : h_vpp_items;
+    int2* items = dalloc<int2>(hv.size(), scr[0].owned, s);
+    h2d(items, hv, s);
+    if (staged)
+      CUDA_TRY(cudaFuncSetAttribute(k_v_pppp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     size_t lo = 0;
     for (int k = 0; k < nsys; k++) {
       size_t hi = lo;
-      while (hi < h_vpp_items.size() && h_ch_sys[h_vpp_items[hi].x] == k) hi++;
-      if (hi > lo)
-        k_v_pppp<<<(unsigned)(hi - lo), 256, 0, s>>>(items + lo, D.ch_pp_off, D.ch_npp,
-                                                    D.ch_vpp_off, D.pp_pair, D.nvec,
-                                                    D.lut + sys[k].lut_off, D.v_pppp);
+      while (hi < hv.size() && h_ch_sys[hv[hi].x] == k) hi++;
+      if (hi > lo) {
+        if (staged)
+          k_v_pppp_rows<<<(unsigned)(hi - lo), 256, smem, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
+                                                               D.pp_pair, D.nvec, D.lut + sys[k].lut_off,
+                                                               sys[k].lut_len, D.v_pppp);
+        else
+          k_v_pppp<<<(unsigned)(hi - lo), 256, 0, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
+                                                      D.pp_pair, D.nvec, D.lut + sys[k].lut_off, D.v_pppp);
+      }
       lo = hi;
     }
   }

@@ -39,13 +39,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     if (ctx->hist) {
       // the old buffer stays owned by the context until destroy
     }
-    void* p = nullptr;
-    if (cudaMalloc(&p, sizeof(double) * (size_t)cap * nsys) != cudaSuccess) {
-      cudaGetLastError();
-      throw PnmError{PNM_ENOMEM, "history buffer"};
-    }
-    ctx->owned.push_back(p);
-    ctx->hist = (double*)p;
+    ctx->hist = ctx_alloc<double>(ctx, (size_t)cap * nsys);
     ctx->hist_cap = cap;
     // graphs capture hist pointer and capacity: rebuild them
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
