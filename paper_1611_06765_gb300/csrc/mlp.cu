@@ -57,6 +57,8 @@ struct FeatSys {
   double epsF;    // hbar^2 k_F^2 / 2m
   double rho, kF;
   int N;
+  double inv_epsF, v_scale;   // 1 / epsF and N / epsF
+  float f19, f20, f21;        // rho / 0.16, k_F, N / 66
 };
 
 // t_MBPT2 per amplitude and partial sums of its square (one per update item).
@@ -70,10 +72,7 @@ __global__ void k_tm2(DevState D, const int4* __restrict__ items, double* __rest
   double s = 0.0;
   if (ab < npp && threadIdx.x < 128) {
     long z = D.ch_t_off[c] + (long)ij * npp + ab;
-    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
-    double den = D.eps[h.x] + D.eps[h.y] - D.eps[p.x] - D.eps[p.y];
-    double t = D.v_pphh[z] / den;
+    double t = D.v_pphh[z] * D.inv_den[z];  // the MBPT2 amplitude v / eps_ij^ab
     tm2[z] = t;
     s = t * t;
   }
@@ -89,11 +88,14 @@ __global__ void k_sigma(const double* __restrict__ parts, const int* __restrict_
   double acc = 0.0;
   for (int k = lo[s] + threadIdx.x; k < hi[s]; k += blockDim.x) acc += parts[k];
   acc = block_sum(acc, sh32);
-  if (threadIdx.x == 0) sigma[s] = sqrt(acc / (double)max(1L, count[s]));
+  if (threadIdx.x == 0) {
+    sigma[s] = sqrt(acc / (double)max(1L, count[s]));
+    sigma[gridDim.x + s] = 1.0 / sigma[s];
+  }
 }
 
 __global__ void k_features(DevState D, const int4* __restrict__ items, const FeatSys* __restrict__ fs,
-                           const double* __restrict__ tm2, const double* __restrict__ sigma,
+                           const double* __restrict__ tm2, const double* __restrict__ inv_sigma,
                            float* __restrict__ X) {
   int4 it = items[blockIdx.x];
   int c = it.x, ij = it.y;
@@ -113,13 +115,14 @@ __global__ void k_features(DevState D, const int4* __restrict__ items, const Fea
   x[6] = k * si.x; x[7] = k * si.y; x[8] = k * si.z;
   x[9] = k * sj.x; x[10] = k * sj.y; x[11] = k * sj.z;
   x[12] = sa.w; x[13] = sb.w; x[14] = si.w; x[15] = sj.w;
-  double den = D.eps[h.x] + D.eps[h.y] - D.eps[p.x] - D.eps[p.y];
-  x[16] = (float)(den / f.epsF);
-  x[17] = (float)(D.v_pphh[z] * f.N / f.epsF);
-  x[18] = (float)(tm2[z] / sigma[sys]);
-  x[19] = (float)(f.rho / 0.16);
-  x[20] = (float)f.kF;
-  x[21] = (float)(f.N / 66.0);
+  // FP64 only where the inputs are FP64: three products (reciprocals prepared per system) and
+  // their conversions; the per-system constants arrive as FP32
+  x[16] = (float)(D.den[z] * f.inv_epsF);
+  x[17] = (float)(D.v_pphh[z] * f.v_scale);
+  x[18] = (float)(tm2[z] * inv_sigma[sys]);
+  x[19] = f.f19;
+  x[20] = f.f20;
+  x[21] = f.f21;
 #pragma unroll
   for (int q = NFEAT; q < MF; q++) x[q] = 0.0f;
 }
@@ -605,7 +608,7 @@ static void mlp_features(pnm_ctx* ctx) {
   int nsys = (int)ctx->sys.size();
   M->X = ctx_alloc<float>(ctx, (size_t)ctx->nt * MF);
   M->tm2 = ctx_alloc<double>(ctx, ctx->nt);
-  M->sigma = ctx_alloc<double>(ctx, nsys);
+  M->sigma = ctx_alloc<double>(ctx, 2 * nsys);  // sigma per system, then 1 / sigma
   std::vector<long> tb(nsys + 1);
   for (int k = 0; k < nsys; k++) tb[k] = ctx->sys[k].t_begin;
   tb[nsys] = ctx->nt;
@@ -623,6 +626,11 @@ static void mlp_features(pnm_ctx* ctx) {
     fs[k].N = S.N;
     fs[k].kscale = (2.0 * PNM_PI / S.L) / kF;
     fs[k].epsF = ctx->hbar2_2m * kF * kF;
+    fs[k].inv_epsF = 1.0 / fs[k].epsF;
+    fs[k].v_scale = S.N / fs[k].epsF;
+    fs[k].f19 = (float)(S.rho / 0.16);
+    fs[k].f20 = (float)kF;
+    fs[k].f21 = (float)(S.N / 66.0);
   }
   long* dcnt = ctx_alloc<long>(ctx, nsys);
   FeatSys* dfs = ctx_alloc<FeatSys>(ctx, nsys);
@@ -630,7 +638,7 @@ static void mlp_features(pnm_ctx* ctx) {
   CUDA_TRY(cudaMemcpyAsync(dfs, fs.data(), sizeof(FeatSys) * nsys, cudaMemcpyHostToDevice, s));
   k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, parts);
   k_sigma<<<nsys, 256, 0, s>>>(parts, ctx->upd_lo_d, ctx->upd_hi_d, dcnt, M->sigma);
-  k_features<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, dfs, M->tm2, M->sigma, M->X);
+  k_features<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, dfs, M->tm2, M->sigma + nsys, M->X);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
 }

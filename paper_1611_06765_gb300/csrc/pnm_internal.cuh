@@ -195,15 +195,18 @@ __device__ __forceinline__ float* next_t32(const DevState& D, const LoopCtl* ctl
 // reduces to 1/2 (V_R + V_S)(1 - P_sigma) (the V_T term cancels), whose antisymmetrized
 // plane-wave element is 1/2 [Vt(n_p - n_r) + Vt(n_p - n_s)] times the spin factor
 // d(s_p,s_r) d(s_q,s_s) - d(s_p,s_s) d(s_q,s_r), with momentum conservation.
-// lut[m] = Vt at |dn|^2 = m for this system.
+// hlut[m] = Vt / 2 at |dn|^2 = m for this system, so the element is one FP64 addition and a
+// sign (bit for bit 0.5 (Vt_1 + Vt_2) sf: halving is exact); the FP64 unit of a GB300 runs
+// at about 1/64 of its FP32 rate, and the V blocks are generated element by element.
 __device__ __forceinline__ double v_minnesota_as(char4 p, char4 q, char4 r, char4 s,
-                                                 const double* __restrict__ lut) {
+                                                 const double* __restrict__ hlut) {
   if (p.x + q.x != r.x + s.x || p.y + q.y != r.y + s.y || p.z + q.z != r.z + s.z) return 0.0;
   int sf = (p.w == r.w && q.w == s.w) - (p.w == s.w && q.w == r.w);
   if (sf == 0) return 0.0;
   int m1 = dot3(p.x - r.x, p.y - r.y, p.z - r.z);
   int m2 = dot3(p.x - s.x, p.y - s.y, p.z - s.z);
-  return 0.5 * (lut[m1] + lut[m2]) * (double)sf;
+  double v = hlut[m1] + hlut[m2];
+  return sf > 0 ? v : __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
 }
 
 // Element offset inside a (rows x 64) BF16 plane stored as 8-row x 16-byte core matrices
@@ -212,10 +215,12 @@ __device__ __forceinline__ int tile_core_off(int r, int k) {
   return (((r >> 3) * 8 + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
 }
 
-// x = hi + lo with hi, lo in BF16 (hi = round(x), lo = round(x - hi)).
+// x = hi + lo with hi, lo in BF16: x is rounded to FP32 once (the only FP64 instruction),
+// hi = round(x), lo = round(x - hi) with the difference exact in FP32.
 __device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn((float)x);
-  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+  float xf = (float)x;
+  hi = __float2bfloat16_rn(xf);
+  lo = __float2bfloat16_rn(xf - __bfloat162float(hi));
 }
 
 template <typename T>

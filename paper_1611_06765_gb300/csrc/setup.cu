@@ -85,10 +85,15 @@ __global__ void k_basis_place(int n2max, int r, const int* __restrict__ start, c
     idx3[2 * c] = idx3[2 * c + 1] = -1;
     return;
   }
+  // same-shell points before (x, y, z) in lexicographic order
   int rank = 0;
-  for (int c2 = 0; c2 < c; c2++) {
-    int x2 = c2 / (w * w) - r, y2 = (c2 / w) % w - r, z2 = c2 % w - r;
-    rank += (dot3(x2, y2, z2) == n2);
+  for (int x2 = -r; x2 <= x; x2++) {
+    int ylim = x2 < x ? r : y;
+    for (int y2 = -r; y2 <= ylim; y2++) {
+      int zlim = (x2 < x || y2 < y) ? r : z - 1;
+      int rest = n2 - x2 * x2 - y2 * y2;
+      for (int z2 = -r; z2 <= zlim; z2++) rank += (z2 * z2 == rest);
+    }
   }
   int slot = start[n2] + rank;
   nvec[2 * slot] = make_char4((char)x, (char)y, (char)z, (char)-1);
@@ -97,15 +102,17 @@ __global__ void k_basis_place(int n2max, int r, const int* __restrict__ start, c
   idx3[2 * c + 1] = 2 * slot + 1;
 }
 
-// lut[m] = sum_{a=R,S} (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)).
-__global__ void k_lut(double* __restrict__ lut, int len, double L, double VR, double kR,
+// hlut[m] = 1/2 sum_{a=R,S} (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)),
+// the half of Vt that the antisymmetrized element adds twice (exact scaling by 1/2).
+__global__ void k_lut(double* __restrict__ hlut, int len, double L, double VR, double kR,
                       double VS, double kS) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= len) return;
   double L3 = L * L * L;
   double q2 = (2.0 * PNM_PI / L) * (2.0 * PNM_PI / L) * (double)m;
-  lut[m] = VR / L3 * pow(PNM_PI / kR, 1.5) * exp(-q2 / (4.0 * kR)) +
-           VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS));
+  double vt = VR / L3 * pow(PNM_PI / kR, 1.5) * exp(-q2 / (4.0 * kR)) +
+              VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS));
+  hlut[m] = 0.5 * vt;
 }
 
 // ------------------------------------------------------------------ twisted boundaries
