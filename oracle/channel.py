@@ -20,6 +20,10 @@ def lib():
         vp = C.c_void_p
         L.om_create.restype = vp
         L.om_create.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.om_create_matter.restype = vp
+        L.om_create_matter.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.om_isospin.argtypes = [vp, vp]
         L.om_create_twisted.restype = vp
         L.om_create_twisted.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_int)]
@@ -68,23 +72,26 @@ def _ptr(a):
 class OracleSystem:
     """One (N, rho, n2max) pure-neutron-matter system in the C oracle."""
 
-    def __init__(self, N, rho, n2max, params, theta=None):
-        """params: (V_R, kappa_R, V_T, kappa_T, V_S, kappa_S, hbar^2/2m); theta: twist angles
-        (radians, one per axis) or None for periodic boundary conditions."""
+    def __init__(self, N, rho, n2max, params, theta=None, Z=0):
+        """N neutrons and Z protons (Z = 0: pure neutron matter; N = Z: symmetric nuclear
+        matter; N = 0: pure proton matter) at total density rho.  params: (V_R, kappa_R, V_T,
+        kappa_T, V_S, kappa_S, hbar^2/2m); theta: twist angles (radians, one per axis) or None
+        for periodic boundary conditions."""
         L = lib()
         p = (C.c_double * 7)(*[float(x) for x in params])
         err = C.c_int(0)
-        if theta is None:
+        th = None if theta is None else (C.c_double * 3)(*[float(x) for x in theta])
+        if Z == 0 and theta is None:
             h = L.om_create(int(N), float(rho), int(n2max), p, C.byref(err))
         else:
-            th = (C.c_double * 3)(*[float(x) for x in theta])
-            h = L.om_create_twisted(int(N), float(rho), int(n2max), p, th, C.byref(err))
+            h = L.om_create_matter(int(N), int(Z), float(rho), int(n2max), p, th, C.byref(err))
         if not h:
             raise ValueError("oracle: invalid system (N=%d is not a closed shell of n2max=%d "
                              "at twist %s?)" % (N, n2max, theta))
         self.theta = None if theta is None else tuple(float(x) for x in theta)
         self._h = C.c_void_p(h)
-        self.N, self.rho, self.n2max = int(N), float(rho), int(n2max)
+        self.N, self.rho, self.n2max = int(N) + int(Z), float(rho), int(n2max)
+        self.Z = int(Z)
         self.nsp = L.om_nsp(self._h)
         self.L = L.om_L(self._h)
 
@@ -96,9 +103,15 @@ class OracleSystem:
 
     # ---- basis and one-body
     def states(self):
+        """(nx, ny, nz, s) per state, and a fifth column t (+1 neutron, -1 proton) when the
+        system holds protons."""
         out = np.zeros((self.nsp, 4), dtype=np.int32)
         lib().om_states(self._h, _ptr(out))
-        return out
+        if self.Z == 0:
+            return out
+        t = np.zeros(self.nsp, dtype=np.int32)
+        lib().om_isospin(self._h, _ptr(t))
+        return np.concatenate([out, t[:, None]], axis=1)
 
     def energies(self):
         ekin = np.zeros(self.nsp)

@@ -24,6 +24,9 @@
  *   truncations  Eq. (ccd1) (pp ladder only) and Eq. (ccd2) (pp and hh ladders) of Sec.
  *                "Coupled cluster theory", and the terms of Eq. (ccd3) linear in t.
  *   MBPT3        diagrams (3), (4), (5) of Fig. goldstone, Eqs. (diag3)-(diag5).
+ *   nuclear      protons and neutrons (Sec. "Infinite nuclear matter"): the full Minnesota
+ *   matter       operator in the 16-dimensional two-nucleon spin-isospin space, V_T active for
+ *                np pairs, channels keyed by (P, S_z, T_z).
  *
  * Readings of the paper taken here (each one is listed with its evidence in the design notes):
  *   - Minnesota signs: V_R = +200 MeV, V_T = -178 MeV, V_S = -91.85 MeV (the table prints
@@ -62,13 +65,15 @@ typedef struct {
 } om_minnesota;
 
 typedef struct om_sys {
-    int N, nsp, n2max, m, M;
+    int N, nsp, n2max, m, M;         /* N: particles (holes) of every species together */
     double rho, L;
     double phi[3];                   /* twist theta / (2 pi) per axis; 0 = periodic */
     om_minnesota P;
-    int *nx, *ny, *nz, *sz;          /* sz in units of hbar/2: -1 or +1 */
+    int species;                     /* 1 neutrons, 2 protons, 3 both (nuclear matter) */
+    int nq;                          /* charge slots of a channel key: 3 (S_z) or 9 (S_z, T_z) */
+    int *nx, *ny, *nz, *sz, *tz;     /* sz, tz in units of 1/2: -1 or +1 (tz +1 neutron) */
     double *ekin, *eps;              /* kinetic and HF single-particle energies */
-    double Ospin[3][4][4];           /* spin/isospin operators of the R, T, S terms */
+    double Ospin[3][16][16];         /* spin-isospin operators of the R, T, S terms */
 
     /* direct channels: those with both restricted hh and pp pairs */
     int nch;
@@ -104,24 +109,29 @@ static int isqrt_floor(int x) {
     return r;
 }
 
-/* Shell-ordered enumeration of plane-wave states with n^2 <= n2max. */
+/* Shell-ordered enumeration of plane-wave states with n^2 <= n2max; per momentum s = -1
+ * then +1 and, within a spin, the species present (proton t = -1 before neutron t = +1). */
 static int build_basis(om_sys *S) {
     int r = isqrt_floor(S->n2max);
-    int cap = 2 * (2 * r + 1) * (2 * r + 1) * (2 * r + 1);
+    int cap = 4 * (2 * r + 1) * (2 * r + 1) * (2 * r + 1);
     S->nx = malloc(sizeof(int) * cap);
     S->ny = malloc(sizeof(int) * cap);
     S->nz = malloc(sizeof(int) * cap);
     S->sz = malloc(sizeof(int) * cap);
+    S->tz = malloc(sizeof(int) * cap);
     int n = 0;
     for (int shell = 0; shell <= S->n2max; shell++)
         for (int x = -r; x <= r; x++)
             for (int y = -r; y <= r; y++)
                 for (int z = -r; z <= r; z++)
                     for (int s = -1; s <= 1; s += 2)
-                        if (x * x + y * y + z * z == shell) {
-                            S->nx[n] = x; S->ny[n] = y; S->nz[n] = z; S->sz[n] = s;
-                            n++;
-                        }
+                        for (int t = -1; t <= 1; t += 2)
+                            if (x * x + y * y + z * z == shell &&
+                                (S->species & (t > 0 ? 1 : 2))) {
+                                S->nx[n] = x; S->ny[n] = y; S->nz[n] = z; S->sz[n] = s;
+                                S->tz[n] = t;
+                                n++;
+                            }
     S->nsp = n;
     return n;
 }
@@ -148,20 +158,20 @@ static int rank_cmp(const void *x, const void *y) {
 
 /* Stable reorder of the shell-ordered states by |n + phi|^2; returns the sorted keys. */
 static double *order_by_energy(om_sys *S) {
-    int n = S->nsp;
+    size_t n = S->nsp > 0 ? (size_t)S->nsp : 1;
     om_rank *r = malloc(sizeof(om_rank) * n);
-    for (int p = 0; p < n; p++) { r[p].key = twisted_n2(S, p); r[p].idx = p; }
+    for (int p = 0; p < (int)n; p++) { r[p].key = twisted_n2(S, p); r[p].idx = p; }
     qsort(r, n, sizeof(om_rank), rank_cmp);
-    int *tmp = malloc(sizeof(int) * 4 * n);
-    for (int p = 0; p < n; p++) {
+    int *tmp = malloc(sizeof(int) * 5 * n);
+    for (int p = 0; p < (int)n; p++) {
         int q = r[p].idx;
-        tmp[4 * p] = S->nx[q]; tmp[4 * p + 1] = S->ny[q];
-        tmp[4 * p + 2] = S->nz[q]; tmp[4 * p + 3] = S->sz[q];
+        tmp[5 * p] = S->nx[q]; tmp[5 * p + 1] = S->ny[q];
+        tmp[5 * p + 2] = S->nz[q]; tmp[5 * p + 3] = S->sz[q]; tmp[5 * p + 4] = S->tz[q];
     }
     double *key = malloc(sizeof(double) * n);
-    for (int p = 0; p < n; p++) {
-        S->nx[p] = tmp[4 * p]; S->ny[p] = tmp[4 * p + 1];
-        S->nz[p] = tmp[4 * p + 2]; S->sz[p] = tmp[4 * p + 3];
+    for (int p = 0; p < (int)n; p++) {
+        S->nx[p] = tmp[5 * p]; S->ny[p] = tmp[5 * p + 1];
+        S->nz[p] = tmp[5 * p + 2]; S->sz[p] = tmp[5 * p + 3]; S->tz[p] = tmp[5 * p + 4];
         key[p] = r[p].key;
     }
     free(tmp);
@@ -171,50 +181,53 @@ static double *order_by_energy(om_sys *S) {
 
 /* ------------------------------------------------------------- Minnesota force */
 
-/* Two-particle spin space, index 2*u1 + u2 with u = (s+1)/2.  For two neutrons the
- * isospin exchange operator is the identity.  The operators multiplying the three
+/* Two-particle spin-isospin space: one particle's label l = 2u + w with u = (s+1)/2 and
+ * w = (t+1)/2; the pair's index is 4 l1 + l2.  The exchange operators swap the spin labels
+ * (P_s) or the isospin labels (P_t) of the two particles.  The operators multiplying the three
  * radial Gaussians are, from V(r) = 1/2 (V_R + 1/2(1+Ps) V_T + 1/2(1-Ps) V_S)(1 - Ps Pt):
- *   O_R = 1/2 (1 - Ps Pt),  O_T = 1/4 (1 + Ps)(1 - Ps Pt),  O_S = 1/4 (1 - Ps)(1 - Ps Pt). */
-static void build_spin_ops(om_sys *S) {
-    double I[4][4] = {{0}}, Ps[4][4] = {{0}}, Pt[4][4] = {{0}};
-    for (int u1 = 0; u1 < 2; u1++)
-        for (int u2 = 0; u2 < 2; u2++) {
-            int ket = 2 * u1 + u2, swapped = 2 * u2 + u1;
-            I[ket][ket] = 1.0;
-            Ps[swapped][ket] = 1.0;   /* Ps |s1 s2> = |s2 s1> */
-            Pt[ket][ket] = 1.0;       /* two neutrons: isospin exchange is +1 */
-        }
-    double PsPt[4][4], X[4][4];
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) {
+ *   O_R = 1/2 (1 - Ps Pt),  O_T = 1/4 (1 + Ps)(1 - Ps Pt),  O_S = 1/4 (1 - Ps)(1 - Ps Pt).
+ * For two neutrons P_t = 1 on every pair state, and O_T vanishes. */
+#define OM_SD 16
+static void matmul16(double A[OM_SD][OM_SD], double B[OM_SD][OM_SD], double C[OM_SD][OM_SD]) {
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) {
             double acc = 0;
-            for (int k = 0; k < 4; k++) acc += Ps[i][k] * Pt[k][j];
-            PsPt[i][j] = acc;
-        }
-    double A[4][4];  /* (1 - Ps Pt) */
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) A[i][j] = I[i][j] - PsPt[i][j];
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) S->Ospin[0][i][j] = 0.5 * A[i][j];
-    /* O_T */
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) X[i][j] = 0.5 * (I[i][j] + Ps[i][j]);
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) {
-            double acc = 0;
-            for (int k = 0; k < 4; k++) acc += X[i][k] * A[k][j];
-            S->Ospin[1][i][j] = 0.5 * acc;
-        }
-    /* O_S */
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) X[i][j] = 0.5 * (I[i][j] - Ps[i][j]);
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) {
-            double acc = 0;
-            for (int k = 0; k < 4; k++) acc += X[i][k] * A[k][j];
-            S->Ospin[2][i][j] = 0.5 * acc;
+            for (int k = 0; k < OM_SD; k++) acc += A[i][k] * B[k][j];
+            C[i][j] = acc;
         }
 }
+
+static void build_spin_ops(om_sys *S) {
+    static double I[OM_SD][OM_SD], Ps[OM_SD][OM_SD], Pt[OM_SD][OM_SD];
+    memset(I, 0, sizeof(I)); memset(Ps, 0, sizeof(Ps)); memset(Pt, 0, sizeof(Pt));
+    for (int u1 = 0; u1 < 2; u1++)
+        for (int w1 = 0; w1 < 2; w1++)
+            for (int u2 = 0; u2 < 2; u2++)
+                for (int w2 = 0; w2 < 2; w2++) {
+                    int ket = 4 * (2 * u1 + w1) + (2 * u2 + w2);
+                    I[ket][ket] = 1.0;
+                    Ps[4 * (2 * u2 + w1) + (2 * u1 + w2)][ket] = 1.0;  /* |u2 w1, u1 w2> */
+                    Pt[4 * (2 * u1 + w2) + (2 * u2 + w1)][ket] = 1.0;  /* |u1 w2, u2 w1> */
+                }
+    double PsPt[OM_SD][OM_SD], A[OM_SD][OM_SD], X[OM_SD][OM_SD], Y[OM_SD][OM_SD];
+    matmul16(Ps, Pt, PsPt);
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) A[i][j] = I[i][j] - PsPt[i][j];   /* 1 - Ps Pt */
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) S->Ospin[0][i][j] = 0.5 * A[i][j];
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) X[i][j] = 0.5 * (I[i][j] + Ps[i][j]);
+    matmul16(X, A, Y);
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) S->Ospin[1][i][j] = 0.5 * Y[i][j];
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) X[i][j] = 0.5 * (I[i][j] - Ps[i][j]);
+    matmul16(X, A, Y);
+    for (int i = 0; i < OM_SD; i++)
+        for (int j = 0; j < OM_SD; j++) S->Ospin[2][i][j] = 0.5 * Y[i][j];
+}
+
+static int label(const om_sys *S, int p) { return 2 * ((S->sz[p] + 1) / 2) + (S->tz[p] + 1) / 2; }
 
 /* Momentum-space Gaussian: (V_a / L^3) (pi / kappa)^{3/2} exp(-q^2 / (4 kappa)). */
 static double gauss_ft(const om_sys *S, double V, double kappa, double q2) {
@@ -227,8 +240,8 @@ static double v_direct(const om_sys *S, int p, int q, int r, int s) {
     if (S->nx[p] + S->nx[q] != S->nx[r] + S->nx[s]) return 0.0;
     if (S->ny[p] + S->ny[q] != S->ny[r] + S->ny[s]) return 0.0;
     if (S->nz[p] + S->nz[q] != S->nz[r] + S->nz[s]) return 0.0;
-    int bra = 2 * ((S->sz[p] + 1) / 2) + (S->sz[q] + 1) / 2;
-    int ket = 2 * ((S->sz[r] + 1) / 2) + (S->sz[s] + 1) / 2;
+    int bra = 4 * label(S, p) + label(S, q);
+    int ket = 4 * label(S, r) + label(S, s);
     double oR = S->Ospin[0][bra][ket], oT = S->Ospin[1][bra][ket], oS = S->Ospin[2][bra][ket];
     if (oR == 0.0 && oT == 0.0 && oS == 0.0) return 0.0;
     /* relative-momentum transfer q = 1/2 (k_p - k_q - k_r + k_s), k = 2 pi n / L */
@@ -251,24 +264,27 @@ double om_v(const om_sys *S, int p, int q, int r, int s) {
 
 /* ------------------------------------------------------------------- channels */
 
-static int chan_key(const om_sys *S, int Px, int Py, int Pz, int Sz) {
+/* Pure neutron matter: ((Px+m)M + Py+m)M + Pz+m, times 3 plus (Sz+2)/2.  With protons the
+ * charge slot is 3 (Sz+2)/2 + (Tz+2)/2 of 9. */
+static int chan_key(const om_sys *S, int Px, int Py, int Pz, int Sz, int Tz) {
     int m = S->m, M = S->M;
-    return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * 3 + (Sz + 2) / 2;
+    int slot = S->nq == 3 ? (Sz + 2) / 2 : 3 * ((Sz + 2) / 2) + (Tz + 2) / 2;
+    return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * S->nq + slot;
 }
 
 static int dir_key(const om_sys *S, int p, int q) {
     return chan_key(S, S->nx[p] + S->nx[q], S->ny[p] + S->ny[q], S->nz[p] + S->nz[q],
-                    S->sz[p] + S->sz[q]);
+                    S->sz[p] + S->sz[q], S->tz[p] + S->tz[q]);
 }
 
 static int cross_key(const om_sys *S, int p, int q) {
     return chan_key(S, S->nx[p] - S->nx[q], S->ny[p] - S->ny[q], S->nz[p] - S->nz[q],
-                    S->sz[p] - S->sz[q]);
+                    S->sz[p] - S->sz[q], S->tz[p] - S->tz[q]);
 }
 
 static void build_direct_channels(om_sys *S) {
     int N = S->N, n = S->nsp;
-    int nkeys = S->M * S->M * S->M * 3;
+    int nkeys = S->M * S->M * S->M * S->nq;
     int *cnt_hh = calloc(nkeys, sizeof(int)), *cnt_pp = calloc(nkeys, sizeof(int));
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++) cnt_hh[dir_key(S, i, j)]++;
@@ -343,7 +359,7 @@ static void build_direct_channels(om_sys *S) {
 
 static void build_cross_channels(om_sys *S) {
     int N = S->N, n = S->nsp;
-    int nkeys = S->M * S->M * S->M * 3;
+    int nkeys = S->M * S->M * S->M * S->nq;
     int *cnt_ph = calloc(nkeys, sizeof(int)), *cnt_hp = calloc(nkeys, sizeof(int));
     for (int a = N; a < n; a++)
         for (int i = 0; i < N; i++) cnt_ph[cross_key(S, a, i)]++;
@@ -423,7 +439,7 @@ static void build_cross_channels(om_sys *S) {
 
 void om_destroy(om_sys *S) {
     if (!S) return;
-    void *ptrs[] = {S->nx, S->ny, S->nz, S->sz, S->ekin, S->eps, S->chkey, S->nhh, S->npp,
+    void *ptrs[] = {S->nx, S->ny, S->nz, S->sz, S->tz, S->ekin, S->eps, S->chkey, S->nhh, S->npp,
                     S->hh_off, S->pp_off, S->hh_p, S->hh_q, S->pp_p, S->pp_q, S->t_off,
                     S->vpp_off, S->vhh_off, S->pair_ch, S->pair_pos, S->xkey, S->nph, S->nhp,
                     S->ph_off, S->hp_off, S->ph_a, S->ph_i, S->hp_k, S->hp_c, S->xt_off,
@@ -433,14 +449,21 @@ void om_destroy(om_sys *S) {
     free(S);
 }
 
-/* Error codes: 0 ok, -1 invalid argument (N not a closed shell, no particle states).
+/* Error codes: 0 ok, -1 invalid argument (not a closed shell, no particle states, or an
+ * unsupported composition).  Nn neutrons and Z protons: Z = 0 pure neutron matter, Nn = 0
+ * pure proton matter, Nn = Z symmetric nuclear matter (Sec. "Infinite nuclear matter": the
+ * channel index then carries T_z); rho is the total density (Nn + Z) / L^3.
  * theta3: twist angles (radians) per axis, NULL for periodic boundary conditions. */
-om_sys *om_create_twisted(int N, double rho, int n2max, const double *params7,
-                          const double *theta3, int *err) {
+om_sys *om_create_matter(int Nn, int Z, double rho, int n2max, const double *params7,
+                         const double *theta3, int *err) {
     *err = -1;
-    if (N <= 0 || rho <= 0.0 || n2max < 0) return NULL;
+    int N = Nn + Z;
+    if (Nn < 0 || Z < 0 || N <= 0 || rho <= 0.0 || n2max < 0) return NULL;
+    if (Nn > 0 && Z > 0 && Nn != Z) return NULL;
     om_sys *S = calloc(1, sizeof(om_sys));
     S->N = N; S->rho = rho; S->n2max = n2max;
+    S->species = (Nn > 0 ? 1 : 0) | (Z > 0 ? 2 : 0);
+    S->nq = S->species == 1 ? 3 : 9;
     S->P.VR = params7[0]; S->P.kR = params7[1];
     S->P.VT = params7[2]; S->P.kT = params7[3];
     S->P.VS = params7[4]; S->P.kS = params7[5];
@@ -473,6 +496,11 @@ om_sys *om_create_twisted(int N, double rho, int n2max, const double *params7,
     return S;
 }
 
+om_sys *om_create_twisted(int N, double rho, int n2max, const double *params7,
+                          const double *theta3, int *err) {
+    return om_create_matter(N, 0, rho, n2max, params7, theta3, err);
+}
+
 om_sys *om_create(int N, double rho, int n2max, const double *params7, int *err) {
     return om_create_twisted(N, rho, n2max, params7, NULL, err);
 }
@@ -492,6 +520,11 @@ void om_states(const om_sys *S, int *out4) {
         out4[4 * p + 2] = S->nz[p];
         out4[4 * p + 3] = S->sz[p];
     }
+}
+
+/* Isospin projection per state (+1 neutron, -1 proton). */
+void om_isospin(const om_sys *S, int *out) {
+    for (int p = 0; p < S->nsp; p++) out[p] = S->tz[p];
 }
 
 void om_energies(const om_sys *S, double *ekin, double *eps) {
