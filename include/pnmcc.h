@@ -120,6 +120,20 @@ int pnm_create_twisted(int n, const int *N, const double *rho, const int *n2max,
                        const double *theta, const pnm_minnesota *params, void *stream,
                        pnm_ctx **out);
 
+/* Nuclear matter (Sec. "Infinite nuclear matter"): as pnm_create_twisted, with system k made
+ * of N[k] neutrons and Z[k] protons: Z = 0 pure neutron matter, N = 0 pure proton matter,
+ * N = Z symmetric nuclear matter (other compositions: PNM_EINVAL).  rho[k] is the total density
+ * (N + Z) / L^3 and n2max[k] the lattice bound; Z = NULL means no protons anywhere.  With
+ * protons every momentum carries four states (s = -1 then +1, within a spin the proton before
+ * the neutron; t = +1 neutron, -1 proton), the full Minnesota operator acts (the V_T term
+ * couples np pairs), and channel keys carry T_z: slot 3 (S_z + 2)/2 + (T_z + 2)/2 of 9 in
+ * place of (S_z + 2)/2 of 3.  pnm_basis then reports the fourth component of a state as
+ * s + 4t.  theta: as pnm_create_twisted (NULL: periodic).  Arrays have n entries, host
+ * memory read during the call. */
+int pnm_create_matter(int n, const int *N, const int *Z, const double *rho, const int *n2max,
+                      const double *theta, const pnm_minnesota *params, void *stream,
+                      pnm_ctx **out);
+
 /* Product Gauss-Legendre twist mesh of the twist-averaging loop (Sec. "Twist-averaged
  * boundary conditions"): nx, ny, nz nodes (1..64) on [0, pi] per axis, points in x-major
  * order (m = (i ny + j) nz + k).  theta: 3 nx ny nz doubles (radians); weight: nx ny nz

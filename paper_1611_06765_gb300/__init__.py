@@ -30,15 +30,17 @@ def _ptr(a):
 class Context:
     """One or more (N, rho, n2max) systems built on the GPU by ``pnm_create_batch``."""
 
-    def __init__(self, N, rho, n2max, params=MINNESOTA, stream=None, theta=None):
-        """theta: twist angles, shape (3,) or (n, 3) radians (``pnm_create_twisted``); None
-        for periodic boundaries."""
+    def __init__(self, N, rho, n2max, params=MINNESOTA, stream=None, theta=None, Z=None):
+        """N neutrons (per system).  theta: twist angles, shape (3,) or (n, 3) radians
+        (``pnm_create_twisted``); None for periodic boundaries.  Z: protons per system
+        (``pnm_create_matter``: 0, or equal to N, or with N = 0); None for neutron matter."""
         L = _lib.load()
         Ns = np.atleast_1d(np.asarray(N, dtype=np.int32))
         rhos = np.atleast_1d(np.asarray(rho, dtype=np.float64))
         n2 = np.atleast_1d(np.asarray(n2max, dtype=np.int32))
         th = None if theta is None else np.atleast_2d(np.asarray(theta, dtype=np.float64))
-        n = max(len(Ns), len(rhos), len(n2), 0 if th is None else len(th))
+        Zs = None if Z is None else np.atleast_1d(np.asarray(Z, dtype=np.int32))
+        n = max(len(Ns), len(rhos), len(n2), 0 if th is None else len(th), 0 if Zs is None else len(Zs))
         Ns, rhos, n2 = (np.ascontiguousarray(np.broadcast_to(a, (n,))) for a in (Ns, rhos, n2))
         self.N, self.rho, self.n2max = Ns.copy(), rhos.copy(), n2.copy()
         p = _lib.pnm_minnesota(*[float(x) for x in params])
@@ -46,7 +48,16 @@ class Context:
         args = (Ns.ctypes.data_as(C.POINTER(C.c_int)), rhos.ctypes.data_as(C.POINTER(C.c_double)),
                 n2.ctypes.data_as(C.POINTER(C.c_int)))
         st = C.c_void_p(stream) if stream else None
-        if th is None:
+        self.Z = np.zeros(n, np.int32)
+        if Zs is not None:
+            Zs = np.ascontiguousarray(np.broadcast_to(Zs, (n,)))
+            self.Z = Zs.copy()
+            self.theta = None if th is None else np.ascontiguousarray(np.broadcast_to(th, (n, 3))).copy()
+            thp = None if th is None else self.theta.ctypes.data_as(C.POINTER(C.c_double))
+            _lib.check(L.pnm_create_matter(n, args[0], Zs.ctypes.data_as(C.POINTER(C.c_int)), args[1], args[2],
+                                           thp, C.byref(p), st, C.byref(h)))
+            self.N = self.N + self.Z
+        elif th is None:
             self.theta = None
             _lib.check(L.pnm_create_batch(n, *args, C.byref(p), st, C.byref(h)))
         else:

@@ -31,7 +31,8 @@ PNM_TERMS_LINEAR = 3
 
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
-    "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_twist_mesh",
+    "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_create_matter",
+    "pnm_twist_mesh",
     "pnm_destroy", "pnm_num_systems",
     "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc", "pnm_mbpt3",
     "pnm_ccd_solve",
@@ -82,6 +83,8 @@ def load(path=None):
     L.pnm_create_twisted.argtypes = [C.c_int, ip, dp, ip, dp, C.POINTER(pnm_minnesota), vp,
                                      C.POINTER(vp)]
     L.pnm_twist_mesh.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+    L.pnm_create_matter.argtypes = [C.c_int, ip, ip, dp, ip, dp, C.POINTER(pnm_minnesota), vp,
+                                    C.POINTER(vp)]
     L.pnm_destroy.argtypes = [vp]
     L.pnm_num_systems.argtypes = [vp, ip]
     L.pnm_basis.argtypes = [vp, C.c_int, ip, ip, vp, vp]

@@ -115,9 +115,9 @@ void pnm_default_opts(pnm_solve_opts* o) {
 
 const char* pnm_last_error(void) { return g_last_error.c_str(); }
 
-int pnm_create_twisted(int n, const int* N, const double* rho, const int* n2max,
-                       const double* theta, const pnm_minnesota* params, void* stream,
-                       pnm_ctx** out) {
+int pnm_create_matter(int n, const int* N, const int* Z, const double* rho, const int* n2max,
+                      const double* theta, const pnm_minnesota* params, void* stream,
+                      pnm_ctx** out) {
   return guarded([&]() {
     if (!out || !N || !rho || !n2max || !params || n <= 0)
       throw PnmError{PNM_EINVAL, "null argument or empty batch"};
@@ -132,7 +132,7 @@ int pnm_create_twisted(int n, const int* N, const double* rho, const int* n2max,
       }
       for (auto& e : ctx->ev) CUDA_TRY(cudaEventCreate(&e));
       CUDA_TRY(cudaEventRecord(ctx->ev[2], ctx->stream));
-      pnm_build(ctx, n, N, rho, n2max, theta, *params);
+      pnm_build(ctx, n, N, Z, rho, n2max, theta, *params);
       pnm_prepare_iteration(ctx);
       pnm_eref_all(ctx);
       CUDA_TRY(cudaEventRecord(ctx->ev[3], ctx->stream));
@@ -149,9 +149,15 @@ int pnm_create_twisted(int n, const int* N, const double* rho, const int* n2max,
   });
 }
 
+int pnm_create_twisted(int n, const int* N, const double* rho, const int* n2max,
+                       const double* theta, const pnm_minnesota* params, void* stream,
+                       pnm_ctx** out) {
+  return pnm_create_matter(n, N, nullptr, rho, n2max, theta, params, stream, out);
+}
+
 int pnm_create_batch(int n, const int* N, const double* rho, const int* n2max,
                      const pnm_minnesota* params, void* stream, pnm_ctx** out) {
-  return pnm_create_twisted(n, N, rho, n2max, nullptr, params, stream, out);
+  return pnm_create_matter(n, N, nullptr, rho, n2max, nullptr, params, stream, out);
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_n from the Chebyshev-like
@@ -314,8 +320,14 @@ int pnm_channels(const pnm_ctx* ctx, int sys, int kind, int* n_chan, int* n_pair
         for (int x = x0; x < x1; x++) {
           int2 pr = ph[ctx->h_x_ph_off[x] - ctx->h_x_ph_off[x0]];
           char4 a = nv[pr.x - S.sp_off], i = nv[pr.y - S.sp_off];
-          keys[x - x0] = (((a.x - i.x + S.m) * S.M + (a.y - i.y + S.m)) * S.M + (a.z - i.z + S.m)) * 3 +
-                         (a.w - i.w + 2) / 2;
+          int dw = a.w - i.w, slot, nq = S.species == 1 ? 3 : 9;
+          if (S.species == 1) {
+            slot = (dw + 2) / 2;
+          } else {  // dw = (s_a - s_i) + 4 (t_a - t_i)
+            int dt = dw >= 6 ? 2 : (dw <= -6 ? -2 : 0);
+            slot = 3 * ((dw - 4 * dt + 2) / 2) + (dt + 2) / 2;
+          }
+          keys[x - x0] = (((a.x - i.x + S.m) * S.M + (a.y - i.y + S.m)) * S.M + (a.z - i.z + S.m)) * nq + slot;
         }
       }
       if (sizes)

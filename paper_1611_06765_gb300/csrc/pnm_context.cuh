@@ -109,8 +109,8 @@ template <typename T>
 T* ctx_alloc(pnm_ctx* ctx, size_t n) {
   return (T*)pnm_ctx_alloc(ctx, (n ? n : 1) * sizeof(T));
 }
-void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
-               const double* thetas, const pnm_minnesota& P);
+void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const double* rhos,
+               const int* n2maxs, const double* thetas, const pnm_minnesota& P);
 void pnm_prepare_iteration(pnm_ctx* ctx);
 void pnm_eref_all(pnm_ctx* ctx);
 void pnm_mbpt2_all(pnm_ctx* ctx, double* out);

@@ -39,7 +39,9 @@ void pnm_set_error(int code, const std::string& msg);
 
 // One system (N, rho, n2max) of a context.
 struct SysInfo {
-  int N, n2max, r, m, M, nkeys;
+  int N, n2max, r, m, M, nkeys;  // N: particles (holes) of all species
+  int Z = 0;                     // protons among them
+  int species = 1;               // 1 neutrons, 2 protons, 3 both
   double rho, L;
   int nsp, sp_off;        // states [sp_off, sp_off + nsp)
   int ch_begin, ch_end;   // direct channels
@@ -191,16 +193,45 @@ __device__ __forceinline__ float* next_t32(const DevState& D, const LoopCtl* ctl
   return (ctl->iter & 1) ? D.t32_0 : D.t32_1;
 }
 
-// Antisymmetrized Minnesota element for two neutrons.  With P_tau = 1 the exchange form
-// reduces to 1/2 (V_R + V_S)(1 - P_sigma) (the V_T term cancels), whose antisymmetrized
-// plane-wave element is 1/2 [Vt(n_p - n_r) + Vt(n_p - n_s)] times the spin factor
-// d(s_p,s_r) d(s_q,s_s) - d(s_p,s_s) d(s_q,s_r), with momentum conservation.
+// Antisymmetrized Minnesota element with protons present.  The charge label w = s + 4t
+// (t = +1 neutron, -1 proton) carries spin and isospin.  From V = 1/2 (V_R + 1/2(1+P_s) V_T +
+// 1/2(1-P_s) V_S)(1 - P_s P_t), with the product-basis structures of the ket (r, s)
+//   one = d(s_p,s_r) d(s_q,s_s) d(t_p,t_r) d(t_q,t_s), ps: spins of r and s exchanged,
+//   pt: isospins exchanged, pst: both,
+// the direct operator weights are 4 O_R = 2(one - pst), 4 O_T = one + ps - pt - pst and
+// 4 O_S = one - ps + pt - pst; the exchange term (r <-> s) carries the opposite weights, so the
+// antisymmetrized element is 1/4 sum_a (4 O_a) [Vt_a(n_p - n_r) + Vt_a(n_p - n_s)].
+// hlut3[3m + a] = Vt_a / 2 at |dn|^2 = m.
+__device__ __forceinline__ double v_minnesota_nucleons(char4 p, char4 q, char4 r, char4 s,
+                                                       const double* __restrict__ hlut3) {
+  auto tz = [](int w) { return w > 0 ? 1 : -1; };
+  int tp = tz(p.w), tq = tz(q.w), tr = tz(r.w), ts = tz(s.w);
+  int sp = p.w - 4 * tp, sq = q.w - 4 * tq, sr = r.w - 4 * tr, ss = s.w - 4 * ts;
+  int one = (sp == sr && sq == ss && tp == tr && tq == ts);
+  int ps = (sp == ss && sq == sr && tp == tr && tq == ts);
+  int pt = (sp == sr && sq == ss && tp == ts && tq == tr);
+  int pst = (sp == ss && sq == sr && tp == ts && tq == tr);
+  int cR = 2 * (one - pst), cT = one + ps - pt - pst, cS = one - ps + pt - pst;
+  if (cR == 0 && cT == 0 && cS == 0) return 0.0;
+  int m1 = 3 * dot3(p.x - r.x, p.y - r.y, p.z - r.z);
+  int m2 = 3 * dot3(p.x - s.x, p.y - s.y, p.z - s.z);
+  double v = (double)cR * (hlut3[m1] + hlut3[m2]) + (double)cT * (hlut3[m1 + 1] + hlut3[m2 + 1]) +
+             (double)cS * (hlut3[m1 + 2] + hlut3[m2 + 2]);
+  return 0.5 * v;
+}
+
+// Antisymmetrized Minnesota element.  For two neutrons (charge labels w = s = +-1) P_tau = 1
+// and the exchange form reduces to 1/2 (V_R + V_S)(1 - P_sigma) (the V_T term cancels), whose
+// antisymmetrized plane-wave element is 1/2 [Vt(n_p - n_r) + Vt(n_p - n_s)] times the spin
+// factor d(s_p,s_r) d(s_q,s_s) - d(s_p,s_s) d(s_q,s_r), with momentum conservation.
 // hlut[m] = Vt / 2 at |dn|^2 = m for this system, so the element is one FP64 addition and a
 // sign (bit for bit 0.5 (Vt_1 + Vt_2) sf: halving is exact); the FP64 unit of a GB300 runs
 // at about 1/64 of its FP32 rate, and the V blocks are generated element by element.
+// Systems with protons (labels |w| >= 3) use v_minnesota_nucleons and its interleaved LUT.
 __device__ __forceinline__ double v_minnesota_as(char4 p, char4 q, char4 r, char4 s,
                                                  const double* __restrict__ hlut) {
   if (p.x + q.x != r.x + s.x || p.y + q.y != r.y + s.y || p.z + q.z != r.z + s.z) return 0.0;
+  if (p.w > 1 || p.w < -1) return v_minnesota_nucleons(p, q, r, s, hlut);
   int sf = (p.w == r.w && q.w == s.w) - (p.w == s.w && q.w == r.w);
   if (sf == 0) return 0.0;
   int m1 = dot3(p.x - r.x, p.y - r.y, p.z - r.z);

@@ -25,26 +25,56 @@ __device__ __forceinline__ int cube_index(int x, int y, int z, int r) {
   return ((x + r) * w + (y + r)) * w + (z + r);
 }
 
-// State index of (n, s) in a system, or -1.
-__device__ __forceinline__ int lookup_state(const int* __restrict__ idx3, int r, int x, int y,
-                                            int z, int s) {
-  int c = cube_index(x, y, z, r);
-  if (c < 0 || (s != -1 && s != 1)) return -1;
-  return idx3[2 * c + ((s + 1) >> 1)];
+// Charge label of a state (the .w of its char4): the spin s = +-1 in systems of neutrons only
+// (species 1); s + 4t (t = +1 neutron, -1 proton) in systems with protons (species 2: protons
+// only, 3: both), so that sums and differences of two labels decode uniquely into (S_z, T_z).
+// A channel key's charge slot is (S_z + 2)/2 of 3 (neutrons only) or 3 (S_z + 2)/2 +
+// (T_z + 2)/2 of 9.
+__device__ __forceinline__ int charge_slot(int wsum, int species) {
+  if (species == 1) return (wsum + 2) >> 1;
+  int tsum = wsum >= 6 ? 2 : (wsum <= -6 ? -2 : 0);
+  int ssum = wsum - 4 * tsum;
+  return 3 * ((ssum + 2) >> 1) + ((tsum + 2) >> 1);
 }
 
-__device__ __forceinline__ void decode_key(int K, int m, int M, int& Px, int& Py, int& Pz,
-                                           int& Sz) {
-  Sz = 2 * (K % 3) - 2;
-  int rest = K / 3;
+__device__ __forceinline__ int charge_sum(int slot, int species) {
+  if (species == 1) return 2 * slot - 2;
+  return (2 * (slot / 3) - 2) + 4 * (2 * (slot % 3) - 2);
+}
+
+__device__ __forceinline__ int charge_slots(int species) { return species == 1 ? 3 : 9; }
+
+// State index of (n, w) in a system, or -1.  A lattice point holds 2 states (one species) or
+// 4 (s = -1 then +1; within a spin the proton before the neutron).
+__device__ __forceinline__ int lookup_state(const int* __restrict__ idx3, int r, int x, int y,
+                                            int z, int w, int species) {
+  int c = cube_index(x, y, z, r);
+  if (c < 0) return -1;
+  int sp, slot;
+  if (species == 1) {
+    if (w != -1 && w != 1) return -1;
+    return idx3[2 * c + ((w + 1) >> 1)];
+  }
+  int t = (w == 3 || w == 5) ? 1 : ((w == -3 || w == -5) ? -1 : 0);
+  if (t == 0 || !(species & (t > 0 ? 1 : 2))) return -1;
+  sp = w - 4 * t;
+  slot = species == 3 ? 2 * ((sp + 1) >> 1) + ((t + 1) >> 1) : (sp + 1) >> 1;
+  return idx3[(species == 3 ? 4 : 2) * c + slot];
+}
+
+__device__ __forceinline__ void decode_key(int K, int m, int M, int species, int& Px, int& Py,
+                                           int& Pz, int& W) {
+  int nq = charge_slots(species);
+  W = charge_sum(K % nq, species);
+  int rest = K / nq;
   Pz = rest % M - m;
   rest /= M;
   Py = rest % M - m;
   Px = rest / M - m;
 }
 
-__device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int Sz, int m, int M) {
-  return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * 3 + (Sz + 2) / 2;
+__device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int W, int m, int M, int species) {
+  return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * charge_slots(species) + charge_slot(W, species);
 }
 
 // ---------------------------------------------------------------------------- basis
@@ -53,7 +83,7 @@ __device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int Sz, int m,
 // shell with a smaller cube index).  k_basis_count: one CTA counts the shells (shared-memory
 // atomics) and writes the shell starts; k_basis_place: one thread per cube point counts the
 // same-shell points before it and writes the two spin states.
-__global__ void k_basis_count(int n2max, int r, int* __restrict__ start, int* __restrict__ nsp_out) {
+__global__ void k_basis_count(int n2max, int r, int g, int* __restrict__ start, int* __restrict__ nsp_out) {
   extern __shared__ int cnt[];  // [n2max + 1]
   int w = 2 * r + 1, ncube = w * w * w;
   for (int k = threadIdx.x; k <= n2max; k += blockDim.x) cnt[k] = 0;
@@ -70,19 +100,20 @@ __global__ void k_basis_count(int n2max, int r, int* __restrict__ start, int* __
       start[k] = acc;
       acc += cnt[k];
     }
-    *nsp_out = 2 * acc;
+    *nsp_out = g * acc;
   }
 }
 
-__global__ void k_basis_place(int n2max, int r, const int* __restrict__ start, char4* __restrict__ nvec,
-                              int* __restrict__ idx3) {
+__global__ void k_basis_place(int n2max, int r, int species, const int* __restrict__ start,
+                              char4* __restrict__ nvec, int* __restrict__ idx3) {
   int w = 2 * r + 1, ncube = w * w * w;
+  int g = species == 3 ? 4 : 2;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncube) return;
   int x = c / (w * w) - r, y = (c / w) % w - r, z = c % w - r;
   int n2 = dot3(x, y, z);
   if (n2 > n2max) {
-    idx3[2 * c] = idx3[2 * c + 1] = -1;
+    for (int j = 0; j < g; j++) idx3[g * c + j] = -1;
     return;
   }
   // same-shell points before (x, y, z) in lexicographic order
@@ -96,10 +127,15 @@ __global__ void k_basis_place(int n2max, int r, const int* __restrict__ start, c
     }
   }
   int slot = start[n2] + rank;
-  nvec[2 * slot] = make_char4((char)x, (char)y, (char)z, (char)-1);
-  nvec[2 * slot + 1] = make_char4((char)x, (char)y, (char)z, (char)1);
-  idx3[2 * c] = 2 * slot;
-  idx3[2 * c + 1] = 2 * slot + 1;
+  int j = 0;
+  for (int sp = -1; sp <= 1; sp += 2)
+    for (int t = -1; t <= 1; t += 2) {
+      if (!(species & (t > 0 ? 1 : 2))) continue;
+      int lab = species == 1 ? sp : sp + 4 * t;
+      nvec[g * slot + j] = make_char4((char)x, (char)y, (char)z, (char)lab);
+      idx3[g * c + j] = g * slot + j;
+      j++;
+    }
 }
 
 // hlut[m] = 1/2 sum_{a=R,S} (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)),
@@ -113,6 +149,19 @@ __global__ void k_lut(double* __restrict__ hlut, int len, double L, double VR, d
   double vt = VR / L3 * pow(PNM_PI / kR, 1.5) * exp(-q2 / (4.0 * kR)) +
               VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS));
   hlut[m] = 0.5 * vt;
+}
+
+// With protons the three Gaussians carry different spin-isospin weights: hlut3[3m + a] =
+// 1/2 (V_a / L^3)(pi/kappa_a)^{3/2} exp(-(2 pi/L)^2 m / (4 kappa_a)) for a = R, T, S.
+__global__ void k_lut3(double* __restrict__ hlut3, int len, double L, double VR, double kR,
+                       double VT, double kT, double VS, double kS) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= len) return;
+  double L3 = L * L * L;
+  double q2 = (2.0 * PNM_PI / L) * (2.0 * PNM_PI / L) * (double)m;
+  hlut3[3 * m] = 0.5 * (VR / L3 * pow(PNM_PI / kR, 1.5) * exp(-q2 / (4.0 * kR)));
+  hlut3[3 * m + 1] = 0.5 * (VT / L3 * pow(PNM_PI / kT, 1.5) * exp(-q2 / (4.0 * kT)));
+  hlut3[3 * m + 2] = 0.5 * (VS / L3 * pow(PNM_PI / kS, 1.5) * exp(-q2 / (4.0 * kS)));
 }
 
 // ------------------------------------------------------------------ twisted boundaries
@@ -199,20 +248,20 @@ __global__ void k_eps(const char4* __restrict__ nvec, const double* __restrict__
 // ---------------------------------------------------------------------- channel counts
 // One warp per direct key: count restricted hh pairs (i<j<N) and pp pairs (N<=a<b).
 __global__ void k_count_direct(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                               int r, int m, int M, int nkeys, int N, int nsp,
+                               int r, int m, int M, int species, int nkeys, int N, int nsp,
                                int* __restrict__ cnt_hh, int* __restrict__ cnt_pp) {
   int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (K >= nkeys) return;
   int Px, Py, Pz, Sz;
-  decode_key(K, m, M, Px, Py, Pz, Sz);
+  decode_key(K, m, M, species, Px, Py, Pz, Sz);
   int nh = 0, np = 0;
   for (int p0 = 0; p0 < nsp; p0 += 32) {
     int p = p0 + lane;
     bool v = false;
     if (p < nsp) {
       char4 s = nvec[p];
-      int q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w);
+      int q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w, species);
       v = (q > p) && ((p < N) == (q < N));
       if (v && p < N) {
         nh++;
@@ -231,19 +280,19 @@ __global__ void k_count_direct(const char4* __restrict__ nvec, const int* __rest
 
 // One warp per cross key D: count ph rows (a >= N, i < N, n_a - n_i = D) and hp columns.
 __global__ void k_count_cross(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                              int r, int m, int M, int nkeys, int N, int nsp,
+                              int r, int m, int M, int species, int nkeys, int N, int nsp,
                               int* __restrict__ cnt_ph, int* __restrict__ cnt_hp) {
   int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (K >= nkeys) return;
   int Dx, Dy, Dz, Ds;
-  decode_key(K, m, M, Dx, Dy, Dz, Ds);
+  decode_key(K, m, M, species, Dx, Dy, Dz, Ds);
   int nph = 0, nhp = 0;
   for (int p0 = 0; p0 < nsp; p0 += 32) {
     int p = p0 + lane;
     if (p < nsp) {
       char4 s = nvec[p];
-      int q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds);
+      int q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds, species);
       if (q >= 0) {
         if (p >= N && q < N) nph++;
         if (p < N && q >= N) nhp++;
@@ -262,7 +311,7 @@ __global__ void k_count_cross(const char4* __restrict__ nvec, const int* __restr
 // One warp per direct channel.  Writes pairs (global state indices) in lexicographic order
 // and the pair -> position tables used by the index maps.
 __global__ void k_fill_direct(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                              int r, int m, int M, int N, int nsp, int sp_off, int nch_sys,
+                              int r, int m, int M, int species, int N, int nsp, int sp_off, int nch_sys,
                               const int* __restrict__ key, const int* __restrict__ hh_off,
                               const int* __restrict__ pp_off, int2* __restrict__ hh_pair,
                               int2* __restrict__ pp_pair, int* __restrict__ pos_hh,
@@ -271,7 +320,7 @@ __global__ void k_fill_direct(const char4* __restrict__ nvec, const int* __restr
   int lane = threadIdx.x & 31;
   if (c >= nch_sys) return;
   int Px, Py, Pz, Sz;
-  decode_key(key[c], m, M, Px, Py, Pz, Sz);
+  decode_key(key[c], m, M, species, Px, Py, Pz, Sz);
   int np = nsp - N;
   int nh_fill = 0, np_fill = 0;
   unsigned lt = (1u << lane) - 1u;
@@ -281,7 +330,7 @@ __global__ void k_fill_direct(const char4* __restrict__ nvec, const int* __restr
     bool vh = false, vp = false;
     if (p < nsp) {
       char4 s = nvec[p];
-      q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w);
+      q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w, species);
       bool v = (q > p) && ((p < N) == (q < N));
       vh = v && p < N;
       vp = v && p >= N;
@@ -305,7 +354,7 @@ __global__ void k_fill_direct(const char4* __restrict__ nvec, const int* __restr
 
 // One warp per cross channel: rows (a,i) and columns (k,c) in lexicographic order.
 __global__ void k_fill_cross(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                             int r, int m, int M, int N, int nsp, int sp_off, int nx_sys,
+                             int r, int m, int M, int species, int N, int nsp, int sp_off, int nx_sys,
                              const int* __restrict__ key, const int* __restrict__ ph_off,
                              const int* __restrict__ hp_off, int2* __restrict__ ph_pair,
                              int2* __restrict__ hp_pair, int* __restrict__ phpos,
@@ -314,7 +363,7 @@ __global__ void k_fill_cross(const char4* __restrict__ nvec, const int* __restri
   int lane = threadIdx.x & 31;
   if (x >= nx_sys) return;
   int Dx, Dy, Dz, Ds;
-  decode_key(key[x], m, M, Dx, Dy, Dz, Ds);
+  decode_key(key[x], m, M, species, Dx, Dy, Dz, Ds);
   int np = nsp - N;
   int f_ph = 0, f_hp = 0;
   unsigned lt = (1u << lane) - 1u;
@@ -324,7 +373,7 @@ __global__ void k_fill_cross(const char4* __restrict__ nvec, const int* __restri
     bool vph = false, vhp = false;
     if (p < nsp) {
       char4 s = nvec[p];
-      q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds);
+      q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds, species);
       vph = (q >= 0) && p >= N && q < N;
       vhp = (q >= 0) && p < N && q >= N;
     }
@@ -353,8 +402,8 @@ __global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restr
                        const long* __restrict__ x_t_off, const int* __restrict__ x_ph_off,
                        const int* __restrict__ x_hp_off, const int2* __restrict__ ph_pair,
                        const int2* __restrict__ hp_pair, const char4* __restrict__ nvec,
-                       int sp_off, int N, int nsp, int m, int M, const int* __restrict__ key2ch,
-                       int ch0, const long* __restrict__ ch_t_off,
+                       int sp_off, int N, int nsp, int m, int M, int species,
+                       const int* __restrict__ key2ch, int ch0, const long* __restrict__ ch_t_off,
                        const int* __restrict__ ch_npp, const int* __restrict__ pos_hh,
                        const int* __restrict__ pos_pp, int* __restrict__ xmap) {
   int x = x0 + blockIdx.x;
@@ -372,7 +421,7 @@ __global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restr
       if (p1 > p2) { int z = p1; p1 = p2; p2 = z; sgn = -sgn; }
       if (h1 > h2) { int z = h1; h1 = h2; h2 = z; sgn = -sgn; }
       char4 s1 = nvec[sp_off + p1], s2 = nvec[sp_off + p2];
-      int K = encode_key(s1.x + s2.x, s1.y + s2.y, s1.z + s2.z, s1.w + s2.w, m, M);
+      int K = encode_key(s1.x + s2.x, s1.y + s2.y, s1.z + s2.z, s1.w + s2.w, m, M, species);
       int ch = key2ch[K];
       if (ch >= 0) {
         int g = ch0 + ch;
@@ -429,7 +478,7 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
 // Pairs containing each state (for the one-body intermediates): count then fill.
 // One warp per state p of the system; partners d of the same class.
 __global__ void k_occ(int fill, const char4* __restrict__ nvec, int sp_off, int N, int nsp,
-                      int m, int M, const int* __restrict__ key2ch, int ch0,
+                      int m, int M, int species, const int* __restrict__ key2ch, int ch0,
                       const int* __restrict__ ch_hh_off, const int* __restrict__ ch_pp_off,
                       const int* __restrict__ pos_hh, const int* __restrict__ pos_pp,
                       int* __restrict__ occ_cnt, const int* __restrict__ occ_off,
@@ -448,7 +497,7 @@ __global__ void k_occ(int fill, const char4* __restrict__ nvec, int sp_off, int 
     int gidx = -1;
     if (d < hi && d != p) {
       char4 sd = nvec[sp_off + d];
-      int K = encode_key(sp.x + sd.x, sp.y + sd.y, sp.z + sd.z, sp.w + sd.w, m, M);
+      int K = encode_key(sp.x + sd.x, sp.y + sd.y, sp.z + sd.z, sp.w + sd.w, m, M, species);
       int ch = key2ch[K];
       if (ch >= 0) {
         int p1 = min(p, d), p2 = max(p, d);
@@ -629,8 +678,8 @@ struct SysScratch {
   }
 };
 
-void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const int* n2maxs,
-               const double* thetas, const pnm_minnesota& P) {
+void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const double* rhos,
+               const int* n2maxs, const double* thetas, const pnm_minnesota& P) {
   cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
   std::vector<SysInfo>& sys = ctx->sys;
@@ -644,7 +693,13 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   int nsp_total = 0, lut_total = 0;
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
-    S.N = Ns[k];
+    int Nn = Ns[k], Z = Zs ? Zs[k] : 0;
+    if (Nn < 0 || Z < 0 || (Nn > 0 && Z > 0 && Nn != Z))
+      throw PnmError{PNM_EINVAL, "system " + std::to_string(k) +
+                                     ": neutrons only, protons only, or equal numbers of both"};
+    S.N = Nn + Z;
+    S.Z = Z;
+    S.species = (Nn > 0 ? 1 : 0) | (Z > 0 ? 2 : 0);
     S.rho = rhos[k];
     S.n2max = n2maxs[k];
     if (S.N <= 0 || !(S.rho > 0.0) || S.n2max < 0 || S.n2max > 400)
@@ -652,7 +707,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     S.r = isqrt_floor(S.n2max);
     S.m = 2 * S.r;
     S.M = 2 * S.m + 1;
-    S.nkeys = S.M * S.M * S.M * 3;
+    S.nkeys = S.M * S.M * S.M * (S.species == 1 ? 3 : 9);
+    int g = S.species == 3 ? 4 : 2;  // states per lattice point
     S.L = std::cbrt((double)S.N / S.rho);
     bool twisted = false;
     for (int a = 0; a < 3; a++) {
@@ -662,12 +718,13 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       twisted = twisted || S.phi[a] != 0.0;
     }
     int w = 2 * S.r + 1, ncube = w * w * w;
-    char4* tvec = dalloc<char4>(2 * ncube, scr[k].owned, s);
-    scr[k].idx3 = dalloc<int>(2 * ncube, scr[k].owned, s);
+    char4* tvec = dalloc<char4>((size_t)g * ncube, scr[k].owned, s);
+    scr[k].idx3 = dalloc<int>((size_t)g * ncube, scr[k].owned, s);
     int* dnsp = dalloc<int>(1, scr[k].owned, s);
     int* shell_start = dalloc<int>(S.n2max + 1, scr[k].owned, s);
-    k_basis_count<<<1, 512, (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, shell_start, dnsp);
-    k_basis_place<<<(ncube + 127) / 128, 128, 0, s>>>(S.n2max, S.r, shell_start, tvec, scr[k].idx3);
+    k_basis_count<<<1, 512, (S.n2max + 1) * sizeof(int), s>>>(S.n2max, S.r, g, shell_start, dnsp);
+    k_basis_place<<<(ncube + 127) / 128, 128, 0, s>>>(S.n2max, S.r, S.species, shell_start, tvec,
+                                                      scr[k].idx3);
     CUDA_TRY(cudaGetLastError());
     S.nsp = d2h(dnsp, 1, s)[0];
     if (S.N >= S.nsp) throw PnmError{PNM_EINVAL, "no particle states: n2max too small for N"};
@@ -684,7 +741,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       int nb = (S.nsp + TWIST_THREADS - 1) / TWIST_THREADS;
       k_twist_keys<<<nb, TWIST_THREADS, 0, s>>>(tvec, S.nsp, S.phi[0], S.phi[1], S.phi[2], key);
       k_twist_rank<<<nb, TWIST_THREADS, 0, s>>>(key, S.nsp, tvec, tv2, skey, perm);
-      k_twist_idx3<<<(2 * ncube + 255) / 256, 256, 0, s>>>(scr[k].idx3, 2 * ncube, perm);
+      k_twist_idx3<<<(g * ncube + 255) / 256, 256, 0, s>>>(scr[k].idx3, g * ncube, perm);
       CUDA_TRY(cudaGetLastError());
       hvec[k] = d2h(tv2, S.nsp, s);
       std::vector<double> hk = d2h(skey, S.nsp, s);
@@ -696,7 +753,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     nsp_total += S.nsp;
     S.lut_off = lut_total;
     S.lut_len = 4 * S.n2max + 1;
-    lut_total += S.lut_len;
+    lut_total += S.lut_len * (S.species == 1 ? 1 : 3);  // interleaved R, T, S halves with protons
   }
   ctx->nsp_total = nsp_total;
   D.nvec = dalloc<char4>(nsp_total, ctx->owned, s);
@@ -709,8 +766,12 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
     h2d(D.nvec + S.sp_off, hvec[k], s);
-    k_lut<<<(S.lut_len + 127) / 128, 128, 0, s>>>(D.lut + S.lut_off, S.lut_len, S.L, P.VR, P.kR,
-                                                 P.VS, P.kS);
+    if (S.species == 1)
+      k_lut<<<(S.lut_len + 127) / 128, 128, 0, s>>>(D.lut + S.lut_off, S.lut_len, S.L, P.VR, P.kR,
+                                                   P.VS, P.kS);
+    else
+      k_lut3<<<(S.lut_len + 127) / 128, 128, 0, s>>>(D.lut + S.lut_off, S.lut_len, S.L, P.VR, P.kR,
+                                                    P.VT, P.kT, P.VS, P.kS);
     k_eps<<<(S.nsp + 127) / 128, 128, 0, s>>>(D.nvec + S.sp_off, D.lut + S.lut_off, S.nsp, S.N,
                                              S.L, P.hbar2_2m, S.phi[0], S.phi[1], S.phi[2],
                                              D.ekin + S.sp_off,
@@ -727,9 +788,9 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     int* c3 = dalloc<int>(S.nkeys, scr[k].owned, s);
     int* c4 = dalloc<int>(S.nkeys, scr[k].owned, s);
     int blocks = (S.nkeys * 32 + 255) / 256;
-    k_count_direct<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.nkeys,
+    k_count_direct<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.species, S.nkeys,
                                           S.N, S.nsp, c1, c2);
-    k_count_cross<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.nkeys,
+    k_count_cross<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.species, S.nkeys,
                                          S.N, S.nsp, c3, c4);
     CUDA_TRY(cudaGetLastError());
     std::vector<int> hh = d2h(c1, S.nkeys, s), pp = d2h(c2, S.nkeys, s);
@@ -781,7 +842,10 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
       h_pp_off.push_back(pp_acc);
       h_t_off.push_back(t_acc);
       h_vhh_off.push_back(vhh_acc);
-      bool szero = (K % 3) == 1;  // S_z = 0: the only spin class with nonzero <ab|v|cd>
+      // <ab|v|cd> vanishes for identical-nucleon pairs of equal spin (|S_z| = |T_z| = 2); in
+      // neutron-only systems that leaves S_z = 0
+      int slot = sys[k].species == 1 ? K % 3 : K % 9;
+      bool szero = sys[k].species == 1 ? slot == 1 : !(slot / 3 != 1 && slot % 3 != 1);
       h_szero.push_back(szero ? 1 : 0);
       h_vpp_off.push_back(szero ? vpp_acc : -1);
       if (szero) {
@@ -925,19 +989,19 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     int nchs = S.ch_end - S.ch_begin, nxs = S.x_end - S.x_begin;
     if (nchs > 0)
       k_fill_direct<<<(nchs * 32 + 255) / 256, 256, 0, s>>>(
-          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.N, S.nsp, S.sp_off, nchs,
+          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.species, S.N, S.nsp, S.sp_off, nchs,
           D.ch_key + S.ch_begin, D.ch_hh_off + S.ch_begin, D.ch_pp_off + S.ch_begin, D.hh_pair,
           D.pp_pair, X.pos_hh, X.pos_pp);
     if (nxs > 0) {
       int* xk = dalloc<int>(nxs, X.owned, s);
       h2d(xk, X.xkeys, s);
       k_fill_cross<<<(nxs * 32 + 255) / 256, 256, 0, s>>>(
-          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.N, S.nsp, S.sp_off, nxs, xk,
+          D.nvec + S.sp_off, X.idx3, S.r, S.m, S.M, S.species, S.N, S.nsp, S.sp_off, nxs, xk,
           D.x_ph_off + S.x_begin, D.x_hp_off + S.x_begin, D.ph_pair, D.hp_pair, X.phpos, X.phch,
           X.hppos);
       k_xmap<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_t_off, D.x_ph_off, D.x_hp_off,
                                  D.ph_pair, D.hp_pair, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M,
-                                 X.key2ch, S.ch_begin, D.ch_t_off, D.ch_npp, X.pos_hh, X.pos_pp,
+                                 S.species, X.key2ch, S.ch_begin, D.ch_t_off, D.ch_npp, X.pos_hh, X.pos_pp,
                                  D.xmap);
       k_v_cross<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_c_off, D.x_w_off,
                                     D.x_ph_off, D.x_hp_off, D.ph_pair, D.hp_pair, D.nvec,
@@ -962,7 +1026,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     // pairs containing each state
     int* cnt = dalloc<int>(S.nsp, X.owned, s);
     int ob = (S.nsp * 32 + 255) / 256;
-    k_occ<<<ob, 256, 0, s>>>(0, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, X.key2ch, S.ch_begin,
+    k_occ<<<ob, 256, 0, s>>>(0, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, S.species, X.key2ch, S.ch_begin,
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, cnt, nullptr, nullptr);
     std::vector<int> hc = d2h(cnt, S.nsp, s);
     for (int p = 0; p < S.nsp; p++) h_occ_off[S.sp_off + p + 1] = h_occ_off[S.sp_off + p] + hc[p];
@@ -973,7 +1037,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
     SysInfo& S = sys[k];
     SysScratch& X = scr[k];
     int ob = (S.nsp * 32 + 255) / 256;
-    k_occ<<<ob, 256, 0, s>>>(1, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, X.key2ch, S.ch_begin,
+    k_occ<<<ob, 256, 0, s>>>(1, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, S.species, X.key2ch, S.ch_begin,
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, nullptr, D.occ_off,
                              D.occ_idx);
   }
@@ -982,7 +1046,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
   // does not fit
   if (!h_vpp_items.empty()) {
     int max_lut = 0;
-    for (const SysInfo& S : sys) max_lut = std::max(max_lut, S.lut_len);
+    for (const SysInfo& S : sys) max_lut = std::max(max_lut, S.lut_len * (S.species == 1 ? 1 : 3));
     size_t smem = sizeof(double) * max_lut + 2 * sizeof(char4) * (size_t)vpp_max_npp;
     bool staged = smem <= 200 * 1024;
     const std::vector<int2>& hv = staged ? h_vpp_chunks : h_vpp_items;
@@ -998,7 +1062,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const double* rhos, const 
         if (staged)
           k_v_pppp_rows<<<(unsigned)(hi - lo), 256, smem, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
                                                                D.pp_pair, D.nvec, D.lut + sys[k].lut_off,
-                                                               sys[k].lut_len, D.v_pppp);
+                                                               sys[k].lut_len * (sys[k].species == 1 ? 1 : 3),
+                                                               D.v_pppp);
         else
           k_v_pppp<<<(unsigned)(hi - lo), 256, 0, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
                                                       D.pp_pair, D.nvec, D.lut + sys[k].lut_off, D.v_pppp);
