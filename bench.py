@@ -20,7 +20,8 @@ same batch from the MBPT2 start (mixed and FP64) and the other configurations, e
 dE/N error against the FP64 oracle, a twist-averaged batch (N = 14, n^2 <= 20, rho = 0.08,
 120 twists of a 4 x 5 x 6 Gauss-Legendre mesh in one context) in both precisions, the ladder
 truncations of Eqs. ccd1 and ccd2 (N = 66, n^2 <= 36, rho = 0.16, FP64) and the third-order
-diagrams of the held-out batch (pnm_mbpt3, with the oracle's time and values).  ``--impl reference`` times the FP64 CPU oracle.
+diagrams of the held-out batch (pnm_mbpt3, with the oracle's time and values), and symmetric
+nuclear matter (14 protons + 14 neutrons, rho = 0.16, n^2 <= 20) in both precisions.  ``--impl reference`` times the FP64 CPU oracle.
 
 Prints one JSON line.
 """
@@ -66,6 +67,11 @@ TRUNC_WORKLOADS = {
     "pnm_N66_rho0.16_n2max36_ccd2_pphh_fp64": (66, (0.16,), 36, "pphh"),
 }
 MBPT3_WORKLOAD = ("pnm_N66_n2max36_heldout3_mbpt3_fp64", 66, HELDOUT, 36)
+# Symmetric nuclear matter (14 protons and 14 neutrons).  name: (N, Z, rho, n2max, precision)
+NUCLEAR_WORKLOADS = {
+    "snm_A28_rho0.16_n2max20_bf16x3": (14, 14, 0.16, 20, "bf16x3"),
+    "snm_A28_rho0.16_n2max20_fp64": (14, 14, 0.16, 20, "fp64"),
+}
 DEFAULT_WORKLOAD = "pnm_N66_n2max36_heldout3_learned_bf16x3"
 COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
            "pnm_N66_n2max36_heldout3_mbpt2_fp64", "pnm_N14_rho0.08_n2max20_bf16x3",
@@ -386,6 +392,47 @@ def measure_trunc(P, torch, stream, flush, workload, steps):
             "dE_per_N": [x / N for x in dEs[-1]], "_key": (N, rhos, n2max, terms)}
 
 
+def measure_nuclear(P, torch, stream, flush, workload, refine, steps):
+    """Mean time-to-converge (ms) of symmetric nuclear matter at the metric's stopping rule."""
+    N, Z, rho, n2max, prec = NUCLEAR_WORKLOADS[workload]
+    ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream, Z=Z)
+    p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
+    kw = dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=2000,
+              refine_sweeps=refine if prec == "bf16x3" else 0)
+    for _ in range(3):
+        ctx.solve(**kw)
+    torch.cuda.synchronize()
+    ms, iters, dEs = timed_solves(ctx, kw, steps, flush, stream, torch)
+    eref = float(ctx.eref()[0])
+    ctx.close()
+    A = N + Z
+    return {"ms": statistics.mean(ms), "N": N, "Z": Z, "rho": rho, "n2max": n2max, "iters": iters[-1],
+            "E_per_A": (eref + dEs[-1][0]) / A, "dE_per_A": dEs[-1][0] / A}
+
+
+_nuc_oracle = {}
+
+
+def oracle_nuclear(r):
+    """The oracle's energy at the same stopping rule and at its fixed point (1e-10 MeV per
+    nucleon): the GPU's error against both."""
+    from oracle import channel
+    key = (r["N"], r["Z"], r["rho"], r["n2max"])
+    if key not in _nuc_oracle:
+        A = r["N"] + r["Z"]
+        o = channel.OracleSystem(r["N"], r["rho"], r["n2max"], MINNESOTA, Z=r["Z"])
+        t0 = time.perf_counter()
+        at_rule = o.ccd(alpha=ALPHA, tol=TOL_PER_N * A, maxit=4000)
+        ms = (time.perf_counter() - t0) * 1e3
+        fixed = o.ccd(alpha=ALPHA, tol=1e-10 * A, maxit=4000)
+        _nuc_oracle[key] = (at_rule[0] / A, at_rule[1], fixed[0] / A, ms)
+    rule, it, fixed, ms = _nuc_oracle[key]
+    r["oracle_iters_at_rule"] = it
+    r["oracle_ms"] = ms
+    r["dE_per_A_minus_oracle_at_rule"] = r["dE_per_A"] - rule
+    r["dE_per_A_minus_oracle_fixed_point"] = r["dE_per_A"] - fixed
+
+
 def oracle_trunc(r, budget_s=60.0):
     from oracle import channel
     N, rhos, n2max, terms = r.pop("_key")
@@ -621,6 +668,8 @@ def run_ours(a):
         for w in TRUNC_WORKLOADS:
             comparison[w] = measure_trunc(P, torch, stream, flush, w, 5)
         comparison[MBPT3_WORKLOAD[0]] = measure_mbpt3(P, torch, stream, 5)
+        for w in NUCLEAR_WORKLOADS:
+            comparison[w] = measure_nuclear(P, torch, stream, flush, w, a.refine, 5)
         if "train_s" in _model:
             comparison["training"] = {"seconds": _model["train_s"], "loss_first_last": _model["loss"],
                                       "epochs": _model["epochs"], "batch": _model["batch"],
@@ -663,6 +712,8 @@ def run_ours(a):
                     oracle_trunc(r)
                 elif w == MBPT3_WORKLOAD[0]:
                     oracle_mbpt3(r)
+                elif w in NUCLEAR_WORKLOADS:
+                    oracle_nuclear(r)
 
     if rank == 0:
         line = {
