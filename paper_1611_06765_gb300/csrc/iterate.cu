@@ -10,7 +10,7 @@
 //              <kl|chi|ij> = <kl|v|ij> + 1/2 <kl|v|cd> t_ij^cd per direct channel
 //   k_dchi     chi_p - eps_p per state, gathered over the pairs holding p
 //   k_ph       T_x = remap(t); C_x = V1_x + 1/2 W_x T_x; Q_x = T_x C_x per cross channel
-//   k_pp64     1/2 sum_cd <ab|v|cd> t_cd^ij, grouped over all S_z = 0 channels (FP64)
+//   k_pp64     1/2 sum_cd <ab|v|cd> t_cd^ij, grouped over all channels with a V_pppp block (FP64)
 //   k_update   Jacobi step t_new = (v + rest) / eps_ij^ab, mixing, energy/residual partials
 //   finalize   (last block of k_update) Eq. (ccdcorr) energy per system, |dE| test,
 //              device-side loop condition
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
     last_block_finalize(fa, ctl);
     return;
   }
-  bool szero = D.ch_szero[c] != 0;
+  bool has_vpp = D.ch_vpp[c] != 0;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
   double* __restrict__ tn = next_t(D, ctl);
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
       if (!frozen) {
         int4 q = D.qmap[z];
         double num = v + (da - row_dij[g]) * tz;
-        if (szero) num += D.rpp[z];
+        if (has_vpp) num += D.rpp[z];
         num += hh[g];
         double ph = 0.0;
         if (q.x >= 0) ph += D.xq[q.x];
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     last_block_finalize(fa, ctl);
     return;
   }
-  bool szero = D.ch_szero[c] != 0;
+  bool has_vpp = D.ch_vpp[c] != 0;
   double alpha = ctl->alpha;
   const double* __restrict__ t = cur_t(D, ctl);
   const float* __restrict__ t32 = cur_t32(D, ctl);
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
         t32z[j] = t32[z[j]];
         idn[j] = D.inv_den[z[j]];
         part[j] = hh[z[j]];
-        if (szero)
+        if (has_vpp)
           for (int pl = 0; pl < nplanes; pl++) part[j] += rpp[pl * pstride + z[j]];
       }
 #pragma unroll
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
           if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
           if (q[j].w >= 0) pk.xt[q[j].w] = o32;
         }
-        if (pk.bt && szero) {
+        if (pk.bt && has_vpp) {
           int npad = pk.ch_npad[c];
           long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
           __nv_bfloat16 bhi = __float2bfloat16_rn(o32);
@@ -885,7 +885,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->row_lo_d = d;
   ctx->row_hi_d = d + nsys;
   ctx->lut_off_d = d + 2 * nsys;
-  // pp work list (S_z = 0 channels): one item per 32 pp columns
+  // pp work list (channels with a V_pppp block): one item per 32 pp columns
   std::vector<int2> items, abit;
   std::vector<int4> upd;
   std::vector<int> ulo(nsys), uhi(nsys);
@@ -894,7 +894,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
     int npp = ctx->h_npp[c];
     max_npp = std::max(max_npp, npp);
     for (int ab0 = 0; ab0 < npp; ab0 += 128) abit.push_back(make_int2(c, ab0));
-    if (!ctx->h_szero[c]) continue;
+    if (!ctx->h_vpp[c]) continue;
     for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS) items.push_back(make_int2(c, ab0));
   }
   // per-row items (channel, ij, first column), 128 columns each, grouped by system (the
@@ -1072,7 +1072,7 @@ void pnm_mbpt2_all(pnm_ctx* ctx, double* out) {
 }
 
 // Third-order diagrams (Fig. goldstone, Eqs. diag3-diag5) from the MBPT2 amplitudes t0 held in
-// D.t0, the pp ladder of t0 in D.rpp (S_z = 0 channels) and the linear ph term of t0 in D.xq:
+// D.t0, the pp ladder of t0 in D.rpp (channels with a V_pppp block) and the linear ph term of t0 in D.xq:
 // per row (channel, ij) the partial sums over ab of
 //   (4)  t0_ab^ij sum_{c<d} <ab|v|cd> t0_cd^ij,
 //   (5)  t0_ab^ij sum_{k<l} t0_ab^kl <kl|v|ij>,
@@ -1086,12 +1086,12 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
   long base = D.ch_t_off[c], row = base + (long)ij * npp;
   const double* __restrict__ vh = D.v_hhhh + D.ch_vhh_off[c];
   const double* __restrict__ t = D.t0;
-  bool szero = D.ch_szero[c] != 0;
+  bool has_vpp = D.ch_vpp[c] != 0;
   double e4 = 0.0, e5 = 0.0, e3 = 0.0;
   for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
     long z = row + ab;
     double tz = t[z];
-    if (szero) e4 += tz * D.rpp[z];
+    if (has_vpp) e4 += tz * D.rpp[z];
     double hh = 0.0;
     for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * vh[(long)kl * nh + ij];
     e5 += tz * hh;

@@ -55,7 +55,7 @@ static_assert(TC_BK == 64, "tile_core_off assumes 64-element k-blocks");
 __device__ __forceinline__ int core_off(int r, int k) { return tile_core_off(r, k); }
 
 // ------------------------------------------------------------------------ kernels
-// V tiles of the S_z = 0 channels (setup): one CTA per (item, k-block).
+// V tiles of the channels with a V_pppp block (setup): one CTA per (item, k-block).
 __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restrict__ v_pppp,
                          const long* __restrict__ ch_vpp_off, __nv_bfloat16* __restrict__ vt) {
   TCItem it = items[blockIdx.x];  // an unsplit item: kb0 = 0, nkb = all k-blocks
@@ -78,7 +78,7 @@ __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restr
   }
 }
 
-// t tiles of the S_z = 0 channels (every update): one CTA per (channel, k-block).
+// t tiles of the channels with a V_pppp block (every update): one CTA per (channel, k-block).
 __global__ void k_pack_t(const int4* __restrict__ pk, const long* __restrict__ pk_boff,
                          DevState D, const LoopCtl* __restrict__ ctl, __nv_bfloat16* __restrict__ bt) {
   int4 p = pk[blockIdx.x];  // (channel, k-block, npad, 0)
@@ -310,7 +310,7 @@ struct MixedState {
   int4* pk = nullptr;
   long* pk_boff = nullptr;
   int npk = 0;
-  long* ch_boff = nullptr;  // per channel: k-block 0 of its t tiles (-1: not an S_z = 0 channel)
+  long* ch_boff = nullptr;  // per channel: k-block 0 of its t tiles (-1: no V_pppp block)
   int* ch_npad = nullptr;
   uint32_t stage_bytes = 0;
   size_t smem = 0;
@@ -428,7 +428,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     long voff = 0, boff = 0;
     int max_npad = 16, max_nkb = 1;
     for (int c = 0; c < ctx->nch; c++) {
-      if (!ctx->h_szero[c]) continue;
+      if (!ctx->h_vpp[c]) continue;
       int npp = ctx->h_npp[c], nh = ctx->h_nhh[c];
       int npad = std::max(16, (nh + 15) / 16 * 16);
       if (npad > 64) throw PnmError{PNM_EINVAL, "n_hh > 64 in one channel: tensor-core tile too small"};
@@ -657,7 +657,7 @@ void pnm_free_mixed(pnm_ctx* ctx) {
 }
 
 // Apply only the particle-particle ladder to amplitudes t (library order, system `sys`):
-// r = sum_{c<d} <ab|v|cd> t_cd^ij on S_z = 0 channels, 0 elsewhere.  Uses the solver's
+// r = sum_{c<d} <ab|v|cd> t_cd^ij on channels with a V_pppp block, 0 elsewhere.  Uses the solver's
 // buffers (the iteration state is reset).
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n) {
   const SysInfo& S = ctx->sys[sys];
@@ -696,7 +696,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   if (err) throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget"};
   for (int c = S.ch_begin; c < S.ch_end; c++) {
     long o = ctx->h_t_off[c], len = (long)ctx->h_nhh[c] * ctx->h_npp[c];
-    for (long z = 0; z < len; z++) r[o - S.t_begin + z] = ctx->h_szero[c] ? out[o + z] : 0.0;
+    for (long z = 0; z < len; z++) r[o - S.t_begin + z] = ctx->h_vpp[c] ? out[o + z] : 0.0;
   }
 }
 

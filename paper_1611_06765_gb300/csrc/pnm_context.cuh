@@ -28,7 +28,7 @@ struct pnm_ctx {
   int max_x_dim = 0, max_npp = 0;
 
   // host copies of the channel metadata
-  std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_szero;
+  std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_vpp;
   std::vector<long> h_t_off, h_vpp_off, h_x_t_off;
   std::vector<int2> h_rows;
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;

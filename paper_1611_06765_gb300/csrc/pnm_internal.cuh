@@ -6,8 +6,9 @@
 //                int2 hh_pair[], pp_pair[] (global state indices, lexicographic per channel)
 //   amplitudes   t[c] is an n_hh x n_pp row-major block (hh rows, pp contiguous): element
 //                (ij, ab) at t_off[c] + ij * n_pp + ab.  v_pphh has the same layout.
-//   V_pppp       only for S_z = 0 channels (same-spin pairs do not interact): n_pp x n_pp,
-//                symmetric, row-major at vpp_off[c].
+//   V_pppp       only for channels where <ab|v|cd> can be nonzero (not both |S_z| = 2 and
+//                |T_z| = 2: identical nucleons of equal spin do not interact; for neutrons
+//                that leaves S_z = 0): n_pp x n_pp, symmetric, row-major at vpp_off[c].
 //   cross chans  per channel x: n_ph rows (a,i), n_hp columns (k,c); T_x/Q_x are
 //                n_ph x n_hp at xt_off[x]; V1_x (<kb|v|cj>) n_hp x n_hp at xc_off[x];
 //                W_x (<kl|v|ce>, n_hp x n_ph) stored transposed (n_ph x n_hp) at xw_off[x].
@@ -61,7 +62,7 @@ struct DevState {
   int* sp_sys;           // state -> system
   int* sp_hole;          // 1 for hole states
   // direct channels
-  int *ch_sys, *ch_key, *ch_nhh, *ch_npp, *ch_hh_off, *ch_pp_off, *ch_szero;
+  int *ch_sys, *ch_key, *ch_nhh, *ch_npp, *ch_hh_off, *ch_pp_off, *ch_vpp;
   long *ch_t_off, *ch_vpp_off, *ch_vhh_off;
   int2 *hh_pair, *pp_pair;
   // rows (channel, ij) for the update and energy partials

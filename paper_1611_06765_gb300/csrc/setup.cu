@@ -552,7 +552,7 @@ __global__ void k_den(int row0, const int2* __restrict__ row_item, const int* __
   }
 }
 
-// <ab|v|cd> for S_z = 0 channels; one CTA per (channel, row cd).
+// <ab|v|cd> for channels with a V_pppp block; one CTA per (channel, row cd).
 __global__ void k_v_pppp(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
                          const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
                          const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
@@ -817,7 +817,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   }
 
   // ---- channel metadata and offsets (host prefix sums over channels)
-  std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_szero;
+  std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_vpp;
   std::vector<long> h_t_off, h_vpp_off, h_vhh_off;
   std::vector<int2> h_rows, h_vpp_items, h_vpp_chunks;
   int vpp_max_npp = 0;
@@ -845,10 +845,10 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       // <ab|v|cd> vanishes for identical-nucleon pairs of equal spin (|S_z| = |T_z| = 2); in
       // neutron-only systems that leaves S_z = 0
       int slot = sys[k].species == 1 ? K % 3 : K % 9;
-      bool szero = sys[k].species == 1 ? slot == 1 : !(slot / 3 != 1 && slot % 3 != 1);
-      h_szero.push_back(szero ? 1 : 0);
-      h_vpp_off.push_back(szero ? vpp_acc : -1);
-      if (szero) {
+      bool has_vpp = sys[k].species == 1 ? slot == 1 : !(slot / 3 != 1 && slot % 3 != 1);
+      h_vpp.push_back(has_vpp ? 1 : 0);
+      h_vpp_off.push_back(has_vpp ? vpp_acc : -1);
+      if (has_vpp) {
         for (int cd = 0; cd < X.dnpp[c]; cd++) h_vpp_items.push_back(make_int2(g, cd));
         for (int cd = 0; cd < X.dnpp[c]; cd += VPP_ROWS) h_vpp_chunks.push_back(make_int2(g, cd));
         vpp_max_npp = std::max(vpp_max_npp, X.dnpp[c]);
@@ -897,7 +897,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   ctx->h_npp = h_npp;
   ctx->h_t_off = h_t_off;
   ctx->h_vpp_off = h_vpp_off;
-  ctx->h_szero = h_szero;
+  ctx->h_vpp = h_vpp;
   ctx->h_rows = h_rows;
   ctx->h_x_nph = h_x_nph;
   ctx->h_x_nhp = h_x_nhp;
@@ -914,7 +914,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   D.ch_npp = dalloc<int>(C, ctx->owned, s);
   D.ch_hh_off = dalloc<int>(C, ctx->owned, s);
   D.ch_pp_off = dalloc<int>(C, ctx->owned, s);
-  D.ch_szero = dalloc<int>(C, ctx->owned, s);
+  D.ch_vpp = dalloc<int>(C, ctx->owned, s);
   D.ch_t_off = dalloc<long>(C, ctx->owned, s);
   D.ch_vpp_off = dalloc<long>(C, ctx->owned, s);
   D.ch_vhh_off = dalloc<long>(C, ctx->owned, s);
@@ -939,7 +939,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   h2d(D.ch_npp, h_npp, s);
   h2d(D.ch_hh_off, h_hh_off, s);
   h2d(D.ch_pp_off, h_pp_off, s);
-  h2d(D.ch_szero, h_szero, s);
+  h2d(D.ch_vpp, h_vpp, s);
   h2d(D.ch_t_off, h_t_off, s);
   h2d(D.ch_vpp_off, h_vpp_off, s);
   h2d(D.ch_vhh_off, h_vhh_off, s);
@@ -1041,7 +1041,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, nullptr, D.occ_off,
                              D.occ_idx);
   }
-  // V_pppp for S_z = 0 channels, one launch per system (the LUT differs per system): chunks of
+  // V_pppp for channels with a V_pppp block, one launch per system (the LUT differs per system): chunks of
   // VPP_ROWS rows with the channel staged in shared memory, or one row per CTA when a channel
   // does not fit
   if (!h_vpp_items.empty()) {
