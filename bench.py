@@ -81,7 +81,7 @@ MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload
 # (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {"k_pp64": 1.820952e9, "k_pp_tc": 0.876660e9, "k_update_mix": 0.341421e9}
+TRAFFIC = {}
 ALPHA = 0.5
 
 
@@ -175,29 +175,32 @@ def dist_setup():
 def chan_sizes(ctx):
     """Channel sizes of every system of a context, concatenated."""
     import numpy as np
-    nhh, npp, sz, nph, nhp = [], [], [], [], []
+    nhh, npp, nlad, nph, nhp = [], [], [], [], []
     for s in range(ctx.nsys):
-        keys, sizes, _ = ctx.channels(s, 0)
+        _, sizes, _ = ctx.channels(s, 0)
         _, xs, _ = ctx.channels(s, 1)
         nhh.append(sizes[:, 0])
         npp.append(sizes[:, 1])
-        sz.append((keys % 3) == 1)
+        nlad.append(ctx.ladder_sizes(s))
         nph.append(xs[:, 0])
         nhp.append(xs[:, 1])
     cat = lambda v: np.concatenate(v).astype(float)
-    return cat(nhh), cat(npp), np.concatenate(sz), cat(nph), cat(nhp)
+    return cat(nhh), cat(npp), cat(nlad), cat(nph), cat(nhp)
 
 
 def algorithmic_cost(ctx, kernel):
     """(bytes, flops) per launch of a kernel, from the channel sizes of all systems of the
     context: every array the kernel must touch, counted once."""
-    nhh, npp, szero, nph, nhp = chan_sizes(ctx)
+    nhh, npp, nlad, nph, nhp = chan_sizes(ctx)
     nt = float((nhh * npp).sum())
     if kernel in ("k_pp64", "k_pp_tc"):
+        # the ladder in its basis (pnm_ladder_sizes): V block n_lad x n_lad, operand and result
+        # n_hh x n_lad per channel
         vb = 8.0 if kernel == "k_pp64" else 4.0          # FP64 V, or BF16 hi + lo
-        tb = 8.0 if kernel == "k_pp64" else 4.0          # t operand
-        byts = float((npp[szero] ** 2).sum()) * vb + float((nhh[szero] * npp[szero]).sum()) * (tb + 8.0)
-        flops = 2.0 * float((nhh[szero] * npp[szero] ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
+        tb = 8.0 if kernel == "k_pp64" else 4.0          # t operand in the ladder basis
+        rb = 8.0 if kernel == "k_pp64" else 4.0          # result
+        byts = float((nlad ** 2).sum()) * vb + float((nhh * nlad).sum()) * (tb + rb)
+        flops = 2.0 * float((nhh * nlad ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
         return byts, flops
     if kernel == "k_ph64":
         # index map and gathered t, W, V1, Q
@@ -213,8 +216,9 @@ def algorithmic_cost(ctx, kernel):
         # t, v, eps, 1/eps, qmap, rpp, four Q values, t_next
         return nt * (8 + 8 + 8 + 8 + 16 + 8 + 4 * 8 + 8), nt * 20.0
     if kernel == "k_update_mix":
-        # t, v, 1/eps, qmap, t32, rpp32, four Q values read; t, t32, BF16 hi/lo, four T entries written
-        return nt * (8 + 8 + 8 + 16 + 4 + 4 + 4 * 4 + 8 + 4 + 4 + 4 * 4), nt * 20.0
+        # t, v, 1/eps, qmap, t32, ladder map, pp ladder, four Q values read; t, t32, four T
+        # entries written
+        return nt * (8 + 8 + 8 + 16 + 4 + 4 + 4 + 4 * 4 + 8 + 4 + 4 * 4), nt * 20.0
     if kernel in ("k_tstats", "k_tstats32"):
         return nt * 8 * 2 + float((nhh * nhh).sum()) * 16, nt * 2.0 * (2 + nhh.mean())
     return nt * 8.0, 0.0

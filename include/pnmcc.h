@@ -180,6 +180,15 @@ int pnm_eref(const pnm_ctx *ctx, double *e_ref);
  * fused pass over the direct channels.  One value per system. */
 int pnm_mbpt2(pnm_ctx *ctx, double *dE);
 
+/* Size of the basis in which the pp ladder of each direct channel of system `sys` is computed
+ * (0 for channels without a pp-pp interaction block).  For neutron pairs of S_z = 0 the
+ * interaction acts only on the spin singlet: pairs whose spatial labels differ by the exchange
+ * of the two spins share one basis vector (with the sign of their stored order), so the basis
+ * has about half as many vectors as the channel has pairs and the ladder's V block and products
+ * shrink to about a quarter; elsewhere one vector per pair.  *n_chan receives the number of
+ * direct channels; nlad (nullable, host) one int per channel in pnm_channels order. */
+int pnm_ladder_sizes(const pnm_ctx *ctx, int sys, int *n_chan, int32_t *nlad);
+
 /* Third-order correlation energy (Sec. "Many-body perturbation theory", Fig. goldstone):
  * e3[3 s + 0] = diagram (4), the pp ladder (Eq. diag4); e3[3 s + 1] = diagram (5), the hh
  * ladder (Eq. diag5); e3[3 s + 2] = diagram (3), the particle-hole ring (Eq. diag3, read with

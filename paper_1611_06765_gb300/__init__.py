@@ -121,6 +121,15 @@ class Context:
         _lib.check(_lib.load().pnm_mbpt2(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
+    def ladder_sizes(self, sys=0):
+        """pnm_ladder_sizes: the pp ladder's basis size per direct channel (0: no V_pppp)."""
+        L = _lib.load()
+        n = C.c_int()
+        _lib.check(L.pnm_ladder_sizes(self._h, sys, C.byref(n), None))
+        out = np.zeros(n.value, np.int32)
+        _lib.check(L.pnm_ladder_sizes(self._h, sys, C.byref(n), out.ctypes.data_as(C.c_void_p)))
+        return out
+
     def mbpt3(self):
         """pnm_mbpt3: (nsys, 3) array of diagrams (4) pp ladder, (5) hh ladder, (3) ph ring."""
         out = np.zeros(3 * self.nsys)

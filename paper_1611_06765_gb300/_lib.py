@@ -34,7 +34,7 @@ EXPORTS = (
     "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_create_matter",
     "pnm_twist_mesh",
     "pnm_destroy", "pnm_num_systems",
-    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc", "pnm_mbpt3",
+    "pnm_basis", "pnm_channels", "pnm_v_element", "pnm_eref", "pnm_mbpt2", "pnm_mbpt2_noalloc", "pnm_mbpt3", "pnm_ladder_sizes",
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_apply_ph_term", "pnm_mlp_num_params", "pnm_mlp_init",
@@ -94,6 +94,7 @@ def load(path=None):
     L.pnm_mbpt2.argtypes = [vp, dp]
     L.pnm_mbpt2_noalloc.argtypes = [vp, dp]
     L.pnm_mbpt3.argtypes = [vp, dp]
+    L.pnm_ladder_sizes.argtypes = [vp, C.c_int, ip, vp]
     L.pnm_ccd_solve.argtypes = [vp, C.POINTER(pnm_solve_opts), dp, ip, dp]
     L.pnm_energy_history.argtypes = [vp, C.c_int, dp, C.c_int, ip]
     L.pnm_amplitude_labels.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t), vp]

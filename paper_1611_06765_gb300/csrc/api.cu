@@ -48,6 +48,16 @@ static cudaMemPool_t library_pool(int dev) {
   return pool;
 }
 
+void pnm_smem_at_least(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> cur;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& c = cur[func];
+  if (bytes <= c) return;
+  CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  c = bytes;
+}
+
 void* pnm_pool_alloc(cudaStream_t s, size_t bytes) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -370,6 +380,17 @@ int pnm_mbpt2(pnm_ctx* ctx, double* dE) {
   return guarded([&]() {
     if (!ctx || !dE) throw PnmError{PNM_EINVAL, "null argument"};
     pnm_mbpt2_all(ctx, dE);
+    return PNM_OK;
+  });
+}
+
+int pnm_ladder_sizes(const pnm_ctx* ctx, int sys, int* n_chan, int32_t* nlad) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    const SysInfo& S = ctx->sys[sys];
+    if (n_chan) *n_chan = S.ch_end - S.ch_begin;
+    if (nlad)
+      for (int c = S.ch_begin; c < S.ch_end; c++) nlad[c - S.ch_begin] = ctx->h_vpp[c] ? ctx->h_nlad[c] : 0;
     return PNM_OK;
   });
 }

@@ -327,12 +327,9 @@ static void launch_ph_classes(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_
 
 template <typename T_, bool GATHER>
 static void ph_attributes(const pnm_ctx* ctx) {
-  CUDA_TRY(cudaFuncSetAttribute(k_ph<T_, 256, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_smem_bytes(ctx->max_x_dim, sizeof(T_))));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph<T_, 128, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_smem_bytes(PH_SMALL_DIM, sizeof(T_))));
-  CUDA_TRY(cudaFuncSetAttribute(k_ph_warp<T_, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ph_warp_smem(sizeof(T_))));
+  smem_at_least(k_ph<T_, 256, GATHER>, ph_smem_bytes(ctx->max_x_dim, sizeof(T_)));
+  smem_at_least(k_ph<T_, 128, GATHER>, ph_smem_bytes(PH_SMALL_DIM, sizeof(T_)));
+  smem_at_least(k_ph_warp<T_, GATHER>, ph_warp_smem(sizeof(T_)));
 }
 
 // FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
@@ -349,6 +346,56 @@ void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* 
 void pnm_ph_attributes(const pnm_ctx* ctx) {
   ph_attributes<double, true>(ctx);
   ph_attributes<float, false>(ctx);
+}
+
+// ------------------------------------------------------------------------ ladder basis
+// s(ij, q) = sum over the (one or two) pairs of vector q of sign * t(ij, pair), from the current
+// amplitudes (FP64) or their FP32 copy; one CTA per (channel, ij) row of a channel with V_pppp.
+template <typename T_>
+__global__ void __launch_bounds__(128) k_lad_gather(DevState D, const LoopCtl* __restrict__ ctl,
+                                                    const int2* __restrict__ rows, T_* __restrict__ out) {
+  int2 it = rows[blockIdx.x];
+  int c = it.x, ij = it.y;
+  if (sys_done(D, ctl, D.ch_sys[c])) return;
+  const T_* __restrict__ t;
+  if constexpr (std::is_same<T_, double>::value) t = cur_t(D, ctl);
+  else t = cur_t32(D, ctl);
+  int npp = D.ch_npp[c], nl = D.ch_nlad[c], off = D.ch_pp_off[c];
+  const T_* tr = t + D.ch_t_off[c] + (long)ij * npp;
+  T_* o = out + D.ch_s_off[c] + (long)ij * nl;
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+    int2 m = D.lad_mem[off + q];
+    T_ a = tr[(m.x > 0 ? m.x : -m.x) - 1];
+    T_ v = m.x > 0 ? a : -a;
+    if (m.y != 0) {
+      T_ b = tr[(m.y > 0 ? m.y : -m.y) - 1];
+      v += m.y > 0 ? b : -b;
+    }
+    o[q] = v;
+  }
+}
+
+// The pp ladder in the amplitude layout, from its ladder-layout value (planes summed): zero in
+// channels without V_pppp.  One CTA per (channel, ij) row.
+template <typename T_>
+__global__ void __launch_bounds__(128) k_lad_expand(DevState D, const T_* __restrict__ rs, int planes,
+                                                    long pstride, double* __restrict__ out) {
+  int2 it = D.row_item[blockIdx.x];
+  int c = it.x, ij = it.y;
+  int npp = D.ch_npp[c];
+  bool vpp = D.ch_vpp[c] != 0;
+  double* o = out + D.ch_t_off[c] + (long)ij * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    double v = 0.0;
+    if (vpp) {
+      int sg;
+      long z = lad_index(D, c, ij, ab, sg);
+      T_ a = 0;
+      for (int p = 0; p < planes; p++) a += rs[p * pstride + z];
+      v = sg > 0 ? (double)a : -(double)a;
+    }
+    o[ab] = v;
+  }
 }
 
 // ---------------------------------------------------------------------- pp ladder FP64
@@ -570,7 +617,11 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
       if (!frozen) {
         int4 q = D.qmap[z];
         double num = v + (da - row_dij[g]) * tz;
-        if (has_vpp) num += D.rpp[z];
+        if (has_vpp) {
+          int sg;
+          double rl = D.rpp[lad_index(D, c, ij0 + g, ab, sg)];
+          num += sg > 0 ? rl : -rl;
+        }
         num += hh[g];
         double ph = 0.0;
         if (q.x >= 0) ph += D.xq[q.x];
@@ -645,8 +696,8 @@ __global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restr
 // unit is the scarce one, so the step is written as t + alpha R / eps with R = bracket -
 // eps t (the value of alpha t_new + (1 - alpha) t).  Rows go in batches of UPD_BATCH: all
 // loads of a batch are issued before any store (rows past ng repeat the last row and are
-// discarded).  Writes the new amplitude in FP64, FP32, as BF16 hi/lo tiles of the next
-// tensor-core pp ladder and at its four places in the ph term's T.
+// discarded).  Writes the new amplitude in FP64, FP32 and at its four places in the ph term's T;
+// the pp ladder arrives in the ladder layout (lad_index).
 __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, LoopCtl* __restrict__ ctl,
                                                     const int4* __restrict__ items, FinArgs fa,
                                                     const float* __restrict__ rpp, const float* __restrict__ hh,
@@ -705,8 +756,13 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
         t32z[j] = t32[z[j]];
         idn[j] = D.inv_den[z[j]];
         part[j] = hh[z[j]];
-        if (has_vpp)
-          for (int pl = 0; pl < nplanes; pl++) part[j] += rpp[pl * pstride + z[j]];
+        if (has_vpp) {
+          int sg;
+          long zl = lad_index(D, c, ij0 + g, ab, sg);
+          float rl = 0.0f;
+          for (int pl = 0; pl < nplanes; pl++) rl += rpp[pl * pstride + zl];
+          part[j] += sg > 0 ? rl : -rl;
+        }
       }
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
@@ -737,15 +793,6 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
           if (q[j].y >= 0) pk.xt[q[j].y] = -o32;
           if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
           if (q[j].w >= 0) pk.xt[q[j].w] = o32;
-        }
-        if (pk.bt && has_vpp) {
-          int npad = pk.ch_npad[c];
-          long tb = pk.ch_boff[c] + (long)(ab >> 6) * 2 * npad * 64;
-          __nv_bfloat16 bhi = __float2bfloat16_rn(o32);
-          __nv_bfloat16 blo = __float2bfloat16_rn(o32 - __bfloat162float(bhi));
-          int o = tile_core_off(ij0 + g, ab & 63);
-          pk.bt[tb + o] = bhi;
-          pk.bt[tb + (long)npad * 64 + o] = blo;
         }
       }
     }
@@ -885,17 +932,21 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->row_lo_d = d;
   ctx->row_hi_d = d + nsys;
   ctx->lut_off_d = d + 2 * nsys;
-  // pp work list (channels with a V_pppp block): one item per 32 pp columns
-  std::vector<int2> items, abit;
+  // pp work list (channels with a V_pppp block): one item per 32 columns of the ladder basis;
+  // ladder rows (channel, ij) for the gather of the ladder-basis amplitudes
+  std::vector<int2> items, abit, lrows;
   std::vector<int4> upd;
   std::vector<int> ulo(nsys), uhi(nsys);
-  int max_npp = 0;
+  int max_npp = 0, max_nlad = 0;
   for (int c = 0; c < ctx->nch; c++) {
     int npp = ctx->h_npp[c];
     max_npp = std::max(max_npp, npp);
     for (int ab0 = 0; ab0 < npp; ab0 += 128) abit.push_back(make_int2(c, ab0));
     if (!ctx->h_vpp[c]) continue;
-    for (int ab0 = 0; ab0 < npp; ab0 += PP64_COLS) items.push_back(make_int2(c, ab0));
+    int nl = ctx->h_nlad[c];
+    max_nlad = std::max(max_nlad, nl);
+    for (int q0 = 0; q0 < nl; q0 += PP64_COLS) items.push_back(make_int2(c, q0));
+    for (int ij = 0; ij < ctx->h_nhh[c]; ij++) lrows.push_back(make_int2(c, ij));
   }
   // per-row items (channel, ij, first column), 128 columns each, grouped by system (the
   // learned-start kernels); update items (channel, first ij, first column, rows) with up to
@@ -934,6 +985,11 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   group_items(G, &grp, &glo, &ghi);
   ctx->upd_rows = G;
   ctx->max_npp = max_npp;
+  ctx->max_nlad = max_nlad;
+  ctx->n_lad_rows = (int)lrows.size();
+  ctx->lad_rows = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, lrows.size()));
+  if (!lrows.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->lad_rows, lrows.data(), sizeof(int2) * lrows.size(), cudaMemcpyHostToDevice, s));
   ctx->n_pp_items = (int)items.size();
   ctx->pp_items = (int2*)dmalloc(ctx, sizeof(int2) * std::max<size_t>(1, items.size()));
   if (!items.empty())
@@ -1021,17 +1077,17 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   if (!xl.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->ph_list, xl.data(), sizeof(int) * xl.size(), cudaMemcpyHostToDevice, s));
   size_t ph_smem = ph_smem_bytes(ctx->max_x_dim, sizeof(double));
-  size_t pp_smem = pp64_smem(max_npp);
+  size_t pp_smem = pp64_smem(max_nlad);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
   pnm_ph_attributes(ctx);
-  CUDA_TRY(cudaFuncSetAttribute(k_hh32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh32_smem_bytes(ctx)));
+  smem_at_least(k_hh32, hh32_smem_bytes(ctx));
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
   }
   CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-  CUDA_TRY(cudaFuncSetAttribute(k_pp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp_smem));
+  smem_at_least(k_pp64, pp_smem);
   CUDA_TRY(cudaStreamSynchronize(s));
 }
 
@@ -1091,7 +1147,11 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
   for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
     long z = row + ab;
     double tz = t[z];
-    if (has_vpp) e4 += tz * D.rpp[z];
+    if (has_vpp) {
+      int sg;
+      double rl = D.rpp[lad_index(D, c, ij, ab, sg)];
+      e4 += tz * (sg > 0 ? rl : -rl);
+    }
     double hh = 0.0;
     for (int kl = 0; kl < nh; kl++) hh += t[base + (long)kl * npp + ab] * vh[(long)kl * nh + ij];
     e5 += tz * hh;
@@ -1172,10 +1232,37 @@ FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool 
   return f;
 }
 
+// The FP64 pp ladder in the ladder basis: the amplitudes gathered into it (s = sum of the
+// signed members of each vector), then k_pp64 on a view of the state whose channel width is
+// the basis size, whose amplitudes are s and whose V blocks are the ladder V; the result stays
+// in the ladder layout (consumers read it through lad_index).
+template <typename T_>
+static void lad_expand(pnm_ctx* ctx, const T_* rs, int planes, long pstride, double* host_out) {
+  cudaStream_t s = ctx->stream;
+  if (!ctx->expand_buf) ctx->expand_buf = (double*)dmalloc(ctx, sizeof(double) * std::max<long>(ctx->nt, 1));
+  if (ctx->nrows > 0)
+    k_lad_expand<T_><<<ctx->nrows, 128, 0, s>>>(ctx->d, rs, planes, pstride, ctx->expand_buf);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(host_out, ctx->expand_buf, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void pnm_lad_expand(pnm_ctx* ctx, const float* rs, int planes, long pstride, double* host_out) {
+  lad_expand(ctx, rs, planes, pstride, host_out);
+}
+
+void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, double* host_out) {
+  lad_expand(ctx, rs, planes, pstride, host_out);
+}
+
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s) {
-  if (ctx->n_pp_items > 0)
-    k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_npp), s>>>(ctx->d, ctx->ctl,
-                                                                             ctx->pp_items);
+  if (ctx->n_pp_items == 0) return;
+  k_lad_gather<double><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->d.s64);
+  DevState L = ctx->d;
+  L.ch_npp = ctx->d.ch_nlad;
+  L.ch_t_off = ctx->d.ch_s_off;
+  L.t0 = L.t1 = ctx->d.s64;
+  k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items);
 }
 
 // The ph term and the pp ladder do not depend on each other nor on the one-body sums: in a

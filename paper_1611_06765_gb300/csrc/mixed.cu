@@ -78,21 +78,37 @@ __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restr
   }
 }
 
-// t tiles of the channels with a V_pppp block (every update): one CTA per (channel, k-block).
+// t tiles of the channels with a V_pppp block, in the ladder basis (before every tensor-core
+// ladder): one CTA per (channel, k-block of 64 basis vectors); each tile entry gathers the
+// signed members of its vector from the current amplitudes (FP32 copy in the iteration, FP64
+// for the operator call) and stores the BF16 hi/lo split.
+template <typename T_>
 __global__ void k_pack_t(const int4* __restrict__ pk, const long* __restrict__ pk_boff,
                          DevState D, const LoopCtl* __restrict__ ctl, __nv_bfloat16* __restrict__ bt) {
   int4 p = pk[blockIdx.x];  // (channel, k-block, npad, 0)
   int c = p.x, kb = p.y, npad = p.z;
-  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
-  const double* t = cur_t(D, ctl) + D.ch_t_off[c];
+  if (sys_done(D, ctl, D.ch_sys[c])) return;
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c], nl = D.ch_nlad[c], off = D.ch_pp_off[c];
+  const T_* t;
+  if constexpr (std::is_same<T_, double>::value) t = cur_t(D, ctl) + D.ch_t_off[c];
+  else t = cur_t32(D, ctl) + D.ch_t_off[c];
   __nv_bfloat16* hi = bt + pk_boff[blockIdx.x];
   __nv_bfloat16* lo = hi + npad * TC_BK;
   for (int e = threadIdx.x; e < npad * TC_BK; e += blockDim.x) {
     int n = e / TC_BK, k = e % TC_BK;
-    int cd = kb * TC_BK + k;
-    double x = (n < nh && cd < npp) ? t[(long)n * npp + cd] : 0.0;
+    int q = kb * TC_BK + k;
+    T_ x = 0;
+    if (n < nh && q < nl) {
+      int2 m = D.lad_mem[off + q];
+      T_ a = t[(long)n * npp + (m.x > 0 ? m.x : -m.x) - 1];
+      x = m.x > 0 ? a : -a;
+      if (m.y != 0) {
+        T_ b = t[(long)n * npp + (m.y > 0 ? m.y : -m.y) - 1];
+        x += m.y > 0 ? b : -b;
+      }
+    }
     __nv_bfloat16 h, l;
-    split_bf16(x, h, l);
+    split_bf16((double)x, h, l);
     hi[core_off(n, k)] = h;
     lo[core_off(n, k)] = l;
   }
@@ -310,8 +326,6 @@ struct MixedState {
   int4* pk = nullptr;
   long* pk_boff = nullptr;
   int npk = 0;
-  long* ch_boff = nullptr;  // per channel: k-block 0 of its t tiles (-1: no V_pppp block)
-  int* ch_npad = nullptr;
   uint32_t stage_bytes = 0;
   size_t smem = 0;
   int nst = 3, ksplit = 1;  // chosen by the autotuner
@@ -423,20 +437,17 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
   try {
     std::vector<TCItem> items;
     std::vector<int4> pk;
-    std::vector<long> pk_boff, ch_boff(ctx->nch, -1);
-    std::vector<int> ch_npad(ctx->nch, 0);
+    std::vector<long> pk_boff;
     long voff = 0, boff = 0;
     int max_npad = 16, max_nkb = 1;
     for (int c = 0; c < ctx->nch; c++) {
       if (!ctx->h_vpp[c]) continue;
-      int npp = ctx->h_npp[c], nh = ctx->h_nhh[c];
+      int npp = ctx->h_nlad[c], nh = ctx->h_nhh[c];  // the ladder basis is the GEMM's M and K
       int npad = std::max(16, (nh + 15) / 16 * 16);
       if (npad > 64) throw PnmError{PNM_EINVAL, "n_hh > 64 in one channel: tensor-core tile too small"};
       int nmt = (npp + TC_M - 1) / TC_M, nkb = (npp + TC_BK - 1) / TC_BK;
       max_npad = std::max(max_npad, npad);
       max_nkb = std::max(max_nkb, nkb);
-      ch_boff[c] = boff;
-      ch_npad[c] = npad;
       for (int mt = 0; mt < nmt; mt++) {
         TCItem t{};
         t.ch = c;
@@ -449,7 +460,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
         t.nhh = nh;
         t.voff = voff + (long)mt * nkb * 2 * (TC_M * TC_BK);
         t.boff = boff;
-        t.toff = ctx->h_t_off[c];
+        t.toff = ctx->h_s_off[c];
         t.sys = ctx->h_ch_sys[c];
         items.push_back(t);
       }
@@ -476,10 +487,6 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       CUDA_TRY(cudaMemcpyAsync(M->pk_boff, pk_boff.data(), sizeof(long) * pk_boff.size(),
                                cudaMemcpyHostToDevice, s));
     }
-    M->ch_boff = mdalloc<long>(ctx, ctx->nch);
-    M->ch_npad = mdalloc<int>(ctx, ctx->nch);
-    CUDA_TRY(cudaMemcpyAsync(M->ch_boff, ch_boff.data(), sizeof(long) * ctx->nch, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(M->ch_npad, ch_npad.data(), sizeof(int) * ctx->nch, cudaMemcpyHostToDevice, s));
     // padding rows/columns of the t tiles are never written again: they stay zero
     CUDA_TRY(cudaMemsetAsync(M->bt, 0, sizeof(__nv_bfloat16) * std::max<long>(boff, 1), s));
     ctx->d.t32_0 = mdalloc<float>(ctx, ctx->nt);
@@ -494,9 +501,9 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
       k_to_float<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.v_pphh, ctx->d.v32, ctx->nt);
     if (ctx->nvhh > 0)
       k_to_float<<<(unsigned)((ctx->nvhh + 255) / 256), 256, 0, s>>>(ctx->d.v_hhhh, ctx->d.vhh32, ctx->nvhh);
-    M->rpp32 = mdalloc<float>(ctx, (size_t)TC_MAX_SPLIT * ctx->nt);
+    M->rpp32 = mdalloc<float>(ctx, (size_t)TC_MAX_SPLIT * ctx->ns);
     // planes a channel with fewer k-blocks than the split never writes stay zero
-    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->ns, 1), s));
     M->xw32 = mdalloc<float>(ctx, ctx->nxt);
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
     M->xq32 = mdalloc<float>(ctx, ctx->nxt);
@@ -516,7 +523,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     if (smem_for(2) > 227 * 1024) throw PnmError{PNM_EINVAL, "tensor-core stage ring exceeds shared memory"};
     int max_st = TC_MAX_STAGES;
     while (smem_for(max_st) > 227 * 1024) max_st--;
-    CUDA_TRY(cudaFuncSetAttribute(k_pp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(max_st)));
+    smem_at_least(k_pp_tc, smem_for(max_st));
     CUDA_TRY(cudaStreamSynchronize(s));
     // Autotuner: time every (k-range split, ring depth) on this context's channels and keep
     // the fastest.  The ladder's cost does not depend on the amplitude values.
@@ -557,10 +564,10 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
         CUDA_TRY(cudaMemcpyAsync(trial, order.data(), sizeof(TCItem) * order.size(), cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(trial_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
         for (int w = 0; w < 2; w++)
-          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->nt, s);
+          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->ns, s);
         CUDA_TRY(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 5; rep++)
-          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->nt, s);
+          launch_pp_tc(trial, trial_off, grid, M, smem_for(nst), nst, ctx->ctl, ctx->ns, s);
         CUDA_TRY(cudaEventRecord(e1, s));
         CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0;
@@ -590,7 +597,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     plan_items(best_items, M->grid, &order, &off);
     CUDA_TRY(cudaMemcpyAsync(M->items, order.data(), sizeof(TCItem) * order.size(), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(M->cta_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->nt, 1), s));
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->ns, 1), s));
     CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
     delete M;
@@ -610,8 +617,12 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
     prof_end(ctx);
   }
   if (M->nitems > 0) {
+    // t tiles of the current amplitudes in the ladder basis, then the ladder (same stream)
+    prof_begin(ctx, KID_PACK);
+    k_pack_t<float><<<M->npk, 256, 0, s_pp>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
+    prof_end(ctx);
     prof_begin(ctx, KID_PP_TC);
-    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->nt, s_pp);
+    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->ns, s_pp);
     prof_end(ctx);
   }
   pnm_enqueue_stats(ctx, true);
@@ -620,24 +631,18 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
   prof_end(ctx);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
-  // the update also writes the BF16 hi/lo tiles of the new amplitudes for the next ladder
-  launch_update_mix(ctx, M->rpp32, M->hh32, M->xq32, use_cond, h, PackArgs{M->bt, M->xt32, M->ch_boff, M->ch_npad},
-                    M->ksplit, ctx->nt);
+  launch_update_mix(ctx, M->rpp32, M->hh32, M->xq32, use_cond, h, PackArgs{M->xt32}, M->ksplit, ctx->ns);
   prof_end(ctx);
 }
 
-// BF16 tiles and the FP32 copy of the start amplitudes (before the first mixed update).
+// The FP32 copies of the start amplitudes (before the first mixed update); the t tiles of the
+// ladder are packed at the start of every mixed update.
 void pnm_mixed_pack_initial(pnm_ctx* ctx) {
   MixedState* M = ctx->mixed;
   if (ctx->nt > 0)
     k_to_float_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
   if (ctx->nxt > 0)
     k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
-  if (M->npk > 0) {
-    prof_begin(ctx, KID_PACK);
-    k_pack_t<<<M->npk, 256, 0, ctx->stream>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
-    prof_end(ctx);
-  }
   CUDA_TRY(cudaGetLastError());
 }
 
@@ -672,24 +677,14 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   std::vector<double> out(ctx->nt, 0.0);
   if (precision == PNM_PREC_BF16X3) {
     MixedState* M = ctx->mixed;
-    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * ctx->nt, s));
-    if (M->npk > 0) k_pack_t<<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
-    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->nt, s);
-    CUDA_TRY(cudaGetLastError());
-    std::vector<float> f((size_t)TC_MAX_SPLIT * ctx->nt);
-    CUDA_TRY(cudaMemcpyAsync(f.data(), M->rpp32, sizeof(float) * f.size(), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    for (long z = 0; z < ctx->nt; z++) {
-      float acc = 0.0f;
-      for (int p = 0; p < M->ksplit; p++) acc += f[(size_t)p * ctx->nt + z];
-      out[z] = acc;
-    }
+    CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->ns, 1), s));
+    if (M->npk > 0) k_pack_t<double><<<M->npk, 256, 0, s>>>(M->pk, M->pk_boff, ctx->d, ctx->ctl, M->bt);
+    launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->ns, s);
+    pnm_lad_expand(ctx, M->rpp32, M->ksplit, ctx->ns, out.data());
   } else {
-    CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * ctx->nt, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
     pnm_launch_pp64(ctx, s);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemcpyAsync(out.data(), ctx->d.rpp, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    pnm_lad_expand(ctx, ctx->d.rpp, 1, ctx->ns, out.data());
   }
   int err = 0;
   CUDA_TRY(cudaMemcpy(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
@@ -725,19 +720,20 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
   unsigned nb = (unsigned)((ctx->nt + 255) / 256);
+  if (!ctx->expand_buf) ctx->expand_buf = ctx_alloc<double>(ctx, ctx->nt);  // the assembled term
   if (precision == PNM_PREC_BF16X3) {
     MixedState* M = ctx->mixed;
     k_to_float_cur<<<nb, 256, 0, s>>>(ctx->d, ctx->ctl, ctx->nt);
     if (ctx->nxt > 0)
       k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, s>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
     if (ctx->nx > 0) launch_ph_mix(ctx, M->xt32, M->xw32, M->xv132, M->xq32, s);
-    k_ph_assemble<float><<<nb, 256, 0, s>>>(ctx->d, M->xq32, ctx->nt, ctx->d.rpp);
+    k_ph_assemble<float><<<nb, 256, 0, s>>>(ctx->d, M->xq32, ctx->nt, ctx->expand_buf);
   } else {
     if (ctx->nx > 0) launch_ph64(ctx, s);
-    k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->d.rpp);
+    k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->expand_buf);
   }
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemcpyAsync(r, ctx->d.rpp + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(r, ctx->expand_buf + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   int err = 0;
   CUDA_TRY(cudaMemcpy(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));

@@ -657,7 +657,7 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
     M->q = ctx_alloc<float>(ctx, NPARAM);
     M->pw = ctx_alloc<__nv_bfloat16>(ctx, PW_TOTAL);
     M->err = ctx_alloc<int>(ctx, 1);
-    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+    smem_at_least(k_mlp_tc, MLP_SMEM);
     CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   }
   float* w = ctx_alloc<float>(ctx, NPARAM);
@@ -767,7 +767,7 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use
       __nv_bfloat16* pw = xalloc<__nv_bfloat16>(PW_TOTAL, sc.owned);
       int* err = xalloc<int>(1, sc.owned);
       CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-      CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+      smem_at_least(k_mlp_tc, MLP_SMEM);
     CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(q, pw);
       tc_infer(s, dX, n, q, pw, MlpOut{dY, nullptr, nullptr, nullptr, nullptr, 0, 1.0f}, err);

@@ -25,11 +25,16 @@ struct pnm_ctx {
   // sizes
   int nsp_total = 0, nch = 0, nx = 0, nrows = 0, n_hh_pairs = 0, n_pp_pairs = 0;
   long nt = 0, nvpp = 0, nvhh = 0, nxt = 0, nxc = 0;
-  int max_x_dim = 0, max_npp = 0;
+  long ns = 0;  // elements of the ladder layout (n_hh x n_lad over the channels with V_pppp)
+  int max_x_dim = 0, max_npp = 0, max_nlad = 0;
+  int2* lad_rows = nullptr;  // (channel, ij) rows of the channels with V_pppp (ladder gather)
+  int n_lad_rows = 0;
 
   // host copies of the channel metadata
   std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_vpp;
-  std::vector<long> h_t_off, h_vpp_off, h_x_t_off;
+  std::vector<long> h_t_off, h_x_t_off;
+  std::vector<int> h_nlad;               // ladder basis size per channel (0: no V_pppp block)
+  std::vector<long> h_s_off, h_vl_off;   // ladder-layout and ladder-V offsets per channel
   std::vector<int2> h_rows;
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
 
@@ -53,7 +58,8 @@ struct pnm_ctx {
   int *row_lo_d = nullptr, *row_hi_d = nullptr, *lut_off_d = nullptr;  // per system
   LoopCtl* ctl = nullptr;     // device
   double* small = nullptr;    // device scratch for single-value queries
-  double* mbpt3_buf = nullptr;  // per-row partials and per-system results of pnm_mbpt3
+  double* mbpt3_buf = nullptr;
+  double* expand_buf = nullptr;  // the pp ladder in the amplitude layout (operator call)  // per-row partials and per-system results of pnm_mbpt3
   SysCtl* sysctl = nullptr;   // device, one per system
   double* hist = nullptr;     // device, (hist_cap) per system
   int hist_cap = 0;
@@ -103,6 +109,14 @@ inline std::string pnm_shape_key(const pnm_ctx* ctx) {
 // loop then maps no new memory).  pnm_pool_alloc throws PNM_ENOMEM.
 void* pnm_pool_alloc(cudaStream_t s, size_t bytes);
 void pnm_pool_free(cudaStream_t s, void* p);
+// Raise a kernel's dynamic shared-memory limit (a property of the function, shared by every
+// context of the process) to at least `bytes`; never lowers it, so a context built later with
+// smaller channels cannot break the launches of an earlier one.
+void pnm_smem_at_least(const void* func, size_t bytes);
+template <typename F>
+void smem_at_least(F* func, size_t bytes) {
+  pnm_smem_at_least((const void*)func, bytes);
+}
 // An allocation on the context stream recorded in ctx->owned (released by pnm_destroy).
 void* pnm_ctx_alloc(pnm_ctx* ctx, size_t bytes);
 template <typename T>
@@ -119,6 +133,9 @@ void pnm_free_mixed(pnm_ctx* ctx);
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_terms(pnm_ctx* ctx, int terms);
 void pnm_mbpt3_all(pnm_ctx* ctx, double* out);
+// The pp ladder from its ladder layout (planes summed) into host memory in the amplitude layout.
+void pnm_lad_expand(pnm_ctx* ctx, const float* rs, int planes, long pstride, double* host_out);
+void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, double* host_out);
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_mixed(pnm_ctx* ctx);
 void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);

@@ -64,6 +64,14 @@ struct DevState {
   // direct channels
   int *ch_sys, *ch_key, *ch_nhh, *ch_npp, *ch_hh_off, *ch_pp_off, *ch_vpp;
   long *ch_t_off, *ch_vpp_off, *ch_vhh_off;
+  // ladder basis of the pp ladder (channels with a V_pppp block): n_lad vectors per channel,
+  // ladder-layout blocks (n_hh x n_lad) at ch_s_off; lad_map per pp pair: its vector and sign
+  // as +-(index + 1); lad_mem per vector (at the channel's pp offset): its one or two pairs as
+  // +-(position + 1), 0 for no second pair
+  int* ch_nlad;
+  long* ch_s_off;
+  int* lad_map;
+  int2* lad_mem;
   int2 *hh_pair, *pp_pair;
   // rows (channel, ij) for the update and energy partials
   int2* row_item;        // (channel, ij)
@@ -79,7 +87,7 @@ struct DevState {
   int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q
   int *occ_off, *occ_idx; // per state: pair indices (pp for particles, hh for holes)
   // blocks
-  double *v_pphh, *v_pppp, *v_hhhh, *x_v1, *x_w;
+  double *v_pphh, *v_pppp, *v_hhhh, *x_v1, *x_w;  // v_pppp: n_lad x n_lad per channel, ladder basis
   double *den, *inv_den;  // eps_i + eps_j - eps_a - eps_b per amplitude, and its reciprocal
   // iteration state
   double *t0, *t1;       // double buffer, parity = iteration & 1
@@ -87,7 +95,8 @@ struct DevState {
   // FP32 intermediates of the mixed-precision iteration (null until it is first prepared):
   // v_pphh and v_hhhh copies, chi_hh, the one-body row/column sums and the one-body terms
   float *v32, *vhh32, *chi32, *sij32, *sab32, *dchi32;
-  double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;
+  double *rpp, *chi_hh, *dchi, *sab, *sij, *xq;  // rpp: pp ladder in the ladder layout
+  double* s64;           // amplitudes in the ladder basis (input of the FP64 pp ladder)
   double *eparts, *rparts;
   // per-system loop state (converged systems are frozen: later steps skip their work)
   const struct SysCtl* sysctl;
@@ -170,11 +179,16 @@ constexpr int PH_SMALL_DIM = 32, PH_WARP_DIM = 16;
 // Where the mixed update writes the BF16 hi/lo copy of the new amplitudes (the B operand
 // tiles of the tensor-core pp ladder).  bt == nullptr: no copy.
 struct PackArgs {
-  __nv_bfloat16* bt;
   float* xt;            // FP32 T of the ph term in the cross-channel layout (scattered), or null
-  const long* ch_boff;  // per channel: element offset of its k-block 0, -1 if not packed
-  const int* ch_npad;   // per channel: n_hh padded to the MMA N
 };
+
+// pp ladder of amplitude (ij, ab) of channel c from its ladder-layout value (planes summed by
+// the caller where there are several).
+__device__ __forceinline__ long lad_index(const DevState& D, int c, int ij, int ab, int& sign) {
+  int m = D.lad_map[D.ch_pp_off[c] + ab];
+  sign = m > 0 ? 1 : -1;
+  return D.ch_s_off[c] + (long)ij * D.ch_nlad[c] + ((m > 0 ? m : -m) - 1);
+}
 
 // --------------------------------------------------------------------- device helpers
 

@@ -552,52 +552,116 @@ __global__ void k_den(int row0, const int2* __restrict__ row_item, const int* __
   }
 }
 
-// <ab|v|cd> for channels with a V_pppp block; one CTA per (channel, row cd).
-__global__ void k_v_pppp(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
-                         const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
-                         const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
-                         const double* __restrict__ lut, double* __restrict__ v_pppp) {
-  int2 it = items[blockIdx.x];
-  int c = it.x, cd = it.y;
-  int npp = ch_npp[c];
-  int2 pc = pp_pair[ch_pp_off[c] + cd];
-  char4 sc = nvec[pc.x], sd = nvec[pc.y];
-  long base = ch_vpp_off[c] + (long)cd * npp;
-  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
-    int2 pb = pp_pair[ch_pp_off[c] + ab];
-    v_pppp[base + ab] = v_minnesota_as(nvec[pb.x], nvec[pb.y], sc, sd, lut);
+// ---------------------------------------------------------------------- ladder basis
+// For two neutrons <ab|v|cd> acts only on the spin singlet: with each pp pair of an S_z = 0
+// channel written with its spin-up particle first (sign e = -1 when the stored order is the
+// other one), the element e_x e_z <x|v|z> depends on the spatial pair of z only through the
+// two Gaussians of n_u - n_u' and n_u - n_d', so it is the same for z and its partner z'
+// (spatial labels of the two spins exchanged).  The pp ladder R_x = sum_z <x|v|z> t_z is then
+// R_x = e_x sum_c W(c(x), c) s_c with one vector per partner couple, s_c = e_z t_z + e_z' t_z'
+// and W(c, c') = e e' <rep c|v|rep c'>: a quarter of the elements and of the products.  Other
+// channels (systems with protons) keep one vector per pair.
+// One CTA (256 threads) per channel with a V_pppp block; dynamic shared memory holds three
+// ints per pair: partner position, sign e, rank of a representative.
+constexpr int LAD_THREADS = 256;
+__global__ void __launch_bounds__(LAD_THREADS) k_ladder_basis(
+    const int* __restrict__ chans, int species, const int* __restrict__ ch_pp_off,
+    const int* __restrict__ ch_npp, const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
+    int N, int nsp, int r, const int* __restrict__ idx3, const int* __restrict__ pos_pp,
+    int* __restrict__ lad_map, int2* __restrict__ lad_mem, int* __restrict__ ch_nlad) {
+  extern __shared__ int lsm[];
+  __shared__ int warp_tot[LAD_THREADS / 32];
+  __shared__ int base_sh;
+  int c = chans[blockIdx.x];
+  int off = ch_pp_off[c], npp = ch_npp[c];
+  if (species != 1) {  // no reduction: one vector per pair
+    for (int x = threadIdx.x; x < npp; x += blockDim.x) {
+      lad_map[off + x] = x + 1;
+      lad_mem[off + x] = make_int2(x + 1, 0);
+    }
+    if (threadIdx.x == 0) ch_nlad[c] = npp;
+    return;
   }
+  int* part = lsm;
+  int* sgn = lsm + npp;
+  int* rnk = lsm + 2 * npp;
+  int np = nsp - N;
+  for (int x = threadIdx.x; x < npp; x += blockDim.x) {
+    int2 pr = pp_pair[off + x];
+    char4 sa = nvec[pr.x], sb = nvec[pr.y];
+    bool a_up = sa.w > 0;
+    char4 su = a_up ? sa : sb, sd = a_up ? sb : sa;
+    sgn[x] = a_up ? 1 : -1;
+    int u2 = lookup_state(idx3, r, sd.x, sd.y, sd.z, 1, 1);   // spin up at the down momentum
+    int d2 = lookup_state(idx3, r, su.x, su.y, su.z, -1, 1);  // spin down at the up momentum
+    int p1 = min(u2, d2), p2 = max(u2, d2);
+    part[x] = (p1 < N) ? x : pos_pp[(size_t)(p1 - N) * np + (p2 - N)];
+  }
+  if (threadIdx.x == 0) base_sh = 0;
+  __syncthreads();
+  // rank of each representative (partner position >= own position) in pair order
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int x0 = 0; x0 < npp; x0 += blockDim.x) {
+    int x = x0 + threadIdx.x;
+    bool rep = x < npp && part[x] >= x;
+    unsigned bal = __ballot_sync(0xffffffffu, rep);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = base_sh;
+    for (int w = 0; w < warp; w++) before += warp_tot[w];
+    if (rep) rnk[x] = before + __popc(bal & ((1u << lane) - 1u));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < LAD_THREADS / 32; w++) tot += warp_tot[w];
+      base_sh += tot;
+    }
+    __syncthreads();
+  }
+  for (int x = threadIdx.x; x < npp; x += blockDim.x) {
+    int px = part[x];
+    int rk = px >= x ? rnk[x] : rnk[px];
+    lad_map[off + x] = (rk + 1) * sgn[x];
+    if (px >= x) lad_mem[off + rk] = make_int2((x + 1) * sgn[x], px != x ? (px + 1) * sgn[px] : 0);
+  }
+  if (threadIdx.x == 0) ch_nlad[c] = base_sh;
 }
 
-// The same elements, VPP_ROWS rows of one channel per CTA: the channel's pair states and the
-// LUT are staged in shared memory once, so the inner loop gathers from shared memory only.
-constexpr int VPP_ROWS = 16;
-__global__ void __launch_bounds__(256) k_v_pppp_rows(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
-                                                     const int* __restrict__ ch_npp, const long* __restrict__ ch_vpp_off,
-                                                     const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
-                                                     const double* __restrict__ lut, int lut_len,
-                                                     double* __restrict__ v_pppp) {
+// W(c, c') = e e' <rep c|v|rep c'> for VLAD_ROWS rows of one channel per CTA; the channel's
+// representative pair states, their signs and the LUT are staged in shared memory.
+constexpr int VLAD_ROWS = 16;
+__global__ void __launch_bounds__(256) k_v_ladder(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
+                                                  const int* __restrict__ ch_nlad, const long* __restrict__ ch_vl_off,
+                                                  const int2* __restrict__ lad_mem, const int2* __restrict__ pp_pair,
+                                                  const char4* __restrict__ nvec, const double* __restrict__ lut,
+                                                  int lut_elems, double* __restrict__ v_lad) {
   extern __shared__ __align__(16) unsigned char vsm[];
   double* slut = reinterpret_cast<double*>(vsm);
-  char4* sa = reinterpret_cast<char4*>(slut + lut_len);
   int2 it = items[blockIdx.x];
-  int c = it.x, cd0 = it.y;
-  int npp = ch_npp[c];
-  char4* sb = sa + npp;
-  const int2* pairs = pp_pair + ch_pp_off[c];
-  for (int m = threadIdx.x; m < lut_len; m += blockDim.x) slut[m] = lut[m];
-  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
-    int2 p = pairs[ab];
-    sa[ab] = nvec[p.x];
-    sb[ab] = nvec[p.y];
+  int c = it.x, r0 = it.y;
+  int nl = ch_nlad[c], off = ch_pp_off[c];
+  char4* sa = reinterpret_cast<char4*>(slut + lut_elems);
+  char4* sb = sa + nl;
+  int* sg = reinterpret_cast<int*>(sb + nl);
+  for (int m = threadIdx.x; m < lut_elems; m += blockDim.x) slut[m] = lut[m];
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+    int m = lad_mem[off + q].x;
+    int pos = (m > 0 ? m : -m) - 1;
+    int2 pr = pp_pair[off + pos];
+    sa[q] = nvec[pr.x];
+    sb[q] = nvec[pr.y];
+    sg[q] = m > 0 ? 1 : -1;
   }
   __syncthreads();
-  int cd1 = min(cd0 + VPP_ROWS, npp);
-  for (int cd = cd0; cd < cd1; cd++) {
-    char4 sc = sa[cd], sd = sb[cd];
-    double* out = v_pppp + ch_vpp_off[c] + (long)cd * npp;
-    for (int ab = threadIdx.x; ab < npp; ab += blockDim.x)
-      out[ab] = v_minnesota_as(sa[ab], sb[ab], sc, sd, slut);
+  int r1 = min(r0 + VLAD_ROWS, nl);
+  for (int row = r0; row < r1; row++) {
+    char4 sc = sa[row], sd = sb[row];
+    int g = sg[row];
+    double* out = v_lad + ch_vl_off[c] + (long)row * nl;
+    for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+      double v = v_minnesota_as(sa[q], sb[q], sc, sd, slut);
+      out[q] = g * sg[q] > 0 ? v : __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+    }
   }
 }
 
@@ -819,11 +883,11 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   // ---- channel metadata and offsets (host prefix sums over channels)
   std::vector<int> h_ch_sys, h_key, h_nhh, h_npp, h_hh_off, h_pp_off, h_vpp;
   std::vector<long> h_t_off, h_vpp_off, h_vhh_off;
-  std::vector<int2> h_rows, h_vpp_items, h_vpp_chunks;
-  int vpp_max_npp = 0;
+  std::vector<int2> h_rows;
+  std::vector<std::vector<int>> h_lad_chans(nsys);  // per system: channels with a V_pppp block
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
   std::vector<long> h_x_t_off, h_x_c_off, h_x_w_off;
-  long t_acc = 0, vpp_acc = 0, vhh_acc = 0, xt_acc = 0, xc_acc = 0;
+  long t_acc = 0, vhh_acc = 0, xt_acc = 0, xc_acc = 0;
   int hh_acc = 0, pp_acc = 0, ph_acc = 0, hp_acc = 0;
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
@@ -847,13 +911,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       int slot = sys[k].species == 1 ? K % 3 : K % 9;
       bool has_vpp = sys[k].species == 1 ? slot == 1 : !(slot / 3 != 1 && slot % 3 != 1);
       h_vpp.push_back(has_vpp ? 1 : 0);
-      h_vpp_off.push_back(has_vpp ? vpp_acc : -1);
-      if (has_vpp) {
-        for (int cd = 0; cd < X.dnpp[c]; cd++) h_vpp_items.push_back(make_int2(g, cd));
-        for (int cd = 0; cd < X.dnpp[c]; cd += VPP_ROWS) h_vpp_chunks.push_back(make_int2(g, cd));
-        vpp_max_npp = std::max(vpp_max_npp, X.dnpp[c]);
-        vpp_acc += (long)X.dnpp[c] * X.dnpp[c];
-      }
+      if (has_vpp) h_lad_chans[k].push_back(g);
       for (int ij = 0; ij < X.dnhh[c]; ij++) h_rows.push_back(make_int2(g, ij));
       hh_acc += X.dnhh[c];
       pp_acc += X.dnpp[c];
@@ -884,7 +942,6 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   ctx->nch = (int)h_key.size();
   ctx->nx = (int)h_x_nph.size();
   ctx->nt = t_acc;
-  ctx->nvpp = vpp_acc;
   ctx->nvhh = vhh_acc;
   ctx->nxt = xt_acc;
   ctx->nxc = xc_acc;
@@ -896,7 +953,6 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   ctx->h_nhh = h_nhh;
   ctx->h_npp = h_npp;
   ctx->h_t_off = h_t_off;
-  ctx->h_vpp_off = h_vpp_off;
   ctx->h_vpp = h_vpp;
   ctx->h_rows = h_rows;
   ctx->h_x_nph = h_x_nph;
@@ -916,7 +972,9 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   D.ch_pp_off = dalloc<int>(C, ctx->owned, s);
   D.ch_vpp = dalloc<int>(C, ctx->owned, s);
   D.ch_t_off = dalloc<long>(C, ctx->owned, s);
-  D.ch_vpp_off = dalloc<long>(C, ctx->owned, s);
+  D.ch_vpp_off = dalloc<long>(C, ctx->owned, s);  // ladder V blocks, set once the basis is known
+  D.ch_nlad = dalloc<int>(C, ctx->owned, s);
+  D.ch_s_off = dalloc<long>(C, ctx->owned, s);
   D.ch_vhh_off = dalloc<long>(C, ctx->owned, s);
   D.row_item = dalloc<int2>(ctx->nrows, ctx->owned, s);
   D.x_nph = dalloc<int>(NX, ctx->owned, s);
@@ -941,7 +999,6 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   h2d(D.ch_pp_off, h_pp_off, s);
   h2d(D.ch_vpp, h_vpp, s);
   h2d(D.ch_t_off, h_t_off, s);
-  h2d(D.ch_vpp_off, h_vpp_off, s);
   h2d(D.ch_vhh_off, h_vhh_off, s);
   h2d(D.row_item, h_rows, s);
   h2d(D.x_nph, h_x_nph, s);
@@ -961,13 +1018,13 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   D.v_pphh = dalloc<double>(t_acc, ctx->owned, s);
   D.den = dalloc<double>(t_acc, ctx->owned, s);
   D.inv_den = dalloc<double>(t_acc, ctx->owned, s);
-  D.v_pppp = dalloc<double>(vpp_acc, ctx->owned, s);
+  D.lad_map = dalloc<int>(pp_acc, ctx->owned, s);
+  D.lad_mem = dalloc<int2>(pp_acc, ctx->owned, s);
   D.v_hhhh = dalloc<double>(vhh_acc, ctx->owned, s);
   D.x_v1 = dalloc<double>(xc_acc, ctx->owned, s);
   D.x_w = dalloc<double>(xt_acc, ctx->owned, s);
   D.t0 = dalloc<double>(t_acc, ctx->owned, s);
   D.t1 = dalloc<double>(t_acc, ctx->owned, s);
-  D.rpp = dalloc<double>(t_acc, ctx->owned, s);
   D.chi_hh = dalloc<double>(vhh_acc, ctx->owned, s);
   D.sab = dalloc<double>(pp_acc, ctx->owned, s);
   D.sij = dalloc<double>(hh_acc, ctx->owned, s);
@@ -1041,33 +1098,66 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
                              D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, nullptr, D.occ_off,
                              D.occ_idx);
   }
-  // V_pppp for channels with a V_pppp block, one launch per system (the LUT differs per system): chunks of
-  // VPP_ROWS rows with the channel staged in shared memory, or one row per CTA when a channel
-  // does not fit
-  if (!h_vpp_items.empty()) {
+  // ---- ladder basis of the pp ladder (pairs and the partner table of each system are ready)
+  CUDA_TRY(cudaMemsetAsync(D.ch_nlad, 0, sizeof(int) * std::max(C, 1), s));
+  int max_npp = 0;
+  for (int c = 0; c < C; c++)
+    if (h_vpp[c]) max_npp = std::max(max_npp, h_npp[c]);
+  size_t lsm = 3 * sizeof(int) * (size_t)max_npp;
+  if (lsm > 200 * 1024) throw PnmError{PNM_EINVAL, "channel too large for the ladder basis"};
+  smem_at_least(k_ladder_basis, lsm);
+  for (int k = 0; k < nsys; k++) {
+    if (h_lad_chans[k].empty()) continue;
+    SysInfo& S = sys[k];
+    int* lc = dalloc<int>(h_lad_chans[k].size(), scr[k].owned, s);
+    h2d(lc, h_lad_chans[k], s);
+    k_ladder_basis<<<(unsigned)h_lad_chans[k].size(), LAD_THREADS, lsm, s>>>(
+        lc, S.species, D.ch_pp_off, D.ch_npp, D.pp_pair, D.nvec, S.N, S.nsp, S.r, scr[k].idx3,
+        scr[k].pos_pp, D.lad_map, D.lad_mem, D.ch_nlad);
+    CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<int> h_nlad = d2h(D.ch_nlad, C, s);
+  std::vector<long> h_s_off(C, 0), h_vl_off(C, -1);
+  long s_acc = 0, vl_acc = 0;
+  int max_nlad = 0;
+  std::vector<int2> vl_items;
+  for (int c = 0; c < C; c++) {
+    h_s_off[c] = s_acc;
+    if (!h_vpp[c]) continue;
+    h_vl_off[c] = vl_acc;
+    s_acc += (long)h_nhh[c] * h_nlad[c];
+    vl_acc += (long)h_nlad[c] * h_nlad[c];
+    max_nlad = std::max(max_nlad, h_nlad[c]);
+    for (int r0 = 0; r0 < h_nlad[c]; r0 += VLAD_ROWS) vl_items.push_back(make_int2(c, r0));
+  }
+  ctx->h_nlad = h_nlad;
+  ctx->h_s_off = h_s_off;
+  ctx->h_vl_off = h_vl_off;
+  ctx->ns = s_acc;
+  ctx->nvpp = vl_acc;
+  h2d(D.ch_s_off, h_s_off, s);
+  h2d(D.ch_vpp_off, h_vl_off, s);
+  D.v_pppp = dalloc<double>(vl_acc, ctx->owned, s);
+  D.rpp = dalloc<double>(s_acc, ctx->owned, s);
+  D.s64 = dalloc<double>(s_acc, ctx->owned, s);
+  // ladder V, one launch per system (the LUT differs per system)
+  if (!vl_items.empty()) {
     int max_lut = 0;
     for (const SysInfo& S : sys) max_lut = std::max(max_lut, S.lut_len * (S.species == 1 ? 1 : 3));
-    size_t smem = sizeof(double) * max_lut + 2 * sizeof(char4) * (size_t)vpp_max_npp;
-    bool staged = smem <= 200 * 1024;
-    const std::vector<int2>& hv = staged ? h_vpp_chunks : h_vpp_items;
-    int2* items = dalloc<int2>(hv.size(), scr[0].owned, s);
-    h2d(items, hv, s);
-    if (staged)
-      CUDA_TRY(cudaFuncSetAttribute(k_v_pppp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    size_t smem = sizeof(double) * max_lut + (2 * sizeof(char4) + sizeof(int)) * (size_t)max_nlad;
+    if (smem > 200 * 1024) throw PnmError{PNM_EINVAL, "channel too large for the staged ladder V"};
+    smem_at_least(k_v_ladder, smem);
+    int2* items = dalloc<int2>(vl_items.size(), scr[0].owned, s);
+    h2d(items, vl_items, s);
     size_t lo = 0;
     for (int k = 0; k < nsys; k++) {
       size_t hi = lo;
-      while (hi < hv.size() && h_ch_sys[hv[hi].x] == k) hi++;
-      if (hi > lo) {
-        if (staged)
-          k_v_pppp_rows<<<(unsigned)(hi - lo), 256, smem, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
-                                                               D.pp_pair, D.nvec, D.lut + sys[k].lut_off,
-                                                               sys[k].lut_len * (sys[k].species == 1 ? 1 : 3),
-                                                               D.v_pppp);
-        else
-          k_v_pppp<<<(unsigned)(hi - lo), 256, 0, s>>>(items + lo, D.ch_pp_off, D.ch_npp, D.ch_vpp_off,
-                                                      D.pp_pair, D.nvec, D.lut + sys[k].lut_off, D.v_pppp);
-      }
+      while (hi < vl_items.size() && h_ch_sys[vl_items[hi].x] == k) hi++;
+      if (hi > lo)
+        k_v_ladder<<<(unsigned)(hi - lo), 256, smem, s>>>(items + lo, D.ch_pp_off, D.ch_nlad, D.ch_vpp_off,
+                                                          D.lad_mem, D.pp_pair, D.nvec, D.lut + sys[k].lut_off,
+                                                          sys[k].lut_len * (sys[k].species == 1 ? 1 : 3),
+                                                          D.v_pppp);
       lo = hi;
     }
   }
