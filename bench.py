@@ -81,7 +81,7 @@ MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload
 # (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {}
+TRAFFIC = {"k_pp64": 3.888e8, "k_pp_tc": 2.594e8, "k_update_mix": 3.446e8}
 ALPHA = 0.5
 
 
@@ -609,9 +609,11 @@ def run_ours(a):
         np.save(a.save_model, _model["blob"])
 
     # e2e through the public API from host inputs (the trained model is an input, like V's parameters)
+    # one untimed end-to-end pass first (the memory pool grows to hold a second context beside
+    # the timed one), then the timed passes
     e2e_ms = []
     n_t = 0
-    for _ in range(max(1, min(a.steps, 10))):
+    for k in range(1 + max(1, min(a.steps, 10))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = make_context(P, a.workload, stream)
@@ -619,7 +621,8 @@ def run_ours(a):
         n_t = sum(c2.get_amplitudes(s).size for s in range(c2.nsys))
         c2.close()
         torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if k > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
 
     # per-kernel durations from one profiled host-driven solve of the same work
     ctx.set_profiling(True)
