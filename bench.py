@@ -173,25 +173,32 @@ def dist_setup():
 
 
 def chan_sizes(ctx):
-    """Channel sizes of every system of a context, concatenated."""
+    """Channel sizes of every system of a context, concatenated; for cross channels also the
+    sign of S_z = s_a - s_i (the ph kernels form S_z > 0 channels in full and mirror them onto
+    S_z < 0, and S_z = 0 channels as half-size sum and difference blocks)."""
     import numpy as np
-    nhh, npp, nlad, nph, nhp = [], [], [], [], []
+    nhh, npp, nlad, nph, nhp, xsz = [], [], [], [], [], []
     for s in range(ctx.nsys):
         _, sizes, _ = ctx.channels(s, 0)
-        _, xs, _ = ctx.channels(s, 1)
+        _, xs, xpairs = ctx.channels(s, 1)
+        nv, _, _ = ctx.basis(s)
+        w = nv[:, 3].astype(int)
+        spin = np.where(np.abs(w) == 1, w, w - 4 * np.sign(w))
+        first = np.concatenate([[0], np.cumsum(xs[:, 0])[:-1]]).astype(int)
         nhh.append(sizes[:, 0])
         npp.append(sizes[:, 1])
         nlad.append(ctx.ladder_sizes(s))
         nph.append(xs[:, 0])
         nhp.append(xs[:, 1])
+        xsz.append(np.sign(spin[xpairs[first, 0]] - spin[xpairs[first, 1]]))
     cat = lambda v: np.concatenate(v).astype(float)
-    return cat(nhh), cat(npp), cat(nlad), cat(nph), cat(nhp)
+    return cat(nhh), cat(npp), cat(nlad), cat(nph), cat(nhp), cat(xsz)
 
 
 def algorithmic_cost(ctx, kernel):
     """(bytes, flops) per launch of a kernel, from the channel sizes of all systems of the
     context: every array the kernel must touch, counted once."""
-    nhh, npp, nlad, nph, nhp = chan_sizes(ctx)
+    nhh, npp, nlad, nph, nhp, xsz = chan_sizes(ctx)
     nt = float((nhh * npp).sum())
     if kernel in ("k_pp64", "k_pp_tc"):
         # the ladder in its basis (pnm_ladder_sizes): V block n_lad x n_lad, operand and result
@@ -202,15 +209,19 @@ def algorithmic_cost(ctx, kernel):
         byts = float((nlad ** 2).sum()) * vb + float((nhh * nlad).sum()) * (tb + rb)
         flops = 2.0 * float((nhh * nlad ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
         return byts, flops
-    if kernel == "k_ph64":
-        # index map and gathered t, W, V1, Q
-        byts = float((nph * nhp).sum()) * (4 + 8 + 8 + 8) + float((nhp * nhp).sum()) * 8
-        flops = 2.0 * float((nhp * nhp * nph + nph * nhp * nhp).sum())
-        return byts, flops
-    if kernel == "k_ph32":
-        # T (scattered by the update), W, V1 read; Q written
-        byts = float((nph * nhp).sum()) * (4 + 4 + 4) + float((nhp * nhp).sum()) * 4
-        flops = 2.0 * float((nhp * nhp * nph + nph * nhp * nhp).sum())
+    if kernel in ("k_ph64", "k_ph32"):
+        # S_z > 0: T (index map + gathered t, or the scattered FP32 copy), W and V1 read, Q
+        # written to the channel and its mirror; S_z = 0: the spin-up half of the rows of T, W
+        # and V1 read, Q written in full; 2 products of (rows x cols x cols) per block, the
+        # S_z = 0 blocks at half size, two of them
+        e = 8.0 if kernel == "k_ph64" else 4.0
+        tin = (4 + 8) if kernel == "k_ph64" else 4
+        full, half = xsz > 0, xsz == 0
+        el, vv = nph * nhp, nhp * nhp
+        byts = (float(el[full].sum()) * (tin + e + 2 * e) + float(vv[full].sum()) * e
+                + float(el[half].sum()) * ((tin + e) / 2 + e) + float(vv[half].sum()) * e / 2)
+        flops = (4.0 * float((nph * nhp * nhp)[full].sum())
+                 + 2 * 4.0 * float(((nph / 2) * (nhp / 2) ** 2)[half].sum()))
         return byts, flops
     if kernel == "k_update":
         # t, v, eps, 1/eps, qmap, rpp, four Q values, t_next

@@ -58,6 +58,12 @@ typedef struct {
 #define PNM_INIT_KEEP 2   /* start from the amplitudes currently held (pnm_set_amplitudes) */
 #define PNM_INIT_MLP 3    /* learned start (pnm_mlp_set_model); falls back to MBPT2 if the
                              iteration from it does not converge */
+/* Kept and learned starts are first symmetrised under the global spin flip F (every state to
+ * the one of opposite spin): t <- (t + F t)/2.  F commutes with H and leaves the
+ * spin-saturated reference unchanged, so the solution is flip-symmetric, and the iteration
+ * forms the ph term for flip-symmetric amplitudes only (S_z < 0 cross channels are mirrors of
+ * S_z > 0 ones; S_z = 0 channels split into half-size sum and difference blocks).  MBPT2 and
+ * zero starts are symmetric already. */
 
 /* Terms the iteration keeps (Sec. "Coupled cluster theory"):
  *   PNM_TERMS_FULL    Eq. (ccd3);
@@ -250,7 +256,8 @@ int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, d
  * (the linear ph term and the quadratic ph term of Eq. ccd3 through the intermediate of Sec.
  * "Developing a CCD code"), computed in the cross-coupled channels (n_a - n_i, s_a - s_i):
  * FP64 kernels, or the mixed-precision ones (FP32 operands and products).  t and r hold n restricted
- * amplitudes of system `sys` in library order.  Resets the solver's iteration state. */
+ * amplitudes of system `sys` in library order; r is the term of the flip-symmetric part
+ * (t + F t)/2 of t (see PNM_INIT_KEEP).  Resets the solver's iteration state. */
 int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, double *r, size_t n);
 
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:

@@ -108,111 +108,43 @@ __global__ void k_dchi(DevState D, int nsp_total) {
 }
 
 // ----------------------------------------------------------------------------- ph term
-// One CTA per cross channel.  Shared buffers, dimensions padded to multiples of 4 with zeros:
-//   Ts[u][s] = T[(a,i)=u][(k,c)=s]          (P4 x H4)
-//   Xt[u][r] = W[r][u] for the first contraction, then T[r][u] transposed for the second
-//   Cs[r][s] = C[r][s]                       (H4 x H4)
-// Each thread accumulates 4 x 4 outputs; per k step it reads two 4-vectors from shared.
-template <typename T_>
-struct Vec4;
+// Global spin flip: Q is computed for the cross channels with S_z > 0 (and written to their
+// mirrors with S_z < 0 as well) and for the S_z = 0 channels on their spin-up half.  In an
+// S_z = 0 channel, with rows ordered (spin-up rows u, their flips F u) and columns alike,
+// every matrix of the term has the block form [[A, B], [B, A]] (A = M[u][v], B = M[u][F v]);
+// products of such matrices are formed from the half-size sums A + B and differences A - B,
+//   (A_1 + B_1)(A_2 + B_2) = A_3 + B_3,  (A_1 - B_1)(A_2 - B_2) = A_3 - B_3,
+// which is a quarter of the flops of the full channel.
+template <typename T_, int TS>
+struct VecT;
 template <>
-struct Vec4<float> {
-  __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
-    float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+struct VecT<double, 2> {
+  __device__ __forceinline__ static void ld(const double* p, double (&v)[2]) {
+    double2 a = *reinterpret_cast<const double2*>(p);
+    v[0] = a.x; v[1] = a.y;
   }
 };
 template <>
-struct Vec4<double> {
+struct VecT<double, 4> {
   __device__ __forceinline__ static void ld(const double* p, double (&v)[4]) {
     double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
-
-// The two contractions of a cross channel from the staged Ts (T) and Xt (W^T); writes Q.
-//   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_{(e,l)} <kl|v|ce> t_lj^eb   (quad false: <kb|v|cj>)
-//   Q[(a,i)][(j,b)] = sum_{(k,c)} t_ik^ac C[(k,c)][(j,b)]
-template <typename T_, int NT>
-__device__ __forceinline__ void ph_contract(T_* Ts, T_* Xt, T_* Cs, int nph, int nhp, int P4, int H4,
-                                            const T_* __restrict__ v1, T_* __restrict__ q, bool quad) {
-  if (!quad) {
-    // linear term only: C = <kb|v|cj>, zero-padded
-    for (int e = threadIdx.x; e < H4 * H4; e += NT) {
-      int r = e / H4, c2 = e % H4;
-      Cs[e] = (r < nhp && c2 < nhp) ? v1[(long)r * nhp + c2] : (T_)0;
-    }
-    __syncthreads();
+template <>
+struct VecT<float, 2> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[2]) {
+    float2 a = *reinterpret_cast<const float2*>(p);
+    v[0] = a.x; v[1] = a.y;
   }
-  // Small channels: one output per thread (more threads busy, shorter chains); large
-  // channels: 4 x 4 register tiles.
-  const bool small = (nph * nhp <= 2 * NT) && (nhp * nhp <= 2 * NT);
-  if (small) {
-    for (int e = threadIdx.x; e < nhp * nhp && quad; e += NT) {
-      int r = e / nhp, c2 = e % nhp;
-      T_ acc = 0;
-      for (int u = 0; u < nph; u++) acc += Xt[u * H4 + r] * Ts[u * H4 + c2];
-      Cs[r * H4 + c2] = v1[(long)r * nhp + c2] + (T_)0.5 * acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nph * nhp; e += NT) {
-      int r = e / nhp, c2 = e % nhp;
-      T_ acc = 0;
-      for (int u = 0; u < nhp; u++) acc += Ts[r * H4 + u] * Cs[u * H4 + c2];
-      q[(long)r * nhp + c2] = acc;
-    }
-    return;
+};
+template <>
+struct VecT<float, 4> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
-  int th = H4 >> 2;
-  for (int tile = threadIdx.x; tile < th * th && quad; tile += NT) {
-    int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
-    T_ acc[4][4] = {};
-    for (int u = 0; u < nph; u++) {
-      T_ a[4], b[4];
-      Vec4<T_>::ld(Xt + u * H4 + r0, a);
-      Vec4<T_>::ld(Ts + u * H4 + s0, b);
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        int r = r0 + i, s = s0 + j;
-        Cs[r * H4 + s] = (r < nhp && s < nhp) ? v1[(long)r * nhp + s] + (T_)0.5 * acc[i][j] : (T_)0;
-      }
-  }
-  __syncthreads();
-  // T transposed into Xt: Xt[u][r] = T[r][u]  (u over hp, r over ph)
-  for (int e = threadIdx.x; e < P4 * H4; e += NT) {
-    int r = e / H4, u = e % H4;
-    Xt[u * P4 + r] = Ts[e];
-  }
-  __syncthreads();
-  int tp = P4 >> 2;
-  for (int tile = threadIdx.x; tile < tp * th; tile += NT) {
-    int r0 = (tile / th) << 2, s0 = (tile % th) << 2;
-    T_ acc[4][4] = {};
-    for (int u = 0; u < nhp; u++) {
-      T_ a[4], b[4];
-      Vec4<T_>::ld(Xt + u * P4 + r0, a);
-      Vec4<T_>::ld(Cs + u * H4 + s0, b);
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        int r = r0 + i, s = s0 + j;
-        if (r < nph && s < nhp) q[(long)r * nhp + s] = acc[i][j];
-      }
-  }
-}
+};
 
 // Element e of a cross channel's T: gathered from the current amplitudes through the signed
 // index map (GATHER: FP64 iteration) or read from the copy the update scatters (mixed).
@@ -228,40 +160,206 @@ __device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__
   }
 }
 
-// One CTA (NT threads) per cross channel of the launch's size class.  Staging: Ts = T,
-// Xt = W^T (W is stored transposed), both zero-padded to multiples of 4.  xw == nullptr: the
-// term linear in t only (C = <kb|v|cj>).
-template <typename T_, int NT, bool GATHER>
+// Bytes of the index tables at the start of a k_ph CTA's shared memory (2 R4 + 2 H4 ints,
+// a multiple of 16 since R4 and H4 are multiples of 4).
+__host__ __device__ __forceinline__ size_t ph_index_bytes(int R4, int H4) { return sizeof(int) * 2 * (size_t)(R4 + H4); }
+
+// One CTA (NT threads) per cross channel of the launch's class.  NM = 1: a channel with
+// S_z > 0, its Q also written to the mirror channel.  NM = 2: an S_z = 0 channel as the pair
+// (sum, difference) of half-size problems.  Per problem, in shared memory zero-padded to
+// multiples of 4 (R rows (a,i), H columns (k,c)):
+//   Ts = T (R x H), Xt = W^T staged as W (R x H), then T^T (H x R), Cs = C (H x H);
+//   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_(e,l) <kl|v|ce> t_lj^eb   (xw == nullptr: <kb|v|cj>)
+//   Q[(a,i)][(j,b)] = sum_(k,c) t_ik^ac C[(k,c)][(j,b)]
+// Each thread accumulates TS x TS outputs of every problem per tile.
+template <typename T_, int NT, int TS, int NM, bool GATHER>
+__device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __restrict__ ctl, int x,
+                                         unsigned char* smraw, const T_* __restrict__ xt,
+                                         const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                         T_* __restrict__ xq) {
+  const int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  const int R = NM == 2 ? nph >> 1 : nph, H = NM == 2 ? nhp >> 1 : nhp;
+  const int R4 = (R + 3) & ~3, H4 = (H + 3) & ~3;
+  const int RH = R4 * H4, HH = H4 * H4;
+  // index tables in shared memory first (no chains of dependent global loads below):
+  // NM = 1: sfr[r] = row of F(r) in the mirror, sfc[s] = column of F(s);
+  // NM = 2: sra[u] = spin-up row, srb[u] = its flip, sca[v] = spin-up column, scb[v] = its flip
+  int* sra = reinterpret_cast<int*>(smraw);
+  int* srb = sra + R4;
+  int* sca = srb + R4;
+  int* scb = sca + H4;
+  T_* Ts = reinterpret_cast<T_*>(smraw + ph_index_bytes(R4, H4));
+  T_* Xt = Ts + NM * RH;
+  T_* Cs = Xt + NM * RH;
+  const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
+  {
+    const int* __restrict__ frow = D.x_frow + D.x_ph_off[x];
+    const int* __restrict__ fcol = D.x_fcol + D.x_hp_off[x];
+    const int* __restrict__ rrow = D.x_rrow + D.x_ph_off[x];
+    const int* __restrict__ rcol = D.x_rcol + D.x_hp_off[x];
+    for (int k = threadIdx.x; k < R4; k += NT) {
+      int a = k < R ? (NM == 2 ? rrow[k] : k) : 0;
+      sra[k] = a;
+      srb[k] = k < R ? frow[a] : 0;
+    }
+    for (int k = threadIdx.x; k < H4; k += NT) {
+      int a = k < H ? (NM == 2 ? rcol[k] : k) : 0;
+      sca[k] = a;
+      scb[k] = k < H ? fcol[a] : 0;
+    }
+  }
+  __syncthreads();
+  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
+  const bool quad = xw != nullptr;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < RH; e += NT) {
+    int u = e / H4, s = e % H4;
+    T_ t0 = 0, t1 = 0, w0 = 0, w1 = 0;
+    if (u < R && s < H) {
+      if constexpr (NM == 1) {
+        long o = (long)u * nhp + s;
+        t0 = ph_t<T_, GATHER>(D, tcur, xt, to + o);
+        if (quad) w0 = xw[wo + o];
+      } else {
+        int row = sra[u], ca = sca[s], cb = scb[s];
+        long oa = (long)row * nhp + ca, ob = (long)row * nhp + cb;
+        T_ ta = ph_t<T_, GATHER>(D, tcur, xt, to + oa), tb = ph_t<T_, GATHER>(D, tcur, xt, to + ob);
+        t0 = ta + tb;
+        t1 = ta - tb;
+        if (quad) {
+          T_ wa = xw[wo + oa], wb = xw[wo + ob];
+          w0 = wa + wb;
+          w1 = wa - wb;
+        }
+      }
+    }
+    Ts[e] = t0;
+    Xt[e] = w0;
+    if constexpr (NM == 2) {
+      Ts[RH + e] = t1;
+      Xt[RH + e] = w1;
+    }
+  }
+#pragma unroll 4
+  for (int e = threadIdx.x; e < HH; e += NT) {
+    int r = e / H4, c = e % H4;
+    T_ v0 = 0, v1 = 0;
+    if (r < H && c < H) {
+      if constexpr (NM == 1) {
+        v0 = xv1[co + (long)r * nhp + c];
+      } else {
+        const long ra = co + (long)sca[r] * nhp;
+        T_ va = xv1[ra + sca[c]], vb = xv1[ra + scb[c]];
+        v0 = va + vb;
+        v1 = va - vb;
+      }
+    }
+    Cs[e] = v0;
+    if constexpr (NM == 2) Cs[HH + e] = v1;
+  }
+  __syncthreads();
+  const int th = H4 / TS;
+  if (quad) {
+    // C += 1/2 W^T T (padded rows and columns stay zero)
+    for (int tile = threadIdx.x; tile < NM * th * th; tile += NT) {
+      const int mtx = tile / (th * th), tt = tile % (th * th);
+      const int r0 = (tt / th) * TS, s0 = (tt % th) * TS;
+      const T_* X = Xt + mtx * RH;
+      const T_* Tm = Ts + mtx * RH;
+      T_ acc[TS][TS] = {};
+      for (int u = 0; u < R; u++) {
+        T_ a[TS], b[TS];
+        VecT<T_, TS>::ld(X + u * H4 + r0, a);
+        VecT<T_, TS>::ld(Tm + u * H4 + s0, b);
+#pragma unroll
+        for (int i = 0; i < TS; i++)
+#pragma unroll
+          for (int j = 0; j < TS; j++) acc[i][j] += a[i] * b[j];
+      }
+      T_* Cm = Cs + mtx * HH;
+#pragma unroll
+      for (int i = 0; i < TS; i++)
+#pragma unroll
+        for (int j = 0; j < TS; j++) Cm[(r0 + i) * H4 + s0 + j] += (T_)0.5 * acc[i][j];
+    }
+    __syncthreads();
+  }
+  // T transposed into Xt: Xt[s][u] = T[u][s]
+  for (int e = threadIdx.x; e < NM * RH; e += NT) {
+    const int mtx = e / RH, f = e % RH;
+    Xt[mtx * RH + (f % H4) * R4 + f / H4] = Ts[e];
+  }
+  __syncthreads();
+  const int tr = R4 / TS;
+  const long mo = NM == 1 ? D.x_t_off[D.x_mir[x]] : 0;
+  for (int tile = threadIdx.x; tile < tr * th; tile += NT) {
+    const int r0 = (tile / th) * TS, s0 = (tile % th) * TS;
+    T_ acc[NM][TS][TS] = {};
+    for (int u = 0; u < H; u++) {
+#pragma unroll
+      for (int mtx = 0; mtx < NM; mtx++) {
+        T_ a[TS], b[TS];
+        VecT<T_, TS>::ld(Xt + mtx * RH + u * R4 + r0, a);
+        VecT<T_, TS>::ld(Cs + mtx * HH + u * H4 + s0, b);
+#pragma unroll
+        for (int i = 0; i < TS; i++)
+#pragma unroll
+          for (int j = 0; j < TS; j++) acc[mtx][i][j] += a[i] * b[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TS; i++) {
+      const int r = r0 + i;
+      if (r >= R) continue;
+      if constexpr (NM == 1) {
+        const long qr = to + (long)r * nhp, mr = mo + (long)srb[r] * nhp;
+#pragma unroll
+        for (int j = 0; j < TS; j++) {
+          const int s = s0 + j;
+          if (s < H) {
+            xq[qr + s] = acc[0][i][j];
+            xq[mr + scb[s]] = acc[0][i][j];
+          }
+        }
+      } else {
+        const long qa = to + (long)sra[r] * nhp, qb = to + (long)srb[r] * nhp;
+#pragma unroll
+        for (int j = 0; j < TS; j++) {
+          const int s = s0 + j;
+          if (s < H) {
+            const int ca = sca[s], cb = scb[s];
+            const T_ A = (T_)0.5 * (acc[0][i][j] + acc[1][i][j]), B = (T_)0.5 * (acc[0][i][j] - acc[1][i][j]);
+            xq[qa + ca] = A;
+            xq[qa + cb] = B;
+            xq[qb + ca] = B;
+            xq[qb + cb] = A;
+          }
+        }
+      }
+    }
+  }
+}
+
+// One CTA per cross channel of the list (S_z >= 0, the costliest first): the S_z > 0 body or
+// the S_z = 0 one, chosen per channel, so that one launch balances all channels.
+template <typename T_, int NT, int TS, bool GATHER>
 __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
                                            const int* __restrict__ xlist, const T_* __restrict__ xt,
                                            const T_* __restrict__ xw, const T_* __restrict__ xv1,
                                            T_* __restrict__ xq) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T_* sm = reinterpret_cast<T_*>(smraw);
-  int x = xlist[blockIdx.x];
+  const int x = xlist[blockIdx.x];
   if (sys_done(D, ctl, D.x_sys[x])) return;
-  int nph = D.x_nph[x], nhp = D.x_nhp[x];
-  int P4 = (nph + 3) & ~3, H4 = (nhp + 3) & ~3;
-  T_* Ts = sm;
-  T_* Xt = Ts + P4 * H4;
-  T_* Cs = Xt + P4 * H4;
-  long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < P4 * H4; e += NT) {
-    int u = e / H4, s = e % H4;
-    bool in = u < nph && s < nhp;
-    long o = (long)u * nhp + s;
-    Ts[e] = in ? ph_t<T_, GATHER>(D, tcur, xt, to + o) : (T_)0;
-    Xt[e] = in && xw ? xw[wo + o] : (T_)0;  // W^T[u][s] = W[s][u]
-  }
-  __syncthreads();
-  ph_contract<T_, NT>(Ts, Xt, Cs, nph, nhp, P4, H4, xv1 + co, xq + to, xw != nullptr);
+  if (D.x_cls[x] == 0)
+    ph_block<T_, NT, TS, 2, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
+  else
+    ph_block<T_, NT, TS, 1, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
 }
 
-// Cross channels of at most PH_WARP_DIM rows/columns: one warp per channel with its own
-// shared buffers (stride PH_WARP_DIM), no block-wide synchronisation.
-constexpr int PH_WARPS = 8;
+// Cross channels of at most PH_WARP_DIM rows and columns (of their halves for S_z = 0): one
+// warp per channel with its own shared buffers (stride PH_WARP_DIM), no block-wide
+// synchronisation; the same two bodies as k_ph, one output element per lane and step.
+constexpr int PH_WARPS = 4;
 template <typename T_, bool GATHER>
 __global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const LoopCtl* __restrict__ ctl,
                                                            const int* __restrict__ xlist, int nlist,
@@ -275,72 +373,134 @@ __global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const Loo
   const int x = xlist[idx];
   if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
+  const bool two = D.x_cls[x] == 0;
+  const int nm = two ? 2 : 1;
+  const int R = two ? nph >> 1 : nph, H = two ? nhp >> 1 : nhp;
   const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  T_* Ts = reinterpret_cast<T_*>(smraw) + (size_t)w * 3 * S * S;  // T[u][s]
-  T_* Ws = Ts + S * S;                                             // W^T[u][r] = W[r][u]
-  T_* Cs = Ws + S * S;                                             // C[r][s]
+  const long mo = two ? to : D.x_t_off[D.x_mir[x]];
+  T_* Ts = reinterpret_cast<T_*>(smraw) + (size_t)w * 6 * S * S;  // [m][u][s]
+  T_* Ws = Ts + 2 * S * S;                                         // [m][u][r] = W[u][r]
+  T_* Cs = Ws + 2 * S * S;                                         // [m][r][s]
+  int* sra = reinterpret_cast<int*>(reinterpret_cast<T_*>(smraw) + (size_t)PH_WARPS * 6 * S * S) + w * 4 * S;
+  int* srb = sra + S;
+  int* sca = srb + S;
+  int* scb = sca + S;
+  {
+    const int* __restrict__ frow = D.x_frow + D.x_ph_off[x];
+    const int* __restrict__ fcol = D.x_fcol + D.x_hp_off[x];
+    const int* __restrict__ rrow = D.x_rrow + D.x_ph_off[x];
+    const int* __restrict__ rcol = D.x_rcol + D.x_hp_off[x];
+    if (lane < R) {
+      int a = two ? rrow[lane] : lane;
+      sra[lane] = a;
+      srb[lane] = frow[a];
+    }
+    if (lane < H) {
+      int a = two ? rcol[lane] : lane;
+      sca[lane] = a;
+      scb[lane] = fcol[a];
+    }
+  }
+  __syncwarp();
   const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
-  for (int e = lane; e < nph * nhp; e += 32) {
-    int u = e / nhp, c = e % nhp;
-    Ts[u * S + c] = ph_t<T_, GATHER>(D, tcur, xt, to + e);
-    Ws[u * S + c] = xw ? xw[wo + e] : (T_)0;
+  const bool quad = xw != nullptr;
+  for (int e = lane; e < R * H; e += 32) {
+    int u = e / H, c = e % H;
+    if (two) {
+      long oa = (long)sra[u] * nhp + sca[c], ob = (long)sra[u] * nhp + scb[c];
+      T_ ta = ph_t<T_, GATHER>(D, tcur, xt, to + oa), tb = ph_t<T_, GATHER>(D, tcur, xt, to + ob);
+      Ts[u * S + c] = ta + tb;
+      Ts[S * S + u * S + c] = ta - tb;
+      T_ wa = quad ? xw[wo + oa] : (T_)0, wb = quad ? xw[wo + ob] : (T_)0;
+      Ws[u * S + c] = wa + wb;
+      Ws[S * S + u * S + c] = wa - wb;
+    } else {
+      long o = (long)u * nhp + c;
+      Ts[u * S + c] = ph_t<T_, GATHER>(D, tcur, xt, to + o);
+      Ws[u * S + c] = quad ? xw[wo + o] : (T_)0;
+    }
   }
   __syncwarp();
-  for (int e = lane; e < nhp * nhp; e += 32) {
-    int r = e / nhp, c = e % nhp;
-    T_ acc = 0;
-    for (int u = 0; u < nph && xw; u++) acc += Ws[u * S + r] * Ts[u * S + c];
-    Cs[r * S + c] = xw ? xv1[co + e] + (T_)0.5 * acc : xv1[co + e];
+  for (int e = lane; e < H * H; e += 32) {
+    int r = e / H, c = e % H;
+    for (int m = 0; m < nm; m++) {
+      T_ v;
+      if (two) {
+        const long ra = co + (long)sca[r] * nhp;
+        T_ va = xv1[ra + sca[c]], vb = xv1[ra + scb[c]];
+        v = m == 0 ? va + vb : va - vb;
+      } else {
+        v = xv1[co + (long)r * nhp + c];
+      }
+      T_ acc = 0;
+      for (int u = 0; u < R && quad; u++) acc += Ws[m * S * S + u * S + r] * Ts[m * S * S + u * S + c];
+      Cs[m * S * S + r * S + c] = v + (T_)0.5 * acc;
+    }
   }
   __syncwarp();
-  for (int e = lane; e < nph * nhp; e += 32) {
-    int r = e / nhp, c = e % nhp;
-    T_ acc = 0;
-    for (int u = 0; u < nhp; u++) acc += Ts[r * S + u] * Cs[u * S + c];
-    xq[to + e] = acc;
+  for (int e = lane; e < R * H; e += 32) {
+    int r = e / H, c = e % H;
+    T_ acc[2] = {0, 0};
+    for (int m = 0; m < nm; m++)
+      for (int u = 0; u < H; u++) acc[m] += Ts[m * S * S + r * S + u] * Cs[m * S * S + u * S + c];
+    if (two) {
+      const T_ A = (T_)0.5 * (acc[0] + acc[1]), B = (T_)0.5 * (acc[0] - acc[1]);
+      const long qa = to + (long)sra[r] * nhp, qb = to + (long)srb[r] * nhp;
+      xq[qa + sca[c]] = A;
+      xq[qa + scb[c]] = B;
+      xq[qb + sca[c]] = B;
+      xq[qb + scb[c]] = A;
+    } else {
+      xq[to + (long)r * nhp + c] = acc[0];
+      xq[mo + (long)srb[r] * nhp + scb[c]] = acc[0];
+    }
   }
 }
 
-size_t ph_smem_bytes(int max_dim, size_t elem) {
-  size_t m4 = (size_t)((max_dim + 3) & ~3);
-  return elem * 3 * m4 * m4;
+static size_t ph_warp_smem(size_t elem) {
+  return (size_t)PH_WARPS * (6 * PH_WARP_DIM * PH_WARP_DIM * elem + 4 * PH_WARP_DIM * sizeof(int));
 }
 
-static size_t ph_warp_smem(size_t elem) { return elem * PH_WARPS * 3 * PH_WARP_DIM * PH_WARP_DIM; }
+// Shared memory of a k_ph CTA for channels of at most max_dim (NM = 1) or 2 max_dim (NM = 2)
+// rows and columns: the index tables, then NM problems of Ts, Xt (R x H) and Cs (H x H).
+size_t ph_smem_bytes(int max_dim, int nm, size_t elem) {
+  int m4 = (max_dim + 3) & ~3;
+  return ph_index_bytes(m4, m4) + elem * 3 * (size_t)nm * m4 * m4;
+}
 
-// The ph term in three size classes: cross channels larger than PH_SMALL_DIM (256-thread
-// CTAs), those larger than PH_WARP_DIM (128-thread CTAs, small shared footprint) and the rest
-// (one warp each).
+template <typename T_>
+static size_t ph_smem_of(const pnm_ctx* ctx) { return sizeof(T_) == 8 ? ctx->ph_smem64 : ctx->ph_smem32; }
+
+// The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).  FP64:
+// 2 x 2 register tiles (little padding; the FP64 pipe bounds the kernel); FP32: 4 x 4 (fewer
+// shared-memory loads per FMA).
 template <typename T_, bool GATHER>
-static void launch_ph_classes(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
-  if (ctx->n_ph_big > 0)
-    k_ph<T_, 256, GATHER><<<ctx->n_ph_big, 256, ph_smem_bytes(ctx->max_x_dim, sizeof(T_)), s>>>(
+static void launch_ph_list(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
+  constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
+  if (ctx->n_ph > 0)
+    k_ph<T_, PH_THREADS, TS, GATHER><<<ctx->n_ph, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
         ctx->d, ctx->ctl, ctx->ph_list, xt, xw, xv1, xq);
-  if (ctx->n_ph_mid > 0)
-    k_ph<T_, 128, GATHER><<<ctx->n_ph_mid, 128, ph_smem_bytes(PH_SMALL_DIM, sizeof(T_)), s>>>(
-        ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph_big, xt, xw, xv1, xq);
-  if (ctx->n_ph_small > 0)
-    k_ph_warp<T_, GATHER><<<(ctx->n_ph_small + PH_WARPS - 1) / PH_WARPS, PH_WARPS * 32, ph_warp_smem(sizeof(T_)),
-                            s>>>(ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph_big + ctx->n_ph_mid, ctx->n_ph_small,
-                                 xt, xw, xv1, xq);
+  if (ctx->n_ph_warp > 0)
+    k_ph_warp<T_, GATHER><<<(ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS, PH_WARPS * 32, ph_warp_smem(sizeof(T_)), s>>>(
+        ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph, ctx->n_ph_warp, xt, xw, xv1, xq);
 }
 
 template <typename T_, bool GATHER>
 static void ph_attributes(const pnm_ctx* ctx) {
-  smem_at_least(k_ph<T_, 256, GATHER>, ph_smem_bytes(ctx->max_x_dim, sizeof(T_)));
-  smem_at_least(k_ph<T_, 128, GATHER>, ph_smem_bytes(PH_SMALL_DIM, sizeof(T_)));
+  constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
+  smem_at_least(k_ph<T_, PH_THREADS, TS, GATHER>, ph_smem_of<T_>(ctx));
   smem_at_least(k_ph_warp<T_, GATHER>, ph_warp_smem(sizeof(T_)));
 }
 
 // FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear) {
-  launch_ph_classes<double, true>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
+  launch_ph_list<double, true>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
 }
 
 // Mixed ph: T read from the copy the update scatters.
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s) {
-  launch_ph_classes<float, false>(ctx, xt, xw, xv1, xq, s);
+  launch_ph_list<float, false>(ctx, xt, xw, xv1, xq, s);
 }
 
 void pnm_ph_attributes(const pnm_ctx* ctx) {
@@ -624,10 +784,10 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
         }
         num += hh[g];
         double ph = 0.0;
-        if (q.x >= 0) ph += D.xq[q.x];
-        if (q.y >= 0) ph -= D.xq[q.y];
-        if (q.z >= 0) ph -= D.xq[q.z];
-        if (q.w >= 0) ph += D.xq[q.w];
+        if (q.x >= 0) ph += D.xq[qpos_of(q.x)];
+        if (q.y >= 0) ph -= D.xq[qpos_of(q.y)];
+        if (q.z >= 0) ph -= D.xq[qpos_of(q.z)];
+        if (q.w >= 0) ph += D.xq[qpos_of(q.w)];
         num += ph;
         double tnew = num * D.inv_den[z];
         double R = num - D.den[z] * tz;
@@ -767,8 +927,8 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
         // P(ij)P(ab) Q: Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba from the cross-channel layout
-        float a0 = q[j].x >= 0 ? xq[q[j].x] : 0.0f, a1 = q[j].y >= 0 ? xq[q[j].y] : 0.0f;
-        float a2 = q[j].z >= 0 ? xq[q[j].z] : 0.0f, a3 = q[j].w >= 0 ? xq[q[j].w] : 0.0f;
+        float a0 = q[j].x >= 0 ? xq[qpos_of(q[j].x)] : 0.0f, a1 = q[j].y >= 0 ? xq[qpos_of(q[j].y)] : 0.0f;
+        float a2 = q[j].z >= 0 ? xq[qpos_of(q[j].z)] : 0.0f, a3 = q[j].w >= 0 ? xq[qpos_of(q[j].w)] : 0.0f;
         qs[j] = (a0 - a1) - (a2 - a3);
       }
 #pragma unroll
@@ -789,10 +949,11 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
         t32n[z[j]] = o32;
         if (pk.xt) {
           // the Q positions of P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba
-          if (q[j].x >= 0) pk.xt[q[j].x] = o32;
-          if (q[j].y >= 0) pk.xt[q[j].y] = -o32;
-          if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
-          if (q[j].w >= 0) pk.xt[q[j].w] = o32;
+          // (those the ph kernels read; flagged ones are skipped, as are -1)
+          if (!(q[j].x & QPOS_SKIP_T)) pk.xt[q[j].x] = o32;
+          if (!(q[j].y & QPOS_SKIP_T)) pk.xt[q[j].y] = -o32;
+          if (!(q[j].z & QPOS_SKIP_T)) pk.xt[q[j].z] = -o32;
+          if (!(q[j].w & QPOS_SKIP_T)) pk.xt[q[j].w] = o32;
         }
       }
     }
@@ -819,6 +980,26 @@ void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const fl
 void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s) {
   if (ctx->n_ab_items > 0)
     k_hh32<<<ctx->n_ab_items, 128, hh32_smem_bytes(ctx), s>>>(ctx->d, ctx->ctl, ctx->ab_items, hh);
+}
+
+// t <- (t + F t) / 2 under the global spin flip F (fmap).  The solution is flip-symmetric
+// and the ph term is formed for flip-symmetric amplitudes, so kept and learned starts are
+// symmetrised first (MBPT2 and zero starts are symmetric already).  A pair (z, F z) is handled
+// by the thread of its smaller index; fmap is an involution.
+__global__ void k_flip_sym(const int* __restrict__ fmap, double* __restrict__ t, long n) {
+  long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n) return;
+  int cd = fmap[z];
+  long f = (long)(cd > 0 ? cd : -cd) - 1;
+  if (f < z) return;
+  double v = 0.5 * (t[z] + (cd > 0 ? t[f] : -t[f]));
+  t[z] = v;
+  if (f != z) t[f] = cd > 0 ? v : -v;
+}
+
+void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s) {
+  if (ctx->nt > 0)
+    k_flip_sym<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.fmap, t, ctx->nt);
 }
 
 // Initial amplitudes (MBPT2 guess or zero) into t0 with energy partials.
@@ -1054,29 +1235,40 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
   CUDA_TRY(cudaMemsetAsync(ctx->sysctl, 0, sizeof(SysCtl) * nsys, s));
   ctx->d.sysctl = ctx->sysctl;
-  // cross channels for the mixed ph launches: the large ones first, each class largest first
-  std::vector<int> big, mid, small;
+  // cross channels of the ph launch: S_z >= 0 (S_z < 0 ones are mirrors), costliest first;
+  // shared memory for the largest (NM = 1: rows/columns; NM = 2: those of the halves, twice)
+  std::vector<int> xl, xw;  // CTA per channel; warp per channel (at most PH_WARP_DIM)
+  std::vector<long> xcost(ctx->nx, 0);
   for (int x = 0; x < ctx->nx; x++) {
-    int d = std::max(ctx->h_x_nph[x], ctx->h_x_nhp[x]);
-    (d > PH_SMALL_DIM ? big : d > PH_WARP_DIM ? mid : small).push_back(x);
+    int c = ctx->h_x_cls[x];
+    if (c < 0) continue;
+    long ph = ctx->h_x_nph[x], hp = ctx->h_x_nhp[x];
+    int d = (int)std::max(ph, hp);
+    if (c == 0) {
+      d /= 2;
+      xcost[x] = ph * hp * hp / 4;
+    } else {
+      xcost[x] = ph * hp * hp;
+    }
+    if (d <= PH_WARP_DIM) {
+      xw.push_back(x);
+      continue;
+    }
+    int nm = c == 0 ? 2 : 1;
+    ctx->ph_smem64 = std::max(ctx->ph_smem64, ph_smem_bytes(d, nm, sizeof(double)));
+    ctx->ph_smem32 = std::max(ctx->ph_smem32, ph_smem_bytes(d, nm, sizeof(float)));
+    xl.push_back(x);
   }
-  auto by_size = [&](int a, int b) {
-    long sa = (long)ctx->h_x_nph[a] * ctx->h_x_nhp[a], sb = (long)ctx->h_x_nph[b] * ctx->h_x_nhp[b];
-    return sa != sb ? sa > sb : a < b;
-  };
-  std::sort(big.begin(), big.end(), by_size);
-  std::sort(mid.begin(), mid.end(), by_size);
-  std::sort(small.begin(), small.end(), by_size);
-  std::vector<int> xl(big);
-  xl.insert(xl.end(), mid.begin(), mid.end());
-  xl.insert(xl.end(), small.begin(), small.end());
-  ctx->n_ph_big = (int)big.size();
-  ctx->n_ph_mid = (int)mid.size();
-  ctx->n_ph_small = (int)small.size();
+  auto costlier = [&](int a, int b) { return xcost[a] != xcost[b] ? xcost[a] > xcost[b] : a < b; };
+  std::sort(xl.begin(), xl.end(), costlier);
+  std::sort(xw.begin(), xw.end(), costlier);
+  ctx->n_ph = (int)xl.size();
+  ctx->n_ph_warp = (int)xw.size();
+  xl.insert(xl.end(), xw.begin(), xw.end());
+  size_t ph_smem = ctx->ph_smem64;
   ctx->ph_list = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, xl.size()));
   if (!xl.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->ph_list, xl.data(), sizeof(int) * xl.size(), cudaMemcpyHostToDevice, s));
-  size_t ph_smem = ph_smem_bytes(ctx->max_x_dim, sizeof(double));
   size_t pp_smem = pp64_smem(max_nlad);
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
@@ -1157,10 +1349,10 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
     e5 += tz * hh;
     int4 q = D.qmap[z];
     double ph = 0.0;
-    if (q.x >= 0) ph += D.xq[q.x];
-    if (q.y >= 0) ph -= D.xq[q.y];
-    if (q.z >= 0) ph -= D.xq[q.z];
-    if (q.w >= 0) ph += D.xq[q.w];
+    if (q.x >= 0) ph += D.xq[qpos_of(q.x)];
+    if (q.y >= 0) ph -= D.xq[qpos_of(q.y)];
+    if (q.z >= 0) ph -= D.xq[qpos_of(q.z)];
+    if (q.w >= 0) ph += D.xq[qpos_of(q.w)];
     e3 += tz * ph;
   }
   e4 = block_sum(e4, sh32);
@@ -1384,6 +1576,33 @@ void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
     CUDA_TRY(cudaMemsetAsync(ctx->d.xq, 0, sizeof(double) * ctx->nxt, s));
 }
 
+// Kernel nodes of a captured update: the ph term at the lowest priority, every other kernel at
+// the highest, so that the shorter branches (pp ladder, one-body sums) are dispatched ahead of
+// the many ph CTAs and run beside them instead of after them.
+static bool is_ph_kernel(const void* f) {
+  return f == (const void*)k_ph<double, PH_THREADS, 2, true> || f == (const void*)k_ph<float, PH_THREADS, 4, false> ||
+         f == (const void*)k_ph_warp<double, true> || f == (const void*)k_ph_warp<float, false>;
+}
+
+static void set_node_priorities(cudaGraph_t body) {
+  int least = 0, greatest = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  size_t n = 0;
+  CUDA_TRY(cudaGraphGetNodes(body, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) CUDA_TRY(cudaGraphGetNodes(body, nodes.data(), &n));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp = {};
+    CUDA_TRY(cudaGraphKernelNodeGetParams(nd, &kp));
+    cudaKernelNodeAttrValue v = {};
+    v.priority = is_ph_kernel(kp.func) ? least : greatest;
+    CUDA_TRY(cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v));
+  }
+}
+
 // Build (once per mode) a graph whose single node is a WHILE conditional looping the body.
 static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
   auto f = ctx->graphs.find(mode);
@@ -1411,8 +1630,9 @@ static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
   }
   cudaGraph_t captured;
   CUDA_TRY(cudaStreamEndCapture(ctx->stream, &captured));
+  set_node_priorities(body);
   cudaGraphExec_t ge;
-  CUDA_TRY(cudaGraphInstantiate(&ge, g, 0));
+  CUDA_TRY(cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority));
   ctx->graphs[mode] = ge;
   ctx->graph_defs[mode] = g;
   return ge;
@@ -1467,6 +1687,7 @@ void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol) {
     hs[k].tol = tol[k];
   }
   CUDA_TRY(cudaMemcpyAsync(ctx->sysctl, hs.data(), sizeof(SysCtl) * nsys, cudaMemcpyHostToDevice, s));
+  if (init == PNM_INIT_KEEP) pnm_flip_symmetrise(ctx, ctx->d.t0, s);
   k_init<<<ctx->nrows, 128, 0, s>>>(ctx->d, init);
   k_start<<<1, 256, 0, s>>>(ctx->d.eparts, ctx->row_lo_d, ctx->row_hi_d, nsys, ctx->sysctl,
                             ctx->ctl, ctx->hist, ctx->hist_cap);

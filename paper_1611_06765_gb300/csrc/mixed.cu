@@ -701,8 +701,8 @@ __global__ void k_ph_assemble(DevState D, const T* __restrict__ xq, long nt, dou
   long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= nt) return;
   int4 q = D.qmap[z];
-  double a0 = q.x >= 0 ? (double)xq[q.x] : 0.0, a1 = q.y >= 0 ? (double)xq[q.y] : 0.0;
-  double a2 = q.z >= 0 ? (double)xq[q.z] : 0.0, a3 = q.w >= 0 ? (double)xq[q.w] : 0.0;
+  double a0 = q.x >= 0 ? (double)xq[qpos_of(q.x)] : 0.0, a1 = q.y >= 0 ? (double)xq[qpos_of(q.y)] : 0.0;
+  double a2 = q.z >= 0 ? (double)xq[qpos_of(q.z)] : 0.0, a3 = q.w >= 0 ? (double)xq[qpos_of(q.w)] : 0.0;
   out[z] = (a0 - a1) - (a2 - a3);
 }
 
@@ -719,6 +719,7 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->dev_error, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->skip_done, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  pnm_flip_symmetrise(ctx, ctx->d.t0, s);  // the term of the flip-symmetric part of t
   unsigned nb = (unsigned)((ctx->nt + 255) / 256);
   if (!ctx->expand_buf) ctx->expand_buf = ctx_alloc<double>(ctx, ctx->nt);  // the assembled term
   if (precision == PNM_PREC_BF16X3) {

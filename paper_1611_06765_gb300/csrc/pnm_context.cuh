@@ -37,6 +37,7 @@ struct pnm_ctx {
   std::vector<long> h_s_off, h_vl_off;   // ladder-layout and ladder-V offsets per channel
   std::vector<int2> h_rows;
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
+  std::vector<int> h_x_cls;  // spin-flip class of each cross channel (+1, 0, -1)
 
   // work lists
   int2* pp_items = nullptr;   // (channel, first pp column) of the FP64 pp ladder
@@ -46,8 +47,9 @@ struct pnm_ctx {
   int *upd_lo_d = nullptr, *upd_hi_d = nullptr;  // per system ranges of the (row, column) items
   int4* grp_items = nullptr;  // (channel, first ij, first pp column, rows) of the update
   int n_grp_items = 0, upd_rows = 1;
-  int* ph_list = nullptr;  // cross channels of the mixed ph launches (large class first)
-  int n_ph_big = 0, n_ph_mid = 0, n_ph_small = 0;
+  int* ph_list = nullptr;  // cross channels of the ph launches (S_z >= 0, costliest first)
+  int n_ph = 0, n_ph_warp = 0;           // channels of the CTA launch, then of the warp launch
+  size_t ph_smem64 = 0, ph_smem32 = 0;   // shared memory of a CTA (the largest channel)
   int *grp_lo_d = nullptr, *grp_hi_d = nullptr;  // per system ranges of the update items
   int *ab_lo_d = nullptr, *ab_hi_d = nullptr;    // per system ranges of the column items
   int max_nhh = 1;
@@ -151,7 +153,7 @@ void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
 void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s);
-size_t ph_smem_bytes(int max_dim, size_t elem);
+size_t ph_smem_bytes(int max_dim, int nm, size_t elem);
 void pnm_mixed_pack_initial(pnm_ctx* ctx);
 void pnm_fork(pnm_ctx* ctx);
 void pnm_join(pnm_ctx* ctx);
@@ -159,6 +161,7 @@ void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results
 void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
+void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s);
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);

@@ -77,6 +77,18 @@ __device__ __forceinline__ int encode_key(int Px, int Py, int Pz, int W, int m, 
   return (((Px + m) * M + (Py + m)) * M + (Pz + m)) * charge_slots(species) + charge_slot(W, species);
 }
 
+// Spin s = +-1 of a state's charge label, and the state with the same momentum and species
+// and the opposite spin (the global spin flip), or -1.
+__device__ __forceinline__ int spin_of(int w, int species) {
+  return species == 1 ? w : w - 4 * (w > 0 ? 1 : -1);
+}
+
+__device__ __forceinline__ int flip_state(const char4* __restrict__ nv, const int* __restrict__ idx3,
+                                          int r, int p, int species) {
+  char4 s = nv[p];
+  return lookup_state(idx3, r, s.x, s.y, s.z, s.w - 2 * spin_of(s.w, species), species);
+}
+
 // ---------------------------------------------------------------------------- basis
 // Cube points c = ((x+r)w + (y+r))w + (z+r) are in (n_x, n_y, n_z) lexicographic order, so a
 // point's slot in the shell-ordered list is (points in lower shells) + (points of the same
@@ -396,6 +408,25 @@ __global__ void k_fill_cross(const char4* __restrict__ nvec, const int* __restri
 }
 
 // ------------------------------------------------------------------------- index maps
+// Position code of t_{h1 h2}^{p1 p2} (system-local states) in the restricted direct blocks:
+// sign * (t index + 1), 0 where it vanishes (p1 = p2 or h1 = h2) or its channel is not held.
+__device__ __forceinline__ int t_code(int p1, int p2, int h1, int h2, const char4* __restrict__ nv, int N,
+                                      int np, int m, int M, int species, const int* __restrict__ key2ch,
+                                      int ch0, const long* __restrict__ ch_t_off,
+                                      const int* __restrict__ ch_npp, const int* __restrict__ pos_hh,
+                                      const int* __restrict__ pos_pp) {
+  if (p1 == p2 || h1 == h2) return 0;
+  int sgn = 1;
+  if (p1 > p2) { int z = p1; p1 = p2; p2 = z; sgn = -sgn; }
+  if (h1 > h2) { int z = h1; h1 = h2; h2 = z; sgn = -sgn; }
+  char4 s1 = nv[p1], s2 = nv[p2];
+  int ch = key2ch[encode_key(s1.x + s2.x, s1.y + s2.y, s1.z + s2.z, s1.w + s2.w, m, M, species)];
+  if (ch < 0) return 0;
+  int g = ch0 + ch;
+  long idx = ch_t_off[g] + (long)pos_hh[h1 * N + h2] * ch_npp[g] + pos_pp[(size_t)(p1 - N) * np + (p2 - N)];
+  return sgn * (int)(idx + 1);
+}
+
 // T_x[(a,i)][(k,c)] = t_ik^ac, read from the restricted direct block with its sign.
 // Encoded as sign * (t index + 1); 0 where the element vanishes (a = c or i = k).
 __global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
@@ -408,44 +439,33 @@ __global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restr
                        const int* __restrict__ pos_pp, int* __restrict__ xmap) {
   int x = x0 + blockIdx.x;
   int nph = x_nph[x], nhp = x_nhp[x];
-  int np = nsp - N;
   long base = x_t_off[x];
   for (int e = threadIdx.x; e < nph * nhp; e += blockDim.x) {
     int rr = e / nhp, ss = e % nhp;
     int2 ai = ph_pair[x_ph_off[x] + rr], kc = hp_pair[x_hp_off[x] + ss];
     int a = ai.x - sp_off, i = ai.y - sp_off, k = kc.x - sp_off, c = kc.y - sp_off;
-    int code = 0;
-    if (a != c && i != k) {
-      int sgn = 1;
-      int p1 = a, p2 = c, h1 = i, h2 = k;
-      if (p1 > p2) { int z = p1; p1 = p2; p2 = z; sgn = -sgn; }
-      if (h1 > h2) { int z = h1; h1 = h2; h2 = z; sgn = -sgn; }
-      char4 s1 = nvec[sp_off + p1], s2 = nvec[sp_off + p2];
-      int K = encode_key(s1.x + s2.x, s1.y + s2.y, s1.z + s2.z, s1.w + s2.w, m, M, species);
-      int ch = key2ch[K];
-      if (ch >= 0) {
-        int g = ch0 + ch;
-        long idx = ch_t_off[g] + (long)pos_hh[h1 * N + h2] * ch_npp[g] +
-                   pos_pp[(size_t)(p1 - N) * np + (p2 - N)];
-        code = sgn * (int)(idx + 1);
-      }
-    }
-    xmap[base + e] = code;
+    xmap[base + e] = t_code(a, c, i, k, nvec + sp_off, N, nsp - N, m, M, species, key2ch, ch0, ch_t_off,
+                            ch_npp, pos_hh, pos_pp);
   }
 }
 
 // For every restricted t element (ij, ab) of a row: the positions of
 // Q_ij^ab, Q_ji^ab, Q_ij^ba, Q_ji^ba with Q_ij^ab = Q_x[(a,i)][(j,b)].
+// Position of Q_x[(p,h)][(h2,p2)], flagged with QPOS_SKIP_T where the ph kernels never read T
+// (channels with S_z < 0 and the spin-down rows of S_z = 0 channels), or -1.
 __device__ __forceinline__ int qpos(int p, int h, int h2, int p2, int N, int np,
                                     const int* __restrict__ phch, const int* __restrict__ phpos,
                                     const int* __restrict__ hppos, int x0,
                                     const long* __restrict__ x_t_off,
-                                    const int* __restrict__ x_nhp) {
+                                    const int* __restrict__ x_nhp, const int* __restrict__ x_cls,
+                                    const char4* __restrict__ nv, int species) {
   size_t u = (size_t)(p - N) * N + h;
   int x = phch[u];
   if (x < 0) return -1;
   int g = x0 + x;
-  return (int)(x_t_off[g] + (long)phpos[u] * x_nhp[g] + hppos[(size_t)h2 * np + (p2 - N)]);
+  int q = (int)(x_t_off[g] + (long)phpos[u] * x_nhp[g] + hppos[(size_t)h2 * np + (p2 - N)]);
+  bool skip = x_cls[g] < 0 || (x_cls[g] == 0 && spin_of(nv[p].w, species) < 0);
+  return skip ? (q | QPOS_SKIP_T) : q;
 }
 
 __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
@@ -455,6 +475,7 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
                        int sp_off, int N, int nsp, const int* __restrict__ phch,
                        const int* __restrict__ phpos, const int* __restrict__ hppos, int x0,
                        const long* __restrict__ x_t_off, const int* __restrict__ x_nhp,
+                       const int* __restrict__ x_cls, const char4* __restrict__ nvec, int species,
                        int4* __restrict__ qmap) {
   int2 it = row_item[row0 + blockIdx.x];
   int c = it.x, ij = it.y;
@@ -463,15 +484,103 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
   int i = h.x - sp_off, j = h.y - sp_off;
   int npp = ch_npp[c];
   long base = ch_t_off[c] + (long)ij * npp;
+  const char4* nv = nvec + sp_off;
   for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
     int2 pb = pp_pair[ch_pp_off[c] + ab];
     int a = pb.x - sp_off, b = pb.y - sp_off;
     int4 q;
-    q.x = qpos(a, i, j, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
-    q.y = qpos(a, j, i, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
-    q.z = qpos(b, i, j, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
-    q.w = qpos(b, j, i, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp);
+    q.x = qpos(a, i, j, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
+    q.y = qpos(a, j, i, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
+    q.z = qpos(b, i, j, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
+    q.w = qpos(b, j, i, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
     qmap[base + ab] = q;
+  }
+}
+
+// ------------------------------------------------------------------------ spin flip
+// The global spin flip F (every state to the one of opposite spin) leaves H and the
+// spin-saturated reference unchanged, so the amplitudes of the solution obey
+// t(F i, F j; F a, F b) = t(i, j; a, b) and every cross-channel matrix M of the ph term
+// (T, W, <kb|v|cj>, Q) obeys M_F(x)[F r][F c] = M_x[r][c].  One thread per cross channel of a
+// system records:
+//   x_cls   +1 for S_z = s_a - s_i > 0 (computed, Q also written to its mirror F(x)), 0 for
+//           S_z = 0 (F maps the channel onto itself), -1 for S_z < 0 (filled from its mirror);
+//   x_mir   the channel F(x);  x_frow / x_fcol  the row (column) of F(x) holding F(row), F(col);
+//   x_rrow / x_rcol (S_z = 0)  the rows (a,i) and columns (k,c) with spin-up a and k, in order
+//           (half of each: the other half are their flips).
+// Sets *err when a table is not closed under F (a reference that is not spin saturated).
+__global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
+                        const int* __restrict__ x_ph_off, const int* __restrict__ x_hp_off,
+                        const int2* __restrict__ ph_pair, const int2* __restrict__ hp_pair,
+                        const char4* __restrict__ nvec, const int* __restrict__ idx3, int r, int species,
+                        int sp_off, int N, int nsp, const int* __restrict__ phpos,
+                        const int* __restrict__ phch, const int* __restrict__ hppos, int* __restrict__ x_cls,
+                        int* __restrict__ x_mir, int* __restrict__ x_frow, int* __restrict__ x_fcol,
+                        int* __restrict__ x_rrow, int* __restrict__ x_rcol, int* __restrict__ err) {
+  int xl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xl >= nxs) return;
+  int x = x0 + xl;
+  int nph = x_nph[x], nhp = x_nhp[x], po = x_ph_off[x], ho = x_hp_off[x];
+  const char4* nv = nvec + sp_off;
+  int np = nsp - N;
+  bool bad = nph <= 0 || nhp <= 0;
+  int sz = 0, mir = -1, nr = 0, nc = 0;
+  if (!bad) {
+    int2 p0 = ph_pair[po];
+    sz = spin_of(nv[p0.x - sp_off].w, species) - spin_of(nv[p0.y - sp_off].w, species);
+  }
+  for (int k = 0; k < nph && !bad; k++) {
+    int2 ai = ph_pair[po + k];
+    int a = ai.x - sp_off, i = ai.y - sp_off;
+    int fa = flip_state(nv, idx3, r, a, species), fi = flip_state(nv, idx3, r, i, species);
+    if (fa < N || fi < 0 || fi >= N) { bad = true; break; }
+    size_t u = (size_t)(fa - N) * N + fi;
+    int ch = phch[u];
+    if (ch < 0 || (mir >= 0 && ch != mir)) { bad = true; break; }
+    mir = ch;
+    x_frow[po + k] = phpos[u];
+    if (sz == 0 && spin_of(nv[a].w, species) > 0) x_rrow[po + nr++] = k;
+  }
+  for (int k = 0; k < nhp && !bad; k++) {
+    int2 hc = hp_pair[ho + k];
+    int h = hc.x - sp_off, p = hc.y - sp_off;
+    int fh = flip_state(nv, idx3, r, h, species), fp = flip_state(nv, idx3, r, p, species);
+    if (fh < 0 || fh >= N || fp < N) { bad = true; break; }
+    x_fcol[ho + k] = hppos[(size_t)fh * np + (fp - N)];
+    if (sz == 0 && spin_of(nv[h].w, species) > 0) x_rcol[ho + nc++] = k;
+  }
+  if (!bad && sz == 0 && (2 * nr != nph || 2 * nc != nhp || mir != xl)) bad = true;
+  if (!bad && sz != 0 && mir == xl) bad = true;
+  x_cls[x] = sz > 0 ? 1 : (sz == 0 ? 0 : -1);
+  x_mir[x] = x0 + (mir < 0 ? xl : mir);
+  if (bad) atomicExch(err, 1);
+}
+
+// Per amplitude: the position code of its spin-flipped amplitude (sign * (index + 1)); one
+// CTA per (channel, ij) row.
+__global__ void k_fmap(int row0, const int2* __restrict__ row_item, const int* __restrict__ ch_hh_off,
+                       const int* __restrict__ ch_pp_off, const int* __restrict__ ch_npp,
+                       const long* __restrict__ ch_t_off, const int2* __restrict__ hh_pair,
+                       const int2* __restrict__ pp_pair, const char4* __restrict__ nvec,
+                       const int* __restrict__ idx3, int r, int species, int sp_off, int N, int nsp, int m,
+                       int M, const int* __restrict__ key2ch, int ch0, const int* __restrict__ pos_hh,
+                       const int* __restrict__ pos_pp, int* __restrict__ fmap, int* __restrict__ err) {
+  int2 it = row_item[row0 + blockIdx.x];
+  int c = it.x, ij = it.y;
+  const char4* nv = nvec + sp_off;
+  int2 h = hh_pair[ch_hh_off[c] + ij];
+  int fi = flip_state(nv, idx3, r, h.x - sp_off, species), fj = flip_state(nv, idx3, r, h.y - sp_off, species);
+  int npp = ch_npp[c];
+  long base = ch_t_off[c] + (long)ij * npp;
+  for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
+    int2 pb = pp_pair[ch_pp_off[c] + ab];
+    int fa = flip_state(nv, idx3, r, pb.x - sp_off, species), fb = flip_state(nv, idx3, r, pb.y - sp_off, species);
+    int code = 0;
+    if (fi >= 0 && fi < N && fj >= 0 && fj < N && fa >= N && fb >= N)
+      code = t_code(fa, fb, fi, fj, nv, N, nsp - N, m, M, species, key2ch, ch0, ch_t_off, ch_npp, pos_hh,
+                    pos_pp);
+    if (code == 0) atomicExch(err, 1);
+    fmap[base + ab] = code;
   }
 }
 
@@ -937,7 +1046,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
     }
     S.x_end = (int)h_x_nph.size();
   }
-  if (t_acc >= (1L << 31) - 2 || xt_acc >= (1L << 31) - 2)
+  if (t_acc >= (1L << 31) - 2 || xt_acc >= (long)QPOS_SKIP_T)
     throw PnmError{PNM_EINVAL, "problem too large for 32-bit element maps"};
   ctx->nch = (int)h_key.size();
   ctx->nx = (int)h_x_nph.size();
@@ -1013,6 +1122,15 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   D.pp_pair = dalloc<int2>(pp_acc, ctx->owned, s);
   D.ph_pair = dalloc<int2>(ph_acc, ctx->owned, s);
   D.hp_pair = dalloc<int2>(hp_acc, ctx->owned, s);
+  D.x_cls = dalloc<int>(NX, ctx->owned, s);
+  D.x_mir = dalloc<int>(NX, ctx->owned, s);
+  D.x_frow = dalloc<int>(ph_acc, ctx->owned, s);
+  D.x_rrow = dalloc<int>(ph_acc, ctx->owned, s);
+  D.x_fcol = dalloc<int>(hp_acc, ctx->owned, s);
+  D.x_rcol = dalloc<int>(hp_acc, ctx->owned, s);
+  D.fmap = dalloc<int>(t_acc, ctx->owned, s);
+  int* flip_err = dalloc<int>(1, ctx->owned, s);
+  CUDA_TRY(cudaMemsetAsync(flip_err, 0, sizeof(int), s));
   D.xmap = dalloc<int>(xt_acc, ctx->owned, s);
   D.qmap = dalloc<int4>(t_acc, ctx->owned, s);
   D.v_pphh = dalloc<double>(t_acc, ctx->owned, s);
@@ -1060,6 +1178,10 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
                                  D.ph_pair, D.hp_pair, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M,
                                  S.species, X.key2ch, S.ch_begin, D.ch_t_off, D.ch_npp, X.pos_hh, X.pos_pp,
                                  D.xmap);
+      k_xflip<<<(nxs + 127) / 128, 128, 0, s>>>(S.x_begin, nxs, D.x_nph, D.x_nhp, D.x_ph_off, D.x_hp_off,
+                                                D.ph_pair, D.hp_pair, D.nvec, X.idx3, S.r, S.species,
+                                                S.sp_off, S.N, S.nsp, X.phpos, X.phch, X.hppos, D.x_cls,
+                                                D.x_mir, D.x_frow, D.x_fcol, D.x_rrow, D.x_rcol, flip_err);
       k_v_cross<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_c_off, D.x_w_off,
                                     D.x_ph_off, D.x_hp_off, D.ph_pair, D.hp_pair, D.nvec,
                                     D.lut + S.lut_off, D.x_v1, D.x_w);
@@ -1069,7 +1191,11 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       k_qmap<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
                                    D.ch_t_off, D.hh_pair, D.pp_pair, S.sp_off, S.N, S.nsp,
                                    X.phch, X.phpos, X.hppos, S.x_begin, D.x_t_off, D.x_nhp,
-                                   D.qmap);
+                                   D.x_cls, D.nvec, S.species, D.qmap);
+      k_fmap<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp, D.ch_t_off,
+                                   D.hh_pair, D.pp_pair, D.nvec, X.idx3, S.r, S.species, S.sp_off, S.N,
+                                   S.nsp, S.m, S.M, X.key2ch, S.ch_begin, X.pos_hh, X.pos_pp, D.fmap,
+                                   flip_err);
       k_v_pphh<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
                                      D.ch_t_off, D.hh_pair, D.pp_pair, D.nvec, D.lut + S.lut_off,
                                      D.v_pphh);
@@ -1117,6 +1243,8 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
     CUDA_TRY(cudaGetLastError());
   }
   std::vector<int> h_nlad = d2h(D.ch_nlad, C, s);
+  if (d2h(flip_err, 1, s)[0]) throw PnmError{PNM_EINVAL, "spin-flip tables not closed (reference not spin saturated)"};
+  ctx->h_x_cls = d2h(D.x_cls, NX, s);
   std::vector<long> h_s_off(C, 0), h_vl_off(C, -1);
   long s_acc = 0, vl_acc = 0;
   int max_nlad = 0;

@@ -11,6 +11,7 @@ import pytest
 
 from conftest import minnesota_params
 from inputs import random_amplitudes
+import spinflip
 from oracle import channel
 
 pytestmark = pytest.mark.gpu
@@ -89,14 +90,43 @@ def test_ph_term_operator(pkg, N, rho, n2):
     (two chained FP32 products over at most 66 terms each: at most 2 * 66 * 2^-24 of it)."""
     g = pkg.Context(N, rho, n2, params=minnesota_params())
     o = channel.OracleSystem(N, rho, n2, minnesota_params())
-    n = len(g.amplitude_labels())
-    t = random_amplitudes(n, seed=9)
-    ref = o.ph_apply(t)
-    bound = o.ph_apply(t, absval=True)
+    lab = g.amplitude_labels()
+    perm = spinflip.flip_permutation(lab, o.states())
+    t = random_amplitudes(len(lab), seed=9)
+    ts = spinflip.symmetrise(t, perm)  # the library forms the term of the symmetric part
+    ref = o.ph_apply(ts)
+    bound = o.ph_apply(ts, absval=True)
     r64 = g.apply_ph_term(t, precision=pkg.PNM_PREC_FP64)
     r16 = g.apply_ph_term(t, precision=pkg.PNM_PREC_BF16X3)
     scale = np.max(np.abs(ref))
     assert scale > 0
     assert np.max(np.abs(r64 - ref)) <= 1e-12 * scale
+    ratio = np.abs(r16 - ref) / (bound + 1e-300)
+    print("mixed ph: max error / element bound = %.3g" % np.max(ratio))
     assert np.all(np.abs(r16 - ref) <= 2e-5 * bound + 1e-30)
+    assert np.array_equal(g.apply_ph_term(spinflip.flip(t, perm), precision=pkg.PNM_PREC_FP64), r64)
+    g.close()
+
+
+def test_keep_start_is_symmetrised(pkg):
+    """A kept start that is not flip-symmetric converges to the solution from the MBPT2 start
+    (the kept amplitudes are symmetrised first), in FP64 and in the mixed path."""
+    N, rho, n2 = 14, 0.08, 20
+    g = pkg.Context(N, rho, n2, params=minnesota_params())
+    o = channel.OracleSystem(N, rho, n2, minnesota_params())
+    dE_o, _, _, _ = o.ccd(alpha=0.5, tol=1e-13, maxit=600)
+    perm = spinflip.flip_permutation(g.amplitude_labels(), o.states())
+    g.solve(alpha=0.5, tol=1e-12, max_iter=600)
+    t = g.get_amplitudes()
+    assert np.max(np.abs(t - spinflip.flip(t, perm))) <= 1e-12 * np.max(np.abs(t))
+    noisy = t + random_amplitudes(len(t), seed=5, scale=2e-3)
+    g.set_amplitudes(noisy)
+    dE, _, _, _ = g.solve(alpha=0.5, tol=1e-13, max_iter=600, init=pkg.PNM_INIT_KEEP)
+    assert abs(dE[0] - dE_o) < 1e-10 * abs(dE_o), (dE[0], dE_o)
+    t2 = g.get_amplitudes()
+    assert np.max(np.abs(t2 - spinflip.flip(t2, perm))) <= 1e-12 * np.max(np.abs(t2))
+    g.set_amplitudes(noisy)
+    dE, _, _, _ = g.solve(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-8,
+                          max_iter=600, init=pkg.PNM_INIT_KEEP, refine_sweeps=2)
+    assert abs(dE[0] - dE_o) / N < 1e-6, (dE[0], dE_o)
     g.close()
