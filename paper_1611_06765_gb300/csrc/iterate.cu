@@ -340,38 +340,16 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
   }
 }
 
-// One CTA per cross channel of the list (S_z >= 0, the costliest first): the S_z > 0 body or
-// the S_z = 0 one, chosen per channel, so that one launch balances all channels.
-template <typename T_, int NT, int TS, bool GATHER>
-__global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
-                                           const int* __restrict__ xlist, const T_* __restrict__ xt,
-                                           const T_* __restrict__ xw, const T_* __restrict__ xv1,
-                                           T_* __restrict__ xq) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int x = xlist[blockIdx.x];
-  if (sys_done(D, ctl, D.x_sys[x])) return;
-  if (D.x_cls[x] == 0)
-    ph_block<T_, NT, TS, 2, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
-  else
-    ph_block<T_, NT, TS, 1, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
-}
-
 // Cross channels of at most PH_WARP_DIM rows and columns (of their halves for S_z = 0): one
 // warp per channel with its own shared buffers (stride PH_WARP_DIM), no block-wide
-// synchronisation; the same two bodies as k_ph, one output element per lane and step.
-constexpr int PH_WARPS = 4;
+// synchronisation; the same two bodies as the CTA path, one output element per lane and step.
+constexpr int PH_WARPS = PH_THREADS / 32;
 template <typename T_, bool GATHER>
-__global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const LoopCtl* __restrict__ ctl,
-                                                           const int* __restrict__ xlist, int nlist,
-                                                           const T_* __restrict__ xt, const T_* __restrict__ xw,
-                                                           const T_* __restrict__ xv1, T_* __restrict__ xq) {
+__device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* __restrict__ ctl, int x, int w,
+                                             int lane, unsigned char* smraw, const T_* __restrict__ xt,
+                                             const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                             T_* __restrict__ xq) {
   constexpr int S = PH_WARP_DIM;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int idx = blockIdx.x * PH_WARPS + w;
-  if (idx >= nlist) return;  // whole warps leave; nothing below synchronises the block
-  const int x = xlist[idx];
-  if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const bool two = D.x_cls[x] == 0;
   const int nm = two ? 2 : 1;
@@ -457,6 +435,33 @@ __global__ void __launch_bounds__(PH_WARPS * 32) k_ph_warp(DevState D, const Loo
   }
 }
 
+// The ph term in one launch over the S_z >= 0 cross channels (xlist): the first nblk CTAs take
+// one channel each (the costliest first), with the S_z > 0 or the S_z = 0 body chosen per
+// channel; the remaining CTAs take PH_WARPS small channels each, one per warp.
+template <typename T_, int NT, int TS, bool GATHER>
+__global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
+                                           const int* __restrict__ xlist, int nblk, int nwarp,
+                                           const T_* __restrict__ xt, const T_* __restrict__ xw,
+                                           const T_* __restrict__ xv1, T_* __restrict__ xq) {
+  static_assert(NT == PH_WARPS * 32, "one warp per small channel");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if ((int)blockIdx.x < nblk) {
+    const int x = xlist[blockIdx.x];
+    if (sys_done(D, ctl, D.x_sys[x])) return;  // CTA-uniform
+    if (D.x_cls[x] == 0)
+      ph_block<T_, NT, TS, 2, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
+    else
+      ph_block<T_, NT, TS, 1, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
+    return;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = ((int)blockIdx.x - nblk) * PH_WARPS + w;
+  if (idx >= nwarp) return;  // whole warps leave; the warp path never synchronises the block
+  const int x = xlist[nblk + idx];
+  if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
+  ph_warp_body<T_, GATHER>(D, ctl, x, w, lane, smraw, xt, xw, xv1, xq);
+}
+
 static size_t ph_warp_smem(size_t elem) {
   return (size_t)PH_WARPS * (6 * PH_WARP_DIM * PH_WARP_DIM * elem + 4 * PH_WARP_DIM * sizeof(int));
 }
@@ -469,7 +474,10 @@ size_t ph_smem_bytes(int max_dim, int nm, size_t elem) {
 }
 
 template <typename T_>
-static size_t ph_smem_of(const pnm_ctx* ctx) { return sizeof(T_) == 8 ? ctx->ph_smem64 : ctx->ph_smem32; }
+static size_t ph_smem_of(const pnm_ctx* ctx) {
+  size_t b = sizeof(T_) == 8 ? ctx->ph_smem64 : ctx->ph_smem32;
+  return ctx->n_ph_warp > 0 ? std::max(b, ph_warp_smem(sizeof(T_))) : b;
+}
 
 // The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).  FP64:
 // 2 x 2 register tiles (little padding; the FP64 pipe bounds the kernel); FP32: 4 x 4 (fewer
@@ -477,19 +485,16 @@ static size_t ph_smem_of(const pnm_ctx* ctx) { return sizeof(T_) == 8 ? ctx->ph_
 template <typename T_, bool GATHER>
 static void launch_ph_list(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
   constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
-  if (ctx->n_ph > 0)
-    k_ph<T_, PH_THREADS, TS, GATHER><<<ctx->n_ph, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
-        ctx->d, ctx->ctl, ctx->ph_list, xt, xw, xv1, xq);
-  if (ctx->n_ph_warp > 0)
-    k_ph_warp<T_, GATHER><<<(ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS, PH_WARPS * 32, ph_warp_smem(sizeof(T_)), s>>>(
-        ctx->d, ctx->ctl, ctx->ph_list + ctx->n_ph, ctx->n_ph_warp, xt, xw, xv1, xq);
+  int grid = ctx->n_ph + (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
+  if (grid > 0)
+    k_ph<T_, PH_THREADS, TS, GATHER><<<grid, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
+        ctx->d, ctx->ctl, ctx->ph_list, ctx->n_ph, ctx->n_ph_warp, xt, xw, xv1, xq);
 }
 
 template <typename T_, bool GATHER>
 static void ph_attributes(const pnm_ctx* ctx) {
   constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
   smem_at_least(k_ph<T_, PH_THREADS, TS, GATHER>, ph_smem_of<T_>(ctx));
-  smem_at_least(k_ph_warp<T_, GATHER>, ph_warp_smem(sizeof(T_)));
 }
 
 // FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
@@ -1580,8 +1585,7 @@ void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
 // the highest, so that the shorter branches (pp ladder, one-body sums) are dispatched ahead of
 // the many ph CTAs and run beside them instead of after them.
 static bool is_ph_kernel(const void* f) {
-  return f == (const void*)k_ph<double, PH_THREADS, 2, true> || f == (const void*)k_ph<float, PH_THREADS, 4, false> ||
-         f == (const void*)k_ph_warp<double, true> || f == (const void*)k_ph_warp<float, false>;
+  return f == (const void*)k_ph<double, PH_THREADS, 2, true> || f == (const void*)k_ph<float, PH_THREADS, 4, false>;
 }
 
 static void set_node_priorities(cudaGraph_t body) {

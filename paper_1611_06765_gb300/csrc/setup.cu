@@ -501,14 +501,15 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
 // The global spin flip F (every state to the one of opposite spin) leaves H and the
 // spin-saturated reference unchanged, so the amplitudes of the solution obey
 // t(F i, F j; F a, F b) = t(i, j; a, b) and every cross-channel matrix M of the ph term
-// (T, W, <kb|v|cj>, Q) obeys M_F(x)[F r][F c] = M_x[r][c].  One thread per cross channel of a
-// system records:
+// (T, W, <kb|v|cj>, Q) obeys M_F(x)[F r][F c] = M_x[r][c].  For every cross channel of a
+// system it records:
 //   x_cls   +1 for S_z = s_a - s_i > 0 (computed, Q also written to its mirror F(x)), 0 for
 //           S_z = 0 (F maps the channel onto itself), -1 for S_z < 0 (filled from its mirror);
 //   x_mir   the channel F(x);  x_frow / x_fcol  the row (column) of F(x) holding F(row), F(col);
 //   x_rrow / x_rcol (S_z = 0)  the rows (a,i) and columns (k,c) with spin-up a and k, in order
 //           (half of each: the other half are their flips).
 // Sets *err when a table is not closed under F (a reference that is not spin saturated).
+// One warp per channel; the spin-up rows and columns are compacted in order with ballots.
 __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
                         const int* __restrict__ x_ph_off, const int* __restrict__ x_hp_off,
                         const int2* __restrict__ ph_pair, const int2* __restrict__ hp_pair,
@@ -517,38 +518,64 @@ __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const in
                         const int* __restrict__ phch, const int* __restrict__ hppos, int* __restrict__ x_cls,
                         int* __restrict__ x_mir, int* __restrict__ x_frow, int* __restrict__ x_fcol,
                         int* __restrict__ x_rrow, int* __restrict__ x_rcol, int* __restrict__ err) {
-  int xl = blockIdx.x * blockDim.x + threadIdx.x;
-  if (xl >= nxs) return;
-  int x = x0 + xl;
-  int nph = x_nph[x], nhp = x_nhp[x], po = x_ph_off[x], ho = x_hp_off[x];
+  const int xl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (xl >= nxs) return;  // warp-uniform
+  const unsigned lt = (1u << lane) - 1u;
+  const int x = x0 + xl;
+  const int nph = x_nph[x], nhp = x_nhp[x], po = x_ph_off[x], ho = x_hp_off[x];
   const char4* nv = nvec + sp_off;
-  int np = nsp - N;
+  const int np = nsp - N;
   bool bad = nph <= 0 || nhp <= 0;
   int sz = 0, mir = -1, nr = 0, nc = 0;
   if (!bad) {
     int2 p0 = ph_pair[po];
     sz = spin_of(nv[p0.x - sp_off].w, species) - spin_of(nv[p0.y - sp_off].w, species);
   }
-  for (int k = 0; k < nph && !bad; k++) {
-    int2 ai = ph_pair[po + k];
-    int a = ai.x - sp_off, i = ai.y - sp_off;
-    int fa = flip_state(nv, idx3, r, a, species), fi = flip_state(nv, idx3, r, i, species);
-    if (fa < N || fi < 0 || fi >= N) { bad = true; break; }
-    size_t u = (size_t)(fa - N) * N + fi;
-    int ch = phch[u];
-    if (ch < 0 || (mir >= 0 && ch != mir)) { bad = true; break; }
-    mir = ch;
-    x_frow[po + k] = phpos[u];
-    if (sz == 0 && spin_of(nv[a].w, species) > 0) x_rrow[po + nr++] = k;
+  for (int k0 = 0; k0 < nph && !bad; k0 += 32) {
+    const int k = k0 + lane;
+    bool lbad = false, up = false;
+    int ch = -1;
+    if (k < nph) {
+      int2 ai = ph_pair[po + k];
+      int a = ai.x - sp_off, i = ai.y - sp_off;
+      int fa = flip_state(nv, idx3, r, a, species), fi = flip_state(nv, idx3, r, i, species);
+      if (fa < N || fi < 0 || fi >= N) {
+        lbad = true;
+      } else {
+        size_t u = (size_t)(fa - N) * N + fi;
+        ch = phch[u];
+        if (ch < 0) lbad = true;
+        else x_frow[po + k] = phpos[u];
+        up = sz == 0 && spin_of(nv[a].w, species) > 0;
+      }
+    }
+    if (mir < 0) mir = __shfl_sync(0xffffffffu, ch, 0);
+    bad = __any_sync(0xffffffffu, lbad || (k < nph && ch != mir));
+    unsigned bu = __ballot_sync(0xffffffffu, up);
+    if (up) x_rrow[po + nr + __popc(bu & lt)] = k;
+    nr += __popc(bu);
   }
-  for (int k = 0; k < nhp && !bad; k++) {
-    int2 hc = hp_pair[ho + k];
-    int h = hc.x - sp_off, p = hc.y - sp_off;
-    int fh = flip_state(nv, idx3, r, h, species), fp = flip_state(nv, idx3, r, p, species);
-    if (fh < 0 || fh >= N || fp < N) { bad = true; break; }
-    x_fcol[ho + k] = hppos[(size_t)fh * np + (fp - N)];
-    if (sz == 0 && spin_of(nv[h].w, species) > 0) x_rcol[ho + nc++] = k;
+  for (int k0 = 0; k0 < nhp && !bad; k0 += 32) {
+    const int k = k0 + lane;
+    bool lbad = false, up = false;
+    if (k < nhp) {
+      int2 hc = hp_pair[ho + k];
+      int h = hc.x - sp_off, p = hc.y - sp_off;
+      int fh = flip_state(nv, idx3, r, h, species), fp = flip_state(nv, idx3, r, p, species);
+      if (fh < 0 || fh >= N || fp < N) {
+        lbad = true;
+      } else {
+        x_fcol[ho + k] = hppos[(size_t)fh * np + (fp - N)];
+        up = sz == 0 && spin_of(nv[h].w, species) > 0;
+      }
+    }
+    bad = __any_sync(0xffffffffu, lbad);
+    unsigned bu = __ballot_sync(0xffffffffu, up);
+    if (up) x_rcol[ho + nc + __popc(bu & lt)] = k;
+    nc += __popc(bu);
   }
+  if (lane != 0) return;
   if (!bad && sz == 0 && (2 * nr != nph || 2 * nc != nhp || mir != xl)) bad = true;
   if (!bad && sz != 0 && mir == xl) bad = true;
   x_cls[x] = sz > 0 ? 1 : (sz == 0 ? 0 : -1);
@@ -1178,7 +1205,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
                                  D.ph_pair, D.hp_pair, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M,
                                  S.species, X.key2ch, S.ch_begin, D.ch_t_off, D.ch_npp, X.pos_hh, X.pos_pp,
                                  D.xmap);
-      k_xflip<<<(nxs + 127) / 128, 128, 0, s>>>(S.x_begin, nxs, D.x_nph, D.x_nhp, D.x_ph_off, D.x_hp_off,
+      k_xflip<<<(nxs * 32 + 255) / 256, 256, 0, s>>>(S.x_begin, nxs, D.x_nph, D.x_nhp, D.x_ph_off, D.x_hp_off,
                                                 D.ph_pair, D.hp_pair, D.nvec, X.idx3, S.r, S.species,
                                                 S.sp_off, S.N, S.nsp, X.phpos, X.phch, X.hppos, D.x_cls,
                                                 D.x_mir, D.x_frow, D.x_fcol, D.x_rrow, D.x_rcol, flip_err);
