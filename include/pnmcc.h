@@ -61,9 +61,10 @@ typedef struct {
 /* Kept and learned starts are first symmetrised under the global spin flip F (every state to
  * the one of opposite spin): t <- (t + F t)/2.  F commutes with H and leaves the
  * spin-saturated reference unchanged, so the solution is flip-symmetric, and the iteration
- * forms the ph term for flip-symmetric amplitudes only (S_z < 0 cross channels are mirrors of
- * S_z > 0 ones; S_z = 0 channels split into half-size sum and difference blocks).  MBPT2 and
- * zero starts are symmetric already. */
+ * works on flip-symmetric amplitudes only: the ph term is formed for S_z >= 0 cross channels
+ * (S_z = 0 ones as half-size sum and difference blocks) and read at the flip elsewhere, and
+ * the update computes one amplitude of each flip pair and writes both.  MBPT2 and zero starts
+ * are symmetric already. */
 
 /* Terms the iteration keeps (Sec. "Coupled cluster theory"):
  *   PNM_TERMS_FULL    Eq. (ccd3);

@@ -108,8 +108,9 @@ __global__ void k_dchi(DevState D, int nsp_total) {
 }
 
 // ----------------------------------------------------------------------------- ph term
-// Global spin flip: Q is computed for the cross channels with S_z > 0 (and written to their
-// mirrors with S_z < 0 as well) and for the S_z = 0 channels on their spin-up half.  In an
+// Global spin flip: Q is formed for the cross channels with S_z > 0 and for the spin-up rows of
+// the S_z = 0 channels; the update reads every other position at its flip (same value for
+// flip-symmetric amplitudes; qmap holds the formed positions only).  In an
 // S_z = 0 channel, with rows ordered (spin-up rows u, their flips F u) and columns alike,
 // every matrix of the term has the block form [[A, B], [B, A]] (A = M[u][v], B = M[u][F v]);
 // products of such matrices are formed from the half-size sums A + B and differences A - B,
@@ -160,13 +161,12 @@ __device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__
   }
 }
 
-// Bytes of the index tables at the start of a k_ph CTA's shared memory (2 R4 + 2 H4 ints,
-// a multiple of 16 since R4 and H4 are multiples of 4).
+// Bytes reserved for the index tables at the start of a k_ph CTA's shared memory (R4 + 2 H4
+// ints are used; 2 (R4 + H4) keeps the reservation a multiple of 16 bytes).
 __host__ __device__ __forceinline__ size_t ph_index_bytes(int R4, int H4) { return sizeof(int) * 2 * (size_t)(R4 + H4); }
 
-// One CTA (NT threads) per cross channel of the launch's class.  NM = 1: a channel with
-// S_z > 0, its Q also written to the mirror channel.  NM = 2: an S_z = 0 channel as the pair
-// (sum, difference) of half-size problems.  Per problem, in shared memory zero-padded to
+// One CTA (NT threads) per cross channel.  NM = 1: a channel with S_z > 0.  NM = 2: an S_z = 0
+// channel as the pair (sum, difference) of half-size problems, Q written on its spin-up rows.  Per problem, in shared memory zero-padded to
 // multiples of 4 (R rows (a,i), H columns (k,c)):
 //   Ts = T (R x H), Xt = W^T staged as W (R x H), then T^T (H x R), Cs = C (H x H);
 //   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_(e,l) <kl|v|ce> t_lj^eb   (xw == nullptr: <kb|v|cj>)
@@ -181,34 +181,27 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
   const int R = NM == 2 ? nph >> 1 : nph, H = NM == 2 ? nhp >> 1 : nhp;
   const int R4 = (R + 3) & ~3, H4 = (H + 3) & ~3;
   const int RH = R4 * H4, HH = H4 * H4;
-  // index tables in shared memory first (no chains of dependent global loads below):
-  // NM = 1: sfr[r] = row of F(r) in the mirror, sfc[s] = column of F(s);
-  // NM = 2: sra[u] = spin-up row, srb[u] = its flip, sca[v] = spin-up column, scb[v] = its flip
+  // NM = 2: index tables in shared memory first (no chains of dependent global loads below):
+  // sra[u] = spin-up row, sca[v] = spin-up column, scb[v] = its flip
   int* sra = reinterpret_cast<int*>(smraw);
-  int* srb = sra + R4;
-  int* sca = srb + R4;
+  int* sca = sra + R4;
   int* scb = sca + H4;
   T_* Ts = reinterpret_cast<T_*>(smraw + ph_index_bytes(R4, H4));
   T_* Xt = Ts + NM * RH;
   T_* Cs = Xt + NM * RH;
   const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  {
-    const int* __restrict__ frow = D.x_frow + D.x_ph_off[x];
+  if constexpr (NM == 2) {
     const int* __restrict__ fcol = D.x_fcol + D.x_hp_off[x];
     const int* __restrict__ rrow = D.x_rrow + D.x_ph_off[x];
     const int* __restrict__ rcol = D.x_rcol + D.x_hp_off[x];
-    for (int k = threadIdx.x; k < R4; k += NT) {
-      int a = k < R ? (NM == 2 ? rrow[k] : k) : 0;
-      sra[k] = a;
-      srb[k] = k < R ? frow[a] : 0;
-    }
+    for (int k = threadIdx.x; k < R4; k += NT) sra[k] = k < R ? rrow[k] : 0;
     for (int k = threadIdx.x; k < H4; k += NT) {
-      int a = k < H ? (NM == 2 ? rcol[k] : k) : 0;
+      int a = k < H ? rcol[k] : 0;
       sca[k] = a;
       scb[k] = k < H ? fcol[a] : 0;
     }
+    __syncthreads();
   }
-  __syncthreads();
   const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
   const bool quad = xw != nullptr;
 #pragma unroll 4
@@ -291,7 +284,6 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
   }
   __syncthreads();
   const int tr = R4 / TS;
-  const long mo = NM == 1 ? D.x_t_off[D.x_mir[x]] : 0;
   for (int tile = threadIdx.x; tile < tr * th; tile += NT) {
     const int r0 = (tile / th) * TS, s0 = (tile % th) * TS;
     T_ acc[NM][TS][TS] = {};
@@ -312,27 +304,19 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
       const int r = r0 + i;
       if (r >= R) continue;
       if constexpr (NM == 1) {
-        const long qr = to + (long)r * nhp, mr = mo + (long)srb[r] * nhp;
+        const long qr = to + (long)r * nhp;
 #pragma unroll
-        for (int j = 0; j < TS; j++) {
-          const int s = s0 + j;
-          if (s < H) {
-            xq[qr + s] = acc[0][i][j];
-            xq[mr + scb[s]] = acc[0][i][j];
-          }
-        }
+        for (int j = 0; j < TS; j++)
+          if (s0 + j < H) xq[qr + s0 + j] = acc[0][i][j];
       } else {
-        const long qa = to + (long)sra[r] * nhp, qb = to + (long)srb[r] * nhp;
+        // the spin-up row's two blocks; the flipped rows are never read (see qpos)
+        const long qa = to + (long)sra[r] * nhp;
 #pragma unroll
         for (int j = 0; j < TS; j++) {
           const int s = s0 + j;
           if (s < H) {
-            const int ca = sca[s], cb = scb[s];
-            const T_ A = (T_)0.5 * (acc[0][i][j] + acc[1][i][j]), B = (T_)0.5 * (acc[0][i][j] - acc[1][i][j]);
-            xq[qa + ca] = A;
-            xq[qa + cb] = B;
-            xq[qb + ca] = B;
-            xq[qb + cb] = A;
+            xq[qa + sca[s]] = (T_)0.5 * (acc[0][i][j] + acc[1][i][j]);
+            xq[qa + scb[s]] = (T_)0.5 * (acc[0][i][j] - acc[1][i][j]);
           }
         }
       }
@@ -355,26 +339,19 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
   const int nm = two ? 2 : 1;
   const int R = two ? nph >> 1 : nph, H = two ? nhp >> 1 : nhp;
   const long to = D.x_t_off[x], wo = D.x_w_off[x], co = D.x_c_off[x];
-  const long mo = two ? to : D.x_t_off[D.x_mir[x]];
   T_* Ts = reinterpret_cast<T_*>(smraw) + (size_t)w * 6 * S * S;  // [m][u][s]
   T_* Ws = Ts + 2 * S * S;                                         // [m][u][r] = W[u][r]
   T_* Cs = Ws + 2 * S * S;                                         // [m][r][s]
-  int* sra = reinterpret_cast<int*>(reinterpret_cast<T_*>(smraw) + (size_t)PH_WARPS * 6 * S * S) + w * 4 * S;
-  int* srb = sra + S;
-  int* sca = srb + S;
+  int* sra = reinterpret_cast<int*>(reinterpret_cast<T_*>(smraw) + (size_t)PH_WARPS * 6 * S * S) + w * 3 * S;
+  int* sca = sra + S;
   int* scb = sca + S;
-  {
-    const int* __restrict__ frow = D.x_frow + D.x_ph_off[x];
+  if (two) {
     const int* __restrict__ fcol = D.x_fcol + D.x_hp_off[x];
     const int* __restrict__ rrow = D.x_rrow + D.x_ph_off[x];
     const int* __restrict__ rcol = D.x_rcol + D.x_hp_off[x];
-    if (lane < R) {
-      int a = two ? rrow[lane] : lane;
-      sra[lane] = a;
-      srb[lane] = frow[a];
-    }
+    if (lane < R) sra[lane] = rrow[lane];
     if (lane < H) {
-      int a = two ? rcol[lane] : lane;
+      int a = rcol[lane];
       sca[lane] = a;
       scb[lane] = fcol[a];
     }
@@ -422,15 +399,11 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
     for (int m = 0; m < nm; m++)
       for (int u = 0; u < H; u++) acc[m] += Ts[m * S * S + r * S + u] * Cs[m * S * S + u * S + c];
     if (two) {
-      const T_ A = (T_)0.5 * (acc[0] + acc[1]), B = (T_)0.5 * (acc[0] - acc[1]);
-      const long qa = to + (long)sra[r] * nhp, qb = to + (long)srb[r] * nhp;
-      xq[qa + sca[c]] = A;
-      xq[qa + scb[c]] = B;
-      xq[qb + sca[c]] = B;
-      xq[qb + scb[c]] = A;
+      const long qa = to + (long)sra[r] * nhp;
+      xq[qa + sca[c]] = (T_)0.5 * (acc[0] + acc[1]);
+      xq[qa + scb[c]] = (T_)0.5 * (acc[0] - acc[1]);
     } else {
       xq[to + (long)r * nhp + c] = acc[0];
-      xq[mo + (long)srb[r] * nhp + scb[c]] = acc[0];
     }
   }
 }
@@ -463,7 +436,7 @@ __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict
 }
 
 static size_t ph_warp_smem(size_t elem) {
-  return (size_t)PH_WARPS * (6 * PH_WARP_DIM * PH_WARP_DIM * elem + 4 * PH_WARP_DIM * sizeof(int));
+  return (size_t)PH_WARPS * (6 * PH_WARP_DIM * PH_WARP_DIM * elem + 3 * PH_WARP_DIM * sizeof(int));
 }
 
 // Shared memory of a k_ph CTA for channels of at most max_dim (NM = 1) or 2 max_dim (NM = 2)
@@ -720,12 +693,13 @@ __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
                                                 const int4* __restrict__ items, FinArgs fa) {
   // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng;
-  // per row: d_i + d_j of the one-body term
+  // per row: its hole pair ij and d_i + d_j of the one-body term
   __shared__ double chs[UPD_MAX_NHH][UPD_ROWS];
   __shared__ double row_dij[UPD_ROWS];
+  __shared__ int row_ij[UPD_ROWS];
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
-  int c = it.x, ij0 = it.y, ng = it.w;
+  int c = it.x, ng = it.w;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   int ab = it.z + threadIdx.x;
   bool frozen = fa.sc[D.ch_sys[c]].done != 0;
@@ -744,14 +718,17 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   double* __restrict__ tn = next_t(D, ctl);
   long base = D.ch_t_off[c];
   long vho = D.ch_vhh_off[c];
-  for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
-    int kl = e / UPD_ROWS, g = e % UPD_ROWS;
-    chs[kl][g] = g < ng ? D.chi_hh[vho + (long)kl * nh + ij0 + g] : 0.0;
-  }
   if ((int)threadIdx.x < UPD_ROWS) {
     int g = min((int)threadIdx.x, ng - 1);
-    int2 h = D.hh_pair[D.ch_hh_off[c] + ij0 + g];
+    int ij = D.upd_row[it.y + g];
+    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+    row_ij[threadIdx.x] = ij;
     row_dij[threadIdx.x] = D.dchi[h.x] + D.dchi[h.y];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
+    int kl = e / UPD_ROWS, g = e % UPD_ROWS;
+    chs[kl][g] = g < ng ? D.chi_hh[vho + (long)kl * nh + row_ij[g]] : 0.0;
   }
   __syncthreads();
   double esum = 0.0, rsum = 0.0;
@@ -775,7 +752,13 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
 #pragma unroll
     for (int g = 0; g < UPD_ROWS; g++) {
       if (g >= ng) break;
-      long z = base + (long)(ij0 + g) * npp + ab;
+      long z = base + (long)row_ij[g] * npp + ab;
+      // one amplitude of each spin-flip pair is computed (the one with the smaller index) and
+      // written to both; the pair counts twice in the energy and the residual norm
+      const int fc = D.fmap[z];
+      const long f = (long)(fc > 0 ? fc : -fc) - 1;
+      if (f < z) continue;
+      const double wgt = f == z ? 1.0 : 2.0;
       double tz = t[z];
       double out = tz;
       double v = D.v_pphh[z];
@@ -784,23 +767,24 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
         double num = v + (da - row_dij[g]) * tz;
         if (has_vpp) {
           int sg;
-          double rl = D.rpp[lad_index(D, c, ij0 + g, ab, sg)];
+          double rl = D.rpp[lad_index(D, c, row_ij[g], ab, sg)];
           num += sg > 0 ? rl : -rl;
         }
         num += hh[g];
         double ph = 0.0;
-        if (q.x >= 0) ph += D.xq[qpos_of(q.x)];
-        if (q.y >= 0) ph -= D.xq[qpos_of(q.y)];
-        if (q.z >= 0) ph -= D.xq[qpos_of(q.z)];
-        if (q.w >= 0) ph += D.xq[qpos_of(q.w)];
+        if (q.x >= 0) ph += D.xq[q.x];
+        if (q.y >= 0) ph -= D.xq[q.y];
+        if (q.z >= 0) ph -= D.xq[q.z];
+        if (q.w >= 0) ph += D.xq[q.w];
         num += ph;
         double tnew = num * D.inv_den[z];
         double R = num - D.den[z] * tz;
-        rsum += R * R;
+        rsum += wgt * (R * R);
         out = alpha * tnew + (1.0 - alpha) * tz;
       }
       tn[z] = out;
-      esum = fma(v, out, esum);
+      if (f != z) tn[f] = fc > 0 ? out : -out;
+      esum = fma(wgt * v, out, esum);
     }
   }
   block_sum2(esum, rsum, sh32);
@@ -870,14 +854,17 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
                                                     long pstride) {
   __shared__ float row_dij[UPD_ROWS];
   __shared__ double row_eij[UPD_ROWS];
+  __shared__ int row_ij[UPD_ROWS];
   __shared__ double sh32[32];
   int4 it = items[blockIdx.x];
-  int c = it.x, ij0 = it.y, ng = it.w;
+  int c = it.x, ng = it.w;
   int npp = D.ch_npp[c];
   int ab = it.z + threadIdx.x;
   if ((int)threadIdx.x < UPD_ROWS) {
     int g = min((int)threadIdx.x, ng - 1);
-    int2 h = D.hh_pair[D.ch_hh_off[c] + ij0 + g];
+    int ij = D.upd_row[it.y + g];
+    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+    row_ij[threadIdx.x] = ij;
     row_dij[threadIdx.x] = D.dchi32[h.x] + D.dchi32[h.y];
     row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
   }
@@ -910,20 +897,22 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
       long z[UPD_BATCH];
       double tz[UPD_BATCH], v[UPD_BATCH], idn[UPD_BATCH];
       int4 q[UPD_BATCH];
+      int fc[UPD_BATCH];
       float t32z[UPD_BATCH], part[UPD_BATCH], qs[UPD_BATCH];
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
         int g = min(gb + j, ng - 1);
-        z[j] = base + (long)(ij0 + g) * npp + ab;
+        z[j] = base + (long)row_ij[g] * npp + ab;
         tz[j] = t[z[j]];
         v[j] = D.v_pphh[z[j]];
         q[j] = D.qmap[z[j]];
+        fc[j] = D.fmap[z[j]];
         t32z[j] = t32[z[j]];
         idn[j] = D.inv_den[z[j]];
         part[j] = hh[z[j]];
         if (has_vpp) {
           int sg;
-          long zl = lad_index(D, c, ij0 + g, ab, sg);
+          long zl = lad_index(D, c, row_ij[g], ab, sg);
           float rl = 0.0f;
           for (int pl = 0; pl < nplanes; pl++) rl += rpp[pl * pstride + zl];
           part[j] += sg > 0 ? rl : -rl;
@@ -932,33 +921,42 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
         // P(ij)P(ab) Q: Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba from the cross-channel layout
-        float a0 = q[j].x >= 0 ? xq[qpos_of(q[j].x)] : 0.0f, a1 = q[j].y >= 0 ? xq[qpos_of(q[j].y)] : 0.0f;
-        float a2 = q[j].z >= 0 ? xq[qpos_of(q[j].z)] : 0.0f, a3 = q[j].w >= 0 ? xq[qpos_of(q[j].w)] : 0.0f;
+        float a0 = q[j].x >= 0 ? xq[q[j].x] : 0.0f, a1 = q[j].y >= 0 ? xq[q[j].y] : 0.0f;
+        float a2 = q[j].z >= 0 ? xq[q[j].z] : 0.0f, a3 = q[j].w >= 0 ? xq[q[j].w] : 0.0f;
         qs[j] = (a0 - a1) - (a2 - a3);
       }
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
         int g = gb + j;
         if (g >= ng) break;
+        // one amplitude of each spin-flip pair is computed (the smaller index) and written to
+        // both; the pair counts twice in the energy and the residual norm
+        const long f = (long)(fc[j] > 0 ? fc[j] : -fc[j]) - 1;
+        if (f < z[j]) continue;
+        const double wgt = f == z[j] ? 1.0 : 2.0;
         double out = tz[j];
         if (!frozen) {
           float corr = (dab - row_dij[g]) * t32z[j] + part[j] + qs[j];
           double num = v[j] + (double)corr;
           double R = fma(eab - row_eij[g], tz[j], num);  // bracket - eps_ij^ab t
-          rsum = fma(R, R, rsum);
+          rsum = fma(wgt * R, R, rsum);
           out = fma(alpha * R, idn[j], tz[j]);
         }
         tn[z[j]] = out;
-        esum = fma(v[j], out, esum);
+        esum = fma(wgt * v[j], out, esum);
         float o32 = (float)out;
         t32n[z[j]] = o32;
+        if (f != z[j]) {
+          tn[f] = fc[j] > 0 ? out : -out;
+          t32n[f] = fc[j] > 0 ? o32 : -o32;
+        }
         if (pk.xt) {
           // the Q positions of P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba
-          // (those the ph kernels read; flagged ones are skipped, as are -1)
-          if (!(q[j].x & QPOS_SKIP_T)) pk.xt[q[j].x] = o32;
-          if (!(q[j].y & QPOS_SKIP_T)) pk.xt[q[j].y] = -o32;
-          if (!(q[j].z & QPOS_SKIP_T)) pk.xt[q[j].z] = -o32;
-          if (!(q[j].w & QPOS_SKIP_T)) pk.xt[q[j].w] = o32;
+          // (formed positions only, so the same for the amplitude and its spin flip)
+          if (q[j].x >= 0) pk.xt[q[j].x] = o32;
+          if (q[j].y >= 0) pk.xt[q[j].y] = -o32;
+          if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
+          if (q[j].w >= 0) pk.xt[q[j].w] = o32;
         }
       }
     }
@@ -985,6 +983,20 @@ void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const fl
 void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s) {
   if (ctx->n_ab_items > 0)
     k_hh32<<<ctx->n_ab_items, 128, hh32_smem_bytes(ctx), s>>>(ctx->d, ctx->ctl, ctx->ab_items, hh);
+}
+
+// Per row (channel, ij) of the amplitudes: 2 if the spin flip maps it onto a later row (it is
+// computed by the updates), 0 onto an earlier one (written by that row's update), 1 onto
+// itself (its columns are paired among themselves).
+__global__ void k_row_mode(DevState D, int nrows, int* __restrict__ mode) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int2 it = D.row_item[r];
+  int npp = D.ch_npp[it.x];
+  long z0 = D.ch_t_off[it.x] + (long)it.y * npp;
+  int cd = D.fmap[z0];
+  long f0 = (long)(cd > 0 ? cd : -cd) - 1;
+  mode[r] = (f0 >= z0 && f0 < z0 + npp) ? 1 : (f0 > z0 ? 2 : 0);
 }
 
 // t <- (t + F t) / 2 under the global spin flip F (fmap).  The solution is flip-symmetric
@@ -1148,15 +1160,39 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   int dev = 0, nsm = 148;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // rows the updates compute: of two rows that the spin flip maps onto each other the one
+  // whose amplitudes come first, and the rows it maps onto themselves (half of their
+  // columns); per channel a run of the list upd_row, which update items index
+  std::vector<int> rmode(ctx->nrows, 2);
+  if (ctx->nrows > 0) {
+    int* dm = (int*)dmalloc(ctx, sizeof(int) * ctx->nrows);
+    k_row_mode<<<(ctx->nrows + 255) / 256, 256, 0, s>>>(ctx->d, ctx->nrows, dm);
+    CUDA_TRY(cudaMemcpyAsync(rmode.data(), dm, sizeof(int) * ctx->nrows, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  std::vector<int> urow, uoff(ctx->nch + 1, 0), ucnt(ctx->nch, 0);
+  for (int r = 0; r < ctx->nrows; r++)
+    if (rmode[r]) ucnt[ctx->h_rows[r].x]++;
+  for (int c = 0; c < ctx->nch; c++) uoff[c + 1] = uoff[c] + ucnt[c];
+  urow.resize(uoff[ctx->nch]);
+  std::fill(ucnt.begin(), ucnt.end(), 0);
+  for (int r = 0; r < ctx->nrows; r++)
+    if (rmode[r]) {
+      int c = ctx->h_rows[r].x;
+      urow[uoff[c] + ucnt[c]++] = ctx->h_rows[r].y;
+    }
+  ctx->d.upd_row = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, urow.size()));
+  if (!urow.empty())
+    CUDA_TRY(cudaMemcpyAsync(ctx->d.upd_row, urow.data(), sizeof(int) * urow.size(), cudaMemcpyHostToDevice, s));
   auto group_items = [&](int G, std::vector<int4>* out, std::vector<int>* glo, std::vector<int>* ghi) {
     size_t n = 0;
     for (int k = 0; k < nsys; k++) {
       if (glo) (*glo)[k] = (int)(out ? out->size() : n);
       for (int c = ctx->sys[k].ch_begin; c < ctx->sys[k].ch_end; c++) {
-        int nh = ctx->h_nhh[c], np = ctx->h_npp[c];
-        for (int ij0 = 0; ij0 < nh; ij0 += G)
+        int nr = uoff[c + 1] - uoff[c], np = ctx->h_npp[c];
+        for (int r0 = 0; r0 < nr; r0 += G)
           for (int ab0 = 0; ab0 < np; ab0 += 128) {
-            if (out) out->push_back(make_int4(c, ij0, ab0, std::min(G, nh - ij0)));
+            if (out) out->push_back(make_int4(c, uoff[c] + r0, ab0, std::min(G, nr - r0)));
             n++;
           }
       }
@@ -1240,7 +1276,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->sysctl = (SysCtl*)dmalloc(ctx, sizeof(SysCtl) * nsys);
   CUDA_TRY(cudaMemsetAsync(ctx->sysctl, 0, sizeof(SysCtl) * nsys, s));
   ctx->d.sysctl = ctx->sysctl;
-  // cross channels of the ph launch: S_z >= 0 (S_z < 0 ones are mirrors), costliest first;
+  // cross channels of the ph launch: S_z >= 0 (S_z < 0 ones are read at their flips), costliest first;
   // shared memory for the largest (NM = 1: rows/columns; NM = 2: those of the halves, twice)
   std::vector<int> xl, xw;  // CTA per channel; warp per channel (at most PH_WARP_DIM)
   std::vector<long> xcost(ctx->nx, 0);
@@ -1354,10 +1390,10 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
     e5 += tz * hh;
     int4 q = D.qmap[z];
     double ph = 0.0;
-    if (q.x >= 0) ph += D.xq[qpos_of(q.x)];
-    if (q.y >= 0) ph -= D.xq[qpos_of(q.y)];
-    if (q.z >= 0) ph -= D.xq[qpos_of(q.z)];
-    if (q.w >= 0) ph += D.xq[qpos_of(q.w)];
+    if (q.x >= 0) ph += D.xq[q.x];
+    if (q.y >= 0) ph -= D.xq[q.y];
+    if (q.z >= 0) ph -= D.xq[q.z];
+    if (q.w >= 0) ph += D.xq[q.w];
     e3 += tz * ph;
   }
   e4 = block_sum(e4, sh32);

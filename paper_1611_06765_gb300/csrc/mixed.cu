@@ -701,8 +701,8 @@ __global__ void k_ph_assemble(DevState D, const T* __restrict__ xq, long nt, dou
   long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= nt) return;
   int4 q = D.qmap[z];
-  double a0 = q.x >= 0 ? (double)xq[qpos_of(q.x)] : 0.0, a1 = q.y >= 0 ? (double)xq[qpos_of(q.y)] : 0.0;
-  double a2 = q.z >= 0 ? (double)xq[qpos_of(q.z)] : 0.0, a3 = q.w >= 0 ? (double)xq[qpos_of(q.w)] : 0.0;
+  double a0 = q.x >= 0 ? (double)xq[q.x] : 0.0, a1 = q.y >= 0 ? (double)xq[q.y] : 0.0;
+  double a2 = q.z >= 0 ? (double)xq[q.z] : 0.0, a3 = q.w >= 0 ? (double)xq[q.w] : 0.0;
   out[z] = (a0 - a1) - (a2 - a3);
 }
 

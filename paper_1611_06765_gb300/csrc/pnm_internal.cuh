@@ -82,15 +82,17 @@ struct DevState {
   int2 *ph_pair, *hp_pair;
   int* x_ph_off;
   int* x_hp_off;
-  // global spin flip F: class of each cross channel (+1: S_z > 0, computed and mirrored;
-  // 0: S_z = 0, computed on its spin-up half; -1: S_z < 0, filled from its mirror), the mirror
-  // channel, the flipped row of every ph row and column of every hp column, and for S_z = 0
-  // channels the spin-up rows and columns (first half of the channel's slots)
-  int *x_cls, *x_mir, *x_frow, *x_fcol, *x_rrow, *x_rcol;
+  // global spin flip F: class of each cross channel (+1: S_z > 0, formed in full; 0: S_z = 0,
+  // formed on its spin-up rows; -1: S_z < 0, not formed), the flipped column of every hp
+  // column, and for S_z = 0 channels the spin-up rows and columns (first half of the slots)
+  int *x_cls, *x_fcol, *x_rrow, *x_rcol;
   int* fmap;             // per t element: sign * (index + 1) of its spin-flipped element
+  // mixed and FP64 updates: the hole-pair rows they compute (flip representatives), per item
+  // a run of this list (items hold (channel, first entry, first column, rows))
+  int* upd_row;
   // maps
   int* xmap;             // per T element: sign * (t index + 1), 0 = structurally zero
-  int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q (QPOS_SKIP_T flag)
+  int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q (formed positions)
   int *occ_off, *occ_idx; // per state: pair indices (pp for particles, hh for holes)
   // blocks
   double *v_pphh, *v_pppp, *v_hhhh, *x_v1, *x_w;  // v_pppp: n_lad x n_lad per channel, ladder basis
@@ -177,12 +179,6 @@ struct FinArgs {
 #endif
 constexpr int UPD_ROWS = PNM_UPD_ROWS, UPD_MAX_NHH = 128, UPD_BATCH = PNM_UPD_BATCH;
 constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
-
-// qmap entries: the position of a Q element, which is also where the mixed update scatters
-// the corresponding T element, or -1.  Bit 30 marks positions whose T the ph kernels never read
-// (S_z < 0 cross channels, spin-down rows of S_z = 0 channels): no scatter there.
-constexpr int QPOS_SKIP_T = 1 << 30;
-__device__ __forceinline__ int qpos_of(int q) { return q & (QPOS_SKIP_T - 1); }
 
 // Threads of a ph-term CTA (one cross channel each); channels of at most PH_WARP_DIM rows and
 // columns (of their halves for S_z = 0) take one warp each.

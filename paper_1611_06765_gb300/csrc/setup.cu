@@ -451,21 +451,30 @@ __global__ void k_xmap(int x0, const int* __restrict__ x_nph, const int* __restr
 
 // For every restricted t element (ij, ab) of a row: the positions of
 // Q_ij^ab, Q_ji^ab, Q_ij^ba, Q_ji^ba with Q_ij^ab = Q_x[(a,i)][(j,b)].
-// Position of Q_x[(p,h)][(h2,p2)], flagged with QPOS_SKIP_T where the ph kernels never read T
-// (channels with S_z < 0 and the spin-down rows of S_z = 0 channels), or -1.
+// Position of Q_x[(p,h)][(h2,p2)], or -1.  The ph kernels form Q (and read T) only in the
+// cross channels with S_z >= 0 and, in those with S_z = 0, only in the rows of a spin-up
+// particle; every other position is replaced by that of its spin flip
+// Q_F(x)[(Fp,Fh)][(Fh2,Fp2)], which holds the same value for flip-symmetric amplitudes.
 __device__ __forceinline__ int qpos(int p, int h, int h2, int p2, int N, int np,
                                     const int* __restrict__ phch, const int* __restrict__ phpos,
                                     const int* __restrict__ hppos, int x0,
                                     const long* __restrict__ x_t_off,
                                     const int* __restrict__ x_nhp, const int* __restrict__ x_cls,
-                                    const char4* __restrict__ nv, int species) {
+                                    const char4* __restrict__ nv, const int* __restrict__ idx3, int r,
+                                    int species) {
   size_t u = (size_t)(p - N) * N + h;
   int x = phch[u];
   if (x < 0) return -1;
   int g = x0 + x;
-  int q = (int)(x_t_off[g] + (long)phpos[u] * x_nhp[g] + hppos[(size_t)h2 * np + (p2 - N)]);
-  bool skip = x_cls[g] < 0 || (x_cls[g] == 0 && spin_of(nv[p].w, species) < 0);
-  return skip ? (q | QPOS_SKIP_T) : q;
+  if (x_cls[g] < 0 || (x_cls[g] == 0 && spin_of(nv[p].w, species) < 0)) {
+    p = flip_state(nv, idx3, r, p, species);
+    h = flip_state(nv, idx3, r, h, species);
+    h2 = flip_state(nv, idx3, r, h2, species);
+    p2 = flip_state(nv, idx3, r, p2, species);
+    u = (size_t)(p - N) * N + h;
+    g = x0 + phch[u];
+  }
+  return (int)(x_t_off[g] + (long)phpos[u] * x_nhp[g] + hppos[(size_t)h2 * np + (p2 - N)]);
 }
 
 __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
@@ -475,8 +484,8 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
                        int sp_off, int N, int nsp, const int* __restrict__ phch,
                        const int* __restrict__ phpos, const int* __restrict__ hppos, int x0,
                        const long* __restrict__ x_t_off, const int* __restrict__ x_nhp,
-                       const int* __restrict__ x_cls, const char4* __restrict__ nvec, int species,
-                       int4* __restrict__ qmap) {
+                       const int* __restrict__ x_cls, const char4* __restrict__ nvec,
+                       const int* __restrict__ idx3, int r, int species, int4* __restrict__ qmap) {
   int2 it = row_item[row0 + blockIdx.x];
   int c = it.x, ij = it.y;
   int np = nsp - N;
@@ -489,10 +498,10 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
     int2 pb = pp_pair[ch_pp_off[c] + ab];
     int a = pb.x - sp_off, b = pb.y - sp_off;
     int4 q;
-    q.x = qpos(a, i, j, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
-    q.y = qpos(a, j, i, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
-    q.z = qpos(b, i, j, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
-    q.w = qpos(b, j, i, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, species);
+    q.x = qpos(a, i, j, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, idx3, r, species);
+    q.y = qpos(a, j, i, b, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, idx3, r, species);
+    q.z = qpos(b, i, j, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, idx3, r, species);
+    q.w = qpos(b, j, i, a, N, np, phch, phpos, hppos, x0, x_t_off, x_nhp, x_cls, nv, idx3, r, species);
     qmap[base + ab] = q;
   }
 }
@@ -503,12 +512,14 @@ __global__ void k_qmap(int row0, const int2* __restrict__ row_item,
 // t(F i, F j; F a, F b) = t(i, j; a, b) and every cross-channel matrix M of the ph term
 // (T, W, <kb|v|cj>, Q) obeys M_F(x)[F r][F c] = M_x[r][c].  For every cross channel of a
 // system it records:
-//   x_cls   +1 for S_z = s_a - s_i > 0 (computed, Q also written to its mirror F(x)), 0 for
-//           S_z = 0 (F maps the channel onto itself), -1 for S_z < 0 (filled from its mirror);
-//   x_mir   the channel F(x);  x_frow / x_fcol  the row (column) of F(x) holding F(row), F(col);
+//   x_cls   +1 for S_z = s_a - s_i > 0 (formed in full), 0 for S_z = 0 (F maps the channel
+//           onto itself; formed on its spin-up rows), -1 for S_z < 0 (not formed: the update
+//           reads the flipped channel F(x) instead, see qpos);
+//   x_fcol  per column (k,c) the column of (F k, F c) in F(x);
 //   x_rrow / x_rcol (S_z = 0)  the rows (a,i) and columns (k,c) with spin-up a and k, in order
 //           (half of each: the other half are their flips).
-// Sets *err when a table is not closed under F (a reference that is not spin saturated).
+// Sets *err when the rows or columns of a channel do not map onto one channel F(x) (a
+// reference that is not spin saturated).
 // One warp per channel; the spin-up rows and columns are compacted in order with ballots.
 __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const int* __restrict__ x_nhp,
                         const int* __restrict__ x_ph_off, const int* __restrict__ x_hp_off,
@@ -516,7 +527,7 @@ __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const in
                         const char4* __restrict__ nvec, const int* __restrict__ idx3, int r, int species,
                         int sp_off, int N, int nsp, const int* __restrict__ phpos,
                         const int* __restrict__ phch, const int* __restrict__ hppos, int* __restrict__ x_cls,
-                        int* __restrict__ x_mir, int* __restrict__ x_frow, int* __restrict__ x_fcol,
+                        int* __restrict__ x_fcol,
                         int* __restrict__ x_rrow, int* __restrict__ x_rcol, int* __restrict__ err) {
   const int xl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -546,7 +557,6 @@ __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const in
         size_t u = (size_t)(fa - N) * N + fi;
         ch = phch[u];
         if (ch < 0) lbad = true;
-        else x_frow[po + k] = phpos[u];
         up = sz == 0 && spin_of(nv[a].w, species) > 0;
       }
     }
@@ -579,7 +589,6 @@ __global__ void k_xflip(int x0, int nxs, const int* __restrict__ x_nph, const in
   if (!bad && sz == 0 && (2 * nr != nph || 2 * nc != nhp || mir != xl)) bad = true;
   if (!bad && sz != 0 && mir == xl) bad = true;
   x_cls[x] = sz > 0 ? 1 : (sz == 0 ? 0 : -1);
-  x_mir[x] = x0 + (mir < 0 ? xl : mir);
   if (bad) atomicExch(err, 1);
 }
 
@@ -1073,7 +1082,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
     }
     S.x_end = (int)h_x_nph.size();
   }
-  if (t_acc >= (1L << 31) - 2 || xt_acc >= (long)QPOS_SKIP_T)
+  if (t_acc >= (1L << 31) - 2 || xt_acc >= (1L << 31) - 2)
     throw PnmError{PNM_EINVAL, "problem too large for 32-bit element maps"};
   ctx->nch = (int)h_key.size();
   ctx->nx = (int)h_x_nph.size();
@@ -1150,8 +1159,6 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   D.ph_pair = dalloc<int2>(ph_acc, ctx->owned, s);
   D.hp_pair = dalloc<int2>(hp_acc, ctx->owned, s);
   D.x_cls = dalloc<int>(NX, ctx->owned, s);
-  D.x_mir = dalloc<int>(NX, ctx->owned, s);
-  D.x_frow = dalloc<int>(ph_acc, ctx->owned, s);
   D.x_rrow = dalloc<int>(ph_acc, ctx->owned, s);
   D.x_fcol = dalloc<int>(hp_acc, ctx->owned, s);
   D.x_rcol = dalloc<int>(hp_acc, ctx->owned, s);
@@ -1208,7 +1215,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       k_xflip<<<(nxs * 32 + 255) / 256, 256, 0, s>>>(S.x_begin, nxs, D.x_nph, D.x_nhp, D.x_ph_off, D.x_hp_off,
                                                 D.ph_pair, D.hp_pair, D.nvec, X.idx3, S.r, S.species,
                                                 S.sp_off, S.N, S.nsp, X.phpos, X.phch, X.hppos, D.x_cls,
-                                                D.x_mir, D.x_frow, D.x_fcol, D.x_rrow, D.x_rcol, flip_err);
+                                                D.x_fcol, D.x_rrow, D.x_rcol, flip_err);
       k_v_cross<<<nxs, 256, 0, s>>>(S.x_begin, D.x_nph, D.x_nhp, D.x_c_off, D.x_w_off,
                                     D.x_ph_off, D.x_hp_off, D.ph_pair, D.hp_pair, D.nvec,
                                     D.lut + S.lut_off, D.x_v1, D.x_w);
@@ -1218,7 +1225,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       k_qmap<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp,
                                    D.ch_t_off, D.hh_pair, D.pp_pair, S.sp_off, S.N, S.nsp,
                                    X.phch, X.phpos, X.hppos, S.x_begin, D.x_t_off, D.x_nhp,
-                                   D.x_cls, D.nvec, S.species, D.qmap);
+                                   D.x_cls, D.nvec, X.idx3, S.r, S.species, D.qmap);
       k_fmap<<<nrows, 128, 0, s>>>(S.row_begin, D.row_item, D.ch_hh_off, D.ch_pp_off, D.ch_npp, D.ch_t_off,
                                    D.hh_pair, D.pp_pair, D.nvec, X.idx3, S.r, S.species, S.sp_off, S.N,
                                    S.nsp, S.m, S.M, X.key2ch, S.ch_begin, X.pos_hh, X.pos_pp, D.fmap,
