@@ -81,7 +81,7 @@ MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload
 # (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {"k_pp64": 3.888e8, "k_pp_tc": 2.594e8, "k_update_mix": None}
+TRAFFIC = {"k_pp64": 3.813e8, "k_pp_tc": 2.594e8, "k_update_mix": 2.045e8}
 ALPHA = 0.5
 
 
@@ -177,14 +177,21 @@ def chan_sizes(ctx):
     sign of S_z = s_a - s_i (the ph kernels form S_z > 0 channels in full and mirror them onto
     S_z < 0, and S_z = 0 channels as half-size sum and difference blocks)."""
     import numpy as np
-    nhh, npp, nlad, nph, nhp, xsz = [], [], [], [], [], []
+    nhh, npp, nlad, nph, nhp, xsz, nself = [], [], [], [], [], [], []
     for s in range(ctx.nsys):
-        _, sizes, _ = ctx.channels(s, 0)
+        _, sizes, dpairs = ctx.channels(s, 0)
         _, xs, xpairs = ctx.channels(s, 1)
         nv, _, _ = ctx.basis(s)
         w = nv[:, 3].astype(int)
         spin = np.where(np.abs(w) == 1, w, w - 4 * np.sign(w))
         first = np.concatenate([[0], np.cumsum(xs[:, 0])[:-1]]).astype(int)
+        # hole pairs that the spin flip maps onto themselves (same momentum and species,
+        # opposite spin): the rows of a channel the updates compute are (n_hh + these) / 2
+        hh = dpairs[: int(sizes[:, 0].sum())]
+        selfp = (np.all(nv[hh[:, 0], :3] == nv[hh[:, 1], :3], axis=1)
+                 & (w[hh[:, 0]] - spin[hh[:, 0]] == w[hh[:, 1]] - spin[hh[:, 1]]))
+        hoff = np.concatenate([[0], np.cumsum(sizes[:, 0])[:-1]]).astype(int)
+        nself.append(np.add.reduceat(selfp.astype(int), hoff) if len(hh) else np.zeros(len(sizes), int))
         nhh.append(sizes[:, 0])
         npp.append(sizes[:, 1])
         nlad.append(ctx.ladder_sizes(s))
@@ -192,44 +199,50 @@ def chan_sizes(ctx):
         nhp.append(xs[:, 1])
         xsz.append(np.sign(spin[xpairs[first, 0]] - spin[xpairs[first, 1]]))
     cat = lambda v: np.concatenate(v).astype(float)
-    return cat(nhh), cat(npp), cat(nlad), cat(nph), cat(nhp), cat(xsz)
+    return cat(nhh), cat(npp), cat(nlad), cat(nph), cat(nhp), cat(xsz), cat(nself)
 
 
 def algorithmic_cost(ctx, kernel):
     """(bytes, flops) per launch of a kernel, from the channel sizes of all systems of the
     context: every array the kernel must touch, counted once."""
-    nhh, npp, nlad, nph, nhp, xsz = chan_sizes(ctx)
+    nhh, npp, nlad, nph, nhp, xsz, nself = chan_sizes(ctx)
     nt = float((nhh * npp).sum())
+    # the updates compute one amplitude of each spin-flip pair and write both
+    ncomp = 0.5 * nt
     if kernel in ("k_pp64", "k_pp_tc"):
         # the ladder in its basis (pnm_ladder_sizes): V block n_lad x n_lad, operand and result
-        # n_hh x n_lad per channel
+        # rows x n_lad per channel; k_pp64 takes the rows the update computes, (n_hh + self
+        # pairs) / 2 (exact for S_z = 0 channels, right in total over a channel and its flip),
+        # k_pp_tc every row
+        rows = 0.5 * (nhh + nself) if kernel == "k_pp64" else nhh
         vb = 8.0 if kernel == "k_pp64" else 4.0          # FP64 V, or BF16 hi + lo
         tb = 8.0 if kernel == "k_pp64" else 4.0          # t operand in the ladder basis
         rb = 8.0 if kernel == "k_pp64" else 4.0          # result
-        byts = float((nlad ** 2).sum()) * vb + float((nhh * nlad).sum()) * (tb + rb)
-        flops = 2.0 * float((nhh * nlad ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
+        byts = float((nlad ** 2).sum()) * vb + float((rows * nlad).sum()) * (tb + rb)
+        flops = 2.0 * float((rows * nlad ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
         return byts, flops
     if kernel in ("k_ph64", "k_ph32"):
         # S_z > 0: T (index map + gathered t, or the scattered FP32 copy), W and V1 read, Q
-        # written to the channel and its mirror; S_z = 0: the spin-up half of the rows of T, W
-        # and V1 read, Q written in full; 2 products of (rows x cols x cols) per block, the
-        # S_z = 0 blocks at half size, two of them
+        # written; S_z = 0: the spin-up half of the rows of T, W and V1 read and of Q written;
+        # 2 products of (rows x cols x cols) per block, the S_z = 0 blocks at half size, two of
+        # them; S_z < 0 channels are not formed
         e = 8.0 if kernel == "k_ph64" else 4.0
         tin = (4 + 8) if kernel == "k_ph64" else 4
         full, half = xsz > 0, xsz == 0
         el, vv = nph * nhp, nhp * nhp
-        byts = (float(el[full].sum()) * (tin + e + 2 * e) + float(vv[full].sum()) * e
-                + float(el[half].sum()) * ((tin + e) / 2 + e) + float(vv[half].sum()) * e / 2)
+        byts = (float(el[full].sum()) * (tin + e + e) + float(vv[full].sum()) * e
+                + float(el[half].sum()) * (tin + e + e) / 2 + float(vv[half].sum()) * e / 2)
         flops = (4.0 * float((nph * nhp * nhp)[full].sum())
                  + 2 * 4.0 * float(((nph / 2) * (nhp / 2) ** 2)[half].sum()))
         return byts, flops
     if kernel == "k_update":
-        # t, v, eps, 1/eps, qmap, rpp, four Q values, t_next
-        return nt * (8 + 8 + 8 + 8 + 16 + 8 + 4 * 8 + 8), nt * 20.0
+        # per computed amplitude: t, v, eps, 1/eps, qmap, flip map, ladder map, rpp, four Q
+        # values read; t_next written for it and its flip
+        return ncomp * (8 + 8 + 8 + 8 + 16 + 4 + 4 + 8 + 4 * 8 + 2 * 8), ncomp * 20.0
     if kernel == "k_update_mix":
-        # t, v, 1/eps, qmap, t32, ladder map, pp ladder, four Q values read; t, t32, four T
-        # entries written
-        return nt * (8 + 8 + 8 + 16 + 4 + 4 + 4 + 4 * 4 + 8 + 4 + 4 * 4), nt * 20.0
+        # per computed amplitude: t, v, 1/eps, qmap, flip map, t32, ladder map, pp ladder, hh
+        # ladder, four Q values read; t and t32 written for it and its flip, four T entries
+        return ncomp * (8 + 8 + 8 + 16 + 4 + 4 + 4 + 4 + 4 + 4 * 4 + 2 * (8 + 4) + 4 * 4), ncomp * 20.0
     if kernel in ("k_tstats", "k_tstats32"):
         return nt * 8 * 2 + float((nhh * nhh).sum()) * 16, nt * 2.0 * (2 + nhh.mean())
     return nt * 8.0, 0.0

@@ -548,12 +548,14 @@ static size_t pp64_smem(int npp) {
 }
 
 __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const LoopCtl* __restrict__ ctl,
-                                                          const int2* __restrict__ items) {
+                                                          const int2* __restrict__ items, int rep_only) {
   extern __shared__ double sm[];  // ts[PP64_ROWS][npp], red[PP64_WARPS][PP64_ROWS][32]
   int2 it = items[blockIdx.x];
   int c = it.x, ab0 = it.y;
   if (sys_done(D, ctl, D.ch_sys[c])) return;
-  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
+  // rep_only: the rows the updates compute (the list upd_row), else every hole pair
+  const int* __restrict__ rows = rep_only ? D.upd_row + D.ch_uoff[c] : nullptr;
+  int npp = D.ch_npp[c], nh = rep_only ? D.ch_uoff[c + 1] - D.ch_uoff[c] : D.ch_nhh[c];
   long tb = D.ch_t_off[c];
   const double* __restrict__ t = cur_t(D, ctl);
   double* ts = sm;
@@ -567,8 +569,10 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const Loop
   for (int g0 = 0; g0 < nh; g0 += PP64_ROWS) {
     int nr = min(PP64_ROWS, nh - g0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * npp; e += blockDim.x)
-      ts[e] = t[tb + (long)(g0 + e / npp) * npp + e % npp];
+    for (int e = threadIdx.x; e < nr * npp; e += blockDim.x) {
+      int g = g0 + e / npp;
+      ts[e] = t[tb + (long)(rows ? rows[g] : g) * npp + e % npp];
+    }
     __syncthreads();
     double acc[PP64_ROWS];
 #pragma unroll
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const Loop
       double s = 0.0;
 #pragma unroll
       for (int w = 0; w < PP64_WARPS; w++) s += red[(w * PP64_ROWS + r) * 32 + l];
-      if (ab0 + l < npp) D.rpp[tb + (long)(g0 + r) * npp + ab0 + l] = s;
+      if (ab0 + l < npp) D.rpp[tb + (long)(rows ? rows[g0 + r] : g0 + r) * npp + ab0 + l] = s;
     }
   }
 }
@@ -1184,6 +1188,8 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->d.upd_row = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, urow.size()));
   if (!urow.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->d.upd_row, urow.data(), sizeof(int) * urow.size(), cudaMemcpyHostToDevice, s));
+  ctx->d.ch_uoff = (int*)dmalloc(ctx, sizeof(int) * (ctx->nch + 1));
+  CUDA_TRY(cudaMemcpyAsync(ctx->d.ch_uoff, uoff.data(), sizeof(int) * (ctx->nch + 1), cudaMemcpyHostToDevice, s));
   auto group_items = [&](int G, std::vector<int4>* out, std::vector<int>* glo, std::vector<int>* ghi) {
     size_t n = 0;
     for (int k = 0; k < nsys; k++) {
@@ -1379,7 +1385,11 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
   double e4 = 0.0, e5 = 0.0, e3 = 0.0;
   for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) {
     long z = row + ab;
-    double tz = t[z];
+    // one amplitude of each spin-flip pair, counted twice (the ladder is formed on those rows)
+    const int fc = D.fmap[z];
+    const long f = (long)(fc > 0 ? fc : -fc) - 1;
+    if (f < z) continue;
+    double tz = (f == z ? 1.0 : 2.0) * t[z];
     if (has_vpp) {
       int sg;
       double rl = D.rpp[lad_index(D, c, ij, ab, sg)];
@@ -1488,14 +1498,17 @@ void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, do
   lad_expand(ctx, rs, planes, pstride, host_out);
 }
 
-void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s) {
+// rep_only: only the rows the updates compute (one of each spin-flip pair of rows); the ladder
+// operator of pnm_apply_pp_ladder takes every row.
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only) {
   if (ctx->n_pp_items == 0) return;
   k_lad_gather<double><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->d.s64);
   DevState L = ctx->d;
   L.ch_npp = ctx->d.ch_nlad;
   L.ch_t_off = ctx->d.ch_s_off;
   L.t0 = L.t1 = ctx->d.s64;
-  k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items);
+  k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items,
+                                                                          rep_only ? 1 : 0);
 }
 
 // The ph term and the pp ladder do not depend on each other nor on the one-body sums: in a

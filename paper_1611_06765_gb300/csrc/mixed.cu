@@ -683,7 +683,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     pnm_lad_expand(ctx, M->rpp32, M->ksplit, ctx->ns, out.data());
   } else {
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
-    pnm_launch_pp64(ctx, s);
+    pnm_launch_pp64(ctx, s, false);  // every row: the operator acts on any amplitudes
     pnm_lad_expand(ctx, ctx->d.rpp, 1, ctx->ns, out.data());
   }
   int err = 0;

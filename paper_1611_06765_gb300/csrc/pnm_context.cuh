@@ -152,7 +152,7 @@ void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
 void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
-void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s);
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only = true);
 size_t ph_smem_bytes(int max_dim, int nm, size_t elem);
 void pnm_mixed_pack_initial(pnm_ctx* ctx);
 void pnm_fork(pnm_ctx* ctx);

@@ -90,6 +90,7 @@ struct DevState {
   // mixed and FP64 updates: the hole-pair rows they compute (flip representatives), per item
   // a run of this list (items hold (channel, first entry, first column, rows))
   int* upd_row;
+  int* ch_uoff;          // per direct channel its run of upd_row (nch + 1 offsets)
   // maps
   int* xmap;             // per T element: sign * (t index + 1), 0 = structurally zero
   int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q (formed positions)
