@@ -40,7 +40,8 @@ struct StatsIO {
   }
 };
 
-// Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for all ij.
+// Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for the ij the updates
+// compute.
 // Blocks [nrows, ...): column chunk (c, ab0): sab[ab] = sum_ij t v.
 template <typename T_>
 __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __restrict__ ctl,
@@ -60,8 +61,12 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
     for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) s += tr[ab] * vr[ab];
     s = block_sum(s, sh32);
     if (threadIdx.x == 0) io.sij[D.ch_hh_off[c] + kl] = s;
+    // chi is read only in the columns ij of the rows the updates compute (the list upd_row)
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int ij = warp; ij < nh; ij += blockDim.x >> 5) {
+    const int* __restrict__ rl = D.upd_row + D.ch_uoff[c];
+    const int nr = D.ch_uoff[c + 1] - D.ch_uoff[c];
+    for (int k = warp; k < nr; k += blockDim.x >> 5) {
+      const int ij = rl[k];
       const T_* tj = t + base + (long)ij * npp;
       T_ acc = 0;
       for (int cd = lane; cd < npp; cd += 32) acc += vr[cd] * tj[cd];
@@ -804,15 +809,18 @@ void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
                                                       fin_args(ctx, use_cond, h, false));
 }
 
-// hh ladder of the mixed iteration, sum_kl t_ab^kl chi_kl^ij in FP32 for every (ij, ab): one
-// CTA per (channel, 128 pp columns); the chi block and the t columns are staged in shared
-// memory (thread = column), rows in groups of 8 accumulated in registers.
+// hh ladder of the mixed iteration, sum_kl t_ab^kl chi_kl^ij in FP32 (read by the mixed update
+// on the rows it computes): one CTA per (channel, 128 pp columns) of the channels with such
+// rows; the chi block and the t columns are staged in shared memory (thread = column), rows in
+// groups of 8 accumulated in registers.
 __global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restrict__ ctl,
                                               const int2* __restrict__ ab_items, float* __restrict__ hh) {
   extern __shared__ __align__(16) float hsm[];
   int2 it = ab_items[blockIdx.x];
   int c = it.x, ab = it.y + threadIdx.x;
   if (sys_done(D, ctl, D.ch_sys[c])) return;
+  // nothing in a channel whose rows are all written as spin flips of another channel's
+  if (D.ch_uoff[c + 1] == D.ch_uoff[c]) return;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   const float* __restrict__ t32 = cur_t32(D, ctl);
   float* chs = hsm;            // chi[kl][ij], nh x nh
@@ -824,6 +832,8 @@ __global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restr
   for (int kl = 0; kl < nh; kl++) ts[kl * 128 + threadIdx.x] = ok ? t32[base + (long)kl * npp + ab] : 0.0f;
   __syncthreads();
   if (!ok) return;
+  // every row in groups of 8 (contiguous chi reads); the rows the update does not compute see
+  // columns of chi that k_tstats left out, and their results are never read
   for (int ij0 = 0; ij0 < nh; ij0 += 8) {
     float acc[8];
 #pragma unroll
