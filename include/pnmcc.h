@@ -58,8 +58,9 @@ typedef struct {
 #define PNM_INIT_KEEP 2   /* start from the amplitudes currently held (pnm_set_amplitudes) */
 #define PNM_INIT_MLP 3    /* learned start (pnm_mlp_set_model); falls back to MBPT2 if the
                              iteration from it does not converge */
-/* Kept and learned starts are first symmetrised under the global spin flip F (every state to
- * the one of opposite spin): t <- (t + F t)/2.  F commutes with H and leaves the
+/* Kept starts are first symmetrised under the global spin flip F (every state to the one of
+ * opposite spin): t <- (t + F t)/2; the learned start is evaluated on one amplitude of each
+ * flip pair and copied to the other.  F commutes with H and leaves the
  * spin-saturated reference unchanged, so the solution is flip-symmetric, and the iteration
  * works on flip-symmetric amplitudes only: the ph term is formed for S_z >= 0 cross channels
  * (S_z = 0 ones as half-size sum and difference blocks) and read at the flip elsewhere, and

@@ -1028,6 +1028,21 @@ __global__ void k_flip_sym(const int* __restrict__ fmap, double* __restrict__ t,
   if (f != z) t[f] = cd > 0 ? v : -v;
 }
 
+// t(F z) <- sign * t(z) for every z that comes before its flip (a start computed on the rows
+// the updates compute, made flip-symmetric).
+__global__ void k_flip_copy(const int* __restrict__ fmap, double* __restrict__ t, long n) {
+  long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n) return;
+  int cd = fmap[z];
+  long f = (long)(cd > 0 ? cd : -cd) - 1;
+  if (f > z) t[f] = cd > 0 ? t[z] : -t[z];
+}
+
+void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s) {
+  if (ctx->nt > 0)
+    k_flip_copy<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.fmap, t, ctx->nt);
+}
+
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s) {
   if (ctx->nt > 0)
     k_flip_sym<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.fmap, t, ctx->nt);
@@ -1184,6 +1199,7 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpyAsync(rmode.data(), dm, sizeof(int) * ctx->nrows, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
   }
+  ctx->h_row_mode = rmode;
   std::vector<int> urow, uoff(ctx->nch + 1, 0), ucnt(ctx->nch, 0);
   for (int r = 0; r < ctx->nrows; r++)
     if (rmode[r]) ucnt[ctx->h_rows[r].x]++;

@@ -343,6 +343,7 @@ struct MlpOut {
   const long* t_begin;
   int nsys;
   float y_scale;
+  const int* idx;  // sample r is amplitude idx[r] (nullptr: amplitude r)
 };
 
 // One CTA (8 warps) loops over 128-sample tiles; two CTAs share an SM, so one CTA's
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
   auto load_x = [&](long tile, float4 (&xr)[4]) {
     long rg = tile * MH + row;
     if (tile < ntiles && rg < n) {
-      const float4* xp = reinterpret_cast<const float4*>(X + rg * MF + k0);
+      const long zg = out.idx ? (long)out.idx[rg] : rg;
+      const float4* xp = reinterpret_cast<const float4*>(X + zg * MF + k0);
 #pragma unroll
       for (int j = 0; j < 4; j++) xr[j] = __ldg(xp + j);
     } else {
@@ -490,11 +492,12 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
           float y = __uint_as_float(r[0]) + par[3 * MH];
           if (out.Y) out.Y[r_glob] = y;
           if (out.t0) {
+            const long z = out.idx ? (long)out.idx[r_glob] : r_glob;
             int sy = 0;
-            while (sy + 1 < out.nsys && r_glob >= out.t_begin[sy + 1]) sy++;
-            double t = out.tm2[r_glob];
+            while (sy + 1 < out.nsys && z >= out.t_begin[sy + 1]) sy++;
+            double t = out.tm2[z];
             if (isfinite(y)) t += out.sigma[sy] * (double)out.y_scale * (double)y;
-            out.t0[r_glob] = t;
+            out.t0[z] = t;
           }
         }
       }
@@ -596,6 +599,8 @@ struct MlpState {
   float* q = nullptr;       // model parameters (BF16-rounded weights)
   __nv_bfloat16* pw = nullptr;
   int* err = nullptr;
+  int* rep = nullptr;       // the amplitudes of the rows the updates compute (learned start)
+  long n_rep = 0;
   float y_scale = 1.0f;
   bool have_model = false;
 };
@@ -687,9 +692,28 @@ void pnm_mlp_start(pnm_ctx* ctx) {
   mlp_features(ctx);
   MlpState* M = ctx->mlp;
   cudaStream_t s = ctx->stream;
+  if (!M->rep) {
+    // the start is made flip-symmetric: the network is evaluated on the rows the updates
+    // compute (about half the amplitudes) and the rest is copied from their spin flips
+    std::vector<int> idx;
+    idx.reserve((size_t)ctx->nt / 2 + 1024);
+    for (int r = 0; r < ctx->nrows; r++) {
+      if (!ctx->h_row_mode[r]) continue;
+      int2 row = ctx->h_rows[r];
+      long base = ctx->h_t_off[row.x] + (long)row.y * ctx->h_npp[row.x];
+      for (int ab = 0; ab < ctx->h_npp[row.x]; ab++) idx.push_back((int)(base + ab));
+    }
+    M->n_rep = (long)idx.size();
+    M->rep = ctx_alloc<int>(ctx, std::max<size_t>(1, idx.size()));
+    if (!idx.empty())
+      CUDA_TRY(cudaMemcpyAsync(M->rep, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   // the network output goes straight into t0 (t_MBPT2 + sigma_sys * y_scale * y)
-  tc_infer(s, M->X, ctx->nt, M->q, M->pw,
-           MlpOut{nullptr, ctx->d.t0, M->tm2, M->sigma, M->t_begin, (int)ctx->sys.size(), M->y_scale}, M->err);
+  tc_infer(s, M->X, M->n_rep, M->q, M->pw,
+           MlpOut{nullptr, ctx->d.t0, M->tm2, M->sigma, M->t_begin, (int)ctx->sys.size(), M->y_scale, M->rep},
+           M->err);
+  pnm_flip_copy(ctx, ctx->d.t0, s);
   CUDA_TRY(cudaGetLastError());
 }
 

@@ -38,6 +38,7 @@ struct pnm_ctx {
   std::vector<int2> h_rows;
   std::vector<int> h_x_nph, h_x_nhp, h_x_ph_off, h_x_hp_off;
   std::vector<int> h_x_cls;  // spin-flip class of each cross channel (+1, 0, -1)
+  std::vector<int> h_row_mode;  // per row (h_rows): 2/1 computed by the updates, 0 a flip
 
   // work lists
   int2* pp_items = nullptr;   // (channel, first pp column) of the FP64 pp ladder
@@ -162,6 +163,7 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
 void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double* r, size_t n);
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s);
+void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
                    cudaStream_t s);
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
