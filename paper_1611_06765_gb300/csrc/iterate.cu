@@ -167,12 +167,12 @@ __device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__
 }
 
 // Bytes reserved for the index tables at the start of a k_ph CTA's shared memory (R4 + 2 H4
-// ints are used; 2 (R4 + H4) keeps the reservation a multiple of 16 bytes).
+// ints are used; 2 (R4 + H4) with R4, H4 even keeps the reservation a multiple of 16 bytes).
 __host__ __device__ __forceinline__ size_t ph_index_bytes(int R4, int H4) { return sizeof(int) * 2 * (size_t)(R4 + H4); }
 
 // One CTA (NT threads) per cross channel.  NM = 1: a channel with S_z > 0.  NM = 2: an S_z = 0
-// channel as the pair (sum, difference) of half-size problems, Q written on its spin-up rows.  Per problem, in shared memory zero-padded to
-// multiples of 4 (R rows (a,i), H columns (k,c)):
+// channel as the pair (sum, difference) of half-size problems, Q written on its spin-up rows.
+// Per problem, in shared memory zero-padded to multiples of TS (R rows (a,i), H columns (k,c)):
 //   Ts = T (R x H), Xt = W^T staged as W (R x H), then T^T (H x R), Cs = C (H x H);
 //   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_(e,l) <kl|v|ce> t_lj^eb   (xw == nullptr: <kb|v|cj>)
 //   Q[(a,i)][(j,b)] = sum_(k,c) t_ik^ac C[(k,c)][(j,b)]
@@ -184,7 +184,8 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
                                          T_* __restrict__ xq) {
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const int R = NM == 2 ? nph >> 1 : nph, H = NM == 2 ? nhp >> 1 : nhp;
-  const int R4 = (R + 3) & ~3, H4 = (H + 3) & ~3;
+  // padded to multiples of the register tile (zeros): the padding costs FMAs in the tiles
+  const int R4 = (R + TS - 1) & ~(TS - 1), H4 = (H + TS - 1) & ~(TS - 1);
   const int RH = R4 * H4, HH = H4 * H4;
   // NM = 2: index tables in shared memory first (no chains of dependent global loads below):
   // sra[u] = spin-up row, sca[v] = spin-up column, scb[v] = its flip
