@@ -685,8 +685,9 @@ def run_ours(a):
                            "traffic": TRAFFIC.get("k_pp_tc") if a.workload == DEFAULT_WORKLOAD else None,
                            "tensor_tflops": f_tc / t_tc / 1e12, "tensor_frac_of_bf16_peak": f_tc / t_tc / 1e12 / bf16}
     # kernels of one solve: the loop bodies and refinement sweeps counted by the profiler, plus
-    # the start (MBPT2: init + energy; learned: features, inference, apply, energy)
-    launches_per_solve = sum(n for _, n in stats.values()) + (4 if start == "mlp" else 2)
+    # the start (MBPT2: init + energy; learned: inference, copy to the spin flips, symmetrise,
+    # init + energy, FP32 copies)
+    launches_per_solve = sum(n for _, n in stats.values()) + (6 if start == "mlp" else 2)
 
     comparison = None
     if rank == 0 and not a.no_extra:
