@@ -110,3 +110,21 @@ def test_unsupported_composition_rejected(pkg):
     with pytest.raises(pkg.PnmError) as e:
         pkg.Context(14, 0.16, 12, params=minnesota_params(), Z=2)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("N,Z,rho,n2,theta", [(14, 14, 0.16, 12, None), (14, 0, 0.08, 20, (0.4, 1.3, 2.6))])
+def test_solved_amplitudes_are_exactly_flip_symmetric(pkg, N, Z, rho, n2, theta):
+    """The updates compute one amplitude of each spin-flip pair and write both: after a solve
+    (FP64 and mixed) the amplitudes equal their flips bit for bit, for symmetric nuclear matter
+    and a twisted neutron box."""
+    import spinflip
+    g = pkg.Context(N, rho, n2, params=minnesota_params(), Z=Z if Z else None, theta=theta)
+    o = channel.OracleSystem(N, rho, n2, minnesota_params(), theta=theta, Z=Z)
+    perm = spinflip.flip_permutation(g.amplitude_labels(), o.states())
+    for prec in (pkg.PNM_PREC_FP64, pkg.PNM_PREC_BF16X3):
+        g.solve(precision=prec, alpha=0.5, tol=1e-30, tol_per_N=1e-7, max_iter=400, refine_sweeps=2,
+                allow=(pkg.PNM_ENOTCONV,))
+        t = g.get_amplitudes()
+        assert np.max(np.abs(t)) > 0
+        assert np.array_equal(t, spinflip.flip(t, perm)), prec
+    g.close()
