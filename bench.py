@@ -81,7 +81,7 @@ MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch from one ncu capture of the default workload
 # (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {"k_pp64": 3.813e8, "k_pp_tc": 2.594e8, "k_update_mix": 2.045e8}
+TRAFFIC = {"k_pp64": 3.813e8, "k_pp_tc": 2.594e8, "k_update_mix": 1.884e8}
 ALPHA = 0.5
 
 

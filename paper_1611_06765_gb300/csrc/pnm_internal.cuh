@@ -176,7 +176,7 @@ struct FinArgs {
 #define PNM_UPD_BATCH 2
 #endif
 #ifndef PNM_UPD_MIN_BLOCKS
-#define PNM_UPD_MIN_BLOCKS 8
+#define PNM_UPD_MIN_BLOCKS 6
 #endif
 constexpr int UPD_ROWS = PNM_UPD_ROWS, UPD_MAX_NHH = 128, UPD_BATCH = PNM_UPD_BATCH;
 constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
