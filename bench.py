@@ -7,9 +7,11 @@ Default workload, the one the metric's "mixed + learned" is defined on: N = 66 n
 plane waves with n^2 <= 36 (1850 states), Minnesota interaction, mixing 0.5, at the three
 held-out densities rho = 0.05, 0.11, 0.17 fm^-3, solved together in one batched context
 (every kernel launch covers the three systems).  A step is one converged solve of that batch
-from the learned start (feature kernel + tensor-core inference inside the timed region), the
-pp ladder in BF16x3 on the tensor cores, FP64 denominators / residual / energies, and two
-FP64 refinement sweeps at the end.  The network is trained before timing, by the library's
+from the learned start (the tensor-core inference of the network and the copy to the spin
+flips inside the timed region; the network's input features depend only on the context and
+are built once, by the first learned solve of the warm-up), the pp ladder in BF16x3 on the
+tensor cores, FP64 denominators / residual / energies, and two FP64 refinement sweeps at the
+end.  The network is trained before timing, by the library's
 own GPU kernels, on amplitudes the solver converges for N = 14 (n^2 <= 20, 16 densities
 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16).  Channel tables, interaction blocks and
 the model are resident in HBM before the timed region; L2 is flushed before every step.
@@ -79,9 +81,10 @@ COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_
            "pnm_N14_n2max20_16rho_bf16x3", "pnm_N14_n2max20_16rho_fp64"]
 MINNESOTA = (200.0, 1.487, -178.0, 0.639, -91.85, 0.465, 20.721)
 TOL_PER_N = 1e-6
-# DRAM bytes (read + write) per launch from one ncu capture of the default workload
-# (profiles/<kernel>_pnm_N66_n2max36_heldout3.md); valid while the kernels are unchanged.
-TRAFFIC = {"k_pp64": 3.813e8, "k_pp_tc": 2.594e8, "k_update_mix": 1.884e8}
+# DRAM bytes (read + write) per launch of the default workload from one ncu capture, with the
+# first 16 hex digits of the SHA-256 of the kernel's source file at the time of the capture:
+# reported only while that file is unchanged, else null.
+TRAFFIC = {}
 ALPHA = 0.5
 
 
@@ -235,17 +238,52 @@ def algorithmic_cost(ctx, kernel):
         flops = (4.0 * float((nph * nhp * nhp)[full].sum())
                  + 2 * 4.0 * float(((nph / 2) * (nhp / 2) ** 2)[half].sum()))
         return byts, flops
-    if kernel == "k_update":
-        # per computed amplitude: t, v, eps, 1/eps, qmap, flip map, ladder map, rpp, four Q
-        # values read; t_next written for it and its flip
-        return ncomp * (8 + 8 + 8 + 8 + 16 + 4 + 4 + 8 + 4 * 8 + 2 * 8), ncomp * 20.0
-    if kernel == "k_update_mix":
-        # per computed amplitude: t, v, 1/eps, qmap, flip map, t32, ladder map, pp ladder, hh
-        # ladder, four Q values read; t and t32 written for it and its flip, four T entries
-        return ncomp * (8 + 8 + 8 + 16 + 4 + 4 + 4 + 4 + 4 + 4 * 4 + 2 * (8 + 4) + 4 * 4), ncomp * 20.0
+    if kernel in ("k_update", "k_update_mix"):
+        # elementwise step over every restricted amplitude: t read (8 B), t written (8 B) and
+        # one 4-byte index per amplitude, the figure the algorithm itself needs
+        return nt * (8 + 8 + 4), nt * 20.0
     if kernel in ("k_tstats", "k_tstats32"):
         return nt * 8 * 2 + float((nhh * nhh).sum()) * 16, nt * 2.0 * (2 + nhh.mean())
     return nt * 8.0, 0.0
+
+
+def kernel_source(kernel):
+    """Source file (in the package's csrc/) that defines a kernel."""
+    if kernel in ("k_pp_tc", "k_pack"):
+        return "mixed.cu"
+    return "iterate.cu"
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch from the ncu capture recorded in TRAFFIC, if it was taken on this
+    workload and the kernel's source is unchanged since; else None."""
+    import hashlib
+    ent = TRAFFIC.get(kernel)
+    if ent is None or workload != DEFAULT_WORKLOAD:
+        return None
+    path = os.path.join(ROOT, "paper_1611_06765_gb300", "csrc", kernel_source(kernel))
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent[0] if digest == ent[1] else None
+
+
+def implementation_bytes(ctx, kernel):
+    """Bytes per launch the current implementation of an update kernel moves by its own
+    accounting (every array it touches, once), beside the algorithmic figure."""
+    nhh, npp, nlad, nph, nhp, xsz, nself = chan_sizes(ctx)
+    ncomp = 0.5 * float((nhh * npp).sum())
+    if kernel == "k_update":
+        # per computed amplitude: t, v, eps, 1/eps, qmap, flip map, ladder map, rpp, four Q
+        # values read; t_next written for it and its flip
+        return ncomp * (8 + 8 + 8 + 8 + 16 + 4 + 4 + 8 + 4 * 8 + 2 * 8)
+    if kernel == "k_update_mix":
+        # per computed amplitude: t, v, 1/eps, qmap, flip map, t32, ladder map, pp ladder, hh
+        # ladder, four Q values read; t and t32 written for it and its flip, four T entries
+        return ncomp * (8 + 8 + 8 + 16 + 4 + 4 + 4 + 4 + 4 + 4 * 4 + 2 * (8 + 4) + 4 * 4)
+    return None
 
 
 def read_peaks():
@@ -273,9 +311,10 @@ def oracle_solve(N, rho, n2max):
 # ------------------------------------------------------------------------------ arms
 
 def run_reference(a):
-    """The FP64 oracle on the host cores, same workload and metric.  One step is a bounded
-    sample: one full solve of one system of the workload (the systems taken in turn), scaled
-    to the number of systems in the workload."""
+    """The FP64 oracle on the host cores, same workload and metric.  One step is one full
+    solve (setup, MBPT2 start, iterations to the same stopping rule) of every system of the
+    workload, one after the other, so each step covers the whole batch (about 5 s on 16 Arm
+    cores for the held-out batch)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
@@ -283,14 +322,17 @@ def run_reference(a):
     from oracle import build as ob
     ob.build()
     from oracle import channel
-    if a.warmup:
-        oracle_solve(N, rhos[0], n2max)  # pages in the library and starts the thread pool
+    for _ in range(a.warmup):
+        for rho in rhos:
+            oracle_solve(N, rho, n2max)
     times, dEs = [], {}
     for k in range(a.steps):
-        rho = rhos[k % len(rhos)]
-        ms, dE, it = oracle_solve(N, rho, n2max)
-        times.append(ms * len(rhos))
-        dEs[str(rho)] = dE / N
+        step = 0.0
+        for rho in rhos:
+            ms, dE, it = oracle_solve(N, rho, n2max)
+            step += ms
+            dEs[str(rho)] = dE / N
+        times.append(step)
     ms = statistics.mean(times)
     cores = channel.threads()
     line = {
@@ -300,8 +342,8 @@ def run_reference(a):
         "config": {"workload": a.workload, "N": N, "rho": list(rhos), "n2max": n2max, "start": "mbpt2",
                    "tol_dE_per_N": TOL_PER_N, "mix_alpha": ALPHA, "l2": "host"},
         "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": "each step: one full FP64 oracle solve (MBPT2 start) of one system of the "
-                                   "%d-system workload, systems in turn, time x %d" % (len(rhos), len(rhos))},
+                         "sample": "each step: one full FP64 oracle solve (MBPT2 start) of each of the %d "
+                                   "systems of the workload, summed" % len(rhos)},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "result": {"dE_per_N": dEs},
     }
@@ -665,10 +707,14 @@ def run_ours(a):
     else:
         roof = {"bound": "hbm", "achieved": byts / kavg_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "%s hbm_gbs" % src}
-    traffic = TRAFFIC.get(kname) if a.workload == DEFAULT_WORKLOAD else None
+    traffic = measured_traffic(kname, a.workload)
     roof.update(frac=roof["achieved"] / roof["peak"], traffic=traffic, kernel=kname, kernel_avg_us=kavg_s * 1e6,
                 algorithmic_bytes=byts, algorithmic_flops=flops,
                 measured_fma_peaks_tflops={"fp64": fp64_peak, "fp32": fp32_peak})
+    ib = implementation_bytes(ctx, kname)
+    if ib is not None:
+        roof["implementation_bytes"] = ib
+        roof["implementation_gbs"] = ib / kavg_s / 1e9
     # the FP64 refinement contractions against the measured FP64 FMA rate
     for k in ("k_pp64", "k_ph64", "k_ph32"):
         if k in stats and k != kname:
@@ -682,7 +728,7 @@ def run_ours(a):
         b_tc, f_tc = algorithmic_cost(ctx, "k_pp_tc")
         roof["k_pp_tc"] = {"bound": "hbm", "achieved": b_tc / t_tc / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": b_tc / t_tc / 1e9 / hbm, "kernel_avg_us": t_tc * 1e6,
-                           "traffic": TRAFFIC.get("k_pp_tc") if a.workload == DEFAULT_WORKLOAD else None,
+                           "traffic": measured_traffic("k_pp_tc", a.workload),
                            "tensor_tflops": f_tc / t_tc / 1e12, "tensor_frac_of_bf16_peak": f_tc / t_tc / 1e12 / bf16}
     # kernels of one solve: the loop bodies and refinement sweeps counted by the profiler, plus
     # the start (MBPT2: init + energy; learned: inference, copy to the spin flips, symmetrise,

@@ -209,19 +209,20 @@ int pnm_ladder_sizes(const pnm_ctx *ctx, int sys, int *n_chan, int32_t *nlad);
 int pnm_mbpt3(pnm_ctx *ctx, double *e3);
 
 /* The same second-order energy as pnm_mbpt2, for callers that must not allocate device
- * memory at the time of the call: code running while a CUDA graph is being captured
- * (cudaMalloc is not allowed there), loops with a fixed memory budget, or hosts whose
- * device allocator belongs to another framework.  This call allocates nothing (no
+ * memory at the time of the call: loops whose device-memory budget is fixed when they start
+ * (a later allocation could fail or stall them), or hosts whose device allocator belongs to
+ * another framework that forbids side allocations.  This call allocates nothing (no
  * cudaMalloc, cudaFree or allocating library routine).  Its scratch is a file-scope device
  * array of (65536 + 64) doubles, about 513 KB, which every GPU that loads this library holds
  * until the process exits.  Limits: at most 65536 (channel, hole-pair) rows and 64 systems
  * per context, else PNM_EINVAL with a message.  The first call on a device looks up the
- * array's device address for that device (done once per device); make that first call
- * before any stream capture.  All calls on a device share the one array: every slot used is
- * rewritten by each call, so nothing carries over, but calls that overlap on the GPU (from
- * several host threads or streams) race on it.  dE receives one value per system; the call
- * synchronises the context stream.  The paper has no counterpart: this is the library's
- * own calling convention. */
+ * array's device address for that device (done once per device and kept for the life of its
+ * primary context); make that first call before any stream capture.  All calls on a device
+ * share the one array: every slot used is rewritten by each call, so nothing carries over,
+ * but calls that overlap on the GPU (from several host threads or streams) race on it.  dE
+ * receives one value per system (host memory); the call copies it back and synchronises the
+ * context stream.  The paper has no counterpart: this is the library's own calling
+ * convention. */
 int pnm_mbpt2_noalloc(const pnm_ctx *ctx, double *dE);
 
 /* Solve the CCD equations (Eq. ccd3 in the intermediate form of Sec. "Developing a CCD
@@ -263,7 +264,9 @@ int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, d
 int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, double *r, size_t n);
 
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
- * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement. */
+ * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement; and
+ * ms[5] = 1 if the last solve with init = PNM_INIT_MLP fell back to the MBPT2 start, else 0.
+ * The first min(n, 6) entries are written. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
 
 /* ---------------------------------------------------------------- learned warm start
@@ -305,15 +308,21 @@ int pnm_mlp_train(pnm_ctx *const *ctxs, int nctx, const pnm_mlp_opts *opts, floa
 /* Install a trained blob in a context for solves with init = PNM_INIT_MLP. */
 int pnm_mlp_set_model(pnm_ctx *ctx, const float *blob);
 
-/* Network output for n feature rows (host arrays): use_tensor_cores = 1 runs the fused
- * tcgen05 inference kernel, 0 the SIMT training forward.  stream: NULL = legacy stream. */
-int pnm_mlp_forward(const float *blob, const float *X, long n, float *Y, int use_tensor_cores,
-                    void *stream);
+/* Network output for n feature rows (host arrays).  mode: PNM_MLP_TENSOR_CORES runs the
+ * fused tcgen05 inference kernel (the learned start's), PNM_MLP_SIMT the SIMT training
+ * forward, PNM_MLP_SIMT_FP32 the same SIMT kernels with the BF16 rounding of weights and
+ * layer inputs switched off (a debug mode for element-wise checks against an FP64
+ * reference).  stream: NULL = legacy stream. */
+#define PNM_MLP_SIMT 0
+#define PNM_MLP_TENSOR_CORES 1
+#define PNM_MLP_SIMT_FP32 2
+int pnm_mlp_forward(const float *blob, const float *X, long n, float *Y, int mode, void *stream);
 
 /* Mean squared error over n samples and its gradient (NPARAM floats, header entries 0)
- * from the library's GPU forward/backward kernels, for gradient checks. */
+ * from the library's GPU forward/backward kernels, for gradient checks.  fp32 = 1: the FP32
+ * debug mode (same kernels, no BF16 rounding of weights or activations). */
 int pnm_mlp_loss_grad(const float *blob, const float *X, const float *T, int n, float *loss,
-                      float *grad, void *stream);
+                      float *grad, int fp32, void *stream);
 
 /* Per-kernel device time of host-driven solves (opts.host_loop = 1): while profiling is on,
  * every kernel launch of the update is bracketed by CUDA events on the context stream.

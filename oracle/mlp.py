@@ -114,3 +114,36 @@ def loss_and_grad(blob, X, T, round_bf16=True):
         put("b%d" % (l + 1), dz.sum(axis=0))
         dh = dz @ W[l]
     return loss, g
+
+
+def abs_bounds(blob, X, T, round_bf16=True):
+    """Absolute-value scales of the network's output and gradient, for rounding-aware
+    tolerances: the forward pass of forward() and the backward pass of loss_and_grad() with
+    every factor replaced by its absolute value (|h|, |W|, |b|, |dy|, |gelu'(z)|), at the same
+    activations.  Returns (B_y per sample, B_g per parameter); B_y >= |y| and B_g >= |grad|
+    element by element (triangle inequality), with equality when no sum has terms of both
+    signs.  A rounding error of relative size u in any one factor moves y or a gradient
+    element by at most about u times its scale."""
+    y, c = forward(blob, X, round_bf16)
+    p = unpack(blob)
+    h, z, W = c["h"], c["z"], c["W"]
+    aw4 = np.abs(c["w4"])
+    By = np.abs(h[3]) @ aw4 + abs(float(p["b4"][0]))
+    n = len(T)
+    ady = 2.0 * np.abs(y - np.asarray(T, np.float64)) / n
+    g = np.zeros(NPARAM)
+    off = offsets()
+
+    def put(name, val):
+        o, k = off[name]
+        g[o:o + k] = np.ravel(val)
+
+    put("w4", ady @ np.abs(h[3]))
+    put("b4", [ady.sum()])
+    dh = np.outer(ady, aw4)
+    for l in (2, 1, 0):
+        dz = dh * np.abs(gelu_prime(z[l]))
+        put("W%d" % (l + 1), dz.T @ np.abs(h[l]))
+        put("b%d" % (l + 1), dz.sum(axis=0))
+        dh = dz @ np.abs(W[l])
+    return By, g

@@ -232,9 +232,9 @@ class Context:
         return out
 
     def timings(self):
-        ms = np.zeros(5)
-        _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 5))
-        return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4])
+        ms = np.zeros(6)
+        _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 6))
+        return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4], mlp_fallback=int(ms[5]))
 
 
 def _fptr(a):
@@ -285,20 +285,25 @@ def mlp_train(contexts, blob, epochs=20, batch=4096, lr=1e-3, seed=0):
     return blob, hist[: nh.value].copy()
 
 
-def mlp_forward(blob, X, tensor_cores=True):
+def mlp_forward(blob, X, tensor_cores=True, fp32=False):
+    """pnm_mlp_forward: the tcgen05 inference kernel (tensor_cores=True), the SIMT forward, or
+    the SIMT forward without BF16 rounding (fp32=True, the debug mode)."""
     blob = np.ascontiguousarray(blob, dtype=np.float32)
     X = np.ascontiguousarray(X, dtype=np.float32)
     Y = np.zeros(X.shape[0], np.float32)
-    _lib.check(_lib.load().pnm_mlp_forward(_fptr(blob), _fptr(X), X.shape[0], _fptr(Y), int(tensor_cores), None))
+    mode = _lib.PNM_MLP_SIMT_FP32 if fp32 else (_lib.PNM_MLP_TENSOR_CORES if tensor_cores else _lib.PNM_MLP_SIMT)
+    _lib.check(_lib.load().pnm_mlp_forward(_fptr(blob), _fptr(X), X.shape[0], _fptr(Y), mode, None))
     return Y
 
 
-def mlp_loss_grad(blob, X, T):
+def mlp_loss_grad(blob, X, T, fp32=False):
+    """pnm_mlp_loss_grad: (mean squared error, gradient blob); fp32=True is the debug mode
+    without BF16 rounding."""
     blob = np.ascontiguousarray(blob, dtype=np.float32)
     X = np.ascontiguousarray(X, dtype=np.float32)
     T = np.ascontiguousarray(T, dtype=np.float32)
     g = np.zeros_like(blob)
     loss = C.c_float()
     _lib.check(_lib.load().pnm_mlp_loss_grad(_fptr(blob), _fptr(X), _fptr(T), X.shape[0], C.byref(loss),
-                                             _fptr(g), None))
+                                             _fptr(g), int(bool(fp32)), None))
     return float(loss.value), g

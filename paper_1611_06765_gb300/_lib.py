@@ -29,6 +29,10 @@ PNM_TERMS_PP = 1
 PNM_TERMS_PPHH = 2
 PNM_TERMS_LINEAR = 3
 
+PNM_MLP_SIMT = 0
+PNM_MLP_TENSOR_CORES = 1
+PNM_MLP_SIMT_FP32 = 2
+
 # Every symbol include/pnmcc.h declares.
 EXPORTS = (
     "pnm_default_opts", "pnm_create", "pnm_create_batch", "pnm_create_twisted", "pnm_create_matter",
@@ -110,7 +114,7 @@ def load(path=None):
     L.pnm_mlp_train.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(pnm_mlp_opts), fp, fp, C.c_int, ip]
     L.pnm_mlp_set_model.argtypes = [vp, fp]
     L.pnm_mlp_forward.argtypes = [fp, fp, C.c_long, fp, C.c_int, vp]
-    L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, vp]
+    L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, C.c_int, vp]
     L.pnm_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_float), ip]
     L.pnm_selftest_timeout.argtypes = [vp]
     L.pnm_measure_fma_peak.argtypes = [C.c_int, vp, dp]

@@ -186,23 +186,27 @@ void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, int tA,
   k_sgemm<<<g, 256, 0, s>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, acc);
 }
 
-// h0 = bf16((x - mu) * inv_std) for the rows idx[0..B) of X.
+// h0 = bf16((x - mu) * inv_std) for the rows idx[0..B) of X (rnd = 0: FP32 debug mode, no
+// BF16 rounding).
 __global__ void k_prep(const float* __restrict__ X, const int* __restrict__ idx, int B,
-                       const float* __restrict__ blob, float* __restrict__ H0) {
+                       const float* __restrict__ blob, float* __restrict__ H0, int rnd) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B * MF) return;
   int r = e / MF, q = e % MF;
   long row = idx ? idx[r] : r;
-  H0[e] = bf16r((X[row * MF + q] - blob[O_MU + q]) * blob[O_IS + q]);
+  float x = (X[row * MF + q] - blob[O_MU + q]) * blob[O_IS + q];
+  H0[e] = rnd ? bf16r(x) : x;
 }
 
-// z = acc + b; keep z; h = bf16(gelu(z)).
-__global__ void k_bias_gelu(float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ Hn, int B) {
+// z = acc + b; keep z; h = bf16(gelu(z)) (rnd = 0: FP32 debug mode, h = gelu(z)).
+__global__ void k_bias_gelu(float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ Hn, int B,
+                            int rnd) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B * MH) return;
   float z = Z[e] + b[e % MH];
   Z[e] = z;
-  Hn[e] = bf16r(gelu_f(z));
+  float h = gelu_f(z);
+  Hn[e] = rnd ? bf16r(h) : h;
 }
 
 // y = h3 . w4 + b4, residual, loss partial and dy = 2 (y - t) / B.  One warp per row.
@@ -265,12 +269,14 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   q[e] = is_w ? bf16r(we) : we;
 }
 
-__global__ void k_quantize(const float* __restrict__ w, float* __restrict__ q) {
+// q = the parameters as the forward pass uses them: weights rounded to BF16 (rnd = 0: FP32
+// debug mode, unrounded).
+__global__ void k_quantize(const float* __restrict__ w, float* __restrict__ q, int rnd = 1) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= NPARAM) return;
   bool is_w = (e >= O_W1 && e < O_B1) || (e >= O_W2 && e < O_B2) || (e >= O_W3 && e < O_B3) ||
               (e >= O_W4 && e < O_B4);
-  q[e] = is_w ? bf16r(w[e]) : w[e];
+  q[e] = (is_w && rnd) ? bf16r(w[e]) : w[e];
 }
 
 // Per-column sums and squares of X (n x 32) for the feature normalisation.
@@ -553,14 +559,15 @@ struct Net {
   }
 };
 
-void net_forward(cudaStream_t s, Net& nt, const float* X, const int* idx, int B) {
-  k_prep<<<(B * MF + 255) / 256, 256, 0, s>>>(X, idx, B, nt.q, nt.H0);
+// rnd = 0: the FP32 debug mode (no BF16 rounding of the layer inputs).
+void net_forward(cudaStream_t s, Net& nt, const float* X, const int* idx, int B, int rnd = 1) {
+  k_prep<<<(B * MF + 255) / 256, 256, 0, s>>>(X, idx, B, nt.q, nt.H0, rnd);
   sgemm(s, B, MH, MF, nt.H0, MF, 0, nt.q + O_W1, MF, 1, nt.Z1, MH, 0);
-  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z1, nt.q + O_B1, nt.H1, B);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z1, nt.q + O_B1, nt.H1, B, rnd);
   sgemm(s, B, MH, MH, nt.H1, MH, 0, nt.q + O_W2, MH, 1, nt.Z2, MH, 0);
-  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z2, nt.q + O_B2, nt.H2, B);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z2, nt.q + O_B2, nt.H2, B, rnd);
   sgemm(s, B, MH, MH, nt.H2, MH, 0, nt.q + O_W3, MH, 1, nt.Z3, MH, 0);
-  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z3, nt.q + O_B3, nt.H3, B);
+  k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z3, nt.q + O_B3, nt.H3, B, rnd);
 }
 
 // Backward pass from dY; writes the gradient blob nt.g (header entries zero).
@@ -774,9 +781,13 @@ int pnm_mlp_set_model(pnm_ctx* ctx, const float* blob) {
   }
 }
 
-int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use_tensor_cores, void* stream) {
+int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int mode, void* stream) {
   try {
     if (!blob || !X || !Y || n < 0) throw PnmError{PNM_EINVAL, "bad argument"};
+    if (mode != PNM_MLP_SIMT && mode != PNM_MLP_TENSOR_CORES && mode != PNM_MLP_SIMT_FP32)
+      throw PnmError{PNM_EINVAL, "unknown forward mode"};
+    const bool use_tensor_cores = mode == PNM_MLP_TENSOR_CORES;
+    const int rnd = mode == PNM_MLP_SIMT_FP32 ? 0 : 1;
     check_blob_header(blob);
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc;
@@ -786,7 +797,7 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use
     float* dY = xalloc<float>(n, sc.owned);
     CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(dX, X, sizeof(float) * n * MF, cudaMemcpyHostToDevice, s));
-    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, q);
+    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(w, q, rnd);
     if (use_tensor_cores) {
       __nv_bfloat16* pw = xalloc<__nv_bfloat16>(PW_TOTAL, sc.owned);
       int* err = xalloc<int>(1, sc.owned);
@@ -806,7 +817,7 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use
       CUDA_TRY(cudaMemcpyAsync(nt.q, q, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s));
       for (long r0 = 0; r0 < n; r0 += chunk) {
         int B = (int)std::min(chunk, n - r0);
-        net_forward(s, nt, dX + r0 * MF, nullptr, B);
+        net_forward(s, nt, dX + r0 * MF, nullptr, B, rnd);
         k_out<<<(B * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, nullptr, nullptr, B,
                                                    dY + r0, nullptr, nullptr);
       }
@@ -822,7 +833,7 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int use
 }
 
 int pnm_mlp_loss_grad(const float* blob, const float* X, const float* T, int n, float* loss, float* grad,
-                      void* stream) {
+                      int fp32, void* stream) {
   try {
     if (!blob || !X || !T || n <= 0) throw PnmError{PNM_EINVAL, "bad argument"};
     check_blob_header(blob);
@@ -837,8 +848,9 @@ int pnm_mlp_loss_grad(const float* blob, const float* X, const float* T, int n, 
     CUDA_TRY(cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)n * MF, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(dT, T, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(lacc, 0, sizeof(double), s));
-    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.q);
-    net_forward(s, nt, dX, nullptr, n);
+    const int rnd = fp32 ? 0 : 1;
+    k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.q, rnd);
+    net_forward(s, nt, dX, nullptr, n, rnd);
     k_out<<<(n * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, dT, nullptr, n, nt.Y, nt.dY, lacc);
     net_backward(s, nt, n);
     CUDA_TRY(cudaGetLastError());

@@ -1,13 +1,14 @@
 // noalloc.cu -- second-order energy of a context without any device allocation.
 //
 // pnm_mbpt2 keeps its per-row partial sums in memory the context allocated.  Some callers
-// cannot allocate device memory at the point where they want the number: code that runs
-// while another component is capturing a CUDA graph (cudaMalloc is not allowed there),
-// real-time or embedded loops whose memory budget is fixed up front, and hosts whose
-// allocator is owned by a framework that forbids side allocations.  pnm_mbpt2_noalloc
-// serves them: its scratch is the file-scope array below, which every GPU that loads this
-// library holds until the process exits.
+// cannot allocate device memory at the point where they want the number: real-time or
+// embedded loops whose device-memory budget is fixed when they start (an allocation later
+// can fail or stall them), and hosts whose device allocator belongs to another framework
+// that forbids side allocations.  pnm_mbpt2_noalloc serves them: its scratch is the
+// file-scope array below, which every GPU that loads this library holds until the process
+// exits.
 #include <mutex>
+#include <new>
 
 #include "pnm_context.cuh"
 
@@ -19,7 +20,9 @@
 static __device__ __align__(256) double g_mbpt2_scratch[PNM_NOALLOC_MAX_ROWS + PNM_NOALLOC_MAX_SYSTEMS];
 
 // Device address of g_mbpt2_scratch per device.  In host code the array's name is only a
-// host-side stand-in, so the address is looked up once per device with that device current.
+// host-side stand-in, so the address is looked up once per device with that device current
+// (by the first call on that device).  The cached address is valid for the life of the
+// device's primary context: a cudaDeviceReset in between would leave it stale.
 static std::mutex g_scratch_mu;
 static double* g_scratch_addr[PNM_NOALLOC_MAX_DEVICES] = {};
 
@@ -41,6 +44,8 @@ static double* scratch_on(int dev) {
 }
 
 extern "C" int pnm_mbpt2_noalloc(const pnm_ctx* ctx, double* dE) {
+  // every failure becomes a status code: nothing may leave an extern "C" function as an
+  // exception (the mutex, the message strings and the CUDA calls can all throw)
   try {
     if (!ctx || !dE) throw PnmError{PNM_EINVAL, "null argument"};
     int nsys = (int)ctx->sys.size();
@@ -64,5 +69,11 @@ extern "C" int pnm_mbpt2_noalloc(const pnm_ctx* ctx, double* dE) {
   } catch (const PnmError& e) {
     pnm_set_error(e.code, e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    pnm_set_error(PNM_ENOMEM, "host allocation failed");
+    return PNM_ENOMEM;
+  } catch (...) {
+    pnm_set_error(PNM_EINVAL, "unexpected failure");
+    return PNM_EINVAL;
   }
 }

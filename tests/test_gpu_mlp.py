@@ -1,6 +1,8 @@
-"""Learned warm start: GPU training kernels against the FP64 reference network, the fused
-tensor-core inference against the SIMT forward, the feature kernel against a numpy
-restatement, and the gain of the trained network over the MBPT2 start at held-out densities.
+"""Learned warm start: GPU training kernels against the FP64 reference network element by
+element (an FP32 debug mode without BF16 rounding, and the BF16 mode against rounding-aware
+scales), the fused tensor-core inference per output, the feature kernel against a numpy
+restatement, and the solve the metric is defined on (learned start, BF16x3 ladders, two FP64
+refinement sweeps; N = 66, n^2 <= 36, held-out densities) against the oracle's fixed point.
 """
 import math
 
@@ -13,6 +15,11 @@ from oracle import channel, mlp
 
 pytestmark = pytest.mark.gpu
 
+HELDOUT = [0.05, 0.11, 0.17]
+# One BF16 unit relative to a value (8 significant bits: 2^-7 at most): the size of the
+# difference a rounding decision taken in FP32 on the GPU and in FP64 in the reference can make.
+BF16_UNIT = 2.0 ** -7
+
 
 @pytest.fixture(scope="module")
 def pkg():
@@ -22,32 +29,71 @@ def pkg():
     return P
 
 
+def _per_tensor(g):
+    for name, (o, k) in mlp.offsets().items():
+        yield name, slice(o, o + k)
+
+
 def test_param_count(pkg):
     assert pkg.mlp_num_params() == mlp.NPARAM
 
 
-def test_loss_and_gradient_match_reference(pkg):
-    """BF16 activations make single elements jump where a rounding decision flips between
-    FP32 and FP64, so the gradient is compared as a whole: relative L2 error <= 1e-2."""
+def test_fp32_gradient_matches_reference_elementwise(pkg):
+    """FP32 debug mode (the training kernels with the BF16 rounding switched off) against the
+    FP64 reference without rounding: every gradient element within 1e-6 of its tensor's
+    largest element, the loss within 1e-6 relative, every output within 1e-6 of the largest."""
+    blob, X, T = random_mlp(n=256, seed=11, nparam=mlp.NPARAM)
+    loss_g, g_g = pkg.mlp_loss_grad(blob, X, T, fp32=True)
+    loss_r, g_r = mlp.loss_and_grad(blob, X, T, round_bf16=False)
+    assert abs(loss_g - loss_r) <= 1e-6 * abs(loss_r)
+    worst = 0.0
+    for name, sl in _per_tensor(g_r):
+        a, b = g_g[sl].astype(np.float64), g_r[sl]
+        scale = np.max(np.abs(b))
+        worst = max(worst, np.max(np.abs(a - b)) / scale)
+        assert np.all(np.abs(a - b) <= 1e-6 * scale), name
+    print("FP32 gradient: max |error| / tensor max = %.3g" % worst)
+    assert np.all(g_g[:mlp.HEADER] == 0)
+    y_g = pkg.mlp_forward(blob, X, tensor_cores=False, fp32=True)
+    y_r, _ = mlp.forward(blob, X, round_bf16=False)
+    assert np.all(np.abs(y_g - y_r) <= 1e-6 * np.max(np.abs(y_r)))
+
+
+def test_bf16_gradient_within_rounding_scale_elementwise(pkg):
+    """BF16 mode: the GPU rounds activations after FP32 arithmetic, the reference after FP64,
+    so a rounding decision can differ by one BF16 unit.  Every gradient element stays within
+    one BF16 unit of its absolute-value scale (oracle.mlp.abs_bounds), every element within
+    1e-4 of its tensor's largest, and the whole gradient within 1e-3 in L2."""
     blob, X, T = random_mlp(n=256, seed=11, nparam=mlp.NPARAM)
     loss_g, g_g = pkg.mlp_loss_grad(blob, X, T)
     loss_r, g_r = mlp.loss_and_grad(blob, X, T, round_bf16=True)
-    assert abs(loss_g - loss_r) <= 1e-3 * abs(loss_r)
-    for name, (o, k) in mlp.offsets().items():
-        a, b = g_g[o:o + k].astype(np.float64), g_r[o:o + k]
-        assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b), name
+    _, B_g = mlp.abs_bounds(blob, X, T, round_bf16=True)
+    assert abs(loss_g - loss_r) <= 1e-4 * abs(loss_r)
+    for name, sl in _per_tensor(g_r):
+        a, b = g_g[sl].astype(np.float64), g_r[sl]
+        assert np.all(np.abs(a - b) <= BF16_UNIT * B_g[sl]), name
+        assert np.all(np.abs(a - b) <= 1e-4 * np.max(np.abs(b))), name
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), name
     assert np.all(g_g[:mlp.HEADER] == 0)
 
 
-def test_tensor_core_forward_matches_simt_and_reference(pkg):
-    blob, X, _ = random_mlp(n=1000, seed=12, nparam=mlp.NPARAM)
-    y_tc = pkg.mlp_forward(blob, X, tensor_cores=True)
-    y_simt = pkg.mlp_forward(blob, X, tensor_cores=False)
+def test_tensor_core_forward_per_output(pkg):
+    """The fused tcgen05 inference (BF16 operands, FP32 accumulation in tensor memory, hardware
+    tanh in GELU) per output against the reference and against the SIMT forward: within two
+    BF16 units of the output's absolute-value scale B_y = sum_k |h3_k w4_k| + |b4|, and the SIMT
+    BF16 forward within one unit.  A misplaced row or column gives errors of the order of |y|,
+    about B_y / 10 for these random networks."""
+    blob, X, T = random_mlp(n=1000, seed=12, nparam=mlp.NPARAM)
+    y_tc = pkg.mlp_forward(blob, X, tensor_cores=True).astype(np.float64)
+    y_simt = pkg.mlp_forward(blob, X, tensor_cores=False).astype(np.float64)
     y_ref, _ = mlp.forward(blob, X, round_bf16=True)
-    scale = np.linalg.norm(y_ref)
-    assert np.linalg.norm(y_tc - y_simt) <= 1e-2 * scale
-    assert np.linalg.norm(y_tc - y_ref) <= 1e-2 * scale
-    assert np.linalg.norm(y_simt - y_ref) <= 1e-2 * scale
+    B_y, _ = mlp.abs_bounds(blob, X, T, round_bf16=True)
+    print("max |tc - ref| / B_y = %.3g, max |simt - ref| / B_y = %.3g"
+          % (np.max(np.abs(y_tc - y_ref) / B_y), np.max(np.abs(y_simt - y_ref) / B_y)))
+    assert np.all(np.abs(y_simt - y_ref) <= BF16_UNIT * B_y)
+    assert np.all(np.abs(y_tc - y_ref) <= 2 * BF16_UNIT * B_y)
+    assert np.all(np.abs(y_tc - y_simt) <= 2 * BF16_UNIT * B_y)
+    assert np.median(np.abs(y_tc - y_ref) / B_y) <= 2.0 ** -12
 
 
 def test_features_match_numpy(pkg):
@@ -83,23 +129,70 @@ def test_features_match_numpy(pkg):
     g.close()
 
 
-def test_warm_start_gain_at_held_out_densities(pkg):
-    """Train on solver amplitudes of N=14 (n^2<=20, 16 densities 0.02..0.32) and N=66
-    (n^2<=36, rho=0.16); start N=66 at held-out rho in {0.05, 0.11, 0.17}.  The learned start
-    must reach the same fixed point (|dE/N| difference < 1e-6 MeV) in fewer updates."""
+@pytest.fixture(scope="module")
+def trained(pkg):
+    """The warm-start network as the benchmark trains it: the library's kernels on the
+    amplitudes the FP64 solver converges (|dE/N| < 1e-8 MeV) for N = 14 (n^2 <= 20, 16
+    densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16); 20 epochs, batch 1024, Adam
+    lr 1e-3, seeds 1 (initial weights) and 2 (shuffling)."""
     P = minnesota_params()
     kw = dict(alpha=0.5, tol=1e-30, tol_per_N=1e-8, max_iter=300)
     train14 = pkg.Context(14, [0.02 * k for k in range(1, 17)], 20, params=P)
     train14.solve(**kw)
     train66 = pkg.Context(66, 0.16, 36, params=P)
     train66.solve(**kw)
-    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=12, batch=4096, lr=1e-3, seed=2)
+    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=20, batch=1024, lr=1e-3, seed=2)
+    for c in (train14, train66):
+        c.close()
     assert hist[-1] < hist[0]
-    test = pkg.Context(66, [0.05, 0.11, 0.17], 36, params=P)
-    test.mlp_set_model(blob)
+    return blob
+
+
+@pytest.fixture(scope="module")
+def heldout_fixed_points():
+    """The oracle's CCD energy per neutron at the held-out densities, converged to
+    |dE change| / N < 1e-10 MeV (mixing 0.5, MBPT2 start)."""
+    P = minnesota_params()
+    out = []
+    for rho in HELDOUT:
+        o = channel.OracleSystem(66, rho, 36, P)
+        dE, _, _, _ = o.ccd(alpha=0.5, tol=1e-10 * 66, maxit=400)
+        out.append(dE / 66)
+    return np.array(out)
+
+
+def test_metric_configuration_against_oracle(pkg, trained, heldout_fixed_points):
+    """The configuration the time-to-converge metric is quoted on: N = 66, n^2 <= 36, held-out
+    rho = 0.05, 0.11, 0.17 in one batched context, learned start, BF16x3 tensor-core ladders
+    with FP32 contractions, stopping rule |dE^(n+1) - dE^(n)| / N < 1e-6 MeV, then two FP64
+    refinement sweeps.  Every density ends within 1e-6 MeV per neutron of the oracle's fixed
+    point, without the MBPT2 fallback, in fewer updates than the same solve from the MBPT2
+    start (Eq. ccdGuess)."""
+    test = pkg.Context(66, HELDOUT, 36, params=minnesota_params())
+    test.mlp_set_model(trained)
+    kw = dict(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-6, max_iter=500,
+              refine_sweeps=2)
+    dE_m, it_m, _, _ = test.solve(init=pkg.PNM_INIT_MBPT2, **kw)
+    dE_l, it_l, _, _ = test.solve(init=pkg.PNM_INIT_MLP, **kw)
+    assert test.timings()["mlp_fallback"] == 0
+    err_l = dE_l / 66 - heldout_fixed_points
+    err_m = dE_m / 66 - heldout_fixed_points
+    print("learned start: updates %s, dE/N - oracle %s; MBPT2 start: updates %s, dE/N - oracle %s"
+          % (it_l, err_l, it_m, err_m))
+    assert np.all(np.abs(err_l) < 1e-6)
+    assert np.all(np.abs(err_m) < 1e-6)
+    assert it_l.sum() < it_m.sum(), (it_l, it_m)
+    test.close()
+
+
+def test_warm_start_gain_fp64(pkg, trained):
+    """In FP64 the learned start reaches the same fixed point as the MBPT2 start
+    (|dE/N| difference < 1e-6 MeV at a 1e-8 MeV rule) in fewer updates."""
+    test = pkg.Context(66, HELDOUT, 36, params=minnesota_params())
+    test.mlp_set_model(trained)
+    kw = dict(alpha=0.5, tol=1e-30, tol_per_N=1e-8, max_iter=300)
     dE_m, it_m, _, _ = test.solve(init=pkg.PNM_INIT_MBPT2, **kw)
     dE_l, it_l, _, _ = test.solve(init=pkg.PNM_INIT_MLP, **kw)
     assert np.all(np.abs(dE_l - dE_m) / 66 < 1e-6)
     assert it_l.sum() < it_m.sum(), (it_l, it_m)
-    for c in (train14, train66, test):
-        c.close()
+    test.close()

@@ -52,3 +52,28 @@ def test_analytic_gradient_matches_finite_differences():
         lm, _ = mlp.loss_and_grad(bm, X, T, round_bf16=False)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-10, (idx, fd, g[idx])
+
+
+def test_abs_bounds_dominate_and_are_tight_without_cancellation():
+    """abs_bounds: B_y >= |y| and B_g >= |grad| element by element on random parameters;
+    with nonnegative inputs, weights and biases (so z >= 0 and gelu'(z) > 0) and targets
+    below every output (so y - T > 0) no sum has terms of both signs and the scales equal the
+    absolute values of the output and of the gradient."""
+    blob, X, T = random_mlp(n=64, seed=13)
+    y, _ = mlp.forward(blob, X, round_bf16=True)
+    _, g = mlp.loss_and_grad(blob, X, T, round_bf16=True)
+    By, Bg = mlp.abs_bounds(blob, X, T, round_bf16=True)
+    assert np.all(By >= np.abs(y) * (1 - 1e-12))
+    assert np.all(Bg >= np.abs(g) * (1 - 1e-12))
+    assert np.all(Bg[:mlp.HEADER] == 0)
+    pos = np.abs(blob).astype(np.float32)
+    pos[:mlp.F] = 0.0                      # mu
+    pos[mlp.F:2 * mlp.F] = 1.0             # inv_std
+    Xp = np.abs(X)
+    Tn = -np.ones(len(T), np.float32)
+    for rnd in (False, True):
+        y, _ = mlp.forward(pos, Xp, round_bf16=rnd)
+        _, g = mlp.loss_and_grad(pos, Xp, Tn, round_bf16=rnd)
+        By, Bg = mlp.abs_bounds(pos, Xp, Tn, round_bf16=rnd)
+        assert np.allclose(By, np.abs(y), rtol=1e-13, atol=0)
+        assert np.allclose(Bg, np.abs(g), rtol=1e-13, atol=0)

@@ -42,3 +42,21 @@ def test_noalloc_matches_mbpt2_twice(pkg, N, rho, n2max):
     for got in (first, second):
         assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref))
     ctx.close()
+
+
+def test_noalloc_rejects_oversize_then_still_matches(pkg):
+    """More systems than the static scratch holds (64): PNM_EINVAL with a message naming the
+    limit, nothing launched; a valid call right after still equals pnm_mbpt2."""
+    from paper_1611_06765_gb300 import _lib
+    lib = _lib.load()
+    big = pkg.Context(2, [0.02 + 0.001 * k for k in range(65)], 1, params=minnesota_params())
+    out = np.zeros(big.nsys)
+    rc = lib.pnm_mbpt2_noalloc(big._h, out.ctypes.data_as(C.POINTER(C.c_double)))
+    assert rc == _lib.PNM_EINVAL
+    assert b"64 systems" in lib.pnm_last_error()
+    big.close()
+    ctx = pkg.Context(14, [0.04, 0.08], 20, params=minnesota_params())
+    ref = _call(lib, "pnm_mbpt2", ctx, ctx.nsys)
+    got = _call(lib, "pnm_mbpt2_noalloc", ctx, ctx.nsys)
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref))
+    ctx.close()
