@@ -43,17 +43,20 @@ METRIC = "PNM CCD time-to-converge (ΔE/N<1e-6 MeV), mixed+learned vs FP64, one 
 HELDOUT = (0.05, 0.11, 0.17)
 SWEEP16 = tuple(round(0.02 * k, 2) for k in range(1, 17))
 WORKLOADS = {
-    # name: (N, densities, n2max, start, precision)
-    "pnm_N66_n2max36_heldout3_learned_bf16x3": (66, HELDOUT, 36, "mlp", "bf16x3"),
-    "pnm_N66_n2max36_heldout3_mbpt2_bf16x3": (66, HELDOUT, 36, "mbpt2", "bf16x3"),
-    "pnm_N66_n2max36_heldout3_mbpt2_fp64": (66, HELDOUT, 36, "mbpt2", "fp64"),
-    "pnm_N14_rho0.08_n2max20_bf16x3": (14, (0.08,), 20, "mbpt2", "bf16x3"),
-    "pnm_N14_rho0.08_n2max20_fp64": (14, (0.08,), 20, "mbpt2", "fp64"),
-    "pnm_N66_rho0.16_n2max36_bf16x3": (66, (0.16,), 36, "mbpt2", "bf16x3"),
-    "pnm_N66_rho0.16_n2max36_fp64": (66, (0.16,), 36, "mbpt2", "fp64"),
-    "pnm_N14_n2max20_16rho_bf16x3": (14, SWEEP16, 20, "mbpt2", "bf16x3"),
-    "pnm_N14_n2max20_16rho_fp64": (14, SWEEP16, 20, "mbpt2", "fp64"),
-    "pnm_N14_rho0.08_n2max4_fp64": (14, (0.08,), 4, "mbpt2", "fp64"),
+    # name: (N, densities, n2max, start, precision, contractions of the refinement sweeps)
+    # "f32pair": FP32-pair contractions (48 significant bits on the FP32 pipe, FP64 results);
+    # "fp64": the FP64 pipe.  The update, denominators, residual and energy are FP64 in both.
+    "pnm_N66_n2max36_heldout3_learned_bf16x3": (66, HELDOUT, 36, "mlp", "bf16x3", "f32pair"),
+    "pnm_N66_n2max36_heldout3_learned_bf16x3_fp64refine": (66, HELDOUT, 36, "mlp", "bf16x3", "fp64"),
+    "pnm_N66_n2max36_heldout3_mbpt2_bf16x3": (66, HELDOUT, 36, "mbpt2", "bf16x3", "f32pair"),
+    "pnm_N66_n2max36_heldout3_mbpt2_fp64": (66, HELDOUT, 36, "mbpt2", "fp64", None),
+    "pnm_N14_rho0.08_n2max20_bf16x3": (14, (0.08,), 20, "mbpt2", "bf16x3", "f32pair"),
+    "pnm_N14_rho0.08_n2max20_fp64": (14, (0.08,), 20, "mbpt2", "fp64", None),
+    "pnm_N66_rho0.16_n2max36_bf16x3": (66, (0.16,), 36, "mbpt2", "bf16x3", "f32pair"),
+    "pnm_N66_rho0.16_n2max36_fp64": (66, (0.16,), 36, "mbpt2", "fp64", None),
+    "pnm_N14_n2max20_16rho_bf16x3": (14, SWEEP16, 20, "mbpt2", "bf16x3", "f32pair"),
+    "pnm_N14_n2max20_16rho_fp64": (14, SWEEP16, 20, "mbpt2", "fp64", None),
+    "pnm_N14_rho0.08_n2max4_fp64": (14, (0.08,), 4, "mbpt2", "fp64", None),
 }
 # Twist-averaged boundary conditions: one system per point of a product Gauss-Legendre twist
 # mesh (4 x 5 x 6 nodes on [0, pi]: no two equal components, so no mesh point has a
@@ -75,7 +78,8 @@ NUCLEAR_WORKLOADS = {
     "snm_A28_rho0.16_n2max20_fp64": (14, 14, 0.16, 20, "fp64"),
 }
 DEFAULT_WORKLOAD = "pnm_N66_n2max36_heldout3_learned_bf16x3"
-COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
+COMPARE = ["pnm_N66_n2max36_heldout3_learned_bf16x3", "pnm_N66_n2max36_heldout3_learned_bf16x3_fp64refine",
+           "pnm_N66_n2max36_heldout3_mbpt2_bf16x3",
            "pnm_N66_n2max36_heldout3_mbpt2_fp64", "pnm_N14_rho0.08_n2max20_bf16x3",
            "pnm_N14_rho0.08_n2max20_fp64", "pnm_N66_rho0.16_n2max36_bf16x3", "pnm_N66_rho0.16_n2max36_fp64",
            "pnm_N14_n2max20_16rho_bf16x3", "pnm_N14_n2max20_16rho_fp64"]
@@ -212,6 +216,8 @@ def algorithmic_cost(ctx, kernel):
     nt = float((nhh * npp).sum())
     # the updates compute one amplitude of each spin-flip pair and write both
     ncomp = 0.5 * nt
+    if kernel == "k_pp_f2":
+        kernel = "k_pp64"  # same arrays (V as FP32 pairs, 8 bytes) and the same flops
     if kernel in ("k_pp64", "k_pp_tc"):
         # the ladder in its basis (pnm_ladder_sizes): V block n_lad x n_lad, operand and result
         # rows x n_lad per channel; k_pp64 takes the rows the update computes, (n_hh + self
@@ -224,13 +230,13 @@ def algorithmic_cost(ctx, kernel):
         byts = float((nlad ** 2).sum()) * vb + float((rows * nlad).sum()) * (tb + rb)
         flops = 2.0 * float((rows * nlad ** 2).sum()) * (1 if kernel == "k_pp64" else 3)
         return byts, flops
-    if kernel in ("k_ph64", "k_ph32"):
+    if kernel in ("k_ph64", "k_ph32", "k_ph_f2"):
         # S_z > 0: T (index map + gathered t, or the scattered FP32 copy), W and V1 read, Q
         # written; S_z = 0: the spin-up half of the rows of T, W and V1 read and of Q written;
         # 2 products of (rows x cols x cols) per block, the S_z = 0 blocks at half size, two of
         # them; S_z < 0 channels are not formed
-        e = 8.0 if kernel == "k_ph64" else 4.0
-        tin = (4 + 8) if kernel == "k_ph64" else 4
+        e = 4.0 if kernel == "k_ph32" else 8.0
+        tin = 4 if kernel == "k_ph32" else (4 + 8)
         full, half = xsz > 0, xsz == 0
         el, vv = nph * nhp, nhp * nhp
         byts = (float(el[full].sum()) * (tin + e + e) + float(vv[full].sum()) * e
@@ -318,7 +324,7 @@ def run_reference(a):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    N, rhos, n2max, _, _ = WORKLOADS[a.workload]
+    N, rhos, n2max = WORKLOADS[a.workload][:3]
     from oracle import build as ob
     ob.build()
     from oracle import channel
@@ -369,11 +375,12 @@ def timed_solves(ctx, solve_kw, steps, flush, stream, torch):
 
 
 def solve_kwargs(P, workload, refine):
-    _, _, _, start, prec = WORKLOADS[workload]
+    _, _, _, start, prec, rk = WORKLOADS[workload]
     p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
     return dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
                 refine_sweeps=refine if p == P.PNM_PREC_BF16X3 else 0,
-                init=P.PNM_INIT_MLP if start == "mlp" else P.PNM_INIT_MBPT2)
+                init=P.PNM_INIT_MLP if start == "mlp" else P.PNM_INIT_MBPT2,
+                refine_kernels=P.PNM_PREC_F32PAIR if rk == "f32pair" else P.PNM_PREC_FP64)
 
 
 _model = {}
@@ -402,7 +409,7 @@ def trained_model(P, stream):
 
 
 def make_context(P, workload, stream):
-    N, rhos, n2max, start, _ = WORKLOADS[workload]
+    N, rhos, n2max, start = WORKLOADS[workload][:4]
     ctx = P.Context(N, list(rhos), n2max, params=MINNESOTA, stream=stream.cuda_stream)
     if start == "mlp":
         ctx.mlp_set_model(trained_model(P, stream))
@@ -430,7 +437,7 @@ def measure_twist(P, torch, stream, flush, workload, refine, steps):
     ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream, theta=theta)
     p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
     kw = dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=500,
-              refine_sweeps=refine if prec == "bf16x3" else 0)
+              refine_sweeps=refine if prec == "bf16x3" else 0, refine_kernels=P.PNM_PREC_F32PAIR)
     for _ in range(3):
         ctx.solve(**kw)
     torch.cuda.synchronize()
@@ -468,7 +475,7 @@ def measure_nuclear(P, torch, stream, flush, workload, refine, steps):
     ctx = P.Context(N, rho, n2max, params=MINNESOTA, stream=stream.cuda_stream, Z=Z)
     p = P.PNM_PREC_BF16X3 if prec == "bf16x3" else P.PNM_PREC_FP64
     kw = dict(precision=p, alpha=ALPHA, tol=1e-30, tol_per_N=TOL_PER_N, max_iter=2000,
-              refine_sweeps=refine if prec == "bf16x3" else 0)
+              refine_sweeps=refine if prec == "bf16x3" else 0, refine_kernels=P.PNM_PREC_F32PAIR)
     for _ in range(3):
         ctx.solve(**kw)
     torch.cuda.synchronize()
@@ -595,7 +602,7 @@ def oracle_leg(workloads, budget_s=60.0):
     from oracle import channel
     seen = []
     for w in workloads:
-        N, rhos, n2max, _, _ = WORKLOADS[w]
+        N, rhos, n2max = WORKLOADS[w][:3]
         for r in rhos:
             if (N, r, n2max) not in seen:
                 seen.append((N, r, n2max))
@@ -627,7 +634,7 @@ def oracle_one_thread():
 
 
 def oracle_errors(res, workload, ora):
-    N, rhos, n2max, _, _ = WORKLOADS[workload]
+    N, rhos, n2max = WORKLOADS[workload][:3]
     err = {}
     for r, e in zip(rhos, res["dE_per_N"]):
         if (N, r, n2max) in ora:
@@ -648,7 +655,7 @@ def run_ours(a):
     from paper_1611_06765_gb300 import build as pb
     pb.build()
     import paper_1611_06765_gb300 as P
-    N, rhos, n2max, start, prec_name = WORKLOADS[a.workload]
+    N, rhos, n2max, start, prec_name, refine_kind = WORKLOADS[a.workload]
     _model["path"] = a.model
     _model["epochs"], _model["batch"] = a.train_epochs, a.train_batch
     stream = torch.cuda.current_stream()
@@ -704,6 +711,11 @@ def run_ours(a):
     if kname in ("k_pp64", "k_ph64"):
         roof = {"bound": "alu", "achieved": flops / kavg_s / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "peak_source": "measured FP64 FMA rate (pnm_measure_fma_peak)"}
+    elif kname in ("k_pp_f2", "k_ph_f2"):
+        # FP64-equivalent flops against the FP32 pipe's rate per FP32-pair multiply-add (12 FP32
+        # instructions, i.e. the measured FP32 FMA rate / 12)
+        roof = {"bound": "alu", "achieved": flops / kavg_s / 1e12, "peak": fp32_peak / 12,
+                "unit": "TFLOP/s", "peak_source": "measured FP32 FMA rate / 12 (FP32-pair multiply-add)"}
     else:
         roof = {"bound": "hbm", "achieved": byts / kavg_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "peak_source": "%s hbm_gbs" % src}
@@ -716,11 +728,11 @@ def run_ours(a):
         roof["implementation_bytes"] = ib
         roof["implementation_gbs"] = ib / kavg_s / 1e9
     # the FP64 refinement contractions against the measured FP64 FMA rate
-    for k in ("k_pp64", "k_ph64", "k_ph32"):
+    for k in ("k_pp64", "k_ph64", "k_ph32", "k_pp_f2", "k_ph_f2"):
         if k in stats and k != kname:
             tk = stats[k][0] / stats[k][1] / 1e3
             bk, fk = algorithmic_cost(ctx, k)
-            pk = fp64_peak if k != "k_ph32" else fp32_peak
+            pk = {"k_ph32": fp32_peak, "k_pp_f2": fp32_peak / 12, "k_ph_f2": fp32_peak / 12}.get(k, fp64_peak)
             roof[k] = {"bound": "alu", "achieved": fk / tk / 1e12, "peak": pk, "unit": "TFLOP/s",
                        "frac": fk / tk / 1e12 / pk, "kernel_avg_us": tk * 1e6}
     if "k_pp_tc" in stats and kname != "k_pp_tc":
@@ -801,7 +813,8 @@ def run_ours(a):
             "dtype": "f64" if prec_name == "fp64" else "bf16x3+f32+f64",
             "data": "synthetic",
             "config": {"workload": a.workload, "N": N, "rho": list(rhos), "n2max": n2max, "start": start,
-                       "precision": prec_name, "refine_sweeps": solve_kw["refine_sweeps"], "mix_alpha": ALPHA,
+                       "precision": prec_name, "refine_sweeps": solve_kw["refine_sweeps"],
+                       "refine_contractions": refine_kind, "mix_alpha": ALPHA,
                        "tol_dE_per_N": TOL_PER_N, "l2": "flushed (512 MB write) before every step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "clocks": clk.summary(),

@@ -52,6 +52,12 @@ typedef struct {
 #define PNM_PREC_BF16X3 2 /* pp ladder as hi/lo BF16 products on tcgen05 (FP32 accumulate),
                              other contractions in FP32, denominators/energy/residual FP64,
                              then `refine_sweeps` FP64 iterations */
+#define PNM_PREC_F32PAIR 3 /* contractions (pp ladder, ph term) with every value carried as the
+                              unevaluated sum of two FP32 numbers, 48 significant bits, on the
+                              FP32 pipe (exact products by fused multiply-add, two-sum
+                              accumulation), results in FP64: an FP64-accurate alternative to
+                              the FP64 pipe for the refinement sweeps (opts.refine_kernels) and
+                              the operator calls; not a solve precision */
 
 #define PNM_INIT_MBPT2 0  /* t = <ab|v|ij> / eps_ij^ab, Eq. (ccdGuess) */
 #define PNM_INIT_ZERO 1   /* t = 0 (the first update then gives MBPT2) */
@@ -95,10 +101,14 @@ typedef struct {
     int init;             /* PNM_INIT_* */
     int host_loop;        /* 0: device-side loop in one CUDA graph; 1: host checks each iteration */
     int terms;            /* PNM_TERMS_*: the full Eq. (ccd3) or a truncation (FP64 only) */
+    int refine_kernels;   /* contractions of the refinement sweeps: PNM_PREC_FP64 (FP64 pipe) or
+                             PNM_PREC_F32PAIR (FP32 pairs); the update, denominators, residual
+                             and energy of the sweeps are FP64 either way */
 } pnm_solve_opts;
 
 /* Fills the defaults of the small FP64 workload: FP64, alpha 0.5, tol 1e-10 MeV,
- * max_iter 500, no refinement, MBPT2 start, device-side loop, full Eq. (ccd3). */
+ * max_iter 500, no refinement (FP64-pipe refinement kernels when enabled), MBPT2 start,
+ * device-side loop, full Eq. (ccd3). */
 void pnm_default_opts(pnm_solve_opts *opts);
 
 /* Build one system: the basis of Sec. "Single-particle basis for infinite matter" (k =
@@ -248,7 +258,8 @@ int pnm_set_amplitudes(pnm_ctx *ctx, int sys, const double *t, size_t n);
 /* The particle-particle ladder alone, as an operator on amplitudes:
  * r_ij^ab = 1/2 sum_cd <ab|v|cd> t_ij^cd = sum_{c<d} <ab|v|cd> t_ij^cd (the pp-ladder term of
  * Eq. ccd3, with <ab|chi|cd> = <ab|v|cd> of Sec. "Developing a CCD code"), evaluated by the
- * FP64 kernel or by the BF16x3 tensor-core kernel (precision).  t and r hold n restricted
+ * FP64 kernel, the FP32-pair kernel (PNM_PREC_F32PAIR) or the BF16x3 tensor-core kernel
+ * (precision).  t and r hold n restricted
  * amplitudes of system `sys` in library order; r is 0 on channels whose V block vanishes
  * (S_z != 0 for neutrons).  Resets the solver's iteration state. */
 int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, double *r,
@@ -258,7 +269,8 @@ int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, d
  * P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj with chi_kb^cj = <kb|v|cj> + 1/2 sum_dl <kl|v|cd> t_lj^db
  * (the linear ph term and the quadratic ph term of Eq. ccd3 through the intermediate of Sec.
  * "Developing a CCD code"), computed in the cross-coupled channels (n_a - n_i, s_a - s_i):
- * FP64 kernels, or the mixed-precision ones (FP32 operands and products).  t and r hold n restricted
+ * FP64 kernels, FP32-pair kernels (PNM_PREC_F32PAIR), or the mixed-precision ones (FP32
+ * operands and products).  t and r hold n restricted
  * amplitudes of system `sys` in library order; r is the term of the flip-symmetric part
  * (t + F t)/2 of t (see PNM_INIT_KEEP).  Resets the solver's iteration state. */
 int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, double *r, size_t n);

@@ -10,10 +10,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PNM_EDIVERGED, PNM_ENOTCONV, PNM_INIT_KEEP, PNM_INIT_MBPT2, PNM_INIT_MLP,
-                   PNM_INIT_ZERO, PNM_PREC_BF16X3, PNM_PREC_FP64, PNM_TERMS_FULL, PNM_TERMS_LINEAR,
+                   PNM_INIT_ZERO, PNM_PREC_BF16X3, PNM_PREC_F32PAIR, PNM_PREC_FP64, PNM_TERMS_FULL, PNM_TERMS_LINEAR,
                    PNM_TERMS_PP, PNM_TERMS_PPHH, PnmError)
 
-__all__ = ["Context", "MINNESOTA", "PnmError", "PNM_PREC_FP64", "PNM_PREC_BF16X3",
+__all__ = ["Context", "MINNESOTA", "PnmError", "PNM_PREC_FP64", "PNM_PREC_BF16X3", "PNM_PREC_F32PAIR",
            "PNM_INIT_MBPT2", "PNM_INIT_ZERO", "PNM_INIT_KEEP", "PNM_INIT_MLP", "PNM_ENOTCONV",
            "PNM_TERMS_FULL", "PNM_TERMS_PP", "PNM_TERMS_PPHH", "PNM_TERMS_LINEAR", "twist_mesh",
            "PNM_EDIVERGED", "mlp_num_params", "mlp_init", "mlp_train", "mlp_forward", "mlp_loss_grad"]
@@ -138,14 +138,17 @@ class Context:
 
     # -------------------------------------------------------------------- solve
     def solve(self, precision=PNM_PREC_FP64, alpha=0.5, tol=1e-10, tol_per_N=0.0, max_iter=500,
-              refine_sweeps=0, init=PNM_INIT_MBPT2, host_loop=False, allow=(), terms=PNM_TERMS_FULL):
-        """pnm_ccd_solve; returns (dE[nsys], iters[nsys], resid[nsys], rc)."""
+              refine_sweeps=0, init=PNM_INIT_MBPT2, host_loop=False, allow=(), terms=PNM_TERMS_FULL,
+              refine_kernels=PNM_PREC_FP64):
+        """pnm_ccd_solve; returns (dE[nsys], iters[nsys], resid[nsys], rc).  refine_kernels:
+        PNM_PREC_FP64 or PNM_PREC_F32PAIR for the contractions of the refinement sweeps."""
         L = _lib.load()
         o = _lib.pnm_solve_opts()
         L.pnm_default_opts(C.byref(o))
         o.precision, o.mix_alpha, o.tol_dE, o.tol_dE_per_N = precision, alpha, tol, tol_per_N
         o.max_iter, o.refine_sweeps, o.init, o.host_loop = max_iter, refine_sweeps, init, int(host_loop)
         o.terms = terms
+        o.refine_kernels = refine_kernels
         dE = np.zeros(self.nsys)
         it = np.zeros(self.nsys, np.int32)
         res = np.zeros(self.nsys)

@@ -19,6 +19,7 @@ PNM_ETIMEOUT = -6
 
 PNM_PREC_FP64 = 0
 PNM_PREC_BF16X3 = 2
+PNM_PREC_F32PAIR = 3
 PNM_INIT_MBPT2 = 0
 PNM_INIT_ZERO = 1
 PNM_INIT_KEEP = 2
@@ -54,7 +55,7 @@ class pnm_minnesota(C.Structure):
 class pnm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("mix_alpha", C.c_double), ("tol_dE", C.c_double),
                 ("tol_dE_per_N", C.c_double), ("max_iter", C.c_int), ("refine_sweeps", C.c_int),
-                ("init", C.c_int), ("host_loop", C.c_int), ("terms", C.c_int)]
+                ("init", C.c_int), ("host_loop", C.c_int), ("terms", C.c_int), ("refine_kernels", C.c_int)]
 
 
 class pnm_mlp_opts(C.Structure):

@@ -121,6 +121,7 @@ void pnm_default_opts(pnm_solve_opts* o) {
   o->init = PNM_INIT_MBPT2;
   o->host_loop = 0;
   o->terms = PNM_TERMS_FULL;
+  o->refine_kernels = PNM_PREC_FP64;
 }
 
 const char* pnm_last_error(void) { return g_last_error.c_str(); }
@@ -502,7 +503,7 @@ int pnm_apply_pp_ladder(pnm_ctx* ctx, int sys, int precision, const double* t, d
   return guarded([&]() {
     check_sys(ctx, sys);
     if (!t || !r) throw PnmError{PNM_EINVAL, "null argument"};
-    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3)
+    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3 && precision != PNM_PREC_F32PAIR)
       throw PnmError{PNM_EINVAL, "unknown precision mode"};
     pnm_apply_pp(ctx, sys, precision, t, r, n);
     return PNM_OK;
@@ -513,7 +514,7 @@ int pnm_apply_ph_term(pnm_ctx* ctx, int sys, int precision, const double* t, dou
   return guarded([&]() {
     check_sys(ctx, sys);
     if (!t || !r) throw PnmError{PNM_EINVAL, "null argument"};
-    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3)
+    if (precision != PNM_PREC_FP64 && precision != PNM_PREC_BF16X3 && precision != PNM_PREC_F32PAIR)
       throw PnmError{PNM_EINVAL, "unknown precision mode"};
     pnm_apply_ph(ctx, sys, precision, t, r, n);
     return PNM_OK;

@@ -131,39 +131,31 @@ struct VecT<double, 2> {
   }
 };
 template <>
-struct VecT<double, 4> {
-  __device__ __forceinline__ static void ld(const double* p, double (&v)[4]) {
-    double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  }
-};
-template <>
-struct VecT<float, 2> {
-  __device__ __forceinline__ static void ld(const float* p, float (&v)[2]) {
-    float2 a = *reinterpret_cast<const float2*>(p);
-    v[0] = a.x; v[1] = a.y;
-  }
-};
-template <>
 struct VecT<float, 4> {
   __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
     float4 q = *reinterpret_cast<const float4*>(p);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
 };
+template <>
+struct VecT<f2, 2> {
+  __device__ __forceinline__ static void ld(const f2* p, f2 (&v)[2]) {
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = f2{q.x, q.y}; v[1] = f2{q.z, q.w};
+  }
+};
 
-// Element e of a cross channel's T: gathered from the current amplitudes through the signed
-// index map (GATHER: FP64 iteration) or read from the copy the update scatters (mixed).
-template <typename T_, bool GATHER>
+// Element e of a cross channel's T: read from the FP32 copy in the cross-channel layout that
+// the mixed update scatters (xt), or gathered from the current FP64 amplitudes through the
+// signed index map (FP64 and FP32-pair kernels, xt == nullptr).
+template <typename T_>
 __device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__ tcur,
                                    const T_* __restrict__ xt, long e) {
-  if constexpr (GATHER) {
-    int cd = D.xmap[e];
-    T_ g = cd == 0 ? (T_)0 : (T_)tcur[cd > 0 ? cd - 1 : -cd - 1];
-    return cd < 0 ? -g : g;
-  } else {
-    return xt[e];
-  }
+  using A = Arith<T_>;
+  if (xt) return xt[e];
+  int cd = D.xmap[e];
+  double g = cd == 0 ? 0.0 : tcur[cd > 0 ? cd - 1 : -cd - 1];
+  return A::from_double(cd < 0 ? -g : g);
 }
 
 // Bytes reserved for the index tables at the start of a k_ph CTA's shared memory (R4 + 2 H4
@@ -176,12 +168,14 @@ __host__ __device__ __forceinline__ size_t ph_index_bytes(int R4, int H4) { retu
 //   Ts = T (R x H), Xt = W^T staged as W (R x H), then T^T (H x R), Cs = C (H x H);
 //   C[(k,c)][(j,b)] = <kb|v|cj> + 1/2 sum_(e,l) <kl|v|ce> t_lj^eb   (xw == nullptr: <kb|v|cj>)
 //   Q[(a,i)][(j,b)] = sum_(k,c) t_ik^ac C[(k,c)][(j,b)]
-// Each thread accumulates TS x TS outputs of every problem per tile.
-template <typename T_, int NT, int TS, int NM, bool GATHER>
+// Each thread accumulates TS x TS outputs of every problem per tile.  Element arithmetic is
+// that of Arith<T_> (FP64, FP32, or FP32 pairs with FP64 results).
+template <typename T_, int NT, int TS, int NM>
 __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __restrict__ ctl, int x,
                                          unsigned char* smraw, const T_* __restrict__ xt,
                                          const T_* __restrict__ xw, const T_* __restrict__ xv1,
-                                         T_* __restrict__ xq) {
+                                         typename Arith<T_>::Out* __restrict__ xq) {
+  using A = Arith<T_>;
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const int R = NM == 2 ? nph >> 1 : nph, H = NM == 2 ? nhp >> 1 : nhp;
   // padded to multiples of the register tile (zeros): the padding costs FMAs in the tiles
@@ -208,27 +202,27 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
     }
     __syncthreads();
   }
-  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
+  const double* tcur = xt ? nullptr : cur_t(D, ctl);
   const bool quad = xw != nullptr;
 #pragma unroll 4
   for (int e = threadIdx.x; e < RH; e += NT) {
     int u = e / H4, s = e % H4;
-    T_ t0 = 0, t1 = 0, w0 = 0, w1 = 0;
+    T_ t0 = A::zero(), t1 = A::zero(), w0 = A::zero(), w1 = A::zero();
     if (u < R && s < H) {
       if constexpr (NM == 1) {
         long o = (long)u * nhp + s;
-        t0 = ph_t<T_, GATHER>(D, tcur, xt, to + o);
+        t0 = ph_t<T_>(D, tcur, xt, to + o);
         if (quad) w0 = xw[wo + o];
       } else {
         int row = sra[u], ca = sca[s], cb = scb[s];
         long oa = (long)row * nhp + ca, ob = (long)row * nhp + cb;
-        T_ ta = ph_t<T_, GATHER>(D, tcur, xt, to + oa), tb = ph_t<T_, GATHER>(D, tcur, xt, to + ob);
-        t0 = ta + tb;
-        t1 = ta - tb;
+        T_ ta = ph_t<T_>(D, tcur, xt, to + oa), tb = ph_t<T_>(D, tcur, xt, to + ob);
+        t0 = A::add(ta, tb);
+        t1 = A::sub(ta, tb);
         if (quad) {
           T_ wa = xw[wo + oa], wb = xw[wo + ob];
-          w0 = wa + wb;
-          w1 = wa - wb;
+          w0 = A::add(wa, wb);
+          w1 = A::sub(wa, wb);
         }
       }
     }
@@ -242,15 +236,15 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
 #pragma unroll 4
   for (int e = threadIdx.x; e < HH; e += NT) {
     int r = e / H4, c = e % H4;
-    T_ v0 = 0, v1 = 0;
+    T_ v0 = A::zero(), v1 = A::zero();
     if (r < H && c < H) {
       if constexpr (NM == 1) {
         v0 = xv1[co + (long)r * nhp + c];
       } else {
         const long ra = co + (long)sca[r] * nhp;
         T_ va = xv1[ra + sca[c]], vb = xv1[ra + scb[c]];
-        v0 = va + vb;
-        v1 = va - vb;
+        v0 = A::add(va, vb);
+        v1 = A::sub(va, vb);
       }
     }
     Cs[e] = v0;
@@ -265,7 +259,11 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
       const int r0 = (tt / th) * TS, s0 = (tt % th) * TS;
       const T_* X = Xt + mtx * RH;
       const T_* Tm = Ts + mtx * RH;
-      T_ acc[TS][TS] = {};
+      T_ acc[TS][TS];
+#pragma unroll
+      for (int i = 0; i < TS; i++)
+#pragma unroll
+        for (int j = 0; j < TS; j++) acc[i][j] = A::zero();
       for (int u = 0; u < R; u++) {
         T_ a[TS], b[TS];
         VecT<T_, TS>::ld(X + u * H4 + r0, a);
@@ -273,13 +271,16 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
 #pragma unroll
         for (int i = 0; i < TS; i++)
 #pragma unroll
-          for (int j = 0; j < TS; j++) acc[i][j] += a[i] * b[j];
+          for (int j = 0; j < TS; j++) A::mac(acc[i][j], a[i], b[j]);
       }
       T_* Cm = Cs + mtx * HH;
 #pragma unroll
       for (int i = 0; i < TS; i++)
 #pragma unroll
-        for (int j = 0; j < TS; j++) Cm[(r0 + i) * H4 + s0 + j] += (T_)0.5 * acc[i][j];
+        for (int j = 0; j < TS; j++) {
+          T_& cv = Cm[(r0 + i) * H4 + s0 + j];
+          cv = A::add(cv, A::half(acc[i][j]));
+        }
     }
     __syncthreads();
   }
@@ -292,7 +293,13 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
   const int tr = R4 / TS;
   for (int tile = threadIdx.x; tile < tr * th; tile += NT) {
     const int r0 = (tile / th) * TS, s0 = (tile % th) * TS;
-    T_ acc[NM][TS][TS] = {};
+    T_ acc[NM][TS][TS];
+#pragma unroll
+    for (int m = 0; m < NM; m++)
+#pragma unroll
+      for (int i = 0; i < TS; i++)
+#pragma unroll
+        for (int j = 0; j < TS; j++) acc[m][i][j] = A::zero();
     for (int u = 0; u < H; u++) {
 #pragma unroll
       for (int mtx = 0; mtx < NM; mtx++) {
@@ -302,7 +309,7 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
 #pragma unroll
         for (int i = 0; i < TS; i++)
 #pragma unroll
-          for (int j = 0; j < TS; j++) acc[mtx][i][j] += a[i] * b[j];
+          for (int j = 0; j < TS; j++) A::mac(acc[mtx][i][j], a[i], b[j]);
       }
     }
 #pragma unroll
@@ -313,7 +320,7 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
         const long qr = to + (long)r * nhp;
 #pragma unroll
         for (int j = 0; j < TS; j++)
-          if (s0 + j < H) xq[qr + s0 + j] = acc[0][i][j];
+          if (s0 + j < H) xq[qr + s0 + j] = A::out(acc[0][i][j]);
       } else {
         // the spin-up row's two blocks; the flipped rows are never read (see qpos)
         const long qa = to + (long)sra[r] * nhp;
@@ -321,8 +328,8 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
         for (int j = 0; j < TS; j++) {
           const int s = s0 + j;
           if (s < H) {
-            xq[qa + sca[s]] = (T_)0.5 * (acc[0][i][j] + acc[1][i][j]);
-            xq[qa + scb[s]] = (T_)0.5 * (acc[0][i][j] - acc[1][i][j]);
+            xq[qa + sca[s]] = A::out(A::half(A::add(acc[0][i][j], acc[1][i][j])));
+            xq[qa + scb[s]] = A::out(A::half(A::sub(acc[0][i][j], acc[1][i][j])));
           }
         }
       }
@@ -334,11 +341,12 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
 // warp per channel with its own shared buffers (stride PH_WARP_DIM), no block-wide
 // synchronisation; the same two bodies as the CTA path, one output element per lane and step.
 constexpr int PH_WARPS = PH_THREADS / 32;
-template <typename T_, bool GATHER>
+template <typename T_>
 __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* __restrict__ ctl, int x, int w,
                                              int lane, unsigned char* smraw, const T_* __restrict__ xt,
                                              const T_* __restrict__ xw, const T_* __restrict__ xv1,
-                                             T_* __restrict__ xq) {
+                                             typename Arith<T_>::Out* __restrict__ xq) {
+  using A = Arith<T_>;
   constexpr int S = PH_WARP_DIM;
   const int nph = D.x_nph[x], nhp = D.x_nhp[x];
   const bool two = D.x_cls[x] == 0;
@@ -363,22 +371,22 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
     }
   }
   __syncwarp();
-  const double* tcur = GATHER ? cur_t(D, ctl) : nullptr;
+  const double* tcur = xt ? nullptr : cur_t(D, ctl);
   const bool quad = xw != nullptr;
   for (int e = lane; e < R * H; e += 32) {
     int u = e / H, c = e % H;
     if (two) {
       long oa = (long)sra[u] * nhp + sca[c], ob = (long)sra[u] * nhp + scb[c];
-      T_ ta = ph_t<T_, GATHER>(D, tcur, xt, to + oa), tb = ph_t<T_, GATHER>(D, tcur, xt, to + ob);
-      Ts[u * S + c] = ta + tb;
-      Ts[S * S + u * S + c] = ta - tb;
-      T_ wa = quad ? xw[wo + oa] : (T_)0, wb = quad ? xw[wo + ob] : (T_)0;
-      Ws[u * S + c] = wa + wb;
-      Ws[S * S + u * S + c] = wa - wb;
+      T_ ta = ph_t<T_>(D, tcur, xt, to + oa), tb = ph_t<T_>(D, tcur, xt, to + ob);
+      Ts[u * S + c] = A::add(ta, tb);
+      Ts[S * S + u * S + c] = A::sub(ta, tb);
+      T_ wa = quad ? xw[wo + oa] : A::zero(), wb = quad ? xw[wo + ob] : A::zero();
+      Ws[u * S + c] = A::add(wa, wb);
+      Ws[S * S + u * S + c] = A::sub(wa, wb);
     } else {
       long o = (long)u * nhp + c;
-      Ts[u * S + c] = ph_t<T_, GATHER>(D, tcur, xt, to + o);
-      Ws[u * S + c] = quad ? xw[wo + o] : (T_)0;
+      Ts[u * S + c] = ph_t<T_>(D, tcur, xt, to + o);
+      Ws[u * S + c] = quad ? xw[wo + o] : A::zero();
     }
   }
   __syncwarp();
@@ -389,27 +397,27 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
       if (two) {
         const long ra = co + (long)sca[r] * nhp;
         T_ va = xv1[ra + sca[c]], vb = xv1[ra + scb[c]];
-        v = m == 0 ? va + vb : va - vb;
+        v = m == 0 ? A::add(va, vb) : A::sub(va, vb);
       } else {
         v = xv1[co + (long)r * nhp + c];
       }
-      T_ acc = 0;
-      for (int u = 0; u < R && quad; u++) acc += Ws[m * S * S + u * S + r] * Ts[m * S * S + u * S + c];
-      Cs[m * S * S + r * S + c] = v + (T_)0.5 * acc;
+      T_ acc = A::zero();
+      for (int u = 0; u < R && quad; u++) A::mac(acc, Ws[m * S * S + u * S + r], Ts[m * S * S + u * S + c]);
+      Cs[m * S * S + r * S + c] = A::add(v, A::half(acc));
     }
   }
   __syncwarp();
   for (int e = lane; e < R * H; e += 32) {
     int r = e / H, c = e % H;
-    T_ acc[2] = {0, 0};
+    T_ acc[2] = {A::zero(), A::zero()};
     for (int m = 0; m < nm; m++)
-      for (int u = 0; u < H; u++) acc[m] += Ts[m * S * S + r * S + u] * Cs[m * S * S + u * S + c];
+      for (int u = 0; u < H; u++) A::mac(acc[m], Ts[m * S * S + r * S + u], Cs[m * S * S + u * S + c]);
     if (two) {
       const long qa = to + (long)sra[r] * nhp;
-      xq[qa + sca[c]] = (T_)0.5 * (acc[0] + acc[1]);
-      xq[qa + scb[c]] = (T_)0.5 * (acc[0] - acc[1]);
+      xq[qa + sca[c]] = A::out(A::half(A::add(acc[0], acc[1])));
+      xq[qa + scb[c]] = A::out(A::half(A::sub(acc[0], acc[1])));
     } else {
-      xq[to + (long)r * nhp + c] = acc[0];
+      xq[to + (long)r * nhp + c] = A::out(acc[0]);
     }
   }
 }
@@ -417,20 +425,20 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
 // The ph term in one launch over the S_z >= 0 cross channels (xlist): the first nblk CTAs take
 // one channel each (the costliest first), with the S_z > 0 or the S_z = 0 body chosen per
 // channel; the remaining CTAs take PH_WARPS small channels each, one per warp.
-template <typename T_, int NT, int TS, bool GATHER>
+template <typename T_, int NT, int TS>
 __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
                                            const int* __restrict__ xlist, int nblk, int nwarp,
                                            const T_* __restrict__ xt, const T_* __restrict__ xw,
-                                           const T_* __restrict__ xv1, T_* __restrict__ xq) {
+                                           const T_* __restrict__ xv1, typename Arith<T_>::Out* __restrict__ xq) {
   static_assert(NT == PH_WARPS * 32, "one warp per small channel");
   extern __shared__ __align__(16) unsigned char smraw[];
   if ((int)blockIdx.x < nblk) {
     const int x = xlist[blockIdx.x];
     if (sys_done(D, ctl, D.x_sys[x])) return;  // CTA-uniform
     if (D.x_cls[x] == 0)
-      ph_block<T_, NT, TS, 2, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
+      ph_block<T_, NT, TS, 2>(D, ctl, x, smraw, xt, xw, xv1, xq);
     else
-      ph_block<T_, NT, TS, 1, GATHER>(D, ctl, x, smraw, xt, xw, xv1, xq);
+      ph_block<T_, NT, TS, 1>(D, ctl, x, smraw, xt, xw, xv1, xq);
     return;
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict
   if (idx >= nwarp) return;  // whole warps leave; the warp path never synchronises the block
   const int x = xlist[nblk + idx];
   if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
-  ph_warp_body<T_, GATHER>(D, ctl, x, w, lane, smraw, xt, xw, xv1, xq);
+  ph_warp_body<T_>(D, ctl, x, w, lane, smraw, xt, xw, xv1, xq);
 }
 
 static size_t ph_warp_smem(size_t elem) {
@@ -458,38 +466,48 @@ static size_t ph_smem_of(const pnm_ctx* ctx) {
   return ctx->n_ph_warp > 0 ? std::max(b, ph_warp_smem(sizeof(T_))) : b;
 }
 
-// The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).  FP64:
-// 2 x 2 register tiles (little padding; the FP64 pipe bounds the kernel); FP32: 4 x 4 (fewer
-// shared-memory loads per FMA).
-template <typename T_, bool GATHER>
-static void launch_ph_list(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, T_* xq, cudaStream_t s) {
-  constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
+// Register tile of the ph kernels: 2 x 2 for FP64 (little padding; the FP64 pipe bounds the
+// kernel) and FP32 pairs, 4 x 4 for FP32 (fewer shared-memory loads per FMA).
+template <typename T_>
+constexpr int ph_tile() { return std::is_same<T_, float>::value ? 4 : 2; }
+
+// The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).
+template <typename T_>
+static void launch_ph_list(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, typename Arith<T_>::Out* xq,
+                           cudaStream_t s) {
+  constexpr int TS = ph_tile<T_>();
   int grid = ctx->n_ph + (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
   if (grid > 0)
-    k_ph<T_, PH_THREADS, TS, GATHER><<<grid, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
+    k_ph<T_, PH_THREADS, TS><<<grid, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
         ctx->d, ctx->ctl, ctx->ph_list, ctx->n_ph, ctx->n_ph_warp, xt, xw, xv1, xq);
 }
 
-template <typename T_, bool GATHER>
+template <typename T_>
 static void ph_attributes(const pnm_ctx* ctx) {
-  constexpr int TS = sizeof(T_) == 8 ? 2 : 4;
-  smem_at_least(k_ph<T_, PH_THREADS, TS, GATHER>, ph_smem_of<T_>(ctx));
+  smem_at_least(k_ph<T_, PH_THREADS, ph_tile<T_>()>, ph_smem_of<T_>(ctx));
 }
 
 // FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear) {
-  launch_ph_list<double, true>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
+  launch_ph_list<double>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
 }
 
-// Mixed ph: T read from the copy the update scatters.
-void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
-                   cudaStream_t s) {
-  launch_ph_list<float, false>(ctx, xt, xw, xv1, xq, s);
+// The same term with FP32-pair arithmetic (FP64 input amplitudes, W and <kb|v|cj> split into
+// FP32 pairs once per context, FP64 Q): the contractions of the refinement sweeps.
+void launch_ph_f2(pnm_ctx* ctx, const f2* xw, const f2* xv1, cudaStream_t s) {
+  launch_ph_list<f2>(ctx, nullptr, xw, xv1, ctx->d.xq, s);
+}
+
+// Mixed ph: T read from the FP32 cross-channel copy the update scatters, Q in FP32 at its
+// cross-channel positions (the update gathers the four terms of each amplitude).
+void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq, cudaStream_t s) {
+  launch_ph_list<float>(ctx, xt, xw, xv1, xq, s);
 }
 
 void pnm_ph_attributes(const pnm_ctx* ctx) {
-  ph_attributes<double, true>(ctx);
-  ph_attributes<float, false>(ctx);
+  ph_attributes<double>(ctx);
+  ph_attributes<float>(ctx);
+  ph_attributes<f2>(ctx);
 }
 
 // ------------------------------------------------------------------------ ladder basis
@@ -546,16 +564,21 @@ __global__ void __launch_bounds__(128) k_lad_expand(DevState D, const T_* __rest
 // R^T(ij, ab) = sum_cd t(ij, cd) <cd|v|ab>, restricted pairs (1/2 sum over ordered cd of a
 // pair-antisymmetric product = sum over c<d).  One CTA per work item (channel, 32 pp
 // columns); its 8 warps split the cd range, lane = column, so each warp streams coalesced
-// 256-byte rows of the symmetric V block.  hh rows go in groups of 8 staged in shared
-// memory; the 8 partial sums per output are added in a fixed order (deterministic).
+// rows of the symmetric V block.  hh rows go in groups of 8 staged in shared memory; the 8
+// partial sums per output are added in a fixed order (deterministic).  Element arithmetic is
+// that of Arith<T_>: FP64, or FP32 pairs (V split once per context, the staged amplitudes
+// split on the way into shared memory, FP64 result).
 constexpr int PP64_COLS = 32, PP64_WARPS = 8, PP64_ROWS = 8;
 static size_t pp64_smem(int npp) {
   return sizeof(double) * ((size_t)PP64_ROWS * npp + PP64_WARPS * PP64_ROWS * 32);
 }
 
-__global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const LoopCtl* __restrict__ ctl,
-                                                          const int2* __restrict__ items, int rep_only) {
-  extern __shared__ double sm[];  // ts[PP64_ROWS][npp], red[PP64_WARPS][PP64_ROWS][32]
+template <typename T_>
+__global__ void __launch_bounds__(PP64_WARPS * 32) k_pp(DevState D, const LoopCtl* __restrict__ ctl,
+                                                        const int2* __restrict__ items, int rep_only,
+                                                        const T_* __restrict__ vpp) {
+  using A = Arith<T_>;
+  extern __shared__ __align__(16) unsigned char smpp[];  // ts[PP64_ROWS][npp], red[PP64_WARPS][PP64_ROWS][32]
   int2 it = items[blockIdx.x];
   int c = it.x, ab0 = it.y;
   if (sys_done(D, ctl, D.ch_sys[c])) return;
@@ -564,46 +587,46 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const Loop
   int npp = D.ch_npp[c], nh = rep_only ? D.ch_uoff[c + 1] - D.ch_uoff[c] : D.ch_nhh[c];
   long tb = D.ch_t_off[c];
   const double* __restrict__ t = cur_t(D, ctl);
-  double* ts = sm;
-  double* red = sm + PP64_ROWS * npp;
+  T_* ts = reinterpret_cast<T_*>(smpp);
+  T_* red = ts + PP64_ROWS * npp;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int ab = ab0 + lane;
   bool col = ab < npp;
   int chunk = (npp + PP64_WARPS - 1) / PP64_WARPS;
   int lo = warp * chunk, hi = min(npp, lo + chunk);
-  const double* __restrict__ V = D.v_pppp + D.ch_vpp_off[c] + (col ? ab : 0);
+  const T_* __restrict__ V = vpp + D.ch_vpp_off[c] + (col ? ab : 0);
   for (int g0 = 0; g0 < nh; g0 += PP64_ROWS) {
     int nr = min(PP64_ROWS, nh - g0);
     __syncthreads();
     for (int e = threadIdx.x; e < nr * npp; e += blockDim.x) {
       int g = g0 + e / npp;
-      ts[e] = t[tb + (long)(rows ? rows[g] : g) * npp + e % npp];
+      ts[e] = A::from_double(t[tb + (long)(rows ? rows[g] : g) * npp + e % npp]);
     }
     __syncthreads();
-    double acc[PP64_ROWS];
+    T_ acc[PP64_ROWS];
 #pragma unroll
-    for (int r = 0; r < PP64_ROWS; r++) acc[r] = 0.0;
+    for (int r = 0; r < PP64_ROWS; r++) acc[r] = A::zero();
     if (col) {
       int cd = lo;
       for (; cd + 4 <= hi; cd += 4) {
-        double v0 = V[(long)cd * npp], v1 = V[(long)(cd + 1) * npp];
-        double v2 = V[(long)(cd + 2) * npp], v3 = V[(long)(cd + 3) * npp];
+        T_ v0 = V[(long)cd * npp], v1 = V[(long)(cd + 1) * npp];
+        T_ v2 = V[(long)(cd + 2) * npp], v3 = V[(long)(cd + 3) * npp];
 #pragma unroll
         for (int r = 0; r < PP64_ROWS; r++) {
           if (r < nr) {
-            const double* tr = ts + r * npp + cd;
-            acc[r] = fma(tr[0], v0, acc[r]);
-            acc[r] = fma(tr[1], v1, acc[r]);
-            acc[r] = fma(tr[2], v2, acc[r]);
-            acc[r] = fma(tr[3], v3, acc[r]);
+            const T_* tr = ts + r * npp + cd;
+            A::mac(acc[r], tr[0], v0);
+            A::mac(acc[r], tr[1], v1);
+            A::mac(acc[r], tr[2], v2);
+            A::mac(acc[r], tr[3], v3);
           }
         }
       }
       for (; cd < hi; cd++) {
-        double v0 = V[(long)cd * npp];
+        T_ v0 = V[(long)cd * npp];
 #pragma unroll
         for (int r = 0; r < PP64_ROWS; r++)
-          if (r < nr) acc[r] = fma(ts[r * npp + cd], v0, acc[r]);
+          if (r < nr) A::mac(acc[r], ts[r * npp + cd], v0);
       }
     }
 #pragma unroll
@@ -611,12 +634,22 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp64(DevState D, const Loop
     __syncthreads();
     if ((int)threadIdx.x < nr * 32) {
       int r = threadIdx.x >> 5, l = threadIdx.x & 31;
-      double s = 0.0;
+      T_ s = A::zero();
 #pragma unroll
-      for (int w = 0; w < PP64_WARPS; w++) s += red[(w * PP64_ROWS + r) * 32 + l];
-      if (ab0 + l < npp) D.rpp[tb + (long)(rows ? rows[g0 + r] : g0 + r) * npp + ab0 + l] = s;
+      for (int w = 0; w < PP64_WARPS; w++) s = A::add(s, red[(w * PP64_ROWS + r) * 32 + l]);
+      if (ab0 + l < npp) D.rpp[tb + (long)(rows ? rows[g0 + r] : g0 + r) * npp + ab0 + l] = A::out(s);
     }
   }
+}
+
+// W in the ladder basis split into FP32 pairs (the refinement sweeps' copy of v_pppp).
+__global__ void k_split_f2(const double* __restrict__ a, f2* __restrict__ b, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = Arith<f2>::from_double(a[i]);
+}
+
+void pnm_split_f2(const double* a, f2* b, long n, cudaStream_t s) {
+  if (n > 0) k_split_f2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
 }
 
 // ----------------------------------------------------------------------- finalize
@@ -810,70 +843,42 @@ void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
                                                       fin_args(ctx, use_cond, h, false));
 }
 
-// hh ladder of the mixed iteration, sum_kl t_ab^kl chi_kl^ij in FP32 (read by the mixed update
-// on the rows it computes): one CTA per (channel, 128 pp columns) of the channels with such
-// rows; the chi block and the t columns are staged in shared memory (thread = column), rows in
-// groups of 8 accumulated in registers.
-__global__ void __launch_bounds__(128) k_hh32(DevState D, const LoopCtl* __restrict__ ctl,
-                                              const int2* __restrict__ ab_items, float* __restrict__ hh) {
-  extern __shared__ __align__(16) float hsm[];
-  int2 it = ab_items[blockIdx.x];
-  int c = it.x, ab = it.y + threadIdx.x;
-  if (sys_done(D, ctl, D.ch_sys[c])) return;
-  // nothing in a channel whose rows are all written as spin flips of another channel's
-  if (D.ch_uoff[c + 1] == D.ch_uoff[c]) return;
-  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
-  const float* __restrict__ t32 = cur_t32(D, ctl);
-  float* chs = hsm;            // chi[kl][ij], nh x nh
-  float* ts = hsm + nh * nh;   // t[kl][column], nh x 128
-  long base = D.ch_t_off[c];
-  const float* chi = D.chi32 + D.ch_vhh_off[c];
-  for (int e = threadIdx.x; e < nh * nh; e += blockDim.x) chs[e] = chi[e];
-  bool ok = ab < npp;
-  for (int kl = 0; kl < nh; kl++) ts[kl * 128 + threadIdx.x] = ok ? t32[base + (long)kl * npp + ab] : 0.0f;
-  __syncthreads();
-  if (!ok) return;
-  // every row in groups of 8 (contiguous chi reads); the rows the update does not compute see
-  // columns of chi that k_tstats left out, and their results are never read
-  for (int ij0 = 0; ij0 < nh; ij0 += 8) {
-    float acc[8];
-#pragma unroll
-    for (int g = 0; g < 8; g++) acc[g] = 0.0f;
-    for (int kl = 0; kl < nh; kl++) {
-      float tk = ts[kl * 128 + threadIdx.x];
-      const float* cr = chs + kl * nh + ij0;
-#pragma unroll
-      for (int g = 0; g < 8; g++)
-        if (ij0 + g < nh) acc[g] = fmaf(tk, cr[g], acc[g]);
-    }
-#pragma unroll
-    for (int g = 0; g < 8; g++)
-      if (ij0 + g < nh) hh[base + (long)(ij0 + g) * npp + ab] = acc[g];
-  }
-}
-
-// Mixed-precision update.  One CTA per item (channel, up to UPD_ROWS hole pairs ij, 128 pp
-// columns); each thread owns one column ab and the item's rows, so the block reductions of
-// the energy and residual are shared by up to UPD_ROWS amplitudes.  The bracket's correction
-// terms (one-body, pp and hh ladders, ph) are taken in FP32 from the FP32 copies; v, the
-// denominator, the Jacobi step with mixing, the residual and the energy in FP64.  The FP64
-// unit is the scarce one, so the step is written as t + alpha R / eps with R = bracket -
-// eps t (the value of alpha t_new + (1 - alpha) t).  Rows go in batches of UPD_BATCH: all
-// loads of a batch are issued before any store (rows past ng repeat the last row and are
-// discarded).  Writes the new amplitude in FP64, FP32 and at its four places in the ph term's T;
-// the pp ladder arrives in the ladder layout (lad_index).
+// Mixed-precision update.  One CTA per item (channel, up to UPD_ROWS hole pairs ij of the rows
+// the updates compute, 128 pp columns); each thread owns one column ab and the item's rows.
+//   hh ladder   sum_kl t_ab^kl chi_kl^ij in FP32 for all rows of the item from one pass over
+//               the FP32 t column (chi's columns of the item's rows staged in shared memory)
+//   bracket     corrections in FP32: one-body (d_a + d_b - d_i - d_j) t, pp ladder (ladder
+//               layout, k-split planes summed), hh ladder, and the ph term
+//               Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba gathered from the cross-channel Q (qmap)
+//   T scatter   the new FP32 amplitude to its four places in the ph term's T (the positions of
+//               the four Q terms, qmap; formed positions only, so the same for the amplitude
+//               and its spin flip), which the next ph kernel reads row by row
+//   FP64        denominator eps_a + eps_b - eps_i - eps_j, residual R = v + bracket - eps_ij^ab t,
+//               step t + alpha R / eps_ij^ab (alpha / eps_ij^ab prepared per solve), energy and
+//               residual partial sums; v = <ab|v|ij> regenerated from the system's interaction
+//               table (bit for bit the stored element, one FP64 addition) instead of streamed
+// Arrays read once per update (t, alpha / eps, flip and Q maps) and the FP64 amplitudes written
+// for the next update are streamed with the evict-first policy, so that the ph term's T and Q
+// (50 MB each for the held-out batch, read and written at random) and the FP32 amplitudes the
+// next update's contractions read stay in L2.
+// The FP64 unit of a GB300 runs at about 1/64 of its FP32 rate, so the FP64 work is held to
+// eight instructions per amplitude; the new amplitude goes to t (FP64) and t32 for itself and,
+// sign applied, for its spin flip.  Rows go in batches of UPD_BATCH with all loads of a batch
+// issued before any store (rows past ng repeat the last row and are discarded).
 __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, LoopCtl* __restrict__ ctl,
                                                     const int4* __restrict__ items, FinArgs fa,
-                                                    const float* __restrict__ rpp, const float* __restrict__ hh,
-                                                    const float* __restrict__ xq, PackArgs pk, int nplanes,
-                                                    long pstride) {
+                                                    const float* __restrict__ rpp, const float* __restrict__ xq,
+                                                    const double* __restrict__ aw, float* __restrict__ xt,
+                                                    const int* __restrict__ lut_off, int nplanes, long pstride) {
+  __shared__ float chs[UPD_MAX_NHH * UPD_ROWS];  // chi32[kl][ij of row g] at kl * UPD_ROWS + g
   __shared__ float row_dij[UPD_ROWS];
   __shared__ double row_eij[UPD_ROWS];
   __shared__ int row_ij[UPD_ROWS];
-  __shared__ double sh32[32];
+  __shared__ char4 row_si[UPD_ROWS], row_sj[UPD_ROWS];
+  __shared__ double red[2][128];
   int4 it = items[blockIdx.x];
   int c = it.x, ng = it.w;
-  int npp = D.ch_npp[c];
+  int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   int ab = it.z + threadIdx.x;
   if ((int)threadIdx.x < UPD_ROWS) {
     int g = min((int)threadIdx.x, ng - 1);
@@ -882,8 +887,10 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     row_ij[threadIdx.x] = ij;
     row_dij[threadIdx.x] = D.dchi32[h.x] + D.dchi32[h.y];
     row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
+    row_si[threadIdx.x] = D.nvec[h.x];
+    row_sj[threadIdx.x] = D.nvec[h.y];
   }
-  bool frozen = fa.sc[D.ch_sys[c]].done != 0;
+  const bool frozen = fa.sc[D.ch_sys[c]].done != 0;
   if (sys_settled(fa.sc[D.ch_sys[c]], ctl)) {
     // converged at least two steps ago: both amplitude buffers already hold its values
     if (threadIdx.x == 0) {
@@ -893,111 +900,160 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     last_block_finalize(fa, ctl);
     return;
   }
-  bool has_vpp = D.ch_vpp[c] != 0;
-  double alpha = ctl->alpha;
+  __syncthreads();
+  if (!frozen) {
+    const float* __restrict__ chi = D.chi32 + D.ch_vhh_off[c];
+    for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
+      const int kl = e / UPD_ROWS, g = e % UPD_ROWS;
+      chs[e] = g < ng ? chi[(long)kl * nh + row_ij[g]] : 0.0f;
+    }
+  }
+  __syncthreads();
+  const bool has_vpp = D.ch_vpp[c] != 0;
   const double* __restrict__ t = cur_t(D, ctl);
   const float* __restrict__ t32 = cur_t32(D, ctl);
   double* __restrict__ tn = next_t(D, ctl);
   float* __restrict__ t32n = next_t32(D, ctl);
-  long base = D.ch_t_off[c];
-  __syncthreads();
-  double esum = 0.0, rsum = 0.0;
+  const long base = D.ch_t_off[c];
+  // energy and residual sums of the amplitudes whose spin flip is another amplitude (counted
+  // twice) and of those that are their own flip (counted once)
+  double e2 = 0.0, e1 = 0.0, r2 = 0.0, r1 = 0.0;
   if (ab < npp) {
-    int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
+    float hh[UPD_ROWS];
+#pragma unroll
+    for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0.0f;
+    if (!frozen) {
+      const float* __restrict__ tc = t32 + base + ab;
+#pragma unroll 4
+      for (int kl = 0; kl < nh; kl++) {
+        const float tk = tc[(long)kl * npp];
+        const float4 c0 = *reinterpret_cast<const float4*>(chs + kl * UPD_ROWS);
+        const float4 c1 = *reinterpret_cast<const float4*>(chs + kl * UPD_ROWS + 4);
+        hh[0] = fmaf(tk, c0.x, hh[0]); hh[1] = fmaf(tk, c0.y, hh[1]);
+        hh[2] = fmaf(tk, c0.z, hh[2]); hh[3] = fmaf(tk, c0.w, hh[3]);
+        hh[4] = fmaf(tk, c1.x, hh[4]); hh[5] = fmaf(tk, c1.y, hh[5]);
+        hh[6] = fmaf(tk, c1.z, hh[6]); hh[7] = fmaf(tk, c1.w, hh[7]);
+      }
+    }
+    const int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
     const float dab = D.dchi32[p.x] + D.dchi32[p.y];
     const double eab = D.eps[p.x] + D.eps[p.y];
+    const char4 sa = D.nvec[p.x], sb = D.nvec[p.y];
+    const double* __restrict__ lut = D.lut + lut_off[D.ch_sys[c]];
+    // the pp ladder's element in the ladder layout: s_off + ij * n_lad + |m| - 1, sign of m
+    long lad0 = 0;
+    int nl = 0;
+    bool lneg = false;
+    if (has_vpp) {
+      const int m = D.lad_map[D.ch_pp_off[c] + ab];
+      lneg = m < 0;
+      nl = D.ch_nlad[c];
+      lad0 = D.ch_s_off[c] + ((m > 0 ? m : -m) - 1);
+    }
 #pragma unroll
     for (int gb = 0; gb < UPD_ROWS; gb += UPD_BATCH) {
       if (gb >= ng) break;
       long z[UPD_BATCH];
-      double tz[UPD_BATCH], v[UPD_BATCH], idn[UPD_BATCH];
-      int4 q[UPD_BATCH];
+      double tz[UPD_BATCH], wz[UPD_BATCH];
       int fc[UPD_BATCH];
       float t32z[UPD_BATCH], part[UPD_BATCH], qs[UPD_BATCH];
+      int4 qm[UPD_BATCH];
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
-        int g = min(gb + j, ng - 1);
+        const int g = min(gb + j, ng - 1);
         z[j] = base + (long)row_ij[g] * npp + ab;
-        tz[j] = t[z[j]];
-        v[j] = D.v_pphh[z[j]];
-        q[j] = D.qmap[z[j]];
-        fc[j] = D.fmap[z[j]];
+        tz[j] = __ldcs(t + z[j]);
+        wz[j] = __ldcs(aw + z[j]);
+        fc[j] = __ldcs(D.fmap + z[j]);
         t32z[j] = t32[z[j]];
-        idn[j] = D.inv_den[z[j]];
-        part[j] = hh[z[j]];
+        qm[j] = __ldcs(D.qmap + z[j]);
+        float rl = 0.0f;
         if (has_vpp) {
-          int sg;
-          long zl = lad_index(D, c, row_ij[g], ab, sg);
-          float rl = 0.0f;
+          const long zl = lad0 + (long)row_ij[g] * nl;
           for (int pl = 0; pl < nplanes; pl++) rl += rpp[pl * pstride + zl];
-          part[j] += sg > 0 ? rl : -rl;
+          if (lneg) rl = -rl;
         }
+        part[j] = rl;
       }
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
         // P(ij)P(ab) Q: Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba from the cross-channel layout
-        float a0 = q[j].x >= 0 ? xq[q[j].x] : 0.0f, a1 = q[j].y >= 0 ? xq[q[j].y] : 0.0f;
-        float a2 = q[j].z >= 0 ? xq[q[j].z] : 0.0f, a3 = q[j].w >= 0 ? xq[q[j].w] : 0.0f;
+        const float a0 = qm[j].x >= 0 ? xq[qm[j].x] : 0.0f, a1 = qm[j].y >= 0 ? xq[qm[j].y] : 0.0f;
+        const float a2 = qm[j].z >= 0 ? xq[qm[j].z] : 0.0f, a3 = qm[j].w >= 0 ? xq[qm[j].w] : 0.0f;
         qs[j] = (a0 - a1) - (a2 - a3);
       }
 #pragma unroll
       for (int j = 0; j < UPD_BATCH; j++) {
-        int g = gb + j;
+        const int g = gb + j;
         if (g >= ng) break;
-        // one amplitude of each spin-flip pair is computed (the smaller index) and written to
-        // both; the pair counts twice in the energy and the residual norm
+        // one amplitude of each spin-flip pair is computed (the smaller index) and written to both
         const long f = (long)(fc[j] > 0 ? fc[j] : -fc[j]) - 1;
         if (f < z[j]) continue;
-        const double wgt = f == z[j] ? 1.0 : 2.0;
-        double out = tz[j];
+        const double v = v_minnesota_as(sa, sb, row_si[g], row_sj[g], lut);
+        double out = tz[j], R = 0.0;
         if (!frozen) {
-          float corr = (dab - row_dij[g]) * t32z[j] + part[j] + qs[j];
-          double num = v[j] + (double)corr;
-          double R = fma(eab - row_eij[g], tz[j], num);  // bracket - eps_ij^ab t
-          rsum = fma(wgt * R, R, rsum);
-          out = fma(alpha * R, idn[j], tz[j]);
+          const float corr = (dab - row_dij[g]) * t32z[j] + (part[j] + hh[g]) + qs[j];
+          R = fma(eab - row_eij[g], tz[j], v) + (double)corr;  // bracket - eps_ij^ab t
+          out = fma(R, wz[j], tz[j]);
         }
-        tn[z[j]] = out;
-        esum = fma(wgt * v[j], out, esum);
-        float o32 = (float)out;
+        const float o32 = (float)out;
+        __stcs(tn + z[j], out);
         t32n[z[j]] = o32;
         if (f != z[j]) {
-          tn[f] = fc[j] > 0 ? out : -out;
-          t32n[f] = fc[j] > 0 ? o32 : -o32;
+          const bool neg = fc[j] < 0;
+          __stcs(tn + f, neg ? -out : out);
+          t32n[f] = neg ? -o32 : o32;
+          e2 = fma(v, out, e2);
+          r2 = fma(R, R, r2);
+        } else {
+          e1 = fma(v, out, e1);
+          r1 = fma(R, R, r1);
         }
-        if (pk.xt) {
-          // the Q positions of P(ij)P(ab) are the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba
-          // (formed positions only, so the same for the amplitude and its spin flip)
-          if (q[j].x >= 0) pk.xt[q[j].x] = o32;
-          if (q[j].y >= 0) pk.xt[q[j].y] = -o32;
-          if (q[j].z >= 0) pk.xt[q[j].z] = -o32;
-          if (q[j].w >= 0) pk.xt[q[j].w] = o32;
+        if (!frozen) {
+          // the T positions of t_ij^ab, t_ji^ab, t_ij^ba, t_ji^ba (the Q positions of the same
+          // amplitude; stores only, nothing waits on them)
+          if (qm[j].x >= 0) xt[qm[j].x] = o32;
+          if (qm[j].y >= 0) xt[qm[j].y] = -o32;
+          if (qm[j].z >= 0) xt[qm[j].z] = -o32;
+          if (qm[j].w >= 0) xt[qm[j].w] = o32;
         }
       }
     }
   }
-  block_sum2(esum, rsum, sh32);
-  if (threadIdx.x == 0) {
-    D.eparts[blockIdx.x] = esum;
-    D.rparts[blockIdx.x] = rsum;
+  // block sums: per thread in FP64, then 128 values per sum added by one warp
+  red[0][threadIdx.x] = fma(2.0, e2, e1);
+  red[1][threadIdx.x] = fma(2.0, r2, r1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double es = (red[0][threadIdx.x] + red[0][threadIdx.x + 32]) + (red[0][threadIdx.x + 64] + red[0][threadIdx.x + 96]);
+    double rs = (red[1][threadIdx.x] + red[1][threadIdx.x + 32]) + (red[1][threadIdx.x + 64] + red[1][threadIdx.x + 96]);
+    es = warp_sum(es);
+    rs = warp_sum(rs);
+    if (threadIdx.x == 0) {
+      D.eparts[blockIdx.x] = es;
+      D.rparts[blockIdx.x] = rs;
+    }
   }
   last_block_finalize(fa, ctl);
 }
 
-size_t hh32_smem_bytes(const pnm_ctx* ctx) {
-  return sizeof(float) * ((size_t)ctx->max_nhh * ctx->max_nhh + (size_t)ctx->max_nhh * 128);
-}
-
-void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const float* xq, int use_cond,
-                       cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride) {
+void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* xq, const double* aw, float* xt, int use_cond,
+                       cudaGraphConditionalHandle h, int nplanes, long pstride) {
   k_update_mix<<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
-                                                         fin_args(ctx, use_cond, h, false), rpp, hh, xq, pk,
-                                                         nplanes, pstride);
+                                                         fin_args(ctx, use_cond, h, false), rpp, xq, aw, xt,
+                                                         ctx->lut_off_d, nplanes, pstride);
 }
 
-void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s) {
-  if (ctx->n_ab_items > 0)
-    k_hh32<<<ctx->n_ab_items, 128, hh32_smem_bytes(ctx), s>>>(ctx->d, ctx->ctl, ctx->ab_items, hh);
+// alpha / eps_ij^ab per amplitude (the step of the mixed update).
+__global__ void k_alpha_inv(const double* __restrict__ inv_den, double alpha, long n, double* __restrict__ aw) {
+  long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n) aw[z] = alpha * inv_den[z];
+}
+
+void pnm_alpha_inv(pnm_ctx* ctx, double alpha, double* aw) {
+  if (ctx->nt > 0)
+    k_alpha_inv<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d.inv_den, alpha, ctx->nt, aw);
+  CUDA_TRY(cudaGetLastError());
 }
 
 // Per row (channel, ij) of the amplitudes: 2 if the spin flip maps it onto a later row (it is
@@ -1347,13 +1403,13 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   if (ph_smem > 227 * 1024 || pp_smem > 227 * 1024)
     throw PnmError{PNM_EINVAL, "channel too large for the shared-memory tiles"};
   pnm_ph_attributes(ctx);
-  smem_at_least(k_hh32, hh32_smem_bytes(ctx));
   for (int k = 0; k < 2; k++) {
     CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
   }
   CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-  smem_at_least(k_pp64, pp_smem);
+  smem_at_least(k_pp<double>, pp_smem);
+  smem_at_least(k_pp<f2>, pp_smem);
   CUDA_TRY(cudaStreamSynchronize(s));
 }
 
@@ -1527,15 +1583,19 @@ void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, do
 
 // rep_only: only the rows the updates compute (one of each spin-flip pair of rows); the ladder
 // operator of pnm_apply_pp_ladder takes every row.
-void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only) {
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only, const f2* vpp_f2) {
   if (ctx->n_pp_items == 0) return;
   k_lad_gather<double><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->d.s64);
   DevState L = ctx->d;
   L.ch_npp = ctx->d.ch_nlad;
   L.ch_t_off = ctx->d.ch_s_off;
   L.t0 = L.t1 = ctx->d.s64;
-  k_pp64<<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items,
-                                                                          rep_only ? 1 : 0);
+  if (vpp_f2)
+    k_pp<f2><<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items,
+                                                                                rep_only ? 1 : 0, vpp_f2);
+  else
+    k_pp<double><<<ctx->n_pp_items, PP64_WARPS * 32, pp64_smem(ctx->max_nlad), s>>>(L, ctx->ctl, ctx->pp_items,
+                                                                                    rep_only ? 1 : 0, ctx->d.v_pppp);
 }
 
 // The ph term and the pp ladder do not depend on each other nor on the one-body sums: in a
@@ -1580,19 +1640,21 @@ void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed) {
 // One FP64 update.  terms (PNM_TERMS_*): the full Eq. (ccd3), or a truncation whose
 // intermediates were fixed by pnm_prepare_terms (one-body terms zero, chi_kl^ij = <kl|v|ij>
 // or zero, the ph term zero unless the linear ph term is launched here).
-static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, int terms) {
+// pair: the ph and pp contractions with FP32-pair arithmetic (full Eq. ccd3 only).
+static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, int terms, bool pair) {
   cudaStream_t s_ph = pnm_concurrent(ctx) ? ctx->side[0] : ctx->stream;
   cudaStream_t s_pp = pnm_concurrent(ctx) ? ctx->side[1] : ctx->stream;
   bool ph_on = terms == PNM_TERMS_FULL || terms == PNM_TERMS_LINEAR;
   pnm_fork(ctx);
   if (ctx->nx > 0 && ph_on) {
-    prof_begin(ctx, KID_PH64);
-    launch_ph64(ctx, s_ph, terms == PNM_TERMS_LINEAR);
+    prof_begin(ctx, pair ? KID_PH_F2 : KID_PH64);
+    if (pair) launch_ph_f2(ctx, ctx->xw_f2, ctx->xv1_f2, s_ph);
+    else launch_ph64(ctx, s_ph, terms == PNM_TERMS_LINEAR);
     prof_end(ctx);
   }
   if (ctx->n_pp_items > 0) {
-    prof_begin(ctx, KID_PP64);
-    pnm_launch_pp64(ctx, s_pp);
+    prof_begin(ctx, pair ? KID_PP_F2 : KID_PP64);
+    pnm_launch_pp64(ctx, s_pp, true, pair ? ctx->vpp_f2 : nullptr);
     prof_end(ctx);
   }
   if (terms == PNM_TERMS_FULL) pnm_enqueue_stats(ctx, false);
@@ -1604,7 +1666,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
 
 const char* const pnm_kernel_names[PNM_NKERNELS] = {
     "k_tstats", "k_dchi", "k_ph64", "k_pp64", "k_update", "k_finalize(unused)",
-    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack", "k_dchi32", "k_hh32"};
+    "k_pp_tc", "k_ph32", "k_tstats32", "k_update_mix", "k_pack", "k_dchi32", "k_ph_f2", "k_pp_f2"};
 
 void prof_begin(pnm_ctx* ctx, int kid) {
   if (!ctx->prof_live) return;
@@ -1635,12 +1697,28 @@ void prof_collect(pnm_ctx* ctx) {
   ctx->prof_pending.clear();
 }
 
-// mode = precision | (terms << 4); truncations (terms != 0) are FP64 only.
+// mode = precision | (terms << 4) | (pair << 8); truncations (terms != 0) are FP64 only; pair
+// selects the FP32-pair contractions for an FP64 update (the refinement sweeps).
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
-  int prec = mode & 15, terms = mode >> 4;
+  int prec = mode & 15, terms = (mode >> 4) & 15;
+  bool pair = ((mode >> 8) & 1) != 0;
   ctx->cur_mode = prec == PNM_PREC_FP64 ? 0 : 1;
-  if (prec == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h, terms);
+  if (prec == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h, terms, pair);
   else pnm_enqueue_body_mixed(ctx, use_cond, h);
+}
+
+// FP32-pair copies of the ladder-basis V_pppp, W and <kb|v|cj> (once per context).
+void pnm_prepare_f2(pnm_ctx* ctx) {
+  if (ctx->vpp_f2) return;
+  cudaStream_t s = ctx->stream;
+  ctx->vpp_f2 = ctx_alloc<f2>(ctx, ctx->nvpp);
+  ctx->xw_f2 = ctx_alloc<f2>(ctx, ctx->nxt);
+  ctx->xv1_f2 = ctx_alloc<f2>(ctx, ctx->nxc);
+  pnm_split_f2(ctx->d.v_pppp, ctx->vpp_f2, ctx->nvpp, s);
+  pnm_split_f2(ctx->d.x_w, ctx->xw_f2, ctx->nxt, s);
+  pnm_split_f2(ctx->d.x_v1, ctx->xv1_f2, ctx->nxc, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));
 }
 
 // Fixed intermediates of a truncated iteration: no one-body terms, chi_kl^ij = <kl|v|ij>
@@ -1661,7 +1739,8 @@ void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
 // the highest, so that the shorter branches (pp ladder, one-body sums) are dispatched ahead of
 // the many ph CTAs and run beside them instead of after them.
 static bool is_ph_kernel(const void* f) {
-  return f == (const void*)k_ph<double, PH_THREADS, 2, true> || f == (const void*)k_ph<float, PH_THREADS, 4, false>;
+  return f == (const void*)k_ph<double, PH_THREADS, 2> || f == (const void*)k_ph<float, PH_THREADS, 4> ||
+         f == (const void*)k_ph<f2, PH_THREADS, 2>;
 }
 
 static void set_node_priorities(cudaGraph_t body) {
@@ -1806,7 +1885,7 @@ void pnm_settle_amplitudes(pnm_ctx* ctx) {
 static std::mutex g_sched_mu;
 static std::map<std::string, bool> g_sched_cache;  // (shape key, mode) -> one stream
 
-void pnm_tune_schedule(pnm_ctx* ctx, int mode) {
+void pnm_tune_schedule(pnm_ctx* ctx, int mode, double alpha) {
   int m = mode == PNM_PREC_FP64 ? 0 : 1;
   if (ctx->sched_tuned[m]) return;
   const std::string key = pnm_shape_key(ctx) + (m ? "|mixed" : "|fp64");
@@ -1834,7 +1913,7 @@ void pnm_tune_schedule(pnm_ctx* ctx, int mode) {
     ctx->serial_sched[m] = serial != 0;
     CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, save, sizeof(double) * ctx->nt, cudaMemcpyDeviceToDevice, s));
     pnm_start(ctx, PNM_INIT_KEEP, never);
-    if (m == 1) pnm_mixed_pack_initial(ctx);
+    if (m == 1) pnm_mixed_pack_initial(ctx, alpha);
     pnm_enqueue_body(ctx, mode, 0, 0);
     CUDA_TRY(cudaEventRecord(e0, s));
     for (int k = 0; k < 4; k++) pnm_enqueue_body(ctx, mode, 0, 0);

@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
   if (warp == 0) {
     if (lane == 0) {
       // producer: per stage one tiled tensor copy of the V tile (hi, lo planes: 256 rows of 64
-      // BF16) and one bulk copy of the t tile
+      // BF16; each read once per launch, so marked first to evict from L2) and one bulk copy of
+      // the t tile
+      const uint64_t vpol = policy_evict_first();
       long g = 0;
       bool ok = true;
       for (int i = i_begin; i < i_end && ok; i++) {
@@ -188,8 +190,8 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
           }
           unsigned char* st = stage0 + s * stage_bytes;
           mbar_expect_tx(&full[s], 2 * A_PLANE + 2 * b_plane);
-          tma_load_2d(st, &tmap_v, 0, (int)((it.voff + (long)(it.kb0 + kb) * 2 * (TC_M * TC_BK)) / TC_BK),
-                      &full[s]);
+          tma_load_2d_hint(st, &tmap_v, 0, (int)((it.voff + (long)(it.kb0 + kb) * 2 * (TC_M * TC_BK)) / TC_BK),
+                           &full[s], vpol);
           bulk_g2s(st + 2 * A_PLANE, tb + (long)kb * 2 * (it.npad * TC_BK), 2 * b_plane, &full[s]);
           g++;
         }
@@ -284,14 +286,6 @@ __global__ void __launch_bounds__(PP_THREADS, 1) k_pp_tc(const __grid_constant__
   if (threadIdx.x == 0 && err) atomicExch(&ctl->dev_error, 1);
 }
 
-// FP32 copy of the current amplitudes.
-__global__ void k_to_float_cur(DevState D, const LoopCtl* __restrict__ ctl, long n) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float* dst = (ctl->iter & 1) ? D.t32_1 : D.t32_0;
-  dst[i] = (float)cur_t(D, ctl)[i];
-}
-
 // T[(a,i)][(k,c)] = t_ik^ac of the current amplitudes through the signed index map (the FP32
 // cross-channel copy the mixed ph term reads; later updates keep it current by scattering).
 __global__ void k_remap_t32(DevState D, const LoopCtl* __restrict__ ctl, float* __restrict__ xt, long n) {
@@ -301,6 +295,14 @@ __global__ void k_remap_t32(DevState D, const LoopCtl* __restrict__ ctl, float* 
   const float* t32 = cur_t32(D, ctl);
   float g = code == 0 ? 0.0f : t32[code > 0 ? code - 1 : -code - 1];
   xt[e] = code < 0 ? -g : g;
+}
+
+// FP32 copy of the current amplitudes.
+__global__ void k_to_float_cur(DevState D, const LoopCtl* __restrict__ ctl, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float* dst = (ctl->iter & 1) ? D.t32_1 : D.t32_0;
+  dst[i] = (float)cur_t(D, ctl)[i];
 }
 
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long n) {
@@ -318,9 +320,11 @@ T* mdalloc(pnm_ctx* ctx, size_t n) {
 struct MixedState {
   __nv_bfloat16* vt = nullptr;
   __nv_bfloat16* bt = nullptr;
-  float *rpp32 = nullptr, *xw32 = nullptr, *xv132 = nullptr, *xq32 = nullptr;
+  float *rpp32 = nullptr, *xw32 = nullptr, *xv132 = nullptr;
   float* xt32 = nullptr;  // T of the ph term, cross-channel layout, written by the update
-  float* hh32 = nullptr;  // hh ladder of the current amplitudes (FP32, t layout)
+  float* xq32 = nullptr;  // Q of the ph term, cross-channel layout, gathered by the update
+  double* aw = nullptr;   // alpha / eps_ij^ab per amplitude (the step of the mixed update)
+  double aw_alpha = -1.0;  // the alpha aw was made for
   TCItem* items = nullptr;
   int nitems = 0;
   int4* pk = nullptr;
@@ -506,11 +510,11 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemsetAsync(M->rpp32, 0, sizeof(float) * TC_MAX_SPLIT * std::max<long>(ctx->ns, 1), s));
     M->xw32 = mdalloc<float>(ctx, ctx->nxt);
     M->xv132 = mdalloc<float>(ctx, ctx->nxc);
-    M->xq32 = mdalloc<float>(ctx, ctx->nxt);
     M->xt32 = mdalloc<float>(ctx, ctx->nxt);
-    M->hh32 = mdalloc<float>(ctx, ctx->nt);
     // entries no amplitude maps to (repeated state index) stay zero
     CUDA_TRY(cudaMemsetAsync(M->xt32, 0, sizeof(float) * std::max<long>(ctx->nxt, 1), s));
+    M->xq32 = mdalloc<float>(ctx, ctx->nxt);
+    M->aw = mdalloc<double>(ctx, ctx->nt);
     if (ctx->nxt > 0)
       k_to_float<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, s>>>(ctx->d.x_w, M->xw32, ctx->nxt);
     if (ctx->nxc > 0)
@@ -626,23 +630,25 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
     prof_end(ctx);
   }
   pnm_enqueue_stats(ctx, true);
-  prof_begin(ctx, KID_HH32);
-  launch_hh32(ctx, M->hh32, ctx->stream);
-  prof_end(ctx);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE_MIX);
-  launch_update_mix(ctx, M->rpp32, M->hh32, M->xq32, use_cond, h, PackArgs{M->xt32}, M->ksplit, ctx->ns);
+  launch_update_mix(ctx, M->rpp32, M->xq32, M->aw, M->xt32, use_cond, h, M->ksplit, ctx->ns);
   prof_end(ctx);
 }
 
-// The FP32 copies of the start amplitudes (before the first mixed update); the t tiles of the
-// ladder are packed at the start of every mixed update.
-void pnm_mixed_pack_initial(pnm_ctx* ctx) {
+// Before the first mixed update of a solve: the FP32 copies of the start amplitudes (t32 and the
+// ph term's T; the t tiles of the ladder are packed at the start of every mixed update), and
+// alpha / eps_ij^ab if alpha changed.
+void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha) {
   MixedState* M = ctx->mixed;
   if (ctx->nt > 0)
     k_to_float_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
   if (ctx->nxt > 0)
     k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
+  if (alpha != M->aw_alpha) {
+    pnm_alpha_inv(ctx, alpha, M->aw);
+    M->aw_alpha = alpha;
+  }
   CUDA_TRY(cudaGetLastError());
 }
 
@@ -682,8 +688,10 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->ns, s);
     pnm_lad_expand(ctx, M->rpp32, M->ksplit, ctx->ns, out.data());
   } else {
+    if (precision == PNM_PREC_F32PAIR) pnm_prepare_f2(ctx);
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
-    pnm_launch_pp64(ctx, s, false);  // every row: the operator acts on any amplitudes
+    // every row: the operator acts on any amplitudes
+    pnm_launch_pp64(ctx, s, false, precision == PNM_PREC_F32PAIR ? ctx->vpp_f2 : nullptr);
     pnm_lad_expand(ctx, ctx->d.rpp, 1, ctx->ns, out.data());
   }
   int err = 0;
@@ -730,7 +738,12 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     if (ctx->nx > 0) launch_ph_mix(ctx, M->xt32, M->xw32, M->xv132, M->xq32, s);
     k_ph_assemble<float><<<nb, 256, 0, s>>>(ctx->d, M->xq32, ctx->nt, ctx->expand_buf);
   } else {
-    if (ctx->nx > 0) launch_ph64(ctx, s);
+    if (precision == PNM_PREC_F32PAIR) {
+      pnm_prepare_f2(ctx);
+      if (ctx->nx > 0) launch_ph_f2(ctx, ctx->xw_f2, ctx->xv1_f2, s);
+    } else if (ctx->nx > 0) {
+      launch_ph64(ctx, s);
+    }
     k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->expand_buf);
   }
   CUDA_TRY(cudaGetLastError());

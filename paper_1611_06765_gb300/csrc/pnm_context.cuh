@@ -11,7 +11,7 @@ struct MlpState;    // learned warm start (mlp.cu)
 // Kernel ids of the per-kernel profiler.
 enum {
   KID_TSTATS = 0, KID_DCHI, KID_PH64, KID_PP64, KID_UPDATE, KID_FINALIZE,
-  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, KID_DCHI32, KID_HH32, PNM_NKERNELS
+  KID_PP_TC, KID_PH32, KID_TSTATS32, KID_UPDATE_MIX, KID_PACK, KID_DCHI32, KID_PH_F2, KID_PP_F2, PNM_NKERNELS
 };
 extern const char* const pnm_kernel_names[PNM_NKERNELS];
 
@@ -75,6 +75,9 @@ struct pnm_ctx {
 
   MixedState* mixed = nullptr;
   MlpState* mlp = nullptr;
+  // FP32-pair copies of the ladder-basis V_pppp, W and <kb|v|cj> (made on first use by the
+  // FP32-pair contractions)
+  f2 *vpp_f2 = nullptr, *xw_f2 = nullptr, *xv1_f2 = nullptr;
   double hbar2_2m = 0.0;
   int mlp_fallback = 0;  // 1 when the last learned start was replaced by the MBPT2 start
 
@@ -153,9 +156,12 @@ void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
 void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
-void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only = true);
+void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only = true, const f2* vpp_f2 = nullptr);
+void launch_ph_f2(pnm_ctx* ctx, const f2* xw, const f2* xv1, cudaStream_t s);
+void pnm_split_f2(const double* a, f2* b, long n, cudaStream_t s);
+void pnm_prepare_f2(pnm_ctx* ctx);
 size_t ph_smem_bytes(int max_dim, int nm, size_t elem);
-void pnm_mixed_pack_initial(pnm_ctx* ctx);
+void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha);
 void pnm_fork(pnm_ctx* ctx);
 void pnm_join(pnm_ctx* ctx);
 void pnm_launch_mbpt2_into(const pnm_ctx* ctx, double* partials, double* results);
@@ -164,14 +170,12 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s);
 void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s);
-void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq,
-                   cudaStream_t s);
+void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq, cudaStream_t s);
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
-void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* hh, const float* xq, int use_cond,
-                       cudaGraphConditionalHandle h, PackArgs pk, int nplanes, long pstride);
-void launch_hh32(pnm_ctx* ctx, float* hh, cudaStream_t s);
-size_t hh32_smem_bytes(const pnm_ctx* ctx);
+void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* xq, const double* aw, float* xt, int use_cond,
+                       cudaGraphConditionalHandle h, int nplanes, long pstride);
+void pnm_alpha_inv(pnm_ctx* ctx, double alpha, double* aw);
 void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask);
 bool pnm_concurrent(const pnm_ctx* ctx);
-void pnm_tune_schedule(pnm_ctx* ctx, int mode);
+void pnm_tune_schedule(pnm_ctx* ctx, int mode, double alpha);
 void pnm_selftest_wait(pnm_ctx* ctx);

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/pnmcc.h"
+#include "fp2.cuh"
 
 #define PNM_PI 3.14159265358979323846
 
@@ -184,12 +185,6 @@ constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
 // Threads of a ph-term CTA (one cross channel each); channels of at most PH_WARP_DIM rows and
 // columns (of their halves for S_z = 0) take one warp each.
 constexpr int PH_THREADS = 128, PH_WARP_DIM = 16;
-
-// Where the mixed update writes the BF16 hi/lo copy of the new amplitudes (the B operand
-// tiles of the tensor-core pp ladder).  bt == nullptr: no copy.
-struct PackArgs {
-  float* xt;            // FP32 T of the ph term in the cross-channel layout (scattered), or null
-};
 
 // pp ladder of amplitude (ij, ab) of channel c from its ladder-layout value (planes summed by
 // the caller where there are several).

@@ -27,6 +27,8 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   if (o.terms < PNM_TERMS_FULL || o.terms > PNM_TERMS_LINEAR) throw PnmError{PNM_EINVAL, "unknown terms"};
   if (o.terms != PNM_TERMS_FULL && o.precision != PNM_PREC_FP64)
     throw PnmError{PNM_EINVAL, "truncated iterations run in FP64 only"};
+  if (o.refine_kernels != PNM_PREC_FP64 && o.refine_kernels != PNM_PREC_F32PAIR)
+    throw PnmError{PNM_EINVAL, "refine_kernels must be PNM_PREC_FP64 or PNM_PREC_F32PAIR"};
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
   // work skipping for converged systems is scoped to the solve loops
@@ -49,8 +51,10 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   }
   bool mixed = o.precision != PNM_PREC_FP64;
   if (mixed) pnm_prepare_mixed(ctx);
-  pnm_tune_schedule(ctx, PNM_PREC_FP64);
-  if (mixed) pnm_tune_schedule(ctx, PNM_PREC_BF16X3);
+  const bool pair_refine = mixed && o.refine_sweeps > 0 && o.refine_kernels == PNM_PREC_F32PAIR;
+  if (pair_refine) pnm_prepare_f2(ctx);
+  pnm_tune_schedule(ctx, PNM_PREC_FP64, o.mix_alpha);
+  if (mixed) pnm_tune_schedule(ctx, PNM_PREC_BF16X3, o.mix_alpha);
 
   cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
   CUDA_TRY(cudaEventRecord(e0, s));
@@ -60,7 +64,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     init = PNM_INIT_KEEP;
   }
   pnm_start(ctx, init, tol);
-  if (mixed) pnm_mixed_pack_initial(ctx);
+  if (mixed) pnm_mixed_pack_initial(ctx, o.mix_alpha);
   pnm_prepare_terms(ctx, o.terms);
   int it0 = 0;
   int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : (PNM_PREC_FP64 | (o.terms << 4)), o.max_iter, 0,
@@ -70,8 +74,8 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     // exactly refine_sweeps FP64 updates, then (if the FP64 test has not passed by then)
     // further FP64 updates until it does, within max_iter more
     pnm_reopen(ctx);
-    status = pnm_run_loop(ctx, PNM_PREC_FP64, it0 + o.refine_sweeps + o.max_iter, it0 + o.refine_sweeps,
-                          o.host_loop, o.mix_alpha);
+    status = pnm_run_loop(ctx, PNM_PREC_FP64 | (pair_refine ? 1 << 8 : 0), it0 + o.refine_sweeps + o.max_iter,
+                          it0 + o.refine_sweeps, o.host_loop, o.mix_alpha);
   }
   CUDA_TRY(cudaEventRecord(e2, s));
   CUDA_TRY(cudaStreamSynchronize(s));

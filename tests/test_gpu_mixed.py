@@ -41,6 +41,7 @@ def test_pp_ladder_operator(pkg, N, rho, n2):
     n = len(g.amplitude_labels())
     t = random_amplitudes(n, seed=7)
     r64 = g.apply_pp_ladder(t, precision=pkg.PNM_PREC_FP64)
+    rf2 = g.apply_pp_ladder(t, precision=pkg.PNM_PREC_F32PAIR)
     r16 = g.apply_pp_ladder(t, precision=pkg.PNM_PREC_BF16X3)
     ref = np.zeros(n)
     bound = np.zeros(n)
@@ -52,6 +53,10 @@ def test_pp_ladder_operator(pkg, N, rho, n2):
     scale = np.max(np.abs(ref))
     assert scale > 0
     assert np.max(np.abs(r64 - ref)) <= 1e-12 * scale
+    # FP32 pairs: 48 significant bits, exact products, two-sum accumulation
+    print("FP32-pair pp ladder: max |error| / max |ref| = %.3g" % (np.max(np.abs(rf2 - ref)) / scale))
+    assert np.max(np.abs(rf2 - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(rf2 - r64)) <= 1e-12 * scale
     assert np.all(np.abs(r16 - ref) <= 5e-5 * bound + 1e-30)
     g.close()
 
@@ -97,10 +102,14 @@ def test_ph_term_operator(pkg, N, rho, n2):
     ref = o.ph_apply(ts)
     bound = o.ph_apply(ts, absval=True)
     r64 = g.apply_ph_term(t, precision=pkg.PNM_PREC_FP64)
+    rf2 = g.apply_ph_term(t, precision=pkg.PNM_PREC_F32PAIR)
     r16 = g.apply_ph_term(t, precision=pkg.PNM_PREC_BF16X3)
     scale = np.max(np.abs(ref))
     assert scale > 0
     assert np.max(np.abs(r64 - ref)) <= 1e-12 * scale
+    print("FP32-pair ph term: max |error| / max |ref| = %.3g" % (np.max(np.abs(rf2 - ref)) / scale))
+    assert np.max(np.abs(rf2 - ref)) <= 1e-12 * scale
+    assert np.max(np.abs(rf2 - r64)) <= 1e-12 * scale
     ratio = np.abs(r16 - ref) / (bound + 1e-300)
     print("mixed ph: max error / element bound = %.3g" % np.max(ratio))
     assert np.all(np.abs(r16 - ref) <= 2e-5 * bound + 1e-30)
@@ -129,4 +138,26 @@ def test_keep_start_is_symmetrised(pkg):
     dE, _, _, _ = g.solve(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-8,
                           max_iter=600, init=pkg.PNM_INIT_KEEP, refine_sweeps=2)
     assert abs(dE[0] - dE_o) / N < 1e-6, (dE[0], dE_o)
+    g.close()
+
+
+@pytest.mark.parametrize("N,rho,n2", [(14, 0.08, 20), (66, [0.05, 0.11, 0.17], 36)])
+def test_pair_refinement_matches_fp64_refinement(pkg, N, rho, n2):
+    """The refinement sweeps with FP32-pair contractions (PNM_PREC_F32PAIR) end where the
+    sweeps with FP64-pipe contractions end: the same number of updates and energies within
+    1e-11 relative (the contractions agree to about 1e-13 of their largest element, the update,
+    denominators, residual and energy are FP64 in both), and within 1e-6 MeV per neutron of the
+    oracle's fixed point."""
+    P = minnesota_params()
+    g = pkg.Context(N, rho, n2, params=P)
+    kw = dict(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-6, max_iter=300, refine_sweeps=2)
+    dE64, it64, _, _ = g.solve(refine_kernels=pkg.PNM_PREC_FP64, **kw)
+    dEf2, itf2, _, _ = g.solve(refine_kernels=pkg.PNM_PREC_F32PAIR, **kw)
+    assert np.array_equal(it64, itf2), (it64, itf2)
+    assert np.all(np.abs(dEf2 - dE64) <= 1e-11 * np.abs(dE64)), (dEf2, dE64)
+    rhos = np.atleast_1d(rho)
+    for k, r in enumerate(rhos):
+        o = channel.OracleSystem(N, r, n2, P)
+        dE_o, _, _, _ = o.ccd(alpha=0.5, tol=1e-10 * N, maxit=400)
+        assert abs(dEf2[k] - dE_o) / N < 1e-6
     g.close()

@@ -164,3 +164,48 @@ def test_ph_term_matches_dense(cfg0):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
     bound = S.ph_apply(t, absval=True)
     assert np.all(bound >= np.abs(got) - 1e-15)
+
+
+def _scan():
+    """Rows (n2max, hbar2_2m, rho, states, E_MBPT2/N, E_CCD/N) of the oracle scan of the readings
+    of Table tab:ecomparison (tests/golden/ecomparison_scan.py wrote them from the oracle)."""
+    return [(int(a), float(b), float(c), int(d), float(e), float(f))
+            for a, b, c, d, e, f, _ in read_golden("ecomparison_scan.txt")]
+
+
+def test_no_scanned_reading_gives_the_printed_rho008_ccd_entry():
+    """Table tab:ecomparison prints E_CCD/N = 9.136 at rho = 0.08 beside E_MBPT2/N = 9.075.
+    Among the spherical bases n^2 <= 36 ... 46 and hbar^2/2m in {20.721, 20.7355}, exactly one
+    reading reproduces the other five entries of the three rows to one unit of the printed
+    third decimal (n^2 <= 42, 2378 states, 20.721), and none gives 9.136 together with MBPT2
+    9.075: the CCD - MBPT2 gap at rho = 0.08 stays between 0.025 and 0.035 MeV for every reading
+    (printed: 0.061), so the printed CCD entry is taken as a misprint."""
+    printed = {(float(r), "mbpt2"): float(m) for r, m, _ in read_golden("ecomparison.txt")}
+    printed.update({(float(r), "ccd"): float(c) for r, _, c in read_golden("ecomparison.txt")})
+    rows = _scan()
+    readings = sorted({(n2, h) for n2, h, *_ in rows})
+    full_match = []
+    for n2, h in readings:
+        got = {(rho, kind): val for n, hh, rho, _, m, c in rows if (n, hh) == (n2, h)
+               for kind, val in (("mbpt2", m), ("ccd", c))}
+        ok = {k: abs(got[k] - v) <= 1.0e-3 for k, v in printed.items()}
+        if all(v for k, v in ok.items() if k != (0.08, "ccd")):
+            full_match.append((n2, h))
+        assert not (ok[(0.08, "ccd")] and ok[(0.08, "mbpt2")]), (n2, h)
+        gap = got[(0.08, "ccd")] - got[(0.08, "mbpt2")]
+        assert 0.025 < gap < 0.035, (n2, h, gap)
+    assert full_match == [(42, 20.721)]
+    assert abs(printed[(0.08, "ccd")] - printed[(0.08, "mbpt2")] - 0.061) < 1e-9
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("rho", [0.04, 0.06, 0.08])
+def test_ecomparison_scan_rows_reproduce(rho):
+    """The stored scan rows of the reading kept (n^2 <= 42, hbar^2/2m = 20.721) are the oracle's."""
+    row = [r for r in _scan() if r[0] == 42 and r[1] == 20.721 and r[2] == rho][0]
+    P = minnesota_params()
+    S = channel.OracleSystem(66, rho, 42, P)
+    er = S.eref()
+    assert abs((er + S.mbpt2()) / 66 - row[4]) < 2e-6
+    dE, _, _, _ = S.ccd(alpha=0.5, tol=1e-10 * 66, maxit=400)
+    assert abs((er + dE) / 66 - row[5]) < 2e-6
