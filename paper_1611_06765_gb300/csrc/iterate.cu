@@ -146,16 +146,17 @@ struct VecT<f2, 2> {
 };
 
 // Element e of a cross channel's T: read from the FP32 copy in the cross-channel layout that
-// the mixed update scatters (xt), or gathered from the current FP64 amplitudes through the
-// signed index map (FP64 and FP32-pair kernels, xt == nullptr).
+// the mixed update scatters (xt), or gathered through the signed index map from the current
+// amplitudes (tcur): FP64, or their FP32-pair copy for the FP32-pair kernels.
 template <typename T_>
-__device__ __forceinline__ T_ ph_t(const DevState& D, const double* __restrict__ tcur,
+__device__ __forceinline__ T_ ph_t(const DevState& D, const T_* __restrict__ tcur,
                                    const T_* __restrict__ xt, long e) {
   using A = Arith<T_>;
   if (xt) return xt[e];
   int cd = D.xmap[e];
-  double g = cd == 0 ? 0.0 : tcur[cd > 0 ? cd - 1 : -cd - 1];
-  return A::from_double(cd < 0 ? -g : g);
+  if (cd == 0) return A::zero();
+  T_ g = tcur[cd > 0 ? cd - 1 : -cd - 1];
+  return cd < 0 ? A::neg(g) : g;
 }
 
 // Bytes reserved for the index tables at the start of a k_ph CTA's shared memory (R4 + 2 H4
@@ -171,8 +172,8 @@ __host__ __device__ __forceinline__ size_t ph_index_bytes(int R4, int H4) { retu
 // Each thread accumulates TS x TS outputs of every problem per tile.  Element arithmetic is
 // that of Arith<T_> (FP64, FP32, or FP32 pairs with FP64 results).
 template <typename T_, int NT, int TS, int NM>
-__device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __restrict__ ctl, int x,
-                                         unsigned char* smraw, const T_* __restrict__ xt,
+__device__ __forceinline__ void ph_block(const DevState& D, int x, unsigned char* smraw,
+                                         const T_* __restrict__ tcur, const T_* __restrict__ xt,
                                          const T_* __restrict__ xw, const T_* __restrict__ xv1,
                                          typename Arith<T_>::Out* __restrict__ xq) {
   using A = Arith<T_>;
@@ -202,11 +203,12 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
     }
     __syncthreads();
   }
-  const double* tcur = xt ? nullptr : cur_t(D, ctl);
   const bool quad = xw != nullptr;
+  // element e = u H4 + s of the staging loops: (u, s) advanced by NT per step without a division
+  const int du = NT / H4, ds = NT % H4;
+  int u = threadIdx.x / H4, s = threadIdx.x % H4;
 #pragma unroll 4
   for (int e = threadIdx.x; e < RH; e += NT) {
-    int u = e / H4, s = e % H4;
     T_ t0 = A::zero(), t1 = A::zero(), w0 = A::zero(), w1 = A::zero();
     if (u < R && s < H) {
       if constexpr (NM == 1) {
@@ -232,10 +234,16 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
       Ts[RH + e] = t1;
       Xt[RH + e] = w1;
     }
+    u += du;
+    s += ds;
+    if (s >= H4) {
+      s -= H4;
+      u++;
+    }
   }
+  int r = threadIdx.x / H4, c = threadIdx.x % H4;
 #pragma unroll 4
   for (int e = threadIdx.x; e < HH; e += NT) {
-    int r = e / H4, c = e % H4;
     T_ v0 = A::zero(), v1 = A::zero();
     if (r < H && c < H) {
       if constexpr (NM == 1) {
@@ -249,6 +257,12 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
     }
     Cs[e] = v0;
     if constexpr (NM == 2) Cs[HH + e] = v1;
+    r += du;
+    c += ds;
+    if (c >= H4) {
+      c -= H4;
+      r++;
+    }
   }
   __syncthreads();
   const int th = H4 / TS;
@@ -342,8 +356,8 @@ __device__ __forceinline__ void ph_block(const DevState& D, const LoopCtl* __res
 // synchronisation; the same two bodies as the CTA path, one output element per lane and step.
 constexpr int PH_WARPS = PH_THREADS / 32;
 template <typename T_>
-__device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* __restrict__ ctl, int x, int w,
-                                             int lane, unsigned char* smraw, const T_* __restrict__ xt,
+__device__ __forceinline__ void ph_warp_body(const DevState& D, int x, int w, int lane, unsigned char* smraw,
+                                             const T_* __restrict__ tcur, const T_* __restrict__ xt,
                                              const T_* __restrict__ xw, const T_* __restrict__ xv1,
                                              typename Arith<T_>::Out* __restrict__ xq) {
   using A = Arith<T_>;
@@ -371,7 +385,6 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
     }
   }
   __syncwarp();
-  const double* tcur = xt ? nullptr : cur_t(D, ctl);
   const bool quad = xw != nullptr;
   for (int e = lane; e < R * H; e += 32) {
     int u = e / H, c = e % H;
@@ -422,23 +435,34 @@ __device__ __forceinline__ void ph_warp_body(const DevState& D, const LoopCtl* _
   }
 }
 
-// The ph term in one launch over the S_z >= 0 cross channels (xlist): the first nblk CTAs take
-// one channel each (the costliest first), with the S_z > 0 or the S_z = 0 body chosen per
-// channel; the remaining CTAs take PH_WARPS small channels each, one per warp.
+// The current amplitudes the ph kernels gather T from (not used when T is read from the
+// scattered FP32 copy): FP64, or the FP32-pair copy made at the start of the sweep.
+template <typename T_>
+__device__ __forceinline__ const T_* ph_tcur(const DevState& D, const LoopCtl* ctl, const T_* tpair) {
+  if constexpr (std::is_same<T_, double>::value) return cur_t(D, ctl);
+  else return tpair;
+}
+
+// The ph term over the S_z >= 0 cross channels (xlist): the first nblk CTAs take one channel
+// each (the costliest first), with the S_z > 0 or the S_z = 0 body chosen per channel; the
+// remaining CTAs take PH_WARPS small channels each, one per warp.  Channels are launched in two
+// size classes with their own shared memory (the larger ones by k_ph_big).
 template <typename T_, int NT, int TS>
 __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict__ ctl,
                                            const int* __restrict__ xlist, int nblk, int nwarp,
-                                           const T_* __restrict__ xt, const T_* __restrict__ xw,
-                                           const T_* __restrict__ xv1, typename Arith<T_>::Out* __restrict__ xq) {
+                                           const T_* __restrict__ tpair, const T_* __restrict__ xt,
+                                           const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                           typename Arith<T_>::Out* __restrict__ xq) {
   static_assert(NT == PH_WARPS * 32, "one warp per small channel");
   extern __shared__ __align__(16) unsigned char smraw[];
+  const T_* tcur = xt ? nullptr : ph_tcur<T_>(D, ctl, tpair);
   if ((int)blockIdx.x < nblk) {
     const int x = xlist[blockIdx.x];
     if (sys_done(D, ctl, D.x_sys[x])) return;  // CTA-uniform
     if (D.x_cls[x] == 0)
-      ph_block<T_, NT, TS, 2>(D, ctl, x, smraw, xt, xw, xv1, xq);
+      ph_block<T_, NT, TS, 2>(D, x, smraw, tcur, xt, xw, xv1, xq);
     else
-      ph_block<T_, NT, TS, 1>(D, ctl, x, smraw, xt, xw, xv1, xq);
+      ph_block<T_, NT, TS, 1>(D, x, smraw, tcur, xt, xw, xv1, xq);
     return;
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -446,7 +470,25 @@ __global__ void __launch_bounds__(NT) k_ph(DevState D, const LoopCtl* __restrict
   if (idx >= nwarp) return;  // whole warps leave; the warp path never synchronises the block
   const int x = xlist[nblk + idx];
   if (sys_done(D, ctl, D.x_sys[x])) return;  // warp-uniform
-  ph_warp_body<T_>(D, ctl, x, w, lane, smraw, xt, xw, xv1, xq);
+  ph_warp_body<T_>(D, x, w, lane, smraw, tcur, xt, xw, xv1, xq);
+}
+
+// The channels of the larger size class: one CTA of PH_BIG_THREADS per channel.
+constexpr int PH_BIG_THREADS = 256;
+template <typename T_, int TS>
+__global__ void __launch_bounds__(PH_BIG_THREADS) k_ph_big(DevState D, const LoopCtl* __restrict__ ctl,
+                                                           const int* __restrict__ xlist,
+                                                           const T_* __restrict__ tpair, const T_* __restrict__ xt,
+                                                           const T_* __restrict__ xw, const T_* __restrict__ xv1,
+                                                           typename Arith<T_>::Out* __restrict__ xq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int x = xlist[blockIdx.x];
+  if (sys_done(D, ctl, D.x_sys[x])) return;  // CTA-uniform
+  const T_* tcur = xt ? nullptr : ph_tcur<T_>(D, ctl, tpair);
+  if (D.x_cls[x] == 0)
+    ph_block<T_, PH_BIG_THREADS, TS, 2>(D, x, smraw, tcur, xt, xw, xv1, xq);
+  else
+    ph_block<T_, PH_BIG_THREADS, TS, 1>(D, x, smraw, tcur, xt, xw, xv1, xq);
 }
 
 static size_t ph_warp_smem(size_t elem) {
@@ -460,10 +502,16 @@ size_t ph_smem_bytes(int max_dim, int nm, size_t elem) {
   return ph_index_bytes(m4, m4) + elem * 3 * (size_t)nm * m4 * m4;
 }
 
+// Shared memory of the two launches: the larger size class alone, the smaller class and the
+// warp path.
 template <typename T_>
 static size_t ph_smem_of(const pnm_ctx* ctx) {
-  size_t b = sizeof(T_) == 8 ? ctx->ph_smem64 : ctx->ph_smem32;
+  size_t b = sizeof(T_) == 8 ? ctx->ph_smem64 : std::max(ctx->ph_smem32, ctx->ph_big_smem32);
   return ctx->n_ph_warp > 0 ? std::max(b, ph_warp_smem(sizeof(T_))) : b;
+}
+template <typename T_>
+static size_t ph_big_smem_of(const pnm_ctx* ctx) {
+  return sizeof(T_) == 8 ? ctx->ph_big_smem64 : ctx->ph_big_smem32;
 }
 
 // Register tile of the ph kernels: 2 x 2 for FP64 (little padding; the FP64 pipe bounds the
@@ -472,36 +520,47 @@ template <typename T_>
 constexpr int ph_tile() { return std::is_same<T_, float>::value ? 4 : 2; }
 
 // The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).
+// The 8-byte element types (FP64, FP32 pairs) are limited by shared memory: the larger channels
+// go to k_ph_big with their own allocation so that the others fit more CTAs per SM.  FP32 is
+// limited by registers: one launch, the larger channels first.
 template <typename T_>
-static void launch_ph_list(pnm_ctx* ctx, const T_* xt, const T_* xw, const T_* xv1, typename Arith<T_>::Out* xq,
-                           cudaStream_t s) {
+static void launch_ph_list(pnm_ctx* ctx, const T_* tpair, const T_* xt, const T_* xw, const T_* xv1,
+                           typename Arith<T_>::Out* xq, cudaStream_t s) {
   constexpr int TS = ph_tile<T_>();
-  int grid = ctx->n_ph + (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
+  constexpr bool split = sizeof(T_) == 8;
+  if (split && ctx->n_ph_big > 0)
+    k_ph_big<T_, TS><<<ctx->n_ph_big, PH_BIG_THREADS, ph_big_smem_of<T_>(ctx), s>>>(
+        ctx->d, ctx->ctl, ctx->ph_list, tpair, xt, xw, xv1, xq);
+  const int nblk = split ? ctx->n_ph : ctx->n_ph_big + ctx->n_ph;
+  const int* list = split ? ctx->ph_list + ctx->n_ph_big : ctx->ph_list;
+  int grid = nblk + (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
   if (grid > 0)
     k_ph<T_, PH_THREADS, TS><<<grid, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
-        ctx->d, ctx->ctl, ctx->ph_list, ctx->n_ph, ctx->n_ph_warp, xt, xw, xv1, xq);
+        ctx->d, ctx->ctl, list, nblk, ctx->n_ph_warp, tpair, xt, xw, xv1, xq);
 }
 
 template <typename T_>
 static void ph_attributes(const pnm_ctx* ctx) {
   smem_at_least(k_ph<T_, PH_THREADS, ph_tile<T_>()>, ph_smem_of<T_>(ctx));
+  smem_at_least(k_ph_big<T_, ph_tile<T_>()>, ph_big_smem_of<T_>(ctx));
 }
 
 // FP64 ph: T gathered from the current FP64 amplitudes (linear: without the quadratic part).
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear) {
-  launch_ph_list<double>(ctx, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
+  launch_ph_list<double>(ctx, nullptr, nullptr, linear ? nullptr : ctx->d.x_w, ctx->d.x_v1, ctx->d.xq, s);
 }
 
-// The same term with FP32-pair arithmetic (FP64 input amplitudes, W and <kb|v|cj> split into
-// FP32 pairs once per context, FP64 Q): the contractions of the refinement sweeps.
-void launch_ph_f2(pnm_ctx* ctx, const f2* xw, const f2* xv1, cudaStream_t s) {
-  launch_ph_list<f2>(ctx, nullptr, xw, xv1, ctx->d.xq, s);
+// The same term with FP32-pair arithmetic (T gathered from the FP32-pair copy of the current
+// amplitudes, W and <kb|v|cj> split into FP32 pairs once per context, FP64 Q): the
+// contractions of the refinement sweeps.
+void launch_ph_f2(pnm_ctx* ctx, const f2* tpair, const f2* xw, const f2* xv1, cudaStream_t s) {
+  launch_ph_list<f2>(ctx, tpair, nullptr, xw, xv1, ctx->d.xq, s);
 }
 
 // Mixed ph: T read from the FP32 cross-channel copy the update scatters, Q in FP32 at its
 // cross-channel positions (the update gathers the four terms of each amplitude).
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq, cudaStream_t s) {
-  launch_ph_list<float>(ctx, xt, xw, xv1, xq, s);
+  launch_ph_list<float>(ctx, nullptr, xt, xw, xv1, xq, s);
 }
 
 void pnm_ph_attributes(const pnm_ctx* ctx) {
@@ -512,29 +571,43 @@ void pnm_ph_attributes(const pnm_ctx* ctx) {
 
 // ------------------------------------------------------------------------ ladder basis
 // s(ij, q) = sum over the (one or two) pairs of vector q of sign * t(ij, pair), from the current
-// amplitudes (FP64) or their FP32 copy; one CTA per (channel, ij) row of a channel with V_pppp.
+// amplitudes (FP64, tsrc == nullptr) or their FP32-pair copy (tsrc); one CTA per (channel, ij)
+// row of a channel with V_pppp.
 template <typename T_>
 __global__ void __launch_bounds__(128) k_lad_gather(DevState D, const LoopCtl* __restrict__ ctl,
-                                                    const int2* __restrict__ rows, T_* __restrict__ out) {
+                                                    const int2* __restrict__ rows, const T_* __restrict__ tsrc,
+                                                    T_* __restrict__ out) {
+  using A = Arith<T_>;
   int2 it = rows[blockIdx.x];
   int c = it.x, ij = it.y;
   if (sys_done(D, ctl, D.ch_sys[c])) return;
   const T_* __restrict__ t;
   if constexpr (std::is_same<T_, double>::value) t = cur_t(D, ctl);
-  else t = cur_t32(D, ctl);
+  else t = tsrc;
   int npp = D.ch_npp[c], nl = D.ch_nlad[c], off = D.ch_pp_off[c];
   const T_* tr = t + D.ch_t_off[c] + (long)ij * npp;
   T_* o = out + D.ch_s_off[c] + (long)ij * nl;
   for (int q = threadIdx.x; q < nl; q += blockDim.x) {
     int2 m = D.lad_mem[off + q];
     T_ a = tr[(m.x > 0 ? m.x : -m.x) - 1];
-    T_ v = m.x > 0 ? a : -a;
+    T_ v = m.x > 0 ? a : A::neg(a);
     if (m.y != 0) {
       T_ b = tr[(m.y > 0 ? m.y : -m.y) - 1];
-      v += m.y > 0 ? b : -b;
+      v = A::add(v, m.y > 0 ? b : A::neg(b));
     }
     o[q] = v;
   }
+}
+
+// FP32-pair copy of the current amplitudes (the start of a sweep with FP32-pair contractions).
+__global__ void k_split_cur(DevState D, const LoopCtl* __restrict__ ctl, f2* __restrict__ tp, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tp[i] = Arith<f2>::from_double(cur_t(D, ctl)[i]);
+}
+
+void pnm_split_cur(pnm_ctx* ctx, cudaStream_t s) {
+  if (ctx->nt > 0)
+    k_split_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d, ctx->ctl, ctx->t_pair, ctx->nt);
 }
 
 // The pp ladder in the amplitude layout, from its ladder-layout value (planes summed): zero in
@@ -586,7 +659,8 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp(DevState D, const LoopCt
   const int* __restrict__ rows = rep_only ? D.upd_row + D.ch_uoff[c] : nullptr;
   int npp = D.ch_npp[c], nh = rep_only ? D.ch_uoff[c + 1] - D.ch_uoff[c] : D.ch_nhh[c];
   long tb = D.ch_t_off[c];
-  const double* __restrict__ t = cur_t(D, ctl);
+  // the ladder-basis amplitudes (FP64, or FP32 pairs in the same 8-byte slots)
+  const T_* __restrict__ t = reinterpret_cast<const T_*>(cur_t(D, ctl));
   T_* ts = reinterpret_cast<T_*>(smpp);
   T_* red = ts + PP64_ROWS * npp;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -600,7 +674,7 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp(DevState D, const LoopCt
     __syncthreads();
     for (int e = threadIdx.x; e < nr * npp; e += blockDim.x) {
       int g = g0 + e / npp;
-      ts[e] = A::from_double(t[tb + (long)(rows ? rows[g] : g) * npp + e % npp]);
+      ts[e] = t[tb + (long)(rows ? rows[g] : g) * npp + e % npp];
     }
     __syncthreads();
     T_ acc[PP64_ROWS];
@@ -1367,7 +1441,9 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->d.sysctl = ctx->sysctl;
   // cross channels of the ph launch: S_z >= 0 (S_z < 0 ones are read at their flips), costliest first;
   // shared memory for the largest (NM = 1: rows/columns; NM = 2: those of the halves, twice)
-  std::vector<int> xl, xw;  // CTA per channel; warp per channel (at most PH_WARP_DIM)
+  // CTA per channel in two size classes (larger than PH_SMALL_DIM: k_ph_big), warp per channel
+  // (at most PH_WARP_DIM)
+  std::vector<int> xb, xl, xw;
   std::vector<long> xcost(ctx->nx, 0);
   for (int x = 0; x < ctx->nx; x++) {
     int c = ctx->h_x_cls[x];
@@ -1385,17 +1461,26 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
       continue;
     }
     int nm = c == 0 ? 2 : 1;
-    ctx->ph_smem64 = std::max(ctx->ph_smem64, ph_smem_bytes(d, nm, sizeof(double)));
-    ctx->ph_smem32 = std::max(ctx->ph_smem32, ph_smem_bytes(d, nm, sizeof(float)));
-    xl.push_back(x);
+    if (d > PH_SMALL_DIM) {
+      ctx->ph_big_smem64 = std::max(ctx->ph_big_smem64, ph_smem_bytes(d, nm, sizeof(double)));
+      ctx->ph_big_smem32 = std::max(ctx->ph_big_smem32, ph_smem_bytes(d, nm, sizeof(float)));
+      xb.push_back(x);
+    } else {
+      ctx->ph_smem64 = std::max(ctx->ph_smem64, ph_smem_bytes(d, nm, sizeof(double)));
+      ctx->ph_smem32 = std::max(ctx->ph_smem32, ph_smem_bytes(d, nm, sizeof(float)));
+      xl.push_back(x);
+    }
   }
   auto costlier = [&](int a, int b) { return xcost[a] != xcost[b] ? xcost[a] > xcost[b] : a < b; };
+  std::sort(xb.begin(), xb.end(), costlier);
   std::sort(xl.begin(), xl.end(), costlier);
   std::sort(xw.begin(), xw.end(), costlier);
+  ctx->n_ph_big = (int)xb.size();
   ctx->n_ph = (int)xl.size();
   ctx->n_ph_warp = (int)xw.size();
   xl.insert(xl.end(), xw.begin(), xw.end());
-  size_t ph_smem = ctx->ph_smem64;
+  xl.insert(xl.begin(), xb.begin(), xb.end());
+  size_t ph_smem = std::max(ctx->ph_smem64, ctx->ph_big_smem64);
   ctx->ph_list = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, xl.size()));
   if (!xl.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->ph_list, xl.data(), sizeof(int) * xl.size(), cudaMemcpyHostToDevice, s));
@@ -1585,7 +1670,11 @@ void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, do
 // operator of pnm_apply_pp_ladder takes every row.
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only, const f2* vpp_f2) {
   if (ctx->n_pp_items == 0) return;
-  k_lad_gather<double><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->d.s64);
+  if (vpp_f2)
+    k_lad_gather<f2><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->t_pair,
+                                                      reinterpret_cast<f2*>(ctx->d.s64));
+  else
+    k_lad_gather<double><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, nullptr, ctx->d.s64);
   DevState L = ctx->d;
   L.ch_npp = ctx->d.ch_nlad;
   L.ch_t_off = ctx->d.ch_s_off;
@@ -1645,10 +1734,11 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
   cudaStream_t s_ph = pnm_concurrent(ctx) ? ctx->side[0] : ctx->stream;
   cudaStream_t s_pp = pnm_concurrent(ctx) ? ctx->side[1] : ctx->stream;
   bool ph_on = terms == PNM_TERMS_FULL || terms == PNM_TERMS_LINEAR;
+  if (pair) pnm_split_cur(ctx, ctx->stream);  // before the fork: both branches read it
   pnm_fork(ctx);
   if (ctx->nx > 0 && ph_on) {
     prof_begin(ctx, pair ? KID_PH_F2 : KID_PH64);
-    if (pair) launch_ph_f2(ctx, ctx->xw_f2, ctx->xv1_f2, s_ph);
+    if (pair) launch_ph_f2(ctx, ctx->t_pair, ctx->xw_f2, ctx->xv1_f2, s_ph);
     else launch_ph64(ctx, s_ph, terms == PNM_TERMS_LINEAR);
     prof_end(ctx);
   }
@@ -1712,6 +1802,7 @@ void pnm_prepare_f2(pnm_ctx* ctx) {
   if (ctx->vpp_f2) return;
   cudaStream_t s = ctx->stream;
   ctx->vpp_f2 = ctx_alloc<f2>(ctx, ctx->nvpp);
+  ctx->t_pair = ctx_alloc<f2>(ctx, ctx->nt);
   ctx->xw_f2 = ctx_alloc<f2>(ctx, ctx->nxt);
   ctx->xv1_f2 = ctx_alloc<f2>(ctx, ctx->nxc);
   pnm_split_f2(ctx->d.v_pppp, ctx->vpp_f2, ctx->nvpp, s);
@@ -1740,7 +1831,8 @@ void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
 // the many ph CTAs and run beside them instead of after them.
 static bool is_ph_kernel(const void* f) {
   return f == (const void*)k_ph<double, PH_THREADS, 2> || f == (const void*)k_ph<float, PH_THREADS, 4> ||
-         f == (const void*)k_ph<f2, PH_THREADS, 2>;
+         f == (const void*)k_ph<f2, PH_THREADS, 2> || f == (const void*)k_ph_big<double, 2> ||
+         f == (const void*)k_ph_big<float, 4> || f == (const void*)k_ph_big<f2, 2>;
 }
 
 static void set_node_priorities(cudaGraph_t body) {

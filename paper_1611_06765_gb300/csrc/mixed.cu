@@ -688,7 +688,10 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     launch_pp_tc(M->items, M->cta_off, M->grid, M, M->smem, M->nst, ctx->ctl, ctx->ns, s);
     pnm_lad_expand(ctx, M->rpp32, M->ksplit, ctx->ns, out.data());
   } else {
-    if (precision == PNM_PREC_F32PAIR) pnm_prepare_f2(ctx);
+    if (precision == PNM_PREC_F32PAIR) {
+      pnm_prepare_f2(ctx);
+      pnm_split_cur(ctx, s);
+    }
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
     // every row: the operator acts on any amplitudes
     pnm_launch_pp64(ctx, s, false, precision == PNM_PREC_F32PAIR ? ctx->vpp_f2 : nullptr);
@@ -740,7 +743,8 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   } else {
     if (precision == PNM_PREC_F32PAIR) {
       pnm_prepare_f2(ctx);
-      if (ctx->nx > 0) launch_ph_f2(ctx, ctx->xw_f2, ctx->xv1_f2, s);
+      pnm_split_cur(ctx, s);
+      if (ctx->nx > 0) launch_ph_f2(ctx, ctx->t_pair, ctx->xw_f2, ctx->xv1_f2, s);
     } else if (ctx->nx > 0) {
       launch_ph64(ctx, s);
     }

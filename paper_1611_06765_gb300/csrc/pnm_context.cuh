@@ -49,8 +49,12 @@ struct pnm_ctx {
   int4* grp_items = nullptr;  // (channel, first ij, first pp column, rows) of the update
   int n_grp_items = 0, upd_rows = 1;
   int* ph_list = nullptr;  // cross channels of the ph launches (S_z >= 0, costliest first)
-  int n_ph = 0, n_ph_warp = 0;           // channels of the CTA launch, then of the warp launch
-  size_t ph_smem64 = 0, ph_smem32 = 0;   // shared memory of a CTA (the largest channel)
+  // channels of the larger size class (k_ph_big), then of the CTA path and of the warp path of
+  // k_ph, in that order in ph_list
+  int n_ph_big = 0, n_ph = 0, n_ph_warp = 0;
+  size_t ph_smem64 = 0, ph_smem32 = 0;          // shared memory of a k_ph CTA (its largest channel)
+  size_t ph_big_smem64 = 0, ph_big_smem32 = 0;  // and of a k_ph_big CTA
+  f2* t_pair = nullptr;                          // FP32-pair copy of the current amplitudes
   int *grp_lo_d = nullptr, *grp_hi_d = nullptr;  // per system ranges of the update items
   int *ab_lo_d = nullptr, *ab_hi_d = nullptr;    // per system ranges of the column items
   int max_nhh = 1;
@@ -157,9 +161,10 @@ void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
 void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only = true, const f2* vpp_f2 = nullptr);
-void launch_ph_f2(pnm_ctx* ctx, const f2* xw, const f2* xv1, cudaStream_t s);
+void launch_ph_f2(pnm_ctx* ctx, const f2* tpair, const f2* xw, const f2* xv1, cudaStream_t s);
 void pnm_split_f2(const double* a, f2* b, long n, cudaStream_t s);
 void pnm_prepare_f2(pnm_ctx* ctx);
+void pnm_split_cur(pnm_ctx* ctx, cudaStream_t s);
 size_t ph_smem_bytes(int max_dim, int nm, size_t elem);
 void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha);
 void pnm_fork(pnm_ctx* ctx);
