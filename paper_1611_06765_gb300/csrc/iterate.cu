@@ -806,12 +806,17 @@ __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
 // One CTA per item (channel, up to UPD_ROWS hole pairs ij, 128 pp columns).  Jacobi step of
 // Eq. (ccd3): the bracket collects v, the non-eps parts of the one-body terms, the pp and hh
 // ladders and P(ij)P(ab) Q; then t_new = bracket / eps_ij^ab and t = alpha t_new + (1 - alpha) t_old.
-// The residual of the amplitude equation is R = bracket - eps_ij^ab t.
+// The residual of the amplitude equation is R = bracket - eps_ij^ab t.  The hh ladder is
+// summed in the element arithmetic of T_: FP64, or FP32 pairs from the pair copy of the
+// amplitudes (the sweeps with FP32-pair contractions); everything else is FP64.
+template <typename T_>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
-                                                const int4* __restrict__ items, FinArgs fa) {
+                                                const int4* __restrict__ items, FinArgs fa,
+                                                const T_* __restrict__ tpair) {
+  using A = Arith<T_>;
   // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng;
   // per row: its hole pair ij and d_i + d_j of the one-body term
-  __shared__ double chs[UPD_MAX_NHH][UPD_ROWS];
+  __shared__ T_ chs[UPD_MAX_NHH][UPD_ROWS];
   __shared__ double row_dij[UPD_ROWS];
   __shared__ int row_ij[UPD_ROWS];
   __shared__ double sh32[32];
@@ -845,23 +850,31 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   __syncthreads();
   for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
     int kl = e / UPD_ROWS, g = e % UPD_ROWS;
-    chs[kl][g] = g < ng ? D.chi_hh[vho + (long)kl * nh + row_ij[g]] : 0.0;
+    chs[kl][g] = g < ng ? A::from_double(D.chi_hh[vho + (long)kl * nh + row_ij[g]]) : A::zero();
   }
   __syncthreads();
   double esum = 0.0, rsum = 0.0;
   if (ab < npp) {
     // hh ladder sum_kl t_ab^kl chi_kl^ij for all rows of the item: one pass over the t column
     double hh[UPD_ROWS];
+    {
+      T_ hs[UPD_ROWS];
 #pragma unroll
-    for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0.0;
-    if (!frozen) {
-      const long col = base + ab;
+      for (int g = 0; g < UPD_ROWS; g++) hs[g] = A::zero();
+      if (!frozen) {
+        const long col = base + ab;
+        const T_* __restrict__ tc;
+        if constexpr (std::is_same<T_, double>::value) tc = t;
+        else tc = tpair;
 #pragma unroll 4
-      for (int kl = 0; kl < nh; kl++) {
-        double tk = t[col + (long)kl * npp];
+        for (int kl = 0; kl < nh; kl++) {
+          const T_ tk = tc[col + (long)kl * npp];
 #pragma unroll
-        for (int g = 0; g < UPD_ROWS; g++) hh[g] = tk * chs[kl][g] + hh[g];
+          for (int g = 0; g < UPD_ROWS; g++) A::mac(hs[g], tk, chs[kl][g]);
+        }
       }
+#pragma unroll
+      for (int g = 0; g < UPD_ROWS; g++) hh[g] = A::out(hs[g]);
     }
     int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
     // one-body part of the bracket: (d_a + d_b - d_i - d_j) t with d_p = chi_p - eps_p
@@ -912,9 +925,13 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   last_block_finalize(fa, ctl);
 }
 
-void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h) {
-  k_update<<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
-                                                      fin_args(ctx, use_cond, h, false));
+void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool pair) {
+  if (pair)
+    k_update<f2><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
+                                                            fin_args(ctx, use_cond, h, false), ctx->t_pair);
+  else
+    k_update<double><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
+                                                                fin_args(ctx, use_cond, h, false), nullptr);
 }
 
 // Mixed-precision update.  One CTA per item (channel, up to UPD_ROWS hole pairs ij of the rows
@@ -1750,7 +1767,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
   if (terms == PNM_TERMS_FULL) pnm_enqueue_stats(ctx, false);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
-  launch_update64(ctx, use_cond, h);
+  launch_update64(ctx, use_cond, h, pair);
   prof_end(ctx);
 }
 

@@ -176,7 +176,7 @@ void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s);
 void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq, cudaStream_t s);
-void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
+void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool pair = false);
 void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* xq, const double* aw, float* xt, int use_cond,
                        cudaGraphConditionalHandle h, int nplanes, long pstride);
 void pnm_alpha_inv(pnm_ctx* ctx, double alpha, double* aw);
