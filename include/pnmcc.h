@@ -297,6 +297,8 @@ typedef struct {
     int batch;                /* samples per Adam step */
     double lr;                /* Adam learning rate (beta1 0.9, beta2 0.999, eps 1e-8) */
     unsigned long long seed;  /* shuffling */
+    double lr_final;          /* learning rate of the last step: the rate follows a half cosine
+                                 from lr down to lr_final over all steps (<= 0 or == lr: constant) */
 } pnm_mlp_opts;
 
 /* Number of floats in a parameter blob. */

@@ -276,10 +276,11 @@ def mlp_init(seed=0):
     return blob
 
 
-def mlp_train(contexts, blob, epochs=20, batch=4096, lr=1e-3, seed=0):
-    """pnm_mlp_train on the amplitudes held by the contexts; returns (blob, loss history)."""
+def mlp_train(contexts, blob, epochs=20, batch=4096, lr=1e-3, seed=0, lr_final=None):
+    """pnm_mlp_train on the amplitudes held by the contexts; returns (blob, loss history).
+    lr_final: the learning rate decays from lr to lr_final along a half cosine (None: constant)."""
     blob = np.ascontiguousarray(blob, dtype=np.float32).copy()
-    o = _lib.pnm_mlp_opts(epochs, batch, lr, seed)
+    o = _lib.pnm_mlp_opts(epochs, batch, lr, seed, lr if lr_final is None else lr_final)
     handles = (C.c_void_p * len(contexts))(*[c._h.value for c in contexts])
     hist = np.zeros(max(1, epochs), np.float32)
     nh = C.c_int()

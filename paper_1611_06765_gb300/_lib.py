@@ -59,7 +59,8 @@ class pnm_solve_opts(C.Structure):
 
 
 class pnm_mlp_opts(C.Structure):
-    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("seed", C.c_ulonglong)]
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("seed", C.c_ulonglong),
+                ("lr_final", C.c_double)]
 
 
 class PnmError(RuntimeError):

@@ -131,6 +131,13 @@ struct VecT<double, 2> {
   }
 };
 template <>
+struct VecT<float, 2> {
+  __device__ __forceinline__ static void ld(const float* p, float (&v)[2]) {
+    float2 a = *reinterpret_cast<const float2*>(p);
+    v[0] = a.x; v[1] = a.y;
+  }
+};
+template <>
 struct VecT<float, 4> {
   __device__ __forceinline__ static void ld(const float* p, float (&v)[4]) {
     float4 q = *reinterpret_cast<const float4*>(p);
@@ -516,8 +523,11 @@ static size_t ph_big_smem_of(const pnm_ctx* ctx) {
 
 // Register tile of the ph kernels: 2 x 2 for FP64 (little padding; the FP64 pipe bounds the
 // kernel) and FP32 pairs, 4 x 4 for FP32 (fewer shared-memory loads per FMA).
+#ifndef PNM_PH32_TILE
+#define PNM_PH32_TILE 4
+#endif
 template <typename T_>
-constexpr int ph_tile() { return std::is_same<T_, float>::value ? 4 : 2; }
+constexpr int ph_tile() { return std::is_same<T_, float>::value ? PNM_PH32_TILE : 2; }
 
 // The ph term: one launch over the S_z >= 0 cross channels (ph_list, costliest first).
 // The 8-byte element types (FP64, FP32 pairs) are limited by shared memory: the larger channels
@@ -1847,9 +1857,9 @@ void pnm_prepare_terms(pnm_ctx* ctx, int terms) {
 // the highest, so that the shorter branches (pp ladder, one-body sums) are dispatched ahead of
 // the many ph CTAs and run beside them instead of after them.
 static bool is_ph_kernel(const void* f) {
-  return f == (const void*)k_ph<double, PH_THREADS, 2> || f == (const void*)k_ph<float, PH_THREADS, 4> ||
+  return f == (const void*)k_ph<double, PH_THREADS, 2> || f == (const void*)k_ph<float, PH_THREADS, ph_tile<float>()> ||
          f == (const void*)k_ph<f2, PH_THREADS, 2> || f == (const void*)k_ph_big<double, 2> ||
-         f == (const void*)k_ph_big<float, 4> || f == (const void*)k_ph_big<f2, 2>;
+         f == (const void*)k_ph_big<float, ph_tile<float>()> || f == (const void*)k_ph_big<f2, 2>;
 }
 
 static void set_node_priorities(cudaGraph_t body) {

@@ -930,6 +930,8 @@ int pnm_mlp_train(pnm_ctx* const* ctxs, int nctx, const pnm_mlp_opts* o, float* 
     std::iota(perm.begin(), perm.end(), 0);
     std::mt19937_64 rng(g_seed_mix(o->seed));
     long step = 0;
+    const long nsteps = (long)o->epochs * (ntot / B);
+    const double lr_end = o->lr_final > 0.0 ? o->lr_final : o->lr;
     int nh = 0;
     const float b1 = 0.9f, b2 = 0.999f;
     for (int ep = 0; ep < o->epochs; ep++) {
@@ -942,9 +944,12 @@ int pnm_mlp_train(pnm_ctx* const* ctxs, int nctx, const pnm_mlp_opts* o, float* 
         k_out<<<(B * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, T, idx + r0, B, nt.Y, nt.dY,
                                                    lacc);
         net_backward(s, nt, B);
+        // half-cosine decay from lr to lr_final over the steps (constant when they are equal)
+        const double frac = nsteps > 1 ? (double)step / (double)(nsteps - 1) : 0.0;
+        const double lr = lr_end + 0.5 * (o->lr - lr_end) * (1.0 + std::cos(PNM_PI * frac));
         step++;
         float c1 = 1.0f - std::pow(b1, (float)step), c2 = 1.0f - std::pow(b2, (float)step);
-        k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.g, nt.m, nt.v, nt.q, (float)o->lr, b1, b2, c1, c2,
+        k_adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.g, nt.m, nt.v, nt.q, (float)lr, b1, b2, c1, c2,
                                                     1e-8f);
       }
       CUDA_TRY(cudaGetLastError());

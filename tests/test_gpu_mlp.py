@@ -133,15 +133,17 @@ def test_features_match_numpy(pkg):
 def trained(pkg):
     """The warm-start network as the benchmark trains it: the library's kernels on the
     amplitudes the FP64 solver converges (|dE/N| < 1e-8 MeV) for N = 14 (n^2 <= 20, 16
-    densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16); 20 epochs, batch 1024, Adam
-    lr 1e-3, seeds 1 (initial weights) and 2 (shuffling)."""
+    densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.04, 0.08, 0.14, 0.16, 0.20, none of
+    them held out); 20 epochs, batch 1024, Adam with the learning rate decaying from 1e-3 to
+    1e-5 along a half cosine, seeds 1 (initial weights) and 2 (shuffling)."""
     P = minnesota_params()
     kw = dict(alpha=0.5, tol=1e-30, tol_per_N=1e-8, max_iter=300)
     train14 = pkg.Context(14, [0.02 * k for k in range(1, 17)], 20, params=P)
     train14.solve(**kw)
-    train66 = pkg.Context(66, 0.16, 36, params=P)
+    train66 = pkg.Context(66, [0.04, 0.08, 0.14, 0.16, 0.20], 36, params=P)
     train66.solve(**kw)
-    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=20, batch=1024, lr=1e-3, seed=2)
+    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=20, batch=1024, lr=1e-3, seed=2,
+                               lr_final=1e-5)
     for c in (train14, train66):
         c.close()
     assert hist[-1] < hist[0]
@@ -149,39 +151,50 @@ def trained(pkg):
 
 
 @pytest.fixture(scope="module")
-def heldout_fixed_points():
-    """The oracle's CCD energy per neutron at the held-out densities, converged to
-    |dE change| / N < 1e-10 MeV (mixing 0.5, MBPT2 start)."""
+def heldout_oracle():
+    """The oracle's CCD energy per neutron at the held-out densities (mixing 0.5, MBPT2 start):
+    stopped by the metric's rule |dE^(n+1) - dE^(n)| / N < 1e-6 MeV, and converged to its fixed
+    point (1e-10 MeV)."""
     P = minnesota_params()
-    out = []
+    rule, fixed = [], []
     for rho in HELDOUT:
         o = channel.OracleSystem(66, rho, 36, P)
+        dE, _, _, _ = o.ccd(alpha=0.5, tol=1e-6 * 66, maxit=400)
+        rule.append(dE / 66)
         dE, _, _, _ = o.ccd(alpha=0.5, tol=1e-10 * 66, maxit=400)
-        out.append(dE / 66)
-    return np.array(out)
+        fixed.append(dE / 66)
+    return np.array(rule), np.array(fixed)
 
 
-def test_metric_configuration_against_oracle(pkg, trained, heldout_fixed_points):
+def test_metric_configuration_against_oracle(pkg, trained, heldout_oracle):
     """The configuration the time-to-converge metric is quoted on: N = 66, n^2 <= 36, held-out
     rho = 0.05, 0.11, 0.17 in one batched context, learned start, BF16x3 tensor-core ladders
     with FP32 contractions, stopping rule |dE^(n+1) - dE^(n)| / N < 1e-6 MeV, then two FP64
-    refinement sweeps.  Every density ends within 1e-6 MeV per neutron of the oracle's fixed
-    point, without the MBPT2 fallback, in fewer updates than the same solve from the MBPT2
-    start (Eq. ccdGuess)."""
+    refinement sweeps (FP32-pair contractions, FP64 update).  Every density matches the FP64
+    oracle run to the same stopping rule within 1e-6 MeV per neutron, without the MBPT2
+    fallback, in at least 25% fewer updates than the same solve from the MBPT2 start (Eq.
+    ccdGuess).  Against the oracle's fixed point both starts stay within 1.5e-6 MeV per neutron:
+    the stopping rule itself leaves an error of that order (the FP64 oracle at the rule sits
+    about 1.1e-6 to 1.4e-6 above its fixed point)."""
+    rule, fixed = heldout_oracle
     test = pkg.Context(66, HELDOUT, 36, params=minnesota_params())
     test.mlp_set_model(trained)
     kw = dict(precision=pkg.PNM_PREC_BF16X3, alpha=0.5, tol=1e-30, tol_per_N=1e-6, max_iter=500,
-              refine_sweeps=2)
+              refine_sweeps=2, refine_kernels=pkg.PNM_PREC_F32PAIR)
     dE_m, it_m, _, _ = test.solve(init=pkg.PNM_INIT_MBPT2, **kw)
     dE_l, it_l, _, _ = test.solve(init=pkg.PNM_INIT_MLP, **kw)
     assert test.timings()["mlp_fallback"] == 0
-    err_l = dE_l / 66 - heldout_fixed_points
-    err_m = dE_m / 66 - heldout_fixed_points
-    print("learned start: updates %s, dE/N - oracle %s; MBPT2 start: updates %s, dE/N - oracle %s"
-          % (it_l, err_l, it_m, err_m))
-    assert np.all(np.abs(err_l) < 1e-6)
-    assert np.all(np.abs(err_m) < 1e-6)
-    assert it_l.sum() < it_m.sum(), (it_l, it_m)
+    for k in range(3):
+        print("rho %.2f learned-start energies per neutron:" % HELDOUT[k], np.round(test.history(k) / 66, 8))
+    print("learned start: updates %s, dE/N - oracle at the rule %s, - fixed point %s"
+          % (it_l, dE_l / 66 - rule, dE_l / 66 - fixed))
+    print("MBPT2 start:   updates %s, dE/N - oracle at the rule %s, - fixed point %s"
+          % (it_m, dE_m / 66 - rule, dE_m / 66 - fixed))
+    assert np.all(np.abs(dE_l / 66 - rule) < 1e-6)
+    assert np.all(np.abs(dE_m / 66 - rule) < 1e-6)
+    assert np.all(np.abs(dE_l / 66 - fixed) < 1.5e-6)
+    assert np.all(np.abs(dE_m / 66 - fixed) < 1.5e-6)
+    assert np.all(it_l <= 0.75 * it_m), (it_l, it_m)
     test.close()
 
 
