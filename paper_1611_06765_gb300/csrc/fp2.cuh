@@ -24,12 +24,15 @@ struct f2 {
 template <typename T_>
 struct Arith;
 
+// Out: the type a kernel stores its results in (FP32 pairs keep the pair, so that a consumer
+// summing several results does so on the FP32 pipe and converts once); to_double converts.
 template <>
 struct Arith<double> {
-  using Out = double;  // type of a stored result
+  using Out = double;
   __device__ __forceinline__ static double zero() { return 0.0; }
   __device__ __forceinline__ static double from_double(double x) { return x; }
   __device__ __forceinline__ static Out out(double x) { return x; }
+  __device__ __forceinline__ static double to_double(double x) { return x; }
   __device__ __forceinline__ static double add(double a, double b) { return a + b; }
   __device__ __forceinline__ static double sub(double a, double b) { return a - b; }
   __device__ __forceinline__ static double neg(double a) { return -a; }
@@ -43,6 +46,7 @@ struct Arith<float> {
   __device__ __forceinline__ static float zero() { return 0.0f; }
   __device__ __forceinline__ static float from_double(double x) { return (float)x; }
   __device__ __forceinline__ static Out out(float x) { return x; }
+  __device__ __forceinline__ static double to_double(float x) { return (double)x; }
   __device__ __forceinline__ static float add(float a, float b) { return a + b; }
   __device__ __forceinline__ static float sub(float a, float b) { return a - b; }
   __device__ __forceinline__ static float neg(float a) { return -a; }
@@ -52,14 +56,15 @@ struct Arith<float> {
 
 template <>
 struct Arith<f2> {
-  using Out = double;
+  using Out = f2;
   __device__ __forceinline__ static f2 zero() { return f2{0.0f, 0.0f}; }
   // x = hi + lo with hi = x rounded to FP32 and lo = (x - hi) rounded (x - hi is exact in FP64)
   __device__ __forceinline__ static f2 from_double(double x) {
     const float h = (float)x;
     return f2{h, (float)(x - (double)h)};
   }
-  __device__ __forceinline__ static Out out(f2 a) { return (double)a.hi + (double)a.lo; }
+  __device__ __forceinline__ static Out out(f2 a) { return a; }
+  __device__ __forceinline__ static double to_double(f2 a) { return (double)a.hi + (double)a.lo; }
   // two-sum of the high parts, the error and the low parts folded and renormalised
   __device__ __forceinline__ static f2 add(f2 a, f2 b) {
     const float s = __fadd_rn(a.hi, b.hi);

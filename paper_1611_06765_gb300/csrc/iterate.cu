@@ -509,11 +509,17 @@ size_t ph_smem_bytes(int max_dim, int nm, size_t elem) {
   return ph_index_bytes(m4, m4) + elem * 3 * (size_t)nm * m4 * m4;
 }
 
-// Shared memory of the two launches: the larger size class alone, the smaller class and the
-// warp path.
+// Shared memory of the launches: the larger size class alone (k_ph_big); for the 8-byte types
+// the middle and the small class each alone and the warp path alone (PNM_PH_CLASSES = 4), or
+// the smaller classes with the warp path in one launch (2, the default: the tails of the extra
+// launches cost more than their higher occupancy gains); FP32 in one launch.
+#ifndef PNM_PH_CLASSES
+#define PNM_PH_CLASSES 2
+#endif
 template <typename T_>
 static size_t ph_smem_of(const pnm_ctx* ctx) {
-  size_t b = sizeof(T_) == 8 ? ctx->ph_smem64 : std::max(ctx->ph_smem32, ctx->ph_big_smem32);
+  size_t b = sizeof(T_) == 8 ? std::max(ctx->ph_smem64, ctx->ph_mid_smem64)
+                             : std::max(std::max(ctx->ph_smem32, ctx->ph_mid_smem32), ctx->ph_big_smem32);
   return ctx->n_ph_warp > 0 ? std::max(b, ph_warp_smem(sizeof(T_))) : b;
 }
 template <typename T_>
@@ -538,15 +544,37 @@ static void launch_ph_list(pnm_ctx* ctx, const T_* tpair, const T_* xt, const T_
                            typename Arith<T_>::Out* xq, cudaStream_t s) {
   constexpr int TS = ph_tile<T_>();
   constexpr bool split = sizeof(T_) == 8;
-  if (split && ctx->n_ph_big > 0)
+  const int nwb = (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
+  if (!split) {
+    // FP32: every channel in one launch, the larger first
+    const int nblk = ctx->n_ph_big + ctx->n_ph_mid + ctx->n_ph;
+    if (nblk + nwb > 0)
+      k_ph<T_, PH_THREADS, TS><<<nblk + nwb, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
+          ctx->d, ctx->ctl, ctx->ph_list, nblk, ctx->n_ph_warp, tpair, xt, xw, xv1, xq);
+    return;
+  }
+  if (ctx->n_ph_big > 0)
     k_ph_big<T_, TS><<<ctx->n_ph_big, PH_BIG_THREADS, ph_big_smem_of<T_>(ctx), s>>>(
         ctx->d, ctx->ctl, ctx->ph_list, tpair, xt, xw, xv1, xq);
-  const int nblk = split ? ctx->n_ph : ctx->n_ph_big + ctx->n_ph;
-  const int* list = split ? ctx->ph_list + ctx->n_ph_big : ctx->ph_list;
-  int grid = nblk + (ctx->n_ph_warp + PH_WARPS - 1) / PH_WARPS;
-  if (grid > 0)
-    k_ph<T_, PH_THREADS, TS><<<grid, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
-        ctx->d, ctx->ctl, list, nblk, ctx->n_ph_warp, tpair, xt, xw, xv1, xq);
+  const int* mid = ctx->ph_list + ctx->n_ph_big;
+  if (PNM_PH_CLASSES == 4) {
+    const int* small = mid + ctx->n_ph_mid;
+    const int* warp = small + ctx->n_ph;
+    if (ctx->n_ph_mid > 0)
+      k_ph<T_, PH_THREADS, TS><<<ctx->n_ph_mid, PH_THREADS, ctx->ph_mid_smem64, s>>>(
+          ctx->d, ctx->ctl, mid, ctx->n_ph_mid, 0, tpair, xt, xw, xv1, xq);
+    if (ctx->n_ph > 0)
+      k_ph<T_, PH_THREADS, TS><<<ctx->n_ph, PH_THREADS, ctx->ph_smem64, s>>>(
+          ctx->d, ctx->ctl, small, ctx->n_ph, 0, tpair, xt, xw, xv1, xq);
+    if (nwb > 0)
+      k_ph<T_, PH_THREADS, TS><<<nwb, PH_THREADS, ph_warp_smem(sizeof(T_)), s>>>(
+          ctx->d, ctx->ctl, warp, 0, ctx->n_ph_warp, tpair, xt, xw, xv1, xq);
+  } else {
+    const int nblk = ctx->n_ph_mid + ctx->n_ph;
+    if (nblk + nwb > 0)
+      k_ph<T_, PH_THREADS, TS><<<nblk + nwb, PH_THREADS, ph_smem_of<T_>(ctx), s>>>(
+          ctx->d, ctx->ctl, mid, nblk, ctx->n_ph_warp, tpair, xt, xw, xv1, xq);
+  }
 }
 
 template <typename T_>
@@ -561,10 +589,10 @@ void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear) {
 }
 
 // The same term with FP32-pair arithmetic (T gathered from the FP32-pair copy of the current
-// amplitudes, W and <kb|v|cj> split into FP32 pairs once per context, FP64 Q): the
-// contractions of the refinement sweeps.
+// amplitudes, W and <kb|v|cj> split into FP32 pairs once per context, Q stored as FP32 pairs in
+// the 8-byte slots of the FP64 Q): the contractions of the refinement sweeps.
 void launch_ph_f2(pnm_ctx* ctx, const f2* tpair, const f2* xw, const f2* xv1, cudaStream_t s) {
-  launch_ph_list<f2>(ctx, tpair, nullptr, xw, xv1, ctx->d.xq, s);
+  launch_ph_list<f2>(ctx, tpair, nullptr, xw, xv1, reinterpret_cast<f2*>(ctx->d.xq), s);
 }
 
 // Mixed ph: T read from the FP32 cross-channel copy the update scatters, Q in FP32 at its
@@ -625,6 +653,7 @@ void pnm_split_cur(pnm_ctx* ctx, cudaStream_t s) {
 template <typename T_>
 __global__ void __launch_bounds__(128) k_lad_expand(DevState D, const T_* __restrict__ rs, int planes,
                                                     long pstride, double* __restrict__ out) {
+  using A = Arith<T_>;
   int2 it = D.row_item[blockIdx.x];
   int c = it.x, ij = it.y;
   int npp = D.ch_npp[c];
@@ -635,9 +664,9 @@ __global__ void __launch_bounds__(128) k_lad_expand(DevState D, const T_* __rest
     if (vpp) {
       int sg;
       long z = lad_index(D, c, ij, ab, sg);
-      T_ a = 0;
-      for (int p = 0; p < planes; p++) a += rs[p * pstride + z];
-      v = sg > 0 ? (double)a : -(double)a;
+      T_ a = A::zero();
+      for (int p = 0; p < planes; p++) a = A::add(a, rs[p * pstride + z]);
+      v = sg > 0 ? A::to_double(a) : -A::to_double(a);
     }
     o[ab] = v;
   }
@@ -721,7 +750,8 @@ __global__ void __launch_bounds__(PP64_WARPS * 32) k_pp(DevState D, const LoopCt
       T_ s = A::zero();
 #pragma unroll
       for (int w = 0; w < PP64_WARPS; w++) s = A::add(s, red[(w * PP64_ROWS + r) * 32 + l]);
-      if (ab0 + l < npp) D.rpp[tb + (long)(rows ? rows[g0 + r] : g0 + r) * npp + ab0 + l] = A::out(s);
+      if (ab0 + l < npp)
+        reinterpret_cast<typename A::Out*>(D.rpp)[tb + (long)(rows ? rows[g0 + r] : g0 + r) * npp + ab0 + l] = A::out(s);
     }
   }
 }
@@ -819,10 +849,14 @@ __device__ void last_block_finalize(const FinArgs& f, LoopCtl* ctl) {
 // The residual of the amplitude equation is R = bracket - eps_ij^ab t.  The hh ladder is
 // summed in the element arithmetic of T_: FP64, or FP32 pairs from the pair copy of the
 // amplitudes (the sweeps with FP32-pair contractions); everything else is FP64.
+// With FP32 pairs the pp ladder, the hh ladder and the ph term arrive as pairs (the 8-byte
+// slots of rpp and xq) and their sum is formed on the FP32 pipe and converted to FP64 once; the
+// denominator, residual, step (alpha / eps_ij^ab prepared per solve, aw) and energy stay FP64.
 template <typename T_>
 __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict__ ctl,
                                                 const int4* __restrict__ items, FinArgs fa,
-                                                const T_* __restrict__ tpair) {
+                                                const T_* __restrict__ tpair, const double* __restrict__ aw) {
+  constexpr bool PAIR = std::is_same<T_, f2>::value;
   using A = Arith<T_>;
   // the hh-ladder factor chi_kl^ij of the item's rows: chs[kl][g], zero for rows past ng;
   // per row: its hole pair ij and d_i + d_j of the one-body term
@@ -866,25 +900,20 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   double esum = 0.0, rsum = 0.0;
   if (ab < npp) {
     // hh ladder sum_kl t_ab^kl chi_kl^ij for all rows of the item: one pass over the t column
-    double hh[UPD_ROWS];
-    {
-      T_ hs[UPD_ROWS];
+    T_ hs[UPD_ROWS];
 #pragma unroll
-      for (int g = 0; g < UPD_ROWS; g++) hs[g] = A::zero();
-      if (!frozen) {
-        const long col = base + ab;
-        const T_* __restrict__ tc;
-        if constexpr (std::is_same<T_, double>::value) tc = t;
-        else tc = tpair;
+    for (int g = 0; g < UPD_ROWS; g++) hs[g] = A::zero();
+    if (!frozen) {
+      const long col = base + ab;
+      const T_* __restrict__ tc;
+      if constexpr (PAIR) tc = tpair;
+      else tc = t;
 #pragma unroll 4
-        for (int kl = 0; kl < nh; kl++) {
-          const T_ tk = tc[col + (long)kl * npp];
+      for (int kl = 0; kl < nh; kl++) {
+        const T_ tk = tc[col + (long)kl * npp];
 #pragma unroll
-          for (int g = 0; g < UPD_ROWS; g++) A::mac(hs[g], tk, chs[kl][g]);
-        }
+        for (int g = 0; g < UPD_ROWS; g++) A::mac(hs[g], tk, chs[kl][g]);
       }
-#pragma unroll
-      for (int g = 0; g < UPD_ROWS; g++) hh[g] = A::out(hs[g]);
     }
     int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
     // one-body part of the bracket: (d_a + d_b - d_i - d_j) t with d_p = chi_p - eps_p
@@ -904,23 +933,43 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
       double v = D.v_pphh[z];
       if (!frozen) {
         int4 q = D.qmap[z];
-        double num = v + (da - row_dij[g]) * tz;
-        if (has_vpp) {
-          int sg;
-          double rl = D.rpp[lad_index(D, c, row_ij[g], ab, sg)];
-          num += sg > 0 ? rl : -rl;
+        if constexpr (PAIR) {
+          // pp ladder + hh ladder + P(ij)P(ab) Q in FP32 pairs, converted once
+          const f2* __restrict__ rp = reinterpret_cast<const f2*>(D.rpp);
+          const f2* __restrict__ xqp = reinterpret_cast<const f2*>(D.xq);
+          f2 corr = hs[g];
+          if (has_vpp) {
+            int sg;
+            const f2 rl = rp[lad_index(D, c, row_ij[g], ab, sg)];
+            corr = A::add(corr, sg > 0 ? rl : A::neg(rl));
+          }
+          if (q.x >= 0) corr = A::add(corr, xqp[q.x]);
+          if (q.y >= 0) corr = A::sub(corr, xqp[q.y]);
+          if (q.z >= 0) corr = A::sub(corr, xqp[q.z]);
+          if (q.w >= 0) corr = A::add(corr, xqp[q.w]);
+          const double num = fma(da - row_dij[g], tz, v) + A::to_double(corr);
+          const double R = fma(-D.den[z], tz, num);  // bracket - eps_ij^ab t
+          rsum = fma(wgt * R, R, rsum);
+          out = fma(R, aw[z], tz);                   // t + alpha R / eps_ij^ab
+        } else {
+          double num = v + (da - row_dij[g]) * tz;
+          if (has_vpp) {
+            int sg;
+            double rl = D.rpp[lad_index(D, c, row_ij[g], ab, sg)];
+            num += sg > 0 ? rl : -rl;
+          }
+          num += A::to_double(hs[g]);
+          double ph = 0.0;
+          if (q.x >= 0) ph += D.xq[q.x];
+          if (q.y >= 0) ph -= D.xq[q.y];
+          if (q.z >= 0) ph -= D.xq[q.z];
+          if (q.w >= 0) ph += D.xq[q.w];
+          num += ph;
+          double tnew = num * D.inv_den[z];
+          double R = num - D.den[z] * tz;
+          rsum += wgt * (R * R);
+          out = alpha * tnew + (1.0 - alpha) * tz;
         }
-        num += hh[g];
-        double ph = 0.0;
-        if (q.x >= 0) ph += D.xq[q.x];
-        if (q.y >= 0) ph -= D.xq[q.y];
-        if (q.z >= 0) ph -= D.xq[q.z];
-        if (q.w >= 0) ph += D.xq[q.w];
-        num += ph;
-        double tnew = num * D.inv_den[z];
-        double R = num - D.den[z] * tz;
-        rsum += wgt * (R * R);
-        out = alpha * tnew + (1.0 - alpha) * tz;
       }
       tn[z] = out;
       if (f != z) tn[f] = fc > 0 ? out : -out;
@@ -938,10 +987,12 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool pair) {
   if (pair)
     k_update<f2><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
-                                                            fin_args(ctx, use_cond, h, false), ctx->t_pair);
+                                                            fin_args(ctx, use_cond, h, false), ctx->t_pair,
+                                                            pnm_mixed_aw(ctx));
   else
     k_update<double><<<ctx->n_grp_items, 128, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->grp_items,
-                                                                fin_args(ctx, use_cond, h, false), nullptr);
+                                                                fin_args(ctx, use_cond, h, false), nullptr,
+                                                                nullptr);
 }
 
 // Mixed-precision update.  One CTA per item (channel, up to UPD_ROWS hole pairs ij of the rows
@@ -1468,9 +1519,9 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->d.sysctl = ctx->sysctl;
   // cross channels of the ph launch: S_z >= 0 (S_z < 0 ones are read at their flips), costliest first;
   // shared memory for the largest (NM = 1: rows/columns; NM = 2: those of the halves, twice)
-  // CTA per channel in two size classes (larger than PH_SMALL_DIM: k_ph_big), warp per channel
-  // (at most PH_WARP_DIM)
-  std::vector<int> xb, xl, xw;
+  // CTA per channel in three size classes (larger than PH_SMALL_DIM: k_ph_big; larger than
+  // PH_MID_DIM; the rest), warp per channel (at most PH_WARP_DIM)
+  std::vector<int> xb, xm, xl, xw;
   std::vector<long> xcost(ctx->nx, 0);
   for (int x = 0; x < ctx->nx; x++) {
     int c = ctx->h_x_cls[x];
@@ -1492,6 +1543,10 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
       ctx->ph_big_smem64 = std::max(ctx->ph_big_smem64, ph_smem_bytes(d, nm, sizeof(double)));
       ctx->ph_big_smem32 = std::max(ctx->ph_big_smem32, ph_smem_bytes(d, nm, sizeof(float)));
       xb.push_back(x);
+    } else if (d > PH_MID_DIM) {
+      ctx->ph_mid_smem64 = std::max(ctx->ph_mid_smem64, ph_smem_bytes(d, nm, sizeof(double)));
+      ctx->ph_mid_smem32 = std::max(ctx->ph_mid_smem32, ph_smem_bytes(d, nm, sizeof(float)));
+      xm.push_back(x);
     } else {
       ctx->ph_smem64 = std::max(ctx->ph_smem64, ph_smem_bytes(d, nm, sizeof(double)));
       ctx->ph_smem32 = std::max(ctx->ph_smem32, ph_smem_bytes(d, nm, sizeof(float)));
@@ -1500,14 +1555,18 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   }
   auto costlier = [&](int a, int b) { return xcost[a] != xcost[b] ? xcost[a] > xcost[b] : a < b; };
   std::sort(xb.begin(), xb.end(), costlier);
+  std::sort(xm.begin(), xm.end(), costlier);
   std::sort(xl.begin(), xl.end(), costlier);
   std::sort(xw.begin(), xw.end(), costlier);
   ctx->n_ph_big = (int)xb.size();
+  ctx->n_ph_mid = (int)xm.size();
   ctx->n_ph = (int)xl.size();
   ctx->n_ph_warp = (int)xw.size();
+  // list order: big, middle, small, warp
   xl.insert(xl.end(), xw.begin(), xw.end());
+  xl.insert(xl.begin(), xm.begin(), xm.end());
   xl.insert(xl.begin(), xb.begin(), xb.end());
-  size_t ph_smem = std::max(ctx->ph_smem64, ctx->ph_big_smem64);
+  size_t ph_smem = std::max(std::max(ctx->ph_smem64, ctx->ph_mid_smem64), ctx->ph_big_smem64);
   ctx->ph_list = (int*)dmalloc(ctx, sizeof(int) * std::max<size_t>(1, xl.size()));
   if (!xl.empty())
     CUDA_TRY(cudaMemcpyAsync(ctx->ph_list, xl.data(), sizeof(int) * xl.size(), cudaMemcpyHostToDevice, s));
@@ -1690,6 +1749,10 @@ void pnm_lad_expand(pnm_ctx* ctx, const float* rs, int planes, long pstride, dou
 }
 
 void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, double* host_out) {
+  lad_expand(ctx, rs, planes, pstride, host_out);
+}
+
+void pnm_lad_expand(pnm_ctx* ctx, const f2* rs, int planes, long pstride, double* host_out) {
   lad_expand(ctx, rs, planes, pstride, host_out);
 }
 

@@ -652,6 +652,11 @@ void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha) {
   CUDA_TRY(cudaGetLastError());
 }
 
+const double* pnm_mixed_aw(const pnm_ctx* ctx) {
+  if (!ctx->mixed) throw PnmError{PNM_EINVAL, "the mixed-precision path has not been prepared"};
+  return ctx->mixed->aw;
+}
+
 void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask) {
   if (serial_mask)
     *serial_mask = (ctx->sched_tuned[0] ? (ctx->serial_sched[0] ? 1 : 0) : 4) |
@@ -695,7 +700,10 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
     // every row: the operator acts on any amplitudes
     pnm_launch_pp64(ctx, s, false, precision == PNM_PREC_F32PAIR ? ctx->vpp_f2 : nullptr);
-    pnm_lad_expand(ctx, ctx->d.rpp, 1, ctx->ns, out.data());
+    if (precision == PNM_PREC_F32PAIR)
+      pnm_lad_expand(ctx, reinterpret_cast<const f2*>(ctx->d.rpp), 1, ctx->ns, out.data());
+    else
+      pnm_lad_expand(ctx, ctx->d.rpp, 1, ctx->ns, out.data());
   }
   int err = 0;
   CUDA_TRY(cudaMemcpy(&err, &ctx->ctl->dev_error, sizeof(int), cudaMemcpyDeviceToHost));
@@ -706,15 +714,20 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
   }
 }
 
-// out[z] = Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba of amplitude z from the cross-channel Q.
+// out[z] = Q_ij^ab - Q_ji^ab - Q_ij^ba + Q_ji^ba of amplitude z from the cross-channel Q (FP32,
+// FP64, or FP32 pairs summed as pairs).
 template <typename T>
 __global__ void k_ph_assemble(DevState D, const T* __restrict__ xq, long nt, double* __restrict__ out) {
+  using A = Arith<T>;
   long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= nt) return;
   int4 q = D.qmap[z];
-  double a0 = q.x >= 0 ? (double)xq[q.x] : 0.0, a1 = q.y >= 0 ? (double)xq[q.y] : 0.0;
-  double a2 = q.z >= 0 ? (double)xq[q.z] : 0.0, a3 = q.w >= 0 ? (double)xq[q.w] : 0.0;
-  out[z] = (a0 - a1) - (a2 - a3);
+  T a0 = q.x >= 0 ? xq[q.x] : A::zero(), a1 = q.y >= 0 ? xq[q.y] : A::zero();
+  T a2 = q.z >= 0 ? xq[q.z] : A::zero(), a3 = q.w >= 0 ? xq[q.w] : A::zero();
+  if constexpr (std::is_same<T, f2>::value)
+    out[z] = A::to_double(A::sub(A::sub(a0, a1), A::sub(a2, a3)));
+  else
+    out[z] = ((double)a0 - (double)a1) - ((double)a2 - (double)a3);
 }
 
 // The ph term P(ij)P(ab) sum_kc t_ik^ac chi_kb^cj as an operator on the amplitudes of one
@@ -745,10 +758,11 @@ void pnm_apply_ph(pnm_ctx* ctx, int sys, int precision, const double* t, double*
       pnm_prepare_f2(ctx);
       pnm_split_cur(ctx, s);
       if (ctx->nx > 0) launch_ph_f2(ctx, ctx->t_pair, ctx->xw_f2, ctx->xv1_f2, s);
-    } else if (ctx->nx > 0) {
-      launch_ph64(ctx, s);
+      k_ph_assemble<f2><<<nb, 256, 0, s>>>(ctx->d, reinterpret_cast<const f2*>(ctx->d.xq), ctx->nt, ctx->expand_buf);
+    } else {
+      if (ctx->nx > 0) launch_ph64(ctx, s);
+      k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->expand_buf);
     }
-    k_ph_assemble<double><<<nb, 256, 0, s>>>(ctx->d, ctx->d.xq, ctx->nt, ctx->expand_buf);
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(r, ctx->expand_buf + S.t_begin, sizeof(double) * n, cudaMemcpyDeviceToHost, s));

@@ -49,10 +49,11 @@ struct pnm_ctx {
   int4* grp_items = nullptr;  // (channel, first ij, first pp column, rows) of the update
   int n_grp_items = 0, upd_rows = 1;
   int* ph_list = nullptr;  // cross channels of the ph launches (S_z >= 0, costliest first)
-  // channels of the larger size class (k_ph_big), then of the CTA path and of the warp path of
-  // k_ph, in that order in ph_list
-  int n_ph_big = 0, n_ph = 0, n_ph_warp = 0;
-  size_t ph_smem64 = 0, ph_smem32 = 0;          // shared memory of a k_ph CTA (its largest channel)
+  // channels of the larger size class (k_ph_big), of the middle and the small class of the CTA
+  // path and of the warp path of k_ph, in that order in ph_list
+  int n_ph_big = 0, n_ph_mid = 0, n_ph = 0, n_ph_warp = 0;
+  size_t ph_smem64 = 0, ph_smem32 = 0;          // shared memory of a small-class k_ph CTA
+  size_t ph_mid_smem64 = 0, ph_mid_smem32 = 0;  // of a middle-class k_ph CTA
   size_t ph_big_smem64 = 0, ph_big_smem32 = 0;  // and of a k_ph_big CTA
   f2* t_pair = nullptr;                          // FP32-pair copy of the current amplitudes
   int *grp_lo_d = nullptr, *grp_hi_d = nullptr;  // per system ranges of the update items
@@ -146,6 +147,9 @@ void pnm_mbpt3_all(pnm_ctx* ctx, double* out);
 // The pp ladder from its ladder layout (planes summed) into host memory in the amplitude layout.
 void pnm_lad_expand(pnm_ctx* ctx, const float* rs, int planes, long pstride, double* host_out);
 void pnm_lad_expand(pnm_ctx* ctx, const double* rs, int planes, long pstride, double* host_out);
+void pnm_lad_expand(pnm_ctx* ctx, const f2* rs, int planes, long pstride, double* host_out);
+// alpha / eps_ij^ab of the current mixed solve (the step of the mixed and refinement updates)
+const double* pnm_mixed_aw(const pnm_ctx* ctx);
 void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h);
 void pnm_prepare_mixed(pnm_ctx* ctx);
 void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol);

@@ -184,9 +184,10 @@ constexpr int UPD_MIN_BLOCKS = PNM_UPD_MIN_BLOCKS;
 
 // Threads of a ph-term CTA (one cross channel each); channels of at most PH_WARP_DIM rows and
 // columns (of their halves for S_z = 0) take one warp each.
-// Channels with more than PH_SMALL_DIM rows or columns go to the larger size class (their own
-// launch and shared-memory size, so that the many smaller channels keep more CTAs per SM).
-constexpr int PH_THREADS = 128, PH_WARP_DIM = 16, PH_SMALL_DIM = 32;
+// Channels with more than PH_SMALL_DIM rows or columns go to the larger size class, those with
+// more than PH_MID_DIM to the middle one (each class with its own launch and shared-memory
+// size, so that the many smaller channels keep more CTAs per SM).
+constexpr int PH_THREADS = 128, PH_WARP_DIM = 16, PH_SMALL_DIM = 32, PH_MID_DIM = 24;
 
 // pp ladder of amplitude (ij, ab) of channel c from its ladder-layout value (planes summed by
 // the caller where there are several).
