@@ -276,9 +276,12 @@ int pnm_apply_pp_ladder(pnm_ctx *ctx, int sys, int precision, const double *t, d
 int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, double *r, size_t n);
 
 /* Device time (ms, CUDA events) of the last pnm_create*, pnm_mbpt2 and pnm_ccd_solve:
- * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement; and
- * ms[5] = 1 if the last solve with init = PNM_INIT_MLP fell back to the MBPT2 start, else 0.
- * The first min(n, 6) entries are written. */
+ * ms[0] setup, ms[1] mbpt2, ms[2] solve (total), ms[3] mixed phase, ms[4] refinement;
+ * ms[5] = 1 if the last solve with init = PNM_INIT_MLP fell back to the MBPT2 start, else 0;
+ * ms[6] host wall time (ms) that the last pnm_ccd_solve spent on the context's one-time
+ * preparation (FP32 and FP32-pair copies, schedule tuning, capture and instantiation of the
+ * iteration graphs); 0 when all of it was done by an earlier solve of the context.
+ * The first min(n, 7) entries are written. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
 
 /* ---------------------------------------------------------------- learned warm start
@@ -321,6 +324,13 @@ int pnm_mlp_train(pnm_ctx *const *ctxs, int nctx, const pnm_mlp_opts *opts, floa
 
 /* Install a trained blob in a context for solves with init = PNM_INIT_MLP. */
 int pnm_mlp_set_model(pnm_ctx *ctx, const float *blob);
+
+/* Write the learned start, the amplitudes a solve with init = PNM_INIT_MLP begins from, into
+ * the context's held amplitudes (pnm_get_amplitudes reads them): t_MBPT2 + sigma_sys y_scale
+ * net(features) on the rows the updates compute, their spin flips on the others.  Needs a
+ * model (PNM_EINVAL otherwise); PNM_ETIMEOUT if a bounded wait of the inference kernel ran
+ * out (the held amplitudes are then incomplete). */
+int pnm_mlp_predict(pnm_ctx *ctx);
 
 /* Network output for n feature rows (host arrays).  mode: PNM_MLP_TENSOR_CORES runs the
  * fused tcgen05 inference kernel (the learned start's), PNM_MLP_SIMT the SIMT training

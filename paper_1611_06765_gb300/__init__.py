@@ -211,6 +211,10 @@ class Context:
         blob = np.ascontiguousarray(blob, dtype=np.float32)
         _lib.check(_lib.load().pnm_mlp_set_model(self._h, blob.ctypes.data_as(C.POINTER(C.c_float))))
 
+    def mlp_predict(self):
+        """Learned start into the held amplitudes (``pnm_mlp_predict``); read with get_amplitudes."""
+        _lib.check(_lib.load().pnm_mlp_predict(self._h))
+
     def tuning(self):
         """Autotuner choices: (k-range splits, ring stages, us per ladder launch, serial mask)."""
         a, b, us, m = C.c_int(), C.c_int(), C.c_float(), C.c_int()
@@ -235,9 +239,10 @@ class Context:
         return out
 
     def timings(self):
-        ms = np.zeros(6)
-        _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 6))
-        return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4], mlp_fallback=int(ms[5]))
+        ms = np.zeros(7)
+        _lib.check(_lib.load().pnm_get_timings(self._h, ms.ctypes.data_as(C.POINTER(C.c_double)), 7))
+        return dict(setup=ms[0], mbpt2=ms[1], solve=ms[2], mixed=ms[3], refine=ms[4], mlp_fallback=int(ms[5]),
+                    prepare=ms[6])
 
 
 def _fptr(a):

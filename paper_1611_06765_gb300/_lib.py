@@ -43,7 +43,7 @@ EXPORTS = (
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_apply_ph_term", "pnm_mlp_num_params", "pnm_mlp_init",
-    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
+    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_predict", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
     "pnm_measure_fma_peak", "pnm_last_error",
 )
 
@@ -115,6 +115,7 @@ def load(path=None):
     L.pnm_mlp_features.argtypes = [vp, C.c_int, vp, vp, vp]
     L.pnm_mlp_train.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(pnm_mlp_opts), fp, fp, C.c_int, ip]
     L.pnm_mlp_set_model.argtypes = [vp, fp]
+    L.pnm_mlp_predict.argtypes = [vp]
     L.pnm_mlp_forward.argtypes = [fp, fp, C.c_long, fp, C.c_int, vp]
     L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, C.c_int, vp]
     L.pnm_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_float), ip]

@@ -490,9 +490,9 @@ int pnm_set_amplitudes(pnm_ctx* ctx, int sys, const double* t, size_t n) {
 int pnm_get_timings(const pnm_ctx* ctx, double* ms, int n) {
   return guarded([&]() {
     if (!ctx || !ms) throw PnmError{PNM_EINVAL, "null argument"};
-    double v[6] = {ctx->t_setup, ctx->t_mbpt2, ctx->t_solve, ctx->t_mixed, ctx->t_refine,
-                   (double)ctx->mlp_fallback};
-    for (int k = 0; k < n && k < 6; k++) ms[k] = v[k];
+    double v[7] = {ctx->t_setup, ctx->t_mbpt2, ctx->t_solve, ctx->t_mixed, ctx->t_refine,
+                   (double)ctx->mlp_fallback, ctx->t_prepare};
+    for (int k = 0; k < n && k < 7; k++) ms[k] = v[k];
     return PNM_OK;
   });
 }

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <map>
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <type_traits>
 
@@ -43,9 +44,13 @@ struct StatsIO {
 // Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for the ij the updates
 // compute.
 // Blocks [nrows, ...): column chunk (c, ab0): sab[ab] = sum_ij t v.
-template <typename T_>
+// PAIR (FP64 only): the chi_hh contraction in FP32-pair arithmetic from the pair copies tp of t
+// and vp of v_pphh (the refinement sweeps); the one-body sums, O(n_t), stay FP64.
+template <typename T_, bool PAIR = false>
 __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __restrict__ ctl,
-                                                int nrows, const int2* __restrict__ ab_items) {
+                                                int nrows, const int2* __restrict__ ab_items,
+                                                const f2* __restrict__ tp = nullptr,
+                                                const f2* __restrict__ vp = nullptr) {
   __shared__ T_ sh32[32];
   StatsIO<T_> io(D, ctl);
   const T_* __restrict__ t = io.t;
@@ -67,10 +72,21 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
     const int nr = D.ch_uoff[c + 1] - D.ch_uoff[c];
     for (int k = warp; k < nr; k += blockDim.x >> 5) {
       const int ij = rl[k];
-      const T_* tj = t + base + (long)ij * npp;
       T_ acc = 0;
-      for (int cd = lane; cd < npp; cd += 32) acc += vr[cd] * tj[cd];
-      acc = warp_sum(acc);
+      if constexpr (PAIR) {
+        const f2* __restrict__ vk = vp + base + (long)kl * npp;
+        const f2* __restrict__ tj = tp + base + (long)ij * npp;
+        f2 a2 = Arith<f2>::zero();
+        for (int cd = lane; cd < npp; cd += 32) Arith<f2>::mac(a2, vk[cd], tj[cd]);
+        for (int o = 16; o; o >>= 1)
+          a2 = Arith<f2>::add(a2, f2{__shfl_xor_sync(0xffffffffu, a2.hi, o),
+                                     __shfl_xor_sync(0xffffffffu, a2.lo, o)});
+        acc = Arith<f2>::to_double(a2);
+      } else {
+        const T_* tj = t + base + (long)ij * npp;
+        for (int cd = lane; cd < npp; cd += 32) acc += vr[cd] * tj[cd];
+        acc = warp_sum(acc);
+      }
       if (lane == 0) {
         long e = D.ch_vhh_off[c] + (long)kl * nh + ij;
         io.chi[e] = io.vhh[e] + acc;
@@ -1801,13 +1817,16 @@ void pnm_join(pnm_ctx* ctx) {
 // One-body intermediates and <kl|chi|ij> (shared by both precision modes, FP64).
 // One-body sums, chi_hh and the one-body terms: FP64 (mixed = false) or from the FP32
 // copies of the mixed-precision iteration.
-void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed) {
+void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed, bool pair) {
   cudaStream_t s = ctx->stream;
   DevState& D = ctx->d;
   unsigned nb = (unsigned)(ctx->nrows + ctx->n_ab_items);
   unsigned nd = (unsigned)((ctx->nsp_total * 32 + 255) / 256);
   prof_begin(ctx, mixed ? KID_TSTATS32 : KID_TSTATS);
   if (mixed) k_tstats<float><<<nb, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
+  else if (pair)
+    k_tstats<double, true><<<nb, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items, ctx->t_pair,
+                                             ctx->vpphh_f2);
   else k_tstats<double><<<nb, 128, 0, s>>>(D, ctx->ctl, ctx->nrows, ctx->ab_items);
   prof_end(ctx);
   prof_begin(ctx, mixed ? KID_DCHI32 : KID_DCHI);
@@ -1837,7 +1856,7 @@ static void enqueue_body_fp64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHa
     pnm_launch_pp64(ctx, s_pp, true, pair ? ctx->vpp_f2 : nullptr);
     prof_end(ctx);
   }
-  if (terms == PNM_TERMS_FULL) pnm_enqueue_stats(ctx, false);
+  if (terms == PNM_TERMS_FULL) pnm_enqueue_stats(ctx, false, pair);
   pnm_join(ctx);
   prof_begin(ctx, KID_UPDATE);
   launch_update64(ctx, use_cond, h, pair);
@@ -1887,7 +1906,7 @@ void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditional
   else pnm_enqueue_body_mixed(ctx, use_cond, h);
 }
 
-// FP32-pair copies of the ladder-basis V_pppp, W and <kb|v|cj> (once per context).
+// FP32-pair copies of the ladder-basis V_pppp, V_pphh, W and <kb|v|cj> (once per context).
 void pnm_prepare_f2(pnm_ctx* ctx) {
   if (ctx->vpp_f2) return;
   cudaStream_t s = ctx->stream;
@@ -1895,7 +1914,9 @@ void pnm_prepare_f2(pnm_ctx* ctx) {
   ctx->t_pair = ctx_alloc<f2>(ctx, ctx->nt);
   ctx->xw_f2 = ctx_alloc<f2>(ctx, ctx->nxt);
   ctx->xv1_f2 = ctx_alloc<f2>(ctx, ctx->nxc);
+  ctx->vpphh_f2 = ctx_alloc<f2>(ctx, ctx->nt);
   pnm_split_f2(ctx->d.v_pppp, ctx->vpp_f2, ctx->nvpp, s);
+  pnm_split_f2(ctx->d.v_pphh, ctx->vpphh_f2, ctx->nt, s);
   pnm_split_f2(ctx->d.x_w, ctx->xw_f2, ctx->nxt, s);
   pnm_split_f2(ctx->d.x_v1, ctx->xv1_f2, ctx->nxc, s);
   CUDA_TRY(cudaGetLastError());
@@ -1948,6 +1969,7 @@ static void set_node_priorities(cudaGraph_t body) {
 static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
   auto f = ctx->graphs.find(mode);
   if (f != ctx->graphs.end()) return f->second;
+  const auto w0 = std::chrono::steady_clock::now();
   cudaGraph_t g;
   CUDA_TRY(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle h;
@@ -1976,6 +1998,7 @@ static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
   CUDA_TRY(cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority));
   ctx->graphs[mode] = ge;
   ctx->graph_defs[mode] = g;
+  ctx->t_graph_host += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   return ge;
 }
 

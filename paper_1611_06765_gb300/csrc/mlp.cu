@@ -10,6 +10,7 @@
 // inference is one fused tcgen05 kernel: the four layers of a 128-sample tile run back to
 // back with the weights resident in shared memory and the accumulator in tensor memory.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -61,7 +62,8 @@ struct FeatSys {
   float f19, f20, f21;        // rho / 0.16, k_F, N / 66
 };
 
-// t_MBPT2 per amplitude and partial sums of its square (one per update item).
+// t_MBPT2 per amplitude (stored when tm2 is given) and partial sums of its square (one per
+// update item).
 __global__ void k_tm2(DevState D, const int4* __restrict__ items, double* __restrict__ tm2,
                       double* __restrict__ parts) {
   __shared__ double sh32[32];
@@ -73,7 +75,7 @@ __global__ void k_tm2(DevState D, const int4* __restrict__ items, double* __rest
   if (ab < npp && threadIdx.x < 128) {
     long z = D.ch_t_off[c] + (long)ij * npp + ab;
     double t = D.v_pphh[z] * D.inv_den[z];  // the MBPT2 amplitude v / eps_ij^ab
-    tm2[z] = t;
+    if (tm2) tm2[z] = t;
     s = t * t;
   }
   s = block_sum(s, sh32);
@@ -94,37 +96,63 @@ __global__ void k_sigma(const double* __restrict__ parts, const int* __restrict_
   }
 }
 
+// Features [16 h, 16 h + 16) of the restricted amplitude z = (channel c, hole pair ij, particle
+// pair ab): h = 0 the momenta of a, b, i, j in units of k_F and their spins; h = 1
+// eps_ij^ab / eps_F, N <ab|v|ij> / eps_F, t_MBPT2 / sigma_sys (t_MBPT2 = v / eps, the product
+// k_tm2 forms), rho / 0.16, k_F, N / 66, zeros.  FP64 only where the inputs are FP64: three
+// products (reciprocals prepared per system) and their conversions.
+__device__ __forceinline__ void feature_half(const DevState& D, const FeatSys& f, double inv_sigma, int c,
+                                             int ij, int ab, long z, int h, float (&x)[16]) {
+  if (h == 0) {
+    const int2 hp = D.hh_pair[D.ch_hh_off[c] + ij];
+    const int2 pp = D.pp_pair[D.ch_pp_off[c] + ab];
+    const char4 sa = D.nvec[pp.x], sb = D.nvec[pp.y], si = D.nvec[hp.x], sj = D.nvec[hp.y];
+    const float k = (float)f.kscale;
+    x[0] = k * sa.x; x[1] = k * sa.y; x[2] = k * sa.z;
+    x[3] = k * sb.x; x[4] = k * sb.y; x[5] = k * sb.z;
+    x[6] = k * si.x; x[7] = k * si.y; x[8] = k * si.z;
+    x[9] = k * sj.x; x[10] = k * sj.y; x[11] = k * sj.z;
+    x[12] = sa.w; x[13] = sb.w; x[14] = si.w; x[15] = sj.w;
+  } else {
+    const double v = D.v_pphh[z];
+    const double tm2 = v * D.inv_den[z];
+    x[0] = (float)(D.den[z] * f.inv_epsF);
+    x[1] = (float)(v * f.v_scale);
+    x[2] = (float)(tm2 * inv_sigma);
+    x[3] = f.f19;
+    x[4] = f.f20;
+    x[5] = f.f21;
+#pragma unroll
+    for (int q = 6; q < 16; q++) x[q] = 0.0f;
+  }
+}
+
 __global__ void k_features(DevState D, const int4* __restrict__ items, const FeatSys* __restrict__ fs,
-                           const double* __restrict__ tm2, const double* __restrict__ inv_sigma,
-                           float* __restrict__ X) {
+                           const double* __restrict__ inv_sigma, float* __restrict__ X) {
   int4 it = items[blockIdx.x];
   int c = it.x, ij = it.y;
   int npp = D.ch_npp[c];
   int ab = it.z + threadIdx.x;
   if (ab >= npp || threadIdx.x >= 128) return;
   int sys = D.ch_sys[c];
-  FeatSys f = fs[sys];
   long z = D.ch_t_off[c] + (long)ij * npp + ab;
-  int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-  int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
-  char4 sa = D.nvec[p.x], sb = D.nvec[p.y], si = D.nvec[h.x], sj = D.nvec[h.y];
   float* x = X + z * MF;
-  float k = (float)f.kscale;
-  x[0] = k * sa.x; x[1] = k * sa.y; x[2] = k * sa.z;
-  x[3] = k * sb.x; x[4] = k * sb.y; x[5] = k * sb.z;
-  x[6] = k * si.x; x[7] = k * si.y; x[8] = k * si.z;
-  x[9] = k * sj.x; x[10] = k * sj.y; x[11] = k * sj.z;
-  x[12] = sa.w; x[13] = sb.w; x[14] = si.w; x[15] = sj.w;
-  // FP64 only where the inputs are FP64: three products (reciprocals prepared per system) and
-  // their conversions; the per-system constants arrive as FP32
-  x[16] = (float)(D.den[z] * f.inv_epsF);
-  x[17] = (float)(D.v_pphh[z] * f.v_scale);
-  x[18] = (float)(tm2[z] * inv_sigma[sys]);
-  x[19] = f.f19;
-  x[20] = f.f20;
-  x[21] = f.f21;
+  for (int h = 0; h < 2; h++) {
+    float xh[16];
+    feature_half(D, fs[sys], inv_sigma[sys], c, ij, ab, z, h, xh);
 #pragma unroll
-  for (int q = NFEAT; q < MF; q++) x[q] = 0.0f;
+    for (int q = 0; q < 16; q++) x[16 * h + q] = xh[q];
+  }
+}
+
+// The learned start's sample list: rep[off + k] = (z, c) for the amplitudes z = t_off[c] +
+// ij npp + ab0 + k of the row chunks items (c, ij, ab0, off) (up to 128 columns each).
+__global__ void k_rep_fill(DevState D, const int4* __restrict__ items, int2* __restrict__ rep) {
+  const int4 it = items[blockIdx.x];
+  const int npp = D.ch_npp[it.x];
+  const int ab = it.z + threadIdx.x;
+  if (ab >= npp || threadIdx.x >= 128) return;
+  rep[it.w + threadIdx.x] = make_int2((int)(D.ch_t_off[it.x] + (long)it.y * npp + ab), it.x);
 }
 
 // Training targets y = (t - t_MBPT2) / sigma_sys from the held amplitudes t0.
@@ -352,14 +380,26 @@ struct MlpOut {
   const int* idx;  // sample r is amplitude idx[r] (nullptr: amplitude r)
 };
 
+// Inputs of the learned start with the features formed in the kernel: sample r is amplitude
+// rep[r].x of channel rep[r].y; its features come from D (feature_half), its t_MBPT2 is
+// v / eps formed as k_tm2 forms it.
+struct MlpFused {
+  DevState D;
+  const int2* rep;
+  const FeatSys* fs;
+  const double* inv_sigma;
+};
+
 // One CTA (8 warps) loops over 128-sample tiles; two CTAs share an SM, so one CTA's
 // epilogue overlaps the other's MMAs.  Warp w reads TMEM lanes 32 (w % 4) ... + 31 (its
 // row quarter) and columns 64 (w / 4) ... + 63 (its column half); thread (w, lane) owns
 // sample row 32 (w % 4) + lane of the tile.
+// FUSED: the samples' features are formed from the context (MlpFused) instead of read from X.
+template <bool FUSED>
 __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restrict__ X, long n,
                                                            const float* __restrict__ q,
                                                            const __nv_bfloat16* __restrict__ pw, MlpOut out,
-                                                           int* __restrict__ err_flag) {
+                                                           MlpFused fin, int* __restrict__ err_flag) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* bar_w = reinterpret_cast<uint64_t*>(smem);
   uint64_t* bar_mma = bar_w + 1;
@@ -411,10 +451,22 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
   auto load_x = [&](long tile, float4 (&xr)[4]) {
     long rg = tile * MH + row;
     if (tile < ntiles && rg < n) {
-      const long zg = out.idx ? (long)out.idx[rg] : rg;
-      const float4* xp = reinterpret_cast<const float4*>(X + zg * MF + k0);
+      if constexpr (FUSED) {
+        const int2 zc = fin.rep[rg];
+        const int npp = fin.D.ch_npp[zc.y];
+        const int rel = (int)(zc.x - fin.D.ch_t_off[zc.y]);
+        const int ij = rel / npp, ab = rel - ij * npp;
+        const int sy = fin.D.ch_sys[zc.y];
+        float xh[16];
+        feature_half(fin.D, fin.fs[sy], fin.inv_sigma[sy], zc.y, ij, ab, zc.x, half, xh);
 #pragma unroll
-      for (int j = 0; j < 4; j++) xr[j] = __ldg(xp + j);
+        for (int j = 0; j < 4; j++) xr[j] = make_float4(xh[4 * j], xh[4 * j + 1], xh[4 * j + 2], xh[4 * j + 3]);
+      } else {
+        const long zg = out.idx ? (long)out.idx[rg] : rg;
+        const float4* xp = reinterpret_cast<const float4*>(X + zg * MF + k0);
+#pragma unroll
+        for (int j = 0; j < 4; j++) xr[j] = __ldg(xp + j);
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < 4; j++) xr[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -498,10 +550,19 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const float* __restri
           float y = __uint_as_float(r[0]) + par[3 * MH];
           if (out.Y) out.Y[r_glob] = y;
           if (out.t0) {
-            const long z = out.idx ? (long)out.idx[r_glob] : r_glob;
+            long z;
             int sy = 0;
-            while (sy + 1 < out.nsys && z >= out.t_begin[sy + 1]) sy++;
-            double t = out.tm2[z];
+            double t;
+            if constexpr (FUSED) {
+              const int2 zc = fin.rep[r_glob];
+              z = zc.x;
+              sy = fin.D.ch_sys[zc.y];
+              t = fin.D.v_pphh[z] * fin.D.inv_den[z];
+            } else {
+              z = out.idx ? (long)out.idx[r_glob] : r_glob;
+              while (sy + 1 < out.nsys && z >= out.t_begin[sy + 1]) sy++;
+              t = out.tm2[z];
+            }
             if (isfinite(y)) t += out.sigma[sy] * (double)out.y_scale * (double)y;
             out.t0[z] = t;
           }
@@ -599,28 +660,29 @@ unsigned long long g_seed_mix(unsigned long long x) {
 
 // ------------------------------------------------------------------- context glue
 struct MlpState {
-  float* X = nullptr;       // features of every amplitude (library order)
-  double* tm2 = nullptr;    // MBPT2 amplitudes
-  double* sigma = nullptr;  // per system
+  float* X = nullptr;       // features of every amplitude (library order; training and pnm_mlp_features)
+  double* tm2 = nullptr;    // MBPT2 amplitudes (idem)
+  double* sigma = nullptr;  // per system, then 1 / sigma per system
   long* t_begin = nullptr;  // first amplitude of each system, then the total
+  FeatSys* fs = nullptr;    // per-system feature constants
   float* q = nullptr;       // model parameters (BF16-rounded weights)
   __nv_bfloat16* pw = nullptr;
   int* err = nullptr;
-  int* rep = nullptr;       // the amplitudes of the rows the updates compute (learned start)
+  int2* rep = nullptr;      // (amplitude, channel) of the rows the updates compute (learned start)
   long n_rep = 0;
   float y_scale = 1.0f;
   bool have_model = false;
 };
 
-static void mlp_features(pnm_ctx* ctx) {
+// Per-system constants of the features: sigma_sys (RMS of the MBPT2 amplitudes), k_F, eps_F,
+// ... (once per context, stream-ordered, no host synchronisation).
+static void mlp_systems(pnm_ctx* ctx) {
   if (!ctx->mlp) ctx->mlp = new MlpState();
   MlpState* M = ctx->mlp;
-  if (M->X) return;
+  if (M->sigma) return;
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
-  M->X = ctx_alloc<float>(ctx, (size_t)ctx->nt * MF);
-  M->tm2 = ctx_alloc<double>(ctx, ctx->nt);
-  M->sigma = ctx_alloc<double>(ctx, 2 * nsys);  // sigma per system, then 1 / sigma
+  M->sigma = ctx_alloc<double>(ctx, 2 * nsys);
   std::vector<long> tb(nsys + 1);
   for (int k = 0; k < nsys; k++) tb[k] = ctx->sys[k].t_begin;
   tb[nsys] = ctx->nt;
@@ -645,14 +707,37 @@ static void mlp_features(pnm_ctx* ctx) {
     fs[k].f21 = (float)(S.N / 66.0);
   }
   long* dcnt = ctx_alloc<long>(ctx, nsys);
-  FeatSys* dfs = ctx_alloc<FeatSys>(ctx, nsys);
+  M->fs = ctx_alloc<FeatSys>(ctx, nsys);
+  // pageable sources: each copy has left the host vector when cudaMemcpyAsync returns
   CUDA_TRY(cudaMemcpyAsync(dcnt, cnt.data(), sizeof(long) * nsys, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(dfs, fs.data(), sizeof(FeatSys) * nsys, cudaMemcpyHostToDevice, s));
-  k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, parts);
+  CUDA_TRY(cudaMemcpyAsync(M->fs, fs.data(), sizeof(FeatSys) * nsys, cudaMemcpyHostToDevice, s));
+  k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, nullptr, parts);
   k_sigma<<<nsys, 256, 0, s>>>(parts, ctx->upd_lo_d, ctx->upd_hi_d, dcnt, M->sigma);
-  k_features<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, dfs, M->tm2, M->sigma + nsys, M->X);
+  CUDA_TRY(cudaGetLastError());
+}
+
+// The feature matrix X and t_MBPT2 of every amplitude, for training and pnm_mlp_features (the
+// learned start forms its features in the inference kernel instead).
+static void mlp_features(pnm_ctx* ctx) {
+  mlp_systems(ctx);
+  MlpState* M = ctx->mlp;
+  if (M->X) return;
+  cudaStream_t s = ctx->stream;
+  int nsys = (int)ctx->sys.size();
+  M->X = ctx_alloc<float>(ctx, (size_t)ctx->nt * MF);
+  M->tm2 = ctx_alloc<double>(ctx, ctx->nt);
+  double* parts = ctx_alloc<double>(ctx, ctx->n_upd_items);
+  k_tm2<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->tm2, parts);
+  k_features<<<ctx->n_upd_items, 128, 0, s>>>(ctx->d, ctx->upd_items, M->fs, M->sigma + nsys, M->X);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+static void mlp_tc_attributes() {
+  smem_at_least(k_mlp_tc<false>, MLP_SMEM);
+  smem_at_least(k_mlp_tc<true>, MLP_SMEM);
+  CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
 }
 
 static void check_blob_header(const float* blob) {
@@ -669,8 +754,7 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
     M->q = ctx_alloc<float>(ctx, NPARAM);
     M->pw = ctx_alloc<__nv_bfloat16>(ctx, PW_TOTAL);
     M->err = ctx_alloc<int>(ctx, 1);
-    smem_at_least(k_mlp_tc, MLP_SMEM);
-    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    mlp_tc_attributes();
   }
   float* w = ctx_alloc<float>(ctx, NPARAM);
   CUDA_TRY(cudaMemcpyAsync(w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
@@ -683,46 +767,62 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
   M->have_model = true;
 }
 
+// One CTA pair per SM over the 128-sample tiles (fin.rep set: features formed in the kernel).
 static void tc_infer(cudaStream_t s, const float* X, long n, const float* q, const __nv_bfloat16* pw,
-                     const MlpOut& out, int* err) {
+                     const MlpOut& out, int* err, const MlpFused* fin = nullptr) {
   long ntiles = (n + MH - 1) / MH;
   int dev = 0, nsm = 148;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   int grid = (int)std::min<long>(ntiles, 2L * nsm);
-  if (grid > 0) k_mlp_tc<<<grid, MLP_THREADS, MLP_SMEM, s>>>(X, n, q, pw, out, err);
+  if (grid <= 0) return;
+  if (fin) k_mlp_tc<true><<<grid, MLP_THREADS, MLP_SMEM, s>>>(X, n, q, pw, out, *fin, err);
+  else k_mlp_tc<false><<<grid, MLP_THREADS, MLP_SMEM, s>>>(X, n, q, pw, out, MlpFused{}, err);
 }
 
 // Learned start into t0 (every system), used by the solver for PNM_INIT_MLP.
 void pnm_mlp_start(pnm_ctx* ctx) {
   if (!ctx->mlp || !ctx->mlp->have_model) throw PnmError{PNM_EINVAL, "no warm-start model set (pnm_mlp_set_model)"};
-  mlp_features(ctx);
+  mlp_systems(ctx);
   MlpState* M = ctx->mlp;
   cudaStream_t s = ctx->stream;
   if (!M->rep) {
     // the start is made flip-symmetric: the network is evaluated on the rows the updates
-    // compute (about half the amplitudes) and the rest is copied from their spin flips
-    std::vector<int> idx;
-    idx.reserve((size_t)ctx->nt / 2 + 1024);
+    // compute (about half the amplitudes) and the rest is copied from their spin flips.  The
+    // sample list is filled on the device from row chunks (channel, ij, first column, offset).
+    std::vector<int4> chunks;
+    long off = 0;
     for (int r = 0; r < ctx->nrows; r++) {
       if (!ctx->h_row_mode[r]) continue;
       int2 row = ctx->h_rows[r];
-      long base = ctx->h_t_off[row.x] + (long)row.y * ctx->h_npp[row.x];
-      for (int ab = 0; ab < ctx->h_npp[row.x]; ab++) idx.push_back((int)(base + ab));
+      const int npp = ctx->h_npp[row.x];
+      for (int ab0 = 0; ab0 < npp; ab0 += 128) {
+        chunks.push_back(make_int4(row.x, row.y, ab0, (int)off));
+        off += std::min(128, npp - ab0);
+      }
     }
-    M->n_rep = (long)idx.size();
-    M->rep = ctx_alloc<int>(ctx, std::max<size_t>(1, idx.size()));
-    if (!idx.empty())
-      CUDA_TRY(cudaMemcpyAsync(M->rep, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    if (ctx->nt > INT_MAX) throw PnmError{PNM_EINVAL, "too many amplitudes for the learned start"};
+    M->n_rep = off;
+    M->rep = ctx_alloc<int2>(ctx, std::max<long>(1, off));
+    if (!chunks.empty()) {
+      int4* dch = ctx_alloc<int4>(ctx, chunks.size());
+      CUDA_TRY(cudaMemcpyAsync(dch, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s));
+      k_rep_fill<<<(unsigned)chunks.size(), 128, 0, s>>>(ctx->d, dch, M->rep);
+      CUDA_TRY(cudaGetLastError());
+    }
   }
   // the network output goes straight into t0 (t_MBPT2 + sigma_sys * y_scale * y)
-  tc_infer(s, M->X, M->n_rep, M->q, M->pw,
-           MlpOut{nullptr, ctx->d.t0, M->tm2, M->sigma, M->t_begin, (int)ctx->sys.size(), M->y_scale, M->rep},
-           M->err);
+  const int nsys = (int)ctx->sys.size();
+  const MlpFused fin{ctx->d, M->rep, M->fs, M->sigma + nsys};
+  tc_infer(s, nullptr, M->n_rep, M->q, M->pw,
+           MlpOut{nullptr, ctx->d.t0, nullptr, M->sigma, M->t_begin, nsys, M->y_scale, nullptr}, M->err, &fin);
   pnm_flip_copy(ctx, ctx->d.t0, s);
   CUDA_TRY(cudaGetLastError());
 }
+
+// Device flag the inference kernel sets when one of its bounded waits ran out (nullptr without
+// a model).
+int* pnm_mlp_err(pnm_ctx* ctx) { return ctx->mlp ? ctx->mlp->err : nullptr; }
 
 void pnm_free_mlp(pnm_ctx* ctx) {
   delete ctx->mlp;
@@ -781,6 +881,24 @@ int pnm_mlp_set_model(pnm_ctx* ctx, const float* blob) {
   }
 }
 
+int pnm_mlp_predict(pnm_ctx* ctx) {
+  try {
+    if (!ctx) throw PnmError{PNM_EINVAL, "null argument"};
+    pnm_mlp_start(ctx);
+    int h_err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h_err, ctx->mlp->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (h_err) {
+      CUDA_TRY(cudaMemsetAsync(ctx->mlp->err, 0, sizeof(int), ctx->stream));
+      throw PnmError{PNM_ETIMEOUT, "a device-side wait ran out of its budget"};
+    }
+    return PNM_OK;
+  } catch (const PnmError& e) {
+    pnm_set_error(e.code, e.msg);
+    return e.code;
+  }
+}
+
 int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int mode, void* stream) {
   try {
     if (!blob || !X || !Y || n < 0) throw PnmError{PNM_EINVAL, "bad argument"};
@@ -802,8 +920,7 @@ int pnm_mlp_forward(const float* blob, const float* X, long n, float* Y, int mod
       __nv_bfloat16* pw = xalloc<__nv_bfloat16>(PW_TOTAL, sc.owned);
       int* err = xalloc<int>(1, sc.owned);
       CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-      smem_at_least(k_mlp_tc, MLP_SMEM);
-    CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+      mlp_tc_attributes();
       k_pack_weights<<<(PW_TOTAL + 255) / 256, 256, 0, s>>>(q, pw);
       tc_infer(s, dX, n, q, pw, MlpOut{dY, nullptr, nullptr, nullptr, nullptr, 0, 1.0f}, err);
       int h_err = 0;

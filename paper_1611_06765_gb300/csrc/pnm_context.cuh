@@ -80,9 +80,9 @@ struct pnm_ctx {
 
   MixedState* mixed = nullptr;
   MlpState* mlp = nullptr;
-  // FP32-pair copies of the ladder-basis V_pppp, W and <kb|v|cj> (made on first use by the
-  // FP32-pair contractions)
-  f2 *vpp_f2 = nullptr, *xw_f2 = nullptr, *xv1_f2 = nullptr;
+  // FP32-pair copies of the ladder-basis V_pppp, V_pphh, W and <kb|v|cj> (made on first use by
+  // the FP32-pair contractions)
+  f2 *vpp_f2 = nullptr, *vpphh_f2 = nullptr, *xw_f2 = nullptr, *xv1_f2 = nullptr;
   double hbar2_2m = 0.0;
   int mlp_fallback = 0;  // 1 when the last learned start was replaced by the MBPT2 start
 
@@ -102,6 +102,9 @@ struct pnm_ctx {
 
   // timings (ms)
   double t_setup = 0, t_mbpt2 = 0, t_solve = 0, t_mixed = 0, t_refine = 0, t_mbpt3 = 0;
+  // host wall time (ms) of the last solve's one-time preparation: pair and FP32 copies, schedule
+  // tuning, and the capture and instantiation of its graphs (t_graph_host accumulates the latter)
+  double t_prepare = 0, t_graph_host = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -159,11 +162,12 @@ void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
 void pnm_mlp_start(pnm_ctx* ctx);
 void pnm_free_mlp(pnm_ctx* ctx);
+int* pnm_mlp_err(pnm_ctx* ctx);
 void prof_begin(pnm_ctx* ctx, int kid);
 void prof_end(pnm_ctx* ctx);
 void prof_collect(pnm_ctx* ctx);
 FinArgs fin_args(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool per_row);
-void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed);
+void pnm_enqueue_stats(pnm_ctx* ctx, bool mixed, bool pair = false);
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only = true, const f2* vpp_f2 = nullptr);
 void launch_ph_f2(pnm_ctx* ctx, const f2* tpair, const f2* xw, const f2* xv1, cudaStream_t s);
 void pnm_split_f2(const double* a, f2* b, long n, cudaStream_t s);

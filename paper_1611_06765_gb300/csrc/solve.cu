@@ -1,6 +1,7 @@
 // solve.cu -- the CCD driver (Sec. "Developing a CCD code": MBPT2 start, Jacobi updates of
 // Eq. ccd3, mixing, stop on |dE^(n+1) - dE^(n)| < eta) and single-element V access.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 
 #include "pnm_context.cuh"
@@ -49,12 +50,15 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     ctx->graphs.clear();
     ctx->graph_defs.clear();
   }
+  const auto w0 = std::chrono::steady_clock::now();
+  const double g0 = ctx->t_graph_host;
   bool mixed = o.precision != PNM_PREC_FP64;
   if (mixed) pnm_prepare_mixed(ctx);
   const bool pair_refine = mixed && o.refine_sweeps > 0 && o.refine_kernels == PNM_PREC_F32PAIR;
   if (pair_refine) pnm_prepare_f2(ctx);
   pnm_tune_schedule(ctx, PNM_PREC_FP64, o.mix_alpha);
   if (mixed) pnm_tune_schedule(ctx, PNM_PREC_BF16X3, o.mix_alpha);
+  const double prep_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
 
   cudaEvent_t e0 = ctx->ev[0], e1 = ctx->ev[1], e2 = ctx->ev[2];
   CUDA_TRY(cudaEventRecord(e0, s));
@@ -82,10 +86,20 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   ctx->t_solve = elapsed(e0, e2);
   ctx->t_mixed = mixed ? elapsed(e0, e1) : 0.0;
   ctx->t_refine = mixed ? elapsed(e1, e2) : 0.0;
+  ctx->t_prepare = prep_ms + (ctx->t_graph_host - g0);
   pnm_settle_amplitudes(ctx);
   std::vector<SysCtl> hs(nsys);
   CUDA_TRY(cudaMemcpyAsync(hs.data(), ctx->sysctl, sizeof(SysCtl) * nsys, cudaMemcpyDeviceToHost, s));
+  int start_err = 0;
+  int* d_err = o.init == PNM_INIT_MLP ? pnm_mlp_err(ctx) : nullptr;
+  if (d_err) CUDA_TRY(cudaMemcpyAsync(&start_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  if (start_err) {
+    // the learned start is incomplete (a bounded wait of the inference kernel ran out)
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    pnm_set_error(PNM_ETIMEOUT, "a device-side wait of the learned start ran out of its budget");
+    return PNM_ETIMEOUT;
+  }
   for (int k = 0; k < nsys; k++) {
     if (dE) dE[k] = hs[k].e_new;
     if (iters) iters[k] = hs[k].iters;
@@ -98,8 +112,10 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
     pnm_solve_opts o2 = o;
     o2.init = PNM_INIT_MBPT2;
     float t_first = (float)ctx->t_solve;
+    double p_first = ctx->t_prepare;
     int rc = pnm_solve(ctx, o2, dE, iters, resid);
     ctx->t_solve += t_first;
+    ctx->t_prepare += p_first;
     ctx->mlp_fallback = 1;
     return rc;
   }

@@ -150,6 +150,51 @@ def trained(pkg):
     return blob
 
 
+def test_learned_start_matches_network_on_features(pkg, trained):
+    """The learned start forms its features inside the inference kernel.  Every amplitude it
+    writes is the network applied to the feature row pnm_mlp_features returns (checked above
+    against a numpy restatement), t_MBPT2 + sigma_sys y_scale y.  Rows the updates compute get
+    their own prediction, the other rows the prediction of their spin-flip partner (sign of
+    the reordering of the restricted pairs).  Two densities in one context, to cover the
+    per-system constants.  The only allowed difference is the rounding of the fused
+    multiply-add the kernel may form: 2^-50 of |t_MBPT2| + |sigma y_scale y|."""
+    P = minnesota_params()
+    g = pkg.Context(14, [0.06, 0.12], 20, params=P)
+    g.mlp_set_model(trained)
+    g.mlp_predict()
+    y_scale = float(trained[2 * 32])  # the blob header: mu[32], inv_std[32], y_scale, pad[3]
+    for sys in range(2):
+        t0 = g.get_amplitudes(sys)
+        X, tm2, sigma = g.mlp_features(sys)
+        y = pkg.mlp_forward(trained, X, tensor_cores=True).astype(np.float64)
+        pred = tm2 + sigma * y_scale * y
+        tol = 2.0 ** -50 * (np.abs(tm2) + np.abs(sigma * y_scale * y))
+        nv, _, _ = g.basis(sys)
+        where = {tuple(int(u) for u in nv[p]): p for p in range(len(nv))}
+        flip = np.array([where[(int(q[0]), int(q[1]), int(q[2]), -int(q[3]))] for q in nv])
+        labels = g.amplitude_labels(sys)
+        index = {tuple(int(u) for u in lab): z for z, lab in enumerate(labels)}
+        own = np.abs(t0 - pred) <= tol
+        partner_ok = np.zeros(len(t0), bool)
+        for z in np.nonzero(~own)[0]:
+            a, b, i, j = (int(flip[p]) for p in labels[z])
+            sign = 1.0
+            if (a, b, i, j) not in index:
+                if (b, a, i, j) in index:
+                    a, b, sign = b, a, -1.0
+                elif (a, b, j, i) in index:
+                    i, j, sign = j, i, -1.0
+                else:
+                    a, b, i, j = b, a, j, i
+            zp = index[(a, b, i, j)]
+            partner_ok[z] = abs(t0[z] - sign * pred[zp]) <= tol[zp]
+        frac_own = own.mean()
+        print("sys %d: %d amplitudes, %.3f own predictions" % (sys, len(t0), frac_own))
+        assert np.all(own | partner_ok)
+        assert 0.4 <= frac_own
+    g.close()
+
+
 @pytest.fixture(scope="module")
 def heldout_oracle():
     """The oracle's CCD energy per neutron at the held-out densities (mixing 0.5, MBPT2 start):
