@@ -1030,9 +1030,12 @@ void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, b
 // (50 MB each for the held-out batch, read and written at random) and the FP32 amplitudes the
 // next update's contractions read stay in L2.
 // The FP64 unit of a GB300 runs at about 1/64 of its FP32 rate, so the FP64 work is held to
-// eight instructions per amplitude; the new amplitude goes to t (FP64) and t32 for itself and,
-// sign applied, for its spin flip.  Rows go in batches of UPD_BATCH with all loads of a batch
-// issued before any store (rows past ng repeat the last row and are discarded).
+// eight instructions per amplitude; the new amplitude goes to t (FP64) for itself and to t32 for
+// itself and, sign applied, for its spin flip.  The FP64 flips are not read before the mixed
+// iteration ends (the update reads t at the amplitudes it computes only); one flip copy of the
+// current buffer fills them then (pnm_flip_copy_current).  Rows go in batches of UPD_BATCH with
+// all loads of a batch issued before any store (rows past ng repeat the last row and are
+// discarded).
 __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, LoopCtl* __restrict__ ctl,
                                                     const int4* __restrict__ items, FinArgs fa,
                                                     const float* __restrict__ rpp, const float* __restrict__ xq,
@@ -1168,9 +1171,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
         __stcs(tn + z[j], out);
         t32n[z[j]] = o32;
         if (f != z[j]) {
-          const bool neg = fc[j] < 0;
-          __stcs(tn + f, neg ? -out : out);
-          t32n[f] = neg ? -o32 : o32;
+          t32n[f] = fc[j] < 0 ? -o32 : o32;
           e2 = fma(v, out, e2);
           r2 = fma(R, R, r2);
         } else {
@@ -1266,6 +1267,14 @@ __global__ void k_flip_copy(const int* __restrict__ fmap, double* __restrict__ t
 void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s) {
   if (ctx->nt > 0)
     k_flip_copy<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, s>>>(ctx->d.fmap, t, ctx->nt);
+}
+
+// The spin flips of the current FP64 amplitudes (t[iter & 1]) from the amplitudes the updates
+// compute, after a mixed-precision iteration (whose updates write the FP64 values of the
+// computed amplitudes only).
+void pnm_flip_copy_current(pnm_ctx* ctx, int iter) {
+  pnm_flip_copy(ctx, (iter & 1) ? ctx->d.t1 : ctx->d.t0, ctx->stream);
+  CUDA_TRY(cudaGetLastError());
 }
 
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s) {

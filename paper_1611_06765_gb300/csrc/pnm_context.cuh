@@ -183,6 +183,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
 void launch_ph64(pnm_ctx* ctx, cudaStream_t s, bool linear = false);
 void pnm_flip_symmetrise(pnm_ctx* ctx, double* t, cudaStream_t s);
 void pnm_flip_copy(pnm_ctx* ctx, double* t, cudaStream_t s);
+void pnm_flip_copy_current(pnm_ctx* ctx, int iter);
 void launch_ph_mix(pnm_ctx* ctx, const float* xt, const float* xw, const float* xv1, float* xq, cudaStream_t s);
 void launch_update64(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHandle h, bool pair = false);
 void launch_update_mix(pnm_ctx* ctx, const float* rpp, const float* xq, const double* aw, float* xt, int use_cond,

@@ -258,65 +258,24 @@ __global__ void k_eps(const char4* __restrict__ nvec, const double* __restrict__
 }
 
 // ---------------------------------------------------------------------- channel counts
-// One warp per direct key: count restricted hh pairs (i<j<N) and pp pairs (N<=a<b).
-__global__ void k_count_direct(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                               int r, int m, int M, int species, int nkeys, int N, int nsp,
-                               int* __restrict__ cnt_hh, int* __restrict__ cnt_pp) {
-  int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (K >= nkeys) return;
-  int Px, Py, Pz, Sz;
-  decode_key(K, m, M, species, Px, Py, Pz, Sz);
-  int nh = 0, np = 0;
-  for (int p0 = 0; p0 < nsp; p0 += 32) {
-    int p = p0 + lane;
-    bool v = false;
-    if (p < nsp) {
-      char4 s = nvec[p];
-      int q = lookup_state(idx3, r, Px - s.x, Py - s.y, Pz - s.z, Sz - s.w, species);
-      v = (q > p) && ((p < N) == (q < N));
-      if (v && p < N) {
-        nh++;
-        v = false;
-      }
-    }
-    np += v;
-  }
-  nh = __reduce_add_sync(0xffffffffu, nh);
-  np = __reduce_add_sync(0xffffffffu, np);
-  if (lane == 0) {
-    cnt_hh[K] = nh;
-    cnt_pp[K] = np;
-  }
-}
-
-// One warp per cross key D: count ph rows (a >= N, i < N, n_a - n_i = D) and hp columns.
-__global__ void k_count_cross(const char4* __restrict__ nvec, const int* __restrict__ idx3,
-                              int r, int m, int M, int species, int nkeys, int N, int nsp,
-                              int* __restrict__ cnt_ph, int* __restrict__ cnt_hp) {
-  int K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (K >= nkeys) return;
-  int Dx, Dy, Dz, Ds;
-  decode_key(K, m, M, species, Dx, Dy, Dz, Ds);
-  int nph = 0, nhp = 0;
-  for (int p0 = 0; p0 < nsp; p0 += 32) {
-    int p = p0 + lane;
-    if (p < nsp) {
-      char4 s = nvec[p];
-      int q = lookup_state(idx3, r, s.x - Dx, s.y - Dy, s.z - Dz, s.w - Ds, species);
-      if (q >= 0) {
-        if (p >= N && q < N) nph++;
-        if (p < N && q >= N) nhp++;
-      }
-    }
-  }
-  nph = __reduce_add_sync(0xffffffffu, nph);
-  nhp = __reduce_add_sync(0xffffffffu, nhp);
-  if (lane == 0) {
-    cnt_ph[K] = nph;
-    cnt_hp[K] = nhp;
-  }
+// One thread per ordered pair (p, q) of a system's states.  Direct keys (total momentum and
+// charge label sum): restricted pairs p < q of one class, counted in cnt_hh (both holes,
+// index < N) or cnt_pp (both particles).  Cross keys (n_p - n_q and the label difference):
+// cnt_ph for p a particle and q a hole, cnt_hp for p a hole and q a particle.  Sums and
+// differences of two states' momenta lie in [-m, m] (m = 2r), and of two labels decode
+// uniquely (charge_slot), so every pair has a key.
+__global__ void k_count_pairs(const char4* __restrict__ nvec, int m, int M, int species, int N, int nsp,
+                              int* __restrict__ cnt_hh, int* __restrict__ cnt_pp, int* __restrict__ cnt_ph,
+                              int* __restrict__ cnt_hp) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)nsp * nsp) return;
+  const int p = (int)(e / nsp), q = (int)(e - (long)p * nsp);
+  const char4 a = nvec[p], b = nvec[q];
+  const bool hole_p = p < N, hole_q = q < N;
+  if (p < q && hole_p == hole_q)
+    atomicAdd((hole_p ? cnt_hh : cnt_pp) + encode_key(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w, m, M, species), 1);
+  if (hole_p != hole_q)
+    atomicAdd((hole_q ? cnt_ph : cnt_hp) + encode_key(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w, m, M, species), 1);
 }
 
 // ------------------------------------------------------------------------ channel fill
@@ -989,21 +948,28 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
     CUDA_TRY(cudaGetLastError());
   }
 
-  // ---- channel counts (GPU) and selection (host: keys with both classes, ascending)
+  // ---- channel counts (GPU, every system, one copy back) and selection (host: keys with
+  // both classes, ascending)
+  std::vector<long> key_off(nsys + 1, 0);
+  for (int k = 0; k < nsys; k++) key_off[k + 1] = key_off[k] + sys[k].nkeys;
+  int* dcnt = dalloc<int>(4 * key_off[nsys], scr[0].owned, s);
+  CUDA_TRY(cudaMemsetAsync(dcnt, 0, sizeof(int) * 4 * key_off[nsys], s));
+  for (int k = 0; k < nsys; k++) {
+    const SysInfo& S = sys[k];
+    int* c = dcnt + 4 * key_off[k];
+    const long npairs = (long)S.nsp * S.nsp;
+    k_count_pairs<<<(unsigned)((npairs + 255) / 256), 256, 0, s>>>(D.nvec + S.sp_off, S.m, S.M, S.species, S.N,
+                                                                  S.nsp, c, c + S.nkeys, c + 2 * S.nkeys,
+                                                                  c + 3 * S.nkeys);
+  }
+  CUDA_TRY(cudaGetLastError());
+  const std::vector<int> hcnt = d2h(dcnt, 4 * key_off[nsys], s);
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
-    int* c1 = dalloc<int>(S.nkeys, scr[k].owned, s);
-    int* c2 = dalloc<int>(S.nkeys, scr[k].owned, s);
-    int* c3 = dalloc<int>(S.nkeys, scr[k].owned, s);
-    int* c4 = dalloc<int>(S.nkeys, scr[k].owned, s);
-    int blocks = (S.nkeys * 32 + 255) / 256;
-    k_count_direct<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.species, S.nkeys,
-                                          S.N, S.nsp, c1, c2);
-    k_count_cross<<<blocks, 256, 0, s>>>(D.nvec + S.sp_off, scr[k].idx3, S.r, S.m, S.M, S.species, S.nkeys,
-                                         S.N, S.nsp, c3, c4);
-    CUDA_TRY(cudaGetLastError());
-    std::vector<int> hh = d2h(c1, S.nkeys, s), pp = d2h(c2, S.nkeys, s);
-    std::vector<int> ph = d2h(c3, S.nkeys, s), hp = d2h(c4, S.nkeys, s);
+    const int* hh = hcnt.data() + 4 * key_off[k];
+    const int* pp = hh + S.nkeys;
+    const int* ph = hh + 2 * S.nkeys;
+    const int* hp = hh + 3 * S.nkeys;
     std::vector<int> key2ch(S.nkeys, -1), key2x(S.nkeys, -1);
     for (int K = 0; K < S.nkeys; K++) {
       if (hh[K] > 0 && pp[K] > 0) {

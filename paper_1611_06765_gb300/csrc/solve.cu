@@ -73,6 +73,7 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   int it0 = 0;
   int status = pnm_run_loop(ctx, mixed ? PNM_PREC_BF16X3 : (PNM_PREC_FP64 | (o.terms << 4)), o.max_iter, 0,
                             o.host_loop, o.mix_alpha, &it0);
+  if (mixed) pnm_flip_copy_current(ctx, it0);
   CUDA_TRY(cudaEventRecord(e1, s));
   if (mixed && status == 1 && o.refine_sweeps > 0) {
     // exactly refine_sweeps FP64 updates, then (if the FP64 test has not passed by then)
