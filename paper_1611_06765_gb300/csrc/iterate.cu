@@ -1051,6 +1051,15 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
   int c = it.x, ng = it.w;
   int npp = D.ch_npp[c], nh = D.ch_nhh[c];
   int ab = it.z + threadIdx.x;
+  const bool col = ab < npp;
+  const bool has_vpp = D.ch_vpp[c] != 0;
+  // the column's pair data does not depend on the rows: loaded beside the row setup
+  int2 p = make_int2(0, 0);
+  int lmap = 0;
+  if (col) {
+    p = D.pp_pair[D.ch_pp_off[c] + ab];
+    if (has_vpp) lmap = D.lad_map[D.ch_pp_off[c] + ab];
+  }
   if ((int)threadIdx.x < UPD_ROWS) {
     int g = min((int)threadIdx.x, ng - 1);
     int ij = D.upd_row[it.y + g];
@@ -1060,6 +1069,15 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
     row_si[threadIdx.x] = D.nvec[h.x];
     row_sj[threadIdx.x] = D.nvec[h.y];
+  }
+  float dab = 0.0f;
+  double eab = 0.0;
+  char4 sa = make_char4(0, 0, 0, 0), sb = sa;
+  if (col) {
+    dab = D.dchi32[p.x] + D.dchi32[p.y];
+    eab = D.eps[p.x] + D.eps[p.y];
+    sa = D.nvec[p.x];
+    sb = D.nvec[p.y];
   }
   const bool frozen = fa.sc[D.ch_sys[c]].done != 0;
   if (sys_settled(fa.sc[D.ch_sys[c]], ctl)) {
@@ -1072,6 +1090,11 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     return;
   }
   __syncthreads();
+  const double* __restrict__ t = cur_t(D, ctl);
+  const float* __restrict__ t32 = cur_t32(D, ctl);
+  double* __restrict__ tn = next_t(D, ctl);
+  float* __restrict__ t32n = next_t32(D, ctl);
+  const long base = D.ch_t_off[c];
   if (!frozen) {
     const float* __restrict__ chi = D.chi32 + D.ch_vhh_off[c];
     for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
@@ -1080,16 +1103,10 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     }
   }
   __syncthreads();
-  const bool has_vpp = D.ch_vpp[c] != 0;
-  const double* __restrict__ t = cur_t(D, ctl);
-  const float* __restrict__ t32 = cur_t32(D, ctl);
-  double* __restrict__ tn = next_t(D, ctl);
-  float* __restrict__ t32n = next_t32(D, ctl);
-  const long base = D.ch_t_off[c];
   // energy and residual sums of the amplitudes whose spin flip is another amplitude (counted
   // twice) and of those that are their own flip (counted once)
   double e2 = 0.0, e1 = 0.0, r2 = 0.0, r1 = 0.0;
-  if (ab < npp) {
+  if (col) {
     float hh[UPD_ROWS];
 #pragma unroll
     for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0.0f;
@@ -1106,17 +1123,13 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
         hh[6] = fmaf(tk, c1.z, hh[6]); hh[7] = fmaf(tk, c1.w, hh[7]);
       }
     }
-    const int2 p = D.pp_pair[D.ch_pp_off[c] + ab];
-    const float dab = D.dchi32[p.x] + D.dchi32[p.y];
-    const double eab = D.eps[p.x] + D.eps[p.y];
-    const char4 sa = D.nvec[p.x], sb = D.nvec[p.y];
     const double* __restrict__ lut = D.lut + lut_off[D.ch_sys[c]];
     // the pp ladder's element in the ladder layout: s_off + ij * n_lad + |m| - 1, sign of m
     long lad0 = 0;
     int nl = 0;
     bool lneg = false;
     if (has_vpp) {
-      const int m = D.lad_map[D.ch_pp_off[c] + ab];
+      const int m = lmap;
       lneg = m < 0;
       nl = D.ch_nlad[c];
       lad0 = D.ch_s_off[c] + ((m > 0 ? m : -m) - 1);
