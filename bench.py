@@ -90,7 +90,7 @@ TOL_PER_N = 1e-6
 # DRAM bytes (read + write) per launch of the default workload from one ncu capture, with the
 # first 16 hex digits of the SHA-256 of the kernel's source file at the time of the capture:
 # reported only while that file is unchanged, else null.
-TRAFFIC = {}
+TRAFFIC = {"k_update_mix": (158600192.0, "e0dd2ebae2006f72"), "k_pp_tc": (257454080.0, "4dba9bd5a00d6728")}
 ALPHA = 0.5
 
 
@@ -276,6 +276,26 @@ def measured_traffic(kernel, workload):
     except OSError:
         return None
     return ent[0] if digest == ent[1] else None
+
+
+MIXED_KERNELS = ("k_update_mix", "k_ph32", "k_pp_tc", "k_tstats32", "k_pack", "k_dchi32")
+
+
+def work_fraction(ctx, kernel, iters, launches, mixed, refine_sweeps):
+    """Average fraction of the full batch that one launch of a kernel processes in a solve:
+    converged systems are skipped (the contractions from the update after the one that met the
+    tolerance, the update itself one update later, when both amplitude buffers hold the
+    values).  iters: updates per system (refinement sweeps included); launches: launches of the
+    kernel in the solve."""
+    import numpy as np
+    n = np.array([float((ctx.channels(s, 0)[1][:, 0] * ctx.channels(s, 0)[1][:, 1]).sum())
+                  for s in range(ctx.nsys)])
+    if (mixed and kernel not in MIXED_KERNELS) or kernel in ("k_dchi32", "k_dchi"):
+        return 1.0  # refinement sweeps (every system reopened); k_dchi never skips
+    m = np.array(iters, float) - (refine_sweeps if mixed else 0)
+    extra = 1 if kernel in ("k_update_mix", "k_update") else 0
+    act = np.minimum(m + extra, launches)
+    return float((n * act).sum() / (n.sum() * launches))
 
 
 def implementation_bytes(ctx, kernel):
@@ -709,13 +729,17 @@ def run_ours(a):
     # graph with a conditional node)
     ctx.set_profiling(True)
     torch.cuda.nvtx.range_push("host_driven_solve")
-    ctx.solve(host_loop=True, **solve_kw)
+    _, it_h, _, _ = ctx.solve(host_loop=True, **solve_kw)
     torch.cuda.nvtx.range_pop()
     stats = ctx.kernel_stats()
     ctx.set_profiling(False)
     kname, (ktot, kn) = max(stats.items(), key=lambda kv: kv[1][0])
     kavg_s = ktot / kn / 1e3
-    byts, flops = algorithmic_cost(ctx, kname)
+    # algorithmic cost of a launch over the full batch, scaled by the fraction of the batch the
+    # solve's launches process on average (converged systems are skipped)
+    byts_full, flops_full = algorithmic_cost(ctx, kname)
+    wfrac = work_fraction(ctx, kname, [int(x) for x in it_h], kn, prec_name != "fp64", solve_kw.get("refine_sweeps", 0))
+    byts, flops = byts_full * wfrac, flops_full * wfrac
     hbm, bf16, src = read_peaks()
     fp64_peak = P.measure_fma_peak(True, stream.cuda_stream)
     fp32_peak = P.measure_fma_peak(False, stream.cuda_stream)
@@ -733,22 +757,29 @@ def run_ours(a):
     traffic = measured_traffic(kname, a.workload)
     roof.update(frac=roof["achieved"] / roof["peak"], traffic=traffic, kernel=kname, kernel_avg_us=kavg_s * 1e6,
                 algorithmic_bytes=byts, algorithmic_flops=flops,
+                algorithmic_bytes_full_batch=byts_full, launch_work_fraction=wfrac, launches=kn,
+                traffic_basis="ncu DRAM read + write of one launch over the full batch (all systems active)",
                 measured_fma_peaks_tflops={"fp64": fp64_peak, "fp32": fp32_peak})
     ib = implementation_bytes(ctx, kname)
     if ib is not None:
-        roof["implementation_bytes"] = ib
-        roof["implementation_gbs"] = ib / kavg_s / 1e9
+        roof["implementation_bytes"] = ib * wfrac
+        roof["implementation_gbs"] = ib * wfrac / kavg_s / 1e9
     # the FP64 refinement contractions against the measured FP64 FMA rate
     for k in ("k_pp64", "k_ph64", "k_ph32", "k_pp_f2", "k_ph_f2"):
         if k in stats and k != kname:
             tk = stats[k][0] / stats[k][1] / 1e3
             bk, fk = algorithmic_cost(ctx, k)
+            fk *= work_fraction(ctx, k, [int(x) for x in it_h], stats[k][1], prec_name != "fp64",
+                                solve_kw.get("refine_sweeps", 0))
             pk = {"k_ph32": fp32_peak, "k_pp_f2": fp32_peak / 12, "k_ph_f2": fp32_peak / 12}.get(k, fp64_peak)
             roof[k] = {"bound": "alu", "achieved": fk / tk / 1e12, "peak": pk, "unit": "TFLOP/s",
                        "frac": fk / tk / 1e12 / pk, "kernel_avg_us": tk * 1e6}
     if "k_pp_tc" in stats and kname != "k_pp_tc":
         t_tc = stats["k_pp_tc"][0] / stats["k_pp_tc"][1] / 1e3
         b_tc, f_tc = algorithmic_cost(ctx, "k_pp_tc")
+        w_tc = work_fraction(ctx, "k_pp_tc", [int(x) for x in it_h], stats["k_pp_tc"][1], prec_name != "fp64",
+                             solve_kw.get("refine_sweeps", 0))
+        b_tc, f_tc = b_tc * w_tc, f_tc * w_tc
         roof["k_pp_tc"] = {"bound": "hbm", "achieved": b_tc / t_tc / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": b_tc / t_tc / 1e9 / hbm, "kernel_avg_us": t_tc * 1e6,
                            "traffic": measured_traffic("k_pp_tc", a.workload),

@@ -44,8 +44,9 @@ struct StatsIO {
 // Blocks [0, nrows): row (c, kl): sij[kl] = sum_ab t v; chi_hh[kl][ij] for the ij the updates
 // compute.
 // Blocks [nrows, ...): column chunk (c, ab0): sab[ab] = sum_ij t v.
-// PAIR (FP64 only): the chi_hh contraction in FP32-pair arithmetic from the pair copies tp of t
-// and vp of v_pphh (the refinement sweeps); the one-body sums, O(n_t), stay FP64.
+// PAIR (FP64 only): the contractions in FP32-pair arithmetic from the pair copies tp of t and vp
+// of v_pphh (the refinement sweeps): chi_hh, and the one-body sums as per-thread pair partials
+// added in FP64.
 template <typename T_, bool PAIR = false>
 __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __restrict__ ctl,
                                                 int nrows, const int2* __restrict__ ab_items,
@@ -63,7 +64,16 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
     const T_* tr = t + base + (long)kl * npp;
     const T_* vr = io.v + base + (long)kl * npp;
     T_ s = 0;
-    for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) s += tr[ab] * vr[ab];
+    if constexpr (PAIR) {
+      // per-thread partial sums in FP32 pairs, the block sum in FP64
+      const f2* __restrict__ tpr = tp + base + (long)kl * npp;
+      const f2* __restrict__ vpr = vp + base + (long)kl * npp;
+      f2 a2 = Arith<f2>::zero();
+      for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) Arith<f2>::mac(a2, tpr[ab], vpr[ab]);
+      s = Arith<f2>::to_double(a2);
+    } else {
+      for (int ab = threadIdx.x; ab < npp; ab += blockDim.x) s += tr[ab] * vr[ab];
+    }
     s = block_sum(s, sh32);
     if (threadIdx.x == 0) io.sij[D.ch_hh_off[c] + kl] = s;
     // chi is read only in the columns ij of the rows the updates compute (the list upd_row)
@@ -100,7 +110,13 @@ __global__ void __launch_bounds__(128) k_tstats(DevState D, const LoopCtl* __res
     if (ab < npp) {
       long base = D.ch_t_off[c] + ab;
       T_ s = 0;
-      for (int ij = 0; ij < nh; ij++) s += t[base + (long)ij * npp] * io.v[base + (long)ij * npp];
+      if constexpr (PAIR) {
+        f2 a2 = Arith<f2>::zero();
+        for (int ij = 0; ij < nh; ij++) Arith<f2>::mac(a2, tp[base + (long)ij * npp], vp[base + (long)ij * npp]);
+        s = Arith<f2>::to_double(a2);
+      } else {
+        for (int ij = 0; ij < nh; ij++) s += t[base + (long)ij * npp] * io.v[base + (long)ij * npp];
+      }
       io.sab[D.ch_pp_off[c] + ab] = s;
     }
   }
