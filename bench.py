@@ -7,14 +7,14 @@ Default workload, the one the metric's "mixed + learned" is defined on: N = 66 n
 plane waves with n^2 <= 36 (1850 states), Minnesota interaction, mixing 0.5, at the three
 held-out densities rho = 0.05, 0.11, 0.17 fm^-3, solved together in one batched context
 (every kernel launch covers the three systems).  A step is one converged solve of that batch
-from the learned start (the tensor-core inference of the network and the copy to the spin
-flips inside the timed region; the network's input features depend only on the context and
-are built once, by the first learned solve of the warm-up), the pp ladder in BF16x3 on the
-tensor cores, FP64 denominators / residual / energies, and two FP64 refinement sweeps at the
-end.  The network is trained before timing, by the library's
-own GPU kernels, on amplitudes the solver converges for N = 14 (n^2 <= 20, 16 densities
-0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.16).  Channel tables, interaction blocks and
-the model are resident in HBM before the timed region; L2 is flushed before every step.
+from the learned start (the tensor-core inference of the network, which forms each sample's
+features from the context in registers, and the copy to the spin flips, inside the timed
+region), the pp ladder in BF16x3 on the tensor cores, FP64 denominators / residual /
+energies, and two FP64 refinement sweeps at the end (their contractions in FP32 pairs).  The
+network is trained before timing, by the library's own GPU kernels, on amplitudes the solver
+converges for N = 14 (n^2 <= 20, 16 densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho =
+0.04, 0.08, 0.14, 0.16, 0.20).  Channel tables, interaction blocks and the model are resident
+in HBM before the timed region; L2 is flushed before every step.
 
 ``e2e`` times the public API from host inputs: context creation (basis, channels and V built
 on the GPU), model upload, solve, converged amplitudes copied back.  ``comparison`` holds the
