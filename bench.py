@@ -106,7 +106,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the comparison workloads")
     ap.add_argument("--model", default=None, help="load the warm-start network (.npy) instead of training it")
     ap.add_argument("--save-model", default=None, help="write the trained warm-start network (.npy)")
-    ap.add_argument("--train-epochs", type=int, default=20, help="warm-start training epochs")
+    ap.add_argument("--train-epochs", type=int, default=40, help="warm-start training epochs")
     ap.add_argument("--train-batch", type=int, default=1024, help="warm-start training batch")
     return ap.parse_args()
 
@@ -412,9 +412,10 @@ _model = {}
 def trained_model(P, stream):
     """Warm-start network trained by the library's GPU kernels on converged amplitudes of
     N = 14 (n^2 <= 20, 16 densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.04, 0.08,
-    0.14, 0.16, 0.20; the held-out 0.05, 0.11, 0.17 are not in the training set): 20 epochs,
+    0.14, 0.16, 0.20; the held-out 0.05, 0.11, 0.17 are not in the training set): 40 epochs,
     batch 1024, Adam with the learning rate decaying from 1e-3 to 1e-5 along a half cosine,
-    seeds 1 (initial weights) and 2 (shuffling); or the one given with --model."""
+    seeds 1 (initial weights) and 2 (shuffling), the matrix products on the tensor cores; or
+    the one given with --model."""
     if "blob" not in _model and _model.get("path"):
         import numpy as np
         _model["blob"] = np.load(_model["path"]).astype(np.float32)
@@ -425,7 +426,7 @@ def trained_model(P, stream):
         tr14.solve(**kw64)
         tr66 = P.Context(66, list(TRAIN66), 36, params=MINNESOTA, stream=stream.cuda_stream)
         tr66.solve(**kw64)
-        blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=_model.get("epochs", 20),
+        blob, hist = P.mlp_train([tr14, tr66], P.mlp_init(seed=1), epochs=_model.get("epochs", 40),
                                  batch=_model.get("batch", 1024), lr=1e-3, seed=2, lr_final=1e-5)
         tr14.close()
         tr66.close()

@@ -316,9 +316,11 @@ int pnm_mlp_features(pnm_ctx *ctx, int sys, float *X, double *t_mbpt2, double *s
 
 /* Train on the amplitudes currently held by the given contexts (after converged solves):
  * target (t - t_MBPT2) / sigma_sys.  Sets the blob's normalisation header from the data,
- * then runs Adam on the GPU (the library's forward/backward kernels).  blob: in = initial
- * parameters, out = trained.  loss_hist (nullable, cap entries) gets the mean loss per
- * epoch (in units of y_scale^2); *n_hist the number of epochs. */
+ * then runs Adam on the GPU (the library's forward/backward kernels; weights and layer inputs
+ * in BF16, the matrix products of both passes on the tcgen05 tensor cores).  blob: in =
+ * initial parameters, out = trained.  loss_hist (nullable, cap entries) gets the mean loss per
+ * epoch (in units of y_scale^2); *n_hist the number of epochs.  PNM_ETIMEOUT if a bounded wait
+ * of the tensor-core products ran out. */
 int pnm_mlp_train(pnm_ctx *const *ctxs, int nctx, const pnm_mlp_opts *opts, float *blob,
                   float *loss_hist, int cap, int *n_hist);
 
@@ -333,8 +335,8 @@ int pnm_mlp_set_model(pnm_ctx *ctx, const float *blob);
 int pnm_mlp_predict(pnm_ctx *ctx);
 
 /* Network output for n feature rows (host arrays).  mode: PNM_MLP_TENSOR_CORES runs the
- * fused tcgen05 inference kernel (the learned start's), PNM_MLP_SIMT the SIMT training
- * forward, PNM_MLP_SIMT_FP32 the same SIMT kernels with the BF16 rounding of weights and
+ * fused tcgen05 inference kernel (the learned start's), PNM_MLP_SIMT the training
+ * forward with its matrix products on the SIMT kernels, PNM_MLP_SIMT_FP32 the same SIMT kernels with the BF16 rounding of weights and
  * layer inputs switched off (a debug mode for element-wise checks against an FP64
  * reference).  stream: NULL = legacy stream. */
 #define PNM_MLP_SIMT 0
@@ -343,8 +345,12 @@ int pnm_mlp_predict(pnm_ctx *ctx);
 int pnm_mlp_forward(const float *blob, const float *X, long n, float *Y, int mode, void *stream);
 
 /* Mean squared error over n samples and its gradient (NPARAM floats, header entries 0)
- * from the library's GPU forward/backward kernels, for gradient checks.  fp32 = 1: the FP32
- * debug mode (same kernels, no BF16 rounding of weights or activations). */
+ * from the library's GPU forward/backward kernels, for gradient checks.  fp32 = 0: the BF16
+ * training mode (weights and layer inputs rounded to BF16) with the matrix products on the
+ * tcgen05 tensor cores, as pnm_mlp_train runs them (operands split into BF16 hi + lo, three
+ * products, FP32 accumulation); 1: the FP32 debug mode (SIMT kernels, no BF16 rounding of
+ * weights or activations); 2: the BF16 mode with the SIMT products.  PNM_ETIMEOUT if a bounded
+ * wait of the tensor-core kernel ran out. */
 int pnm_mlp_loss_grad(const float *blob, const float *X, const float *T, int n, float *loss,
                       float *grad, int fp32, void *stream);
 

@@ -305,14 +305,15 @@ def mlp_forward(blob, X, tensor_cores=True, fp32=False):
     return Y
 
 
-def mlp_loss_grad(blob, X, T, fp32=False):
+def mlp_loss_grad(blob, X, T, fp32=False, tensor_cores=True):
     """pnm_mlp_loss_grad: (mean squared error, gradient blob); fp32=True is the debug mode
-    without BF16 rounding."""
+    without BF16 rounding (SIMT products); in the BF16 mode tensor_cores selects the tcgen05
+    products that training uses (else the SIMT ones)."""
     blob = np.ascontiguousarray(blob, dtype=np.float32)
     X = np.ascontiguousarray(X, dtype=np.float32)
     T = np.ascontiguousarray(T, dtype=np.float32)
     g = np.zeros_like(blob)
     loss = C.c_float()
     _lib.check(_lib.load().pnm_mlp_loss_grad(_fptr(blob), _fptr(X), _fptr(T), X.shape[0], C.byref(loss),
-                                             _fptr(g), int(bool(fp32)), None))
+                                             _fptr(g), 1 if fp32 else (0 if tensor_cores else 2), None))
     return float(loss.value), g

@@ -214,6 +214,187 @@ void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, int tA,
   k_sgemm<<<g, 256, 0, s>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, acc);
 }
 
+// ------------------------------------------------------------ tensor-core training GEMM
+// The k_sgemm contract, C[M][N] (+)= op(A)[M][K] op(B)[K][N], on the tcgen05 tensor cores for the
+// BF16 training mode: each operand element is split as it is staged into BF16 hi + lo (exact for
+// the BF16-rounded weights and layer inputs, whose lo part is zero; 2^-18 relative for the FP32
+// error signals of the backward pass), three products per 16-wide k step (hi hi + hi lo +
+// lo hi) accumulate in FP32 in tensor memory.  One CTA (four warps) per 128 x bn tile of C and
+// k-range blockIdx.z (K split into gridDim.z ranges of whole 64-wide stages, results to
+// C + blockIdx.z * cz, summed in order by k_sum_splits); all threads stage a 64-wide k slice of
+// both operands into shared memory in the K-major core-matrix layout, thread 0 issues the MMAs
+// and commits them to an mbarrier (bounded wait: on timeout the CTA stops, writes nothing and
+// sets *err), and each thread drains its TMEM lane (row of C).
+constexpr int TG_BM = 128, TG_BN = 128, TG_BK = 64;
+constexpr int TG_PLANE_A = TG_BM * TG_BK, TG_PLANE_B = TG_BN * TG_BK;  // BF16 elements per plane
+constexpr size_t TG_SMEM = 1024 + 2 * (size_t)(TG_PLANE_A + TG_PLANE_B) * sizeof(__nv_bfloat16);
+constexpr int TG_MAX_SPLIT = 16, TG_BATCH = 16;
+
+__device__ __forceinline__ void tg_split(float x, __nv_bfloat16* hi, __nv_bfloat16* lo, int o) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  hi[o] = h;
+  lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, int lda, int tA,
+                                                 const float* __restrict__ B, int ldb, int tB,
+                                                 float* __restrict__ C, int ldc, long cz, int acc, int bn,
+                                                 int* __restrict__ err_flag) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 8);
+  __nv_bfloat16* Ah = reinterpret_cast<__nv_bfloat16*>(smem + 1024);
+  __nv_bfloat16* Al = Ah + TG_PLANE_A;
+  __nv_bfloat16* Bh = Al + TG_PLANE_A;
+  __nv_bfloat16* Bl = Bh + TG_PLANE_B;
+  __shared__ int bad;
+  const int m0 = blockIdx.y * TG_BM, n0 = blockIdx.x * bn;  // bn: 32, 64 or TG_BN columns per CTA
+  const int nt = min(bn, N - n0);
+  const int np = (nt + 15) & ~15;  // the MMA's N: a multiple of 16
+  // this CTA's k-range: whole stages
+  const int nstage = (K + TG_BK - 1) / TG_BK;
+  const int per = (nstage + gridDim.z - 1) / gridDim.z;
+  const int kb = blockIdx.z * per * TG_BK, ke = min(K, (int)(blockIdx.z + 1) * per * TG_BK);
+  float* __restrict__ Cz = C + blockIdx.z * cz;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(tslot, 128);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t idesc = tc::idesc_bf16(TG_BM, np);
+  const uint32_t sbo = (TG_BK / 8) * 128;
+  uint32_t phase = 0, fail_parity = 0;
+  bool issued = false;
+  for (int k0 = kb; k0 < ke; k0 += TG_BK) {
+    __syncthreads();
+    const int stop = bad;
+    __syncthreads();
+    if (stop) break;
+    // coalesced along each operand's contiguous index; TG_BATCH independent loads in flight
+    // per thread before their splits are stored
+    for (int e0 = 0; e0 < TG_BM * TG_BK; e0 += TG_BATCH * 128) {
+      float x[TG_BATCH];
+#pragma unroll
+      for (int j = 0; j < TG_BATCH; j++) {
+        const int e = e0 + j * 128 + threadIdx.x;
+        const int r = tA ? e % TG_BM : e / TG_BK, k = tA ? e / TG_BM : e % TG_BK;
+        const int m = m0 + r, kk = k0 + k;
+        x[j] = (m < M && kk < ke) ? (tA ? A[(long)kk * lda + m] : A[(long)m * lda + kk]) : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < TG_BATCH; j++) {
+        const int e = e0 + j * 128 + threadIdx.x;
+        const int r = tA ? e % TG_BM : e / TG_BK, k = tA ? e / TG_BM : e % TG_BK;
+        tg_split(x[j], Ah, Al, tc::core_off(r, k, TG_BK / 8));
+      }
+    }
+    for (int e0 = 0; e0 < np * TG_BK; e0 += TG_BATCH * 128) {
+      float x[TG_BATCH];
+#pragma unroll
+      for (int j = 0; j < TG_BATCH; j++) {
+        const int e = e0 + j * 128 + threadIdx.x;
+        const int r = tB ? e / TG_BK : e % np, k = tB ? e % TG_BK : e / np;
+        const int kk = k0 + k;
+        x[j] = (e < np * TG_BK && r < nt && kk < ke)
+                   ? (tB ? B[(long)(n0 + r) * ldb + kk] : B[(long)kk * ldb + n0 + r])
+                   : 0.0f;
+      }
+#pragma unroll
+      for (int j = 0; j < TG_BATCH; j++) {
+        const int e = e0 + j * 128 + threadIdx.x;
+        if (e < np * TG_BK) {
+          const int r = tB ? e / TG_BK : e % np, k = tB ? e % TG_BK : e / np;
+          tg_split(x[j], Bh, Bl, tc::core_off(r, k, TG_BK / 8));
+        }
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0) {
+      for (int ks = 0; ks < TG_BK / 16; ks++) {
+        const uint64_t ah = tc::smem_desc(reinterpret_cast<const unsigned char*>(Ah) + ks * 256, 128, sbo);
+        const uint64_t al = tc::smem_desc(reinterpret_cast<const unsigned char*>(Al) + ks * 256, 128, sbo);
+        const uint64_t bh = tc::smem_desc(reinterpret_cast<const unsigned char*>(Bh) + ks * 256, 128, sbo);
+        const uint64_t bl = tc::smem_desc(reinterpret_cast<const unsigned char*>(Bl) + ks * 256, 128, sbo);
+        tc::mma_bf16(tbase, ah, bh, idesc, (issued || ks > 0) ? 1u : 0u);
+        tc::mma_bf16(tbase, ah, bl, idesc, 1u);
+        tc::mma_bf16(tbase, al, bh, idesc, 1u);
+      }
+      tc::commit(bar);
+    }
+    issued = true;
+    __syncwarp();
+    // every thread waits: the next stage overwrites the operands the MMAs read
+    if (!tc::mbar_wait(bar, phase & 1)) {
+      bad = 1;
+      fail_parity = phase & 1;
+    }
+    phase++;
+    tc::fence_after();
+  }
+  __syncthreads();
+  const int ok = !bad;
+  // after a wait that ran out, give the MMAs still in flight one more bounded wait before the
+  // tensor memory they write is freed
+  if (!ok && threadIdx.x == 0) tc::mbar_wait(bar, fail_parity);
+  // epilogue through shared memory (the operand planes are free once the last wait passed), 64
+  // columns at a time: thread = TMEM lane = row of the tile into Cs, then rows of C written with
+  // consecutive threads on consecutive columns (an empty k-range leaves zeros)
+  constexpr int CS_LD = 65;
+  float* Cs = reinterpret_cast<float*>(smem + 1024);  // 128 x CS_LD floats
+  const int r = threadIdx.x;
+  const uint32_t lane_addr = tbase + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+  for (int c0 = 0; c0 < np; c0 += 64) {
+    const int cw = min(64, np - c0);
+    __syncthreads();
+    if (ok) {
+      for (int cc = 0; cc < cw; cc += 16) {
+        uint32_t v[16];
+        tc::tmem_ld16(lane_addr + c0 + cc, v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) Cs[r * CS_LD + cc + j] = issued ? __uint_as_float(v[j]) : 0.0f;
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      for (int e = threadIdx.x; e < TG_BM * cw; e += blockDim.x) {
+        const int rr = e / cw, c = e % cw;
+        const int m = m0 + rr, n = c0 + c;
+        if (m < M && n < nt) {
+          float* dst = Cz + (long)m * ldc + n0 + n;
+          const float y = Cs[rr * CS_LD + c];
+          *dst = acc ? *dst + y : y;
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 128);
+  if (threadIdx.x == 0 && !ok) atomicExch(err_flag, 1);
+}
+
+// C (+)= sum over z of W[z] (M x N, row stride N), in the order z = 0, 1, ...
+__global__ void k_sum_splits(const float* __restrict__ W, int nz, int M, int N, float* __restrict__ C, int ldc,
+                             int acc) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)M * N) return;
+  const int m = (int)(e / N), n = (int)(e % N);
+  float s = acc ? C[(long)m * ldc + n] : 0.0f;
+  for (int z = 0; z < nz; z++) s += W[(long)z * M * N + e];
+  C[(long)m * ldc + n] = s;
+}
+
 // h0 = bf16((x - mu) * inv_std) for the rows idx[0..B) of X (rnd = 0: FP32 debug mode, no
 // BF16 rounding).
 __global__ void k_prep(const float* __restrict__ X, const int* __restrict__ idx, int B,
@@ -265,11 +446,16 @@ __global__ void k_dz(const float* __restrict__ dH, const float* __restrict__ Z, 
 }
 
 // Column sums of a (B x ncol) matrix into g (fixed order per column).
-__global__ void k_colsum(const float* __restrict__ A, int B, int ncol, float* __restrict__ g) {
+// g[col] = sum_r w[r] A[r][col] (w == nullptr: w = 1), one block per column.
+__global__ void k_colsum(const float* __restrict__ A, int B, int ncol, float* __restrict__ g,
+                         const float* __restrict__ w = nullptr) {
   __shared__ float sh[256];
   int col = blockIdx.x;
   float s = 0.0f;
-  for (int r = threadIdx.x; r < B; r += blockDim.x) s += A[(long)r * ncol + col];
+  if (w)
+    for (int r = threadIdx.x; r < B; r += blockDim.x) s = fmaf(w[r], A[(long)r * ncol + col], s);
+  else
+    for (int r = threadIdx.x; r < B; r += blockDim.x) s += A[(long)r * ncol + col];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -599,8 +785,22 @@ struct Net {
   float *w, *q, *g, *m, *v;  // parameters, BF16-rounded copy, gradient, Adam moments
   float *H0, *Z1, *H1, *Z2, *H2, *Z3, *H3, *Y, *dY, *dA, *dB;
   int B;
-  void alloc(int b, Scratch& s) {
+  // tc = 1: the matrix products on the tensor cores (k_gemm_tc; BF16 mode only); ws holds the
+  // partial tiles of a k-split product, err the kernel's timeout flag
+  int tc = 0;
+  float* ws = nullptr;
+  long ws_cap = 0;
+  int* err = nullptr;
+  void alloc(int b, Scratch& s, int use_tc = 0, cudaStream_t st = nullptr) {
     B = b;
+    tc = use_tc;
+    if (tc) {
+      ws_cap = (long)TG_MAX_SPLIT * std::max(b, MH) * MH;
+      ws = xalloc<float>(ws_cap, s.owned);
+      err = xalloc<int>(1, s.owned);
+      CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+      smem_at_least(k_gemm_tc, TG_SMEM);
+    }
     w = xalloc<float>(NPARAM, s.owned);
     q = xalloc<float>(NPARAM, s.owned);
     g = xalloc<float>(NPARAM, s.owned);
@@ -620,32 +820,59 @@ struct Net {
   }
 };
 
+// A matrix product of the training passes: on the tensor cores when nt.tc is set and both output
+// dimensions are at least 16 (the output layer's vector products stay on k_sgemm), with the k
+// range split over up to TG_MAX_SPLIT CTAs when the output has few tiles.
+void gemm(cudaStream_t s, const Net& nt, int M, int N, int K, const float* A, int lda, int tA, const float* B,
+          int ldb, int tB, float* C, int ldc, int acc) {
+  if (!nt.tc || M < 16 || N < 16) {
+    sgemm(s, M, N, K, A, lda, tA, B, ldb, tB, C, ldc, acc);
+    return;
+  }
+  // about 64 CTAs: narrower column tiles first (the row tiles are fixed at 128), then the k split
+  const int gy = (M + TG_BM - 1) / TG_BM;
+  int bn = TG_BN;
+  while (bn > 32 && ((N + bn - 1) / bn) * gy < 64) bn >>= 1;
+  const int gx = (N + bn - 1) / bn;
+  const int nstage = (K + TG_BK - 1) / TG_BK;
+  int kz = 1;
+  if (gx * gy < 64) kz = std::max(1, std::min(std::min(TG_MAX_SPLIT, nstage), 64 / (gx * gy)));
+  while (kz > 1 && (long)kz * M * N > nt.ws_cap) kz--;
+  if (kz == 1) {
+    k_gemm_tc<<<dim3(gx, gy, 1), 128, TG_SMEM, s>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, 0, acc, bn, nt.err);
+  } else {
+    k_gemm_tc<<<dim3(gx, gy, kz), 128, TG_SMEM, s>>>(M, N, K, A, lda, tA, B, ldb, tB, nt.ws, N, (long)M * N, 0,
+                                                     bn, nt.err);
+    k_sum_splits<<<(unsigned)(((long)M * N + 255) / 256), 256, 0, s>>>(nt.ws, kz, M, N, C, ldc, acc);
+  }
+}
+
 // rnd = 0: the FP32 debug mode (no BF16 rounding of the layer inputs).
 void net_forward(cudaStream_t s, Net& nt, const float* X, const int* idx, int B, int rnd = 1) {
   k_prep<<<(B * MF + 255) / 256, 256, 0, s>>>(X, idx, B, nt.q, nt.H0, rnd);
-  sgemm(s, B, MH, MF, nt.H0, MF, 0, nt.q + O_W1, MF, 1, nt.Z1, MH, 0);
+  gemm(s, nt, B, MH, MF, nt.H0, MF, 0, nt.q + O_W1, MF, 1, nt.Z1, MH, 0);
   k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z1, nt.q + O_B1, nt.H1, B, rnd);
-  sgemm(s, B, MH, MH, nt.H1, MH, 0, nt.q + O_W2, MH, 1, nt.Z2, MH, 0);
+  gemm(s, nt, B, MH, MH, nt.H1, MH, 0, nt.q + O_W2, MH, 1, nt.Z2, MH, 0);
   k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z2, nt.q + O_B2, nt.H2, B, rnd);
-  sgemm(s, B, MH, MH, nt.H2, MH, 0, nt.q + O_W3, MH, 1, nt.Z3, MH, 0);
+  gemm(s, nt, B, MH, MH, nt.H2, MH, 0, nt.q + O_W3, MH, 1, nt.Z3, MH, 0);
   k_bias_gelu<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.Z3, nt.q + O_B3, nt.H3, B, rnd);
 }
 
 // Backward pass from dY; writes the gradient blob nt.g (header entries zero).
 void net_backward(cudaStream_t s, Net& nt, int B) {
   CUDA_TRY(cudaMemsetAsync(nt.g, 0, sizeof(float) * NPARAM, s));
-  // output layer: dw4 = dY^T H3, db4 = sum dY, dH3 = dY w4
-  sgemm(s, 1, MH, B, nt.dY, 1, 1, nt.H3, MH, 0, nt.g + O_W4, MH, 0);
+  // output layer: dw4 = dY^T H3 (a weighted column sum), db4 = sum dY, dH3 = dY w4
+  k_colsum<<<MH, 256, 0, s>>>(nt.H3, B, MH, nt.g + O_W4, nt.dY);
   k_colsum<<<1, 256, 0, s>>>(nt.dY, B, 1, nt.g + O_B4);
-  sgemm(s, B, MH, 1, nt.dY, 1, 0, nt.q + O_W4, MH, 0, nt.dA, MH, 0);
+  gemm(s, nt, B, MH, 1, nt.dY, 1, 0, nt.q + O_W4, MH, 0, nt.dA, MH, 0);
   const float* Zs[3] = {nt.Z1, nt.Z2, nt.Z3};
   const float* Hin[3] = {nt.H0, nt.H1, nt.H2};
   const int Ow[3] = {O_W1, O_W2, O_W3}, Ob[3] = {O_B1, O_B2, O_B3}, Kin[3] = {MF, MH, MH};
   for (int l = 2; l >= 0; l--) {
     k_dz<<<(B * MH + 255) / 256, 256, 0, s>>>(nt.dA, Zs[l], nt.dB, B * MH);
-    sgemm(s, MH, Kin[l], B, nt.dB, MH, 1, Hin[l], Kin[l], 0, nt.g + Ow[l], Kin[l], 0);
+    gemm(s, nt, MH, Kin[l], B, nt.dB, MH, 1, Hin[l], Kin[l], 0, nt.g + Ow[l], Kin[l], 0);
     k_colsum<<<MH, 256, 0, s>>>(nt.dB, B, MH, nt.g + Ob[l]);
-    if (l > 0) sgemm(s, B, MH, MH, nt.dB, MH, 0, nt.q + Ow[l], MH, 0, nt.dA, MH, 0);
+    if (l > 0) gemm(s, nt, B, MH, MH, nt.dB, MH, 0, nt.q + Ow[l], MH, 0, nt.dA, MH, 0);
   }
 }
 
@@ -955,9 +1182,10 @@ int pnm_mlp_loss_grad(const float* blob, const float* X, const float* T, int n, 
     if (!blob || !X || !T || n <= 0) throw PnmError{PNM_EINVAL, "bad argument"};
     check_blob_header(blob);
     cudaStream_t s = (cudaStream_t)stream;
+    if (fp32 < 0 || fp32 > 2) throw PnmError{PNM_EINVAL, "unknown gradient mode"};
     Scratch sc;
     Net nt;
-    nt.alloc(n, sc);
+    nt.alloc(n, sc, fp32 == 0 ? 1 : 0, s);  // 0: BF16 on the tensor cores, 2: BF16 on k_sgemm
     float* dX = xalloc<float>((size_t)n * MF, sc.owned);
     float* dT = xalloc<float>(n, sc.owned);
     double* lacc = xalloc<double>(1, sc.owned);
@@ -965,16 +1193,19 @@ int pnm_mlp_loss_grad(const float* blob, const float* X, const float* T, int n, 
     CUDA_TRY(cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)n * MF, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(dT, T, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemsetAsync(lacc, 0, sizeof(double), s));
-    const int rnd = fp32 ? 0 : 1;
+    const int rnd = fp32 == 1 ? 0 : 1;
     k_quantize<<<(NPARAM + 255) / 256, 256, 0, s>>>(nt.w, nt.q, rnd);
     net_forward(s, nt, dX, nullptr, n, rnd);
     k_out<<<(n * 32 + 255) / 256, 256, 0, s>>>(nt.H3, nt.q + O_W4, nt.q + O_B4, dT, nullptr, n, nt.Y, nt.dY, lacc);
     net_backward(s, nt, n);
     CUDA_TRY(cudaGetLastError());
     double l = 0;
+    int h_err = 0;
     CUDA_TRY(cudaMemcpyAsync(&l, lacc, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (grad) CUDA_TRY(cudaMemcpyAsync(grad, nt.g, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
+    if (nt.err) CUDA_TRY(cudaMemcpyAsync(&h_err, nt.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err) throw PnmError{PNM_ETIMEOUT, "a device-side wait of the training products ran out of its budget"};
     if (loss) *loss = (float)(l / n);
     return PNM_OK;
   } catch (const PnmError& e) {
@@ -1036,7 +1267,7 @@ int pnm_mlp_train(pnm_ctx* const* ctxs, int nctx, const pnm_mlp_opts* o, float* 
     }
     int B = (int)std::min<long>(o->batch, ntot);
     Net nt;
-    nt.alloc(B, sc);
+    nt.alloc(B, sc, 1, s);  // BF16 training: the matrix products on the tensor cores
     int* idx = xalloc<int>(ntot, sc.owned);
     double* lacc = xalloc<double>(1, sc.owned);
     CUDA_TRY(cudaMemcpyAsync(nt.w, blob, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s));
@@ -1071,8 +1302,11 @@ int pnm_mlp_train(pnm_ctx* const* ctxs, int nctx, const pnm_mlp_opts* o, float* 
       }
       CUDA_TRY(cudaGetLastError());
       double l = 0;
+      int h_err = 0;
       CUDA_TRY(cudaMemcpyAsync(&l, lacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(&h_err, nt.err, sizeof(int), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
+      if (h_err) throw PnmError{PNM_ETIMEOUT, "a device-side wait of the training products ran out of its budget"};
       if (loss_hist && nh < cap) loss_hist[nh] = (float)(l / std::max(1L, nb * B));
       nh++;
     }

