@@ -24,6 +24,11 @@
 
 #include "pnm_context.cuh"
 
+#ifndef PNM_UPD_HH_UNROLL
+#define PNM_UPD_HH_UNROLL 4
+#endif
+constexpr int UPD_HH_UNROLL = PNM_UPD_HH_UNROLL;  // loads of the mixed update's hh-ladder pass in flight
+
 
 // ----------------------------------------------------------------------------- stats
 // Element type T_: double for the FP64 iteration (t, v_pphh, v_hhhh, chi_hh, sij, sab), float
@@ -916,17 +921,16 @@ __global__ void __launch_bounds__(128) k_update(DevState D, LoopCtl* __restrict_
   double* __restrict__ tn = next_t(D, ctl);
   long base = D.ch_t_off[c];
   long vho = D.ch_vhh_off[c];
+  const UpdRow* __restrict__ rt = D.upd_rowinfo + (long)blockIdx.x * UPD_ROWS;
   if ((int)threadIdx.x < UPD_ROWS) {
-    int g = min((int)threadIdx.x, ng - 1);
-    int ij = D.upd_row[it.y + g];
-    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-    row_ij[threadIdx.x] = ij;
-    row_dij[threadIdx.x] = D.dchi[h.x] + D.dchi[h.y];
+    const UpdRow ri = rt[threadIdx.x];
+    row_ij[threadIdx.x] = ri.ij;
+    row_dij[threadIdx.x] = D.dchi[ri.hx] + D.dchi[ri.hy];
   }
-  __syncthreads();
+  // chi's columns of the item's rows from the row table (one barrier covers both)
   for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
     int kl = e / UPD_ROWS, g = e % UPD_ROWS;
-    chs[kl][g] = g < ng ? A::from_double(D.chi_hh[vho + (long)kl * nh + row_ij[g]]) : A::zero();
+    chs[kl][g] = g < ng ? A::from_double(D.chi_hh[vho + (long)kl * nh + rt[g].ij]) : A::zero();
   }
   __syncthreads();
   double esum = 0.0, rsum = 0.0;
@@ -1076,15 +1080,14 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     p = D.pp_pair[D.ch_pp_off[c] + ab];
     if (has_vpp) lmap = D.lad_map[D.ch_pp_off[c] + ab];
   }
+  const UpdRow* __restrict__ rt = D.upd_rowinfo + (long)blockIdx.x * UPD_ROWS;
   if ((int)threadIdx.x < UPD_ROWS) {
-    int g = min((int)threadIdx.x, ng - 1);
-    int ij = D.upd_row[it.y + g];
-    int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
-    row_ij[threadIdx.x] = ij;
-    row_dij[threadIdx.x] = D.dchi32[h.x] + D.dchi32[h.y];
-    row_eij[threadIdx.x] = D.eps[h.x] + D.eps[h.y];
-    row_si[threadIdx.x] = D.nvec[h.x];
-    row_sj[threadIdx.x] = D.nvec[h.y];
+    const UpdRow ri = rt[threadIdx.x];
+    row_ij[threadIdx.x] = ri.ij;
+    row_dij[threadIdx.x] = D.dchi32[ri.hx] + D.dchi32[ri.hy];
+    row_eij[threadIdx.x] = ri.eij;
+    row_si[threadIdx.x] = ri.si;
+    row_sj[threadIdx.x] = ri.sj;
   }
   float dab = 0.0f;
   double eab = 0.0;
@@ -1105,20 +1108,21 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     last_block_finalize(fa, ctl);
     return;
   }
+  // chi's columns of the item's rows, their indices read from the row table (no wait for the
+  // row setup above: one barrier covers both)
+  if (!frozen) {
+    const float* __restrict__ chi = D.chi32 + D.ch_vhh_off[c];
+    for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
+      const int kl = e / UPD_ROWS, g = e % UPD_ROWS;
+      chs[e] = g < ng ? chi[(long)kl * nh + rt[g].ij] : 0.0f;
+    }
+  }
   __syncthreads();
   const double* __restrict__ t = cur_t(D, ctl);
   const float* __restrict__ t32 = cur_t32(D, ctl);
   double* __restrict__ tn = next_t(D, ctl);
   float* __restrict__ t32n = next_t32(D, ctl);
   const long base = D.ch_t_off[c];
-  if (!frozen) {
-    const float* __restrict__ chi = D.chi32 + D.ch_vhh_off[c];
-    for (int e = threadIdx.x; e < nh * UPD_ROWS; e += blockDim.x) {
-      const int kl = e / UPD_ROWS, g = e % UPD_ROWS;
-      chs[e] = g < ng ? chi[(long)kl * nh + row_ij[g]] : 0.0f;
-    }
-  }
-  __syncthreads();
   // energy and residual sums of the amplitudes whose spin flip is another amplitude (counted
   // twice) and of those that are their own flip (counted once)
   double e2 = 0.0, e1 = 0.0, r2 = 0.0, r1 = 0.0;
@@ -1128,7 +1132,7 @@ __global__ void __launch_bounds__(128, UPD_MIN_BLOCKS) k_update_mix(DevState D, 
     for (int g = 0; g < UPD_ROWS; g++) hh[g] = 0.0f;
     if (!frozen) {
       const float* __restrict__ tc = t32 + base + ab;
-#pragma unroll 4
+#pragma unroll UPD_HH_UNROLL
       for (int kl = 0; kl < nh; kl++) {
         const float tk = tc[(long)kl * npp];
         const float4 c0 = *reinterpret_cast<const float4*>(chs + kl * UPD_ROWS);
@@ -1405,6 +1409,24 @@ __global__ void k_start(const double* __restrict__ parts, const int* __restrict_
 
 static void* dmalloc(pnm_ctx* ctx, size_t bytes) { return pnm_ctx_alloc(ctx, bytes); }
 
+// Static row data of the update items: row g of item i is the (min(g, ng - 1))-th row of its run.
+__global__ void k_rowinfo(DevState D, const int4* __restrict__ items, UpdRow* __restrict__ out) {
+  const int g = threadIdx.x;
+  if (g >= UPD_ROWS) return;
+  const int4 it = items[blockIdx.x];
+  const int c = it.x, ij = D.upd_row[it.y + min(g, it.w - 1)];
+  const int2 h = D.hh_pair[D.ch_hh_off[c] + ij];
+  UpdRow r;
+  r.ij = ij;
+  r.hx = h.x;
+  r.hy = h.y;
+  r.pad = 0;
+  r.si = D.nvec[h.x];
+  r.sj = D.nvec[h.y];
+  r.eij = D.eps[h.x] + D.eps[h.y];
+  out[(long)blockIdx.x * UPD_ROWS + g] = r;
+}
+
 void pnm_prepare_iteration(pnm_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   int nsys = (int)ctx->sys.size();
@@ -1500,6 +1522,8 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   std::vector<int4> grp;
   std::vector<int> glo(nsys), ghi(nsys);
   group_items(G, &grp, &glo, &ghi);
+  // static row data of every update item, filled on the device (pairs and energies live there)
+  ctx->d.upd_rowinfo = (UpdRow*)dmalloc(ctx, sizeof(UpdRow) * UPD_ROWS * std::max<size_t>(1, grp.size()));
   ctx->upd_rows = G;
   ctx->max_npp = max_npp;
   ctx->max_nlad = max_nlad;
@@ -1550,9 +1574,12 @@ void pnm_prepare_iteration(pnm_ctx* ctx) {
   ctx->upd_hi_d = ud + nsys;
   ctx->n_grp_items = (int)grp.size();
   ctx->grp_items = (int4*)dmalloc(ctx, sizeof(int4) * std::max<size_t>(1, grp.size()));
-  if (!grp.empty())
+  if (!grp.empty()) {
     CUDA_TRY(cudaMemcpyAsync(ctx->grp_items, grp.data(), sizeof(int4) * grp.size(),
                              cudaMemcpyHostToDevice, s));
+    k_rowinfo<<<(unsigned)grp.size(), 32, 0, s>>>(ctx->d, ctx->grp_items, ctx->d.upd_rowinfo);
+    CUDA_TRY(cudaGetLastError());
+  }
   int* gd = (int*)dmalloc(ctx, sizeof(int) * 2 * nsys);
   CUDA_TRY(cudaMemcpyAsync(gd, glo.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(gd + nsys, ghi.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, s));

@@ -55,6 +55,14 @@ struct SysInfo {
   double phi[3];          // twist theta / (2 pi) per axis; all zero = periodic
 };
 
+// Static data of one row (hole pair ij) of an update item: the pair's states, their spin labels
+// and eps_i + eps_j, so that an update's row setup is one load and the one-body gathers.
+struct __align__(16) UpdRow {
+  int ij, hx, hy, pad;
+  char4 si, sj;
+  double eij;
+};
+
 // Device arena pointers; all arrays are global over the systems of the context.
 struct DevState {
   // states
@@ -92,6 +100,7 @@ struct DevState {
   // a run of this list (items hold (channel, first entry, first column, rows))
   int* upd_row;
   int* ch_uoff;          // per direct channel its run of upd_row (nch + 1 offsets)
+  UpdRow* upd_rowinfo;   // per update item UPD_ROWS rows (rows past the item's last repeat it)
   // maps
   int* xmap;             // per T element: sign * (t index + 1), 0 = structurally zero
   int4* qmap;            // per t element: the four Q positions of P(ij)P(ab) Q (formed positions)
