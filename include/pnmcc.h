@@ -280,7 +280,7 @@ int pnm_apply_ph_term(pnm_ctx *ctx, int sys, int precision, const double *t, dou
  * ms[5] = 1 if the last solve with init = PNM_INIT_MLP fell back to the MBPT2 start, else 0;
  * ms[6] host wall time (ms) that the last pnm_ccd_solve spent on the context's one-time
  * preparation (FP32 and FP32-pair copies, schedule tuning, capture and instantiation of the
- * iteration graphs); 0 when all of it was done by an earlier solve of the context.
+ * iteration graphs); about 0 when all of it was done by an earlier solve of the context.
  * The first min(n, 7) entries are written. */
 int pnm_get_timings(const pnm_ctx *ctx, double *ms, int n);
 

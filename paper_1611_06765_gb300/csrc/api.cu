@@ -84,6 +84,8 @@ static void release(pnm_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
   for (auto& g : ctx->graph_defs) cudaGraphDestroy(g.second);
+  pnm_drop_solve_graphs(ctx);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   pnm_free_mixed(ctx);
   pnm_free_mlp(ctx);
   for (void* p : ctx->owned) pnm_pool_free(ctx->stream, p);

@@ -2011,7 +2011,7 @@ static bool is_ph_kernel(const void* f) {
          f == (const void*)k_ph_big<float, ph_tile<float>()> || f == (const void*)k_ph_big<f2, 2>;
 }
 
-static void set_node_priorities(cudaGraph_t body) {
+void pnm_set_node_priorities(cudaGraph_t body) {
   int least = 0, greatest = 0;
   CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   size_t n = 0;
@@ -2058,7 +2058,7 @@ static cudaGraphExec_t graph_for(pnm_ctx* ctx, int mode) {
   }
   cudaGraph_t captured;
   CUDA_TRY(cudaStreamEndCapture(ctx->stream, &captured));
-  set_node_priorities(body);
+  pnm_set_node_priorities(body);
   cudaGraphExec_t ge;
   CUDA_TRY(cudaGraphInstantiate(&ge, g, cudaGraphInstantiateFlagUseNodePriority));
   ctx->graphs[mode] = ge;
@@ -2147,6 +2147,111 @@ void pnm_settle_amplitudes(pnm_ctx* ctx) {
     CUDA_TRY(cudaMemcpyAsync(&ctx->ctl->iter, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   }
   ctx->last_iters_host = it;
+}
+
+// ------------------------------------------------- device-side steps of a whole-solve graph
+// Start of a solve: every system's control block cleared with its tolerance; kernels do not
+// skip converged systems until the loop begins.
+__global__ void k_solve_begin(SysCtl* __restrict__ sc, const double* __restrict__ tol, int nsys,
+                              LoopCtl* __restrict__ ctl) {
+  for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
+    SysCtl z = {};
+    z.tol = tol[k];
+    sc[k] = z;
+  }
+  if (threadIdx.x == 0) ctl->skip_done = 0;
+}
+
+// Parameters of the first iteration loop (what pnm_run_loop sets from the host).
+__global__ void k_loop_begin(LoopCtl* __restrict__ ctl, const SolveParams* __restrict__ par, int mode) {
+  ctl->max_iter = par->max_iter;
+  ctl->min_iter = 0;
+  ctl->alpha = par->alpha;
+  ctl->mode = mode;
+  ctl->skip_done = 1;
+}
+
+// After the mixed loop: if it converged, reopen every system for exactly refine_sweeps FP64
+// updates and then the FP64 test (within max_iter more) and run the refinement loop; else
+// skip it (the loop status stays the mixed loop's).
+__global__ void k_refine_gate(LoopCtl* __restrict__ ctl, SysCtl* __restrict__ sc, int nsys,
+                              const SolveParams* __restrict__ par, cudaGraphConditionalHandle h) {
+  const bool go = ctl->status == 1;
+  if (go) {
+    for (int k = 0; k < nsys; k++) sc[k].done = 0;
+    const int it0 = ctl->iter;
+    ctl->status = 0;
+    ctl->max_iter = it0 + par->refine_sweeps + par->max_iter;
+    ctl->min_iter = it0 + par->refine_sweeps;
+    ctl->mode = 0;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_loop_end(LoopCtl* __restrict__ ctl) { ctl->skip_done = 0; }
+
+// t0 = the latest amplitudes (the loop leaves them in t[iter & 1]); the iteration parity is
+// reset by k_settle_reset once every block has copied.
+__global__ void k_settle_copy(DevState D, const LoopCtl* __restrict__ ctl, long n) {
+  if (!(ctl->iter & 1)) return;
+  for (long z = (long)blockIdx.x * blockDim.x + threadIdx.x; z < n; z += (long)gridDim.x * blockDim.x)
+    D.t0[z] = D.t1[z];
+}
+__global__ void k_settle_reset(LoopCtl* __restrict__ ctl) {
+  if (ctl->iter & 1) ctl->iter = 0;
+}
+
+// The spin flips of the current FP64 amplitudes, the buffer chosen on the device.
+__global__ void k_flip_copy_cur(DevState D, const LoopCtl* __restrict__ ctl, long n) {
+  long z = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= n) return;
+  double* t = (ctl->iter & 1) ? D.t1 : D.t0;
+  int cd = D.fmap[z];
+  long f = (long)(cd > 0 ? cd : -cd) - 1;
+  if (f > z) t[f] = cd > 0 ? t[z] : -t[z];
+}
+
+void pnm_solve_begin(pnm_ctx* ctx) {
+  k_solve_begin<<<1, 256, 0, ctx->stream>>>(ctx->sysctl, ctx->d_tol, (int)ctx->sys.size(), ctx->ctl);
+  CUDA_TRY(cudaGetLastError());
+}
+
+// Initial amplitudes and their energy (the device-side pnm_start: control blocks from
+// k_solve_begin).
+void pnm_start_device(pnm_ctx* ctx, int init) {
+  cudaStream_t s = ctx->stream;
+  if (init == PNM_INIT_KEEP) pnm_flip_symmetrise(ctx, ctx->d.t0, s);
+  k_init<<<ctx->nrows, 128, 0, s>>>(ctx->d, init);
+  k_start<<<1, 256, 0, s>>>(ctx->d.eparts, ctx->row_lo_d, ctx->row_hi_d, (int)ctx->sys.size(), ctx->sysctl,
+                            ctx->ctl, ctx->hist, ctx->hist_cap);
+  CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_loop_begin(pnm_ctx* ctx, int mode) {
+  k_loop_begin<<<1, 1, 0, ctx->stream>>>(ctx->ctl, ctx->d_par, (mode & 15) == PNM_PREC_FP64 ? 0 : 1);
+  CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_refine_gate(pnm_ctx* ctx, cudaGraphConditionalHandle h) {
+  k_refine_gate<<<1, 1, 0, ctx->stream>>>(ctx->ctl, ctx->sysctl, (int)ctx->sys.size(), ctx->d_par, h);
+  CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_loop_end_settle(pnm_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  k_loop_end<<<1, 1, 0, s>>>(ctx->ctl);
+  if (ctx->nt > 0) {
+    const long blocks = std::min<long>((ctx->nt + 255) / 256, 4096);
+    k_settle_copy<<<(unsigned)blocks, 256, 0, s>>>(ctx->d, ctx->ctl, ctx->nt);
+  }
+  k_settle_reset<<<1, 1, 0, s>>>(ctx->ctl);
+  CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_flip_copy_device(pnm_ctx* ctx) {
+  if (ctx->nt > 0)
+    k_flip_copy_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
+  CUDA_TRY(cudaGetLastError());
 }
 
 // Schedule tuning: time a few updates with the ph term and the pp ladder on side streams

@@ -639,17 +639,29 @@ void pnm_enqueue_body_mixed(pnm_ctx* ctx, int use_cond, cudaGraphConditionalHand
 // Before the first mixed update of a solve: the FP32 copies of the start amplitudes (t32 and the
 // ph term's T; the t tiles of the ladder are packed at the start of every mixed update), and
 // alpha / eps_ij^ab if alpha changed.
-void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha) {
+// FP32 copies of the starting amplitudes, in the direct and the cross-channel layouts.
+void pnm_mixed_pack_t(pnm_ctx* ctx) {
   MixedState* M = ctx->mixed;
   if (ctx->nt > 0)
     k_to_float_cur<<<(unsigned)((ctx->nt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, ctx->nt);
   if (ctx->nxt > 0)
     k_remap_t32<<<(unsigned)((ctx->nxt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d, ctx->ctl, M->xt32, ctx->nxt);
+  CUDA_TRY(cudaGetLastError());
+}
+
+// alpha / eps_ij^ab per amplitude for this mixing (recomputed only when alpha changes).
+void pnm_mixed_set_alpha(pnm_ctx* ctx, double alpha) {
+  MixedState* M = ctx->mixed;
   if (alpha != M->aw_alpha) {
     pnm_alpha_inv(ctx, alpha, M->aw);
     M->aw_alpha = alpha;
   }
   CUDA_TRY(cudaGetLastError());
+}
+
+void pnm_mixed_pack_initial(pnm_ctx* ctx, double alpha) {
+  pnm_mixed_pack_t(ctx);
+  pnm_mixed_set_alpha(ctx, alpha);
 }
 
 const double* pnm_mixed_aw(const pnm_ctx* ctx) {

@@ -992,6 +992,7 @@ static void set_model(pnm_ctx* ctx, const float* blob) {
   CUDA_TRY(cudaStreamSynchronize(s));
   M->y_scale = blob[O_YS];
   M->have_model = true;
+  pnm_drop_solve_graphs(ctx);  // the learned start's kernels hold y_scale as an argument
 }
 
 // One CTA pair per SM over the 128-sample tiles (fin.rep set: features formed in the kernel).
@@ -1007,8 +1008,8 @@ static void tc_infer(cudaStream_t s, const float* X, long n, const float* q, con
   else k_mlp_tc<false><<<grid, MLP_THREADS, MLP_SMEM, s>>>(X, n, q, pw, out, MlpFused{}, err);
 }
 
-// Learned start into t0 (every system), used by the solver for PNM_INIT_MLP.
-void pnm_mlp_start(pnm_ctx* ctx) {
+// One-time state of the learned start (per-system constants and the sample list).
+void pnm_mlp_prepare(pnm_ctx* ctx) {
   if (!ctx->mlp || !ctx->mlp->have_model) throw PnmError{PNM_EINVAL, "no warm-start model set (pnm_mlp_set_model)"};
   mlp_systems(ctx);
   MlpState* M = ctx->mlp;
@@ -1038,6 +1039,12 @@ void pnm_mlp_start(pnm_ctx* ctx) {
       CUDA_TRY(cudaGetLastError());
     }
   }
+}
+
+// The learned start's kernels (after pnm_mlp_prepare): inference into t0, then the spin flips.
+void pnm_mlp_enqueue(pnm_ctx* ctx) {
+  MlpState* M = ctx->mlp;
+  cudaStream_t s = ctx->stream;
   // the network output goes straight into t0 (t_MBPT2 + sigma_sys * y_scale * y)
   const int nsys = (int)ctx->sys.size();
   const MlpFused fin{ctx->d, M->rep, M->fs, M->sigma + nsys};
@@ -1045,6 +1052,12 @@ void pnm_mlp_start(pnm_ctx* ctx) {
            MlpOut{nullptr, ctx->d.t0, nullptr, M->sigma, M->t_begin, nsys, M->y_scale, nullptr}, M->err, &fin);
   pnm_flip_copy(ctx, ctx->d.t0, s);
   CUDA_TRY(cudaGetLastError());
+}
+
+// Learned start into t0 (every system), used by the solver for PNM_INIT_MLP.
+void pnm_mlp_start(pnm_ctx* ctx) {
+  pnm_mlp_prepare(ctx);
+  pnm_mlp_enqueue(ctx);
 }
 
 // Device flag the inference kernel sets when one of its bounded waits ran out (nullptr without

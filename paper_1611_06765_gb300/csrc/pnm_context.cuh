@@ -76,6 +76,18 @@ struct pnm_ctx {
   // graphs, one per precision mode
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> graph_defs;
+  // whole-solve graphs (start, iteration loop, refinement loop, settling, read-back), one per
+  // solve configuration; their run-time parameters and results pass through pinned host memory
+  std::map<int, cudaGraphExec_t> solve_graphs;
+  std::map<int, cudaGraph_t> solve_graph_defs;
+  void* h_pinned = nullptr;      // one block: h_par, h_ctl, h_sc[nsys], h_mlp_err
+  SolveParams* h_par = nullptr;
+  LoopCtl* h_ctl = nullptr;
+  SysCtl* h_sc = nullptr;
+  int* h_mlp_err = nullptr;
+  SolveParams* d_par = nullptr;
+  double* d_tol = nullptr;       // per-system tolerance of the energy test
+  std::vector<double> tol_host;  // the values d_tol holds
   unsigned long long cond_handle_for_mode[4] = {0, 0, 0, 0};
 
   MixedState* mixed = nullptr;
@@ -161,6 +173,18 @@ int pnm_run_loop(pnm_ctx* ctx, int mode, int max_iter, int min_iter, int host_lo
 void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
 void pnm_mlp_start(pnm_ctx* ctx);
+void pnm_mlp_prepare(pnm_ctx* ctx);
+void pnm_mlp_enqueue(pnm_ctx* ctx);
+void pnm_drop_solve_graphs(pnm_ctx* ctx);
+void pnm_set_node_priorities(cudaGraph_t body);
+void pnm_solve_begin(pnm_ctx* ctx);
+void pnm_start_device(pnm_ctx* ctx, int init);
+void pnm_loop_begin(pnm_ctx* ctx, int mode);
+void pnm_refine_gate(pnm_ctx* ctx, cudaGraphConditionalHandle h);
+void pnm_loop_end_settle(pnm_ctx* ctx);
+void pnm_flip_copy_device(pnm_ctx* ctx);
+void pnm_mixed_pack_t(pnm_ctx* ctx);
+void pnm_mixed_set_alpha(pnm_ctx* ctx, double alpha);
 void pnm_free_mlp(pnm_ctx* ctx);
 int* pnm_mlp_err(pnm_ctx* ctx);
 void prof_begin(pnm_ctx* ctx, int kid);

@@ -142,6 +142,13 @@ struct LoopCtl {
   double alpha;
 };
 
+// Run-time parameters of a whole-solve graph, copied from pinned host memory by its first node.
+struct SolveParams {
+  int max_iter;       // iteration cap of the first loop; the refinement adds refine_sweeps + it
+  int refine_sweeps;  // refinement updates before the FP64 test may stop the loop
+  double alpha;       // mixing
+};
+
 struct SysCtl {
   double e_old, e_new, resid;
   double tol;
