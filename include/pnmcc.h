@@ -368,8 +368,9 @@ int pnm_kernel_stats(const pnm_ctx *ctx, int id, const char **name, double *tota
  * tensor-core pp ladder (run when the mixed-precision path is first prepared): number of
  * k-range splits per (channel, ab tile) item, depth of the shared-memory copy ring and the
  * measured microseconds per launch.  Schedule autotuner (run at the first solve of each
- * precision): serial_mask bit 0 / bit 1 set when the FP64 / mixed update runs on one stream
- * instead of three concurrent ones; bit 2 / bit 3 set while that mode is not tuned yet.
+ * precision): serial_mask bit 0 / bit 1 / bit 4 set when the FP64 update / the mixed update /
+ * the refinement update with FP32-pair contractions runs on one stream instead of three
+ * concurrent ones; bit 2 / bit 3 / bit 5 set while that mode is not tuned yet.
  * Any output may be NULL; PNM_EINVAL (after writing serial_mask) before the first
  * mixed-precision solve. */
 int pnm_get_tuning(const pnm_ctx *ctx, int *ksplit, int *stages, float *us, int *serial_mask);

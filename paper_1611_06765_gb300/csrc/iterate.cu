@@ -1755,6 +1755,7 @@ __global__ void __launch_bounds__(128) k_mbpt3_rows(DevState D, double* __restri
 // amplitudes by the MBPT2 guess.
 void pnm_mbpt3_all(pnm_ctx* ctx, double* out) {
   cudaStream_t s = ctx->stream;
+  pnm_need_vpp64(ctx);
   int nsys = (int)ctx->sys.size();
   if (!ctx->mbpt3_buf) ctx->mbpt3_buf = (double*)dmalloc(ctx, sizeof(double) * (3 * (size_t)ctx->nrows + 3 * nsys));
   double* parts = ctx->mbpt3_buf;
@@ -1840,6 +1841,8 @@ void pnm_lad_expand(pnm_ctx* ctx, const f2* rs, int planes, long pstride, double
 // rep_only: only the rows the updates compute (one of each spin-flip pair of rows); the ladder
 // operator of pnm_apply_pp_ladder takes every row.
 void pnm_launch_pp64(pnm_ctx* ctx, cudaStream_t s, bool rep_only, const f2* vpp_f2) {
+  // the FP64 ladder V is built before any capture by the host-side callers (pnm_need_vpp64)
+  if (!vpp_f2 && !ctx->d.v_pppp) throw PnmError{PNM_EINVAL, "the FP64 ladder V has not been built"};
   if (ctx->n_pp_items == 0) return;
   if (vpp_f2)
     k_lad_gather<f2><<<ctx->n_lad_rows, 128, 0, s>>>(ctx->d, ctx->ctl, ctx->lad_rows, ctx->t_pair,
@@ -1966,21 +1969,20 @@ void prof_collect(pnm_ctx* ctx) {
 void pnm_enqueue_body(pnm_ctx* ctx, int mode, int use_cond, cudaGraphConditionalHandle h) {
   int prec = mode & 15, terms = (mode >> 4) & 15;
   bool pair = ((mode >> 8) & 1) != 0;
-  ctx->cur_mode = prec == PNM_PREC_FP64 ? 0 : 1;
+  ctx->cur_mode = prec == PNM_PREC_FP64 ? (pair ? 2 : 0) : 1;
   if (prec == PNM_PREC_FP64) enqueue_body_fp64(ctx, use_cond, h, terms, pair);
   else pnm_enqueue_body_mixed(ctx, use_cond, h);
 }
 
 // FP32-pair copies of the ladder-basis V_pppp, V_pphh, W and <kb|v|cj> (once per context).
 void pnm_prepare_f2(pnm_ctx* ctx) {
-  if (ctx->vpp_f2) return;
+  if (ctx->t_pair) return;
   cudaStream_t s = ctx->stream;
-  ctx->vpp_f2 = ctx_alloc<f2>(ctx, ctx->nvpp);
+  pnm_need_vpp_f2(ctx);
   ctx->t_pair = ctx_alloc<f2>(ctx, ctx->nt);
   ctx->xw_f2 = ctx_alloc<f2>(ctx, ctx->nxt);
   ctx->xv1_f2 = ctx_alloc<f2>(ctx, ctx->nxc);
   ctx->vpphh_f2 = ctx_alloc<f2>(ctx, ctx->nt);
-  pnm_split_f2(ctx->d.v_pppp, ctx->vpp_f2, ctx->nvpp, s);
   pnm_split_f2(ctx->d.v_pphh, ctx->vpphh_f2, ctx->nt, s);
   pnm_split_f2(ctx->d.x_w, ctx->xw_f2, ctx->nxt, s);
   pnm_split_f2(ctx->d.x_v1, ctx->xv1_f2, ctx->nxc, s);
@@ -2261,9 +2263,11 @@ static std::mutex g_sched_mu;
 static std::map<std::string, bool> g_sched_cache;  // (shape key, mode) -> one stream
 
 void pnm_tune_schedule(pnm_ctx* ctx, int mode, double alpha) {
-  int m = mode == PNM_PREC_FP64 ? 0 : 1;
+  const bool pair = ((mode >> 8) & 1) != 0;
+  int m = (mode & 15) == PNM_PREC_FP64 ? (pair ? 2 : 0) : 1;
   if (ctx->sched_tuned[m]) return;
-  const std::string key = pnm_shape_key(ctx) + (m ? "|mixed" : "|fp64");
+  if (m == 0) pnm_need_vpp64(ctx);
+  const std::string key = pnm_shape_key(ctx) + (m == 1 ? "|mixed" : m == 2 ? "|pair" : "|fp64");
   {
     std::lock_guard<std::mutex> lock(g_sched_mu);
     auto f = g_sched_cache.find(key);

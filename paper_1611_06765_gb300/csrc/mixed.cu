@@ -56,12 +56,14 @@ __device__ __forceinline__ int core_off(int r, int k) { return tile_core_off(r, 
 
 // ------------------------------------------------------------------------ kernels
 // V tiles of the channels with a V_pppp block (setup): one CTA per (item, k-block).
-__global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restrict__ v_pppp,
+// Read from the FP32-pair copy of V: its high part is the FP32 rounding of the FP64 element,
+// the value the BF16 split starts from.
+__global__ void k_pack_v(const TCItem* __restrict__ items, const f2* __restrict__ v_pppp,
                          const long* __restrict__ ch_vpp_off, __nv_bfloat16* __restrict__ vt) {
   TCItem it = items[blockIdx.x];  // an unsplit item: kb0 = 0, nkb = all k-blocks
   int kb = blockIdx.y;
   if (kb >= it.nkb) return;
-  const double* V = v_pppp + ch_vpp_off[it.ch];
+  const f2* V = v_pppp + ch_vpp_off[it.ch];
   __nv_bfloat16* hi = vt + it.voff + (long)kb * 2 * (TC_M * TC_BK);
   __nv_bfloat16* lo = hi + TC_M * TC_BK;
   // V is symmetric (bit for bit: <ab|v|cd> and <cd|v|ab> are evaluated by the same
@@ -70,7 +72,7 @@ __global__ void k_pack_v(const TCItem* __restrict__ items, const double* __restr
   for (int e = threadIdx.x; e < TC_M * TC_BK; e += blockDim.x) {
     int r = e / TC_BK, k = e % TC_BK;
     int ab = it.mt * TC_M + r, cd = kb * TC_BK + k;
-    double x = (ab < it.npp && cd < it.npp) ? V[(long)ab * it.npp + cd] : 0.0;
+    double x = (ab < it.npp && cd < it.npp) ? (double)V[(long)ab * it.npp + cd].hi : 0.0;
     __nv_bfloat16 h, l;
     split_bf16(x, h, l);
     hi[core_off(r, k)] = h;
@@ -436,6 +438,7 @@ static std::map<std::string, std::tuple<int, int, float>> g_tile_cache;
 void pnm_prepare_mixed(pnm_ctx* ctx) {
   if (ctx->mixed) return;
   cudaStream_t s = ctx->stream;
+  pnm_need_vpp_f2(ctx);  // the V tiles are split from it
   MixedState* M = new MixedState();
   M->sysctl = ctx->sysctl;
   try {
@@ -520,7 +523,7 @@ void pnm_prepare_mixed(pnm_ctx* ctx) {
     if (ctx->nxc > 0)
       k_to_float<<<(unsigned)((ctx->nxc + 255) / 256), 256, 0, s>>>(ctx->d.x_v1, M->xv132, ctx->nxc);
     if (M->nitems > 0)
-      k_pack_v<<<dim3(M->nitems, max_nkb), 256, 0, s>>>(M->items, ctx->d.v_pppp, ctx->d.ch_vpp_off, M->vt);
+      k_pack_v<<<dim3(M->nitems, max_nkb), 256, 0, s>>>(M->items, ctx->vpp_f2, ctx->d.ch_vpp_off, M->vt);
     CUDA_TRY(cudaGetLastError());
     M->stage_bytes = (2 * A_PLANE + 2 * (uint32_t)max_npad * TC_BK * 2 + 1023) / 1024 * 1024;
     auto smem_for = [&](int nst) { return 1024 + (size_t)nst * M->stage_bytes + 8192; };  // tail guard
@@ -672,7 +675,8 @@ const double* pnm_mixed_aw(const pnm_ctx* ctx) {
 void pnm_mixed_tuning(const pnm_ctx* ctx, int* ksplit, int* stages, float* us, int* serial_mask) {
   if (serial_mask)
     *serial_mask = (ctx->sched_tuned[0] ? (ctx->serial_sched[0] ? 1 : 0) : 4) |
-                   (ctx->sched_tuned[1] ? (ctx->serial_sched[1] ? 2 : 0) : 8);
+                   (ctx->sched_tuned[1] ? (ctx->serial_sched[1] ? 2 : 0) : 8) |
+                   (ctx->sched_tuned[2] ? (ctx->serial_sched[2] ? 16 : 0) : 32);
   if (!ctx->mixed) throw PnmError{PNM_EINVAL, "the mixed-precision path has not been prepared"};
   if (ksplit) *ksplit = ctx->mixed->ksplit;
   if (stages) *stages = ctx->mixed->nst;
@@ -709,6 +713,7 @@ void pnm_apply_pp(pnm_ctx* ctx, int sys, int precision, const double* t, double*
       pnm_prepare_f2(ctx);
       pnm_split_cur(ctx, s);
     }
+    if (precision == PNM_PREC_FP64) pnm_need_vpp64(ctx);
     CUDA_TRY(cudaMemsetAsync(ctx->d.rpp, 0, sizeof(double) * std::max<long>(ctx->ns, 1), s));
     // every row: the operator acts on any amplitudes
     pnm_launch_pp64(ctx, s, false, precision == PNM_PREC_F32PAIR ? ctx->vpp_f2 : nullptr);

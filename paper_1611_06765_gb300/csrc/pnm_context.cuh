@@ -95,14 +95,19 @@ struct pnm_ctx {
   // FP32-pair copies of the ladder-basis V_pppp, V_pphh, W and <kb|v|cj> (made on first use by
   // the FP32-pair contractions)
   f2 *vpp_f2 = nullptr, *vpphh_f2 = nullptr, *xw_f2 = nullptr, *xv1_f2 = nullptr;
+  // work list of the ladder-basis V (items (channel, first row), per system a run) and the
+  // shared memory of its kernel; the V itself is built on first use (pnm_need_vpp64 / _f2)
+  int2* vl_items = nullptr;
+  std::vector<int> vl_sys;
+  size_t vl_smem = 0;
   double hbar2_2m = 0.0;
   int mlp_fallback = 0;  // 1 when the last learned start was replaced by the MBPT2 start
 
   // side streams for the independent parts of an update (ph term, pp ladder), joined by events
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
-  bool serial_sched[2] = {false, false};  // per mode (0 FP64, 1 mixed): one stream only
-  bool sched_tuned[2] = {false, false};
+  bool serial_sched[3] = {false, false, false};  // per mode (0 FP64, 1 mixed, 2 FP32-pair refinement): one stream only
+  bool sched_tuned[3] = {false, false, false};
   int cur_mode = 0;
 
   // per-kernel CUDA-event profiling of host-driven solves (never active during capture)
@@ -174,6 +179,9 @@ void pnm_reopen(pnm_ctx* ctx);
 void pnm_settle_amplitudes(pnm_ctx* ctx);
 void pnm_mlp_start(pnm_ctx* ctx);
 void pnm_mlp_prepare(pnm_ctx* ctx);
+void pnm_ladder_v(pnm_ctx* ctx, double* out64, f2* out2);
+void pnm_need_vpp64(pnm_ctx* ctx);
+void pnm_need_vpp_f2(pnm_ctx* ctx);
 void pnm_mlp_enqueue(pnm_ctx* ctx);
 void pnm_drop_solve_graphs(pnm_ctx* ctx);
 void pnm_set_node_priorities(cudaGraph_t body);

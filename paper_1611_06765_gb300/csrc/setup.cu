@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <type_traits>
+
 #include "pnm_context.cuh"
 
 namespace {
@@ -734,11 +736,13 @@ __global__ void __launch_bounds__(LAD_THREADS) k_ladder_basis(
 // W(c, c') = e e' <rep c|v|rep c'> for VLAD_ROWS rows of one channel per CTA; the channel's
 // representative pair states, their signs and the LUT are staged in shared memory.
 constexpr int VLAD_ROWS = 16;
+// Out: double (the FP64 ladder V) or f2 (its FP32-pair copy, the element split once).
+template <typename Out>
 __global__ void __launch_bounds__(256) k_v_ladder(const int2* __restrict__ items, const int* __restrict__ ch_pp_off,
                                                   const int* __restrict__ ch_nlad, const long* __restrict__ ch_vl_off,
                                                   const int2* __restrict__ lad_mem, const int2* __restrict__ pp_pair,
                                                   const char4* __restrict__ nvec, const double* __restrict__ lut,
-                                                  int lut_elems, double* __restrict__ v_lad) {
+                                                  int lut_elems, Out* __restrict__ v_lad) {
   extern __shared__ __align__(16) unsigned char vsm[];
   double* slut = reinterpret_cast<double*>(vsm);
   int2 it = items[blockIdx.x];
@@ -761,10 +765,12 @@ __global__ void __launch_bounds__(256) k_v_ladder(const int2* __restrict__ items
   for (int row = r0; row < r1; row++) {
     char4 sc = sa[row], sd = sb[row];
     int g = sg[row];
-    double* out = v_lad + ch_vl_off[c] + (long)row * nl;
+    Out* out = v_lad + ch_vl_off[c] + (long)row * nl;
     for (int q = threadIdx.x; q < nl; q += blockDim.x) {
       double v = v_minnesota_as(sa[q], sb[q], sc, sd, slut);
-      out[q] = g * sg[q] > 0 ? v : __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+      v = g * sg[q] > 0 ? v : __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+      if constexpr (std::is_same<Out, f2>::value) out[q] = Arith<f2>::from_double(v);
+      else out[q] = v;
     }
   }
 }
@@ -845,6 +851,45 @@ struct SysScratch {
     for (void* p : owned) pnm_pool_free(stream, p);
   }
 };
+
+// The ladder-basis V_pppp of every system into out64 (FP64) or out2 (FP32 pairs).
+void pnm_ladder_v(pnm_ctx* ctx, double* out64, f2* out2) {
+  cudaStream_t s = ctx->stream;
+  DevState& D = ctx->d;
+  const int nsys = (int)ctx->sys.size();
+  if (out64) smem_at_least(k_v_ladder<double>, ctx->vl_smem);
+  if (out2) smem_at_least(k_v_ladder<f2>, ctx->vl_smem);
+  for (int k = 0; k < nsys; k++) {
+    const int lo = ctx->vl_sys[k], hi = ctx->vl_sys[k + 1];
+    if (hi <= lo) continue;
+    const SysInfo& S = ctx->sys[k];
+    const int lut_elems = S.lut_len * (S.species == 1 ? 1 : 3);
+    if (out64)
+      k_v_ladder<double><<<(unsigned)(hi - lo), 256, ctx->vl_smem, s>>>(
+          ctx->vl_items + lo, D.ch_pp_off, D.ch_nlad, D.ch_vpp_off, D.lad_mem, D.pp_pair, D.nvec,
+          D.lut + S.lut_off, lut_elems, out64);
+    if (out2)
+      k_v_ladder<f2><<<(unsigned)(hi - lo), 256, ctx->vl_smem, s>>>(
+          ctx->vl_items + lo, D.ch_pp_off, D.ch_nlad, D.ch_vpp_off, D.lad_mem, D.pp_pair, D.nvec,
+          D.lut + S.lut_off, lut_elems, out2);
+  }
+  CUDA_TRY(cudaGetLastError());
+}
+
+// The FP64 ladder V (the FP64 pp ladder and operator): built once, on first use.
+void pnm_need_vpp64(pnm_ctx* ctx) {
+  if (ctx->d.v_pppp) return;
+  ctx->d.v_pppp = ctx_alloc<double>(ctx, std::max<long>(ctx->nvpp, 1));
+  pnm_ladder_v(ctx, ctx->d.v_pppp, nullptr);
+}
+
+// The FP32-pair ladder V (the refinement sweeps' pp ladder, and the source of the tensor-core
+// ladder's BF16 tiles, whose split starts from the same FP32 rounding): built once.
+void pnm_need_vpp_f2(pnm_ctx* ctx) {
+  if (ctx->vpp_f2) return;
+  ctx->vpp_f2 = ctx_alloc<f2>(ctx, std::max<long>(ctx->nvpp, 1));
+  pnm_ladder_v(ctx, nullptr, ctx->vpp_f2);
+}
 
 void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const double* rhos,
                const int* n2maxs, const double* thetas, const pnm_minnesota& P) {
@@ -1265,27 +1310,25 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
   ctx->nvpp = vl_acc;
   h2d(D.ch_s_off, h_s_off, s);
   h2d(D.ch_vpp_off, h_vl_off, s);
-  D.v_pppp = dalloc<double>(vl_acc, ctx->owned, s);
+  D.v_pppp = nullptr;  // the ladder V is built on first use, in the representation a path needs
   D.rpp = dalloc<double>(s_acc, ctx->owned, s);
   D.s64 = dalloc<double>(s_acc, ctx->owned, s);
-  // ladder V, one launch per system (the LUT differs per system)
+  // work list of the ladder V (one launch per system: the LUT differs per system), kept for
+  // pnm_ladder_v
+  ctx->vl_sys.assign(nsys + 1, 0);
   if (!vl_items.empty()) {
     int max_lut = 0;
     for (const SysInfo& S : sys) max_lut = std::max(max_lut, S.lut_len * (S.species == 1 ? 1 : 3));
     size_t smem = sizeof(double) * max_lut + (2 * sizeof(char4) + sizeof(int)) * (size_t)max_nlad;
     if (smem > 200 * 1024) throw PnmError{PNM_EINVAL, "channel too large for the staged ladder V"};
-    smem_at_least(k_v_ladder, smem);
-    int2* items = dalloc<int2>(vl_items.size(), scr[0].owned, s);
-    h2d(items, vl_items, s);
+    ctx->vl_smem = smem;
+    ctx->vl_items = dalloc<int2>(vl_items.size(), ctx->owned, s);
+    h2d(ctx->vl_items, vl_items, s);
     size_t lo = 0;
     for (int k = 0; k < nsys; k++) {
       size_t hi = lo;
       while (hi < vl_items.size() && h_ch_sys[vl_items[hi].x] == k) hi++;
-      if (hi > lo)
-        k_v_ladder<<<(unsigned)(hi - lo), 256, smem, s>>>(items + lo, D.ch_pp_off, D.ch_nlad, D.ch_vpp_off,
-                                                          D.lad_mem, D.pp_pair, D.nvec, D.lut + sys[k].lut_off,
-                                                          sys[k].lut_len * (sys[k].species == 1 ? 1 : 3),
-                                                          D.v_pppp);
+      ctx->vl_sys[k + 1] = (int)hi;
       lo = hi;
     }
   }

@@ -196,10 +196,20 @@ int pnm_solve(pnm_ctx* ctx, const pnm_solve_opts& o, double* dE, int* iters, dou
   const auto w0 = std::chrono::steady_clock::now();
   const double g0 = ctx->t_graph_host;
   bool mixed = o.precision != PNM_PREC_FP64;
-  if (mixed) pnm_prepare_mixed(ctx);
+  if (mixed) {
+    pnm_prepare_mixed(ctx);
+    pnm_mixed_set_alpha(ctx, o.mix_alpha);  // alpha / eps, read by the tuned updates too
+  }
   const bool pair_refine = mixed && o.refine_sweeps > 0 && o.refine_kernels == PNM_PREC_F32PAIR;
   if (pair_refine) pnm_prepare_f2(ctx);
-  pnm_tune_schedule(ctx, PNM_PREC_FP64, o.mix_alpha);
+  // the FP64 ladder V and schedule only where an FP64 pp ladder runs (the FP64 iteration, or
+  // refinement sweeps on the FP64 pipe); FP32-pair refinement has its own schedule slot
+  const bool fp64_ladder = !mixed || (o.refine_sweeps > 0 && !pair_refine);
+  if (fp64_ladder) {
+    pnm_need_vpp64(ctx);
+    pnm_tune_schedule(ctx, PNM_PREC_FP64, o.mix_alpha);
+  }
+  if (pair_refine) pnm_tune_schedule(ctx, PNM_PREC_FP64 | (1 << 8), o.mix_alpha);
   if (mixed) pnm_tune_schedule(ctx, PNM_PREC_BF16X3, o.mix_alpha);
   if (!o.host_loop) {
     // one graph launch: the learned start's one-time state, the tolerances and alpha / eps
