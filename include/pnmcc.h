@@ -35,7 +35,8 @@ extern "C" {
 #define PNM_ENOMEM (-2)     /* device or host allocation failed */
 #define PNM_ECUDA (-3)      /* a CUDA runtime call failed */
 #define PNM_ENOTCONV (-4)   /* iteration cap reached before the energy change met the tolerance */
-#define PNM_EDIVERGED (-5)  /* NaN/Inf energy or residual */
+#define PNM_EDIVERGED (-5)  /* NaN/Inf energy or residual, or |dE| of a system at least doubling
+                               (above its tolerance) over 6 consecutive updates */
 #define PNM_ETIMEOUT (-6)   /* a device-side wait ran out of its budget */
 
 typedef struct pnm_ctx pnm_ctx;
@@ -254,6 +255,30 @@ int pnm_amplitude_labels(const pnm_ctx *ctx, int sys, size_t *n, int32_t *abij);
  * n must equal the count of pnm_amplitude_labels.  Checkpoint and training-data path. */
 int pnm_get_amplitudes(const pnm_ctx *ctx, int sys, double *t, size_t n);
 int pnm_set_amplitudes(pnm_ctx *ctx, int sys, const double *t, size_t n);
+
+/* Checkpoint header of one system: what fixes its amplitude layout.  twist = theta / 2 pi per
+ * axis (0 for periodic boundaries); channel_hash = FNV-1a (64 bit) over the system's direct
+ * channels in pnm_channels order: per channel its key, n_hh and n_pp, then every hole and
+ * particle pair (state indices within the system). */
+typedef struct {
+  int32_t N, Z, n2max, reserved;
+  double rho;
+  double twist[3];
+  int64_t n_amplitudes;
+  uint64_t channel_hash;
+} pnm_checkpoint_header;
+int pnm_checkpoint_header_of(const pnm_ctx *ctx, int sys, pnm_checkpoint_header *h);
+
+/* Checkpoint / resume (not in the paper): write the held amplitudes of every system (those
+ * pnm_get_amplitudes reads: after a solve the converged ones) to `path`, with their headers;
+ * read them back into a context built for the same systems.  File: the 8 bytes "PNMCKPT1",
+ * int32 number of systems, int32 0, the headers, then each system's amplitudes (FP64, library
+ * order), host byte order.  pnm_checkpoint_load returns PNM_EINVAL, leaving the context's
+ * amplitudes unchanged, when the file cannot be read, is truncated or any header differs from
+ * the context's (bit for bit); a solve with init = PNM_INIT_KEEP resumes from the loaded
+ * amplitudes. */
+int pnm_checkpoint_save(const pnm_ctx *ctx, const char *path);
+int pnm_checkpoint_load(pnm_ctx *ctx, const char *path);
 
 /* The particle-particle ladder alone, as an operator on amplitudes:
  * r_ij^ab = 1/2 sum_cd <ab|v|cd> t_ij^cd = sum_{c<d} <ab|v|cd> t_ij^cd (the pp-ladder term of

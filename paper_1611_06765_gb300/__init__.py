@@ -211,6 +211,22 @@ class Context:
         blob = np.ascontiguousarray(blob, dtype=np.float32)
         _lib.check(_lib.load().pnm_mlp_set_model(self._h, blob.ctypes.data_as(C.POINTER(C.c_float))))
 
+    def checkpoint_header(self, sys=0):
+        """pnm_checkpoint_header_of: what fixes the system's amplitude layout."""
+        h = _lib.pnm_checkpoint_header()
+        _lib.check(_lib.load().pnm_checkpoint_header_of(self._h, sys, C.byref(h)))
+        return dict(N=h.N, Z=h.Z, n2max=h.n2max, rho=h.rho, twist=tuple(h.twist), n_amplitudes=h.n_amplitudes,
+                    channel_hash=h.channel_hash)
+
+    def save_checkpoint(self, path):
+        """pnm_checkpoint_save: the held amplitudes of every system with their headers."""
+        _lib.check(_lib.load().pnm_checkpoint_save(self._h, str(path).encode()))
+
+    def load_checkpoint(self, path):
+        """pnm_checkpoint_load: amplitudes from a checkpoint of the same systems (resume with
+        init=PNM_INIT_KEEP); PnmError if a header does not match."""
+        _lib.check(_lib.load().pnm_checkpoint_load(self._h, str(path).encode()))
+
     def mlp_predict(self):
         """Learned start into the held amplitudes (``pnm_mlp_predict``); read with get_amplitudes."""
         _lib.check(_lib.load().pnm_mlp_predict(self._h))

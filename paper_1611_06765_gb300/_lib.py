@@ -43,7 +43,7 @@ EXPORTS = (
     "pnm_ccd_solve",
     "pnm_energy_history", "pnm_amplitude_labels", "pnm_get_amplitudes", "pnm_set_amplitudes",
     "pnm_get_timings", "pnm_apply_pp_ladder", "pnm_apply_ph_term", "pnm_mlp_num_params", "pnm_mlp_init",
-    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_predict", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
+    "pnm_mlp_features", "pnm_mlp_train", "pnm_mlp_set_model", "pnm_mlp_predict", "pnm_checkpoint_header_of", "pnm_checkpoint_save", "pnm_checkpoint_load", "pnm_mlp_forward", "pnm_mlp_loss_grad", "pnm_set_profiling", "pnm_kernel_stats", "pnm_get_tuning", "pnm_selftest_timeout",
     "pnm_measure_fma_peak", "pnm_last_error",
 )
 
@@ -56,6 +56,12 @@ class pnm_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("mix_alpha", C.c_double), ("tol_dE", C.c_double),
                 ("tol_dE_per_N", C.c_double), ("max_iter", C.c_int), ("refine_sweeps", C.c_int),
                 ("init", C.c_int), ("host_loop", C.c_int), ("terms", C.c_int), ("refine_kernels", C.c_int)]
+
+
+class pnm_checkpoint_header(C.Structure):
+    _fields_ = [("N", C.c_int32), ("Z", C.c_int32), ("n2max", C.c_int32), ("reserved", C.c_int32),
+                ("rho", C.c_double), ("twist", C.c_double * 3), ("n_amplitudes", C.c_int64),
+                ("channel_hash", C.c_uint64)]
 
 
 class pnm_mlp_opts(C.Structure):
@@ -116,6 +122,9 @@ def load(path=None):
     L.pnm_mlp_train.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(pnm_mlp_opts), fp, fp, C.c_int, ip]
     L.pnm_mlp_set_model.argtypes = [vp, fp]
     L.pnm_mlp_predict.argtypes = [vp]
+    L.pnm_checkpoint_header_of.argtypes = [vp, C.c_int, C.POINTER(pnm_checkpoint_header)]
+    L.pnm_checkpoint_save.argtypes = [vp, C.c_char_p]
+    L.pnm_checkpoint_load.argtypes = [vp, C.c_char_p]
     L.pnm_mlp_forward.argtypes = [fp, fp, C.c_long, fp, C.c_int, vp]
     L.pnm_mlp_loss_grad.argtypes = [fp, fp, fp, C.c_int, fp, fp, C.c_int, vp]
     L.pnm_get_tuning.argtypes = [vp, ip, ip, C.POINTER(C.c_float), ip]

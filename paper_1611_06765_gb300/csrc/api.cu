@@ -5,6 +5,8 @@
 #include <string>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdint>
 
 #include "pnm_context.cuh"
 
@@ -484,6 +486,115 @@ int pnm_set_amplitudes(pnm_ctx* ctx, int sys, const double* t, size_t n) {
     if (!t || n != (size_t)(S.t_end - S.t_begin)) throw PnmError{PNM_EINVAL, "size mismatch"};
     CUDA_TRY(cudaMemcpyAsync(ctx->d.t0 + S.t_begin, t, sizeof(double) * n, cudaMemcpyHostToDevice,
                              ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PNM_OK;
+  });
+}
+
+// FNV-1a, 64 bit: offset basis 14695981039346656037, prime 1099511628211.
+static uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; i++) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+static pnm_checkpoint_header header_of(const pnm_ctx* ctx, int sys) {
+  const SysInfo& S = ctx->sys[sys];
+  pnm_checkpoint_header h;
+  std::memset(&h, 0, sizeof(h));
+  h.N = S.N - S.Z;
+  h.Z = S.Z;
+  h.n2max = S.n2max;
+  h.rho = S.rho;
+  for (int a = 0; a < 3; a++) h.twist[a] = S.phi[a];
+  h.n_amplitudes = S.t_end - S.t_begin;
+  int nch = 0, npairs = 0;
+  int rc = pnm_channels(ctx, sys, 0, &nch, &npairs, nullptr, nullptr, nullptr);
+  if (rc != PNM_OK) throw PnmError{rc, "channel tables unavailable"};
+  std::vector<int32_t> keys(std::max(nch, 1)), sizes(2 * std::max(nch, 1)), pairs(2 * std::max(npairs, 1));
+  rc = pnm_channels(ctx, sys, 0, &nch, &npairs, keys.data(), sizes.data(), pairs.data());
+  if (rc != PNM_OK) throw PnmError{rc, "channel tables unavailable"};
+  uint64_t x = 14695981039346656037ull;
+  for (int c = 0; c < nch; c++) {
+    x = fnv1a(x, &keys[c], sizeof(int32_t));
+    x = fnv1a(x, &sizes[2 * c], 2 * sizeof(int32_t));
+  }
+  x = fnv1a(x, pairs.data(), sizeof(int32_t) * 2 * (size_t)npairs);
+  h.channel_hash = x;
+  return h;
+}
+
+int pnm_checkpoint_header_of(const pnm_ctx* ctx, int sys, pnm_checkpoint_header* h) {
+  return guarded([&]() {
+    check_sys(ctx, sys);
+    if (!h) throw PnmError{PNM_EINVAL, "null argument"};
+    *h = header_of(ctx, sys);
+    return PNM_OK;
+  });
+}
+
+static const char kCkptMagic[8] = {'P', 'N', 'M', 'C', 'K', 'P', 'T', '1'};
+
+int pnm_checkpoint_save(const pnm_ctx* ctx, const char* path) {
+  return guarded([&]() {
+    if (!ctx || !path) throw PnmError{PNM_EINVAL, "null argument"};
+    const int nsys = (int)ctx->sys.size();
+    std::vector<pnm_checkpoint_header> hs(nsys);
+    for (int k = 0; k < nsys; k++) hs[k] = header_of(ctx, k);
+    std::vector<double> t((size_t)std::max<long>(ctx->nt, 1));
+    CUDA_TRY(cudaMemcpyAsync(t.data(), ctx->d.t0, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) throw PnmError{PNM_EINVAL, std::string("cannot open ") + path + " for writing"};
+    const int32_t head[2] = {nsys, 0};
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(head, sizeof(int32_t), 2, f) == 2 &&
+              std::fwrite(hs.data(), sizeof(pnm_checkpoint_header), nsys, f) == (size_t)nsys;
+    for (int k = 0; k < nsys && ok; k++) {
+      const SysInfo& S = ctx->sys[k];
+      const size_t n = (size_t)(S.t_end - S.t_begin);
+      ok = std::fwrite(t.data() + S.t_begin, sizeof(double), n, f) == n;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) throw PnmError{PNM_EINVAL, std::string("writing ") + path + " failed"};
+    return PNM_OK;
+  });
+}
+
+int pnm_checkpoint_load(pnm_ctx* ctx, const char* path) {
+  return guarded([&]() {
+    if (!ctx || !path) throw PnmError{PNM_EINVAL, "null argument"};
+    const int nsys = (int)ctx->sys.size();
+    FILE* f = std::fopen(path, "rb");
+    if (!f) throw PnmError{PNM_EINVAL, std::string("cannot open ") + path};
+    struct Closer {
+      FILE* f;
+      ~Closer() { std::fclose(f); }
+    } closer{f};
+    char magic[8];
+    int32_t head[2];
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0)
+      throw PnmError{PNM_EINVAL, "not a checkpoint file"};
+    if (std::fread(head, sizeof(int32_t), 2, f) != 2) throw PnmError{PNM_EINVAL, "truncated checkpoint"};
+    if (head[0] != nsys) throw PnmError{PNM_EINVAL, "checkpoint holds another number of systems"};
+    std::vector<pnm_checkpoint_header> hs(nsys);
+    if (std::fread(hs.data(), sizeof(pnm_checkpoint_header), nsys, f) != (size_t)nsys)
+      throw PnmError{PNM_EINVAL, "truncated checkpoint"};
+    for (int k = 0; k < nsys; k++) {
+      const pnm_checkpoint_header own = header_of(ctx, k);
+      if (std::memcmp(&own, &hs[k], sizeof(own)) != 0)
+        throw PnmError{PNM_EINVAL, "checkpoint header of system " + std::to_string(k) +
+                                       " does not match the context (N, Z, n2max, rho, twist or channel tables)"};
+    }
+    std::vector<double> t((size_t)std::max<long>(ctx->nt, 1));
+    for (int k = 0; k < nsys; k++) {
+      const SysInfo& S = ctx->sys[k];
+      const size_t n = (size_t)(S.t_end - S.t_begin);
+      if (std::fread(t.data() + S.t_begin, sizeof(double), n, f) != n) throw PnmError{PNM_EINVAL, "truncated checkpoint"};
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->d.t0, t.data(), sizeof(double) * ctx->nt, cudaMemcpyHostToDevice, ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return PNM_OK;
   });

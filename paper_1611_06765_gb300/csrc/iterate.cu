@@ -832,7 +832,9 @@ __device__ void finalize_systems(const FinArgs& f, LoopCtl* ctl) {
         if (S.iters < f.hist_cap) f.hist[(long)s * f.hist_cap + S.iters] = e;
         double diff = fabs(e - S.e_old);
         S.e_old = e;
-        if (!isfinite(e) || !isfinite(r)) bad = 1;
+        S.grow = (diff > 2.0 * S.d_old && diff > S.tol) ? S.grow + 1 : 0;
+        S.d_old = diff;
+        if (!isfinite(e) || !isfinite(r) || S.grow >= PNM_DIVERGE_STEPS) bad = 1;
         if (diff < S.tol && ctl->iter + 1 >= ctl->min_iter) {
           S.done = 1;
           S.frozen_at = ctl->iter;
@@ -2128,7 +2130,10 @@ void pnm_start(pnm_ctx* ctx, int init, const std::vector<double>& tol) {
 // Reopen the convergence test of every system for a further phase (refinement), keeping
 // amplitudes, energies and iteration counts.
 __global__ void k_reopen(SysCtl* sc, int nsys, LoopCtl* ctl) {
-  for (int s = 0; s < nsys; s++) sc[s].done = 0;
+  for (int s = 0; s < nsys; s++) {
+    sc[s].done = 0;
+    sc[s].grow = 0;
+  }
   ctl->status = 0;
 }
 
@@ -2180,7 +2185,10 @@ __global__ void k_refine_gate(LoopCtl* __restrict__ ctl, SysCtl* __restrict__ sc
                               const SolveParams* __restrict__ par, cudaGraphConditionalHandle h) {
   const bool go = ctl->status == 1;
   if (go) {
-    for (int k = 0; k < nsys; k++) sc[k].done = 0;
+    for (int k = 0; k < nsys; k++) {
+      sc[k].done = 0;
+      sc[k].grow = 0;
+    }
     const int it0 = ctl->iter;
     ctl->status = 0;
     ctl->max_iter = it0 + par->refine_sweeps + par->max_iter;

@@ -155,7 +155,13 @@ struct SysCtl {
   int done;       // 1 once converged
   int iters;
   int frozen_at;  // index of the update after which it converged (valid while done)
+  int grow;       // consecutive updates whose |dE| at least doubled (above tol): divergence
+  double d_old;   // |dE| of the previous update
 };
+
+// Divergence: |dE| at least doubling, above the tolerance, over this many consecutive updates
+// (a 64-fold geometric growth; NaN or Inf diverges at once).
+constexpr int PNM_DIVERGE_STEPS = 6;
 
 // True inside the solve loop once system `sys` has met its stopping rule (its amplitudes are
 // frozen): the contraction kernels of later steps skip its work, and the update skips it too

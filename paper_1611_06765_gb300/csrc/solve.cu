@@ -319,7 +319,8 @@ static int pnm_solve_finish(pnm_ctx* ctx, const pnm_solve_opts& o, int status, d
   }
   if (status == 1) return PNM_OK;
   if (status == PNM_ENOTCONV) pnm_set_error(status, "iteration cap reached before convergence");
-  if (status == PNM_EDIVERGED) pnm_set_error(status, "NaN or Inf in the energy or residual");
+  if (status == PNM_EDIVERGED)
+    pnm_set_error(status, "NaN or Inf in the energy or residual, or an energy change growing geometrically");
   if (status == PNM_ETIMEOUT) pnm_set_error(status, "a device-side wait ran out of its budget");
   return status;
 }
