@@ -2,7 +2,7 @@
 
 Integer tables (basis, direct and cross channels) must be bit-exact; FP64 energies and
 amplitudes agree to 1e-10 relative (the kernels differ from the oracle only in summation
-order); the benchmark spec's bound for the FP64 GPU path is 1e-8 relative in E_corr/N.
+order); the bound required of the FP64 GPU path is 1e-8 relative in E_corr/N.
 """
 import math
 
