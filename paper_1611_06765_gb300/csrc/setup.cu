@@ -1196,6 +1196,7 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
 
   // ---- pair lists, maps, V blocks per system
   std::vector<int> h_occ_off(nsp_total + 1, 0);
+  int* occ_cnt = dalloc<int>(std::max(nsp_total, 1), scr[0].owned, s);
   for (int k = 0; k < nsys; k++) {
     SysInfo& S = sys[k];
     SysScratch& X = scr[k];
@@ -1251,13 +1252,14 @@ void pnm_build(pnm_ctx* ctx, int nsys, const int* Ns, const int* Zs, const doubl
       k_v_hhhh<<<nchs, 128, 0, s>>>(S.ch_begin, D.ch_hh_off, D.ch_nhh, D.ch_vhh_off, D.hh_pair,
                                     D.nvec, D.lut + S.lut_off, D.v_hhhh);
     CUDA_TRY(cudaGetLastError());
-    // pairs containing each state
-    int* cnt = dalloc<int>(S.nsp, X.owned, s);
+    // pairs containing each state (counted for every system, copied back once below)
     int ob = (S.nsp * 32 + 255) / 256;
     k_occ<<<ob, 256, 0, s>>>(0, D.nvec, S.sp_off, S.N, S.nsp, S.m, S.M, S.species, X.key2ch, S.ch_begin,
-                             D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, cnt, nullptr, nullptr);
-    std::vector<int> hc = d2h(cnt, S.nsp, s);
-    for (int p = 0; p < S.nsp; p++) h_occ_off[S.sp_off + p + 1] = h_occ_off[S.sp_off + p] + hc[p];
+                             D.ch_hh_off, D.ch_pp_off, X.pos_hh, X.pos_pp, occ_cnt + S.sp_off, nullptr, nullptr);
+  }
+  {
+    const std::vector<int> hc = d2h(occ_cnt, nsp_total, s);
+    for (int p = 0; p < nsp_total; p++) h_occ_off[p + 1] = h_occ_off[p] + hc[p];
   }
   h2d(D.occ_off, h_occ_off, s);
   D.occ_idx = dalloc<int>(h_occ_off[nsp_total], ctx->owned, s);
