@@ -442,6 +442,8 @@ def rank_densities(rhos, rank):
     1 + 0.01 r.  The held-out densities differ by factors of 1.5 or more, so the ranks' sets
     are disjoint up to rank 49, and every replica does the work of a batch of the same shape
     (weak scaling: N replicas solve N different batches)."""
+    if rank == 0:
+        return list(rhos)
     f = 1.0 + RANK_RHO_STEP * rank
     return [round(r * f, 12) for r in rhos]
 
